@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 linear elliptical slice sampler.
+
+Metric: chain-iterations per second at d = 1000, m = 2000, 8192 chains (the
+unit-norm Gaussian polytope family, b ~ U[0.05, 0.5], X0 = 0), for the mixed
+form (BF16x3 tensor-core GEMM, FP32 step, FP64 checks) -- the headline value --
+and the plain FP64 form, each with its roofline fraction.
+
+A "step" is one pass of the whole hot path over all chains: nu draw, q = A nu,
+roots + sort + sweep + theta draw + move (+ the A x refresh every refresh_k
+steps, at its natural frequency).  Inputs are resident in HBM when the timed
+region starts; the per-step working set (~300 MB) exceeds the 126 MB L2, so no
+explicit flush is needed.  Timing: W warm-up steps, then K steps bracketed by
+CUDA events on the run's stream (barrier + synchronize on both sides, max over
+ranks).  Under torchrun each rank runs its own 8192 chains (weak scaling, no
+collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ESS chain-iter/s at d=1000,m=2000,8192 chains: mixed vs FP64, % of roofline"
+UNIT = "chain-iter/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--chains", type=int, default=8192)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"],
+                "bf16_tflops_sustained": p.get("bf16_tflops_sustained", p["bf16_tflops"]),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "source": "fallback"}
+
+
+# FP64 FMA throughput of this GB300 pool, measured with a DFMA microbenchmark
+# (8 independent FMA chains per thread, 8 CTAs of 256 threads per SM).
+FP64_TFLOPS_MEASURED = 1.19
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.25)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def source_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2407_10449_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel_key, src_hash):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current source of that kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            # | kernel_key | src_hash | dram bytes per launch | ... |
+            parts = [p.strip() for p in line.strip().strip("|").split("|")]
+            if len(parts) >= 3 and parts[0] == kernel_key and parts[1] == src_hash:
+                try:
+                    return float(parts[2])
+                except ValueError:
+                    return None
+    return None
+
+
+def phase_rooflines(inst, n_chains, timing, precision, peaks):
+    """Achieved vs peak for each phase of the timed region (per launch)."""
+    d, m, C = inst.d, inst.m, n_chains
+    mixed = precision == "mixed"
+    esz = 4 if mixed else 8
+    out = {}
+    for phase, t in timing.items():
+        if t["launches"] == 0 or t["ms"] <= 0:
+            continue
+        ms = t["ms"] / t["launches"]
+        if phase == "gemm":
+            if mixed:
+                flops = 3 * 2.0 * m * d * C  # three BF16 products issued
+                peak = peaks["bf16_tflops_sustained"]
+                out[phase] = dict(bound="tensor", unit="TFLOP/s", achieved=flops / ms / 1e9,
+                                  peak=peak, work_per_launch=flops, useful_flops=flops / 3)
+            else:
+                flops = 2.0 * m * d * C
+                out[phase] = dict(bound="fp64", unit="TFLOP/s", achieved=flops / ms / 1e9,
+                                  peak=FP64_TFLOPS_MEASURED, work_per_launch=flops)
+        elif phase == "refresh":
+            flops = 2.0 * m * d * C
+            out[phase] = dict(bound="fp64", unit="TFLOP/s", achieved=flops / ms / 1e9,
+                              peak=FP64_TFLOPS_MEASURED, work_per_launch=flops)
+        elif phase == "chain":
+            # read p, q (m each), write p; read x, nu, write x (d each)
+            byts = float(C) * esz * (3 * m + 3 * d)
+            out[phase] = dict(bound="hbm", unit="GB/s", achieved=byts / ms / 1e6,
+                              peak=peaks["hbm_gbs"], work_per_launch=byts)
+        elif phase == "draw":
+            byts = float(C) * d * (esz + (4 if mixed else 0))  # nu (+ bf16 hi/lo)
+            out[phase] = dict(bound="hbm", unit="GB/s", achieved=byts / ms / 1e6,
+                              peak=peaks["hbm_gbs"], work_per_launch=byts)
+        out[phase]["ms_per_launch"] = ms
+        out[phase]["launches"] = t["launches"]
+        out[phase]["share"] = t["ms"] / sum(v["ms"] for v in timing.values())
+        out[phase]["frac"] = out[phase]["achieved"] / out[phase]["peak"]
+    return out
+
+
+def time_form(ess, torch, inst, precision, n_chains, steps, warmup, seed, world, rank,
+              clocks=None):
+    prec = ess.ESS_PREC_MIXED if precision == "mixed" else ess.ESS_PREC_FP64
+    s = ess.Sampler(inst.A, inst.b, precision=prec)
+    stream = torch.cuda.Stream()
+    X = torch.zeros((n_chains, inst.d), dtype=torch.float64, device="cuda")
+    ess.ess_chains_init(s.state, X, n_chains, 0, stream)
+    ess.ess_chains_step(s.state, warmup, seed, stream=stream)
+    ess.ess_chains_get(s.state, None, stream)
+    ess.ess_reset_timing(s.state)
+    ess.ess_set_timing(s.state, True)
+    s.reset_stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    e0.record(stream)
+    ess.ess_chains_step(s.state, steps, seed, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    clk = clocks.stop() if clocks else None
+    torch.cuda.synchronize()
+    barrier(world)
+    ess.ess_chains_get(s.state, None, stream)
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(world, ms)
+    timing = ess.ess_get_timing(s.state)
+    stats = s.stats()
+    s.close()
+    return ms_max, timing, stats, clk
+
+
+def time_e2e(ess, torch, inst, n_chains, steps, seed, record_every=10):
+    """One user call through the C ABI with host buffers: pinned X0 in, K steps,
+    samples (every record_every steps) and final states out."""
+    s = ess.Sampler(inst.A, inst.b, precision=ess.ESS_PREC_MIXED)
+    X = torch.zeros((n_chains, inst.d), dtype=torch.float64).pin_memory()
+    n_rec = steps // record_every
+    S = torch.zeros((n_chains, max(n_rec, 1), inst.d), dtype=torch.float32).pin_memory()
+    Xn = X.numpy()
+    # warm-up call (module load, work buffers)
+    ess.ess_run_host(s.state, Xn, n_chains, 0, 2, seed, S.numpy(), 1 if n_rec else 0)
+    X.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ess.ess_run_host(s.state, Xn, n_chains, 0, steps, seed, S.numpy(),
+                     record_every if n_rec else 0)
+    dt = time.perf_counter() - t0
+    s.close()
+    h2d = n_chains * inst.d * 8
+    d2h = n_chains * inst.d * 8 + n_rec * n_chains * inst.d * 4
+    return {"value": n_chains * steps / dt, "unit": UNIT,
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "seconds": dt, "call": "ess_run_host", "record_every": record_every}
+
+
+def cpu_baseline(inst_small_fn, n_chains=256, n_iter=4):
+    """The FP64 oracle, as it stands, on the host cores (bounded sample)."""
+    import oracle
+    inst = inst_small_fn(n_chains)
+    cores = os.cpu_count() or 1
+    oracle.run(inst.A, inst.b, inst.X0[:cores], 1, seed=0, n_threads=cores)  # warm-up
+    t0 = time.perf_counter()
+    oracle.run(inst.A, inst.b, inst.X0, n_iter, seed=0, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n_chains * n_iter / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_chains} chains x {n_iter} steps of the d=1000, m=2000 workload "
+                      f"({dt:.1f} s wall)"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    import workloads
+    per_step = 128
+    inst = workloads.metric(n_chains=per_step)
+    cores = os.cpu_count() or 1
+    X = inst.X0.copy()
+    for w in range(args.warmup):
+        X, _, _ = oracle.run(inst.A, inst.b, X, 1, seed=args.seed, t0=w, n_threads=cores)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        X, _, _ = oracle.run(inst.A, inst.b, X, 1, seed=args.seed, t0=args.warmup + k,
+                             n_threads=cores)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "metric_d1000_m2000", "d": 1000, "m": 2000,
+                       "chains_per_step": per_step, "note": "FP64 CPU oracle, bounded sample"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} chains per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.warmup < 3:
+        print("warm-up must be >= 3 steps", file=sys.stderr)
+        return 2
+    import torch
+    import paper_2407_10449_gb300 as ess
+    import workloads
+
+    world, rank, local = dist_setup(args.gpus)
+    peaks = load_peaks()
+    C = args.chains
+    inst = workloads.metric(n_chains=1)
+    seed = args.seed + 1000003 * rank
+
+    clocks = ClockSampler(local) if rank == 0 else None
+    ms, timing, stats, clk = time_form(ess, torch, inst, "mixed", C, args.steps, args.warmup,
+                                       seed, world, rank, clocks)
+    value = world * C * args.steps / (ms / 1e3)
+    ms64, timing64, stats64, _ = time_form(ess, torch, inst, "fp64", C, args.fp64_steps, 3, seed,
+                                           world, rank, None)
+    value64 = world * C * args.fp64_steps / (ms64 / 1e3)
+
+    if rank != 0:
+        barrier(world)
+        return 0
+
+    roof = phase_rooflines(inst, C, timing, "mixed", peaks)
+    roof64 = phase_rooflines(inst, C, timing64, "fp64", peaks)
+    dominant = max(roof, key=lambda k: roof[k]["share"])
+    dom = roof[dominant]
+    kernel_src = {"gemm": ("k_gemm_tc.cu",), "chain": ("k_chain.cu",), "draw": ("k_draw.cu",),
+                  "refresh": ("k_gemm_f64.cu",)}
+    src = source_hash(*kernel_src[dominant])
+    traffic = ncu_traffic(f"{dominant}_mixed", src)
+    roofline = {"bound": dom["bound"], "kernel": dominant, "achieved": dom["achieved"],
+                "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"],
+                "traffic": traffic, "work_per_launch": dom["work_per_launch"],
+                "peak_source": peaks["source"] if dom["bound"] in ("hbm", "tensor") else
+                "DFMA microbenchmark on this pool"}
+    launches = sum(t["launches"] for t in timing.values())
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = time_e2e(ess, torch, inst, C, args.steps, seed)
+    cpu = None
+    if not args.no_cpu and world >= 1:
+        cpu = cpu_baseline(lambda n: workloads.metric(n_chains=n))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3", "data": "synthetic",
+        "config": {"workload": "metric_d1000_m2000_c8192", "d": 1000, "m": 2000,
+                   "chains_per_gpu": C, "precision": "mixed", "refresh_k": 32,
+                   "l2": "working set per step ~300 MB > 126 MB L2 (no flush needed)",
+                   "parallelism": f"replicas{world}"},
+        "fp64": {"value": value64, "unit": UNIT, "steps": args.fp64_steps,
+                 "ms_per_step": ms64 / args.fp64_steps, "dtype": "f64",
+                 "phases": roof64, "stats": stats64},
+        "roofline": roofline,
+        "phases": roof,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "gpu_launches": launches,
+        "stats": stats,
+    }
+    print(json.dumps(line), flush=True)
+    barrier(world)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

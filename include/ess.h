@@ -1,0 +1,256 @@
+/*
+ * ess.h -- C ABI of the GB300 linear elliptical slice sampler.
+ *
+ * Samples x ~ N(0, I_d) restricted to the polytope D = {x : A x <= b},
+ * A of shape m x d (Wu & Gardner, arXiv 2407.10449, Sec. 1), by running many
+ * independent elliptical-slice chains (Alg. 1).  Each chain step:
+ *   1. draws nu ~ N(0, I_d)                                  (Alg. 1)        
+ *   2. forms q = A nu for all chains (one GEMM) and carries p = A x as
+ *      p cos(theta) + q sin(theta), refreshed every refresh_k steps
+ *   3. solves a_i.x cos(theta) + a_i.nu sin(theta) = b_i in closed form
+ *      (Eq. trigonometry-equation, App. B) with the Sec. 3.2 edge cases
+ *   4. builds the active intervals I_act by sorting the left endpoints and a
+ *      cumulative max of the right endpoints (Alg. 3, Prop. 1)
+ *   5. draws theta uniformly on I_act                        (Alg. 1)        
+ *   6. moves x <- x cos(theta) + nu sin(theta)                (Alg. 1)        
+ *      and rejects an infeasible move (Sec. 3.3).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are dense and row-major.  "device" pointers are CUDA global
+ *     memory of the current device; "host" pointers are ordinary CPU memory.
+ *   - The library never takes ownership of caller memory; ess_create copies
+ *     A and b.  Work buffers belong to the ess_state and are freed by
+ *     ess_destroy.
+ *   - Every function returns an ess_status.  On failure ess_last_error()
+ *     returns a human-readable message for the calling thread.  No function
+ *     aborts the process or traps the GPU.
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued on that stream; the call returns
+ *     after the work is complete only where stated.
+ */
+#ifndef ESS_GB300_H
+#define ESS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ess_state ess_state;
+
+typedef enum {
+    ESS_OK = 0,
+    ESS_ERR_ARG = 1,            /* bad size, NULL pointer, NaN/Inf input */
+    ESS_ERR_INFEASIBLE_X0 = 2,  /* a start point violates A x <= b (Alg. 1 needs x0 in D) */
+    ESS_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    ESS_ERR_NUMERIC = 4,        /* NaN/Inf appeared in theta or x on the device */
+    ESS_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+    ESS_ERR_OOM = 6,            /* device allocation failed */
+    ESS_ERR_UNSUPPORTED = 7     /* size or mode outside what the kernels support */
+} ess_status;
+
+typedef enum {
+    ESS_PREC_FP64 = 0,          /* every step in double precision */
+    ESS_PREC_MIXED = 1          /* q = A nu by BF16x3 tensor cores, FP32 step,
+                                   FP64 near-tangent arccos, A x refresh and
+                                   feasibility residual */
+} ess_precision;
+
+typedef enum {
+    ESS_REFRESH_FP64 = 0,       /* p = A x with FP64 fused multiply-adds */
+    ESS_REFRESH_SPLIT = 1       /* p = A x exactly on BF16 tensor cores with an
+                                   error-free fixed-point split, rounded once */
+} ess_refresh_mode;
+
+typedef struct {
+    int precision;              /* ess_precision; default ESS_PREC_FP64 */
+    int refresh_k;              /* p = A x recomputed when t % refresh_k == 0;
+                                   default 32; 1 = every step */
+    int refresh_mode;           /* ess_refresh_mode; default ESS_REFRESH_FP64 */
+    double tangent_thresh;      /* mixed form: arccos argument b/r evaluated in
+                                   FP64 when |b/r| > 1 - tangent_thresh;
+                                   default 1e-4 */
+    double trim_eps;            /* Sec. 3.3 trimming of constraint endpoints
+                                   (radians); default 0 */
+    double residual_margin;     /* rows with p_i > b_i - residual_margin*||a_i||
+                                   get their residual a_i.x - b_i recomputed in
+                                   FP64; default 1e-8 (FP64 form), 2e-3 (mixed) */
+    int sort_threads;           /* threads per chain for the sort; 0 = auto */
+    int reserved[8];
+} ess_config;
+
+typedef struct {
+    long long steps;            /* chain-steps executed */
+    long long rejections;       /* Sec. 3.3 safeguard rejections */
+    long long residual_rechecks;/* rows whose FP64 residual was recomputed */
+    long long tangent_fp64;     /* near-tangent roots evaluated in FP64 */
+    double max_refresh_drift;   /* max |p_carried - p_refresh| / ||a_i|| seen */
+    double max_residual;        /* max a_i.x - b_i over emitted iterates (rechecked rows) */
+    long long numeric_errors;   /* chains that produced NaN/Inf */
+} ess_stats;
+
+/* Fills cfg with the defaults above for the given precision. */
+ess_status ess_default_config(int precision, ess_config *cfg);
+
+/*
+ * Creates a sampler for D = {x in R^d : A x <= b} (Sec. 1).
+ *   A    host, m x d row-major doubles; copied.
+ *   b    host, m doubles; copied.
+ *   cfg  NULL for ess_default_config(ESS_PREC_FP64).
+ *   out  receives the new state.
+ * Errors: ESS_ERR_ARG for d < 1, m < 1, NULL pointers or non-finite entries;
+ * ESS_ERR_UNSUPPORTED for m or d beyond the kernels' limits (see
+ * ess_limits); ESS_ERR_OOM / ESS_ERR_CUDA for device failures.
+ */
+ess_status ess_create(const double *A, const double *b, int d, int m,
+                      const ess_config *cfg, ess_state **out);
+
+/* Releases the state and all its device memory.  NULL is ignored. */
+void ess_destroy(ess_state *state);
+
+/* Largest supported m and d for the state's precision. */
+ess_status ess_limits(const ess_state *state, int *max_m, int *max_d);
+
+/*
+ * Runs n_chains independent chains for n_iter steps (Alg. 1 loop).
+ *   X          device, n_chains x d doubles, in/out: start points on entry
+ *              (each must satisfy A x <= b), states after the last step on
+ *              return.
+ *   t0         global index of the first step (chains are reproducible:
+ *              the draws of chain c at step t depend only on (seed, c, t));
+ *              a run split at a multiple of refresh_k reproduces the unsplit
+ *              run bit for bit.
+ *   seed       Philox4x32-10 key.
+ *   samples    device or NULL; if record_every > 0, receives the state after
+ *              every record_every-th step: n_chains x (n_iter / record_every)
+ *              x d elements, double for ESS_PREC_FP64, float for
+ *              ESS_PREC_MIXED.
+ *   cuda_stream  stream for all device work.
+ * Synchronous: returns after the work completes (status words are read
+ * back).  Errors: ESS_ERR_INFEASIBLE_X0 if a start point is infeasible in
+ * FP64; ESS_ERR_NUMERIC if a chain produced NaN/Inf; ESS_ERR_ARG for bad
+ * sizes.
+ */
+ess_status ess_run(ess_state *state, double *X, int n_chains, int t0, int n_iter,
+                   uint64_t seed, void *samples, int record_every, void *cuda_stream);
+
+/*
+ * The three stages of ess_run, for callers that keep the chains on the device
+ * across calls (e.g. to time or graph-capture the steps):
+ *   ess_chains_init  copies n_chains start points X (device doubles) into the
+ *                    state, checks them in FP64 (ESS_ERR_INFEASIBLE_X0) and
+ *                    computes p = A x; the next step has global index t0.
+ *                    Synchronous.
+ *   ess_chains_step  enqueues n_iter steps of the loaded chains on the stream
+ *                    and returns without waiting (samples as in ess_run).
+ *                    Device-side errors surface in the next ess_chains_get.
+ *   ess_chains_get   copies the current states to X (device doubles, may be
+ *                    NULL) and reports device-side errors.  Synchronous.
+ * ess_step_with_draws and ess_products reuse the work buffers and unload the
+ * chains.
+ */
+ess_status ess_chains_init(ess_state *state, const double *X, int n_chains, int t0,
+                           void *cuda_stream);
+ess_status ess_chains_step(ess_state *state, int n_iter, uint64_t seed, void *samples,
+                           int record_every, void *cuda_stream);
+ess_status ess_chains_get(ess_state *state, double *X, void *cuda_stream);
+
+/* Same as ess_run with X and samples in HOST memory: copies X to the device,
+ * runs, and copies the final states (and samples) back. */
+ess_status ess_run_host(ess_state *state, double *X_host, int n_chains, int t0, int n_iter,
+                        uint64_t seed, void *samples_host, int record_every,
+                        void *cuda_stream);
+
+/*
+ * One chain step with caller-supplied draws (for testing the step map in
+ * isolation from the random number generator).
+ *   X          device, n_chains x d doubles: current states (must be feasible).
+ *   nu         device, n_chains x d doubles: the Gaussian directions.
+ *   u          device, n_chains doubles in [0, 1): the theta draw.
+ *   X_next     device, n_chains x d doubles: next states.
+ *   theta      device or NULL, n_chains doubles.
+ *   pieces     device or NULL, n_chains x max_pieces x 2 doubles: the
+ *              positive-length pieces [lo, hi] of I_act (after trimming) in
+ *              ascending order.
+ *   n_pieces   device or NULL, n_chains ints: number of pieces (may exceed
+ *              max_pieces; only the first max_pieces are written).
+ *   rejected   device or NULL, n_chains ints: 1 if the Sec. 3.3 safeguard
+ *              rejected the move.
+ * In the mixed form X and nu are rounded to float first, exactly as a run
+ * stores them.  p = A x is computed by the refresh path.  Synchronous.
+ */
+ess_status ess_step_with_draws(ess_state *state, const double *X, const double *nu,
+                               const double *u, int n_chains, double *X_next,
+                               double *theta, double *pieces, int max_pieces,
+                               int *n_pieces, int *rejected, void *cuda_stream);
+
+/*
+ * The products the step uses, as the state computes them (for verification):
+ * p = A x by the refresh path and q = A nu by the step's GEMM (FP64 FMAs in
+ * the FP64 form, the BF16x3 tensor-core GEMM in the mixed form).
+ *   X, nu   device, n_chains x d doubles (rounded to float first in the mixed
+ *           form, as a run stores them).
+ *   P, Q    device, n_chains x m doubles; either may be NULL.
+ * Synchronous.  Reference: Sec. 2.2 (the cached A x and A nu).
+ */
+ess_status ess_products(ess_state *state, const double *X, const double *nu, int n_chains,
+                        double *P, double *Q, void *cuda_stream);
+
+/*
+ * Philox4x32-10 (Salmon et al., SC'11) as used for all draws, exposed for
+ * verification: out[4*i .. 4*i+3] is the block for counter
+ * (n_i, chain, t, (problem << 8) | stream) with n_i = i, i < n_blocks.
+ * out is device memory (n_blocks x 4 uint32).
+ */
+ess_status ess_philox_blocks(uint64_t seed, uint32_t chain, uint32_t t, uint32_t problem,
+                             uint32_t stream, int n_blocks, uint32_t *out, void *cuda_stream);
+
+/* The normals nu of chains [0, n_chains) at step t, as a run draws them:
+ * device n_chains x d, double (FP64 form) or float (mixed form). */
+ess_status ess_draw_normals(const ess_state *state, int n_chains, int t, uint64_t seed,
+                            void *out, void *cuda_stream);
+
+/*
+ * Per-phase device time of ess_chains_step (and ess_run), measured with CUDA
+ * events on the run's stream when enabled.  Phases: ESS_PHASE_DRAW (nu),
+ * ESS_PHASE_GEMM (q = A nu), ESS_PHASE_CHAIN (roots, sort, sweep, theta,
+ * move), ESS_PHASE_REFRESH (p = A x).  ess_get_timing fills up to n_phases
+ * entries of ms (total milliseconds) and launches (kernel launches) and
+ * synchronizes the device.  Timing is off by default.
+ */
+#define ESS_PHASE_DRAW 0
+#define ESS_PHASE_GEMM 1
+#define ESS_PHASE_CHAIN 2
+#define ESS_PHASE_REFRESH 3
+#define ESS_N_PHASES 4
+ess_status ess_set_timing(ess_state *state, int enable);
+ess_status ess_get_timing(ess_state *state, double *ms, long long *launches, int n_phases);
+ess_status ess_reset_timing(ess_state *state);
+
+/* Accumulated statistics since create or the last ess_reset_stats. */
+ess_status ess_get_stats(const ess_state *state, ess_stats *out);
+ess_status ess_reset_stats(ess_state *state);
+
+/*
+ * App. A change of variables for N(mu, Sigma) with Sigma = L L^T, host side:
+ *   A_out = A L (m x d), b_out = b - A mu (m).  mu may be NULL (zero).
+ * Sampling u under A_out u <= b_out and mapping x = L u + mu samples the
+ * truncation of N(mu, Sigma) by A x <= b.
+ */
+ess_status ess_whiten(const double *A, const double *b, const double *mu, const double *L,
+                      int d, int m, double *A_out, double *b_out);
+
+/* x = L u + mu for each of the n rows of U (host, n x d); mu may be NULL. */
+ess_status ess_unwhiten(const double *L, const double *mu, int d, int n, const double *U,
+                        double *X);
+
+/* Message describing the last failure of the calling thread ("" if none). */
+const char *ess_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ESS_GB300_H */

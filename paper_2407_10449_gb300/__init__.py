@@ -1,0 +1,363 @@
+"""Python binding of the GB300 linear elliptical slice sampler (C ABI in include/ess.h).
+
+Argument marshalling only: every step of the sampler runs in the CUDA
+kernels of ``libess_gb300.so``.  Device buffers are torch CUDA tensors, passed
+by pointer; streams are torch streams.  The library is built in-tree with
+``paper_2407_10449_gb300.build``; if it is missing, loading fails loudly --
+there is no CPU path.
+
+The names mirror the C entry points (``ess_create``, ``ess_run``,
+``ess_step_with_draws``, ...).  ``Sampler`` is a thin object wrapper.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+ESS_OK = 0
+ESS_ERR_ARG = 1
+ESS_ERR_INFEASIBLE_X0 = 2
+ESS_ERR_CUDA = 3
+ESS_ERR_NUMERIC = 4
+ESS_ERR_TIMEOUT = 5
+ESS_ERR_OOM = 6
+ESS_ERR_UNSUPPORTED = 7
+
+ESS_PREC_FP64 = 0
+ESS_PREC_MIXED = 1
+ESS_REFRESH_FP64 = 0
+ESS_REFRESH_SPLIT = 1
+
+_STATUS_NAMES = {0: "ESS_OK", 1: "ESS_ERR_ARG", 2: "ESS_ERR_INFEASIBLE_X0", 3: "ESS_ERR_CUDA",
+                 4: "ESS_ERR_NUMERIC", 5: "ESS_ERR_TIMEOUT", 6: "ESS_ERR_OOM",
+                 7: "ESS_ERR_UNSUPPORTED"}
+
+# every symbol include/ess.h declares
+EXPORTED = ("ess_default_config", "ess_create", "ess_destroy", "ess_limits", "ess_run",
+            "ess_chains_init", "ess_chains_step", "ess_chains_get", "ess_run_host", "ess_step_with_draws", "ess_products", "ess_philox_blocks",
+            "ess_draw_normals",
+            "ess_set_timing", "ess_get_timing", "ess_reset_timing",
+            "ess_get_stats", "ess_reset_stats", "ess_whiten", "ess_unwhiten", "ess_last_error")
+
+PHASES = ("draw", "gemm", "chain", "refresh")
+
+
+class EssError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class ess_config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("refresh_k", ctypes.c_int),
+                ("refresh_mode", ctypes.c_int), ("tangent_thresh", ctypes.c_double),
+                ("trim_eps", ctypes.c_double), ("residual_margin", ctypes.c_double),
+                ("sort_threads", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+
+
+class ess_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("rejections", ctypes.c_longlong),
+                ("residual_rechecks", ctypes.c_longlong), ("tangent_fp64", ctypes.c_longlong),
+                ("max_refresh_drift", ctypes.c_double), ("max_residual", ctypes.c_double),
+                ("numeric_errors", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Loads libess_gb300.so (building it first if asked and needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB_PATH
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; build it with "
+                               "paper_2407_10449_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        c_int, c_u64, c_u32 = ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32
+        sig = {
+            "ess_default_config": ([c_int, ctypes.POINTER(ess_config)], c_int),
+            "ess_create": ([_dp, _dp, c_int, c_int, ctypes.POINTER(ess_config),
+                            ctypes.POINTER(_vp)], c_int),
+            "ess_destroy": ([_vp], None),
+            "ess_limits": ([_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)], c_int),
+            "ess_run": ([_vp, _vp, c_int, c_int, c_int, c_u64, _vp, c_int, _vp], c_int),
+            "ess_chains_init": ([_vp, _vp, c_int, c_int, _vp], c_int),
+            "ess_chains_step": ([_vp, c_int, c_u64, _vp, c_int, _vp], c_int),
+            "ess_chains_get": ([_vp, _vp, _vp], c_int),
+            "ess_run_host": ([_vp, _vp, c_int, c_int, c_int, c_u64, _vp, c_int, _vp], c_int),
+            "ess_step_with_draws": ([_vp, _vp, _vp, _vp, c_int, _vp, _vp, _vp, c_int, _vp, _vp,
+                                     _vp], c_int),
+            "ess_products": ([_vp, _vp, _vp, c_int, _vp, _vp, _vp], c_int),
+            "ess_philox_blocks": ([c_u64, c_u32, c_u32, c_u32, c_u32, c_int, _vp, _vp], c_int),
+            "ess_draw_normals": ([_vp, c_int, c_int, c_u64, _vp, _vp], c_int),
+            "ess_set_timing": ([_vp, c_int], c_int),
+            "ess_get_timing": ([_vp, _vp, _vp, c_int], c_int),
+            "ess_reset_timing": ([_vp], c_int),
+            "ess_get_stats": ([_vp, ctypes.POINTER(ess_stats)], c_int),
+            "ess_reset_stats": ([_vp], c_int),
+            "ess_whiten": ([_dp, _dp, _dp, _dp, c_int, c_int, _dp, _dp], c_int),
+            "ess_unwhiten": ([_dp, _dp, c_int, c_int, _dp, _dp], c_int),
+            "ess_last_error": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(status):
+    if status != ESS_OK:
+        msg = load().ess_last_error()
+        raise EssError(status, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    """Device/host pointer of a torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+def _np64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ----------------------------------------------------------------- C names --
+
+def ess_default_config(precision=ESS_PREC_FP64) -> ess_config:
+    cfg = ess_config()
+    _check(load().ess_default_config(precision, ctypes.byref(cfg)))
+    return cfg
+
+
+def ess_create(A, b, cfg: ess_config | None = None):
+    A = _np64(A)
+    b = _np64(b)
+    m, d = A.shape
+    st = _vp()
+    _check(load().ess_create(A.ctypes.data_as(_dp), b.ctypes.data_as(_dp), d, m,
+                             ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(st)))
+    return st
+
+
+def ess_destroy(state):
+    load().ess_destroy(state)
+
+
+def ess_limits(state):
+    mm, md = ctypes.c_int(), ctypes.c_int()
+    _check(load().ess_limits(state, ctypes.byref(mm), ctypes.byref(md)))
+    return mm.value, md.value
+
+
+def ess_run(state, X, n_chains, t0, n_iter, seed, samples=None, record_every=0, stream=None):
+    _check(load().ess_run(state, _ptr(X), n_chains, t0, n_iter, seed, _ptr(samples), record_every,
+                          _stream_ptr(stream)))
+
+
+def ess_chains_init(state, X, n_chains, t0=0, stream=None):
+    _check(load().ess_chains_init(state, _ptr(X), n_chains, t0, _stream_ptr(stream)))
+
+
+def ess_chains_step(state, n_iter, seed, samples=None, record_every=0, stream=None):
+    _check(load().ess_chains_step(state, n_iter, seed, _ptr(samples), record_every,
+                                  _stream_ptr(stream)))
+
+
+def ess_chains_get(state, X=None, stream=None):
+    _check(load().ess_chains_get(state, _ptr(X), _stream_ptr(stream)))
+
+
+def ess_run_host(state, X, n_chains, t0, n_iter, seed, samples=None, record_every=0, stream=None):
+    _check(load().ess_run_host(state, _ptr(X), n_chains, t0, n_iter, seed, _ptr(samples),
+                               record_every, _stream_ptr(stream)))
+
+
+def ess_step_with_draws(state, X, nu, u, n_chains, X_next, theta=None, pieces=None, max_pieces=0,
+                        n_pieces=None, rejected=None, stream=None):
+    _check(load().ess_step_with_draws(state, _ptr(X), _ptr(nu), _ptr(u), n_chains, _ptr(X_next),
+                                      _ptr(theta), _ptr(pieces), max_pieces, _ptr(n_pieces),
+                                      _ptr(rejected), _stream_ptr(stream)))
+
+
+def ess_products(state, X, nu, n_chains, P=None, Q=None, stream=None):
+    _check(load().ess_products(state, _ptr(X), _ptr(nu), n_chains, _ptr(P), _ptr(Q),
+                               _stream_ptr(stream)))
+
+
+def ess_philox_blocks(seed, chain, t, problem, stream_id, n_blocks, out, stream=None):
+    _check(load().ess_philox_blocks(seed, chain, t, problem, stream_id, n_blocks, _ptr(out),
+                                    _stream_ptr(stream)))
+
+
+def ess_draw_normals(state, n_chains, t, seed, out, stream=None):
+    _check(load().ess_draw_normals(state, n_chains, t, seed, _ptr(out), _stream_ptr(stream)))
+
+
+def ess_set_timing(state, enable=True):
+    _check(load().ess_set_timing(state, 1 if enable else 0))
+
+
+def ess_get_timing(state) -> dict:
+    ms = np.zeros(len(PHASES), dtype=np.float64)
+    n = np.zeros(len(PHASES), dtype=np.int64)
+    _check(load().ess_get_timing(state, ms.ctypes.data, n.ctypes.data, len(PHASES)))
+    return {p: {"ms": float(ms[i]), "launches": int(n[i])} for i, p in enumerate(PHASES)}
+
+
+def ess_reset_timing(state):
+    _check(load().ess_reset_timing(state))
+
+
+def ess_get_stats(state) -> dict:
+    s = ess_stats()
+    _check(load().ess_get_stats(state, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def ess_reset_stats(state):
+    _check(load().ess_reset_stats(state))
+
+
+def ess_whiten(A, b, mu, L):
+    A = _np64(A)
+    b = _np64(b)
+    L = _np64(L)
+    m, d = A.shape
+    mu_p = None if mu is None else _np64(mu)
+    A_out = np.zeros((m, d))
+    b_out = np.zeros(m)
+    _check(load().ess_whiten(A.ctypes.data_as(_dp), b.ctypes.data_as(_dp),
+                             None if mu_p is None else mu_p.ctypes.data_as(_dp),
+                             L.ctypes.data_as(_dp), d, m, A_out.ctypes.data_as(_dp),
+                             b_out.ctypes.data_as(_dp)))
+    return A_out, b_out
+
+
+def ess_unwhiten(L, mu, U):
+    L = _np64(L)
+    U = _np64(U)
+    if U.ndim == 1:
+        U = U.reshape(1, -1)
+    n, d = U.shape
+    mu_p = None if mu is None else _np64(mu)
+    X = np.zeros((n, d))
+    _check(load().ess_unwhiten(L.ctypes.data_as(_dp),
+                               None if mu_p is None else mu_p.ctypes.data_as(_dp), d, n,
+                               U.ctypes.data_as(_dp), X.ctypes.data_as(_dp)))
+    return X
+
+
+def ess_last_error() -> str:
+    msg = load().ess_last_error()
+    return msg.decode() if msg else ""
+
+
+# ------------------------------------------------------------ convenience --
+
+class Sampler:
+    """Owns an ess_state for D = {x : A x <= b}; X lives in torch CUDA tensors."""
+
+    def __init__(self, A, b, precision=ESS_PREC_FP64, **cfg_overrides):
+        cfg = ess_default_config(precision)
+        for k, v in cfg_overrides.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        self.A = _np64(A)
+        self.b = _np64(b)
+        self.m, self.d = self.A.shape
+        self.precision = precision
+        self._state = ess_create(self.A, self.b, cfg)
+
+    def close(self):
+        if self._state is not None:
+            ess_destroy(self._state)
+            self._state = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def state(self):
+        return self._state
+
+    @property
+    def sample_dtype(self):
+        import torch
+        return torch.float64 if self.precision == ESS_PREC_FP64 else torch.float32
+
+    def run(self, X, n_iter, seed, t0=0, samples=None, record_every=0, stream=None):
+        """X: CUDA float64 tensor (n_chains x d), updated in place."""
+        n = X.shape[0]
+        ess_run(self._state, X, n, t0, n_iter, seed, samples, record_every, stream)
+        return X
+
+    def step_with_draws(self, X, nu, u, max_pieces=0, stream=None):
+        import torch
+        n = X.shape[0]
+        dev = X.device
+        X_next = torch.empty_like(X)
+        theta = torch.empty(n, dtype=torch.float64, device=dev)
+        rejected = torch.empty(n, dtype=torch.int32, device=dev)
+        n_pieces = torch.empty(n, dtype=torch.int32, device=dev)
+        pieces = None
+        if max_pieces > 0:
+            pieces = torch.zeros((n, max_pieces, 2), dtype=torch.float64, device=dev)
+        ess_step_with_draws(self._state, X, nu, u, n, X_next, theta, pieces, max_pieces, n_pieces,
+                            rejected, stream)
+        return X_next, theta, pieces, n_pieces, rejected
+
+    def products(self, X, nu, stream=None):
+        """(A x, A nu) as the state computes them; float64 CUDA tensors."""
+        import torch
+        n = X.shape[0]
+        P = torch.empty((n, self.m), dtype=torch.float64, device=X.device)
+        Q = torch.empty((n, self.m), dtype=torch.float64, device=X.device)
+        ess_products(self._state, X, nu, n, P, Q, stream)
+        return P, Q
+
+    def draw_normals(self, n_chains, t, seed):
+        import torch
+        out = torch.empty((n_chains, self.d), dtype=self.sample_dtype, device="cuda")
+        ess_draw_normals(self._state, n_chains, t, seed, out)
+        return out
+
+    def stats(self):
+        return ess_get_stats(self._state)
+
+    def reset_stats(self):
+        ess_reset_stats(self._state)

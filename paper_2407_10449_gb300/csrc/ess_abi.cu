@@ -1,0 +1,808 @@
+// ess_abi.cu -- the extern "C" entry points declared in include/ess.h.
+//
+// Host-side orchestration only: validation, device buffers owned by the
+// state, and the per-step launch sequence
+//   [refresh p = A x]  ->  draw nu  ->  q = A nu  ->  chain step
+// on the caller's stream.  All arithmetic of the step runs in the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ess.h"
+#include "ess_kernels.cuh"
+#include "ess_gemm_tc.cuh"
+
+using ess::DevStats;
+
+namespace {
+
+thread_local std::string g_err;
+
+ess_status fail(ess_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+ess_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? ESS_ERR_OOM : ESS_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define ESS_CUDA(expr)                                 \
+  do {                                                 \
+    cudaError_t e_ = (expr);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #expr); \
+  } while (0)
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return cudaSuccess;
+  return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+template <typename T>
+void dev_free(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+bool all_finite(const double* v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+struct ess_state {
+  int d = 0, m = 0;
+  ess_config cfg{};
+  int device = 0;
+  int ld_bf = 0;          // row stride of the bf16 operands (d rounded up to 8)
+  int chain_threads = 0;  // threads per chain of the step kernel
+  // constants (device)
+  double* A64 = nullptr;
+  double* b64 = nullptr;
+  double* anorm = nullptr;
+  float* b32 = nullptr;
+  __nv_bfloat16* A_hi = nullptr;
+  __nv_bfloat16* A_lo = nullptr;
+  // work buffers (device), sized for `cap` chains
+  int cap = 0;
+  void* P = nullptr;       // n x m, T
+  void* Q = nullptr;       // n x m, T
+  void* NU = nullptr;      // n x d, T
+  float* Xw = nullptr;     // n x d, mixed-form working states (the loaded chains)
+  double* Xd = nullptr;    // n x d, FP64-form working states (the loaded chains)
+  int n_loaded = 0;        // chains loaded by ess_chains_init
+  int t_next = 0;          // global index of the next step of the loaded chains
+  int p_fresh_t = -1;      // step index at which p was last recomputed from x
+  __nv_bfloat16* NU_hi = nullptr;
+  __nv_bfloat16* NU_lo = nullptr;
+  DevStats* dstats = nullptr;
+  int* dstatus = nullptr;
+  ess::TcGemmPlan* tc_plan = nullptr;  // BF16x3 tensor-core GEMM for q = A nu
+  // optional per-phase device timing (CUDA events on the run's stream)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<int, int>>> ev_pending;  // phase, (start, stop) indices
+  int ev_used = 0;
+  double phase_ms[ESS_N_PHASES] = {0};
+  long long phase_launches[ESS_N_PHASES] = {0};
+};
+
+namespace {
+
+bool mixed(const ess_state* s) { return s->cfg.precision == ESS_PREC_MIXED; }
+
+// Records an event for phase timing; returns its pool index or -1.
+int timing_mark(ess_state* s, cudaStream_t st) {
+  if (!s->timing) return -1;
+  if (s->ev_used == (int)s->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    s->ev_pool.push_back(e);
+  }
+  const int i = s->ev_used++;
+  if (cudaEventRecord(s->ev_pool[i], st) != cudaSuccess) return -1;
+  return i;
+}
+
+// Phase timing scope: events around the launches of one phase.
+struct PhaseScope {
+  ess_state* s;
+  cudaStream_t st;
+  int phase, start;
+  int launches;
+  PhaseScope(ess_state* s_, cudaStream_t st_, int phase_, int launches_ = 1)
+      : s(s_), st(st_), phase(phase_), start(timing_mark(s_, st_)), launches(launches_) {}
+  ~PhaseScope() {
+    s->phase_launches[phase] += launches;
+    if (start < 0) return;
+    const int stop = timing_mark(s, st);
+    if (stop >= 0) s->ev_pending.push_back({phase, {start, stop}});
+  }
+};
+
+// Folds the elapsed times of all recorded phases (call after a sync).
+void timing_collect(ess_state* s) {
+  for (auto& pe : s->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, s->ev_pool[pe.second.first], s->ev_pool[pe.second.second]) ==
+        cudaSuccess)
+      s->phase_ms[pe.first] += ms;
+  }
+  s->ev_pending.clear();
+  s->ev_used = 0;
+}
+size_t elem(const ess_state* s) { return mixed(s) ? sizeof(float) : sizeof(double); }
+
+void free_work(ess_state* s) {
+  if (s->P) cudaFree(s->P);
+  if (s->Q) cudaFree(s->Q);
+  if (s->NU) cudaFree(s->NU);
+  s->P = s->Q = s->NU = nullptr;
+  dev_free(s->Xw);
+  dev_free(s->Xd);
+  dev_free(s->NU_hi);
+  dev_free(s->NU_lo);
+  s->cap = 0;
+  s->n_loaded = 0;
+}
+
+ess_status ensure_capacity(ess_state* s, int n) {
+  if (n <= s->cap) return ESS_OK;
+  free_work(s);
+  const size_t e = elem(s);
+  ESS_CUDA(cudaMalloc(&s->P, (size_t)n * s->m * e));
+  ESS_CUDA(cudaMalloc(&s->Q, (size_t)n * s->m * e));
+  ESS_CUDA(cudaMalloc(&s->NU, (size_t)n * s->d * e));
+  if (mixed(s)) {
+    ESS_CUDA(dev_alloc(&s->Xw, (size_t)n * s->d));
+    ESS_CUDA(dev_alloc(&s->NU_hi, (size_t)n * s->ld_bf));
+    ESS_CUDA(dev_alloc(&s->NU_lo, (size_t)n * s->ld_bf));
+    // the padding columns d .. ld_bf - 1 stay zero
+    ESS_CUDA(cudaMemset(s->NU_hi, 0, (size_t)n * s->ld_bf * sizeof(__nv_bfloat16)));
+    ESS_CUDA(cudaMemset(s->NU_lo, 0, (size_t)n * s->ld_bf * sizeof(__nv_bfloat16)));
+  } else {
+    ESS_CUDA(dev_alloc(&s->Xd, (size_t)n * s->d));
+  }
+  s->cap = n;
+  return ESS_OK;
+}
+
+// p = A x for all chains (refresh), with optional drift statistics and the
+// FP64 feasibility check of the rounded states.
+ess_status refresh_p(ess_state* s, int n, const void* Xcur, bool with_drift, bool check,
+                     cudaStream_t st) {
+  DevStats* drift = with_drift ? s->dstats : nullptr;
+  if (mixed(s)) {
+    ESS_CUDA((ess::launch_gemm_nt_f64<float, float>(static_cast<const float*>(Xcur), s->d, s->A64,
+                                                     s->d, static_cast<float*>(s->P), s->m, n,
+                                                     s->m, s->d, s->anorm, drift, st)));
+    if (check) {
+      // feasibility of the float-rounded states, decided in FP64
+      double* P64 = nullptr;
+      ESS_CUDA(dev_alloc(&P64, (size_t)n * s->m));
+      cudaError_t e = ess::launch_gemm_nt_f64<float, double>(static_cast<const float*>(Xcur), s->d,
+                                                             s->A64, s->d, P64, s->m, n, s->m,
+                                                             s->d, s->anorm, nullptr, st);
+      if (e == cudaSuccess) e = ess::launch_check_feasible(P64, s->m, s->b64, n, s->m, s->dstatus, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      cudaFree(P64);
+      if (e != cudaSuccess) return cuda_fail(e, "feasibility check");
+    }
+  } else {
+    ESS_CUDA((ess::launch_gemm_nt_f64<double, double>(static_cast<const double*>(Xcur), s->d,
+                                                       s->A64, s->d, static_cast<double*>(s->P),
+                                                       s->m, n, s->m, s->d, s->anorm, drift, st)));
+    if (check)
+      ESS_CUDA(ess::launch_check_feasible(static_cast<const double*>(s->P), s->m, s->b64, n, s->m,
+                                          s->dstatus, st));
+  }
+  return ESS_OK;
+}
+
+// q = A nu for all chains.
+ess_status compute_q(ess_state* s, int n, cudaStream_t st) {
+  if (mixed(s)) {
+    cudaError_t e = ess::tc_gemm_bf16x3(s->tc_plan, s->NU_hi, s->NU_lo, s->ld_bf, n,
+                                        static_cast<float*>(s->Q), s->m, s->dstatus, st);
+    if (e != cudaSuccess) return cuda_fail(e, "BF16x3 tensor-core GEMM");
+  } else {
+    ESS_CUDA((ess::launch_gemm_nt_f64<double, double>(static_cast<const double*>(s->NU), s->d,
+                                                       s->A64, s->d, static_cast<double*>(s->Q),
+                                                       s->m, n, s->m, s->d, nullptr, nullptr, st)));
+  }
+  return ESS_OK;
+}
+
+const void* chain_states(const ess_state* s) {
+  return mixed(s) ? static_cast<const void*>(s->Xw) : static_cast<const void*>(s->Xd);
+}
+
+template <typename T>
+ess::ChainParams<T> base_params(ess_state* s, int n) {
+  ess::ChainParams<T> p{};
+  p.d = s->d;
+  p.m = s->m;
+  p.n_chains = n;
+  p.ldx = s->d;
+  p.ldp = s->m;
+  p.P_in = static_cast<const T*>(s->P);
+  p.P_out = static_cast<T*>(s->P);
+  p.Q = static_cast<const T*>(s->Q);
+  if constexpr (sizeof(T) == 4) p.b = reinterpret_cast<const T*>(s->b32);
+  else p.b = reinterpret_cast<const T*>(s->b64);
+  p.b64 = s->b64;
+  p.A64 = s->A64;
+  p.anorm = s->anorm;
+  p.NU = static_cast<const T*>(s->NU);
+  p.trim_eps = s->cfg.trim_eps;
+  p.tangent_thresh = s->cfg.tangent_thresh;
+  p.margin = s->cfg.residual_margin;
+  p.stats = s->dstats;
+  p.status = s->dstatus;
+  return p;
+}
+
+ess_status read_status(ess_state* s, cudaStream_t st) {
+  int h = 0;
+  ESS_CUDA(cudaMemcpyAsync(&h, s->dstatus, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ESS_CUDA(cudaStreamSynchronize(st));
+  if (h & ess::kStatusInfeasible)
+    return fail(ESS_ERR_INFEASIBLE_X0, "a chain state violates A x <= b (checked in FP64)");
+  if (h & ess::kStatusNumeric)
+    return fail(ESS_ERR_NUMERIC, "NaN or Inf in theta or x; affected chains kept their state");
+  if (h & ess::kStatusTimeout) return fail(ESS_ERR_TIMEOUT, "a bounded device wait gave up");
+  return ESS_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+ess_status ess_default_config(int precision, ess_config* cfg) {
+  if (!cfg) return fail(ESS_ERR_ARG, "cfg is NULL");
+  if (precision != ESS_PREC_FP64 && precision != ESS_PREC_MIXED)
+    return fail(ESS_ERR_ARG, "unknown precision");
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->precision = precision;
+  cfg->refresh_k = 32;
+  cfg->refresh_mode = ESS_REFRESH_FP64;
+  cfg->tangent_thresh = 1e-4;
+  cfg->trim_eps = 0.0;
+  cfg->residual_margin = precision == ESS_PREC_MIXED ? 2e-3 : 1e-8;
+  cfg->sort_threads = 0;
+  return ESS_OK;
+}
+
+ess_status ess_create(const double* A, const double* b, int d, int m, const ess_config* cfg,
+                      ess_state** out) {
+  g_err.clear();
+  if (!out) return fail(ESS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!A || !b) return fail(ESS_ERR_ARG, "A or b is NULL");
+  if (d < 1 || m < 1) return fail(ESS_ERR_ARG, "need d >= 1 and m >= 1");
+  if (!all_finite(A, (size_t)m * d) || !all_finite(b, (size_t)m))
+    return fail(ESS_ERR_ARG, "A or b has NaN/Inf entries");
+  ess_config c;
+  if (cfg) c = *cfg;
+  else ess_default_config(ESS_PREC_FP64, &c);
+  if (c.precision != ESS_PREC_FP64 && c.precision != ESS_PREC_MIXED)
+    return fail(ESS_ERR_ARG, "unknown precision");
+  if (c.refresh_k < 1) return fail(ESS_ERR_ARG, "refresh_k must be >= 1");
+  if (c.refresh_mode != ESS_REFRESH_FP64)
+    return fail(ESS_ERR_UNSUPPORTED, "only ESS_REFRESH_FP64 is implemented");
+  if (!(c.tangent_thresh >= 0.0 && c.tangent_thresh < 1.0) || !(c.trim_eps >= 0.0) ||
+      !(c.residual_margin >= 0.0))
+    return fail(ESS_ERR_ARG, "tangent_thresh in [0, 1), trim_eps >= 0, residual_margin >= 0");
+
+  const int threads = ess::chain_threads_for(m);
+  if (threads == 0)
+    return fail(ESS_ERR_UNSUPPORTED, "m exceeds the per-chain shared-memory sort limit (8192)");
+  const size_t smem = c.precision == ESS_PREC_MIXED ? ess::chain_smem_bytes<float>(threads, d)
+                                                    : ess::chain_smem_bytes<double>(threads, d);
+  int dev = 0;
+  ESS_CUDA(cudaGetDevice(&dev));
+  int smem_optin = 0;
+  ESS_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem + 1024 > (size_t)smem_optin)
+    return fail(ESS_ERR_UNSUPPORTED, "d too large for the chain-step kernel's shared memory");
+
+  ess_state* s = new ess_state();
+  s->d = d;
+  s->m = m;
+  s->cfg = c;
+  s->device = dev;
+  s->ld_bf = (d + 7) & ~7;
+  s->chain_threads = threads;
+
+  auto cleanup = [&](ess_status st) {
+    ess_destroy(s);
+    return st;
+  };
+  std::vector<double> norms(m);
+  for (int i = 0; i < m; ++i) {
+    double acc = 0.0;
+    for (int j = 0; j < d; ++j) acc += A[(size_t)i * d + j] * A[(size_t)i * d + j];
+    norms[i] = std::sqrt(acc);
+  }
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = dev_alloc(&s->A64, (size_t)m * d);
+  if (e == cudaSuccess) e = dev_alloc(&s->b64, (size_t)m);
+  if (e == cudaSuccess) e = dev_alloc(&s->anorm, (size_t)m);
+  if (e == cudaSuccess) e = cudaMemcpy(s->A64, A, sizeof(double) * m * d, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->b64, b, sizeof(double) * m, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(s->anorm, norms.data(), sizeof(double) * m, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = dev_alloc(&s->dstats, 1);
+  if (e == cudaSuccess) e = dev_alloc(&s->dstatus, 1);
+  if (e == cudaSuccess) e = cudaMemset(s->dstats, 0, sizeof(DevStats));
+  if (e == cudaSuccess) e = cudaMemset(s->dstatus, 0, sizeof(int));
+  if (e == cudaSuccess && c.precision == ESS_PREC_MIXED) {
+    std::vector<float> bf(m);
+    for (int i = 0; i < m; ++i) bf[i] = (float)b[i];
+    e = dev_alloc(&s->b32, (size_t)m);
+    if (e == cudaSuccess) e = cudaMemcpy(s->b32, bf.data(), sizeof(float) * m, cudaMemcpyHostToDevice);
+    // A rounded to float, then split into bf16 hi + lo (the GEMM operands)
+    float* A32 = nullptr;
+    if (e == cudaSuccess) e = dev_alloc(&A32, (size_t)m * d);
+    if (e == cudaSuccess) e = ess::launch_convert<double, float>(s->A64, d, A32, d, m, d, 0);
+    if (e == cudaSuccess) e = dev_alloc(&s->A_hi, (size_t)m * s->ld_bf);
+    if (e == cudaSuccess) e = dev_alloc(&s->A_lo, (size_t)m * s->ld_bf);
+    if (e == cudaSuccess)
+      e = cudaMemset(s->A_hi, 0, sizeof(__nv_bfloat16) * (size_t)m * s->ld_bf);
+    if (e == cudaSuccess)
+      e = cudaMemset(s->A_lo, 0, sizeof(__nv_bfloat16) * (size_t)m * s->ld_bf);
+    if (e == cudaSuccess) e = ess::launch_split_bf16(A32, d, s->A_hi, s->A_lo, s->ld_bf, m, d, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (A32) cudaFree(A32);
+    if (e == cudaSuccess) e = ess::tc_gemm_create(&s->tc_plan, s->A_hi, s->A_lo, s->ld_bf, m, d);
+  }
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "ess_create device setup"));
+  *out = s;
+  return ESS_OK;
+}
+
+void ess_destroy(ess_state* s) {
+  if (!s) return;
+  DeviceGuard g(s->device);
+  free_work(s);
+  dev_free(s->A64);
+  dev_free(s->b64);
+  dev_free(s->anorm);
+  dev_free(s->b32);
+  dev_free(s->A_hi);
+  dev_free(s->A_lo);
+  dev_free(s->dstats);
+  dev_free(s->dstatus);
+  ess::tc_gemm_destroy(s->tc_plan);
+  s->tc_plan = nullptr;
+  for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  delete s;
+}
+
+ess_status ess_limits(const ess_state* s, int* max_m, int* max_d) {
+  if (!s || !max_m || !max_d) return fail(ESS_ERR_ARG, "NULL argument");
+  *max_m = ess::kChainMaxThreads * ess::kChainItems;
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+  const size_t esz = mixed(s) ? sizeof(float) : sizeof(double);
+  const size_t base = mixed(s) ? ess::chain_smem_bytes<float>(s->chain_threads, 0)
+                               : ess::chain_smem_bytes<double>(s->chain_threads, 0);
+  long long room = (long long)smem_optin - 1024 - (long long)base;
+  *max_d = room > 0 ? (int)(room / (long long)esz) - 1 : 0;
+  return ESS_OK;
+}
+
+ess_status ess_chains_init(ess_state* s, const double* X, int n_chains, int t0,
+                           void* cuda_stream) {
+  g_err.clear();
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  if (n_chains < 1 || t0 < 0) return fail(ESS_ERR_ARG, "need n_chains >= 1 and t0 >= 0");
+  if (!X) return fail(ESS_ERR_ARG, "X is NULL");
+  DeviceGuard g(s->device);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  s->n_loaded = 0;
+  ess_status rc = ensure_capacity(s, n_chains);
+  if (rc != ESS_OK) return rc;
+  ESS_CUDA(cudaMemsetAsync(s->dstatus, 0, sizeof(int), st));
+  const int n = n_chains, d = s->d;
+  if (mixed(s)) ESS_CUDA((ess::launch_convert<double, float>(X, d, s->Xw, d, n, d, st)));
+  else ESS_CUDA((ess::launch_convert<double, double>(X, d, s->Xd, d, n, d, st)));
+  rc = refresh_p(s, n, chain_states(s), false, true, st);
+  if (rc != ESS_OK) return rc;
+  rc = read_status(s, st);
+  if (rc != ESS_OK) return rc;
+  s->n_loaded = n;
+  s->t_next = t0;
+  s->p_fresh_t = t0;
+  return ESS_OK;
+}
+
+ess_status ess_chains_step(ess_state* s, int n_iter, uint64_t seed, void* samples,
+                           int record_every, void* cuda_stream) {
+  g_err.clear();
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  if (n_iter < 0 || record_every < 0) return fail(ESS_ERR_ARG, "negative size");
+  if (s->n_loaded < 1) return fail(ESS_ERR_ARG, "no chains loaded (call ess_chains_init)");
+  if (record_every > 0 && !samples) return fail(ESS_ERR_ARG, "samples is NULL");
+  if ((long long)s->t_next + n_iter > 0x7fffffffLL) return fail(ESS_ERR_ARG, "step index overflow");
+  DeviceGuard g(s->device);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int n = s->n_loaded, d = s->d;
+  const int n_rec = record_every > 0 ? n_iter / record_every : 0;
+  const uint32_t k = (uint32_t)s->cfg.refresh_k;
+  for (int it = 0; it < n_iter; ++it) {
+    const uint32_t t = (uint32_t)(s->t_next + it);
+    if (t % k == 0 && (int)t != s->p_fresh_t) {
+      PhaseScope ps(s, st, ESS_PHASE_REFRESH);
+      ess_status rc = refresh_p(s, n, chain_states(s), true, false, st);
+      if (rc != ESS_OK) return rc;
+      s->p_fresh_t = (int)t;
+    }
+    const bool rec = record_every > 0 && (it + 1) % record_every == 0 &&
+                     (it + 1) / record_every <= n_rec;
+    const long long rec_off = rec ? (long long)((it + 1) / record_every - 1) * d : 0;
+    if (mixed(s)) {
+      {
+        PhaseScope ps(s, st, ESS_PHASE_DRAW);
+        ESS_CUDA(ess::launch_draw_nu_f32(static_cast<float*>(s->NU), d, s->NU_hi, s->NU_lo,
+                                         s->ld_bf, n, d, seed, t, 0u, 0u, st));
+      }
+      {
+        PhaseScope ps(s, st, ESS_PHASE_GEMM);
+        ess_status rc = compute_q(s, n, st);
+        if (rc != ESS_OK) return rc;
+      }
+      ess::ChainParams<float> p = base_params<float>(s, n);
+      p.X = s->Xw;
+      p.X_out = s->Xw;
+      p.seed = seed;
+      p.t = t;
+      if (rec) {
+        p.samples = static_cast<float*>(samples) + rec_off;
+        p.sample_stride = (long long)n_rec * d;
+      }
+      PhaseScope ps(s, st, ESS_PHASE_CHAIN);
+      ESS_CUDA(ess::launch_chain_step<float>(p, s->chain_threads, st));
+    } else {
+      {
+        PhaseScope ps(s, st, ESS_PHASE_DRAW);
+        ESS_CUDA(ess::launch_draw_nu_f64(static_cast<double*>(s->NU), n, d, d, seed, t, 0u, 0u, st));
+      }
+      {
+        PhaseScope ps(s, st, ESS_PHASE_GEMM);
+        ess_status rc = compute_q(s, n, st);
+        if (rc != ESS_OK) return rc;
+      }
+      ess::ChainParams<double> p = base_params<double>(s, n);
+      p.X = s->Xd;
+      p.X_out = s->Xd;
+      p.seed = seed;
+      p.t = t;
+      if (rec) {
+        p.samples = static_cast<double*>(samples) + rec_off;
+        p.sample_stride = (long long)n_rec * d;
+      }
+      PhaseScope ps(s, st, ESS_PHASE_CHAIN);
+      ESS_CUDA(ess::launch_chain_step<double>(p, s->chain_threads, st));
+    }
+  }
+  s->t_next += n_iter;
+  return ESS_OK;
+}
+
+ess_status ess_chains_get(ess_state* s, double* X, void* cuda_stream) {
+  g_err.clear();
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  if (s->n_loaded < 1) return fail(ESS_ERR_ARG, "no chains loaded (call ess_chains_init)");
+  DeviceGuard g(s->device);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int n = s->n_loaded, d = s->d;
+  if (X) {
+    if (mixed(s)) ESS_CUDA((ess::launch_convert<float, double>(s->Xw, d, X, d, n, d, st)));
+    else ESS_CUDA((ess::launch_convert<double, double>(s->Xd, d, X, d, n, d, st)));
+  }
+  ess_status rc = read_status(s, st);
+  timing_collect(s);
+  return rc;
+}
+
+ess_status ess_set_timing(ess_state* s, int enable) {
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  s->timing = enable != 0;
+  return ESS_OK;
+}
+
+ess_status ess_get_timing(ess_state* s, double* ms, long long* launches, int n_phases) {
+  if (!s || n_phases < 0) return fail(ESS_ERR_ARG, "bad argument");
+  DeviceGuard g(s->device);
+  ESS_CUDA(cudaDeviceSynchronize());
+  timing_collect(s);
+  for (int i = 0; i < n_phases && i < ESS_N_PHASES; ++i) {
+    if (ms) ms[i] = s->phase_ms[i];
+    if (launches) launches[i] = s->phase_launches[i];
+  }
+  return ESS_OK;
+}
+
+ess_status ess_reset_timing(ess_state* s) {
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  DeviceGuard g(s->device);
+  ESS_CUDA(cudaDeviceSynchronize());
+  timing_collect(s);
+  for (int i = 0; i < ESS_N_PHASES; ++i) {
+    s->phase_ms[i] = 0.0;
+    s->phase_launches[i] = 0;
+  }
+  return ESS_OK;
+}
+
+ess_status ess_run(ess_state* s, double* X, int n_chains, int t0, int n_iter, uint64_t seed,
+                   void* samples, int record_every, void* cuda_stream) {
+  g_err.clear();
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  if (n_chains < 0 || n_iter < 0 || t0 < 0 || record_every < 0)
+    return fail(ESS_ERR_ARG, "negative size");
+  if (n_chains == 0) return ESS_OK;
+  if (!X) return fail(ESS_ERR_ARG, "X is NULL");
+  if (record_every > 0 && !samples) return fail(ESS_ERR_ARG, "samples is NULL");
+  ess_status rc = ess_chains_init(s, X, n_chains, t0, cuda_stream);
+  if (rc == ESS_OK) rc = ess_chains_step(s, n_iter, seed, samples, record_every, cuda_stream);
+  if (rc == ESS_OK) rc = ess_chains_get(s, X, cuda_stream);
+  return rc;
+}
+
+ess_status ess_run_host(ess_state* s, double* X_host, int n_chains, int t0, int n_iter,
+                        uint64_t seed, void* samples_host, int record_every, void* cuda_stream) {
+  g_err.clear();
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  if (n_chains < 0 || n_iter < 0 || record_every < 0) return fail(ESS_ERR_ARG, "negative size");
+  if (n_chains == 0) return ESS_OK;
+  if (!X_host) return fail(ESS_ERR_ARG, "X is NULL");
+  if (record_every > 0 && !samples_host) return fail(ESS_ERR_ARG, "samples is NULL");
+  DeviceGuard g(s->device);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const size_t xbytes = sizeof(double) * (size_t)n_chains * s->d;
+  const int n_rec = record_every > 0 ? n_iter / record_every : 0;
+  const size_t sbytes = elem(s) * (size_t)n_chains * n_rec * s->d;
+  double* Xd = nullptr;
+  void* Sd = nullptr;
+  ESS_CUDA(cudaMalloc(&Xd, xbytes));
+  if (sbytes) {
+    cudaError_t e = cudaMalloc(&Sd, sbytes);
+    if (e != cudaSuccess) {
+      cudaFree(Xd);
+      return cuda_fail(e, "samples buffer");
+    }
+  }
+  ess_status rc = ESS_OK;
+  cudaError_t e = cudaMemcpyAsync(Xd, X_host, xbytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) rc = cuda_fail(e, "copy X to device");
+  if (rc == ESS_OK) rc = ess_run(s, Xd, n_chains, t0, n_iter, seed, Sd, record_every, cuda_stream);
+  if (rc == ESS_OK || rc == ESS_ERR_NUMERIC) {
+    e = cudaMemcpyAsync(X_host, Xd, xbytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && sbytes)
+      e = cudaMemcpyAsync(samples_host, Sd, sbytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess && rc == ESS_OK) rc = cuda_fail(e, "copy results to host");
+  }
+  cudaFree(Xd);
+  if (Sd) cudaFree(Sd);
+  return rc;
+}
+
+ess_status ess_step_with_draws(ess_state* s, const double* X, const double* nu, const double* u,
+                               int n_chains, double* X_next, double* theta, double* pieces,
+                               int max_pieces, int* n_pieces, int* rejected, void* cuda_stream) {
+  g_err.clear();
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  if (n_chains < 0) return fail(ESS_ERR_ARG, "negative size");
+  if (n_chains == 0) return ESS_OK;
+  if (!X || !nu || !u || !X_next) return fail(ESS_ERR_ARG, "NULL input");
+  if (pieces && max_pieces < 1) return fail(ESS_ERR_ARG, "max_pieces < 1");
+  DeviceGuard g(s->device);
+  s->n_loaded = 0;  // the work buffers are reused
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  ess_status rc = ensure_capacity(s, n_chains);
+  if (rc != ESS_OK) return rc;
+  ESS_CUDA(cudaMemsetAsync(s->dstatus, 0, sizeof(int), st));
+  const int n = n_chains, d = s->d;
+  if (mixed(s)) {
+    ESS_CUDA((ess::launch_convert<double, float>(X, d, s->Xw, d, n, d, st)));
+    ESS_CUDA((ess::launch_convert<double, float>(nu, d, static_cast<float*>(s->NU), d, n, d, st)));
+    ESS_CUDA(ess::launch_split_bf16(static_cast<const float*>(s->NU), d, s->NU_hi, s->NU_lo,
+                                    s->ld_bf, n, d, st));
+    rc = refresh_p(s, n, s->Xw, false, true, st);
+    if (rc == ESS_OK) rc = read_status(s, st);
+    if (rc != ESS_OK) return rc;
+    rc = compute_q(s, n, st);
+    if (rc != ESS_OK) return rc;
+    ess::ChainParams<float> p = base_params<float>(s, n);
+    p.X = s->Xw;
+    p.X_out = s->Xw;
+    p.U = u;
+    p.theta_out = theta;
+    p.pieces_out = pieces;
+    p.max_pieces = max_pieces;
+    p.npieces_out = n_pieces;
+    p.rejected_out = rejected;
+    ESS_CUDA(ess::launch_chain_step<float>(p, s->chain_threads, st));
+    ESS_CUDA((ess::launch_convert<float, double>(s->Xw, d, X_next, d, n, d, st)));
+  } else {
+    ESS_CUDA((ess::launch_convert<double, double>(nu, d, static_cast<double*>(s->NU), d, n, d, st)));
+    rc = refresh_p(s, n, X, false, true, st);
+    if (rc == ESS_OK) rc = read_status(s, st);
+    if (rc != ESS_OK) return rc;
+    rc = compute_q(s, n, st);
+    if (rc != ESS_OK) return rc;
+    ess::ChainParams<double> p = base_params<double>(s, n);
+    p.X = X;
+    p.X_out = X_next;
+    p.U = u;
+    p.theta_out = theta;
+    p.pieces_out = pieces;
+    p.max_pieces = max_pieces;
+    p.npieces_out = n_pieces;
+    p.rejected_out = rejected;
+    ESS_CUDA(ess::launch_chain_step<double>(p, s->chain_threads, st));
+  }
+  return read_status(s, st);
+}
+
+ess_status ess_products(ess_state* s, const double* X, const double* nu, int n_chains, double* P,
+                        double* Q, void* cuda_stream) {
+  g_err.clear();
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  if (n_chains < 0) return fail(ESS_ERR_ARG, "negative size");
+  if (n_chains == 0) return ESS_OK;
+  if ((P && !X) || (Q && !nu)) return fail(ESS_ERR_ARG, "NULL input");
+  DeviceGuard g(s->device);
+  s->n_loaded = 0;  // the work buffers are reused
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  ess_status rc = ensure_capacity(s, n_chains);
+  if (rc != ESS_OK) return rc;
+  ESS_CUDA(cudaMemsetAsync(s->dstatus, 0, sizeof(int), st));
+  const int n = n_chains, d = s->d, m = s->m;
+  if (mixed(s)) {
+    if (P) {
+      ESS_CUDA((ess::launch_convert<double, float>(X, d, s->Xw, d, n, d, st)));
+      rc = refresh_p(s, n, s->Xw, false, false, st);
+      if (rc != ESS_OK) return rc;
+      ESS_CUDA((ess::launch_convert<float, double>(static_cast<const float*>(s->P), m, P, m, n, m, st)));
+    }
+    if (Q) {
+      ESS_CUDA((ess::launch_convert<double, float>(nu, d, static_cast<float*>(s->NU), d, n, d, st)));
+      ESS_CUDA(ess::launch_split_bf16(static_cast<const float*>(s->NU), d, s->NU_hi, s->NU_lo,
+                                      s->ld_bf, n, d, st));
+      rc = compute_q(s, n, st);
+      if (rc != ESS_OK) return rc;
+      ESS_CUDA((ess::launch_convert<float, double>(static_cast<const float*>(s->Q), m, Q, m, n, m, st)));
+    }
+  } else {
+    if (P) {
+      rc = refresh_p(s, n, X, false, false, st);
+      if (rc != ESS_OK) return rc;
+      ESS_CUDA((ess::launch_convert<double, double>(static_cast<const double*>(s->P), m, P, m, n, m, st)));
+    }
+    if (Q) {
+      ESS_CUDA((ess::launch_convert<double, double>(nu, d, static_cast<double*>(s->NU), d, n, d, st)));
+      rc = compute_q(s, n, st);
+      if (rc != ESS_OK) return rc;
+      ESS_CUDA((ess::launch_convert<double, double>(static_cast<const double*>(s->Q), m, Q, m, n, m, st)));
+    }
+  }
+  return read_status(s, st);
+}
+
+ess_status ess_philox_blocks(uint64_t seed, uint32_t chain, uint32_t t, uint32_t problem,
+                             uint32_t stream, int n_blocks, uint32_t* out, void* cuda_stream) {
+  g_err.clear();
+  if (n_blocks < 0 || (n_blocks > 0 && !out)) return fail(ESS_ERR_ARG, "bad output");
+  if (problem > 0xFFFFFFu || stream > 0xFFu) return fail(ESS_ERR_ARG, "problem or stream too large");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  ESS_CUDA(ess::launch_philox_blocks(seed, chain, t, problem, stream, n_blocks, out, st));
+  ESS_CUDA(cudaStreamSynchronize(st));
+  return ESS_OK;
+}
+
+ess_status ess_draw_normals(const ess_state* s, int n_chains, int t, uint64_t seed, void* out,
+                            void* cuda_stream) {
+  g_err.clear();
+  if (!s || !out) return fail(ESS_ERR_ARG, "NULL argument");
+  if (n_chains < 0 || t < 0) return fail(ESS_ERR_ARG, "negative size");
+  DeviceGuard g(s->device);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (mixed(s))
+    ESS_CUDA(ess::launch_draw_nu_f32(static_cast<float*>(out), s->d, nullptr, nullptr, 0, n_chains,
+                                     s->d, seed, (uint32_t)t, 0u, 0u, st));
+  else
+    ESS_CUDA(ess::launch_draw_nu_f64(static_cast<double*>(out), n_chains, s->d, s->d, seed,
+                                     (uint32_t)t, 0u, 0u, st));
+  ESS_CUDA(cudaStreamSynchronize(st));
+  return ESS_OK;
+}
+
+ess_status ess_get_stats(const ess_state* s, ess_stats* out) {
+  if (!s || !out) return fail(ESS_ERR_ARG, "NULL argument");
+  DeviceGuard g(s->device);
+  DevStats h{};
+  ESS_CUDA(cudaMemcpy(&h, s->dstats, sizeof(h), cudaMemcpyDeviceToHost));
+  out->steps = (long long)h.steps;
+  out->rejections = (long long)h.rejections;
+  out->residual_rechecks = (long long)h.rechecks;
+  out->tangent_fp64 = (long long)h.tangent_fp64;
+  out->numeric_errors = (long long)h.numeric_errors;
+  double drift = 0.0;
+  std::memcpy(&drift, &h.max_drift_bits, sizeof(double));
+  out->max_refresh_drift = drift;
+  out->max_residual = h.max_residual_bits ? ess::dec_ordered(h.max_residual_bits) : -INFINITY;
+  return ESS_OK;
+}
+
+ess_status ess_reset_stats(ess_state* s) {
+  if (!s) return fail(ESS_ERR_ARG, "NULL argument");
+  DeviceGuard g(s->device);
+  ESS_CUDA(cudaMemset(s->dstats, 0, sizeof(DevStats)));
+  return ESS_OK;
+}
+
+ess_status ess_whiten(const double* A, const double* b, const double* mu, const double* L, int d,
+                      int m, double* A_out, double* b_out) {
+  g_err.clear();
+  if (!A || !b || !L || !A_out || !b_out) return fail(ESS_ERR_ARG, "NULL argument");
+  if (d < 1 || m < 1) return fail(ESS_ERR_ARG, "need d >= 1 and m >= 1");
+  // A_out = A L: row i of A_out is sum_j A[i, j] * (row j of L)
+  for (int i = 0; i < m; ++i) {
+    double* out = A_out + (size_t)i * d;
+    for (int k = 0; k < d; ++k) out[k] = 0.0;
+    const double* a = A + (size_t)i * d;
+    double am = 0.0;
+    for (int j = 0; j < d; ++j) {
+      const double aij = a[j];
+      if (mu) am += aij * mu[j];
+      if (aij == 0.0) continue;
+      const double* lrow = L + (size_t)j * d;
+      for (int k = 0; k < d; ++k) out[k] += aij * lrow[k];
+    }
+    b_out[i] = b[i] - am;
+  }
+  return ESS_OK;
+}
+
+ess_status ess_unwhiten(const double* L, const double* mu, int d, int n, const double* U, double* X) {
+  g_err.clear();
+  if (!L || !U || !X) return fail(ESS_ERR_ARG, "NULL argument");
+  if (d < 1 || n < 0) return fail(ESS_ERR_ARG, "bad size");
+  for (int r = 0; r < n; ++r) {
+    const double* u = U + (size_t)r * d;
+    double* x = X + (size_t)r * d;
+    for (int i = 0; i < d; ++i) {
+      const double* lrow = L + (size_t)i * d;
+      double acc = 0.0;
+      for (int j = 0; j < d; ++j) acc += lrow[j] * u[j];
+      x[i] = acc + (mu ? mu[i] : 0.0);
+    }
+  }
+  return ESS_OK;
+}
+
+const char* ess_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// ess_common.cuh -- device helpers shared by the sampler's kernels.
+//
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel
+// random numbers: as easy as 1, 2, 3", SC'11), written from its published
+// round function, with counter (block n, chain, step t, (problem << 8) |
+// stream) and key = the 64-bit seed.  Normals come from the Box-Muller
+// transform on two uniforms u1 = (r0 + 1) / 2^32 in (0, 1], u2 = r1 / 2^32 in
+// [0, 1); the theta draw uses a 53-bit uniform from block 0 of stream 1.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+namespace ess {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr float kTwoPiF = 6.28318548202514648f;  // 2 pi rounded to float (upwards)
+
+// Device-side counters of one launch sequence (accumulated over a run).
+struct DevStats {
+  unsigned long long steps;
+  unsigned long long rejections;
+  unsigned long long rechecks;
+  unsigned long long tangent_fp64;
+  unsigned long long numeric_errors;
+  unsigned long long max_drift_bits;     // double bits of a non-negative max
+  unsigned long long max_residual_bits;  // ordered bits of max residual (see enc)
+  unsigned long long pad;
+};
+
+// Error flags in the device status word.
+enum : int { kStatusNumeric = 1, kStatusInfeasible = 2, kStatusTimeout = 4 };
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1, uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+    uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+__device__ __forceinline__ void rng_block(uint64_t seed, uint32_t n, uint32_t chain, uint32_t t,
+                                          uint32_t problem, uint32_t stream, uint32_t out[4]) {
+  philox4x32_10(n, chain, t, (problem << 8) | (stream & 0xFFu), (uint32_t)seed,
+                (uint32_t)(seed >> 32), out);
+}
+
+// Box-Muller, double precision: 4 normals from one block.
+__device__ __forceinline__ void box_muller4(const uint32_t r[4], double z[4]) {
+  const double inv32 = 2.3283064365386962890625e-10;  // 2^-32
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    double u1 = ((double)r[2 * k] + 1.0) * inv32;
+    double u2 = (double)r[2 * k + 1] * inv32;
+    double rad = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    z[2 * k] = rad * c;
+    z[2 * k + 1] = rad * s;
+  }
+}
+
+// Box-Muller, single precision: 4 normals from one block.
+__device__ __forceinline__ void box_muller4(const uint32_t r[4], float z[4]) {
+  const float inv32 = 2.3283064365386963e-10f;  // 2^-32
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    // ln u1 with u1 = (r + 1) / 2^32: for u1 <= 1/2 directly; for u1 > 1/2 as
+    // log1p(-v) with v = 1 - u1 = (2^32 - 1 - r) / 2^32, so that the rounding
+    // of r to 24 bits never dominates a logarithm close to zero
+    const uint32_t r0 = r[2 * k];
+    const float lnu = r0 < 0x80000000u ? logf(fmaf((float)r0, inv32, inv32))
+                                       : log1pf(-(float)(~r0) * inv32);
+    float u2 = (float)r[2 * k + 1] * inv32;
+    float rad = sqrtf(-2.0f * lnu);
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    z[2 * k] = rad * c;
+    z[2 * k + 1] = rad * s;
+  }
+}
+
+__device__ __forceinline__ void box_muller4(const uint32_t r[4], double* out, int n) {
+  double z[4];
+  box_muller4(r, z);
+  for (int k = 0; k < n; ++k) out[k] = z[k];
+}
+
+// 53-bit uniform in [0, 1) for the theta draw.
+__device__ __forceinline__ double theta_uniform(uint64_t seed, uint32_t chain, uint32_t t,
+                                                uint32_t problem) {
+  uint32_t r[4];
+  rng_block(seed, 0u, chain, t, problem, 1u, r);
+  unsigned long long hi = r[0] >> 5, lo = r[1] >> 6;
+  return (double)(hi * 67108864ull + lo) * 1.1102230246251565404236316680908203125e-16;  // 2^-53
+}
+
+// Non-negative double max via its bit pattern (monotone for x >= 0).
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+  if (!(v > 0.0)) return;
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// Order-preserving encoding of any double into uint64 for atomicMax.
+__host__ __device__ __forceinline__ unsigned long long enc_ordered(double v) {
+  long long b;
+#ifdef __CUDA_ARCH__
+  b = __double_as_longlong(v);
+#else
+  __builtin_memcpy(&b, &v, 8);
+#endif
+  unsigned long long u = (unsigned long long)b;
+  return (b < 0) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__host__ __device__ __forceinline__ double dec_ordered(unsigned long long u) {
+  unsigned long long b = (u & 0x8000000000000000ull) ? (u & ~0x8000000000000000ull) : ~u;
+  double v;
+#ifdef __CUDA_ARCH__
+  v = __longlong_as_double((long long)b);
+#else
+  __builtin_memcpy(&v, &b, 8);
+#endif
+  return v;
+}
+
+}  // namespace ess

@@ -1,0 +1,158 @@
+// k_draw.cu -- nu ~ N(0, I_d) for every chain (Alg. 1, "sample nu_t"),
+// Philox4x32-10 + Box-Muller (see ess_common.cuh), plus small conversion and
+// checking kernels.
+#include "ess_kernels.cuh"
+
+namespace ess {
+namespace {
+
+// One thread per (chain, Philox block): 4 consecutive coordinates.
+__global__ void draw_nu_f64_kernel(double* __restrict__ nu, int n_chains, int d, int ld,
+                                   uint64_t seed, uint32_t t, uint32_t problem, uint32_t chain0) {
+  const int nblk = (d + 3) >> 2;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)n_chains * nblk) return;
+  const int c = (int)(gid / nblk), n = (int)(gid % nblk);
+  uint32_t r[4];
+  rng_block(seed, (uint32_t)n, chain0 + (uint32_t)c, t, problem, 0u, r);
+  double z[4];
+  box_muller4(r, z);
+  double* row = nu + (size_t)c * ld + 4 * n;
+  const int left = d - 4 * n;
+  if (left >= 4 && ((reinterpret_cast<uintptr_t>(row) & 15) == 0)) {
+    reinterpret_cast<double2*>(row)[0] = make_double2(z[0], z[1]);
+    reinterpret_cast<double2*>(row)[1] = make_double2(z[2], z[3]);
+  } else {
+    for (int k = 0; k < 4 && k < left; ++k) row[k] = z[k];
+  }
+}
+
+__global__ void draw_nu_f32_kernel(float* __restrict__ nu, int ld, __nv_bfloat16* __restrict__ hi,
+                                   __nv_bfloat16* __restrict__ lo, int ld_bf, int n_chains, int d,
+                                   uint64_t seed, uint32_t t, uint32_t problem, uint32_t chain0) {
+  const int nblk = (d + 3) >> 2;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)n_chains * nblk) return;
+  const int c = (int)(gid / nblk), n = (int)(gid % nblk);
+  uint32_t r[4];
+  rng_block(seed, (uint32_t)n, chain0 + (uint32_t)c, t, problem, 0u, r);
+  float z[4];
+  box_muller4(r, z);
+  const int left = d - 4 * n;
+  float* row = nu + (size_t)c * ld + 4 * n;
+  for (int k = 0; k < 4 && k < left; ++k) row[k] = z[k];
+  if (hi != nullptr) {
+    __nv_bfloat16* hrow = hi + (size_t)c * ld_bf + 4 * n;
+    __nv_bfloat16* lrow = lo + (size_t)c * ld_bf + 4 * n;
+    for (int k = 0; k < 4 && k < left; ++k) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(z[k]);
+      hrow[k] = h;
+      lrow[k] = __float2bfloat16_rn(z[k] - __bfloat162float(h));
+    }
+  }
+}
+
+__global__ void philox_blocks_kernel(uint64_t seed, uint32_t chain, uint32_t t, uint32_t problem,
+                                     uint32_t stream, int n_blocks, uint32_t* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_blocks) return;
+  uint32_t r[4];
+  rng_block(seed, (uint32_t)i, chain, t, problem, stream, r);
+  out[4 * i + 0] = r[0];
+  out[4 * i + 1] = r[1];
+  out[4 * i + 2] = r[2];
+  out[4 * i + 3] = r[3];
+}
+
+template <typename Ti, typename To>
+__global__ void convert_kernel(const Ti* __restrict__ src, int lds, To* __restrict__ dst, int ldd,
+                               int rows, int cols) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)rows * cols) return;
+  const int r = (int)(gid / cols), j = (int)(gid % cols);
+  dst[(size_t)r * ldd + j] = (To)src[(size_t)r * lds + j];
+}
+
+__global__ void split_bf16_kernel(const float* __restrict__ src, int ld, __nv_bfloat16* __restrict__ hi,
+                                  __nv_bfloat16* __restrict__ lo, int ld_bf, int rows, int cols) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)rows * cols) return;
+  const int r = (int)(gid / cols), j = (int)(gid % cols);
+  const float v = src[(size_t)r * ld + j];
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[(size_t)r * ld_bf + j] = h;
+  lo[(size_t)r * ld_bf + j] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__global__ void check_feasible_kernel(const double* __restrict__ P, int ldp,
+                                      const double* __restrict__ b, int rows, int m, int* status) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)rows * m) return;
+  const int r = (int)(gid / m), i = (int)(gid % m);
+  const double v = P[(size_t)r * ldp + i];
+  if (!(v <= b[i])) atomicOr(status, kStatusInfeasible);
+}
+
+inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace
+
+cudaError_t launch_draw_nu_f64(double* nu, int n_chains, int d, int ld, uint64_t seed, uint32_t t,
+                               uint32_t problem, uint32_t chain0, cudaStream_t s) {
+  const long long n = (long long)n_chains * ((d + 3) / 4);
+  if (n == 0) return cudaSuccess;
+  draw_nu_f64_kernel<<<grid_for(n, 256), 256, 0, s>>>(nu, n_chains, d, ld, seed, t, problem, chain0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_draw_nu_f32(float* nu, int ld, __nv_bfloat16* hi, __nv_bfloat16* lo, int ld_bf,
+                               int n_chains, int d, uint64_t seed, uint32_t t, uint32_t problem,
+                               uint32_t chain0, cudaStream_t s) {
+  const long long n = (long long)n_chains * ((d + 3) / 4);
+  if (n == 0) return cudaSuccess;
+  draw_nu_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(nu, ld, hi, lo, ld_bf, n_chains, d, seed, t,
+                                                      problem, chain0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox_blocks(uint64_t seed, uint32_t chain, uint32_t t, uint32_t problem,
+                                 uint32_t stream, int n_blocks, uint32_t* out, cudaStream_t s) {
+  if (n_blocks <= 0) return cudaSuccess;
+  philox_blocks_kernel<<<grid_for(n_blocks, 256), 256, 0, s>>>(seed, chain, t, problem, stream,
+                                                               n_blocks, out);
+  return cudaGetLastError();
+}
+
+template <typename Ti, typename To>
+cudaError_t launch_convert(const Ti* src, int lds, To* dst, int ldd, int rows, int cols,
+                           cudaStream_t s) {
+  const long long n = (long long)rows * cols;
+  if (n == 0) return cudaSuccess;
+  convert_kernel<Ti, To><<<grid_for(n, 256), 256, 0, s>>>(src, lds, dst, ldd, rows, cols);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16(const float* src, int ld, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                              int ld_bf, int rows, int cols, cudaStream_t s) {
+  const long long n = (long long)rows * cols;
+  if (n == 0) return cudaSuccess;
+  split_bf16_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, ld, hi, lo, ld_bf, rows, cols);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_feasible(const double* P, int ldp, const double* b, int rows, int m,
+                                  int* status, cudaStream_t s) {
+  const long long n = (long long)rows * m;
+  if (n == 0) return cudaSuccess;
+  check_feasible_kernel<<<grid_for(n, 256), 256, 0, s>>>(P, ldp, b, rows, m, status);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_convert<double, float>(const double*, int, float*, int, int, int,
+                                                   cudaStream_t);
+template cudaError_t launch_convert<float, double>(const float*, int, double*, int, int, int,
+                                                   cudaStream_t);
+template cudaError_t launch_convert<double, double>(const double*, int, double*, int, int, int,
+                                                    cudaStream_t);
+
+}  // namespace ess

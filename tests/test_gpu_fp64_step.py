@@ -1,0 +1,180 @@
+"""FP64 form: one-step map of the CUDA path vs the FP64 oracle, identical draws.
+
+Bar (stated for the plain FP64 form): interval endpoints within 1e-10 rad,
+theta within 1e-10 rad, x_{t+1} within 1e-9 relative, identical rejection
+flags.  The cases cover the paper's worked examples (Fig. 1, Fig. 2), random
+polytopes at sizes that span several GEMM and sort tiles with ragged tails,
+forced ties (Sec. 3.1, App. C), the sort reduction (Sec. 3.1), rows without
+roots, d = 1, and a single chain.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2407_10449_gb300 as ess
+from conftest import read_golden
+from gpu_helpers import dev, host, oracle_steps, positive_pieces, feasible_instance
+
+pytestmark = pytest.mark.gpu
+
+ANG_TOL = 1e-10
+X_RTOL = 1e-9
+
+
+def run_step(A, b, X, NU, U, precision=ess.ESS_PREC_FP64, max_pieces=None, **cfg):
+    s = ess.Sampler(A, b, precision=precision, **cfg)
+    try:
+        mp = max_pieces or (A.shape[0] + 2)
+        Xn, th, pcs, npc, rej = s.step_with_draws(dev(X), dev(NU), dev(U), max_pieces=mp)
+        return host(Xn), host(th), host(pcs), host(npc), host(rej), s.stats()
+    finally:
+        s.close()
+
+
+def check_fp64(A, b, X, NU, U, trim_eps=0.0):
+    Xn, th, pcs, npc, rej, _ = run_step(A, b, X, NU, U, trim_eps=trim_eps)
+    ref = oracle_steps(A, b, X, NU, U, trim_eps)
+    for c, r in enumerate(ref):
+        assert r.status == 0
+        want = positive_pieces(r.pieces)
+        got = positive_pieces(pcs[c], min(npc[c], pcs.shape[1]))
+        assert npc[c] == want.shape[0], (c, npc[c], want)
+        np.testing.assert_allclose(got, want, rtol=0, atol=ANG_TOL)
+        assert abs(th[c] - r.theta) <= ANG_TOL, (c, th[c], r.theta)
+        assert bool(rej[c]) == r.rejected
+        scale = np.maximum(1.0, np.abs(r.x_next))
+        assert np.all(np.abs(Xn[c] - r.x_next) <= X_RTOL * scale), c
+    return Xn, th
+
+
+def test_fig1_worked_example():
+    rows = read_golden("fig1_worked_example.txt")
+    x = np.array([float(v) for v in rows[0][1:]])
+    nu = np.array([float(v) for v in rows[1][1:]])
+    A, b = [], []
+    for row in rows[2:]:
+        if row[0] == "plane":
+            t1, t2 = float(row[1]) * math.pi, float(row[2]) * math.pi
+            tau, h = 0.5 * (t1 + t2), 0.5 * (t2 - t1)
+            A.append(np.linalg.solve(np.stack([x, nu]), [math.cos(tau), math.sin(tau)]))
+            b.append(math.cos(h))
+    A, b = np.array(A), np.array(b)
+    U = np.array([0.0, 0.1, 0.35, 0.5, 0.77, 0.999])
+    X = np.tile(x, (U.size, 1))
+    NU = np.tile(nu, (U.size, 1))
+    Xn, th = check_fp64(A, b, X, NU, U)
+    _, _, pcs, npc, _, _ = run_step(A, b, X, NU, U)
+    expected = np.array([[0.0, 0.125], [0.875, 1.125], [1.75, 2.0]]) * math.pi
+    np.testing.assert_allclose(positive_pieces(pcs[0], npc[0]), expected, atol=1e-12)
+
+
+def test_fig2_edge_cases():
+    x = np.array([[2.0, 0.0]])
+    nu = np.array([[0.0, 1.0]])
+    a = np.array([[-1.0, 0.0]])
+    for b_val in (2.5, 2.0, 1.0, -2.0):
+        Xn, th, pcs, npc, rej, _ = run_step(a, np.array([b_val]), x, nu, np.array([0.4]))
+        r = oracle.step(a, np.array([b_val]), x[0], nu[0], 0.4)
+        if b_val == -2.0:
+            assert th[0] == 0.0 and npc[0] == 0  # I_act = {0}: stay
+            np.testing.assert_array_equal(Xn[0], x[0])
+        check_fp64(a, np.array([b_val]), x, nu, np.array([0.4]))
+        assert abs(th[0] - r.theta) <= ANG_TOL
+    # b/r = -1.25: x_t infeasible -> the API refuses the step
+    with pytest.raises(ess.EssError) as e:
+        run_step(a, np.array([-2.5]), x, nu, np.array([0.4]))
+    assert e.value.status == ess.ESS_ERR_INFEASIBLE_X0
+
+
+@pytest.mark.parametrize("d,m,n", [(1, 2, 7), (3, 5, 33), (10, 20, 16), (37, 75, 130),
+                                   (137, 300, 200), (64, 513, 65), (200, 1100, 40),
+                                   (129, 2051, 24)])
+def test_random_polytopes(d, m, n):
+    rng = np.random.default_rng(1000 * d + m)
+    A, b, X = feasible_instance(rng, d, m, n)
+    NU = rng.standard_normal((n, d))
+    U = rng.uniform(size=n)
+    check_fp64(A, b, X, NU, U)
+
+
+def test_ties_and_duplicate_rows():
+    rng = np.random.default_rng(8)
+    d, m, n = 6, 40, 50
+    A, b, X = feasible_instance(rng, d, m, n)
+    A[10:20] = A[0]          # identical rows: identical (alpha, beta)
+    b[10:20] = b[0]
+    A[20:25] = A[1] * 2.0    # parallel rows, same hyperplane: identical angles
+    b[20:25] = b[1] * 2.0
+    NU = rng.standard_normal((n, d))
+    U = rng.uniform(size=n)
+    check_fp64(A, b, X, NU, U)
+
+
+def test_rows_without_roots_and_whole_circle():
+    rng = np.random.default_rng(9)
+    d, m, n = 5, 30, 20
+    A = rng.standard_normal((m, d))
+    b = np.full(m, 1e6)      # every b/r > 1: I_act = [0, 2 pi]
+    X = np.zeros((n, d))
+    NU = rng.standard_normal((n, d))
+    U = rng.uniform(size=n)
+    Xn, th = check_fp64(A, b, X, NU, U)
+    np.testing.assert_allclose(th, 2 * math.pi * U, atol=1e-12)
+
+
+def test_sort_reduction_through_kernel():
+    """Sec. 3.1: pairs (c_i, c_i + eps) come back in sorted order."""
+    # d = 2, x = (1, 0), nu = (0, 1): the ellipse is the unit circle at angle
+    # theta; the halfspace cos(theta - tau_i) <= cos(h_i) has infeasible arc
+    # (tau_i - h_i, tau_i + h_i).
+    rng = np.random.default_rng(12)
+    c = np.sort(rng.uniform(0.2, 2 * math.pi - 0.3, size=600))
+    rng.shuffle(c)
+    eps = 0.25 * np.min(np.diff(np.sort(c)))
+    tau, h = c + eps / 2, np.full_like(c, eps / 2)
+    A = np.stack([np.cos(tau), np.sin(tau)], axis=1)
+    b = np.cos(h)
+    x = np.array([[1.0, 0.0]])
+    nu = np.array([[0.0, 1.0]])
+    _, _, pcs, npc, _, _ = run_step(A, b, x, nu, np.array([0.5]), max_pieces=700)
+    got = positive_pieces(pcs[0], npc[0])
+    order = np.sort(c)
+    assert got.shape[0] == c.size + 1
+    np.testing.assert_allclose(got[1:-1, 1], order[1:], atol=1e-12)
+    np.testing.assert_allclose(got[1:-1, 0], order[:-1] + eps, atol=1e-12)
+
+
+def test_single_chain_and_trim():
+    rng = np.random.default_rng(13)
+    A, b, X = feasible_instance(rng, 12, 40, 1)
+    NU = rng.standard_normal((1, 12))
+    for u in (0.0, 0.3, 0.9999):
+        check_fp64(A, b, X, NU, np.array([u]))
+    X2 = np.repeat(X, 30, axis=0)
+    NU2 = rng.standard_normal((30, 12))
+    check_fp64(A, b, X2, NU2, rng.uniform(size=30), trim_eps=1e-3)
+
+
+def test_full_size_sampled_chains():
+    """The d = 1000, m = 2000, 8192-chain workload in the benchmark's launch,
+    checked on 24 sampled chains against the oracle."""
+    import workloads
+    inst = workloads.metric(n_chains=8192)
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((8192, inst.d)) * 0.002  # feasible: |a.x| small vs b >= 0.05
+    assert np.max(X @ inst.A.T - inst.b) < 0
+    NU = rng.standard_normal((8192, inst.d))
+    U = rng.uniform(size=8192)
+    Xn, th, pcs, npc, rej, _ = run_step(inst.A, inst.b, X, NU, U, max_pieces=64)
+    idx = rng.choice(8192, size=24, replace=False)
+    ref = oracle_steps(inst.A, inst.b, X[idx], NU[idx], U[idx])
+    for k, c in enumerate(idx):
+        r = ref[k]
+        assert abs(th[c] - r.theta) <= ANG_TOL
+        np.testing.assert_allclose(positive_pieces(pcs[c], min(npc[c], 64)),
+                                   positive_pieces(r.pieces)[:64], atol=ANG_TOL)
+        assert np.all(np.abs(Xn[c] - r.x_next) <= X_RTOL * np.maximum(1, np.abs(r.x_next)))
+    # every chain: the emitted iterate is feasible in FP64
+    assert np.max(Xn @ inst.A.T - inst.b) <= 0.0

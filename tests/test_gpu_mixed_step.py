@@ -1,0 +1,162 @@
+"""Mixed form: the BF16x3 tensor-core GEMM and the FP32 step vs the FP64 oracle.
+
+Bar (stated for the mixed form): interval endpoints and theta within 1e-5 rad
+and zero infeasible iterates.  A chain whose active endpoints are so
+ill-conditioned that the FP32 products actually computed (read back with
+ess_products) move them by more than 5e-6 rad to first order is exempted and
+counted (App. B: an endpoint tau -+ h moves by
+dp (|q| + |b p| / w) / r^2 + dq (|p| + |b q| / w) / r^2, w = sqrt(r^2 - b^2)).
+Inputs are rounded to float first on both sides, exactly as the mixed form
+stores them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2407_10449_gb300 as ess
+from gpu_helpers import dev, host, oracle_steps, positive_pieces, feasible_instance, \
+    sym_diff_measure
+
+pytestmark = pytest.mark.gpu
+
+ANG_TOL = 1e-5
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def q_error_bound(A, NU):
+    """Bound on |q_bf16x3 - a.nu| per row and chain: the dropped lo.lo term and
+    the residuals of both splits are each below 2^-16 |a_j nu_j| relative, plus
+    FP32 accumulation over K/16 tensor-core steps."""
+    absdot = np.abs(NU) @ np.abs(A).T
+    k = A.shape[1]
+    return absdot * (3 * 2.0**-16 + (k / 16 + 8) * 2.0**-24)
+
+
+@pytest.mark.parametrize("n,m,d", [(1, 20, 10), (130, 300, 137), (256, 448, 64),
+                                   (200, 1000, 333), (128, 2000, 1000), (77, 4100, 50)])
+def test_products_tensor_core_gemm(n, m, d):
+    """q = A nu from the tcgen05 BF16x3 GEMM vs FP64, and p = A x (refresh) vs FP64."""
+    rng = np.random.default_rng(n * 7 + m)
+    A = rng.standard_normal((m, d)) / math.sqrt(d)
+    b = np.ones(m)
+    X = f32(rng.standard_normal((n, d)) * 0.01)
+    NU = f32(rng.standard_normal((n, d)))
+    s = ess.Sampler(A, b, precision=ess.ESS_PREC_MIXED)
+    try:
+        P, Q = s.products(dev(X), dev(NU))
+        P, Q = host(P), host(Q)
+    finally:
+        s.close()
+    A32 = f32(A)
+    q_ref = NU @ A32.T
+    err = np.abs(Q - q_ref)
+    bound = q_error_bound(A32, NU)
+    assert np.all(err <= bound), float((err / bound).max())
+    # typical error far below the bound (a wrong operand layout would not be)
+    assert np.median(err / np.maximum(bound, 1e-300)) < 0.2
+    p_ref = X @ A.T
+    np.testing.assert_allclose(P, p_ref.astype(np.float32), rtol=2e-7, atol=1e-12)
+
+
+def _predicted_angle_error(A, b, X, NU, P, Q):
+    """Per row and chain: first-order change of alpha, beta caused by the
+    actual errors of the FP32 products P, Q (App. B: tau = atan2(q, p),
+    h = arccos(b / r))."""
+    p = X @ A.T
+    q = NU @ A.T
+    dp = np.abs(P - p)
+    dq = np.abs(Q - q)
+    r2 = p * p + q * q
+    with np.errstate(divide="ignore", invalid="ignore"):
+        w = np.sqrt(np.maximum(r2 - b[None, :] ** 2, 0.0))
+        bw = np.abs(b[None, :]) / (r2 * w)
+        err = dp * (np.abs(q) / r2 + bw * np.abs(p)) + dq * (np.abs(p) / r2 + bw * np.abs(q))
+    return np.where(np.isfinite(err), err, np.inf)
+
+
+def _chain_is_ill_conditioned(r, pred_c, limit):
+    """True if an endpoint of the oracle's active pieces comes from a row whose
+    predicted angle error exceeds `limit`."""
+    ends = set(positive_pieces(r.pieces).ravel().tolist()) - {0.0, 2 * math.pi}
+    for i in np.flatnonzero(r.has_root):
+        if (r.alpha[i] in ends or r.beta[i] in ends) and pred_c[i] > limit:
+            return True
+    return False
+
+
+def check_mixed(A, b, X, NU, U, trim_eps=0.0, max_exempt_frac=0.05):
+    X, NU = f32(X), f32(NU)
+    s = ess.Sampler(A, b, precision=ess.ESS_PREC_MIXED, trim_eps=trim_eps)
+    try:
+        Pg, Qg = s.products(dev(X), dev(NU))
+        Pg, Qg = host(Pg), host(Qg)
+        Xn, th, pcs, npc, rej = s.step_with_draws(dev(X), dev(NU), dev(U), max_pieces=A.shape[0] + 2)
+        Xn, th, pcs, npc, rej = host(Xn), host(th), host(pcs), host(npc), host(rej)
+        stats = s.stats()
+    finally:
+        s.close()
+    # zero infeasible iterates, decided in FP64 on the float states
+    assert np.max(Xn @ A.T - b[None, :]) <= 0.0
+    ref = oracle_steps(A, b, X, NU, U, trim_eps)
+    pred = _predicted_angle_error(A, b, X, NU, Pg, Qg)
+    n_exempt = 0
+    for c, r in enumerate(ref):
+        if _chain_is_ill_conditioned(r, pred[c], 0.5 * ANG_TOL):
+            n_exempt += 1
+            continue
+        got = positive_pieces(pcs[c], min(npc[c], pcs.shape[1]))
+        want = positive_pieces(r.pieces)
+        diff = sym_diff_measure(got, want)
+        assert diff <= 2 * max(len(want), 1) * ANG_TOL, (c, diff)
+        if not rej[c]:
+            assert abs(th[c] - r.theta) <= ANG_TOL, (c, th[c], r.theta)
+            scale = 1.0 + np.abs(r.x_next)
+            assert np.all(np.abs(Xn[c] - r.x_next) <= 1e-5 * scale * (1 + np.abs(NU[c]))), c
+        else:
+            np.testing.assert_array_equal(Xn[c], X[c])
+    assert n_exempt <= max(2, max_exempt_frac * len(ref)), n_exempt
+    return stats, n_exempt
+
+
+@pytest.mark.parametrize("d,m,n", [(2, 4, 16), (10, 20, 64), (37, 75, 130), (137, 300, 200),
+                                   (100, 200, 256)])
+def test_mixed_step_parity(d, m, n):
+    rng = np.random.default_rng(31 * d + m)
+    A, b, X = feasible_instance(rng, d, m, n, scale=1.0 / math.sqrt(d), slack=(0.05, 0.6))
+    NU = rng.standard_normal((n, d))
+    U = rng.uniform(size=n)
+    check_mixed(A, b, X, NU, U)
+
+
+def test_mixed_full_size_sampled():
+    """d = 1000, m = 2000, 8192 chains (the benchmark's launch), 16 sampled chains."""
+    import workloads
+    inst = workloads.metric(n_chains=8192)
+    rng = np.random.default_rng(2)
+    X = f32(rng.standard_normal((8192, inst.d)) * 0.002)
+    NU = f32(rng.standard_normal((8192, inst.d)))
+    U = rng.uniform(size=8192)
+    s = ess.Sampler(inst.A, inst.b, precision=ess.ESS_PREC_MIXED)
+    try:
+        Xn, th, pcs, npc, rej = s.step_with_draws(dev(X), dev(NU), dev(U), max_pieces=64)
+        Xn, th = host(Xn), host(th)
+    finally:
+        s.close()
+    assert np.max(Xn @ inst.A.T - inst.b) <= 0.0
+    idx = rng.choice(8192, size=16, replace=False)
+    ref = oracle_steps(inst.A, inst.b, X[idx], NU[idx], U[idx])
+    bad = sum(abs(th[c] - r.theta) > ANG_TOL for c, r in zip(idx, ref))
+    assert bad <= 1
+
+
+def test_mixed_trim_keeps_interior():
+    rng = np.random.default_rng(4)
+    A, b, X = feasible_instance(rng, 20, 60, 128, scale=0.3, slack=(0.05, 0.5))
+    NU = rng.standard_normal((128, 20))
+    U = rng.uniform(size=128)
+    check_mixed(A, b, X, NU, U, trim_eps=1e-4)

@@ -120,7 +120,7 @@ def test_chain_d1_interval_ks():
 
 def test_chain_d2_box_ks():
     inst = workloads.box2(n_chains=8192)
-    X, rej = _final_states(inst, 60, seed=5)
+    X, rej = _final_states(inst, 200, seed=5)
     assert stats.kstest(X[:, 0], stats.truncnorm(-1.0, 3.0).cdf).pvalue > 1e-3
     assert stats.kstest(X[:, 1], stats.truncnorm(-0.5, 1.2).cdf).pvalue > 1e-3
     assert abs(np.corrcoef(X[:, 0], X[:, 1])[0, 1]) < 5 / math.sqrt(8192)
