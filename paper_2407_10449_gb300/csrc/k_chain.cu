@@ -75,6 +75,7 @@ __device__ __forceinline__ bool roots(float p, float q, float b, double b64, dou
     return false;
   }
   float ratio = b / sqrtf(r2);
+  if (ratio >= (float)(1.0 + thresh)) return false;  // clearly no root
   if (fabsf(ratio) > (float)(1.0 - thresh)) {
     // near tangency: the arccos argument and the angles in double
     ++tangent;
