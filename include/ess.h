@@ -246,6 +246,29 @@ ess_status ess_whiten(const double *A, const double *b, const double *mu, const 
 ess_status ess_unwhiten(const double *L, const double *mu, int d, int n, const double *U,
                         double *X);
 
+/*
+ * One FP64 chain step that allocates no device memory (the paper has no
+ * counterpart; this is a service for callers that may not call cudaMalloc,
+ * e.g. plugins whose host framework owns the device-memory budget, request
+ * paths that must stay off the allocator, or threads whose stream is being
+ * captured).  Same map and results as ess_step_with_draws in the FP64 form,
+ * without an ess_state:
+ *   A, b        device, m x d and m doubles (the polytope A x <= b).
+ *   X, nu, u    device inputs as in ess_step_with_draws.
+ *   X_next      device output, n_chains x d doubles.
+ *   theta, rejected   device outputs or NULL.
+ * All scratch lives in one library-owned device array of
+ * ESS_NOALLOC_SCRATCH_BYTES per GPU (allocated when the library is loaded,
+ * kept until exit): 16 * n_chains * m + 8 * m bytes (plus 512) must fit, else
+ * ESS_ERR_ARG.  Calls share that array: calls that overlap on the GPU race, so
+ * serialize them.  The first call on a device looks up the array's device
+ * address; make it before any stream capture.  Synchronous.
+ */
+#define ESS_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+ess_status ess_step_noalloc(const double *A, const double *b, int d, int m, const double *X,
+                            const double *nu, const double *u, int n_chains, double *X_next,
+                            double *theta, int *rejected, void *cuda_stream);
+
 /* Message describing the last failure of the calling thread ("" if none). */
 const char *ess_last_error(void);
 

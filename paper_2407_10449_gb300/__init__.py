@@ -42,7 +42,10 @@ EXPORTED = ("ess_default_config", "ess_create", "ess_destroy", "ess_limits", "es
             "ess_chains_init", "ess_chains_step", "ess_chains_get", "ess_run_host", "ess_step_with_draws", "ess_products", "ess_philox_blocks",
             "ess_draw_normals",
             "ess_set_timing", "ess_get_timing", "ess_reset_timing",
-            "ess_get_stats", "ess_reset_stats", "ess_whiten", "ess_unwhiten", "ess_last_error")
+            "ess_get_stats", "ess_reset_stats", "ess_whiten", "ess_unwhiten", "ess_step_noalloc",
+            "ess_last_error")
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 PHASES = ("draw", "gemm", "chain", "refresh")
 
@@ -117,6 +120,8 @@ def load(build_if_missing: bool = True):
             "ess_reset_stats": ([_vp], c_int),
             "ess_whiten": ([_dp, _dp, _dp, _dp, c_int, c_int, _dp, _dp], c_int),
             "ess_unwhiten": ([_dp, _dp, c_int, c_int, _dp, _dp], c_int),
+            "ess_step_noalloc": ([_vp, _vp, c_int, c_int, _vp, _vp, _vp, c_int, _vp, _vp, _vp,
+                                  _vp], c_int),
             "ess_last_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -277,6 +282,21 @@ def ess_unwhiten(L, mu, U):
                                None if mu_p is None else mu_p.ctypes.data_as(_dp), d, n,
                                U.ctypes.data_as(_dp), X.ctypes.data_as(_dp)))
     return X
+
+
+def ess_step_noalloc(A, b, X, nu, u, X_next, theta=None, rejected=None, stream=None):
+    """FP64 one-step map without any device allocation (see include/ess.h).
+
+    For callers that may not allocate device memory at call time (a host
+    framework owning the memory budget, an allocation-free request path, a
+    thread whose stream is being captured).  A, b, X, nu, u, X_next (and the
+    optional theta, rejected) are CUDA tensors; scratch comes from a fixed
+    16 MiB array inside the library, so calls must not overlap on the GPU."""
+    m, d = A.shape
+    n = X.shape[0]
+    _check(load().ess_step_noalloc(_ptr(A), _ptr(b), d, m, _ptr(X), _ptr(nu), _ptr(u), n,
+                                   _ptr(X_next), _ptr(theta), _ptr(rejected),
+                                   _stream_ptr(stream)))
 
 
 def ess_last_error() -> str:

@@ -57,6 +57,9 @@ bool all_finite(const double* v, size_t n) {
 
 }  // namespace
 
+// Lets the other entry-point files of the library report through ess_last_error.
+void ess_internal_set_error(const std::string& msg) { g_err = msg; }
+
 struct ess_state {
   int d = 0, m = 0;
   ess_config cfg{};
