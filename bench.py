@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mixed-only", action="store_true",
+                    help="time only the mixed form (profiling runs)")
     return ap.parse_args()
 
 
@@ -196,18 +198,26 @@ def phase_rooflines(inst, n_chains, timing, precision, peaks):
         ms = t["ms"] / t["launches"]
         if phase == "gemm":
             if mixed:
-                flops = 3 * 2.0 * m * d * C  # three BF16 products issued
+                flops = 6 * 2.0 * m * d * C  # six BF16 slice products issued (BF16x6)
                 peak = peaks["bf16_tflops_sustained"]
                 out[phase] = dict(bound="tensor", unit="TFLOP/s", achieved=flops / ms / 1e9,
-                                  peak=peak, work_per_launch=flops, useful_flops=flops / 3)
+                                  peak=peak, work_per_launch=flops, useful_flops=flops / 6)
             else:
                 flops = 2.0 * m * d * C
                 out[phase] = dict(bound="fp64", unit="TFLOP/s", achieved=flops / ms / 1e9,
                                   peak=FP64_TFLOPS_MEASURED, work_per_launch=flops)
         elif phase == "refresh":
-            flops = 2.0 * m * d * C
-            out[phase] = dict(bound="fp64", unit="TFLOP/s", achieved=flops / ms / 1e9,
-                              peak=FP64_TFLOPS_MEASURED, work_per_launch=flops)
+            if mixed:
+                # exact split: K (K + 1) / 2 BF16 slice products (K = 5 at d = 1000)
+                K = 5
+                flops = K * (K + 1) / 2 * 2.0 * m * d * C
+                out[phase] = dict(bound="tensor", unit="TFLOP/s", achieved=flops / ms / 1e9,
+                                  peak=peaks["bf16_tflops_sustained"], work_per_launch=flops,
+                                  useful_flops=2.0 * m * d * C)
+            else:
+                flops = 2.0 * m * d * C
+                out[phase] = dict(bound="fp64", unit="TFLOP/s", achieved=flops / ms / 1e9,
+                                  peak=FP64_TFLOPS_MEASURED, work_per_launch=flops)
         elif phase == "chain":
             # read p, q (m each), write p; read x, nu, write x (d each)
             byts = float(C) * esz * (3 * m + 3 * d)
@@ -350,20 +360,23 @@ def main():
     ms, timing, stats, clk = time_form(ess, torch, inst, "mixed", C, args.steps, args.warmup,
                                        seed, world, rank, clocks)
     value = world * C * args.steps / (ms / 1e3)
-    ms64, timing64, stats64, _ = time_form(ess, torch, inst, "fp64", C, args.fp64_steps, 3, seed,
-                                           world, rank, None)
-    value64 = world * C * args.fp64_steps / (ms64 / 1e3)
+    if args.mixed_only:
+        ms64, timing64, stats64, value64 = float("nan"), {}, {}, None
+    else:
+        ms64, timing64, stats64, _ = time_form(ess, torch, inst, "fp64", C, args.fp64_steps, 3,
+                                               seed, world, rank, None)
+        value64 = world * C * args.fp64_steps / (ms64 / 1e3)
 
     if rank != 0:
         barrier(world)
         return 0
 
     roof = phase_rooflines(inst, C, timing, "mixed", peaks)
-    roof64 = phase_rooflines(inst, C, timing64, "fp64", peaks)
+    roof64 = phase_rooflines(inst, C, timing64, "fp64", peaks) if timing64 else {}
     dominant = max(roof, key=lambda k: roof[k]["share"])
     dom = roof[dominant]
     kernel_src = {"gemm": ("k_gemm_tc.cu",), "chain": ("k_chain.cu",), "draw": ("k_draw.cu",),
-                  "refresh": ("k_gemm_f64.cu",)}
+                  "refresh": ("k_gemm_tc.cu",)}
     src = source_hash(*kernel_src[dominant])
     traffic = ncu_traffic(f"{dominant}_mixed", src)
     roofline = {"bound": dom["bound"], "kernel": dominant, "achieved": dom["achieved"],
@@ -388,9 +401,10 @@ def main():
                    "chains_per_gpu": C, "precision": "mixed", "refresh_k": 32,
                    "l2": "working set per step ~300 MB > 126 MB L2 (no flush needed)",
                    "parallelism": f"replicas{world}"},
-        "fp64": {"value": value64, "unit": UNIT, "steps": args.fp64_steps,
-                 "ms_per_step": ms64 / args.fp64_steps, "dtype": "f64",
-                 "phases": roof64, "stats": stats64},
+        "fp64": None if args.mixed_only else {
+            "value": value64, "unit": UNIT, "steps": args.fp64_steps,
+            "ms_per_step": ms64 / args.fp64_steps, "dtype": "f64",
+            "phases": roof64, "stats": stats64},
         "roofline": roofline,
         "phases": roof,
         "e2e": e2e,

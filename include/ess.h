@@ -53,7 +53,7 @@ typedef enum {
 
 typedef enum {
     ESS_PREC_FP64 = 0,          /* every step in double precision */
-    ESS_PREC_MIXED = 1          /* q = A nu by BF16x3 tensor cores, FP32 step,
+    ESS_PREC_MIXED = 1          /* q = A nu by BF16x6 tensor cores, FP32 step,
                                    FP64 near-tangent arccos, A x refresh and
                                    feasibility residual */
 } ess_precision;
@@ -68,7 +68,9 @@ typedef struct {
     int precision;              /* ess_precision; default ESS_PREC_FP64 */
     int refresh_k;              /* p = A x recomputed when t % refresh_k == 0;
                                    default 32; 1 = every step */
-    int refresh_mode;           /* ess_refresh_mode; default ESS_REFRESH_FP64 */
+    int refresh_mode;           /* ess_refresh_mode; default ESS_REFRESH_SPLIT
+                                   for the mixed form (the FP64 form always
+                                   uses ESS_REFRESH_FP64) */
     double tangent_thresh;      /* mixed form: arccos argument b/r evaluated in
                                    FP64 when |b/r| > 1 - tangent_thresh;
                                    default 1e-4 */
@@ -76,7 +78,7 @@ typedef struct {
                                    (radians); default 0 */
     double residual_margin;     /* rows with p_i > b_i - residual_margin*||a_i||
                                    get their residual a_i.x - b_i recomputed in
-                                   FP64; default 1e-8 (FP64 form), 2e-3 (mixed) */
+                                   FP64; default 1e-8 (FP64 form), 2e-4 (mixed) */
     int sort_threads;           /* threads per chain for the sort; 0 = auto */
     int reserved[8];
 } ess_config;

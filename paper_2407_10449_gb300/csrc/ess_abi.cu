@@ -71,8 +71,6 @@ struct ess_state {
   double* b64 = nullptr;
   double* anorm = nullptr;
   float* b32 = nullptr;
-  __nv_bfloat16* A_hi = nullptr;
-  __nv_bfloat16* A_lo = nullptr;
   // work buffers (device), sized for `cap` chains
   int cap = 0;
   void* P = nullptr;       // n x m, T
@@ -83,11 +81,14 @@ struct ess_state {
   int n_loaded = 0;        // chains loaded by ess_chains_init
   int t_next = 0;          // global index of the next step of the loaded chains
   int p_fresh_t = -1;      // step index at which p was last recomputed from x
-  __nv_bfloat16* NU_hi = nullptr;
-  __nv_bfloat16* NU_lo = nullptr;
+  long long host_steps = 0;  // chain-steps enqueued since the last stats reset
+  __nv_bfloat16* NU_s[3] = {nullptr, nullptr, nullptr};  // exact bf16 split of nu
+  __nv_bfloat16* x_slices = nullptr;  // refresh: fixed-point slices of the states
+  float* row_scale = nullptr;         // refresh: per-chain power-of-two scales
+  double* P64 = nullptr;              // refresh: FP64 product for the start check
   DevStats* dstats = nullptr;
   int* dstatus = nullptr;
-  ess::TcGemmPlan* tc_plan = nullptr;  // BF16x3 tensor-core GEMM for q = A nu
+  ess::TcGemmPlan* tc_plan = nullptr;  // tensor-core GEMMs (q = A nu, exact refresh)
   // optional per-phase device timing (CUDA events on the run's stream)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -150,8 +151,10 @@ void free_work(ess_state* s) {
   s->P = s->Q = s->NU = nullptr;
   dev_free(s->Xw);
   dev_free(s->Xd);
-  dev_free(s->NU_hi);
-  dev_free(s->NU_lo);
+  for (auto& p : s->NU_s) dev_free(p);
+  dev_free(s->x_slices);
+  dev_free(s->row_scale);
+  dev_free(s->P64);
   s->cap = 0;
   s->n_loaded = 0;
 }
@@ -165,11 +168,18 @@ ess_status ensure_capacity(ess_state* s, int n) {
   ESS_CUDA(cudaMalloc(&s->NU, (size_t)n * s->d * e));
   if (mixed(s)) {
     ESS_CUDA(dev_alloc(&s->Xw, (size_t)n * s->d));
-    ESS_CUDA(dev_alloc(&s->NU_hi, (size_t)n * s->ld_bf));
-    ESS_CUDA(dev_alloc(&s->NU_lo, (size_t)n * s->ld_bf));
-    // the padding columns d .. ld_bf - 1 stay zero
-    ESS_CUDA(cudaMemset(s->NU_hi, 0, (size_t)n * s->ld_bf * sizeof(__nv_bfloat16)));
-    ESS_CUDA(cudaMemset(s->NU_lo, 0, (size_t)n * s->ld_bf * sizeof(__nv_bfloat16)));
+    for (auto& p : s->NU_s) {
+      ESS_CUDA(dev_alloc(&p, (size_t)n * s->ld_bf));
+      // the padding columns d .. ld_bf - 1 stay zero
+      ESS_CUDA(cudaMemset(p, 0, (size_t)n * s->ld_bf * sizeof(__nv_bfloat16)));
+    }
+    if (s->cfg.refresh_mode == ESS_REFRESH_SPLIT) {
+      const int K = ess::tc_refresh_num_slices(s->tc_plan);
+      ESS_CUDA(dev_alloc(&s->x_slices, (size_t)K * n * s->ld_bf));
+      ESS_CUDA(cudaMemset(s->x_slices, 0, (size_t)K * n * s->ld_bf * sizeof(__nv_bfloat16)));
+      ESS_CUDA(dev_alloc(&s->row_scale, (size_t)n));
+      ESS_CUDA(dev_alloc(&s->P64, (size_t)n * s->m));
+    }
   } else {
     ESS_CUDA(dev_alloc(&s->Xd, (size_t)n * s->d));
   }
@@ -182,7 +192,19 @@ ess_status ensure_capacity(ess_state* s, int n) {
 ess_status refresh_p(ess_state* s, int n, const void* Xcur, bool with_drift, bool check,
                      cudaStream_t st) {
   DevStats* drift = with_drift ? s->dstats : nullptr;
-  if (mixed(s)) {
+  if (mixed(s) && s->cfg.refresh_mode == ESS_REFRESH_SPLIT) {
+    // exact products on the tensor cores (fixed-point split), rounded once
+    const float* Xf = static_cast<const float*>(Xcur);
+    ESS_CUDA(ess::tc_refresh(s->tc_plan, Xf, s->d, n, s->x_slices, (size_t)n * s->ld_bf,
+                             s->row_scale, static_cast<float*>(s->P), check ? s->P64 : nullptr,
+                             s->m, s->anorm, with_drift ? &s->dstats->max_drift_bits : nullptr,
+                             s->dstatus, st));
+    if (check) {
+      ESS_CUDA(ess::launch_check_feasible_bounded(
+          s->P64, s->m, s->b64, n, s->m, s->row_scale, ess::tc_refresh_col_scale(s->tc_plan),
+          ess::tc_refresh_bound_factor(s->tc_plan), Xf, s->d, s->A64, s->d, s->dstatus, st));
+    }
+  } else if (mixed(s)) {
     ESS_CUDA((ess::launch_gemm_nt_f64<float, float>(static_cast<const float*>(Xcur), s->d, s->A64,
                                                      s->d, static_cast<float*>(s->P), s->m, n,
                                                      s->m, s->d, s->anorm, drift, st)));
@@ -212,9 +234,9 @@ ess_status refresh_p(ess_state* s, int n, const void* Xcur, bool with_drift, boo
 // q = A nu for all chains.
 ess_status compute_q(ess_state* s, int n, cudaStream_t st) {
   if (mixed(s)) {
-    cudaError_t e = ess::tc_gemm_bf16x3(s->tc_plan, s->NU_hi, s->NU_lo, s->ld_bf, n,
-                                        static_cast<float*>(s->Q), s->m, s->dstatus, st);
-    if (e != cudaSuccess) return cuda_fail(e, "BF16x3 tensor-core GEMM");
+    cudaError_t e = ess::tc_gemm_q(s->tc_plan, s->NU_s, s->ld_bf, n, static_cast<float*>(s->Q),
+                                   s->m, s->dstatus, st);
+    if (e != cudaSuccess) return cuda_fail(e, "BF16x6 tensor-core GEMM");
   } else {
     ESS_CUDA((ess::launch_gemm_nt_f64<double, double>(static_cast<const double*>(s->NU), s->d,
                                                        s->A64, s->d, static_cast<double*>(s->Q),
@@ -286,10 +308,10 @@ ess_status ess_default_config(int precision, ess_config* cfg) {
   std::memset(cfg, 0, sizeof(*cfg));
   cfg->precision = precision;
   cfg->refresh_k = 32;
-  cfg->refresh_mode = ESS_REFRESH_FP64;
+  cfg->refresh_mode = precision == ESS_PREC_MIXED ? ESS_REFRESH_SPLIT : ESS_REFRESH_FP64;
   cfg->tangent_thresh = 1e-4;
   cfg->trim_eps = 0.0;
-  cfg->residual_margin = precision == ESS_PREC_MIXED ? 2e-3 : 1e-8;
+  cfg->residual_margin = precision == ESS_PREC_MIXED ? 2e-4 : 1e-8;
   cfg->sort_threads = 0;
   return ESS_OK;
 }
@@ -309,8 +331,9 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
   if (c.precision != ESS_PREC_FP64 && c.precision != ESS_PREC_MIXED)
     return fail(ESS_ERR_ARG, "unknown precision");
   if (c.refresh_k < 1) return fail(ESS_ERR_ARG, "refresh_k must be >= 1");
-  if (c.refresh_mode != ESS_REFRESH_FP64)
-    return fail(ESS_ERR_UNSUPPORTED, "only ESS_REFRESH_FP64 is implemented");
+  if (c.refresh_mode != ESS_REFRESH_FP64 && c.refresh_mode != ESS_REFRESH_SPLIT)
+    return fail(ESS_ERR_ARG, "unknown refresh_mode");
+  if (c.precision == ESS_PREC_FP64) c.refresh_mode = ESS_REFRESH_FP64;  // FP64 form: FP64 products
   if (!(c.tangent_thresh >= 0.0 && c.tangent_thresh < 1.0) || !(c.trim_eps >= 0.0) ||
       !(c.residual_margin >= 0.0))
     return fail(ESS_ERR_ARG, "tangent_thresh in [0, 1), trim_eps >= 0, residual_margin >= 0");
@@ -362,20 +385,7 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
     for (int i = 0; i < m; ++i) bf[i] = (float)b[i];
     e = dev_alloc(&s->b32, (size_t)m);
     if (e == cudaSuccess) e = cudaMemcpy(s->b32, bf.data(), sizeof(float) * m, cudaMemcpyHostToDevice);
-    // A rounded to float, then split into bf16 hi + lo (the GEMM operands)
-    float* A32 = nullptr;
-    if (e == cudaSuccess) e = dev_alloc(&A32, (size_t)m * d);
-    if (e == cudaSuccess) e = ess::launch_convert<double, float>(s->A64, d, A32, d, m, d, 0);
-    if (e == cudaSuccess) e = dev_alloc(&s->A_hi, (size_t)m * s->ld_bf);
-    if (e == cudaSuccess) e = dev_alloc(&s->A_lo, (size_t)m * s->ld_bf);
-    if (e == cudaSuccess)
-      e = cudaMemset(s->A_hi, 0, sizeof(__nv_bfloat16) * (size_t)m * s->ld_bf);
-    if (e == cudaSuccess)
-      e = cudaMemset(s->A_lo, 0, sizeof(__nv_bfloat16) * (size_t)m * s->ld_bf);
-    if (e == cudaSuccess) e = ess::launch_split_bf16(A32, d, s->A_hi, s->A_lo, s->ld_bf, m, d, 0);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (A32) cudaFree(A32);
-    if (e == cudaSuccess) e = ess::tc_gemm_create(&s->tc_plan, s->A_hi, s->A_lo, s->ld_bf, m, d);
+    if (e == cudaSuccess) e = ess::tc_gemm_create(&s->tc_plan, A, m, d);
   }
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "ess_create device setup"));
   *out = s;
@@ -390,8 +400,6 @@ void ess_destroy(ess_state* s) {
   dev_free(s->b64);
   dev_free(s->anorm);
   dev_free(s->b32);
-  dev_free(s->A_hi);
-  dev_free(s->A_lo);
   dev_free(s->dstats);
   dev_free(s->dstatus);
   ess::tc_gemm_destroy(s->tc_plan);
@@ -465,8 +473,8 @@ ess_status ess_chains_step(ess_state* s, int n_iter, uint64_t seed, void* sample
     if (mixed(s)) {
       {
         PhaseScope ps(s, st, ESS_PHASE_DRAW);
-        ESS_CUDA(ess::launch_draw_nu_f32(static_cast<float*>(s->NU), d, s->NU_hi, s->NU_lo,
-                                         s->ld_bf, n, d, seed, t, 0u, 0u, st));
+        ESS_CUDA(ess::launch_draw_nu_f32(static_cast<float*>(s->NU), d, s->NU_s, s->ld_bf, n, d,
+                                         seed, t, 0u, 0u, st));
       }
       {
         PhaseScope ps(s, st, ESS_PHASE_GEMM);
@@ -508,6 +516,7 @@ ess_status ess_chains_step(ess_state* s, int n_iter, uint64_t seed, void* sample
     }
   }
   s->t_next += n_iter;
+  s->host_steps += (long long)n * n_iter;
   return ESS_OK;
 }
 
@@ -630,8 +639,8 @@ ess_status ess_step_with_draws(ess_state* s, const double* X, const double* nu, 
   if (mixed(s)) {
     ESS_CUDA((ess::launch_convert<double, float>(X, d, s->Xw, d, n, d, st)));
     ESS_CUDA((ess::launch_convert<double, float>(nu, d, static_cast<float*>(s->NU), d, n, d, st)));
-    ESS_CUDA(ess::launch_split_bf16(static_cast<const float*>(s->NU), d, s->NU_hi, s->NU_lo,
-                                    s->ld_bf, n, d, st));
+    ESS_CUDA(ess::tc_split3(static_cast<const float*>(s->NU), d, n, d, s->NU_s[0], s->NU_s[1],
+                            s->NU_s[2], s->ld_bf, st));
     rc = refresh_p(s, n, s->Xw, false, true, st);
     if (rc == ESS_OK) rc = read_status(s, st);
     if (rc != ESS_OK) return rc;
@@ -648,6 +657,7 @@ ess_status ess_step_with_draws(ess_state* s, const double* X, const double* nu, 
     p.rejected_out = rejected;
     ESS_CUDA(ess::launch_chain_step<float>(p, s->chain_threads, st));
     ESS_CUDA((ess::launch_convert<float, double>(s->Xw, d, X_next, d, n, d, st)));
+    s->host_steps += n;
   } else {
     ESS_CUDA((ess::launch_convert<double, double>(nu, d, static_cast<double*>(s->NU), d, n, d, st)));
     rc = refresh_p(s, n, X, false, true, st);
@@ -665,6 +675,7 @@ ess_status ess_step_with_draws(ess_state* s, const double* X, const double* nu, 
     p.npieces_out = n_pieces;
     p.rejected_out = rejected;
     ESS_CUDA(ess::launch_chain_step<double>(p, s->chain_threads, st));
+    s->host_steps += n;
   }
   return read_status(s, st);
 }
@@ -692,8 +703,8 @@ ess_status ess_products(ess_state* s, const double* X, const double* nu, int n_c
     }
     if (Q) {
       ESS_CUDA((ess::launch_convert<double, float>(nu, d, static_cast<float*>(s->NU), d, n, d, st)));
-      ESS_CUDA(ess::launch_split_bf16(static_cast<const float*>(s->NU), d, s->NU_hi, s->NU_lo,
-                                      s->ld_bf, n, d, st));
+      ESS_CUDA(ess::tc_split3(static_cast<const float*>(s->NU), d, n, d, s->NU_s[0], s->NU_s[1],
+                              s->NU_s[2], s->ld_bf, st));
       rc = compute_q(s, n, st);
       if (rc != ESS_OK) return rc;
       ESS_CUDA((ess::launch_convert<float, double>(static_cast<const float*>(s->Q), m, Q, m, n, m, st)));
@@ -733,7 +744,7 @@ ess_status ess_draw_normals(const ess_state* s, int n_chains, int t, uint64_t se
   DeviceGuard g(s->device);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   if (mixed(s))
-    ESS_CUDA(ess::launch_draw_nu_f32(static_cast<float*>(out), s->d, nullptr, nullptr, 0, n_chains,
+    ESS_CUDA(ess::launch_draw_nu_f32(static_cast<float*>(out), s->d, nullptr, 0, n_chains,
                                      s->d, seed, (uint32_t)t, 0u, 0u, st));
   else
     ESS_CUDA(ess::launch_draw_nu_f64(static_cast<double*>(out), n_chains, s->d, s->d, seed,
@@ -747,7 +758,7 @@ ess_status ess_get_stats(const ess_state* s, ess_stats* out) {
   DeviceGuard g(s->device);
   DevStats h{};
   ESS_CUDA(cudaMemcpy(&h, s->dstats, sizeof(h), cudaMemcpyDeviceToHost));
-  out->steps = (long long)h.steps;
+  out->steps = s->host_steps;
   out->rejections = (long long)h.rejections;
   out->residual_rechecks = (long long)h.rechecks;
   out->tangent_fp64 = (long long)h.tangent_fp64;
@@ -763,6 +774,7 @@ ess_status ess_reset_stats(ess_state* s) {
   if (!s) return fail(ESS_ERR_ARG, "NULL argument");
   DeviceGuard g(s->device);
   ESS_CUDA(cudaMemset(s->dstats, 0, sizeof(DevStats)));
+  s->host_steps = 0;
   return ESS_OK;
 }
 

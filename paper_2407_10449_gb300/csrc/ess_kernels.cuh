@@ -13,9 +13,9 @@ namespace ess {
 // nu[c, j] for chains chain0 .. chain0 + n_chains - 1 at step t (row stride ld).
 cudaError_t launch_draw_nu_f64(double* nu, int n_chains, int d, int ld, uint64_t seed,
                                uint32_t t, uint32_t problem, uint32_t chain0, cudaStream_t s);
-// float nu plus its bf16 hi/lo split (hi = bf16(nu), lo = bf16(nu - hi)), rows of
-// ld_bf elements; columns d .. ld_bf - 1 of hi/lo are left untouched.
-cudaError_t launch_draw_nu_f32(float* nu, int ld, __nv_bfloat16* hi, __nv_bfloat16* lo, int ld_bf,
+// float nu plus (if split != nullptr) its exact three-way bf16 split, rows of
+// ld_bf elements; columns d .. ld_bf - 1 of the split are left untouched.
+cudaError_t launch_draw_nu_f32(float* nu, int ld, __nv_bfloat16* const split[3], int ld_bf,
                                int n_chains, int d, uint64_t seed, uint32_t t, uint32_t problem,
                                uint32_t chain0, cudaStream_t s);
 cudaError_t launch_philox_blocks(uint64_t seed, uint32_t chain, uint32_t t, uint32_t problem,
@@ -26,9 +26,6 @@ cudaError_t launch_philox_blocks(uint64_t seed, uint32_t chain, uint32_t t, uint
 template <typename Ti, typename To>
 cudaError_t launch_convert(const Ti* src, int lds, To* dst, int ldd, int rows, int cols,
                            cudaStream_t s);
-// bf16 hi/lo split of a float matrix (rows x cols, strides ld / ld_bf).
-cudaError_t launch_split_bf16(const float* src, int ld, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                              int ld_bf, int rows, int cols, cudaStream_t s);
 
 // ------------------------------------------------------------ FP64 GEMM ----
 // C[r, i] = sum_j X[r, j] * A[i, j] in FP64 (X: M x K, A: N x K, both K
@@ -44,6 +41,13 @@ cudaError_t launch_gemm_nt_f64(const TX* X, int ldx, const double* A, int lda, T
 // P[r, i] > b[i] (P computed in FP64).
 cudaError_t launch_check_feasible(const double* P, int ldp, const double* b, int rows, int m,
                                   int* status, cudaStream_t s);
+
+// Feasibility of float states X from a product P known to within
+// bound * row_scale[r] * col_scale[i]; undecided entries recomputed in FP64.
+cudaError_t launch_check_feasible_bounded(const double* P, int ldp, const double* b, int rows,
+                                          int m, const float* row_scale, const float* col_scale,
+                                          double bound, const float* X, int ldx, const double* A,
+                                          int d, int* status, cudaStream_t s);
 
 // ------------------------------------------------------------ chain step ---
 template <typename T>

@@ -137,19 +137,41 @@ __device__ V block_exclusive_scan(V v, V identity, Op op, V* tmp, V& total) {
 }
 
 // ---- kernel ----------------------------------------------------------------
+template <typename T> struct BitsOf;
+template <> struct BitsOf<float> {
+  typedef unsigned int type;
+  __device__ static type get(float v) { return __float_as_uint(v); }
+  __device__ static float put(type v) { return __uint_as_float(v); }
+};
+template <> struct BitsOf<double> {
+  typedef unsigned long long type;
+  __device__ static type get(double v) { return (unsigned long long)__double_as_longlong(v); }
+  __device__ static double put(type v) { return __longlong_as_double((long long)v); }
+};
+
+// Shared-memory slot of sorted position e: one padding word per 32 keeps the
+// per-thread chunks (stride ITEMS) on distinct banks.
+__device__ __forceinline__ int pad_idx(int e) { return e + (e >> 5); }
+
+constexpr int kBuckets = 64;  // alpha buckets of the domination prune
+
 template <typename T, int NT, int ITEMS>
-__global__ void __launch_bounds__(NT) chain_step_kernel(ChainParams<T> prm) {
+__global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_kernel(ChainParams<T> prm) {
   constexpr int NSLOT = NT * ITEMS;
+  constexpr int NPAD = NSLOT + NSLOT / 32;
   constexpr int NW = NT / 32;
+  typedef typename BitsOf<T>::type Bits;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s_key = reinterpret_cast<T*>(smem_raw);
-  T* s_val = s_key + NSLOT;
-  T* s_x = s_val + NSLOT;
+  T* s_val = s_key + NPAD;
+  T* s_x = s_val + NPAD;
   int* s_flag = reinterpret_cast<int*>(s_x + ((prm.d + 1) & ~1));
 
   __shared__ int s_itmp[NW];
   __shared__ T s_ttmp[NW];
-  __shared__ int s_nflag, s_reject, s_best, s_bad;
+  __shared__ Bits s_bmax[kBuckets];   // max beta (bits) of the arcs whose alpha falls in a bucket
+  __shared__ T s_gearly[kBuckets];    // max beta of the arcs in all earlier buckets
+  __shared__ int s_nflag, s_reject, s_best, s_bad, s_tangent;
   __shared__ T s_theta;
 
   const int c = blockIdx.x;
@@ -164,15 +186,19 @@ __global__ void __launch_bounds__(NT) chain_step_kernel(ChainParams<T> prm) {
     s_reject = 0;
     s_best = -1;
     s_bad = 0;
+    s_tangent = 0;
   }
+  for (int k = tid; k < kBuckets; k += NT) s_bmax[k] = 0;
+  __syncthreads();
 
   // ---- 1. roots of every row, kept in registers --------------------------
   const T* Prow = prm.P_in + (size_t)c * prm.ldp;
   const T* Qrow = prm.Q + (size_t)c * prm.ldp;
   T p[ITEMS], q[ITEMS], al[ITEMS], be[ITEMS];
   bool has[ITEMS];
-  int my_count = 0, tangent = 0;
+  int tangent = 0;
   bool infeasible = false, nonfinite = false;
+  const T to_bucket = (T)(kBuckets / kTwoPi);
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
     const int i = tid + r * NT;
@@ -187,6 +213,42 @@ __global__ void __launch_bounds__(NT) chain_step_kernel(ChainParams<T> prm) {
       has[r] = roots(p[r], q[r], prm.b[i], prm.b64[i], prm.tangent_thresh, al[r], be[r], inf_row,
                      tangent);
       infeasible |= inf_row;
+      if (has[r]) {
+        const int bk = min(kBuckets - 1, (int)(al[r] * to_bucket));
+        atomicMax(&s_bmax[bk], BitsOf<T>::get(be[r]));
+      }
+    }
+  }
+  if (tangent) atomicAdd(&s_tangent, tangent);
+  __syncthreads();
+
+  // ---- domination prune ------------------------------------------------------
+  // An arc (alpha_i, beta_i) lies inside an arc that starts in an earlier
+  // alpha bucket whenever beta_i <= max beta of the earlier buckets (bucket
+  // indices are monotone in alpha), so it cannot change the union of arcs:
+  // I_act and its piece endpoints are unchanged when it is dropped.
+  if (warp == 0) {
+    // exclusive prefix max over the buckets, two buckets per lane
+    const T b0 = BitsOf<T>::put(s_bmax[2 * lane]);
+    const T b1 = BitsOf<T>::put(s_bmax[2 * lane + 1]);
+    T incl = b0 > b1 ? b0 : b1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl = y > incl ? y : incl;
+    }
+    T excl = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0) excl = T(-1);
+    s_gearly[2 * lane] = excl;
+    s_gearly[2 * lane + 1] = b0 > excl ? b0 : excl;
+  }
+  __syncthreads();
+  int my_count = 0;
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    if (has[r]) {
+      const int bk = min(kBuckets - 1, (int)(al[r] * to_bucket));
+      has[r] = be[r] > s_gearly[bk];
       my_count += has[r] ? 1 : 0;
     }
   }
@@ -195,23 +257,28 @@ __global__ void __launch_bounds__(NT) chain_step_kernel(ChainParams<T> prm) {
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
     if (has[r]) {
-      s_key[offset] = al[r];
-      s_val[offset] = be[r];
+      s_key[pad_idx(offset)] = al[r];
+      s_val[pad_idx(offset)] = be[r];
       ++offset;
     }
   }
-  for (int k = n_roots + tid; k < NSLOT; k += NT) {
-    s_key[k] = inf;
-    s_val[k] = T(0);
+  const int n_active_slots = ((n_roots + ITEMS - 1) / ITEMS) * ITEMS;
+  for (int k = n_roots + tid; k < n_active_slots; k += NT) {
+    s_key[pad_idx(k)] = inf;
+    s_val[pad_idx(k)] = T(0);
   }
   __syncthreads();
 
   // ---- 2. Alg. 3: sort alpha ascending, beta as payload -----------------
+  // Only the first n_active_slots positions hold arcs; the rest is padding
+  // (+inf keys) that the sort never needs to touch.
+  const int base = tid * ITEMS;
+  const bool owns = base < n_active_slots;
   T key[ITEMS], val[ITEMS];
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
-    key[i] = s_key[tid * ITEMS + i];
-    val[i] = s_val[tid * ITEMS + i];
+    key[i] = owns ? s_key[pad_idx(base + i)] : inf;
+    val[i] = owns ? s_val[pad_idx(base + i)] : T(0);
   }
   // bitonic network over the thread's ITEMS registers
 #pragma unroll
@@ -231,47 +298,48 @@ __global__ void __launch_bounds__(NT) chain_step_kernel(ChainParams<T> prm) {
       }
     }
   }
-  // merge-path merges of sorted runs, width ITEMS, 2 ITEMS, ...
-  const int n_active_slots = ((n_roots + ITEMS - 1) / ITEMS) * ITEMS;
-  for (int w = ITEMS; w < NSLOT; w <<= 1) {
-    if (w >= n_active_slots && w >= ITEMS) {
-      // every run beyond the first is padding: nothing left to merge
-      break;
+  // merge-path merges of sorted runs of width ITEMS, 2 ITEMS, ... until one
+  // run holds every arc
+  for (int w = ITEMS; w < n_active_slots; w <<= 1) {
+    __syncthreads();
+    if (owns) {
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        s_key[pad_idx(base + i)] = key[i];
+        s_val[pad_idx(base + i)] = val[i];
+      }
     }
     __syncthreads();
+    if (owns) {
+      const int start = base & ~(2 * w - 1);
+      const int diag = base - start;
+      // runs [start, start + w) and [start + w, start + 2w), clipped to the arcs
+      const int a_end = min(w, n_active_slots - start);
+      const int b_len = max(0, min(w, n_active_slots - start - w));
+      int lo = diag - b_len > 0 ? diag - b_len : 0;
+      int hi = diag < a_end ? diag : a_end;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (!(s_key[pad_idx(start + w + diag - 1 - mid)] < s_key[pad_idx(start + mid)])) lo = mid + 1;
+        else hi = mid;
+      }
+      int ia = lo, ib = diag - lo;
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      s_key[tid * ITEMS + i] = key[i];
-      s_val[tid * ITEMS + i] = val[i];
-    }
-    __syncthreads();
-    const int pos = tid * ITEMS;
-    const int start = pos & ~(2 * w - 1);
-    const int diag = pos - start;
-    const T* ak = s_key + start;
-    const T* bk = ak + w;
-    const T* av = s_val + start;
-    const T* bv = av + w;
-    int lo = diag - w > 0 ? diag - w : 0;
-    int hi = diag < w ? diag : w;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (!(bk[diag - 1 - mid] < ak[mid])) lo = mid + 1;
-      else hi = mid;
-    }
-    int ia = lo, ib = diag - lo;
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      const bool take_a = ia < w && (ib >= w || !(bk[ib] < ak[ia]));
-      key[i] = take_a ? ak[ia] : bk[ib];
-      val[i] = take_a ? av[ia] : bv[ib];
-      ia += take_a ? 1 : 0;
-      ib += take_a ? 0 : 1;
+      for (int i = 0; i < ITEMS; ++i) {
+        const bool a_ok = ia < a_end;
+        const bool b_ok = ib < b_len;
+        const T ka = a_ok ? s_key[pad_idx(start + ia)] : inf;
+        const T kb = b_ok ? s_key[pad_idx(start + w + ib)] : inf;
+        const bool take_a = a_ok && (!b_ok || !(kb < ka));
+        key[i] = take_a ? ka : kb;
+        val[i] = take_a ? s_val[pad_idx(start + ia)] : (b_ok ? s_val[pad_idx(start + w + ib)] : T(0));
+        ia += take_a ? 1 : 0;
+        ib += take_a ? 0 : 1;
+      }
     }
   }
 
   // ---- 3. Alg. 3: gamma_k = cumulative max of beta ----------------------
-  const int base = tid * ITEMS;
   T g[ITEMS];
   T run = T(0);
 #pragma unroll
@@ -451,9 +519,8 @@ __global__ void __launch_bounds__(NT) chain_step_kernel(ChainParams<T> prm) {
   }
 
   // ---- statistics ----------------------------------------------------------
-  int blk_tangent, blk_flags;
-  (void)block_exclusive_scan<NT>(tangent, 0, OpAdd(), s_itmp, blk_tangent);
-  (void)block_exclusive_scan<NT>(my_flags, 0, OpAdd(), s_itmp, blk_flags);
+  const int blk_tangent = s_tangent;
+  const int blk_flags = nflag;
   // max residual across warps
   double wmax = my_maxres;
 #pragma unroll
@@ -463,7 +530,6 @@ __global__ void __launch_bounds__(NT) chain_step_kernel(ChainParams<T> prm) {
   if (tid == 0) {
     if (prm.theta_out) prm.theta_out[c] = (double)theta;
     if (prm.rejected_out) prm.rejected_out[c] = reject ? 1 : 0;
-    atomicAdd(&prm.stats->steps, 1ull);
     if (reject && s_bad == 0) atomicAdd(&prm.stats->rejections, 1ull);
     if (s_bad) {
       atomicAdd(&prm.stats->numeric_errors, 1ull);
@@ -486,7 +552,8 @@ int chain_threads_for(int m) {
 template <typename T>
 size_t chain_smem_bytes(int threads, int d) {
   const size_t nslot = (size_t)threads * kChainItems;
-  return 2 * nslot * sizeof(T) + (size_t)((d + 1) & ~1) * sizeof(T) + nslot * sizeof(int);
+  const size_t npad = nslot + nslot / 32;
+  return 2 * npad * sizeof(T) + (size_t)((d + 1) & ~1) * sizeof(T) + nslot * sizeof(int);
 }
 
 template <typename T>

@@ -27,8 +27,9 @@ __global__ void draw_nu_f64_kernel(double* __restrict__ nu, int n_chains, int d,
   }
 }
 
-__global__ void draw_nu_f32_kernel(float* __restrict__ nu, int ld, __nv_bfloat16* __restrict__ hi,
-                                   __nv_bfloat16* __restrict__ lo, int ld_bf, int n_chains, int d,
+__global__ void draw_nu_f32_kernel(float* __restrict__ nu, int ld, __nv_bfloat16* __restrict__ s0,
+                                   __nv_bfloat16* __restrict__ s1, __nv_bfloat16* __restrict__ s2,
+                                   int ld_bf, int n_chains, int d,
                                    uint64_t seed, uint32_t t, uint32_t problem, uint32_t chain0) {
   const int nblk = (d + 3) >> 2;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -41,13 +42,16 @@ __global__ void draw_nu_f32_kernel(float* __restrict__ nu, int ld, __nv_bfloat16
   const int left = d - 4 * n;
   float* row = nu + (size_t)c * ld + 4 * n;
   for (int k = 0; k < 4 && k < left; ++k) row[k] = z[k];
-  if (hi != nullptr) {
-    __nv_bfloat16* hrow = hi + (size_t)c * ld_bf + 4 * n;
-    __nv_bfloat16* lrow = lo + (size_t)c * ld_bf + 4 * n;
+  if (s0 != nullptr) {
+    // exact three-way bf16 split: z = a + b + c
+    const size_t o = (size_t)c * ld_bf + 4 * n;
     for (int k = 0; k < 4 && k < left; ++k) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(z[k]);
-      hrow[k] = h;
-      lrow[k] = __float2bfloat16_rn(z[k] - __bfloat162float(h));
+      const __nv_bfloat16 a = __float2bfloat16_rn(z[k]);
+      const float r1 = z[k] - __bfloat162float(a);
+      const __nv_bfloat16 b = __float2bfloat16_rn(r1);
+      s0[o + k] = a;
+      s1[o + k] = b;
+      s2[o + k] = __float2bfloat16_rn(r1 - __bfloat162float(b));
     }
   }
 }
@@ -73,17 +77,6 @@ __global__ void convert_kernel(const Ti* __restrict__ src, int lds, To* __restri
   dst[(size_t)r * ldd + j] = (To)src[(size_t)r * lds + j];
 }
 
-__global__ void split_bf16_kernel(const float* __restrict__ src, int ld, __nv_bfloat16* __restrict__ hi,
-                                  __nv_bfloat16* __restrict__ lo, int ld_bf, int rows, int cols) {
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long long)rows * cols) return;
-  const int r = (int)(gid / cols), j = (int)(gid % cols);
-  const float v = src[(size_t)r * ld + j];
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  hi[(size_t)r * ld_bf + j] = h;
-  lo[(size_t)r * ld_bf + j] = __float2bfloat16_rn(v - __bfloat162float(h));
-}
-
 __global__ void check_feasible_kernel(const double* __restrict__ P, int ldp,
                                       const double* __restrict__ b, int rows, int m, int* status) {
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -91,6 +84,31 @@ __global__ void check_feasible_kernel(const double* __restrict__ P, int ldp,
   const int r = (int)(gid / m), i = (int)(gid % m);
   const double v = P[(size_t)r * ldp + i];
   if (!(v <= b[i])) atomicOr(status, kStatusInfeasible);
+}
+
+// Feasibility of float states from an exact-split product P (error at most
+// bound * s_i * t_c): certain violations and certain passes are decided from
+// P; the few entries within the bound are recomputed with FP64 FMAs.
+__global__ void check_feasible_bounded_kernel(const double* __restrict__ P, int ldp,
+                                              const double* __restrict__ b, int rows, int m,
+                                              const float* __restrict__ row_scale,
+                                              const float* __restrict__ col_scale, double bound,
+                                              const float* __restrict__ X, int ldx,
+                                              const double* __restrict__ A, int d, int* status) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)rows * m) return;
+  const int r = (int)(gid / m), i = (int)(gid % m);
+  const double v = P[(size_t)r * ldp + i];
+  const double e = bound * (double)row_scale[r] * (double)col_scale[i];
+  if (!(v <= b[i] + e)) {
+    atomicOr(status, kStatusInfeasible);
+  } else if (v > b[i] - e) {
+    const float* x = X + (size_t)r * ldx;
+    const double* a = A + (size_t)i * d;
+    double acc = 0.0;
+    for (int j = 0; j < d; ++j) acc = fma(a[j], (double)x[j], acc);
+    if (acc > b[i]) atomicOr(status, kStatusInfeasible);
+  }
 }
 
 inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
@@ -105,13 +123,16 @@ cudaError_t launch_draw_nu_f64(double* nu, int n_chains, int d, int ld, uint64_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_draw_nu_f32(float* nu, int ld, __nv_bfloat16* hi, __nv_bfloat16* lo, int ld_bf,
+cudaError_t launch_draw_nu_f32(float* nu, int ld, __nv_bfloat16* const split[3], int ld_bf,
                                int n_chains, int d, uint64_t seed, uint32_t t, uint32_t problem,
                                uint32_t chain0, cudaStream_t s) {
   const long long n = (long long)n_chains * ((d + 3) / 4);
   if (n == 0) return cudaSuccess;
-  draw_nu_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(nu, ld, hi, lo, ld_bf, n_chains, d, seed, t,
-                                                      problem, chain0);
+  __nv_bfloat16* s0 = split ? split[0] : nullptr;
+  __nv_bfloat16* s1 = split ? split[1] : nullptr;
+  __nv_bfloat16* s2 = split ? split[2] : nullptr;
+  draw_nu_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(nu, ld, s0, s1, s2, ld_bf, n_chains, d, seed,
+                                                      t, problem, chain0);
   return cudaGetLastError();
 }
 
@@ -132,19 +153,23 @@ cudaError_t launch_convert(const Ti* src, int lds, To* dst, int ldd, int rows, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_bf16(const float* src, int ld, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                              int ld_bf, int rows, int cols, cudaStream_t s) {
-  const long long n = (long long)rows * cols;
-  if (n == 0) return cudaSuccess;
-  split_bf16_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, ld, hi, lo, ld_bf, rows, cols);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_check_feasible(const double* P, int ldp, const double* b, int rows, int m,
                                   int* status, cudaStream_t s) {
   const long long n = (long long)rows * m;
   if (n == 0) return cudaSuccess;
   check_feasible_kernel<<<grid_for(n, 256), 256, 0, s>>>(P, ldp, b, rows, m, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_feasible_bounded(const double* P, int ldp, const double* b, int rows,
+                                          int m, const float* row_scale, const float* col_scale,
+                                          double bound, const float* X, int ldx, const double* A,
+                                          int d, int* status, cudaStream_t s) {
+  const long long n = (long long)rows * m;
+  if (n == 0) return cudaSuccess;
+  check_feasible_bounded_kernel<<<grid_for(n, 256), 256, 0, s>>>(P, ldp, b, rows, m, row_scale,
+                                                                 col_scale, bound, X, ldx, A, d,
+                                                                 status);
   return cudaGetLastError();
 }
 

@@ -22,8 +22,11 @@
 // sets kStatusTimeout, drains its own copies, frees TMEM and returns.
 #include <cuda.h>
 
+#include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "ess_common.cuh"
 #include "ess_gemm_tc.cuh"
@@ -33,7 +36,38 @@ namespace {
 
 constexpr int BM = 128;             // chains per tile (MMA M)
 constexpr int BK = 64;              // bf16 elements per 128-byte swizzle row
-constexpr int NTHREADS = 128;
+constexpr int kThreads = 192;       // producer warp, MMA warp, 4 epilogue warps
+constexpr int kRefreshBN = 64;      // tile width of the exact refresh
+constexpr int kMaxSlices = 7;       // operand slices of the exact refresh
+constexpr int kMaxPasses = 28;      // products per launch
+enum { kModeSum = 0, kModePairs = 1 };
+
+struct PassDesc {
+  unsigned char xi, bi;     // slice indices of the two operands
+  unsigned char group : 7;  // accumulator (sum mode)
+  unsigned char first : 1;  // first product into its accumulator
+  unsigned char shift;      // pairs mode: weight 2^-shift
+};
+
+struct TcMaps {
+  CUtensorMap x[kMaxSlices];  // chain-side operand slices (M = chains)
+  CUtensorMap b[kMaxSlices];  // constraint-side operand slices (N = rows of A)
+};
+
+struct TcArgs {
+  int n_rows, n_cols, kblocks, npass, ngroups;
+  PassDesc pass[kMaxPasses];
+  float* Q;                   // sum mode output
+  int ldq;
+  const float* row_scale;     // pairs mode: t_c per chain
+  const float* col_scale;     // pairs mode: s_i per constraint
+  float* P32;                 // pairs mode outputs (either may be null)
+  double* P64;
+  int ldp;
+  const double* anorm;        // drift normalisation
+  unsigned long long* drift_bits;
+  int* status;
+};
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound per wait
 
 // ---- PTX wrappers ------------------------------------------------------------
@@ -162,30 +196,33 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
          | ((uint32_t)(M >> 4) << 24);      // M / 16
 }
 
-struct TcArgs {
-  int n_rows;    // total chains
-  int n_cols;    // total constraints
-  int kblocks;   // ceil(d / 64)
-  int npass;     // 3 = BF16x3, 1 = plain BF16
-  float* Q;
-  int ldq;
-  int* status;
-};
 
-template <int BN>
-constexpr uint32_t tmem_cols_for() {
-  return BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
+// mbarrier arrive without a transaction count (one arrival).
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <int BN, int STAGES>
-__global__ void __launch_bounds__(NTHREADS, 1)
-tc_gemm_kernel(const __grid_constant__ CUtensorMap map_x0, const __grid_constant__ CUtensorMap map_x1,
-               const __grid_constant__ CUtensorMap map_b0, const __grid_constant__ CUtensorMap map_b1,
-               TcArgs args) {
+// Error-free sum: s + e == a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <int BN>
+constexpr uint32_t tmem_cols_for(int groups) {
+  return groups * BN <= 32 ? 32u : groups * BN <= 64 ? 64u : groups * BN <= 128 ? 128u
+         : groups * BN <= 256 ? 256u : 512u;
+}
+
+template <int BN, int STAGES, int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcArgs args) {
   constexpr uint32_t A_BYTES = BM * BK * 2;
   constexpr uint32_t B_BYTES = BN * BK * 2;
   constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
-  constexpr uint32_t TMEM_COLS = tmem_cols_for<BN>();
+  constexpr int GROUPS = 2;  // sum mode: up to 2 accumulators; pairs mode: 2 buffers
+  constexpr uint32_t TMEM_COLS = tmem_cols_for<BN>(GROUPS);
   static_assert(B_BYTES % 1024 == 0, "BN must be a multiple of 8");
   static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "BN in {32, ..., 256}, multiple of 32");
 
@@ -194,12 +231,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_x0, const __grid_constant
   unsigned char* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
   const uint32_t sbase = smem_u32(smem);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  // bars[0, S): full, bars[S, 2S): empty, bars[2S]: accumulator ready
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  // bars: [0, S) full, [S, 2S) empty, 2S + {0, 1} accumulator full, 2S + {2, 3} accumulator empty
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto full_bar = [&](int s) { return smem_u32(bars + s); };
   auto empty_bar = [&](int s) { return smem_u32(bars + STAGES + s); };
-  const uint32_t accum_bar = smem_u32(bars + 2 * STAGES);
+  auto accf_bar = [&](int b) { return smem_u32(bars + 2 * STAGES + b); };
+  auto acce_bar = [&](int b) { return smem_u32(bars + 2 * STAGES + 2 + b); };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * BN;
@@ -210,7 +248,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_x0, const __grid_constant
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    mbar_init(accum_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf_bar(b), 1);
+      mbar_init(acce_bar(b), 4);  // one arrival per epilogue warp
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -222,7 +263,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_x0, const __grid_constant
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_d = *tmem_slot;
-  const int total = args.kblocks * args.npass;
+  const int npass = args.npass, kblocks = args.kblocks;
+  const int total = kblocks * npass;
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
@@ -237,14 +279,14 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_x0, const __grid_constant
         break;
       }
       if (*abort_flag) break;
-      const int kb = it / args.npass, pass = it % args.npass;
-      // pass 0: hi.hi, pass 1: lo.hi, pass 2: hi.lo
-      const CUtensorMap* mx = pass == 1 ? &map_x1 : &map_x0;
-      const CUtensorMap* mb = pass == 2 ? &map_b1 : &map_b0;
+      int kb, pass;
+      if (MODE == kModeSum) { kb = it / npass; pass = it % npass; }
+      else { pass = it / kblocks; kb = it % kblocks; }
+      const PassDesc pd = args.pass[pass];
       const uint32_t sa = sbase + s * STAGE_BYTES;
       mbar_expect_tx(full_bar(s), STAGE_BYTES);
-      tma_load_2d(sa, mx, kb * BK, m0, full_bar(s));
-      tma_load_2d(sa + A_BYTES, mb, kb * BK, n0, full_bar(s));
+      tma_load_2d(sa, &maps.x[pd.xi], kb * BK, m0, full_bar(s));
+      tma_load_2d(sa + A_BYTES, &maps.b[pd.bi], kb * BK, n0, full_bar(s));
       last_round[s] = round;
     }
     if (*abort_flag) {
@@ -259,6 +301,26 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_x0, const __grid_constant
     for (int it = 0; it < total; ++it) {
       const int s = it % STAGES;
       const int round = it / STAGES;
+      int kb, pass;
+      if (MODE == kModeSum) { kb = it / npass; pass = it % npass; }
+      else { pass = it / kblocks; kb = it % kblocks; }
+      const PassDesc pd = args.pass[pass];
+      uint32_t acc_col;
+      bool fresh;  // first MMA into this accumulator: overwrite instead of add
+      if (MODE == kModeSum) {
+        acc_col = (uint32_t)(pd.group * BN);
+        fresh = kb == 0 && pd.first;
+      } else {
+        const int buf = pass & 1;
+        acc_col = (uint32_t)(buf * BN);
+        fresh = kb == 0;
+        if (kb == 0 && pass >= 2 &&
+            !mbar_wait(acce_bar(buf), (uint32_t)(((pass >> 1) - 1) & 1))) {
+          *abort_flag = 1;
+          break;
+        }
+        if (kb == 0) tc_fence_after();
+      }
       if (!mbar_wait(full_bar(s), (uint32_t)(round & 1))) {
         *abort_flag = 1;
         break;
@@ -270,46 +332,163 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_x0, const __grid_constant
 #pragma unroll
       for (int k = 0; k < BK / 16; ++k) {
         // each K = 16 step advances 32 bytes inside the swizzled row
-        umma_bf16(tmem_d, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc,
-                  (it > 0 || k > 0) ? 1u : 0u);
+        umma_bf16(tmem_d + acc_col, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc,
+                  (fresh && k == 0) ? 0u : 1u);
       }
       umma_commit(empty_bar(s));
+      if (MODE == kModePairs && kb == kblocks - 1) umma_commit(accf_bar(pass & 1));
     }
-    umma_commit(accum_bar);
-  }
-
-  // ---------------- epilogue: TMEM -> registers -> Q ----------------
-  __syncwarp();
-  const bool ready = mbar_wait(accum_bar, 0);
-  tc_fence_after();
-  if (!ready) *abort_flag = 1;
-  const int row = m0 + warp * 32 + lane;
-  const bool row_ok = row < args.n_rows && ready && !*abort_flag;
-  float* qrow = args.Q + (size_t)(row_ok ? row : 0) * args.ldq;
-  const bool vec_ok = (args.ldq & 3) == 0 && ((reinterpret_cast<uintptr_t>(args.Q) & 15) == 0);
+    if (MODE == kModeSum) umma_commit(accf_bar(0));
+  } else if (warp >= 2) {
+    // ---------------- epilogue warps 2..5: TMEM lane quarter warp % 4 ----------------
+    const int quarter = warp & 3;
+    const int row = m0 + quarter * 32 + lane;
+    const uint32_t lane_base = tmem_d + ((uint32_t)(quarter * 32) << 16);
+    if constexpr (MODE == kModeSum) {
+      const bool ready = mbar_wait(accf_bar(0), 0);
+      tc_fence_after();
+      if (!ready) *abort_flag = 1;
+      const bool row_ok = row < args.n_rows && ready && !*abort_flag;
+      float* qrow = args.Q + (size_t)(row_ok ? row : 0) * args.ldq;
+      const bool vec_ok = (args.ldq & 3) == 0 && ((reinterpret_cast<uintptr_t>(args.Q) & 15) == 0);
 #pragma unroll 1
-  for (int c0 = 0; c0 < BN; c0 += 32) {
-    uint32_t v[32];
-    tmem_ld_32cols(tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-    tmem_ld_wait();
-    if (!row_ok) continue;
-    const int col = n0 + c0;
-    if (vec_ok && col + 32 <= args.n_cols) {
-      float4* dst = reinterpret_cast<float4*>(qrow + col);
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld_32cols(lane_base + (uint32_t)c0, v);
+        tmem_ld_wait();
+        float f[32];
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
-                             __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+        for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]);
+        if (args.ngroups > 1) {
+          tmem_ld_32cols(lane_base + (uint32_t)(BN + c0), v);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) f[j] += __uint_as_float(v[j]);
+        }
+        if (!row_ok) continue;
+        const int col = n0 + c0;
+        if (vec_ok && col + 32 <= args.n_cols) {
+          float4* dst = reinterpret_cast<float4*>(qrow + col);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            dst[j] = make_float4(f[4 * j], f[4 * j + 1], f[4 * j + 2], f[4 * j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (col + j < args.n_cols) qrow[col + j] = f[j];
+        }
+      }
     } else {
+      // exact integer products of one slice pair per buffer, accumulated
+      // error-free into (hi, lo) float pairs with the pair's power-of-two weight
+      float hi[BN], lo[BN];
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (col + j < args.n_cols) qrow[col + j] = __uint_as_float(v[j]);
+      for (int j = 0; j < BN; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+      bool ok = true;
+      for (int pass = 0; pass < npass; ++pass) {
+        const int buf = pass & 1;
+        if (*abort_flag || !mbar_wait(accf_bar(buf), (uint32_t)((pass >> 1) & 1))) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // 2^-shift as a float (shift <= 126)
+        const float w = __uint_as_float((uint32_t)(127 - args.pass[pass].shift) << 23);
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          uint32_t v[32];
+          tmem_ld_32cols(lane_base + (uint32_t)(buf * BN + c0), v);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            float sum, err;
+            two_sum(hi[c0 + j], __uint_as_float(v[j]) * w, sum, err);
+            hi[c0 + j] = sum;
+            lo[c0 + j] += err;
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acce_bar(buf));
+      }
+      if (ok && row < args.n_rows) {
+        const float rs = args.row_scale[row];
+        const size_t base = (size_t)row * args.ldp;
+        double drift = 0.0;
+#pragma unroll
+        for (int j = 0; j < BN; ++j) {
+          const int col = n0 + j;
+          if (col < args.n_cols) {
+            const float cs = args.col_scale[col];
+            if (args.P64) args.P64[base + col] = ((double)hi[j] + (double)lo[j]) * (double)rs * (double)cs;
+            if (args.P32) {
+              const float pnew = (hi[j] + lo[j]) * rs * cs;
+              if (args.drift_bits) {
+                const float old = args.P32[base + col];
+                drift = fmax(drift, fabs((double)pnew - (double)old) / args.anorm[col]);
+              }
+              args.P32[base + col] = pnew;
+            }
+          }
+        }
+        if (args.drift_bits && drift > 0.0)
+          atomicMax(args.drift_bits, (unsigned long long)__double_as_longlong(drift));
+      }
     }
   }
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0 && *abort_flag) atomicOr(args.status, kStatusTimeout);
   if (warp == 0) tmem_dealloc(tmem_d, TMEM_COLS);
+}
+
+// Fixed-point slices of the chain states for the exact refresh: per row c,
+// t_c = 2^e with max_j |x_cj| < t_c, and x_cj / t_c = sum_l e_l 2^(-w l) + r,
+// e_l integers in (-2^w, 2^w) stored exactly as bf16.  One warp per row.
+__global__ void slice_rows_kernel(const float* __restrict__ X, int ldx, int rows, int d, int w,
+                                  int K, __nv_bfloat16* __restrict__ slices, int ld_bf,
+                                  size_t slice_stride, float* __restrict__ row_scale) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const float* x = X + (size_t)row * ldx;
+  float mx = 0.f;
+  for (int j = lane; j < d; j += 32) mx = fmaxf(mx, fabsf(x[j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  int e = 0;
+  if (mx > 0.f) (void)frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1): mx < 2^e
+  const float inv_t = ldexpf(1.f, -e);
+  if (lane == 0) row_scale[row] = mx > 0.f ? ldexpf(1.f, e) : 0.f;
+  const float up = ldexpf(1.f, w);
+  for (int j = lane; j < d; j += 32) {
+    float y = x[j] * inv_t;  // exact: power-of-two scaling
+    for (int l = 0; l < K; ++l) {
+      y *= up;
+      const float c = truncf(y);
+      y -= c;
+      slices[(size_t)l * slice_stride + (size_t)row * ld_bf + j] = __float2bfloat16_rn(c);
+    }
+  }
+}
+
+// Floating-point 3-way bf16 split of a float matrix: v = s0 + s1 + s2 exactly.
+__global__ void split3_kernel(const float* __restrict__ src, int ld, int rows, int cols,
+                              __nv_bfloat16* __restrict__ s0, __nv_bfloat16* __restrict__ s1,
+                              __nv_bfloat16* __restrict__ s2, int ld_bf) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)rows * cols) return;
+  const int r = (int)(gid / cols), j = (int)(gid % cols);
+  const float v = src[(size_t)r * ld + j];
+  const __nv_bfloat16 a = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(a);
+  const __nv_bfloat16 b = __float2bfloat16_rn(r1);
+  const __nv_bfloat16 c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+  const size_t o = (size_t)r * ld_bf + j;
+  s0[o] = a;
+  s1[o] = b;
+  s2[o] = c;
 }
 
 // ---- host side ---------------------------------------------------------------
@@ -364,28 +543,28 @@ size_t smem_for() {
   return (size_t)stages_for<BN>() * (BM + BN) * BK * 2 + 1024 + 256;
 }
 
-template <int BN>
-cudaError_t launch_bn(const CUtensorMap& x0, const CUtensorMap& x1, const CUtensorMap& b0,
-                      const CUtensorMap& b1, const TcArgs& args, cudaStream_t s) {
+template <int BN, int MODE>
+cudaError_t launch_bn(const TcMaps& maps, const TcArgs& args, cudaStream_t s) {
   constexpr int ST = stages_for<BN>();
-  auto k = tc_gemm_kernel<BN, ST>;
+  auto k = tc_gemm_kernel<BN, ST, MODE>;
   const size_t smem = smem_for<BN>();
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((args.n_cols + BN - 1) / BN, (args.n_rows + BM - 1) / BM);
-  k<<<grid, NTHREADS, smem, s>>>(x0, x1, b0, b1, args);
+  k<<<grid, kThreads, smem, s>>>(maps, args);
   return cudaGetLastError();
 }
 
-cudaError_t launch_any(int bn, const CUtensorMap& x0, const CUtensorMap& x1, const CUtensorMap& b0,
-                       const CUtensorMap& b1, const TcArgs& args, cudaStream_t s) {
+const int kWidths[6] = {64, 128, 160, 192, 224, 256};
+
+cudaError_t launch_sum(int bn, const TcMaps& maps, const TcArgs& args, cudaStream_t s) {
   switch (bn) {
-    case 64: return launch_bn<64>(x0, x1, b0, b1, args, s);
-    case 128: return launch_bn<128>(x0, x1, b0, b1, args, s);
-    case 160: return launch_bn<160>(x0, x1, b0, b1, args, s);
-    case 192: return launch_bn<192>(x0, x1, b0, b1, args, s);
-    case 224: return launch_bn<224>(x0, x1, b0, b1, args, s);
-    case 256: return launch_bn<256>(x0, x1, b0, b1, args, s);
+    case 64: return launch_bn<64, kModeSum>(maps, args, s);
+    case 128: return launch_bn<128, kModeSum>(maps, args, s);
+    case 160: return launch_bn<160, kModeSum>(maps, args, s);
+    case 192: return launch_bn<192, kModeSum>(maps, args, s);
+    case 224: return launch_bn<224, kModeSum>(maps, args, s);
+    case 256: return launch_bn<256, kModeSum>(maps, args, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -401,16 +580,22 @@ int num_sms() {
   return n;
 }
 
+inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
+
 }  // namespace
 
 struct TcGemmPlan {
-  CUtensorMap a_hi[6], a_lo[6];  // one per tile width (box rows differ)
-  const __nv_bfloat16* A_hi;
-  const __nv_bfloat16* A_lo;
-  int ld_bf, m, d;
+  int ld_bf = 0, m = 0, d = 0;
+  // q = A nu (BF16x6): exact 3-way bf16 split of A rounded to float
+  __nv_bfloat16* a3[3] = {nullptr, nullptr, nullptr};
+  CUtensorMap qmaps[6][3];
+  // exact refresh: fixed-point slices of A (per-row power-of-two scale)
+  int w = 7, K = 5;
+  __nv_bfloat16* aK = nullptr;      // K slices, m x ld_bf each
+  float* col_scale = nullptr;       // s_i
+  CUtensorMap rmaps[kMaxSlices];
+  double bound_factor = 0.0;        // |p_exact - p| <= bound_factor * s_i * t_c
 };
-
-static const int kWidths[6] = {64, 128, 160, 192, 224, 256};
 
 void tc_gemm_tile_for(int n_chains, int m, int* bn, int* stages) {
   // Pick the tile width that minimises (waves of tiles) x (tile width): the
@@ -441,73 +626,193 @@ void tc_gemm_tile_for(int n_chains, int m, int* bn, int* stages) {
   }
 }
 
-cudaError_t tc_gemm_create(TcGemmPlan** plan, const __nv_bfloat16* A_hi, const __nv_bfloat16* A_lo,
-                           int ld_bf, int m, int d) {
+int tc_refresh_slices(int d, int* w_out) {
+  // widest slice w with (2^w - 1)^2 d <= 2^24 (exact FP32 sums), at most 8 bits
+  int w = 8;
+  while (w > 1 && (double)((1 << w) - 1) * ((1 << w) - 1) * d > 16777216.0) --w;
+  int K = (35 + w - 1) / w;
+  if (K > kMaxSlices) K = kMaxSlices;
+  if (w_out) *w_out = w;
+  return K;
+}
+
+cudaError_t tc_gemm_create(TcGemmPlan** plan, const double* A, int m, int d) {
   *plan = nullptr;
   TcGemmPlan* p = new TcGemmPlan();
-  p->A_hi = A_hi;
-  p->A_lo = A_lo;
-  p->ld_bf = ld_bf;
   p->m = m;
   p->d = d;
-  for (int i = 0; i < 6; ++i) {
-    cudaError_t e = make_map(&p->a_hi[i], A_hi, m, d, ld_bf, kWidths[i]);
-    if (e == cudaSuccess) e = make_map(&p->a_lo[i], A_lo, m, d, ld_bf, kWidths[i]);
-    if (e != cudaSuccess) {
-      delete p;
-      return e;
+  p->ld_bf = (d + 7) & ~7;
+  const int ld = p->ld_bf;
+  auto fail = [&](cudaError_t e) {
+    tc_gemm_destroy(p);
+    return e;
+  };
+  // --- BF16x6 operands: A rounded to float, split into three bf16 slices
+  std::vector<float> A32((size_t)m * d);
+  for (size_t i = 0; i < A32.size(); ++i) A32[i] = (float)A[i];
+  float* dA32 = nullptr;
+  cudaError_t e = cudaMalloc(&dA32, sizeof(float) * A32.size());
+  if (e == cudaSuccess) e = cudaMemcpy(dA32, A32.data(), sizeof(float) * A32.size(), cudaMemcpyHostToDevice);
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+    e = cudaMalloc(&p->a3[k], sizeof(__nv_bfloat16) * (size_t)m * ld);
+    if (e == cudaSuccess) e = cudaMemset(p->a3[k], 0, sizeof(__nv_bfloat16) * (size_t)m * ld);
+  }
+  if (e == cudaSuccess) {
+    split3_kernel<<<grid_for((long long)m * d, 256), 256>>>(dA32, d, m, d, p->a3[0], p->a3[1],
+                                                           p->a3[2], ld);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (dA32) cudaFree(dA32);
+  if (e != cudaSuccess) return fail(e);
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i)
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+      e = make_map(&p->qmaps[i][k], p->a3[k], m, d, ld, kWidths[i]);
+  if (e != cudaSuccess) return fail(e);
+
+  // --- exact refresh operands: fixed-point slices of A in FP64 on the host
+  p->K = tc_refresh_slices(d, &p->w);
+  const int w = p->w, K = p->K;
+  std::vector<__nv_bfloat16> slices((size_t)K * m * ld, __float2bfloat16_rn(0.f));
+  std::vector<float> cs(m);
+  for (int i = 0; i < m; ++i) {
+    const double* a = A + (size_t)i * d;
+    double mx = 0.0;
+    for (int j = 0; j < d; ++j) mx = std::fmax(mx, std::fabs(a[j]));
+    int ex = 0;
+    if (mx > 0.0) (void)std::frexp(mx, &ex);
+    cs[i] = mx > 0.0 ? std::ldexp(1.0f, ex) : 0.0f;
+    for (int j = 0; j < d; ++j) {
+      double y = mx > 0.0 ? std::ldexp(a[j], -ex) : 0.0;
+      for (int k = 0; k < K; ++k) {
+        y = std::ldexp(y, w);
+        const double c = std::trunc(y);
+        y -= c;
+        slices[(size_t)k * m * ld + (size_t)i * ld + j] = __float2bfloat16_rn((float)c);
+      }
     }
   }
+  e = cudaMalloc(&p->aK, sizeof(__nv_bfloat16) * slices.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->aK, slices.data(), sizeof(__nv_bfloat16) * slices.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&p->col_scale, sizeof(float) * m);
+  if (e == cudaSuccess) e = cudaMemcpy(p->col_scale, cs.data(), sizeof(float) * m, cudaMemcpyHostToDevice);
+  for (int k = 0; k < K && e == cudaSuccess; ++k)
+    e = make_map(&p->rmaps[k], p->aK + (size_t)k * m * ld, m, d, ld, kRefreshBN);
+  if (e != cudaSuccess) return fail(e);
+  // truncation of both operands (3 terms) plus the dropped pairs k + l > K + 1,
+  // each below 2^(-wK) per element, summed over d elements
+  p->bound_factor = (double)d * (3.0 + K * (K - 1) / 2.0) * std::ldexp(1.0, -w * K);
   *plan = p;
   return cudaSuccess;
 }
 
 void tc_gemm_destroy(TcGemmPlan* plan) {
+  if (!plan) return;
+  for (int k = 0; k < 3; ++k)
+    if (plan->a3[k]) cudaFree(plan->a3[k]);
+  if (plan->aK) cudaFree(plan->aK);
+  if (plan->col_scale) cudaFree(plan->col_scale);
   delete plan;
 }
 
-cudaError_t tc_gemm_bf16x3(TcGemmPlan* plan, const __nv_bfloat16* nu_hi,
-                           const __nv_bfloat16* nu_lo, int ld_bf, int n_chains, float* Q, int ldq,
-                           int* status, cudaStream_t s) {
-  if (!plan || n_chains <= 0) return n_chains == 0 ? cudaSuccess : cudaErrorInvalidValue;
+int tc_refresh_num_slices(const TcGemmPlan* plan) { return plan->K; }
+double tc_refresh_bound_factor(const TcGemmPlan* plan) { return plan->bound_factor; }
+const float* tc_refresh_col_scale(const TcGemmPlan* plan) { return plan->col_scale; }
+
+cudaError_t tc_split3(const float* src, int ld, int rows, int cols, __nv_bfloat16* s0,
+                      __nv_bfloat16* s1, __nv_bfloat16* s2, int ld_bf, cudaStream_t s) {
+  const long long n = (long long)rows * cols;
+  if (n == 0) return cudaSuccess;
+  split3_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, ld, rows, cols, s0, s1, s2, ld_bf);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_q(TcGemmPlan* plan, __nv_bfloat16* const nu[3], int ld_bf, int n_chains,
+                      float* Q, int ldq, int* status, cudaStream_t s) {
+  if (!plan) return cudaErrorInvalidValue;
+  if (n_chains == 0) return cudaSuccess;
   if (ld_bf != plan->ld_bf) return cudaErrorInvalidValue;
   int bn = 0;
   tc_gemm_tile_for(n_chains, plan->m, &bn, nullptr);
   int wi = 0;
   while (kWidths[wi] != bn) ++wi;
-  CUtensorMap x0, x1;
-  cudaError_t e = make_map(&x0, nu_hi, n_chains, plan->d, ld_bf, BM);
-  if (e == cudaSuccess) e = make_map(&x1, nu_lo, n_chains, plan->d, ld_bf, BM);
-  if (e != cudaSuccess) return e;
+  TcMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int k = 0; k < 3; ++k) {
+    cudaError_t e = make_map(&maps.x[k], nu[k], n_chains, plan->d, ld_bf, BM);
+    if (e != cudaSuccess) return e;
+    maps.b[k] = plan->qmaps[wi][k];
+  }
   TcArgs a;
+  std::memset(&a, 0, sizeof(a));
   a.n_rows = n_chains;
   a.n_cols = plan->m;
   a.kblocks = (plan->d + BK - 1) / BK;
-  a.npass = 3;
+  // group 0: hi.hi; group 1: the five products of order 2^-8 and 2^-16
+  const unsigned char order[6][3] = {{0, 0, 0}, {2, 0, 1}, {1, 1, 1}, {0, 2, 1}, {1, 0, 1}, {0, 1, 1}};
+  a.npass = 6;
+  a.ngroups = 2;
+  for (int i = 0; i < 6; ++i) {
+    a.pass[i].xi = order[i][0];
+    a.pass[i].bi = order[i][1];
+    a.pass[i].group = order[i][2];
+    a.pass[i].first = (i == 0 || i == 1) ? 1 : 0;
+    a.pass[i].shift = 0;
+  }
   a.Q = Q;
   a.ldq = ldq;
   a.status = status;
-  return launch_any(bn, x0, x1, plan->a_hi[wi], plan->a_lo[wi], a, s);
+  return launch_sum(bn, maps, a, s);
 }
 
-cudaError_t tc_gemm_bf16(const __nv_bfloat16* X, const __nv_bfloat16* B, int ld_bf, int n, int m,
-                         int d, float* Q, int ldq, int* status, cudaStream_t s) {
-  if (n <= 0 || m <= 0) return cudaSuccess;
-  int bn = 0;
-  tc_gemm_tile_for(n, m, &bn, nullptr);
-  CUtensorMap x0, b0;
-  cudaError_t e = make_map(&x0, X, n, d, ld_bf, BM);
-  if (e == cudaSuccess) e = make_map(&b0, B, m, d, ld_bf, bn);
+cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
+                       __nv_bfloat16* x_slices, size_t slice_stride, float* row_scale,
+                       float* P32, double* P64, int ldp, const double* anorm,
+                       unsigned long long* drift_bits, int* status, cudaStream_t s) {
+  if (!plan) return cudaErrorInvalidValue;
+  if (n_chains == 0) return cudaSuccess;
+  const int K = plan->K, ld = plan->ld_bf;
+  slice_rows_kernel<<<grid_for((long long)n_chains * 32, 256), 256, 0, s>>>(
+      X, ldx, n_chains, plan->d, plan->w, K, x_slices, ld, slice_stride, row_scale);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  TcMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int k = 0; k < K; ++k) {
+    e = make_map(&maps.x[k], x_slices + (size_t)k * slice_stride, n_chains, plan->d, ld, BM);
+    if (e != cudaSuccess) return e;
+    maps.b[k] = plan->rmaps[k];
+  }
   TcArgs a;
-  a.n_rows = n;
-  a.n_cols = m;
-  a.kblocks = (d + BK - 1) / BK;
-  a.npass = 1;
-  a.Q = Q;
-  a.ldq = ldq;
+  std::memset(&a, 0, sizeof(a));
+  a.n_rows = n_chains;
+  a.n_cols = plan->m;
+  a.kblocks = (plan->d + BK - 1) / BK;
+  // slice pairs (k, l), k + l <= K + 1 (1-based), smallest weight first
+  int np = 0;
+  for (int sum = K + 1; sum >= 2; --sum)
+    for (int k = 1; k < sum; ++k) {
+      const int l = sum - k;
+      if (k > K || l > K) continue;
+      a.pass[np].xi = (unsigned char)(l - 1);
+      a.pass[np].bi = (unsigned char)(k - 1);
+      a.pass[np].group = 0;
+      a.pass[np].first = 1;
+      a.pass[np].shift = (unsigned char)(plan->w * sum);
+      ++np;
+    }
+  a.npass = np;
+  a.ngroups = np;
+  a.row_scale = row_scale;
+  a.col_scale = plan->col_scale;
+  a.P32 = P32;
+  a.P64 = P64;
+  a.ldp = ldp;
+  a.anorm = anorm;
+  a.drift_bits = drift_bits;
   a.status = status;
-  return launch_any(bn, x0, x0, b0, b0, a, s);
+  return launch_bn<kRefreshBN, kModePairs>(maps, a, s);
 }
 
 }  // namespace ess

@@ -29,12 +29,14 @@ def f32(a):
 
 
 def q_error_bound(A, NU):
-    """Bound on |q_bf16x3 - a.nu| per row and chain: the dropped lo.lo term and
-    the residuals of both splits are each below 2^-16 |a_j nu_j| relative, plus
-    FP32 accumulation over K/16 tensor-core steps."""
+    """Bound on |q - a.nu| per row and chain for the BF16x6 GEMM: both operands
+    are split exactly into three bf16 slices (relative weights 1, 2^-8, 2^-16);
+    the three dropped slice products are each below 2^-24 |a_j nu_j|, plus the
+    FP32 accumulation over K/16 tensor-core steps and the final addition of the
+    two accumulators."""
     absdot = np.abs(NU) @ np.abs(A).T
     k = A.shape[1]
-    return absdot * (3 * 2.0**-16 + (k / 16 + 8) * 2.0**-24)
+    return absdot * (12 + k / 16) * 2.0**-24
 
 
 @pytest.mark.parametrize("n,m,d", [(1, 20, 10), (130, 300, 137), (256, 448, 64),
@@ -59,8 +61,27 @@ def test_products_tensor_core_gemm(n, m, d):
     assert np.all(err <= bound), float((err / bound).max())
     # typical error far below the bound (a wrong operand layout would not be)
     assert np.median(err / np.maximum(bound, 1e-300)) < 0.2
+    # p = A x by the exact-split refresh: within its stated bound (truncated
+    # fixed-point slices) plus one rounding to float
     p_ref = X @ A.T
-    np.testing.assert_allclose(P, p_ref.astype(np.float32), rtol=2e-7, atol=1e-12)
+    tol = np.abs(p_ref) * 2.0**-23 + refresh_bound(A, X)
+    assert np.all(np.abs(P - p_ref) <= tol), float(np.max(np.abs(P - p_ref) / tol))
+
+
+def refresh_bound(A, X):
+    """|p_refresh - A x| bound of the exact-split refresh: w-bit slices with
+    (2^w - 1)^2 d <= 2^24, K = ceil(35 / w) slices per operand, per-row and
+    per-chain power-of-two scales s_i > max |a_i|, t_c > max |x_c|."""
+    d = A.shape[1]
+    w = 8
+    while w > 1 and ((1 << w) - 1) ** 2 * d > 2**24:
+        w -= 1
+    K = min(-(-35 // w), 7)
+    factor = d * (3 + K * (K - 1) / 2) * 2.0 ** (-w * K)
+    s = 2.0 ** (np.floor(np.log2(np.abs(A).max(axis=1))) + 1)
+    mx = np.abs(X.astype(np.float32)).max(axis=1).astype(np.float64)
+    t = np.where(mx > 0, 2.0 ** (np.floor(np.log2(np.maximum(mx, 1e-300))) + 1), 0.0)
+    return factor * t[:, None] * s[None, :]
 
 
 def _predicted_angle_error(A, b, X, NU, P, Q):
