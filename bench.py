@@ -3,7 +3,7 @@
 
 Metric: chain-iterations per second at d = 1000, m = 2000, 8192 chains (the
 unit-norm Gaussian polytope family, b ~ U[0.05, 0.5], X0 = 0), for the mixed
-form (BF16x3 tensor-core GEMM, FP32 step, FP64 checks) -- the headline value --
+form (BF16x6 tensor-core GEMM, FP32 step, FP64 checks) -- the headline value --
 and the plain FP64 form, each with its roofline fraction.
 
 A "step" is one pass of the whole hot path over all chains: nu draw, q = A nu,
