@@ -79,7 +79,10 @@ typedef struct {
     double residual_margin;     /* rows with p_i > b_i - residual_margin*||a_i||
                                    get their residual a_i.x - b_i recomputed in
                                    FP64; default 1e-8 (FP64 form), 2e-4 (mixed) */
-    int sort_threads;           /* threads per chain for the sort; 0 = auto */
+    int sort_threads;           /* 0 (default): one warp per chain, with a
+                                   CTA per chain for chains that keep more than
+                                   128 arcs after the domination prune;
+                                   > 0: a CTA per chain for every chain */
     int reserved[8];
 } ess_config;
 
@@ -91,6 +94,7 @@ typedef struct {
     double max_refresh_drift;   /* max |p_carried - p_refresh| / ||a_i|| seen */
     double max_residual;        /* max a_i.x - b_i over emitted iterates (rechecked rows) */
     long long numeric_errors;   /* chains that produced NaN/Inf */
+    long long sort_keys;        /* arcs left to sort after dropping dominated ones */
 } ess_stats;
 
 /* Fills cfg with the defaults above for the given precision. */

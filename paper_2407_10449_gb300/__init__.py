@@ -67,7 +67,7 @@ class ess_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("rejections", ctypes.c_longlong),
                 ("residual_rechecks", ctypes.c_longlong), ("tangent_fp64", ctypes.c_longlong),
                 ("max_refresh_drift", ctypes.c_double), ("max_residual", ctypes.c_double),
-                ("numeric_errors", ctypes.c_longlong)]
+                ("numeric_errors", ctypes.c_longlong), ("sort_keys", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

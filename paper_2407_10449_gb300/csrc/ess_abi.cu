@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "ess.h"
@@ -71,9 +72,12 @@ struct ess_state {
   double* b64 = nullptr;
   double* anorm = nullptr;
   float* b32 = nullptr;
+  void* slack = nullptr;   // m thresholds b_i - margin ||a_i|| (T, rounded down)
   // work buffers (device), sized for `cap` chains
   int cap = 0;
-  void* P = nullptr;       // n x m, T
+  void* P = nullptr;       // n x m, T: p = A x of the current states
+  void* P2 = nullptr;      // n x m, T: next p (double buffer; swapped after each step)
+  int* ovf = nullptr;      // n + 1 ints: [0] count, [1..] chains left to the CTA kernel
   void* Q = nullptr;       // n x m, T
   void* NU = nullptr;      // n x d, T
   float* Xw = nullptr;     // n x d, mixed-form working states (the loaded chains)
@@ -146,6 +150,9 @@ size_t elem(const ess_state* s) { return mixed(s) ? sizeof(float) : sizeof(doubl
 
 void free_work(ess_state* s) {
   if (s->P) cudaFree(s->P);
+  if (s->P2) cudaFree(s->P2);
+  s->P2 = nullptr;
+  dev_free(s->ovf);
   if (s->Q) cudaFree(s->Q);
   if (s->NU) cudaFree(s->NU);
   s->P = s->Q = s->NU = nullptr;
@@ -164,6 +171,8 @@ ess_status ensure_capacity(ess_state* s, int n) {
   free_work(s);
   const size_t e = elem(s);
   ESS_CUDA(cudaMalloc(&s->P, (size_t)n * s->m * e));
+  ESS_CUDA(cudaMalloc(&s->P2, (size_t)n * s->m * e));
+  ESS_CUDA(dev_alloc(&s->ovf, (size_t)n + 1));
   ESS_CUDA(cudaMalloc(&s->Q, (size_t)n * s->m * e));
   ESS_CUDA(cudaMalloc(&s->NU, (size_t)n * s->d * e));
   if (mixed(s)) {
@@ -265,6 +274,7 @@ ess::ChainParams<T> base_params(ess_state* s, int n) {
   p.b64 = s->b64;
   p.A64 = s->A64;
   p.anorm = s->anorm;
+  p.slack = static_cast<const T*>(s->slack);
   p.NU = static_cast<const T*>(s->NU);
   p.trim_eps = s->cfg.trim_eps;
   p.tangent_thresh = s->cfg.tangent_thresh;
@@ -272,6 +282,28 @@ ess::ChainParams<T> base_params(ess_state* s, int n) {
   p.stats = s->dstats;
   p.status = s->dstatus;
   return p;
+}
+
+// One chain step of all chains: the warp-per-chain kernel, then the
+// CTA-per-chain kernel for the chains it left (too many arcs after the prune),
+// reading P and writing P2; the buffers are swapped afterwards.
+template <typename T>
+ess_status launch_step(ess_state* s, ess::ChainParams<T> p, cudaStream_t st) {
+  p.P_in = static_cast<const T*>(s->P);
+  p.P_out = static_cast<T*>(s->P2);
+  if (s->cfg.sort_threads > 0) {
+    ESS_CUDA(ess::launch_chain_step<T>(p, s->chain_threads, st));
+  } else {
+    ESS_CUDA(cudaMemsetAsync(s->ovf, 0, sizeof(int), st));
+    p.overflow_count = s->ovf;
+    p.overflow_list = s->ovf + 1;
+    ESS_CUDA(ess::launch_chain_step_warp<T>(p, st));
+    p.chain_list = s->ovf + 1;
+    p.list_count = s->ovf;
+    ESS_CUDA(ess::launch_chain_step<T>(p, s->chain_threads, st));
+  }
+  std::swap(s->P, s->P2);
+  return ESS_OK;
 }
 
 ess_status read_status(ess_state* s, cudaStream_t st) {
@@ -376,6 +408,23 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
   if (e == cudaSuccess) e = cudaMemcpy(s->b64, b, sizeof(double) * m, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(s->anorm, norms.data(), sizeof(double) * m, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    // residual-recheck thresholds, rounded towards -inf in the step's precision
+    const size_t esz = c.precision == ESS_PREC_MIXED ? sizeof(float) : sizeof(double);
+    std::vector<unsigned char> buf(esz * m);
+    for (int i = 0; i < m; ++i) {
+      const double v = b[i] - c.residual_margin * norms[i];
+      if (c.precision == ESS_PREC_MIXED) {
+        float f = (float)v;
+        if ((double)f > v) f = std::nextafter(f, -INFINITY);
+        std::memcpy(&buf[esz * i], &f, esz);
+      } else {
+        std::memcpy(&buf[esz * i], &v, esz);
+      }
+    }
+    e = cudaMalloc(&s->slack, esz * m);
+    if (e == cudaSuccess) e = cudaMemcpy(s->slack, buf.data(), esz * m, cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = dev_alloc(&s->dstats, 1);
   if (e == cudaSuccess) e = dev_alloc(&s->dstatus, 1);
   if (e == cudaSuccess) e = cudaMemset(s->dstats, 0, sizeof(DevStats));
@@ -399,6 +448,8 @@ void ess_destroy(ess_state* s) {
   dev_free(s->A64);
   dev_free(s->b64);
   dev_free(s->anorm);
+  if (s->slack) cudaFree(s->slack);
+  s->slack = nullptr;
   dev_free(s->b32);
   dev_free(s->dstats);
   dev_free(s->dstatus);
@@ -490,8 +541,9 @@ ess_status ess_chains_step(ess_state* s, int n_iter, uint64_t seed, void* sample
         p.samples = static_cast<float*>(samples) + rec_off;
         p.sample_stride = (long long)n_rec * d;
       }
-      PhaseScope ps(s, st, ESS_PHASE_CHAIN);
-      ESS_CUDA(ess::launch_chain_step<float>(p, s->chain_threads, st));
+      PhaseScope ps(s, st, ESS_PHASE_CHAIN, s->cfg.sort_threads > 0 ? 1 : 2);
+      ess_status rc = launch_step<float>(s, p, st);
+      if (rc != ESS_OK) return rc;
     } else {
       {
         PhaseScope ps(s, st, ESS_PHASE_DRAW);
@@ -511,8 +563,9 @@ ess_status ess_chains_step(ess_state* s, int n_iter, uint64_t seed, void* sample
         p.samples = static_cast<double*>(samples) + rec_off;
         p.sample_stride = (long long)n_rec * d;
       }
-      PhaseScope ps(s, st, ESS_PHASE_CHAIN);
-      ESS_CUDA(ess::launch_chain_step<double>(p, s->chain_threads, st));
+      PhaseScope ps(s, st, ESS_PHASE_CHAIN, s->cfg.sort_threads > 0 ? 1 : 2);
+      ess_status rc = launch_step<double>(s, p, st);
+      if (rc != ESS_OK) return rc;
     }
   }
   s->t_next += n_iter;
@@ -655,7 +708,8 @@ ess_status ess_step_with_draws(ess_state* s, const double* X, const double* nu, 
     p.max_pieces = max_pieces;
     p.npieces_out = n_pieces;
     p.rejected_out = rejected;
-    ESS_CUDA(ess::launch_chain_step<float>(p, s->chain_threads, st));
+    rc = launch_step<float>(s, p, st);
+    if (rc != ESS_OK) return rc;
     ESS_CUDA((ess::launch_convert<float, double>(s->Xw, d, X_next, d, n, d, st)));
     s->host_steps += n;
   } else {
@@ -674,7 +728,8 @@ ess_status ess_step_with_draws(ess_state* s, const double* X, const double* nu, 
     p.max_pieces = max_pieces;
     p.npieces_out = n_pieces;
     p.rejected_out = rejected;
-    ESS_CUDA(ess::launch_chain_step<double>(p, s->chain_threads, st));
+    rc = launch_step<double>(s, p, st);
+    if (rc != ESS_OK) return rc;
     s->host_steps += n;
   }
   return read_status(s, st);
@@ -763,6 +818,7 @@ ess_status ess_get_stats(const ess_state* s, ess_stats* out) {
   out->residual_rechecks = (long long)h.rechecks;
   out->tangent_fp64 = (long long)h.tangent_fp64;
   out->numeric_errors = (long long)h.numeric_errors;
+  out->sort_keys = (long long)h.sort_keys;
   double drift = 0.0;
   std::memcpy(&drift, &h.max_drift_bits, sizeof(double));
   out->max_refresh_drift = drift;

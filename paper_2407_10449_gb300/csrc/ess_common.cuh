@@ -26,7 +26,7 @@ struct DevStats {
   unsigned long long numeric_errors;
   unsigned long long max_drift_bits;     // double bits of a non-negative max
   unsigned long long max_residual_bits;  // ordered bits of max residual (see enc)
-  unsigned long long pad;
+  unsigned long long sort_keys;          // arcs left for the sort after the prune
 };
 
 // Error flags in the device status word.

@@ -62,6 +62,8 @@ struct ChainParams {
   const double* b64;    // m, exact b
   const double* A64;    // m x d, exact A (residual rechecks)
   const double* anorm;  // m, ||a_i||_2
+  const T* slack;       // m, b_i - margin ||a_i|| rounded down (nullptr: computed from
+                        // b64, margin and anorm)
   const T* X;           // current states
   T* X_out;             // next states (may alias X)
   const T* NU;          // nu (n_chains x d)
@@ -78,10 +80,26 @@ struct ChainParams {
   int* rejected_out;
   DevStats* stats;
   int* status;
+  // CTA kernel, list mode: process the chains chain_list[0 .. *list_count)
+  const int* chain_list;
+  const int* list_count;
+  // warp kernel: chains with too many arcs to sort in a warp are appended here
+  int* overflow_list;
+  int* overflow_count;
 };
 
 template <typename T>
 cudaError_t launch_chain_step(const ChainParams<T>& p, int threads, cudaStream_t s);
+
+// One warp per chain: prune, sort up to kWarpSortCap arcs in registers, sweep,
+// draw and move.  Chains with more arcs left after the prune are appended to
+// p.overflow_list (untouched) for launch_chain_step in list mode.
+// p.P_out must differ from p.P_in (a rejected move restores p from P_in).
+template <typename T>
+cudaError_t launch_chain_step_warp(const ChainParams<T>& p, cudaStream_t s);
+template <typename T>
+size_t chain_warp_smem_bytes(int m);
+constexpr int kWarpSortCap = 128;
 
 // Threads per chain the chain-step kernel uses for m constraints (0 if m is
 // beyond the supported maximum), and the dynamic shared memory it needs.

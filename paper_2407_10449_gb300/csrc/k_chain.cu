@@ -21,79 +21,17 @@
 // roots run in float except near tangency (|b/r| > 1 - tangent_thresh), where
 // r, b/r, atan2 and arccos are evaluated in double (Sec. 3.2 discusses why
 // b/r ~ +-1 is the delicate case).
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
+#include "chain_math.cuh"
 #include "ess_kernels.cuh"
 
 namespace ess {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-template <typename T> struct Lim;
-template <> struct Lim<float> {
-  __device__ static float inf() { return INFINITY; }
-  __device__ static float two_pi() { return kTwoPiF; }
-};
-template <> struct Lim<double> {
-  __device__ static double inf() { return INFINITY; }
-  __device__ static double two_pi() { return kTwoPi; }
-};
-
-// ---- roots (App. B, Sec. 3.2) ------------------------------------------
-__device__ __forceinline__ bool roots_dp(double p, double q, double b, double& al, double& be,
-                                         bool& infeasible) {
-  double r = sqrt(p * p + q * q);
-  if (r == 0.0) {
-    infeasible = b < 0.0;
-    return false;
-  }
-  double ratio = b / r;
-  if (ratio >= 1.0) return false;
-  if (ratio < -1.0) ratio = -1.0;
-  double tau = atan2(q, p);
-  if (tau < 0.0) tau += kTwoPi;
-  double h = acos(ratio);
-  al = fmax(0.0, tau - h);
-  be = fmin(kTwoPi, tau + h);
-  return true;
-}
-
-__device__ __forceinline__ bool roots(double p, double q, double b, double b64, double,
-                                      double& al, double& be, bool& infeasible, int& tangent) {
-  (void)b;
-  (void)tangent;
-  return roots_dp(p, q, b64, al, be, infeasible);
-}
-
-__device__ __forceinline__ bool roots(float p, float q, float b, double b64, double thresh,
-                                      float& al, float& be, bool& infeasible, int& tangent) {
-  float r2 = fmaf(p, p, q * q);
-  if (r2 == 0.0f) {
-    infeasible = b64 < 0.0;
-    return false;
-  }
-  float ratio = b / sqrtf(r2);
-  if (ratio >= (float)(1.0 + thresh)) return false;  // clearly no root
-  if (fabsf(ratio) > (float)(1.0 - thresh)) {
-    // near tangency: the arccos argument and the angles in double
-    ++tangent;
-    double ad, bd;
-    bool has = roots_dp((double)p, (double)q, b64, ad, bd, infeasible);
-    if (has) {
-      al = (float)ad;
-      be = fminf((float)bd, kTwoPiF);
-    }
-    return has;
-  }
-  float tau = atan2f(q, p);
-  if (tau < 0.0f) tau += kTwoPiF;
-  float h = acosf(ratio);
-  al = fmaxf(0.0f, tau - h);
-  be = fminf(kTwoPiF, tau + h);
-  return true;
-}
+using namespace chainmath;
 
 // ---- block scans ---------------------------------------------------------
 struct OpAdd {
@@ -137,18 +75,6 @@ __device__ V block_exclusive_scan(V v, V identity, Op op, V* tmp, V& total) {
 }
 
 // ---- kernel ----------------------------------------------------------------
-template <typename T> struct BitsOf;
-template <> struct BitsOf<float> {
-  typedef unsigned int type;
-  __device__ static type get(float v) { return __float_as_uint(v); }
-  __device__ static float put(type v) { return __uint_as_float(v); }
-};
-template <> struct BitsOf<double> {
-  typedef unsigned long long type;
-  __device__ static type get(double v) { return (unsigned long long)__double_as_longlong(v); }
-  __device__ static double put(type v) { return __longlong_as_double((long long)v); }
-};
-
 // Shared-memory slot of sorted position e: one padding word per 32 keeps the
 // per-thread chunks (stride ITEMS) on distinct banks.
 __device__ __forceinline__ int pad_idx(int e) { return e + (e >> 5); }
@@ -160,7 +86,6 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
   constexpr int NSLOT = NT * ITEMS;
   constexpr int NPAD = NSLOT + NSLOT / 32;
   constexpr int NW = NT / 32;
-  typedef typename BitsOf<T>::type Bits;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s_key = reinterpret_cast<T*>(smem_raw);
   T* s_val = s_key + NPAD;
@@ -169,105 +94,136 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
 
   __shared__ int s_itmp[NW];
   __shared__ T s_ttmp[NW];
-  __shared__ Bits s_bmax[kBuckets];   // max beta (bits) of the arcs whose alpha falls in a bucket
-  __shared__ T s_gearly[kBuckets];    // max beta of the arcs in all earlier buckets
-  __shared__ int s_nflag, s_reject, s_best, s_bad, s_tangent;
+  __shared__ unsigned int s_bmax[kBuckets];  // max approximate beta (bits) per alpha bucket
+  __shared__ float s_gearly[kBuckets];       // max approximate beta over buckets <= j - 2
+  __shared__ int s_nflag, s_reject, s_best, s_bad, s_tangent, s_noroot;
   __shared__ T s_theta;
 
-  const int c = blockIdx.x;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int m = prm.m, d = prm.d;
   const T two_pi = Lim<T>::two_pi();
   const T inf = Lim<T>::inf();
 
+  // one chain per CTA, or (list mode) the chains of prm.chain_list, strided
+  // over the grid
+  const int n_work = prm.chain_list ? *prm.list_count : prm.n_chains;
+  for (int work = blockIdx.x; work < n_work; work += gridDim.x) {
+  const int c = prm.chain_list ? prm.chain_list[work] : work;
+  __syncthreads();
   if (tid == 0) {
     s_nflag = 0;
     s_reject = 0;
     s_best = -1;
     s_bad = 0;
     s_tangent = 0;
+    s_noroot = 0;
   }
   for (int k = tid; k < kBuckets; k += NT) s_bmax[k] = 0;
   __syncthreads();
 
-  // ---- 1. roots of every row, kept in registers --------------------------
+  // ---- 1. p, q of every row (kept in registers) and approximate arcs --------
   const T* Prow = prm.P_in + (size_t)c * prm.ldp;
   const T* Qrow = prm.Q + (size_t)c * prm.ldp;
-  T p[ITEMS], q[ITEMS], al[ITEMS], be[ITEMS];
-  bool has[ITEMS];
-  int tangent = 0;
-  bool infeasible = false, nonfinite = false;
-  const T to_bucket = (T)(kBuckets / kTwoPi);
+  T p[ITEMS], q[ITEMS];
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
     const int i = tid + r * NT;
-    has[r] = false;
-    p[r] = T(0);
-    q[r] = T(0);
+    p[r] = i < m ? Prow[i] : T(0);
+    q[r] = i < m ? Qrow[i] : T(0);
+  }
+  const T tlo = (T)(1.0 - prm.tangent_thresh);
+  const T thi = (T)(1.0 + prm.tangent_thresh);
+  int cls[ITEMS];
+  float a_ap[ITEMS], b_ap[ITEMS];
+  bool infeasible = false, nonfinite = false;
+  const float to_bucket = (float)(kBuckets / kTwoPi);
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    const int i = tid + r * NT;
+    cls[r] = kRowNone;
+    a_ap[r] = 0.f;
+    b_ap[r] = 0.f;
     if (i < m) {
-      p[r] = Prow[i];
-      q[r] = Qrow[i];
-      nonfinite |= !isfinite((double)p[r]) || !isfinite((double)q[r]);
+      nonfinite |= !isfinite(p[r]) || !isfinite(q[r]);
       bool inf_row = false;
-      has[r] = roots(p[r], q[r], prm.b[i], prm.b64[i], prm.tangent_thresh, al[r], be[r], inf_row,
-                     tangent);
+      cls[r] = classify_row<T>(p[r], q[r], prm.b[i], prm.b64[i], tlo, thi, a_ap[r], b_ap[r],
+                               inf_row);
       infeasible |= inf_row;
-      if (has[r]) {
-        const int bk = min(kBuckets - 1, (int)(al[r] * to_bucket));
-        atomicMax(&s_bmax[bk], BitsOf<T>::get(be[r]));
+      if (cls[r] == kRowApprox) {
+        const int bk = min(kBuckets - 1, (int)(a_ap[r] * to_bucket));
+        atomicMax(&s_bmax[bk], __float_as_uint(b_ap[r]));
       }
     }
   }
-  if (tangent) atomicAdd(&s_tangent, tangent);
   __syncthreads();
 
   // ---- domination prune ------------------------------------------------------
-  // An arc (alpha_i, beta_i) lies inside an arc that starts in an earlier
-  // alpha bucket whenever beta_i <= max beta of the earlier buckets (bucket
-  // indices are monotone in alpha), so it cannot change the union of arcs:
-  // I_act and its piece endpoints are unchanged when it is dropped.
+  // Arc i (alpha_i in bucket j) lies inside an arc D from a bucket <= j - 2
+  // whenever beta_i <= beta_D: then alpha_D < alpha_i (buckets are wider than
+  // twice the approximation error) and D covers arc i, so dropping arc i
+  // leaves the union of arcs -- I_act and its piece endpoints -- unchanged.
+  // With approximate angles the test is b_ap_i + 2 margin <= max b_ap over
+  // the buckets <= j - 2.
   if (warp == 0) {
-    // exclusive prefix max over the buckets, two buckets per lane
-    const T b0 = BitsOf<T>::put(s_bmax[2 * lane]);
-    const T b1 = BitsOf<T>::put(s_bmax[2 * lane + 1]);
-    T incl = b0 > b1 ? b0 : b1;
+    // lane l holds buckets 2l and 2l + 1; incl = max over buckets <= 2l + 1
+    const float b0 = __uint_as_float(s_bmax[2 * lane]);
+    const float b1 = __uint_as_float(s_bmax[2 * lane + 1]);
+    float incl = fmaxf(b0, b1);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const T y = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl = y > incl ? y : incl;
+      const float y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl = fmaxf(y, incl);
     }
-    T excl = __shfl_up_sync(kFull, incl, 1);
-    if (lane == 0) excl = T(-1);
-    s_gearly[2 * lane] = excl;
-    s_gearly[2 * lane + 1] = b0 > excl ? b0 : excl;
+    const float incl1 = __shfl_up_sync(kFull, incl, 1);  // buckets <= 2l - 1
+    const float incl2 = __shfl_up_sync(kFull, incl, 2);  // buckets <= 2l - 3
+    const float b0_prev = __shfl_up_sync(kFull, b0, 1);  // bucket 2l - 2
+    // max over buckets <= j - 2 for j = 2l and j = 2l + 1 (-1: no such bucket)
+    s_gearly[2 * lane] = lane == 0 ? -1.f : (lane == 1 ? b0_prev : fmaxf(incl2, b0_prev));
+    s_gearly[2 * lane + 1] = lane == 0 ? -1.f : incl1;
   }
   __syncthreads();
   int my_count = 0;
+  bool keep[ITEMS];
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
-    if (has[r]) {
-      const int bk = min(kBuckets - 1, (int)(al[r] * to_bucket));
-      has[r] = be[r] > s_gearly[bk];
-      my_count += has[r] ? 1 : 0;
+    keep[r] = cls[r] == kRowKeep;
+    if (cls[r] == kRowApprox) {
+      const int bk = min(kBuckets - 1, (int)(a_ap[r] * to_bucket));
+      keep[r] = !(b_ap[r] + 2.f * kPruneMargin <= s_gearly[bk]);
     }
+    my_count += keep[r] ? 1 : 0;
   }
-  int n_roots;
-  int offset = block_exclusive_scan<NT>(my_count, 0, OpAdd(), s_itmp, n_roots);
+  int n_keep;
+  int offset = block_exclusive_scan<NT>(my_count, 0, OpAdd(), s_itmp, n_keep);
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
-    if (has[r]) {
-      s_key[pad_idx(offset)] = al[r];
-      s_val[pad_idx(offset)] = be[r];
-      ++offset;
-    }
+    if (keep[r]) s_flag[offset++] = tid + r * NT;  // kept row indices (s_flag is free until step 5)
   }
-  const int n_active_slots = ((n_roots + ITEMS - 1) / ITEMS) * ITEMS;
-  for (int k = n_roots + tid; k < n_active_slots; k += NT) {
+  __syncthreads();
+
+  // ---- exact roots of the kept rows (App. B, Sec. 3.2) ------------------------
+  int tangent = 0, no_root = 0;
+  for (int k = tid; k < n_keep; k += NT) {
+    const int i = s_flag[k];
+    T al, be;
+    bool inf_row = false;
+    const bool has = roots(Prow[i], Qrow[i], prm.b[i], prm.b64[i], prm.tangent_thresh, al, be,
+                           inf_row, tangent);
+    infeasible |= inf_row;
+    s_key[pad_idx(k)] = has ? al : inf;
+    s_val[pad_idx(k)] = has ? be : T(0);
+    no_root += has ? 0 : 1;
+  }
+  if (tangent) atomicAdd(&s_tangent, tangent);
+  if (no_root) atomicAdd(&s_noroot, no_root);
+  const int n_active_slots = ((n_keep + ITEMS - 1) / ITEMS) * ITEMS;
+  for (int k = n_keep + tid; k < n_active_slots; k += NT) {
     s_key[pad_idx(k)] = inf;
     s_val[pad_idx(k)] = T(0);
   }
   __syncthreads();
+  const int n_roots = n_keep - s_noroot;  // rows without roots sort to the end (+inf)
 
   // ---- 2. Alg. 3: sort alpha ascending, beta as payload -----------------
   // Only the first n_active_slots positions hold arcs; the rest is padding
@@ -446,13 +402,13 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
   } else {
     sincosf((float)theta, reinterpret_cast<float*>(&sn), reinterpret_cast<float*>(&cs));
   }
-  const bool theta_ok = isfinite((double)theta);
+  const bool theta_ok = isfinite(theta);
   const T* xrow = prm.X + (size_t)c * prm.ldx;
   const T* nurow = prm.NU + (size_t)c * prm.ldx;
   bool bad = !theta_ok || nonfinite;
   for (int j = tid; j < d; j += NT) {
     const T xn = xrow[j] * cs + nurow[j] * sn;
-    bad |= !isfinite((double)xn);
+    bad |= !isfinite(xn);
     s_x[j] = xn;
   }
   T pn[ITEMS];
@@ -462,8 +418,8 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
     const int i = tid + r * NT;
     pn[r] = p[r] * cs + q[r] * sn;
     if (i < m) {
-      const double slack_bound = prm.b64[i] - prm.margin * prm.anorm[i];
-      if (!((double)pn[r] <= slack_bound)) {  // within the margin (or NaN)
+      const T slack_bound = prm.slack ? prm.slack[i] : (T)(prm.b64[i] - prm.margin * prm.anorm[i]);
+      if (!(pn[r] <= slack_bound)) {  // within the margin (or NaN)
         const int at = atomicAdd(&s_nflag, 1);
         s_flag[at] = i;
         ++my_flags;
@@ -536,9 +492,11 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
       atomicOr(prm.status, kStatusNumeric);
     }
     if (blk_tangent) atomicAdd(&prm.stats->tangent_fp64, (unsigned long long)blk_tangent);
+    atomicAdd(&prm.stats->sort_keys, (unsigned long long)n_roots);
     if (blk_flags) atomicAdd(&prm.stats->rechecks, (unsigned long long)blk_flags);
   }
   if (infeasible) atomicOr(prm.status, kStatusInfeasible);
+  }  // chains of this CTA
 }
 
 }  // namespace
@@ -559,7 +517,13 @@ size_t chain_smem_bytes(int threads, int d) {
 template <typename T>
 cudaError_t launch_chain_step(const ChainParams<T>& p, int threads, cudaStream_t s) {
   const size_t smem = chain_smem_bytes<T>(threads, p.d);
-  dim3 grid(p.n_chains);
+  int sms = 1, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // list mode: a grid that fills the GPU once and strides over the list
+  dim3 grid(p.chain_list ? (unsigned)std::min(p.n_chains, sms * std::max(1, 768 / threads))
+                         : (unsigned)p.n_chains);
+  if (grid.x == 0) return cudaSuccess;
 #define ESS_CHAIN_CASE(NT)                                                              \
   case NT: {                                                                            \
     auto k = chain_step_kernel<T, NT, kChainItems>;                                     \

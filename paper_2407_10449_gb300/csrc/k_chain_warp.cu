@@ -1,0 +1,461 @@
+// k_chain_warp.cu -- one elliptical-slice step per chain, one WARP per chain.
+//
+// The same map as chain_step_kernel (Alg. 1 body: App. B roots, Alg. 3 sort
+// and cumulative-max sweep, inverse-CDF theta, move and Sec. 3.3 safeguard),
+// organised for the common case where few arcs matter:
+//   1. stream the m rows (p_i, q_i): classify each row (no root / near
+//      tangency / approximate arc) and keep the per-bucket max of the
+//      approximate beta in 1024 alpha buckets;
+//   2. prefix-max over the buckets; stream the rows again (from L2) and drop
+//      every arc contained in an arc that starts at least two buckets earlier
+//      (the union of arcs, hence I_act and its piece endpoints, is unchanged;
+//      see chain_step_kernel);
+//   3. exact roots for the <= 128 surviving rows, bitonic sort of alpha with
+//      beta as payload in registers (4 per lane, warp shuffles), cumulative
+//      max and piece lengths by warp scans, theta by the inverse CDF;
+//   4. stream the rows again: p' = p cos + q sin written to P_out, rows near
+//      their bound rechecked in FP64 against x' = x cos + nu sin; then x'.
+// No block-wide barrier is needed.  Chains with more than 128 surviving arcs
+// are left untouched and listed for the CTA-per-chain kernel.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "chain_math.cuh"
+#include "ess_kernels.cuh"
+
+namespace ess {
+namespace {
+
+using namespace chainmath;
+
+constexpr int kWB = 1024;                 // alpha buckets
+constexpr int kCap = kWarpSortCap;        // arcs a warp sorts
+constexpr int kPer = kCap / 32;           // per lane
+constexpr int kWarps = 8;                 // chains per CTA
+constexpr int kWBP = kWB + kWB / 32;      // padded bucket array: bucket j at j + j / 32
+constexpr int kBatch = 8;                 // rows per lane in flight per loop trip
+
+// Bucket j lives at j + j / 32: a lane's 32 consecutive buckets then sit on
+// 32 different banks.
+__device__ __forceinline__ int bslot(int j) { return j + (j >> 5); }
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_max(T v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v = y > v ? y : v;
+  }
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_sum(T v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += y;
+  }
+  return v;
+}
+
+template <typename T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 3) chain_warp_kernel(ChainParams<T> prm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = prm.m, d = prm.d;
+  // per-warp shared memory: padded buckets[kWBP], survivor rows[kCap]
+  const size_t per_warp = ((size_t)kWBP + kCap) * 4;
+  unsigned* bmax = reinterpret_cast<unsigned*>(smem_raw + per_warp * warp);
+  int* surv = reinterpret_cast<int*>(bmax + kWBP);
+  __shared__ unsigned long long s_sort_keys;
+  if (threadIdx.x == 0) s_sort_keys = 0;
+  __syncthreads();
+
+  const int c = blockIdx.x * WARPS + warp;
+  const T two_pi = Lim<T>::two_pi();
+  const T inf = Lim<T>::inf();
+  int my_sort_keys = 0;
+
+  if (c < prm.n_chains) {
+    const T* Prow = prm.P_in + (size_t)c * prm.ldp;
+    const T* Qrow = prm.Q + (size_t)c * prm.ldp;
+    for (int k = lane; k < kWBP; k += 32) bmax[k] = 0u;
+    __syncwarp();
+
+    // ---- 1. classify every row, bucket maxima of the approximate beta ----
+    const T tlo = (T)(1.0 - prm.tangent_thresh);
+    const T thi = (T)(1.0 + prm.tangent_thresh);
+    const float to_bucket = (float)(kWB / kTwoPi);
+    bool infeasible = false, nonfinite = false;
+    for (int i0 = 0; i0 < m; i0 += 32 * kBatch) {
+      // issue every load of the batch before using any (memory-level parallelism)
+      T pv[kBatch], qv[kBatch];
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) {
+        const int i = i0 + lane + 32 * k;
+        pv[k] = i < m ? Prow[i] : T(0);
+        qv[k] = i < m ? Qrow[i] : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) {
+        const int i = i0 + lane + 32 * k;
+        if (i >= m) continue;
+        nonfinite |= !isfinite(pv[k]) || !isfinite(qv[k]);
+        float a_ap = 0.f, b_ap = 0.f;
+        bool inf_row = false;
+        const int cls =
+            classify_row<T>(pv[k], qv[k], prm.b[i], prm.b64[i], tlo, thi, a_ap, b_ap, inf_row);
+        infeasible |= inf_row;
+        if (cls == kRowApprox) {
+          const int bk = min(kWB - 1, (int)(a_ap * to_bucket));
+          atomicMax(&bmax[bslot(bk)], __float_as_uint(b_ap));
+        }
+      }
+    }
+    __syncwarp();
+
+    // ---- 2. prefix max over the buckets (32 consecutive buckets per lane) ----
+    {
+      unsigned run = 0u;
+      unsigned* mine = bmax + bslot(lane * (kWB / 32));
+#pragma unroll 4
+      for (int k = 0; k < kWB / 32; ++k) {
+        run = max(run, mine[k]);
+        mine[k] = run;
+      }
+      const unsigned incl = warp_incl_max<unsigned>(run, lane);
+      unsigned before = __shfl_up_sync(kFull, incl, 1);
+      if (lane == 0) before = 0u;
+#pragma unroll 4
+      for (int k = 0; k < kWB / 32; ++k) mine[k] = max(mine[k], before);
+    }
+    __syncwarp();
+
+    // ---- keep test (rows re-read from L2 and reclassified), compaction ----
+    int n_surv = 0;
+    for (int i0 = 0; i0 < m; i0 += 32 * kBatch) {
+      T pv[kBatch], qv[kBatch];
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) {
+        const int i = i0 + lane + 32 * k;
+        pv[k] = i < m ? Prow[i] : T(0);
+        qv[k] = i < m ? Qrow[i] : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) {
+        const int i = i0 + lane + 32 * k;
+        bool keep = false;
+        if (i < m) {
+          float a_ap = 0.f, b_ap = 0.f;
+          bool inf_row = false;
+          const int cls =
+              classify_row<T>(pv[k], qv[k], prm.b[i], prm.b64[i], tlo, thi, a_ap, b_ap, inf_row);
+          if (cls == kRowKeep) {
+            keep = true;
+          } else if (cls == kRowApprox) {
+            const int bk = min(kWB - 1, (int)(a_ap * to_bucket));
+            keep = bk < 2 ||
+                   !(b_ap + 2.f * kPruneMargin <= __uint_as_float(bmax[bslot(bk - 2)]));
+          }
+        }
+        const unsigned ball = __ballot_sync(kFull, keep);
+        const int at = n_surv + __popc(ball & ((1u << lane) - 1u));
+        if (keep && at < kCap) surv[at] = i;
+        n_surv += __popc(ball);
+      }
+    }
+    __syncwarp();
+
+    if (n_surv > kCap) {
+      // too many arcs for one warp: the CTA-per-chain kernel takes this chain
+      if (lane == 0) {
+        const int at = atomicAdd(prm.overflow_count, 1);
+        prm.overflow_list[at] = c;
+      }
+    } else {
+      // ---- 3. exact roots of the survivors, sorted in registers ----
+      T key[kPer], val[kPer];
+      int tangent = 0, no_root = 0;
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int e = lane + 32 * j;
+        key[j] = inf;
+        val[j] = T(0);
+        if (e < n_surv) {
+          const int i = surv[e];
+          T al, be;
+          bool inf_row = false;
+          const bool has = roots(Prow[i], Qrow[i], prm.b[i], prm.b64[i], prm.tangent_thresh, al,
+                                 be, inf_row, tangent);
+          infeasible |= inf_row;
+          if (has) {
+            key[j] = al;
+            val[j] = be;
+          } else {
+            ++no_root;
+          }
+        }
+      }
+      // bitonic network over kCap elements, element e = lane + 32 j
+#pragma unroll
+      for (int kk = 2; kk <= kCap; kk <<= 1) {
+#pragma unroll
+        for (int st = kk >> 1; st > 0; st >>= 1) {
+          if (st >= 32) {
+            const int js = st >> 5;
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+              const int jp = j ^ js;
+              if (jp > j) {
+                const int e = lane + 32 * j;
+                const bool up = (e & kk) == 0;
+                if ((key[j] > key[jp]) == up) {
+                  T tk = key[j]; key[j] = key[jp]; key[jp] = tk;
+                  T tv = val[j]; val[j] = val[jp]; val[jp] = tv;
+                }
+              }
+            }
+          } else {
+            const bool lower = (lane & st) == 0;
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+              const int e = lane + 32 * j;
+              const bool up = (e & kk) == 0;
+              const T ok = __shfl_xor_sync(kFull, key[j], st);
+              const T ov = __shfl_xor_sync(kFull, val[j], st);
+              // the lower element keeps the smaller key when sorting upwards
+              const bool take = lower == up ? ok < key[j] : ok > key[j];
+              if (take) {
+                key[j] = ok;
+                val[j] = ov;
+              }
+            }
+          }
+        }
+      }
+      // warp-wide counts
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        no_root += __shfl_xor_sync(kFull, no_root, o);
+        tangent += __shfl_xor_sync(kFull, tangent, o);
+      }
+      const int n_roots = n_surv - no_root;
+      my_sort_keys = n_roots;
+
+      // ---- Alg. 3: cumulative max gamma, pieces, lengths ----
+      const T eps = (T)prm.trim_eps;
+      T plo[kPer], phi[kPer], plen[kPer], sexcl[kPer];
+      T gcarry = T(0), scarry = T(0);
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int e = lane + 32 * j;
+        const bool valid = e < n_roots;
+        const T v = valid ? val[j] : T(0);
+        T incl = warp_incl_max<T>(v, lane);
+        incl = incl > gcarry ? incl : gcarry;
+        T gprev = __shfl_up_sync(kFull, incl, 1);
+        if (lane == 0) gprev = gcarry;
+        gcarry = __shfl_sync(kFull, incl, 31);
+        // piece e: [gamma_(e-1), alpha_(e)]; piece 0 starts at the glued point 0
+        const T lo = e == 0 ? T(0) : gprev + eps;
+        const T hi = key[j] - eps;
+        plo[j] = lo;
+        phi[j] = hi;
+        plen[j] = valid && hi > lo ? hi - lo : T(0);
+        const T sincl = warp_incl_sum<T>(plen[j], lane) + scarry;
+        T sx = __shfl_up_sync(kFull, sincl, 1);
+        sexcl[j] = lane == 0 ? scarry : sx;
+        scarry = __shfl_sync(kFull, sincl, 31);
+      }
+      const T mid_total = scarry;
+      const T tail_lo = n_roots > 0 ? gcarry + eps : T(0);
+      const T tail_len = two_pi > tail_lo ? two_pi - tail_lo : T(0);
+      const T total = mid_total + tail_len;
+
+      // ---- theta ~ U(I_act): the last positive piece starting at or below s ----
+      const double u = prm.U ? prm.U[c] : theta_uniform(prm.seed, prm.chain0 + (uint32_t)c,
+                                                         prm.t, prm.problem);
+      const T s = (T)(u * (double)total);
+      int cand = -1;
+      T cand_theta = T(0);
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        if (plen[j] > T(0) && sexcl[j] <= s) {
+          cand = lane + 32 * j;
+          const T th = plo[j] + (s - sexcl[j]);
+          cand_theta = th < phi[j] ? th : phi[j];
+        }
+      }
+      if (tail_len > T(0) && mid_total <= s) {
+        cand = kCap;  // the tail is the last piece
+        const T th = tail_lo + (s - mid_total);
+        cand_theta = th < two_pi ? th : two_pi;
+      }
+      int best = cand;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(kFull, best, o));
+      const unsigned owners = __ballot_sync(kFull, cand == best);
+      T theta = __shfl_sync(kFull, cand_theta, __ffs(owners) - 1);
+      if (best < 0 || !(total > T(0))) theta = T(0);
+
+      // optional: the positive-length pieces (test/diagnostic output)
+      if (prm.pieces_out != nullptr || prm.npieces_out != nullptr) {
+        double* out = prm.pieces_out ? prm.pieces_out + (size_t)c * prm.max_pieces * 2 : nullptr;
+        int at = 0;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+          const bool pos = plen[j] > T(0);
+          const unsigned ball = __ballot_sync(kFull, pos);
+          const int k = at + __popc(ball & ((1u << lane) - 1u));
+          if (pos && out && k < prm.max_pieces) {
+            out[2 * k] = (double)plo[j];
+            out[2 * k + 1] = (double)phi[j];
+          }
+          at += __popc(ball);
+        }
+        if (lane == 0) {
+          if (out && tail_len > T(0) && at < prm.max_pieces) {
+            out[2 * at] = (double)tail_lo;
+            out[2 * at + 1] = (double)two_pi;
+          }
+          if (prm.npieces_out) prm.npieces_out[c] = at + (tail_len > T(0) ? 1 : 0);
+        }
+      }
+
+      // ---- 4. move: p' for every row, FP64 recheck of rows near their bound ----
+      T sn, cs;
+      if constexpr (sizeof(T) == 8) {
+        sincos((double)theta, reinterpret_cast<double*>(&sn), reinterpret_cast<double*>(&cs));
+      } else {
+        sincosf((float)theta, reinterpret_cast<float*>(&sn), reinterpret_cast<float*>(&cs));
+      }
+      const T* xrow = prm.X + (size_t)c * prm.ldx;
+      const T* nurow = prm.NU + (size_t)c * prm.ldx;
+      T* prow_out = prm.P_out + (size_t)c * prm.ldp;
+      bool bad = nonfinite || !isfinite(theta);
+      bool violated = false;
+      int rechecks = 0;
+      double maxres = -INFINITY;
+      for (int i0 = 0; i0 < m; i0 += 32 * kBatch) {
+        T pv[kBatch], qv[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+          const int i = i0 + lane + 32 * k;
+          pv[k] = i < m ? Prow[i] : T(0);
+          qv[k] = i < m ? Qrow[i] : T(0);
+        }
+        unsigned flags = 0u;
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+          const int i = i0 + lane + 32 * k;
+          if (i < m) {
+            const T pn = pv[k] * cs + qv[k] * sn;
+            prow_out[i] = pn;
+            const T slack =
+                prm.slack ? prm.slack[i] : (T)(prm.b64[i] - prm.margin * prm.anorm[i]);
+            if (!(pn <= slack)) flags |= 1u << k;
+          }
+        }
+        for (int k = 0; k < kBatch; ++k) {
+        unsigned ball = __ballot_sync(kFull, (flags >> k) & 1u);
+        rechecks += __popc(ball);
+        while (ball) {
+          const int src = __ffs(ball) - 1;
+          ball &= ball - 1;
+          const int row = i0 + src + 32 * k;
+          const double* arow = prm.A64 + (size_t)row * d;
+          double acc = 0.0;
+          for (int jj = lane; jj < d; jj += 32) {
+            const T xn = xrow[jj] * cs + nurow[jj] * sn;
+            acc = fma(arow[jj], (double)xn, acc);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+          const double res = acc - prm.b64[row];
+          maxres = fmax(maxres, res);
+          violated |= res > 0.0;
+        }
+        }
+      }
+      // x' is finite whenever theta, x and nu are (x_0 passes an FP64 check)
+      const bool reject = __any_sync(kFull, violated || bad);
+      bad = __any_sync(kFull, bad);
+      T* xout = prm.X_out + (size_t)c * prm.ldx;
+      T* srow = prm.samples ? prm.samples + (size_t)c * prm.sample_stride : nullptr;
+      if (!reject) {
+        for (int j0 = 0; j0 < d; j0 += 32 * kBatch) {
+          T xv[kBatch], nv[kBatch];
+#pragma unroll
+          for (int k = 0; k < kBatch; ++k) {
+            const int jj = j0 + lane + 32 * k;
+            xv[k] = jj < d ? xrow[jj] : T(0);
+            nv[k] = jj < d ? nurow[jj] : T(0);
+          }
+#pragma unroll
+          for (int k = 0; k < kBatch; ++k) {
+            const int jj = j0 + lane + 32 * k;
+            if (jj < d) {
+              const T xn = xv[k] * cs + nv[k] * sn;
+              xout[jj] = xn;
+              if (srow) srow[jj] = xn;
+            }
+          }
+        }
+      } else {
+        // Sec. 3.3: stay at x_t; p is restored
+        for (int i = lane; i < m; i += 32) prow_out[i] = Prow[i];
+        for (int jj = lane; jj < d; jj += 32) {
+          if (prm.X_out != prm.X) xout[jj] = xrow[jj];
+          if (srow) srow[jj] = xrow[jj];
+        }
+      }
+      if (lane == 0) {
+        if (prm.theta_out) prm.theta_out[c] = (double)theta;
+        if (prm.rejected_out) prm.rejected_out[c] = reject ? 1 : 0;
+        if (reject && !bad) atomicAdd(&prm.stats->rejections, 1ull);
+        if (bad) {
+          atomicAdd(&prm.stats->numeric_errors, 1ull);
+          atomicOr(prm.status, kStatusNumeric);
+        }
+        if (tangent) atomicAdd(&prm.stats->tangent_fp64, (unsigned long long)tangent);
+        if (rechecks) atomicAdd(&prm.stats->rechecks, (unsigned long long)rechecks);
+      }
+      if (rechecks && maxres > -INFINITY)
+        atomicMax(&prm.stats->max_residual_bits, enc_ordered(maxres));
+    }
+    if (__any_sync(kFull, infeasible) && lane == 0) atomicOr(prm.status, kStatusInfeasible);
+    if (lane == 0 && my_sort_keys) atomicAdd(&s_sort_keys, (unsigned long long)my_sort_keys);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_sort_keys) atomicAdd(&prm.stats->sort_keys, s_sort_keys);
+}
+
+}  // namespace
+
+template <typename T>
+size_t chain_warp_smem_bytes(int m) {
+  (void)m;
+  return (size_t)kWarps * ((size_t)kWBP + kCap) * 4;
+}
+
+template <typename T>
+cudaError_t launch_chain_step_warp(const ChainParams<T>& p, cudaStream_t s) {
+  if (p.n_chains <= 0) return cudaSuccess;
+  if (p.P_out == p.P_in || !p.overflow_list || !p.overflow_count) return cudaErrorInvalidValue;
+  const size_t smem = chain_warp_smem_bytes<T>(p.m);
+  auto k = chain_warp_kernel<T, kWarps>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((p.n_chains + kWarps - 1) / kWarps);
+  k<<<grid, kWarps * 32, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template size_t chain_warp_smem_bytes<float>(int);
+template size_t chain_warp_smem_bytes<double>(int);
+template cudaError_t launch_chain_step_warp<float>(const ChainParams<float>&, cudaStream_t);
+template cudaError_t launch_chain_step_warp<double>(const ChainParams<double>&, cudaStream_t);
+
+}  // namespace ess

@@ -33,8 +33,8 @@ def run_step(A, b, X, NU, U, precision=ess.ESS_PREC_FP64, max_pieces=None, **cfg
         s.close()
 
 
-def check_fp64(A, b, X, NU, U, trim_eps=0.0):
-    Xn, th, pcs, npc, rej, _ = run_step(A, b, X, NU, U, trim_eps=trim_eps)
+def check_fp64(A, b, X, NU, U, trim_eps=0.0, **cfg):
+    Xn, th, pcs, npc, rej, _ = run_step(A, b, X, NU, U, trim_eps=trim_eps, **cfg)
     ref = oracle_steps(A, b, X, NU, U, trim_eps)
     for c, r in enumerate(ref):
         assert r.status == 0
@@ -178,3 +178,28 @@ def test_full_size_sampled_chains():
         assert np.all(np.abs(Xn[c] - r.x_next) <= X_RTOL * np.maximum(1, np.abs(r.x_next)))
     # every chain: the emitted iterate is feasible in FP64
     assert np.max(Xn @ inst.A.T - inst.b) <= 0.0
+
+
+@pytest.mark.parametrize("sort_threads", [0, 256])
+def test_both_step_kernels(sort_threads):
+    """The warp-per-chain kernel (default) and the CTA-per-chain kernel give the
+    oracle's step on the same inputs, including chains whose arcs all survive
+    the domination prune (equal half-widths: b = 0) and go to the CTA kernel."""
+    rng = np.random.default_rng(21)
+    d, m, n = 40, 600, 96
+    A, b, X = feasible_instance(rng, d, m, n)
+    NU = rng.standard_normal((n, d))
+    U = rng.uniform(size=n)
+    check_fp64(A, b, X, NU, U, sort_threads=sort_threads)
+    # a probit-style orthant (A = -diag(y) L, b = 0): every arc has half-width
+    # pi / 2, no arc contains another, so all 200 arcs survive the prune and
+    # the chain goes to the CTA kernel
+    M = rng.standard_normal((200, 200))
+    L = np.linalg.cholesky(M @ M.T / 200 + np.eye(200))
+    z = rng.standard_normal(200)
+    y = np.sign(L @ z)
+    A2 = -y[:, None] * L
+    b2 = np.zeros(200)
+    X2 = np.tile(z, (32, 1))
+    check_fp64(A2, b2, X2, rng.standard_normal((32, 200)), rng.uniform(size=32),
+               sort_threads=sort_threads)
