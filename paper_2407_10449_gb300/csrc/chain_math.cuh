@@ -149,5 +149,56 @@ __device__ __forceinline__ int classify_row(T p, T q, T b, double b64, T tlo, T 
 }
 
 
+// Pseudo-angle of a nonzero vector (x, y): a strictly increasing function of
+// its polar angle in [0, 2 pi), with values in [0, 4) ("diamond angle", one
+// unit per quadrant).  Comparisons of pseudo-angles are comparisons of angles.
+__device__ __forceinline__ float diamond_angle(float x, float y) {
+  if (y >= 0.f) return x >= 0.f ? __fdividef(y, x + y) : 1.f + __fdividef(-x, y - x);
+  return x < 0.f ? 2.f + __fdividef(-y, -x - y) : 3.f + __fdividef(x, x - y);
+}
+
+// Pseudo-angles of the two roots: with w = sqrt(r^2 - b^2), the points of the
+// ellipse on the hyperplane sit at the angles of
+//   u_alpha = (p b + q w, q b - p w)   (= r^2 (cos(tau - h), sin(tau - h)))
+//   u_beta  = (p b - q w, q b + p w)   (= r^2 (cos(tau + h), sin(tau + h)))
+// (App. B: cos tau = p / r, sin tau = q / r, cos h = b / r, sin h = w / r).
+// The row classes match roots(): the no-root and near-tangent decisions are
+// taken only outside a 1e-6 relative slack of the b/r computed here, and rows
+// whose arc would wrap through 0 (boundary points) are always kept.
+template <typename T>
+__device__ __forceinline__ int classify_phi(T p, T q, T b, double b64, T tlo, T thi, float& pa,
+                                            float& pb, bool& infeasible) {
+  float ratio;
+  const float pf = (float)p, qf = (float)q, bf = (float)b;
+  if constexpr (sizeof(T) == 4) {
+    const float r2 = fmaf(p, p, q * q);
+    if (r2 == 0.0f) {
+      infeasible = b64 < 0.0;
+      return kRowNone;
+    }
+    ratio = b * rsqrtf(r2);
+    if (ratio >= thi * 1.000001f) return kRowNone;
+    if (fabsf(ratio) > tlo * 0.999999f) return kRowKeep;
+  } else {
+    const double r = sqrt(p * p + q * q);
+    if (r == 0.0) {
+      infeasible = b64 < 0.0;
+      return kRowNone;
+    }
+    const double rd = b64 / r;
+    if (rd >= 1.0) return kRowNone;
+    if (fabs(rd) > tlo || r < 1e-30 || r > 1e30) return kRowKeep;
+    ratio = (float)rd;
+  }
+  const float r2f = fmaf(pf, pf, qf * qf);
+  const float w2 = fmaf(-bf, bf, r2f);
+  if (!(w2 > 0.f)) return kRowKeep;
+  const float w = w2 * rsqrtf(w2);
+  pa = diamond_angle(fmaf(pf, bf, qf * w), fmaf(qf, bf, -pf * w));
+  pb = diamond_angle(fmaf(pf, bf, -qf * w), fmaf(qf, bf, pf * w));
+  (void)ratio;
+  return pa < pb ? kRowApprox : kRowKeep;
+}
+
 }  // namespace chainmath
 }  // namespace ess

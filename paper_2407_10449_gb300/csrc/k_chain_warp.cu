@@ -3,13 +3,15 @@
 // The same map as chain_step_kernel (Alg. 1 body: App. B roots, Alg. 3 sort
 // and cumulative-max sweep, inverse-CDF theta, move and Sec. 3.3 safeguard),
 // organised for the common case where few arcs matter:
-//   1. stream the m rows (p_i, q_i): classify each row (no root / near
-//      tangency / approximate arc) and keep the per-bucket max of the
-//      approximate beta in 1024 alpha buckets;
-//   2. prefix-max over the buckets; stream the rows again (from L2) and drop
-//      every arc contained in an arc that starts at least two buckets earlier
-//      (the union of arcs, hence I_act and its piece endpoints, is unchanged;
-//      see chain_step_kernel);
+//   1. classify each row (no root / near tangency / arc) and place its arc by
+//      pseudo-angles of the two roots (a monotone stand-in for the angle,
+//      computed without trigonometry); a first batch of 256 rows gives
+//      per-bucket maxima of beta over 512 alpha buckets, then every row is
+//      tested against them (and added to the full maxima): rows whose arc lies
+//      inside an arc that starts at least two buckets earlier are dropped;
+//   2. the remaining candidates are tested again against the full maxima (the
+//      union of arcs, hence I_act and its piece endpoints, is unchanged by
+//      dropping contained arcs; see chain_step_kernel);
 //   3. exact roots for the <= 128 surviving rows, bitonic sort of alpha with
 //      beta as payload in registers (4 per lane, warp shuffles), cumulative
 //      max and piece lengths by warp scans, theta by the inverse CDF;
@@ -29,16 +31,46 @@ namespace {
 
 using namespace chainmath;
 
-constexpr int kWB = 1024;                 // alpha buckets
+constexpr int kWB = 512;                  // pseudo-angle buckets of alpha
+constexpr int kCand = 256;                // candidates after the first-batch test
+// Slack of pseudo-angle comparisons: far above the FP32 rounding of the
+// pseudo-angles (~1e-6) and far below the bucket width (4 / kWB)
+constexpr float kPhiMargin = 1e-5f;
 constexpr int kCap = kWarpSortCap;        // arcs a warp sorts
 constexpr int kPer = kCap / 32;           // per lane
 constexpr int kWarps = 8;                 // chains per CTA
 constexpr int kWBP = kWB + kWB / 32;      // padded bucket array: bucket j at j + j / 32
 constexpr int kBatch = 8;                 // rows per lane in flight per loop trip
 
-// Bucket j lives at j + j / 32: a lane's 32 consecutive buckets then sit on
-// 32 different banks.
+// Bucket j lives at j + j / 32: a lane's consecutive buckets then sit on
+// different banks.
 __device__ __forceinline__ int bslot(int j) { return j + (j >> 5); }
+
+// Bucket of a pseudo-angle in [0, 4).
+__device__ __forceinline__ int pbucket(float pa) {
+  return min(kWB - 1, (int)(pa * (kWB / 4.0f)));
+}
+
+// In-place inclusive prefix max of kWB bucket maxima (float bits, >= 0).
+__device__ __forceinline__ void prefix_max(unsigned* b, int lane) {
+  unsigned run = 0u;
+  unsigned* mine = b + bslot(lane * (kWB / 32));
+#pragma unroll 4
+  for (int k = 0; k < kWB / 32; ++k) {
+    run = max(run, mine[k]);
+    mine[k] = run;
+  }
+  unsigned incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl = max(incl, y);
+  }
+  unsigned before = __shfl_up_sync(kFull, incl, 1);
+  if (lane == 0) before = 0u;
+#pragma unroll 4
+  for (int k = 0; k < kWB / 32; ++k) mine[k] = max(mine[k], before);
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_incl_max(T v, int lane) {
@@ -65,10 +97,14 @@ __global__ void __launch_bounds__(WARPS * 32, 3) chain_warp_kernel(ChainParams<T
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = prm.m, d = prm.d;
-  // per-warp shared memory: padded buckets[kWBP], survivor rows[kCap]
-  const size_t per_warp = ((size_t)kWBP + kCap) * 4;
-  unsigned* bmax = reinterpret_cast<unsigned*>(smem_raw + per_warp * warp);
-  int* surv = reinterpret_cast<int*>(bmax + kWBP);
+  // per-warp shared memory: two padded bucket arrays, candidates (code,
+  // pseudo-beta), survivor rows
+  const size_t per_warp = ((size_t)2 * kWBP + 2 * kCand + kCap) * 4;
+  unsigned* bsub = reinterpret_cast<unsigned*>(smem_raw + per_warp * warp);
+  unsigned* bfull = bsub + kWBP;
+  unsigned* candc = bfull + kWBP;
+  float* candb = reinterpret_cast<float*>(candc + kCand);
+  int* surv = reinterpret_cast<int*>(candb + kCand);
   __shared__ unsigned long long s_sort_keys;
   if (threadIdx.x == 0) s_sort_keys = 0;
   __syncthreads();
@@ -81,60 +117,40 @@ __global__ void __launch_bounds__(WARPS * 32, 3) chain_warp_kernel(ChainParams<T
   if (c < prm.n_chains) {
     const T* Prow = prm.P_in + (size_t)c * prm.ldp;
     const T* Qrow = prm.Q + (size_t)c * prm.ldp;
-    for (int k = lane; k < kWBP; k += 32) bmax[k] = 0u;
+    for (int k = lane; k < 2 * kWBP; k += 32) bsub[k] = 0u;  // bsub and bfull
     __syncwarp();
-
-    // ---- 1. classify every row, bucket maxima of the approximate beta ----
     const T tlo = (T)(1.0 - prm.tangent_thresh);
     const T thi = (T)(1.0 + prm.tangent_thresh);
-    const float to_bucket = (float)(kWB / kTwoPi);
     bool infeasible = false, nonfinite = false;
-    for (int i0 = 0; i0 < m; i0 += 32 * kBatch) {
-      // issue every load of the batch before using any (memory-level parallelism)
-      T pv[kBatch], qv[kBatch];
-#pragma unroll
-      for (int k = 0; k < kBatch; ++k) {
-        const int i = i0 + lane + 32 * k;
-        pv[k] = i < m ? Prow[i] : T(0);
-        qv[k] = i < m ? Qrow[i] : T(0);
-      }
-#pragma unroll
-      for (int k = 0; k < kBatch; ++k) {
-        const int i = i0 + lane + 32 * k;
-        if (i >= m) continue;
-        nonfinite |= !isfinite(pv[k]) || !isfinite(qv[k]);
-        float a_ap = 0.f, b_ap = 0.f;
-        bool inf_row = false;
-        const int cls =
-            classify_row<T>(pv[k], qv[k], prm.b[i], prm.b64[i], tlo, thi, a_ap, b_ap, inf_row);
-        infeasible |= inf_row;
-        if (cls == kRowApprox) {
-          const int bk = min(kWB - 1, (int)(a_ap * to_bucket));
-          atomicMax(&bmax[bslot(bk)], __float_as_uint(b_ap));
-        }
-      }
-    }
-    __syncwarp();
 
-    // ---- 2. prefix max over the buckets (32 consecutive buckets per lane) ----
+    // ---- 1a. a first batch of rows builds bucket maxima of beta ---------------
+    const int m_sub = min(m, 32 * kBatch);
     {
-      unsigned run = 0u;
-      unsigned* mine = bmax + bslot(lane * (kWB / 32));
-#pragma unroll 4
-      for (int k = 0; k < kWB / 32; ++k) {
-        run = max(run, mine[k]);
-        mine[k] = run;
+      T pv[kBatch], qv[kBatch];
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) {
+        const int i = lane + 32 * k;
+        pv[k] = i < m_sub ? Prow[i] : T(0);
+        qv[k] = i < m_sub ? Qrow[i] : T(0);
       }
-      const unsigned incl = warp_incl_max<unsigned>(run, lane);
-      unsigned before = __shfl_up_sync(kFull, incl, 1);
-      if (lane == 0) before = 0u;
-#pragma unroll 4
-      for (int k = 0; k < kWB / 32; ++k) mine[k] = max(mine[k], before);
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) {
+        const int i = lane + 32 * k;
+        if (i >= m_sub) continue;
+        float pa = 0.f, pb = 0.f;
+        bool inf_row = false;
+        if (classify_phi<T>(pv[k], qv[k], prm.b[i], prm.b64[i], tlo, thi, pa, pb, inf_row) ==
+            kRowApprox)
+          atomicMax(&bsub[bslot(pbucket(pa))], __float_as_uint(pb));
+      }
     }
     __syncwarp();
+    prefix_max(bsub, lane);
+    __syncwarp();
 
-    // ---- keep test (rows re-read from L2 and reclassified), compaction ----
-    int n_surv = 0;
+    // ---- 1b. every row: full bucket maxima, candidates not dominated by an
+    //          arc of the first batch ------------------------------------------
+    int n_cand = 0;
     for (int i0 = 0; i0 < m; i0 += 32 * kBatch) {
       T pv[kBatch], qv[kBatch];
 #pragma unroll
@@ -146,23 +162,59 @@ __global__ void __launch_bounds__(WARPS * 32, 3) chain_warp_kernel(ChainParams<T
 #pragma unroll
       for (int k = 0; k < kBatch; ++k) {
         const int i = i0 + lane + 32 * k;
-        bool keep = false;
+        bool cand = false;
+        unsigned code = 0u;
+        float pb = 0.f;
         if (i < m) {
-          float a_ap = 0.f, b_ap = 0.f;
+          nonfinite |= !isfinite(pv[k]) || !isfinite(qv[k]);
+          float pa = 0.f;
           bool inf_row = false;
           const int cls =
-              classify_row<T>(pv[k], qv[k], prm.b[i], prm.b64[i], tlo, thi, a_ap, b_ap, inf_row);
+              classify_phi<T>(pv[k], qv[k], prm.b[i], prm.b64[i], tlo, thi, pa, pb, inf_row);
+          infeasible |= inf_row;
           if (cls == kRowKeep) {
-            keep = true;
+            cand = true;
+            code = 0x80000000u | (unsigned)i;
           } else if (cls == kRowApprox) {
-            const int bk = min(kWB - 1, (int)(a_ap * to_bucket));
-            keep = bk < 2 ||
-                   !(b_ap + 2.f * kPruneMargin <= __uint_as_float(bmax[bslot(bk - 2)]));
+            const int bk = pbucket(pa);
+            atomicMax(&bfull[bslot(bk)], __float_as_uint(pb));
+            cand = bk < 2 || !(pb + 2.f * kPhiMargin <= __uint_as_float(bsub[bslot(bk - 2)]));
+            code = ((unsigned)bk << 14) | (unsigned)i;
+          }
+        }
+        const unsigned ball = __ballot_sync(kFull, cand);
+        const int at = n_cand + __popc(ball & ((1u << lane) - 1u));
+        if (cand && at < kCand) {
+          candc[at] = code;
+          candb[at] = pb;
+        }
+        n_cand += __popc(ball);
+      }
+    }
+    __syncwarp();
+    int n_surv = kCap + 1;  // overflow unless the candidates fit
+    if (n_cand <= kCand) {
+      prefix_max(bfull, lane);
+      __syncwarp();
+      // ---- 2. survivors: candidates not dominated by any arc ----
+      n_surv = 0;
+      for (int e0 = 0; e0 < n_cand; e0 += 32) {
+        const int e = e0 + lane;
+        bool keep = false;
+        int row = 0;
+        if (e < n_cand) {
+          const unsigned code = candc[e];
+          row = (int)(code & 0x3FFFu);
+          if (code & 0x80000000u) {
+            keep = true;
+          } else {
+            const int bk = (int)((code >> 14) & 0x3FFu);
+            keep = bk < 2 || !(candb[e] + 2.f * kPhiMargin <= __uint_as_float(bfull[bslot(bk - 2)]));
           }
         }
         const unsigned ball = __ballot_sync(kFull, keep);
         const int at = n_surv + __popc(ball & ((1u << lane) - 1u));
-        if (keep && at < kCap) surv[at] = i;
+        if (keep && at < kCap) surv[at] = row;
         n_surv += __popc(ball);
       }
     }
@@ -437,7 +489,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3) chain_warp_kernel(ChainParams<T
 template <typename T>
 size_t chain_warp_smem_bytes(int m) {
   (void)m;
-  return (size_t)kWarps * ((size_t)kWBP + kCap) * 4;
+  return (size_t)kWarps * ((size_t)2 * kWBP + 2 * kCand + kCap) * 4;
 }
 
 template <typename T>
