@@ -192,10 +192,14 @@ def phase_rooflines(inst, n_chains, timing, precision, peaks):
     mixed = precision == "mixed"
     esz = 4 if mixed else 8
     out = {}
+    steps = timing.get("draw", {}).get("launches", 0)
     for phase, t in timing.items():
         if t["launches"] == 0 or t["ms"] <= 0:
             continue
-        ms = t["ms"] / t["launches"]
+        # the chain phase is one warp-per-chain launch plus the (usually empty)
+        # CTA-per-chain launch for overflow chains: time it per step
+        units = steps if phase == "chain" and steps else t["launches"]
+        ms = t["ms"] / units
         if phase == "gemm":
             if mixed:
                 flops = 6 * 2.0 * m * d * C  # six BF16 slice products issued (BF16x6)
@@ -224,11 +228,12 @@ def phase_rooflines(inst, n_chains, timing, precision, peaks):
             out[phase] = dict(bound="hbm", unit="GB/s", achieved=byts / ms / 1e6,
                               peak=peaks["hbm_gbs"], work_per_launch=byts)
         elif phase == "draw":
-            byts = float(C) * d * (esz + (4 if mixed else 0))  # nu (+ bf16 hi/lo)
+            byts = float(C) * d * (esz + (6 if mixed else 0))  # nu (+ three bf16 slices)
             out[phase] = dict(bound="hbm", unit="GB/s", achieved=byts / ms / 1e6,
                               peak=peaks["hbm_gbs"], work_per_launch=byts)
         out[phase]["ms_per_launch"] = ms
         out[phase]["launches"] = t["launches"]
+        out[phase]["units"] = units
         out[phase]["share"] = t["ms"] / sum(v["ms"] for v in timing.values())
         out[phase]["frac"] = out[phase]["achieved"] / out[phase]["peak"]
     return out
@@ -375,8 +380,9 @@ def main():
     roof64 = phase_rooflines(inst, C, timing64, "fp64", peaks) if timing64 else {}
     dominant = max(roof, key=lambda k: roof[k]["share"])
     dom = roof[dominant]
-    kernel_src = {"gemm": ("k_gemm_tc.cu",), "chain": ("k_chain.cu",), "draw": ("k_draw.cu",),
-                  "refresh": ("k_gemm_tc.cu",)}
+    kernel_src = {"gemm": ("k_gemm_tc.cu",),
+                  "chain": ("k_chain_warp.cu", "chain_math.cuh", "k_chain.cu"),
+                  "draw": ("k_draw.cu", "ess_common.cuh"), "refresh": ("k_gemm_tc.cu",)}
     src = source_hash(*kernel_src[dominant])
     traffic = ncu_traffic(f"{dominant}_mixed", src)
     roofline = {"bound": dom["bound"], "kernel": dominant, "achieved": dom["achieved"],
@@ -396,7 +402,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x6", "data": "synthetic",
         "config": {"workload": "metric_d1000_m2000_c8192", "d": 1000, "m": 2000,
                    "chains_per_gpu": C, "precision": "mixed", "refresh_k": 32,
                    "l2": "working set per step ~300 MB > 126 MB L2 (no flush needed)",

@@ -195,7 +195,7 @@ ess_status ess_step_with_draws(ess_state *state, const double *X, const double *
 /*
  * The products the step uses, as the state computes them (for verification):
  * p = A x by the refresh path and q = A nu by the step's GEMM (FP64 FMAs in
- * the FP64 form, the BF16x3 tensor-core GEMM in the mixed form).
+ * the FP64 form, the BF16x6 tensor-core GEMM in the mixed form).
  *   X, nu   device, n_chains x d doubles (rounded to float first in the mixed
  *           form, as a run stores them).
  *   P, Q    device, n_chains x m doubles; either may be NULL.

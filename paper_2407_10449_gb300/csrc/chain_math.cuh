@@ -152,9 +152,11 @@ __device__ __forceinline__ int classify_row(T p, T q, T b, double b64, T tlo, T 
 // Pseudo-angle of a nonzero vector (x, y): a strictly increasing function of
 // its polar angle in [0, 2 pi), with values in [0, 4) ("diamond angle", one
 // unit per quadrant).  Comparisons of pseudo-angles are comparisons of angles.
+// With yn = y / (|x| + |y|): quadrant I gives yn, II and III give 2 - yn,
+// IV gives 4 + yn (continuous across the quadrant boundaries).
 __device__ __forceinline__ float diamond_angle(float x, float y) {
-  if (y >= 0.f) return x >= 0.f ? __fdividef(y, x + y) : 1.f + __fdividef(-x, y - x);
-  return x < 0.f ? 2.f + __fdividef(-y, -x - y) : 3.f + __fdividef(x, x - y);
+  const float yn = __fdividef(y, fabsf(x) + fabsf(y));
+  return x >= 0.f ? (y >= 0.f ? yn : 4.f + yn) : 2.f - yn;
 }
 
 // Pseudo-angles of the two roots: with w = sqrt(r^2 - b^2), the points of the

@@ -40,7 +40,13 @@ constexpr int kCap = kWarpSortCap;        // arcs a warp sorts
 constexpr int kPer = kCap / 32;           // per lane
 constexpr int kWarps = 8;                 // chains per CTA
 constexpr int kWBP = kWB + kWB / 32;      // padded bucket array: bucket j at j + j / 32
-constexpr int kBatch = 8;                 // rows per lane in flight per loop trip
+#ifndef ESS_WARP_BATCH
+#define ESS_WARP_BATCH 8
+#endif
+#ifndef ESS_WARP_MINBLOCKS
+#define ESS_WARP_MINBLOCKS 4
+#endif
+constexpr int kBatch = ESS_WARP_BATCH;    // rows per lane in flight per loop trip
 
 // Bucket j lives at j + j / 32: a lane's consecutive buckets then sit on
 // different banks.
@@ -92,8 +98,53 @@ __device__ __forceinline__ T warp_incl_sum(T v, int lane) {
   return v;
 }
 
+
+// Bitonic sort of 32 P elements held as element e = lane + 32 j in key[j]
+// (ascending, val travels with its key); entries j >= P are left untouched.
+template <typename T, int P>
+__device__ __forceinline__ void warp_bitonic(T (&key)[kPer], T (&val)[kPer], int lane) {
+  constexpr int N = 32 * P;
+#pragma unroll
+  for (int kk = 2; kk <= N; kk <<= 1) {
+#pragma unroll
+    for (int st = kk >> 1; st > 0; st >>= 1) {
+      if (st >= 32) {
+        const int js = st >> 5;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          const int jp = j ^ js;
+          if (jp > j) {
+            const int e = lane + 32 * j;
+            const bool up = (e & kk) == 0;
+            if ((key[j] > key[jp]) == up) {
+              T tk = key[j]; key[j] = key[jp]; key[jp] = tk;
+              T tv = val[j]; val[j] = val[jp]; val[jp] = tv;
+            }
+          }
+        }
+      } else {
+        const bool lower = (lane & st) == 0;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          const int e = lane + 32 * j;
+          const bool up = (e & kk) == 0;
+          const T ok = __shfl_xor_sync(kFull, key[j], st);
+          const T ov = __shfl_xor_sync(kFull, val[j], st);
+          // the lower element keeps the smaller key when sorting upwards
+          const bool take = lower == up ? ok < key[j] : ok > key[j];
+          if (take) {
+            key[j] = ok;
+            val[j] = ov;
+          }
+        }
+      }
+    }
+  }
+}
+
 template <typename T, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 3) chain_warp_kernel(ChainParams<T> prm) {
+__global__ void __launch_bounds__(WARPS * 32, ESS_WARP_MINBLOCKS)
+chain_warp_kernel(ChainParams<T> prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = prm.m, d = prm.d;
@@ -250,43 +301,10 @@ __global__ void __launch_bounds__(WARPS * 32, 3) chain_warp_kernel(ChainParams<T
           }
         }
       }
-      // bitonic network over kCap elements, element e = lane + 32 j
-#pragma unroll
-      for (int kk = 2; kk <= kCap; kk <<= 1) {
-#pragma unroll
-        for (int st = kk >> 1; st > 0; st >>= 1) {
-          if (st >= 32) {
-            const int js = st >> 5;
-#pragma unroll
-            for (int j = 0; j < kPer; ++j) {
-              const int jp = j ^ js;
-              if (jp > j) {
-                const int e = lane + 32 * j;
-                const bool up = (e & kk) == 0;
-                if ((key[j] > key[jp]) == up) {
-                  T tk = key[j]; key[j] = key[jp]; key[jp] = tk;
-                  T tv = val[j]; val[j] = val[jp]; val[jp] = tv;
-                }
-              }
-            }
-          } else {
-            const bool lower = (lane & st) == 0;
-#pragma unroll
-            for (int j = 0; j < kPer; ++j) {
-              const int e = lane + 32 * j;
-              const bool up = (e & kk) == 0;
-              const T ok = __shfl_xor_sync(kFull, key[j], st);
-              const T ov = __shfl_xor_sync(kFull, val[j], st);
-              // the lower element keeps the smaller key when sorting upwards
-              const bool take = lower == up ? ok < key[j] : ok > key[j];
-              if (take) {
-                key[j] = ok;
-                val[j] = ov;
-              }
-            }
-          }
-        }
-      }
+      // bitonic sort of the smallest power-of-two size that holds the arcs
+      if (n_surv <= 32) warp_bitonic<T, 1>(key, val, lane);
+      else if (n_surv <= 64) warp_bitonic<T, 2>(key, val, lane);
+      else warp_bitonic<T, kPer>(key, val, lane);
       // warp-wide counts
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {

@@ -2,12 +2,15 @@
 //
 // The products q_i = a_i . nu of Sec. 2.2 for all chains form one GEMM
 // Q (chains x m) = NU (chains x d) . A^T (A: m x d), both operands K-major.
-// The mixed form evaluates it with the BF16x3 scheme: with nu = nu_hi + nu_lo
-// and a = a_hi + a_lo (bf16 splits of the float values),
-//     q ~= nu_hi.a_hi + nu_lo.a_hi + nu_hi.a_lo,
-// three BF16 products accumulated in one FP32 accumulator in tensor memory.
+// The mixed form evaluates it with exact three-way bf16 splits of the float
+// values, nu = n0 + n1 + n2 and a = a0 + a1 + a2 (relative weights 1, 2^-8,
+// 2^-16), keeping the six products of weight >= 2^-16 ("BF16x6"):
+//     q ~= n0.a0 + (n2.a0 + n1.a1 + n0.a2 + n1.a0 + n0.a1),
+// the leading product and the five smaller ones in two FP32 accumulators in
+// tensor memory.  The same kernel, in "pairs" mode, evaluates the exact
+// fixed-point refresh of p = A x (see tc_refresh).
 //
-// Kernel structure (one 128 x BN output tile per CTA, 4 warps):
+// Kernel structure (one 128 x BN output tile per CTA, 6 warps):
 //   warp 0 / lane 0   TMA producer: for every (K block, pass) loads the
 //                     128 x 64 nu tile and the BN x 64 A tile of that pass
 //                     into a ring of shared-memory stages (128-byte swizzle),
@@ -16,8 +19,11 @@
 //                     tcgen05.mma.kind::f16 (K = 16 each) into the TMEM
 //                     accumulator and commits to the stage's "empty"
 //                     mbarrier so the producer can refill it;
-//   all 4 warps       epilogue: tcgen05.ld of the accumulator rows (TMEM lane
-//                     = chain row) and coalesced 16-byte stores to Q.
+//   warps 2..5        epilogue: tcgen05.ld of the accumulator rows (TMEM lane
+//                     = chain row, warp w reads lanes 32 (w % 4) ..) and
+//                     16-byte stores to Q; in pairs mode they consume each
+//                     slice pair's accumulator while the next pair runs in
+//                     the other TMEM buffer.
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the kernel
 // sets kStatusTimeout, drains its own copies, frees TMEM and returns.
 #include <cuda.h>

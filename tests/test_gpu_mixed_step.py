@@ -1,4 +1,4 @@
-"""Mixed form: the BF16x3 tensor-core GEMM and the FP32 step vs the FP64 oracle.
+"""Mixed form: the BF16x6 tensor-core GEMM and the FP32 step vs the FP64 oracle.
 
 Bar (stated for the mixed form): interval endpoints and theta within 1e-5 rad
 and zero infeasible iterates.  A chain whose active endpoints are so
@@ -42,7 +42,7 @@ def q_error_bound(A, NU):
 @pytest.mark.parametrize("n,m,d", [(1, 20, 10), (130, 300, 137), (256, 448, 64),
                                    (200, 1000, 333), (128, 2000, 1000), (77, 4100, 50)])
 def test_products_tensor_core_gemm(n, m, d):
-    """q = A nu from the tcgen05 BF16x3 GEMM vs FP64, and p = A x (refresh) vs FP64."""
+    """q = A nu from the tcgen05 BF16x6 GEMM vs FP64, and p = A x (refresh) vs FP64."""
     rng = np.random.default_rng(n * 7 + m)
     A = rng.standard_normal((m, d)) / math.sqrt(d)
     b = np.ones(m)
