@@ -6,6 +6,12 @@
 namespace ess {
 namespace {
 
+__device__ __forceinline__ uint2 pack4(const __nv_bfloat16 (&v)[4]) {
+  const uint32_t lo = (uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16);
+  const uint32_t hi = (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16);
+  return make_uint2(lo, hi);
+}
+
 // One thread per (chain, Philox block): 4 consecutive coordinates.
 __global__ void draw_nu_f64_kernel(double* __restrict__ nu, int n_chains, int d, int ld,
                                    uint64_t seed, uint32_t t, uint32_t problem, uint32_t chain0) {
@@ -41,17 +47,33 @@ __global__ void draw_nu_f32_kernel(float* __restrict__ nu, int ld, __nv_bfloat16
   box_muller4(r, z);
   const int left = d - 4 * n;
   float* row = nu + (size_t)c * ld + 4 * n;
-  for (int k = 0; k < 4 && k < left; ++k) row[k] = z[k];
+  if (left >= 4 && (reinterpret_cast<uintptr_t>(row) & 15) == 0) {
+    *reinterpret_cast<float4*>(row) = make_float4(z[0], z[1], z[2], z[3]);
+  } else {
+    for (int k = 0; k < 4 && k < left; ++k) row[k] = z[k];
+  }
   if (s0 != nullptr) {
     // exact three-way bf16 split: z = a + b + c
+    __nv_bfloat16 a[4], b[4], e[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      a[k] = __float2bfloat16_rn(z[k]);
+      const float r1 = z[k] - __bfloat162float(a[k]);
+      b[k] = __float2bfloat16_rn(r1);
+      e[k] = __float2bfloat16_rn(r1 - __bfloat162float(b[k]));
+    }
     const size_t o = (size_t)c * ld_bf + 4 * n;
-    for (int k = 0; k < 4 && k < left; ++k) {
-      const __nv_bfloat16 a = __float2bfloat16_rn(z[k]);
-      const float r1 = z[k] - __bfloat162float(a);
-      const __nv_bfloat16 b = __float2bfloat16_rn(r1);
-      s0[o + k] = a;
-      s1[o + k] = b;
-      s2[o + k] = __float2bfloat16_rn(r1 - __bfloat162float(b));
+    if (left >= 4 && (o & 3) == 0) {
+      // 8-byte stores of four bf16 values (ld_bf is a multiple of 8)
+      *reinterpret_cast<uint2*>(s0 + o) = pack4(a);
+      *reinterpret_cast<uint2*>(s1 + o) = pack4(b);
+      *reinterpret_cast<uint2*>(s2 + o) = pack4(e);
+    } else {
+      for (int k = 0; k < 4 && k < left; ++k) {
+        s0[o + k] = a[k];
+        s1[o + k] = b[k];
+        s2[o + k] = e[k];
+      }
     }
   }
 }

@@ -30,6 +30,8 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -108,15 +110,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity to complete.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
+// Bounded wait for the phase with the given parity to complete (slow path).
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity) {
   const unsigned long long t0 = global_ns();
   for (;;) {
     for (int i = 0; i < 256; ++i)
       if (mbar_try_wait(bar, parity)) return true;
     if (global_ns() - t0 > kWaitNs) return false;
   }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity);
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
@@ -449,6 +454,197 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
   if (warp == 0) tmem_dealloc(tmem_d, TMEM_COLS);
 }
 
+
+// ---- persistent BF16x6 GEMM: every operand tile loaded once per K block ------
+//
+// q tiles of 128 chains x 128 rows of A, taken round-robin by one CTA per SM.
+// A K block needs six 16 KB tiles (three nu slices, three A slices); they
+// stream through a ring of 12 shared-memory slots in the order
+// nu0, A0, A1, nu1, A2, nu2, each slot with a "full" (TMA landed) and an
+// "empty" (last MMA reading it finished) mbarrier.  The six products of a K
+// block, in issue order, and the tiles each reads (ring positions):
+//   (nu0, A0) -> acc 0;  (nu0, A1) (nu1, A0) (nu0, A2) (nu1, A1) (nu2, A0) -> acc 1
+// A tile's slot is released after its last product.  Accumulators are
+// double-buffered in TMEM (2 buffers x 2 accumulators x 128 columns), so the
+// four epilogue warps drain tile i while the MMA warp computes tile i + 1.
+constexpr int kQBN = 128;
+constexpr int kQSlots = 12;
+constexpr uint32_t kQTile = 128 * BK * 2;  // 16 KB
+
+struct QProd { unsigned char xs, as, acc, first; };  // ring positions of the nu and A tiles
+__constant__ QProd kQProds[6] = {{0, 1, 0, 1}, {0, 2, 1, 1}, {3, 1, 1, 0},
+                                 {0, 4, 1, 0}, {3, 2, 1, 0}, {5, 1, 1, 0}};
+// after product p, release these ring positions (0xFF: none)
+__constant__ unsigned char kQRelease[6][2] = {{0xFF, 0xFF}, {0xFF, 0xFF}, {0xFF, 0xFF},
+                                              {0, 4},       {2, 3},       {1, 5}};
+
+__global__ void __launch_bounds__(kThreads, 1)
+tc_q6_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcArgs args) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  unsigned char* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  const uint32_t sbase = smem_u32(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kQSlots * kQTile);
+  // bars: [0, 12) full, [12, 24) empty, 24 + {0, 1} acc full, 26 + {0, 1} acc empty
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kQSlots + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto full_bar = [&](int s) { return smem_u32(bars + s); };
+  auto empty_bar = [&](int s) { return smem_u32(bars + kQSlots + s); };
+  auto accf_bar = [&](int b) { return smem_u32(bars + 2 * kQSlots + b); };
+  auto acce_bar = [&](int b) { return smem_u32(bars + 2 * kQSlots + 2 + b); };
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kQSlots; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf_bar(b), 1);
+      mbar_init(acce_bar(b), 4);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_d = *tmem_slot;
+  const int n_nt = (args.n_cols + kQBN - 1) / kQBN;
+  const int n_mt = (args.n_rows + BM - 1) / BM;
+  const int n_tiles = n_nt * n_mt;
+  const int KB = args.kblocks;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    // the ring holds two K blocks: K block number gkb uses slots
+    // 6 (gkb & 1) .. + 5, in round gkb >> 1
+    int gkb = 0;
+    int last_round[kQSlots];
+#pragma unroll
+    for (int s = 0; s < kQSlots; ++s) last_round[s] = -1;
+    for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+      const int m0 = (tile / n_nt) * BM, n0 = (tile % n_nt) * kQBN;
+      for (int kb = 0; kb < KB && !*abort_flag; ++kb, ++gkb) {
+        const int sbase6 = (gkb & 1) * 6;
+        const int round = gkb >> 1;
+#pragma unroll 1
+        for (int t = 0; t < 6; ++t) {
+          const int slot = sbase6 + t;
+          if (round > 0 && !mbar_wait(empty_bar(slot), (uint32_t)((round - 1) & 1))) {
+            *abort_flag = 1;
+            break;
+          }
+          // ring order nu0, A0, A1, nu1, A2, nu2
+          const bool is_nu = t == 0 || t == 3 || t == 5;
+          const int sl = t == 0 ? 0 : t == 1 ? 0 : t == 2 ? 1 : t == 3 ? 1 : t == 4 ? 2 : 2;
+          const CUtensorMap* map = is_nu ? &maps.x[sl] : &maps.b[sl];
+          mbar_expect_tx(full_bar(slot), kQTile);
+          tma_load_2d(sbase + slot * kQTile, map, kb * BK, is_nu ? m0 : n0, full_bar(slot));
+          last_round[slot] = round;
+        }
+      }
+    }
+    if (*abort_flag) {
+#pragma unroll
+      for (int s = 0; s < kQSlots; ++s)
+        if (last_round[s] >= 0) (void)mbar_wait(full_bar(s), (uint32_t)(last_round[s] & 1));
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t idesc = idesc_bf16(BM, kQBN);
+    int gkb = 0;
+    int lt = 0;
+    for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x, ++lt) {
+      const int buf = lt & 1;
+      if (lt >= 2 && !mbar_wait(acce_bar(buf), (uint32_t)(((lt >> 1) - 1) & 1))) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      for (int kb = 0; kb < KB; ++kb, ++gkb) {
+        const int sbase6 = (gkb & 1) * 6;
+        const uint32_t par = (uint32_t)((gkb >> 1) & 1);
+        for (int p = 0; p < 6; ++p) {
+          const QProd pr = kQProds[p];
+          const int sx = sbase6 + pr.xs, sa = sbase6 + pr.as;
+          if (!mbar_wait(full_bar(sx), par) || !mbar_wait(full_bar(sa), par)) {
+            *abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t adesc = smem_desc_sw128(sbase + (uint32_t)sx * kQTile);
+          const uint64_t bdesc = smem_desc_sw128(sbase + (uint32_t)sa * kQTile);
+          const uint32_t acc = tmem_d + (uint32_t)((buf * 2 + pr.acc) * kQBN);
+          const bool fresh = kb == 0 && pr.first;
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k)
+            umma_bf16(acc, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc,
+                      (fresh && k == 0) ? 0u : 1u);
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const unsigned char pos = kQRelease[p][r];
+            if (pos != 0xFF) umma_commit(empty_bar(sbase6 + pos));
+          }
+        }
+        if (*abort_flag) break;
+      }
+      umma_commit(accf_bar(buf));
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue warps 2..5 ----------------
+    const int quarter = warp & 3;
+    const uint32_t lane_base = tmem_d + ((uint32_t)(quarter * 32) << 16);
+    const bool vec_ok = (args.ldq & 3) == 0 && ((reinterpret_cast<uintptr_t>(args.Q) & 15) == 0);
+    int lt = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++lt) {
+      const int buf = lt & 1;
+      if (*abort_flag || !mbar_wait(accf_bar(buf), (uint32_t)((lt >> 1) & 1))) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const int m0 = (tile / n_nt) * BM, n0 = (tile % n_nt) * kQBN;
+      const int row = m0 + quarter * 32 + lane;
+      const bool row_ok = row < args.n_rows;
+      float* qrow = args.Q + (size_t)(row_ok ? row : 0) * args.ldq;
+#pragma unroll 1
+      for (int c0 = 0; c0 < kQBN; c0 += 32) {
+        uint32_t v0[32], v1[32];
+        tmem_ld_32cols(lane_base + (uint32_t)((buf * 2) * kQBN + c0), v0);
+        tmem_ld_32cols(lane_base + (uint32_t)((buf * 2 + 1) * kQBN + c0), v1);
+        tmem_ld_wait();
+        if (!row_ok) continue;
+        float f[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v0[j]) + __uint_as_float(v1[j]);
+        const int col = n0 + c0;
+        if (vec_ok && col + 32 <= args.n_cols) {
+          float4* dst = reinterpret_cast<float4*>(qrow + col);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            dst[j] = make_float4(f[4 * j], f[4 * j + 1], f[4 * j + 2], f[4 * j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (col + j < args.n_cols) qrow[col + j] = f[j];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce_bar(buf));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(args.status, kStatusTimeout);
+  if (warp == 0) tmem_dealloc(tmem_d, 512);
+}
+
 // Fixed-point slices of the chain states for the exact refresh: per row c,
 // t_c = 2^e with max_j |x_cj| < t_c, and x_cj / t_c = sum_l e_l 2^(-w l) + r,
 // e_l integers in (-2^w, 2^w) stored exactly as bf16.  One warp per row.
@@ -588,6 +784,16 @@ int num_sms() {
 
 inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
 
+cudaError_t launch_q6(const TcMaps& maps, const TcArgs& args, int sms, cudaStream_t s) {
+  const size_t smem = (size_t)kQSlots * kQTile + 1024 + 256;
+  cudaError_t e = cudaFuncSetAttribute(tc_q6_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int tiles = ((args.n_rows + BM - 1) / BM) * ((args.n_cols + kQBN - 1) / kQBN);
+  tc_q6_kernel<<<std::min(tiles, sms), kThreads, smem, s>>>(maps, args);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 struct TcGemmPlan {
@@ -601,6 +807,7 @@ struct TcGemmPlan {
   float* col_scale = nullptr;       // s_i
   CUtensorMap rmaps[kMaxSlices];
   double bound_factor = 0.0;        // |p_exact - p| <= bound_factor * s_i * t_c
+  bool q_persistent = false;        // persistent load-once kernel for q (else per-pass tiles)
 };
 
 void tc_gemm_tile_for(int n_chains, int m, int* bn, int* stages) {
@@ -645,6 +852,10 @@ int tc_refresh_slices(int d, int* w_out) {
 cudaError_t tc_gemm_create(TcGemmPlan** plan, const double* A, int m, int d) {
   *plan = nullptr;
   TcGemmPlan* p = new TcGemmPlan();
+  // q GEMM variant: "passes" = one operand-tile pair per pipeline stage,
+  // "ring" = persistent kernel loading each slice tile once per K block
+  const char* qk = std::getenv("ESS_Q_KERNEL");
+  p->q_persistent = qk != nullptr && std::strcmp(qk, "ring") == 0;
   p->m = m;
   p->d = d;
   p->ld_bf = (d + 7) & ~7;
@@ -739,6 +950,24 @@ cudaError_t tc_gemm_q(TcGemmPlan* plan, __nv_bfloat16* const nu[3], int ld_bf, i
   if (!plan) return cudaErrorInvalidValue;
   if (n_chains == 0) return cudaSuccess;
   if (ld_bf != plan->ld_bf) return cudaErrorInvalidValue;
+  if (plan->q_persistent) {
+    TcMaps maps;
+    std::memset(&maps, 0, sizeof(maps));
+    for (int k = 0; k < 3; ++k) {
+      cudaError_t e = make_map(&maps.x[k], nu[k], n_chains, plan->d, ld_bf, BM);
+      if (e != cudaSuccess) return e;
+      maps.b[k] = plan->qmaps[1][k];  // 128-row boxes
+    }
+    TcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n_rows = n_chains;
+    a.n_cols = plan->m;
+    a.kblocks = (plan->d + BK - 1) / BK;
+    a.Q = Q;
+    a.ldq = ldq;
+    a.status = status;
+    return launch_q6(maps, a, num_sms(), s);
+  }
   int bn = 0;
   tc_gemm_tile_for(n_chains, plan->m, &bn, nullptr);
   int wi = 0;
