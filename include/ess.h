@@ -53,7 +53,7 @@ typedef enum {
 
 typedef enum {
     ESS_PREC_FP64 = 0,          /* every step in double precision */
-    ESS_PREC_MIXED = 1          /* q = A nu by BF16x6 tensor cores, FP32 step,
+    ESS_PREC_MIXED = 1          /* q = A nu by FP16x3 tensor cores, FP32 step,
                                    FP64 near-tangent arccos, A x refresh and
                                    feasibility residual */
 } ess_precision;
@@ -195,7 +195,7 @@ ess_status ess_step_with_draws(ess_state *state, const double *X, const double *
 /*
  * The products the step uses, as the state computes them (for verification):
  * p = A x by the refresh path and q = A nu by the step's GEMM (FP64 FMAs in
- * the FP64 form, the BF16x6 tensor-core GEMM in the mixed form).
+ * the FP64 form, the FP16x3 tensor-core GEMM in the mixed form).
  *   X, nu   device, n_chains x d doubles (rounded to float first in the mixed
  *           form, as a run stores them).
  *   P, Q    device, n_chains x m doubles; either may be NULL.

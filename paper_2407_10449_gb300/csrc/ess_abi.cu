@@ -65,7 +65,7 @@ struct ess_state {
   int d = 0, m = 0;
   ess_config cfg{};
   int device = 0;
-  int ld_bf = 0;          // row stride of the bf16 operands (d rounded up to 8)
+  int ld16 = 0;           // row stride of the 16-bit operands (d rounded up to 8)
   int chain_threads = 0;  // threads per chain of the step kernel
   // constants (device)
   double* A64 = nullptr;
@@ -86,7 +86,8 @@ struct ess_state {
   int t_next = 0;          // global index of the next step of the loaded chains
   int p_fresh_t = -1;      // step index at which p was last recomputed from x
   long long host_steps = 0;  // chain-steps enqueued since the last stats reset
-  __nv_bfloat16* NU_s[3] = {nullptr, nullptr, nullptr};  // exact bf16 split of nu
+  __half* NU_h[2] = {nullptr, nullptr};  // scaled fp16 split of nu (tensor-core q)
+  float* nu_unscale = nullptr;           // 1 / t_c of caller-supplied nu (scanned per chain)
   __nv_bfloat16* x_slices = nullptr;  // refresh: fixed-point slices of the states
   float* row_scale = nullptr;         // refresh: per-chain power-of-two scales
   double* P64 = nullptr;              // refresh: FP64 product for the start check
@@ -158,7 +159,8 @@ void free_work(ess_state* s) {
   s->P = s->Q = s->NU = nullptr;
   dev_free(s->Xw);
   dev_free(s->Xd);
-  for (auto& p : s->NU_s) dev_free(p);
+  for (auto& p : s->NU_h) dev_free(p);
+  dev_free(s->nu_unscale);
   dev_free(s->x_slices);
   dev_free(s->row_scale);
   dev_free(s->P64);
@@ -177,15 +179,16 @@ ess_status ensure_capacity(ess_state* s, int n) {
   ESS_CUDA(cudaMalloc(&s->NU, (size_t)n * s->d * e));
   if (mixed(s)) {
     ESS_CUDA(dev_alloc(&s->Xw, (size_t)n * s->d));
-    for (auto& p : s->NU_s) {
-      ESS_CUDA(dev_alloc(&p, (size_t)n * s->ld_bf));
-      // the padding columns d .. ld_bf - 1 stay zero
-      ESS_CUDA(cudaMemset(p, 0, (size_t)n * s->ld_bf * sizeof(__nv_bfloat16)));
+    for (auto& p : s->NU_h) {
+      ESS_CUDA(dev_alloc(&p, (size_t)n * s->ld16));
+      // the padding columns d .. ld16 - 1 stay zero
+      ESS_CUDA(cudaMemset(p, 0, (size_t)n * s->ld16 * sizeof(__half)));
     }
+    ESS_CUDA(dev_alloc(&s->nu_unscale, (size_t)n));
     if (s->cfg.refresh_mode == ESS_REFRESH_SPLIT) {
       const int K = ess::tc_refresh_num_slices(s->tc_plan);
-      ESS_CUDA(dev_alloc(&s->x_slices, (size_t)K * n * s->ld_bf));
-      ESS_CUDA(cudaMemset(s->x_slices, 0, (size_t)K * n * s->ld_bf * sizeof(__nv_bfloat16)));
+      ESS_CUDA(dev_alloc(&s->x_slices, (size_t)K * n * s->ld16));
+      ESS_CUDA(cudaMemset(s->x_slices, 0, (size_t)K * n * s->ld16 * sizeof(__nv_bfloat16)));
       ESS_CUDA(dev_alloc(&s->row_scale, (size_t)n));
       ESS_CUDA(dev_alloc(&s->P64, (size_t)n * s->m));
     }
@@ -204,7 +207,7 @@ ess_status refresh_p(ess_state* s, int n, const void* Xcur, bool with_drift, boo
   if (mixed(s) && s->cfg.refresh_mode == ESS_REFRESH_SPLIT) {
     // exact products on the tensor cores (fixed-point split), rounded once
     const float* Xf = static_cast<const float*>(Xcur);
-    ESS_CUDA(ess::tc_refresh(s->tc_plan, Xf, s->d, n, s->x_slices, (size_t)n * s->ld_bf,
+    ESS_CUDA(ess::tc_refresh(s->tc_plan, Xf, s->d, n, s->x_slices, (size_t)n * s->ld16,
                              s->row_scale, static_cast<float*>(s->P), check ? s->P64 : nullptr,
                              s->m, s->anorm, with_drift ? &s->dstats->max_drift_bits : nullptr,
                              s->dstatus, st));
@@ -240,12 +243,13 @@ ess_status refresh_p(ess_state* s, int n, const void* Xcur, bool with_drift, boo
   return ESS_OK;
 }
 
-// q = A nu for all chains.
-ess_status compute_q(ess_state* s, int n, cudaStream_t st) {
+// q = A nu for all chains.  drawn: nu came from the draw kernel (fixed fp16
+// split scale); otherwise the caller's nu was split with per-chain scales.
+ess_status compute_q(ess_state* s, int n, cudaStream_t st, bool drawn = true) {
   if (mixed(s)) {
-    cudaError_t e = ess::tc_gemm_q(s->tc_plan, s->NU_s, s->ld_bf, n, static_cast<float*>(s->Q),
-                                   s->m, s->dstatus, st);
-    if (e != cudaSuccess) return cuda_fail(e, "BF16x6 tensor-core GEMM");
+    cudaError_t e = ess::tc_gemm_q(s->tc_plan, s->NU_h, drawn ? nullptr : s->nu_unscale, s->ld16,
+                                   n, static_cast<float*>(s->Q), s->m, s->dstatus, st);
+    if (e != cudaSuccess) return cuda_fail(e, "FP16x3 tensor-core GEMM");
   } else {
     ESS_CUDA((ess::launch_gemm_nt_f64<double, double>(static_cast<const double*>(s->NU), s->d,
                                                        s->A64, s->d, static_cast<double*>(s->Q),
@@ -387,7 +391,7 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
   s->m = m;
   s->cfg = c;
   s->device = dev;
-  s->ld_bf = (d + 7) & ~7;
+  s->ld16 = (d + 7) & ~7;
   s->chain_threads = threads;
 
   auto cleanup = [&](ess_status st) {
@@ -524,7 +528,7 @@ ess_status ess_chains_step(ess_state* s, int n_iter, uint64_t seed, void* sample
     if (mixed(s)) {
       {
         PhaseScope ps(s, st, ESS_PHASE_DRAW);
-        ESS_CUDA(ess::launch_draw_nu_f32(static_cast<float*>(s->NU), d, s->NU_s, s->ld_bf, n, d,
+        ESS_CUDA(ess::launch_draw_nu_f32(static_cast<float*>(s->NU), d, s->NU_h, s->ld16, n, d,
                                          seed, t, 0u, 0u, st));
       }
       {
@@ -692,12 +696,12 @@ ess_status ess_step_with_draws(ess_state* s, const double* X, const double* nu, 
   if (mixed(s)) {
     ESS_CUDA((ess::launch_convert<double, float>(X, d, s->Xw, d, n, d, st)));
     ESS_CUDA((ess::launch_convert<double, float>(nu, d, static_cast<float*>(s->NU), d, n, d, st)));
-    ESS_CUDA(ess::tc_split3(static_cast<const float*>(s->NU), d, n, d, s->NU_s[0], s->NU_s[1],
-                            s->NU_s[2], s->ld_bf, st));
+    ESS_CUDA(ess::tc_split2_rows(static_cast<const float*>(s->NU), d, n, d, s->NU_h[0],
+                                 s->NU_h[1], s->ld16, s->nu_unscale, st));
     rc = refresh_p(s, n, s->Xw, false, true, st);
     if (rc == ESS_OK) rc = read_status(s, st);
     if (rc != ESS_OK) return rc;
-    rc = compute_q(s, n, st);
+    rc = compute_q(s, n, st, false);
     if (rc != ESS_OK) return rc;
     ess::ChainParams<float> p = base_params<float>(s, n);
     p.X = s->Xw;
@@ -758,9 +762,9 @@ ess_status ess_products(ess_state* s, const double* X, const double* nu, int n_c
     }
     if (Q) {
       ESS_CUDA((ess::launch_convert<double, float>(nu, d, static_cast<float*>(s->NU), d, n, d, st)));
-      ESS_CUDA(ess::tc_split3(static_cast<const float*>(s->NU), d, n, d, s->NU_s[0], s->NU_s[1],
-                              s->NU_s[2], s->ld_bf, st));
-      rc = compute_q(s, n, st);
+      ESS_CUDA(ess::tc_split2_rows(static_cast<const float*>(s->NU), d, n, d, s->NU_h[0],
+                                   s->NU_h[1], s->ld16, s->nu_unscale, st));
+      rc = compute_q(s, n, st, false);
       if (rc != ESS_OK) return rc;
       ESS_CUDA((ess::launch_convert<float, double>(static_cast<const float*>(s->Q), m, Q, m, n, m, st)));
     }

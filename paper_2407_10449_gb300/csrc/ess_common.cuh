@@ -11,11 +11,16 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace ess {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr float kTwoPiF = 6.28318548202514648f;  // 2 pi rounded to float (upwards)
+// Scale of drawn nu in its fp16 split for the tensor-core product: the float
+// Box-Muller radius sqrt(-2 ln u1) with u1 >= 2^-32 stays below 6.67, so
+// nu * 2^12 stays below 2^15, inside the fp16 range, with no per-chain scan.
+constexpr float kNuSplitScale = 4096.f;
 
 // Device-side counters of one launch sequence (accumulated over a run).
 struct DevStats {

@@ -4,29 +4,33 @@
 #include <cstddef>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace ess {
 
 struct TcGemmPlan;
 
-// Prepares the constant operand A (host, m x d row-major doubles): the exact
-// three-way bf16 split of A rounded to float (for q = A nu) and the
-// fixed-point slices of A with per-row power-of-two scales (for the exact
-// refresh).  Operand rows are padded to a multiple of 8 elements.
+// Prepares the constant operand A (host, m x d row-major doubles): the scaled
+// two-way fp16 split of A rounded to float (for q = A nu) and the fixed-point
+// slices of A with per-row power-of-two scales (for the exact refresh).
+// Operand rows are padded to a multiple of 8 elements.
 cudaError_t tc_gemm_create(TcGemmPlan** plan, const double* A, int m, int d);
 void tc_gemm_destroy(TcGemmPlan* plan);
 
-// Q[c, i] = a_i . nu_c with nu = nu0 + nu1 + nu2 (exact bf16 split of the
-// float nu, rows of ld_bf elements) and a = a0 + a1 + a2, using the six
-// products whose weight is at least 2^-16 (BF16x6), accumulated in FP32 in
-// tensor memory: the leading product in one accumulator, the five smaller
-// ones in a second, added in the epilogue.
-cudaError_t tc_gemm_q(TcGemmPlan* plan, __nv_bfloat16* const nu[3], int ld_bf, int n_chains,
-                      float* Q, int ldq, int* status, cudaStream_t s);
+// Q[c, i] = a_i . nu_c from the scaled fp16 splits nu_c t_c = h0 + h1 (rows of
+// ld16 elements) and a_i s_i = a0 + a1, using the three products h0.a0,
+// h1.a0, h0.a1 (FP16x3), accumulated in FP32 in tensor memory (the leading
+// product in one accumulator, the other two in a second, added in the
+// epilogue), then multiplied by 1 / s_i and 1 / t_c (powers of two).
+// nu_unscale holds 1 / t_c per chain; nullptr means 1 / kNuSplitScale for all
+// (drawn nu, see ess_common.cuh).
+cudaError_t tc_gemm_q(TcGemmPlan* plan, __half* const nu[2], const float* nu_unscale, int ld16,
+                      int n_chains, float* Q, int ldq, int* status, cudaStream_t s);
 
-// Exact split of a float matrix into three bf16 slices (v = s0 + s1 + s2).
-cudaError_t tc_split3(const float* src, int ld, int rows, int cols, __nv_bfloat16* s0,
-                      __nv_bfloat16* s1, __nv_bfloat16* s2, int ld_bf, cudaStream_t s);
+// Scaled fp16 split of float rows (see tc_gemm_q): per row t = 2^(15 - e) with
+// max |v| in [2^(e-1), 2^e); unscale[row] = 1 / t.
+cudaError_t tc_split2_rows(const float* src, int ld, int rows, int cols, __half* h0, __half* h1,
+                           int ld16, float* unscale, cudaStream_t s);
 
 // p = A x for float chain states X (n_chains x d, row stride ldx) with every
 // product exact: x and A are cut into w-bit integer slices scaled by powers of
@@ -36,7 +40,7 @@ cudaError_t tc_split3(const float* src, int ld, int rows, int cols, __nv_bfloat1
 // from A x by at most bound_factor * s_i * t_c (truncated slices and dropped
 // pairs).  Writes P32 (rounded once to float) and/or P64; if drift_bits is
 // set, folds max |P32_new - P32_old| / anorm_i into it.  x_slices needs
-// K x slice_stride bf16 (slice_stride >= n_chains * ld_bf) and row_scale
+// K x slice_stride bf16 (slice_stride >= n_chains * ld16) and row_scale
 // n_chains floats of scratch.
 cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
                        __nv_bfloat16* x_slices, size_t slice_stride, float* row_scale,

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "ess_common.cuh"
 
@@ -13,11 +14,12 @@ namespace ess {
 // nu[c, j] for chains chain0 .. chain0 + n_chains - 1 at step t (row stride ld).
 cudaError_t launch_draw_nu_f64(double* nu, int n_chains, int d, int ld, uint64_t seed,
                                uint32_t t, uint32_t problem, uint32_t chain0, cudaStream_t s);
-// float nu plus (if split != nullptr) its exact three-way bf16 split, rows of
-// ld_bf elements; columns d .. ld_bf - 1 of the split are left untouched.
-cudaError_t launch_draw_nu_f32(float* nu, int ld, __nv_bfloat16* const split[3], int ld_bf,
-                               int n_chains, int d, uint64_t seed, uint32_t t, uint32_t problem,
-                               uint32_t chain0, cudaStream_t s);
+// float nu plus (if split != nullptr) the two-way fp16 split of nu * kNuSplitScale
+// (h0 = fp16(y), h1 = fp16(y - h0)), rows of ld16 elements; columns
+// d .. ld16 - 1 of the split are left untouched.
+cudaError_t launch_draw_nu_f32(float* nu, int ld, __half* const split[2], int ld16, int n_chains,
+                               int d, uint64_t seed, uint32_t t, uint32_t problem, uint32_t chain0,
+                               cudaStream_t s);
 cudaError_t launch_philox_blocks(uint64_t seed, uint32_t chain, uint32_t t, uint32_t problem,
                                  uint32_t stream, int n_blocks, uint32_t* out, cudaStream_t s);
 

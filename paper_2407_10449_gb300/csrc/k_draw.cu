@@ -6,9 +6,9 @@
 namespace ess {
 namespace {
 
-__device__ __forceinline__ uint2 pack4(const __nv_bfloat16 (&v)[4]) {
-  const uint32_t lo = (uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16);
-  const uint32_t hi = (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16);
+__device__ __forceinline__ uint2 pack4(const __half (&v)[4]) {
+  const uint32_t lo = (uint32_t)__half_as_ushort(v[0]) | ((uint32_t)__half_as_ushort(v[1]) << 16);
+  const uint32_t hi = (uint32_t)__half_as_ushort(v[2]) | ((uint32_t)__half_as_ushort(v[3]) << 16);
   return make_uint2(lo, hi);
 }
 
@@ -33,9 +33,8 @@ __global__ void draw_nu_f64_kernel(double* __restrict__ nu, int n_chains, int d,
   }
 }
 
-__global__ void draw_nu_f32_kernel(float* __restrict__ nu, int ld, __nv_bfloat16* __restrict__ s0,
-                                   __nv_bfloat16* __restrict__ s1, __nv_bfloat16* __restrict__ s2,
-                                   int ld_bf, int n_chains, int d,
+__global__ void draw_nu_f32_kernel(float* __restrict__ nu, int ld, __half* __restrict__ h0,
+                                   __half* __restrict__ h1, int ld16, int n_chains, int d,
                                    uint64_t seed, uint32_t t, uint32_t problem, uint32_t chain0) {
   const int nblk = (d + 3) >> 2;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -52,27 +51,25 @@ __global__ void draw_nu_f32_kernel(float* __restrict__ nu, int ld, __nv_bfloat16
   } else {
     for (int k = 0; k < 4 && k < left; ++k) row[k] = z[k];
   }
-  if (s0 != nullptr) {
-    // exact three-way bf16 split: z = a + b + c
-    __nv_bfloat16 a[4], b[4], e[4];
+  if (h0 != nullptr) {
+    // two-way fp16 split of nu * 2^12 (|nu| < 6.67 keeps it below 2^15):
+    // y = a + b + r with a = fp16(y), b = fp16(y - a)
+    __half a[4], b[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      a[k] = __float2bfloat16_rn(z[k]);
-      const float r1 = z[k] - __bfloat162float(a[k]);
-      b[k] = __float2bfloat16_rn(r1);
-      e[k] = __float2bfloat16_rn(r1 - __bfloat162float(b[k]));
+      const float y = z[k] * kNuSplitScale;
+      a[k] = __float2half_rn(y);
+      b[k] = __float2half_rn(y - __half2float(a[k]));
     }
-    const size_t o = (size_t)c * ld_bf + 4 * n;
+    const size_t o = (size_t)c * ld16 + 4 * n;
     if (left >= 4 && (o & 3) == 0) {
-      // 8-byte stores of four bf16 values (ld_bf is a multiple of 8)
-      *reinterpret_cast<uint2*>(s0 + o) = pack4(a);
-      *reinterpret_cast<uint2*>(s1 + o) = pack4(b);
-      *reinterpret_cast<uint2*>(s2 + o) = pack4(e);
+      // 8-byte stores of four fp16 values (ld16 is a multiple of 8)
+      *reinterpret_cast<uint2*>(h0 + o) = pack4(a);
+      *reinterpret_cast<uint2*>(h1 + o) = pack4(b);
     } else {
       for (int k = 0; k < 4 && k < left; ++k) {
-        s0[o + k] = a[k];
-        s1[o + k] = b[k];
-        s2[o + k] = e[k];
+        h0[o + k] = a[k];
+        h1[o + k] = b[k];
       }
     }
   }
@@ -145,16 +142,15 @@ cudaError_t launch_draw_nu_f64(double* nu, int n_chains, int d, int ld, uint64_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_draw_nu_f32(float* nu, int ld, __nv_bfloat16* const split[3], int ld_bf,
-                               int n_chains, int d, uint64_t seed, uint32_t t, uint32_t problem,
-                               uint32_t chain0, cudaStream_t s) {
+cudaError_t launch_draw_nu_f32(float* nu, int ld, __half* const split[2], int ld16, int n_chains,
+                               int d, uint64_t seed, uint32_t t, uint32_t problem, uint32_t chain0,
+                               cudaStream_t s) {
   const long long n = (long long)n_chains * ((d + 3) / 4);
   if (n == 0) return cudaSuccess;
-  __nv_bfloat16* s0 = split ? split[0] : nullptr;
-  __nv_bfloat16* s1 = split ? split[1] : nullptr;
-  __nv_bfloat16* s2 = split ? split[2] : nullptr;
-  draw_nu_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(nu, ld, s0, s1, s2, ld_bf, n_chains, d, seed,
-                                                      t, problem, chain0);
+  __half* h0 = split ? split[0] : nullptr;
+  __half* h1 = split ? split[1] : nullptr;
+  draw_nu_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(nu, ld, h0, h1, ld16, n_chains, d, seed, t,
+                                                      problem, chain0);
   return cudaGetLastError();
 }
 

@@ -2,13 +2,15 @@
 //
 // The products q_i = a_i . nu of Sec. 2.2 for all chains form one GEMM
 // Q (chains x m) = NU (chains x d) . A^T (A: m x d), both operands K-major.
-// The mixed form evaluates it with exact three-way bf16 splits of the float
-// values, nu = n0 + n1 + n2 and a = a0 + a1 + a2 (relative weights 1, 2^-8,
-// 2^-16), keeping the six products of weight >= 2^-16 ("BF16x6"):
-//     q ~= n0.a0 + (n2.a0 + n1.a1 + n0.a2 + n1.a0 + n0.a1),
-// the leading product and the five smaller ones in two FP32 accumulators in
-// tensor memory.  The same kernel, in "pairs" mode, evaluates the exact
-// fixed-point refresh of p = A x (see tc_refresh).
+// The mixed form evaluates it with two-way fp16 splits of the float values,
+// each scaled by a power of two into the top of the fp16 range (per chain
+// t_c for nu, per row s_i for A): nu t_c = h0 + h1 + r, a s_i = a0 + a1 + r',
+// |r| <= 2^-22 |nu t_c| + 2^-25.  Three products are kept ("FP16x3"):
+//     q ~= (h0.a0 + (h1.a0 + h0.a1)) / (s_i t_c),
+// the leading product and the two smaller ones in two FP32 accumulators in
+// tensor memory; the dropped h1.a1 is below 2^-22 |a s_i| |nu t_c|.  The same
+// kernel, in "pairs" mode, evaluates the exact fixed-point refresh of p = A x
+// (see tc_refresh) on bf16 integer slices.
 //
 // Kernel structure (one 128 x BN output tile per CTA, 6 warps):
 //   warp 0 / lane 0   TMA producer: for every (K block, pass) loads the
@@ -20,10 +22,10 @@
 //                     accumulator and commits to the stage's "empty"
 //                     mbarrier so the producer can refill it;
 //   warps 2..5        epilogue: tcgen05.ld of the accumulator rows (TMEM lane
-//                     = chain row, warp w reads lanes 32 (w % 4) ..) and
-//                     16-byte stores to Q; in pairs mode they consume each
-//                     slice pair's accumulator while the next pair runs in
-//                     the other TMEM buffer.
+//                     = chain row, warp w reads lanes 32 (w % 4) ..), the
+//                     power-of-two unscaling and 16-byte stores to Q; in pairs
+//                     mode they consume each slice pair's accumulator while
+//                     the next pair runs in the other TMEM buffer.
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the kernel
 // sets kStatusTimeout, drains its own copies, frees TMEM and returns.
 #include <cuda.h>
@@ -43,7 +45,7 @@ namespace ess {
 namespace {
 
 constexpr int BM = 128;             // chains per tile (MMA M)
-constexpr int BK = 64;              // bf16 elements per 128-byte swizzle row
+constexpr int BK = 64;              // 16-bit elements per 128-byte swizzle row
 constexpr int kThreads = 192;       // producer warp, MMA warp, 4 epilogue warps
 constexpr int kRefreshBN = 64;      // tile width of the exact refresh
 constexpr int kMaxSlices = 7;       // operand slices of the exact refresh
@@ -67,8 +69,9 @@ struct TcArgs {
   PassDesc pass[kMaxPasses];
   float* Q;                   // sum mode output
   int ldq;
-  const float* row_scale;     // pairs mode: t_c per chain
-  const float* col_scale;     // pairs mode: s_i per constraint
+  const float* row_scale;     // t_c per chain (sum mode: 1 / t_c, or nullptr: row_const)
+  const float* col_scale;     // s_i per constraint (sum mode: 1 / s_i)
+  float row_const;            // sum mode: 1 / t_c of every chain when row_scale is null
   float* P32;                 // pairs mode outputs (either may be null)
   double* P64;
   int ldp;
@@ -197,12 +200,12 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor of kind::f16: BF16 A and B, FP32 accumulator, both
-// operands K-major, shape M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+// Instruction descriptor of kind::f16: A and B both FP16 (bf16 = false) or
+// both BF16, FP32 accumulator, both operands K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16) {
   return (1u << 4)                          // D format: F32
-         | (1u << 7)                        // A format: BF16
-         | (1u << 10)                       // B format: BF16
+         | ((bf16 ? 1u : 0u) << 7)          // A format: FP16 (0) or BF16 (1)
+         | ((bf16 ? 1u : 0u) << 10)         // B format: FP16 (0) or BF16 (1)
          | ((uint32_t)(N >> 3) << 17)       // N / 8
          | ((uint32_t)(M >> 4) << 24);      // M / 16
 }
@@ -308,7 +311,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    constexpr uint32_t idesc = idesc_f16(BM, BN, MODE == kModePairs);
     for (int it = 0; it < total; ++it) {
       const int s = it % STAGES;
       const int round = it / STAGES;
@@ -362,6 +365,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
       const bool row_ok = row < args.n_rows && ready && !*abort_flag;
       float* qrow = args.Q + (size_t)(row_ok ? row : 0) * args.ldq;
       const bool vec_ok = (args.ldq & 3) == 0 && ((reinterpret_cast<uintptr_t>(args.Q) & 15) == 0);
+      const float rsc = args.row_scale ? args.row_scale[row_ok ? row : 0] : args.row_const;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t v[32];
@@ -379,14 +383,19 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
         if (!row_ok) continue;
         const int col = n0 + c0;
         if (vec_ok && col + 32 <= args.n_cols) {
+          // unscale by powers of two (exact): 1 / s_i per column, 1 / t_c per row
+          const float4* cs4 = reinterpret_cast<const float4*>(args.col_scale + col);
           float4* dst = reinterpret_cast<float4*>(qrow + col);
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            dst[j] = make_float4(f[4 * j], f[4 * j + 1], f[4 * j + 2], f[4 * j + 3]);
+          for (int j = 0; j < 8; ++j) {
+            const float4 cs = __ldg(cs4 + j);
+            dst[j] = make_float4(f[4 * j] * cs.x * rsc, f[4 * j + 1] * cs.y * rsc,
+                                 f[4 * j + 2] * cs.z * rsc, f[4 * j + 3] * cs.w * rsc);
+          }
         } else {
 #pragma unroll
           for (int j = 0; j < 32; ++j)
-            if (col + j < args.n_cols) qrow[col + j] = f[j];
+            if (col + j < args.n_cols) qrow[col + j] = f[j] * args.col_scale[col + j] * rsc;
         }
       }
     } else {
@@ -455,196 +464,6 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
 }
 
 
-// ---- persistent BF16x6 GEMM: every operand tile loaded once per K block ------
-//
-// q tiles of 128 chains x 128 rows of A, taken round-robin by one CTA per SM.
-// A K block needs six 16 KB tiles (three nu slices, three A slices); they
-// stream through a ring of 12 shared-memory slots in the order
-// nu0, A0, A1, nu1, A2, nu2, each slot with a "full" (TMA landed) and an
-// "empty" (last MMA reading it finished) mbarrier.  The six products of a K
-// block, in issue order, and the tiles each reads (ring positions):
-//   (nu0, A0) -> acc 0;  (nu0, A1) (nu1, A0) (nu0, A2) (nu1, A1) (nu2, A0) -> acc 1
-// A tile's slot is released after its last product.  Accumulators are
-// double-buffered in TMEM (2 buffers x 2 accumulators x 128 columns), so the
-// four epilogue warps drain tile i while the MMA warp computes tile i + 1.
-constexpr int kQBN = 128;
-constexpr int kQSlots = 12;
-constexpr uint32_t kQTile = 128 * BK * 2;  // 16 KB
-
-struct QProd { unsigned char xs, as, acc, first; };  // ring positions of the nu and A tiles
-__constant__ QProd kQProds[6] = {{0, 1, 0, 1}, {0, 2, 1, 1}, {3, 1, 1, 0},
-                                 {0, 4, 1, 0}, {3, 2, 1, 0}, {5, 1, 1, 0}};
-// after product p, release these ring positions (0xFF: none)
-__constant__ unsigned char kQRelease[6][2] = {{0xFF, 0xFF}, {0xFF, 0xFF}, {0xFF, 0xFF},
-                                              {0, 4},       {2, 3},       {1, 5}};
-
-__global__ void __launch_bounds__(kThreads, 1)
-tc_q6_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcArgs args) {
-  extern __shared__ unsigned char smem_raw[];
-  const uint32_t raw = smem_u32(smem_raw);
-  unsigned char* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-  const uint32_t sbase = smem_u32(smem);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kQSlots * kQTile);
-  // bars: [0, 12) full, [12, 24) empty, 24 + {0, 1} acc full, 26 + {0, 1} acc empty
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kQSlots + 4);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  auto full_bar = [&](int s) { return smem_u32(bars + s); };
-  auto empty_bar = [&](int s) { return smem_u32(bars + kQSlots + s); };
-  auto accf_bar = [&](int b) { return smem_u32(bars + 2 * kQSlots + b); };
-  auto acce_bar = [&](int b) { return smem_u32(bars + 2 * kQSlots + 2 + b); };
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kQSlots; ++s) {
-      mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(accf_bar(b), 1);
-      mbar_init(acce_bar(b), 4);
-    }
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    tmem_alloc(smem_u32(tmem_slot), 512);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem_d = *tmem_slot;
-  const int n_nt = (args.n_cols + kQBN - 1) / kQBN;
-  const int n_mt = (args.n_rows + BM - 1) / BM;
-  const int n_tiles = n_nt * n_mt;
-  const int KB = args.kblocks;
-
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer ----------------
-    // the ring holds two K blocks: K block number gkb uses slots
-    // 6 (gkb & 1) .. + 5, in round gkb >> 1
-    int gkb = 0;
-    int last_round[kQSlots];
-#pragma unroll
-    for (int s = 0; s < kQSlots; ++s) last_round[s] = -1;
-    for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
-      const int m0 = (tile / n_nt) * BM, n0 = (tile % n_nt) * kQBN;
-      for (int kb = 0; kb < KB && !*abort_flag; ++kb, ++gkb) {
-        const int sbase6 = (gkb & 1) * 6;
-        const int round = gkb >> 1;
-#pragma unroll 1
-        for (int t = 0; t < 6; ++t) {
-          const int slot = sbase6 + t;
-          if (round > 0 && !mbar_wait(empty_bar(slot), (uint32_t)((round - 1) & 1))) {
-            *abort_flag = 1;
-            break;
-          }
-          // ring order nu0, A0, A1, nu1, A2, nu2
-          const bool is_nu = t == 0 || t == 3 || t == 5;
-          const int sl = t == 0 ? 0 : t == 1 ? 0 : t == 2 ? 1 : t == 3 ? 1 : t == 4 ? 2 : 2;
-          const CUtensorMap* map = is_nu ? &maps.x[sl] : &maps.b[sl];
-          mbar_expect_tx(full_bar(slot), kQTile);
-          tma_load_2d(sbase + slot * kQTile, map, kb * BK, is_nu ? m0 : n0, full_bar(slot));
-          last_round[slot] = round;
-        }
-      }
-    }
-    if (*abort_flag) {
-#pragma unroll
-      for (int s = 0; s < kQSlots; ++s)
-        if (last_round[s] >= 0) (void)mbar_wait(full_bar(s), (uint32_t)(last_round[s] & 1));
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer ----------------
-    constexpr uint32_t idesc = idesc_bf16(BM, kQBN);
-    int gkb = 0;
-    int lt = 0;
-    for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x, ++lt) {
-      const int buf = lt & 1;
-      if (lt >= 2 && !mbar_wait(acce_bar(buf), (uint32_t)(((lt >> 1) - 1) & 1))) {
-        *abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
-      for (int kb = 0; kb < KB; ++kb, ++gkb) {
-        const int sbase6 = (gkb & 1) * 6;
-        const uint32_t par = (uint32_t)((gkb >> 1) & 1);
-        for (int p = 0; p < 6; ++p) {
-          const QProd pr = kQProds[p];
-          const int sx = sbase6 + pr.xs, sa = sbase6 + pr.as;
-          if (!mbar_wait(full_bar(sx), par) || !mbar_wait(full_bar(sa), par)) {
-            *abort_flag = 1;
-            break;
-          }
-          tc_fence_after();
-          const uint64_t adesc = smem_desc_sw128(sbase + (uint32_t)sx * kQTile);
-          const uint64_t bdesc = smem_desc_sw128(sbase + (uint32_t)sa * kQTile);
-          const uint32_t acc = tmem_d + (uint32_t)((buf * 2 + pr.acc) * kQBN);
-          const bool fresh = kb == 0 && pr.first;
-#pragma unroll
-          for (int k = 0; k < BK / 16; ++k)
-            umma_bf16(acc, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc,
-                      (fresh && k == 0) ? 0u : 1u);
-#pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            const unsigned char pos = kQRelease[p][r];
-            if (pos != 0xFF) umma_commit(empty_bar(sbase6 + pos));
-          }
-        }
-        if (*abort_flag) break;
-      }
-      umma_commit(accf_bar(buf));
-    }
-  } else if (warp >= 2) {
-    // ---------------- epilogue warps 2..5 ----------------
-    const int quarter = warp & 3;
-    const uint32_t lane_base = tmem_d + ((uint32_t)(quarter * 32) << 16);
-    const bool vec_ok = (args.ldq & 3) == 0 && ((reinterpret_cast<uintptr_t>(args.Q) & 15) == 0);
-    int lt = 0;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++lt) {
-      const int buf = lt & 1;
-      if (*abort_flag || !mbar_wait(accf_bar(buf), (uint32_t)((lt >> 1) & 1))) {
-        *abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
-      const int m0 = (tile / n_nt) * BM, n0 = (tile % n_nt) * kQBN;
-      const int row = m0 + quarter * 32 + lane;
-      const bool row_ok = row < args.n_rows;
-      float* qrow = args.Q + (size_t)(row_ok ? row : 0) * args.ldq;
-#pragma unroll 1
-      for (int c0 = 0; c0 < kQBN; c0 += 32) {
-        uint32_t v0[32], v1[32];
-        tmem_ld_32cols(lane_base + (uint32_t)((buf * 2) * kQBN + c0), v0);
-        tmem_ld_32cols(lane_base + (uint32_t)((buf * 2 + 1) * kQBN + c0), v1);
-        tmem_ld_wait();
-        if (!row_ok) continue;
-        float f[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v0[j]) + __uint_as_float(v1[j]);
-        const int col = n0 + c0;
-        if (vec_ok && col + 32 <= args.n_cols) {
-          float4* dst = reinterpret_cast<float4*>(qrow + col);
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            dst[j] = make_float4(f[4 * j], f[4 * j + 1], f[4 * j + 2], f[4 * j + 3]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (col + j < args.n_cols) qrow[col + j] = f[j];
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acce_bar(buf));
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (threadIdx.x == 0 && *abort_flag) atomicOr(args.status, kStatusTimeout);
-  if (warp == 0) tmem_dealloc(tmem_d, 512);
-}
-
 // Fixed-point slices of the chain states for the exact refresh: per row c,
 // t_c = 2^e with max_j |x_cj| < t_c, and x_cj / t_c = sum_l e_l 2^(-w l) + r,
 // e_l integers in (-2^w, 2^w) stored exactly as bf16.  One warp per row.
@@ -675,22 +494,32 @@ __global__ void slice_rows_kernel(const float* __restrict__ X, int ldx, int rows
   }
 }
 
-// Floating-point 3-way bf16 split of a float matrix: v = s0 + s1 + s2 exactly.
-__global__ void split3_kernel(const float* __restrict__ src, int ld, int rows, int cols,
-                              __nv_bfloat16* __restrict__ s0, __nv_bfloat16* __restrict__ s1,
-                              __nv_bfloat16* __restrict__ s2, int ld_bf) {
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long long)rows * cols) return;
-  const int r = (int)(gid / cols), j = (int)(gid % cols);
-  const float v = src[(size_t)r * ld + j];
-  const __nv_bfloat16 a = __float2bfloat16_rn(v);
-  const float r1 = v - __bfloat162float(a);
-  const __nv_bfloat16 b = __float2bfloat16_rn(r1);
-  const __nv_bfloat16 c = __float2bfloat16_rn(r1 - __bfloat162float(b));
-  const size_t o = (size_t)r * ld_bf + j;
-  s0[o] = a;
-  s1[o] = b;
-  s2[o] = c;
+// Scaled two-way fp16 split of float rows, one warp per row: t = 2^(15 - e)
+// with max_j |v_j| in [2^(e-1), 2^e), so every v_j t lies below 2^15, and
+// v_j t = h0 + h1 + r with h0 = fp16(v_j t), h1 = fp16(v_j t - h0) (the
+// subtraction is exact).  unscale[row] = 1 / t (0 for an all-zero row).
+__global__ void split2_rows_kernel(const float* __restrict__ src, int ld, int rows, int cols,
+                                   __half* __restrict__ h0, __half* __restrict__ h1, int ld_h,
+                                   float* __restrict__ unscale) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const float* v = src + (size_t)row * ld;
+  float mx = 0.f;
+  for (int j = lane; j < cols; j += 32) mx = fmaxf(mx, fabsf(v[j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  int e = 0;
+  if (mx > 0.f) (void)frexpf(mx, &e);
+  const float t = mx > 0.f ? ldexpf(1.f, 15 - e) : 1.f;
+  if (lane == 0) unscale[row] = mx > 0.f ? ldexpf(1.f, e - 15) : 0.f;
+  const size_t o = (size_t)row * ld_h;
+  for (int j = lane; j < cols; j += 32) {
+    const float y = v[j] * t;
+    const __half a = __float2half_rn(y);
+    h0[o + j] = a;
+    h1[o + j] = __float2half_rn(y - __half2float(a));
+  }
 }
 
 // ---- host side ---------------------------------------------------------------
@@ -713,10 +542,11 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D bf16 tensor map over a rows x cols matrix (row stride ld elements),
-// box = box_rows x 64 columns, 128-byte swizzle, zero fill out of bounds.
-cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int cols, int ld,
-                     int box_rows) {
+// 2-D tensor map of 16-bit elements (bf16 or fp16) over a rows x cols matrix
+// (row stride ld elements), box = box_rows x 64 columns, 128-byte swizzle,
+// zero fill out of bounds.
+cudaError_t make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld,
+                     int box_rows, bool bf16 = true) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld * 2) % 16 != 0)
@@ -725,7 +555,8 @@ cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int 
   cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims,
+  CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                  2, const_cast<void*>(base), dims,
                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -784,30 +615,20 @@ int num_sms() {
 
 inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
 
-cudaError_t launch_q6(const TcMaps& maps, const TcArgs& args, int sms, cudaStream_t s) {
-  const size_t smem = (size_t)kQSlots * kQTile + 1024 + 256;
-  cudaError_t e = cudaFuncSetAttribute(tc_q6_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  const int tiles = ((args.n_rows + BM - 1) / BM) * ((args.n_cols + kQBN - 1) / kQBN);
-  tc_q6_kernel<<<std::min(tiles, sms), kThreads, smem, s>>>(maps, args);
-  return cudaGetLastError();
-}
-
 }  // namespace
 
 struct TcGemmPlan {
-  int ld_bf = 0, m = 0, d = 0;
-  // q = A nu (BF16x6): exact 3-way bf16 split of A rounded to float
-  __nv_bfloat16* a3[3] = {nullptr, nullptr, nullptr};
-  CUtensorMap qmaps[6][3];
+  int ld16 = 0, m = 0, d = 0;
+  // q = A nu (FP16x3): scaled 2-way fp16 split of A rounded to float
+  __half* a2[2] = {nullptr, nullptr};
+  float* q_col_scale = nullptr;     // 1 / s_i
+  CUtensorMap qmaps[6][2];
   // exact refresh: fixed-point slices of A (per-row power-of-two scale)
   int w = 7, K = 5;
   __nv_bfloat16* aK = nullptr;      // K slices, m x ld_bf each
   float* col_scale = nullptr;       // s_i
   CUtensorMap rmaps[kMaxSlices];
   double bound_factor = 0.0;        // |p_exact - p| <= bound_factor * s_i * t_c
-  bool q_persistent = false;        // persistent load-once kernel for q (else per-pass tiles)
 };
 
 void tc_gemm_tile_for(int n_chains, int m, int* bn, int* stages) {
@@ -852,39 +673,46 @@ int tc_refresh_slices(int d, int* w_out) {
 cudaError_t tc_gemm_create(TcGemmPlan** plan, const double* A, int m, int d) {
   *plan = nullptr;
   TcGemmPlan* p = new TcGemmPlan();
-  // q GEMM variant: "passes" = one operand-tile pair per pipeline stage,
-  // "ring" = persistent kernel loading each slice tile once per K block
-  const char* qk = std::getenv("ESS_Q_KERNEL");
-  p->q_persistent = qk != nullptr && std::strcmp(qk, "ring") == 0;
   p->m = m;
   p->d = d;
-  p->ld_bf = (d + 7) & ~7;
-  const int ld = p->ld_bf;
+  p->ld16 = (d + 7) & ~7;
+  const int ld = p->ld16;
   auto fail = [&](cudaError_t e) {
     tc_gemm_destroy(p);
     return e;
   };
-  // --- BF16x6 operands: A rounded to float, split into three bf16 slices
-  std::vector<float> A32((size_t)m * d);
-  for (size_t i = 0; i < A32.size(); ++i) A32[i] = (float)A[i];
-  float* dA32 = nullptr;
-  cudaError_t e = cudaMalloc(&dA32, sizeof(float) * A32.size());
-  if (e == cudaSuccess) e = cudaMemcpy(dA32, A32.data(), sizeof(float) * A32.size(), cudaMemcpyHostToDevice);
-  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
-    e = cudaMalloc(&p->a3[k], sizeof(__nv_bfloat16) * (size_t)m * ld);
-    if (e == cudaSuccess) e = cudaMemset(p->a3[k], 0, sizeof(__nv_bfloat16) * (size_t)m * ld);
+  // --- FP16x3 operands: A rounded to float, row i scaled by s_i = 2^(15 - e_i)
+  // (max_j |a_ij| in [2^(e_i - 1), 2^e_i)) and split as a s_i = a0 + a1
+  std::vector<__half> h0((size_t)m * ld, __float2half_rn(0.f)), h1 = h0;
+  std::vector<float> qcs(m);
+  for (int i = 0; i < m; ++i) {
+    float mx = 0.f;
+    for (int j = 0; j < d; ++j) mx = std::fmax(mx, std::fabs((float)A[(size_t)i * d + j]));
+    int ex = 0;
+    if (mx > 0.f) (void)std::frexp(mx, &ex);
+    const float t = mx > 0.f ? std::ldexp(1.f, 15 - ex) : 1.f;
+    qcs[i] = mx > 0.f ? std::ldexp(1.f, ex - 15) : 0.f;
+    for (int j = 0; j < d; ++j) {
+      const float y = (float)A[(size_t)i * d + j] * t;
+      const __half a = __float2half_rn(y);
+      h0[(size_t)i * ld + j] = a;
+      h1[(size_t)i * ld + j] = __float2half_rn(y - __half2float(a));
+    }
   }
-  if (e == cudaSuccess) {
-    split3_kernel<<<grid_for((long long)m * d, 256), 256>>>(dA32, d, m, d, p->a3[0], p->a3[1],
-                                                           p->a3[2], ld);
-    e = cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaMalloc(&p->a2[k], sizeof(__half) * (size_t)m * ld);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->a2[k], (k == 0 ? h0 : h1).data(), sizeof(__half) * (size_t)m * ld,
+                     cudaMemcpyHostToDevice);
   }
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  if (dA32) cudaFree(dA32);
+  if (e == cudaSuccess) e = cudaMalloc(&p->q_col_scale, sizeof(float) * m);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->q_col_scale, qcs.data(), sizeof(float) * m, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(e);
   for (int i = 0; i < 6 && e == cudaSuccess; ++i)
-    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
-      e = make_map(&p->qmaps[i][k], p->a3[k], m, d, ld, kWidths[i]);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+      e = make_map(&p->qmaps[i][k], p->a2[k], m, d, ld, kWidths[i], false);
   if (e != cudaSuccess) return fail(e);
 
   // --- exact refresh operands: fixed-point slices of A in FP64 on the host
@@ -926,8 +754,9 @@ cudaError_t tc_gemm_create(TcGemmPlan** plan, const double* A, int m, int d) {
 
 void tc_gemm_destroy(TcGemmPlan* plan) {
   if (!plan) return;
-  for (int k = 0; k < 3; ++k)
-    if (plan->a3[k]) cudaFree(plan->a3[k]);
+  for (int k = 0; k < 2; ++k)
+    if (plan->a2[k]) cudaFree(plan->a2[k]);
+  if (plan->q_col_scale) cudaFree(plan->q_col_scale);
   if (plan->aK) cudaFree(plan->aK);
   if (plan->col_scale) cudaFree(plan->col_scale);
   delete plan;
@@ -937,45 +766,27 @@ int tc_refresh_num_slices(const TcGemmPlan* plan) { return plan->K; }
 double tc_refresh_bound_factor(const TcGemmPlan* plan) { return plan->bound_factor; }
 const float* tc_refresh_col_scale(const TcGemmPlan* plan) { return plan->col_scale; }
 
-cudaError_t tc_split3(const float* src, int ld, int rows, int cols, __nv_bfloat16* s0,
-                      __nv_bfloat16* s1, __nv_bfloat16* s2, int ld_bf, cudaStream_t s) {
-  const long long n = (long long)rows * cols;
-  if (n == 0) return cudaSuccess;
-  split3_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, ld, rows, cols, s0, s1, s2, ld_bf);
+cudaError_t tc_split2_rows(const float* src, int ld, int rows, int cols, __half* h0, __half* h1,
+                           int ld16, float* unscale, cudaStream_t s) {
+  if (rows == 0) return cudaSuccess;
+  split2_rows_kernel<<<grid_for((long long)rows * 32, 256), 256, 0, s>>>(src, ld, rows, cols, h0,
+                                                                          h1, ld16, unscale);
   return cudaGetLastError();
 }
 
-cudaError_t tc_gemm_q(TcGemmPlan* plan, __nv_bfloat16* const nu[3], int ld_bf, int n_chains,
-                      float* Q, int ldq, int* status, cudaStream_t s) {
+cudaError_t tc_gemm_q(TcGemmPlan* plan, __half* const nu[2], const float* nu_unscale, int ld16,
+                      int n_chains, float* Q, int ldq, int* status, cudaStream_t s) {
   if (!plan) return cudaErrorInvalidValue;
   if (n_chains == 0) return cudaSuccess;
-  if (ld_bf != plan->ld_bf) return cudaErrorInvalidValue;
-  if (plan->q_persistent) {
-    TcMaps maps;
-    std::memset(&maps, 0, sizeof(maps));
-    for (int k = 0; k < 3; ++k) {
-      cudaError_t e = make_map(&maps.x[k], nu[k], n_chains, plan->d, ld_bf, BM);
-      if (e != cudaSuccess) return e;
-      maps.b[k] = plan->qmaps[1][k];  // 128-row boxes
-    }
-    TcArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.n_rows = n_chains;
-    a.n_cols = plan->m;
-    a.kblocks = (plan->d + BK - 1) / BK;
-    a.Q = Q;
-    a.ldq = ldq;
-    a.status = status;
-    return launch_q6(maps, a, num_sms(), s);
-  }
+  if (ld16 != plan->ld16) return cudaErrorInvalidValue;
   int bn = 0;
   tc_gemm_tile_for(n_chains, plan->m, &bn, nullptr);
   int wi = 0;
   while (kWidths[wi] != bn) ++wi;
   TcMaps maps;
   std::memset(&maps, 0, sizeof(maps));
-  for (int k = 0; k < 3; ++k) {
-    cudaError_t e = make_map(&maps.x[k], nu[k], n_chains, plan->d, ld_bf, BM);
+  for (int k = 0; k < 2; ++k) {
+    cudaError_t e = make_map(&maps.x[k], nu[k], n_chains, plan->d, ld16, BM, false);
     if (e != cudaSuccess) return e;
     maps.b[k] = plan->qmaps[wi][k];
   }
@@ -984,19 +795,22 @@ cudaError_t tc_gemm_q(TcGemmPlan* plan, __nv_bfloat16* const nu[3], int ld_bf, i
   a.n_rows = n_chains;
   a.n_cols = plan->m;
   a.kblocks = (plan->d + BK - 1) / BK;
-  // group 0: hi.hi; group 1: the five products of order 2^-8 and 2^-16
-  const unsigned char order[6][3] = {{0, 0, 0}, {2, 0, 1}, {1, 1, 1}, {0, 2, 1}, {1, 0, 1}, {0, 1, 1}};
-  a.npass = 6;
+  // group 0: h0.a0; group 1: h1.a0 and h0.a1 (weight 2^-11 each)
+  const unsigned char order[3][3] = {{0, 0, 0}, {1, 0, 1}, {0, 1, 1}};
+  a.npass = 3;
   a.ngroups = 2;
-  for (int i = 0; i < 6; ++i) {
+  for (int i = 0; i < 3; ++i) {
     a.pass[i].xi = order[i][0];
     a.pass[i].bi = order[i][1];
     a.pass[i].group = order[i][2];
-    a.pass[i].first = (i == 0 || i == 1) ? 1 : 0;
+    a.pass[i].first = i < 2 ? 1 : 0;
     a.pass[i].shift = 0;
   }
   a.Q = Q;
   a.ldq = ldq;
+  a.row_scale = nu_unscale;
+  a.row_const = 1.f / kNuSplitScale;
+  a.col_scale = plan->q_col_scale;
   a.status = status;
   return launch_sum(bn, maps, a, s);
 }
@@ -1007,7 +821,7 @@ cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
                        unsigned long long* drift_bits, int* status, cudaStream_t s) {
   if (!plan) return cudaErrorInvalidValue;
   if (n_chains == 0) return cudaSuccess;
-  const int K = plan->K, ld = plan->ld_bf;
+  const int K = plan->K, ld = plan->ld16;
   slice_rows_kernel<<<grid_for((long long)n_chains * 32, 256), 256, 0, s>>>(
       X, ldx, n_chains, plan->d, plan->w, K, x_slices, ld, slice_stride, row_scale);
   cudaError_t e = cudaGetLastError();

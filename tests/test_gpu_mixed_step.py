@@ -1,4 +1,4 @@
-"""Mixed form: the BF16x6 tensor-core GEMM and the FP32 step vs the FP64 oracle.
+"""Mixed form: the FP16x3 tensor-core GEMM and the FP32 step vs the FP64 oracle.
 
 Bar (stated for the mixed form): interval endpoints and theta within 1e-5 rad
 and zero infeasible iterates.  A chain whose active endpoints are so
@@ -29,20 +29,26 @@ def f32(a):
 
 
 def q_error_bound(A, NU):
-    """Bound on |q - a.nu| per row and chain for the BF16x6 GEMM: both operands
-    are split exactly into three bf16 slices (relative weights 1, 2^-8, 2^-16);
-    the three dropped slice products are each below 2^-24 |a_j nu_j|, plus the
-    FP32 accumulation over K/16 tensor-core steps and the final addition of the
-    two accumulators."""
+    """Bound on |q - a.nu| per row and chain for the FP16x3 GEMM.  Row i of A
+    (rounded to float: 2^-24 relative) is scaled by s_i so that its largest
+    entry lies in [2^14, 2^15), chain c of nu by t_c likewise, and each is split
+    as v = h0 + h1 + r with fp16 h0, h1: |r| <= 2^-22 |v| + 2^-25 (the second
+    term when h1 is subnormal).  The two residuals and the dropped h1.a1
+    product give 12 x 2^-24 relative to |a||nu|; the FP32 accumulation over
+    K/16 tensor-core steps and the final addition of the two accumulators add
+    K/16 + 2.  Unscaled, the subnormal terms are below 2^-38 max|nu_c| per
+    |a_j| and 2^-38 max|a_i| per |nu_j|."""
     absdot = np.abs(NU) @ np.abs(A).T
     k = A.shape[1]
-    return absdot * (12 + k / 16) * 2.0**-24
+    sub = 2.0**-38 * (np.abs(NU).max(axis=1)[:, None] * np.abs(A).sum(axis=1)[None, :]
+                      + np.abs(NU).sum(axis=1)[:, None] * np.abs(A).max(axis=1)[None, :])
+    return absdot * (16 + k / 16) * 2.0**-24 + sub
 
 
 @pytest.mark.parametrize("n,m,d", [(1, 20, 10), (130, 300, 137), (256, 448, 64),
                                    (200, 1000, 333), (128, 2000, 1000), (77, 4100, 50)])
 def test_products_tensor_core_gemm(n, m, d):
-    """q = A nu from the tcgen05 BF16x6 GEMM vs FP64, and p = A x (refresh) vs FP64."""
+    """q = A nu from the tcgen05 FP16x3 GEMM vs FP64, and p = A x (refresh) vs FP64."""
     rng = np.random.default_rng(n * 7 + m)
     A = rng.standard_normal((m, d)) / math.sqrt(d)
     b = np.ones(m)
@@ -55,7 +61,7 @@ def test_products_tensor_core_gemm(n, m, d):
     finally:
         s.close()
     A32 = f32(A)
-    q_ref = NU @ A32.T
+    q_ref = NU.astype(np.float64) @ A32.astype(np.float64).T
     err = np.abs(Q - q_ref)
     bound = q_error_bound(A32, NU)
     assert np.all(err <= bound), float((err / bound).max())
