@@ -275,6 +275,83 @@ ess_status ess_step_noalloc(const double *A, const double *b, int d, int m, cons
                             const double *nu, const double *u, int n_chains, double *X_next,
                             double *theta, int *rejected, void *cuda_stream);
 
+/* ---- Batched problems -------------------------------------------------------
+ * Many independent polytopes {x : A_p x <= b_p} of uneven sizes d_p x m_p,
+ * each with its own chains, advanced together: per step one grouped GEMM for
+ * q = A_p nu over all problems (work items of 64 rows x 64 chains taken from a
+ * device work queue by a persistent grid), one chain-step launch for all
+ * chains, and whole refresh periods replayed from a CUDA graph.  The sampler
+ * of every chain is the one of ess_run (Alg. 1 with the roots of App. B and
+ * the intersection of Alg. 3); the batch only changes how the work is laid
+ * out.  The paper runs one polytope at a time and has no counterpart.
+ *
+ * Packing.  A holds the problems' m_p x d_p row-major matrices one after
+ * another, b their right-hand sides one after another.  Chain states are
+ * packed problem by problem, chain-major: problem p's n_p chains occupy
+ * n_p x d_p consecutive doubles; products P, Q likewise with n_p x m_p.
+ * Chain k of problem p draws from Philox with chain counter k and problem
+ * index p, so its trajectory is the one-problem trajectory with that
+ * problem index.
+ *
+ * Precision.  cfg->precision as for ess_create.  Mixed form: q = A nu with
+ * FP32 fused multiply-adds (d_p <= a few hundred keeps the FP32 dot products
+ * within ~d_p 2^-24 of sum |a||nu|), FP32 step, near-tangent roots, the
+ * refresh of p = A x (every refresh_k steps, in double-float arithmetic on the
+ * FP32 pipe, FP64-class accuracy) and the feasibility residual as in
+ * ess_create.  FP64 form: everything in double.  cfg->sort_threads and
+ * cfg->refresh_mode are ignored.
+ */
+typedef struct ess_batch ess_batch;
+
+/* Copies the n_problems polytopes (host arrays) to the current device.
+ * Errors: ESS_ERR_ARG (n_problems < 1, some d_p or m_p < 1, non-finite A or
+ * b, NULL pointers); ESS_ERR_UNSUPPORTED when the largest problem exceeds the
+ * chain-step kernels (m_p up to 8192, d_p up to the shared-memory limit). */
+ess_status ess_batch_create(int n_problems, const int *d, const int *m, const double *A,
+                            const double *b, const ess_config *cfg, ess_batch **out);
+void ess_batch_destroy(ess_batch *batch);
+
+/* n_iter steps of every chain.
+ *   n_chains  host, n_problems counts (0 allowed).
+ *   X         device, packed chain states (doubles); every state must satisfy
+ *             A_p x <= b_p (FP64 check; ESS_ERR_INFEASIBLE_X0 otherwise);
+ *             overwritten with the final states.
+ *   samples   NULL or device buffer of (n_iter / record_every) records, each
+ *             the packed states after every record_every-th step, in the
+ *             run's precision (float in the mixed form, double in FP64).
+ * Steps t0 .. t0 + n_iter - 1; p = A x is recomputed when t % refresh_k == 0.
+ * Without sample recording and with refresh_k even, full refresh periods run
+ * as CUDA-graph replays.  Synchronous on return.  Reference: Alg. 1. */
+ess_status ess_batch_run(ess_batch *batch, const int *n_chains, double *X, int t0, int n_iter,
+                         uint64_t seed, void *samples, int record_every, void *cuda_stream);
+
+/* One step with caller-supplied draws (packed device arrays): nu like X,
+ * u one uniform per chain; X_next, theta (per chain, may be NULL) and
+ * rejected (per chain, may be NULL) are written.  Synchronous. */
+ess_status ess_batch_step_with_draws(ess_batch *batch, const int *n_chains, const double *X,
+                                     const double *nu, const double *u, double *X_next,
+                                     double *theta, int *rejected, void *cuda_stream);
+
+/* The products the batched step uses (verification): P = A x by the refresh
+ * path (double result) and Q = A nu by the step's grouped GEMM, packed per
+ * problem (n_p x m_p doubles each); either may be NULL.  Synchronous. */
+ess_status ess_batch_products(ess_batch *batch, const int *n_chains, const double *X,
+                              const double *nu, double *P, double *Q, void *cuda_stream);
+
+/* Statistics and per-phase timing as for a single state (timing disables
+ * graph replays, so every phase is timed by events); graphs can be switched
+ * off to compare with plain launches. */
+ess_status ess_batch_get_stats(const ess_batch *batch, ess_stats *out);
+ess_status ess_batch_reset_stats(ess_batch *batch);
+ess_status ess_batch_set_graphs(ess_batch *batch, int enable);
+ess_status ess_batch_set_timing(ess_batch *batch, int enable);
+ess_status ess_batch_get_timing(ess_batch *batch, double *ms, long long *launches, int n_phases);
+ess_status ess_batch_reset_timing(ess_batch *batch);
+/* Sizes of the current chain layout: packed state and product lengths, GEMM
+ * work items, and the graph replays since the last timing reset. */
+ess_status ess_batch_info(const ess_batch *batch, long long *total_x, long long *total_p,
+                          int *n_items, long long *graph_launches);
+
 /* Message describing the last failure of the calling thread ("" if none). */
 const char *ess_last_error(void);
 

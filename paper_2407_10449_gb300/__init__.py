@@ -43,6 +43,10 @@ EXPORTED = ("ess_default_config", "ess_create", "ess_destroy", "ess_limits", "es
             "ess_draw_normals",
             "ess_set_timing", "ess_get_timing", "ess_reset_timing",
             "ess_get_stats", "ess_reset_stats", "ess_whiten", "ess_unwhiten", "ess_step_noalloc",
+            "ess_batch_create", "ess_batch_destroy", "ess_batch_run", "ess_batch_step_with_draws",
+            "ess_batch_products", "ess_batch_get_stats", "ess_batch_reset_stats",
+            "ess_batch_set_graphs", "ess_batch_set_timing", "ess_batch_get_timing",
+            "ess_batch_reset_timing", "ess_batch_info",
             "ess_last_error")
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -122,6 +126,19 @@ def load(build_if_missing: bool = True):
             "ess_unwhiten": ([_dp, _dp, c_int, c_int, _dp, _dp], c_int),
             "ess_step_noalloc": ([_vp, _vp, c_int, c_int, _vp, _vp, _vp, c_int, _vp, _vp, _vp,
                                   _vp], c_int),
+            "ess_batch_create": ([c_int, _vp, _vp, _dp, _dp, ctypes.POINTER(ess_config),
+                                  ctypes.POINTER(_vp)], c_int),
+            "ess_batch_destroy": ([_vp], None),
+            "ess_batch_run": ([_vp, _vp, _vp, c_int, c_int, c_u64, _vp, c_int, _vp], c_int),
+            "ess_batch_step_with_draws": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], c_int),
+            "ess_batch_products": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp], c_int),
+            "ess_batch_get_stats": ([_vp, ctypes.POINTER(ess_stats)], c_int),
+            "ess_batch_reset_stats": ([_vp], c_int),
+            "ess_batch_set_graphs": ([_vp, c_int], c_int),
+            "ess_batch_set_timing": ([_vp, c_int], c_int),
+            "ess_batch_get_timing": ([_vp, _vp, _vp, c_int], c_int),
+            "ess_batch_reset_timing": ([_vp], c_int),
+            "ess_batch_info": ([_vp, _vp, _vp, _vp, _vp], c_int),
             "ess_last_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -299,6 +316,87 @@ def ess_step_noalloc(A, b, X, nu, u, X_next, theta=None, rejected=None, stream=N
                                    _stream_ptr(stream)))
 
 
+def ess_batch_create(As, bs, cfg: ess_config | None = None):
+    """As, bs: sequences of (m_p x d_p) matrices and (m_p,) vectors."""
+    d = np.array([np.shape(a)[1] for a in As], dtype=np.int32)
+    m = np.array([np.shape(a)[0] for a in As], dtype=np.int32)
+    A = _np64(np.concatenate([_np64(a).ravel() for a in As]))
+    b = _np64(np.concatenate([_np64(v).ravel() for v in bs]))
+    st = _vp()
+    _check(load().ess_batch_create(len(As), d.ctypes.data, m.ctypes.data, A.ctypes.data_as(_dp),
+                                   b.ctypes.data_as(_dp),
+                                   ctypes.byref(cfg) if cfg is not None else None,
+                                   ctypes.byref(st)))
+    return st
+
+
+def ess_batch_destroy(batch):
+    load().ess_batch_destroy(batch)
+
+
+def _counts(n_chains):
+    return np.ascontiguousarray(n_chains, dtype=np.int32)
+
+
+def ess_batch_run(batch, n_chains, X, t0, n_iter, seed, samples=None, record_every=0,
+                  stream=None):
+    nc = _counts(n_chains)
+    _check(load().ess_batch_run(batch, nc.ctypes.data, _ptr(X), t0, n_iter, seed, _ptr(samples),
+                                record_every, _stream_ptr(stream)))
+
+
+def ess_batch_step_with_draws(batch, n_chains, X, nu, u, X_next, theta=None, rejected=None,
+                              stream=None):
+    nc = _counts(n_chains)
+    _check(load().ess_batch_step_with_draws(batch, nc.ctypes.data, _ptr(X), _ptr(nu), _ptr(u),
+                                            _ptr(X_next), _ptr(theta), _ptr(rejected),
+                                            _stream_ptr(stream)))
+
+
+def ess_batch_products(batch, n_chains, X, nu, P=None, Q=None, stream=None):
+    nc = _counts(n_chains)
+    _check(load().ess_batch_products(batch, nc.ctypes.data, _ptr(X), _ptr(nu), _ptr(P), _ptr(Q),
+                                     _stream_ptr(stream)))
+
+
+def ess_batch_get_stats(batch) -> dict:
+    s = ess_stats()
+    _check(load().ess_batch_get_stats(batch, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def ess_batch_reset_stats(batch):
+    _check(load().ess_batch_reset_stats(batch))
+
+
+def ess_batch_set_graphs(batch, enable=True):
+    _check(load().ess_batch_set_graphs(batch, 1 if enable else 0))
+
+
+def ess_batch_set_timing(batch, enable=True):
+    _check(load().ess_batch_set_timing(batch, 1 if enable else 0))
+
+
+def ess_batch_get_timing(batch) -> dict:
+    ms = np.zeros(len(PHASES), dtype=np.float64)
+    n = np.zeros(len(PHASES), dtype=np.int64)
+    _check(load().ess_batch_get_timing(batch, ms.ctypes.data, n.ctypes.data, len(PHASES)))
+    return {p: {"ms": float(ms[i]), "launches": int(n[i])} for i, p in enumerate(PHASES)}
+
+
+def ess_batch_reset_timing(batch):
+    _check(load().ess_batch_reset_timing(batch))
+
+
+def ess_batch_info(batch) -> dict:
+    tx, tp, ni, gl = (ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int(),
+                      ctypes.c_longlong())
+    _check(load().ess_batch_info(batch, ctypes.byref(tx), ctypes.byref(tp), ctypes.byref(ni),
+                                 ctypes.byref(gl)))
+    return {"total_x": tx.value, "total_p": tp.value, "n_items": ni.value,
+            "graph_launches": gl.value}
+
+
 def ess_last_error() -> str:
     msg = load().ess_last_error()
     return msg.decode() if msg else ""
@@ -381,3 +479,87 @@ class Sampler:
 
     def reset_stats(self):
         ess_reset_stats(self._state)
+
+
+class BatchSampler:
+    """Owns an ess_batch for the polytopes {x : A_p x <= b_p}; chain states are
+    packed problem by problem (chain-major) in one CUDA float64 tensor."""
+
+    def __init__(self, As, bs, precision=ESS_PREC_FP64, **cfg_overrides):
+        cfg = ess_default_config(precision)
+        for k, v in cfg_overrides.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        self.As = [_np64(a) for a in As]
+        self.bs = [_np64(v) for v in bs]
+        self.d = [a.shape[1] for a in self.As]
+        self.m = [a.shape[0] for a in self.As]
+        self.precision = precision
+        self._batch = ess_batch_create(self.As, self.bs, cfg)
+
+    def close(self):
+        if self._batch is not None:
+            ess_batch_destroy(self._batch)
+            self._batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def batch(self):
+        return self._batch
+
+    @property
+    def sample_dtype(self):
+        import torch
+        return torch.float64 if self.precision == ESS_PREC_FP64 else torch.float32
+
+    def offsets(self, n_chains):
+        """Start of every problem's block in the packed states and products."""
+        xo = np.concatenate([[0], np.cumsum([n * d for n, d in zip(n_chains, self.d)])])
+        po = np.concatenate([[0], np.cumsum([n * m for n, m in zip(n_chains, self.m)])])
+        return xo.astype(np.int64), po.astype(np.int64)
+
+    def pack(self, Xs):
+        import torch
+        return torch.cat([torch.as_tensor(np.asarray(x, dtype=np.float64)).reshape(-1)
+                          for x in Xs]).cuda()
+
+    def unpack(self, flat, n_chains, width="d"):
+        w = self.d if width == "d" else self.m
+        flat = flat.detach().cpu().numpy() if hasattr(flat, "detach") else np.asarray(flat)
+        out, at = [], 0
+        for n, k in zip(n_chains, w):
+            out.append(flat[at:at + n * k].reshape(n, k))
+            at += n * k
+        return out
+
+    def run(self, n_chains, X, n_iter, seed, t0=0, samples=None, record_every=0, stream=None):
+        ess_batch_run(self._batch, n_chains, X, t0, n_iter, seed, samples, record_every, stream)
+        return X
+
+    def step_with_draws(self, n_chains, X, nu, u, stream=None):
+        import torch
+        n = int(np.sum(n_chains))
+        X_next = torch.empty_like(X)
+        theta = torch.empty(n, dtype=torch.float64, device=X.device)
+        rejected = torch.empty(n, dtype=torch.int32, device=X.device)
+        ess_batch_step_with_draws(self._batch, n_chains, X, nu, u, X_next, theta, rejected, stream)
+        return X_next, theta, rejected
+
+    def products(self, n_chains, X, nu, stream=None):
+        import torch
+        tp = int(sum(n * m for n, m in zip(n_chains, self.m)))
+        P = torch.empty(tp, dtype=torch.float64, device=X.device)
+        Q = torch.empty(tp, dtype=torch.float64, device=X.device)
+        ess_batch_products(self._batch, n_chains, X, nu, P, Q, stream)
+        return P, Q
+
+    def stats(self):
+        return ess_batch_get_stats(self._batch)
+
+    def reset_stats(self):
+        ess_batch_reset_stats(self._batch)

@@ -1,0 +1,755 @@
+// ess_batch.cu -- extern "C" entry points of the batched sampler (include/ess.h,
+// "batched problems"): hundreds of independent polytopes of uneven d and m,
+// each with its own chain count, advanced together on one stream.
+//
+// Per step (all problems at once):
+//   [refresh p = A x]  ->  draw nu  ->  q = A nu (grouped GEMM, work queue)
+//   ->  chain step (warp per chain, CTA per chain for overflow chains)
+// The chain of problem p with index k inside p draws from Philox with chain
+// counter k and problem index p, so its trajectory is the one a one-problem
+// run with that problem index produces.  Whole refresh periods (refresh plus
+// refresh_k steps) are captured once in a CUDA graph and replayed, the step
+// index coming from a device counter that the graph advances.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "ess.h"
+#include "ess_kernels.cuh"
+
+void ess_internal_set_error(const std::string& msg);  // ess_abi.cu
+
+using ess::BatchItem;
+using ess::ChainDesc;
+using ess::DevStats;
+
+namespace {
+
+ess_status bfail(ess_status st, const std::string& msg) {
+  ess_internal_set_error(msg);
+  return st;
+}
+
+ess_status bcuda(cudaError_t e, const char* what) {
+  return bfail(e == cudaErrorMemoryAllocation ? ESS_ERR_OOM : ESS_ERR_CUDA,
+               std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define BESS_CUDA(expr)                              \
+  do {                                               \
+    cudaError_t e_ = (expr);                         \
+    if (e_ != cudaSuccess) return bcuda(e_, #expr);  \
+  } while (0)
+
+template <typename T>
+void bfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <typename T>
+cudaError_t balloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return cudaSuccess;
+  return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+struct BDeviceGuard {
+  int prev = -1;
+  explicit BDeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~BDeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct ess_batch {
+  int np = 0;
+  ess_config cfg{};
+  int device = 0;
+  std::vector<int> d, m;
+  std::vector<long long> a_off;  // per problem, into A64 / A32
+  std::vector<int> b_off;        // per problem, into b, anorm, slack
+  int max_d = 0, max_m = 0;
+  int chain_threads = 0;         // CTA kernel width for max_m
+  // constants (device)
+  double* A64 = nullptr;
+  float* A32 = nullptr;          // mixed form: A rounded to float (q GEMM)
+  double* b64 = nullptr;
+  float* b32 = nullptr;
+  double* anorm = nullptr;
+  void* slack = nullptr;         // b - margin ||a||, rounded down in the step's type
+  // current chain layout
+  std::vector<int> nc;
+  int n = 0;
+  long long total_x = 0, total_p = 0;
+  ChainDesc* desc = nullptr;
+  BatchItem* items = nullptr;
+  int n_items = 0;
+  int layout_version = 0;
+  // work buffers (device)
+  int cap_n = 0, cap_items = 0;
+  long long cap_x = 0, cap_p = 0;
+  void* X = nullptr;             // working states (T)
+  void* NU = nullptr;
+  void* P = nullptr;
+  void* P2 = nullptr;
+  void* Q = nullptr;
+  double* P64 = nullptr;
+  int* ovf = nullptr;            // [0] overflow count, [1..] overflow chains
+  int* queue = nullptr;          // work-queue head of the grouped GEMMs
+  unsigned* t_dev = nullptr;     // step index base of replayed graphs
+  DevStats* dstats = nullptr;
+  int* dstatus = nullptr;
+  long long host_steps = 0;
+  // CUDA graphs of one refresh period, keyed by layout, seed and P parity
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  struct GraphEntry {
+    int version;
+    uint64_t seed;
+    void* p_first;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+  long long graph_launches = 0;
+  // optional per-phase timing (direct launches only)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<int, int>>> ev_pending;
+  int ev_used = 0;
+  double phase_ms[ESS_N_PHASES] = {0};
+  long long phase_launches[ESS_N_PHASES] = {0};
+};
+
+namespace {
+
+bool bmixed(const ess_batch* s) { return s->cfg.precision == ESS_PREC_MIXED; }
+size_t belem(const ess_batch* s) { return bmixed(s) ? sizeof(float) : sizeof(double); }
+
+int bmark(ess_batch* s, cudaStream_t st) {
+  if (!s->timing) return -1;
+  if (s->ev_used == (int)s->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    s->ev_pool.push_back(e);
+  }
+  const int i = s->ev_used++;
+  if (cudaEventRecord(s->ev_pool[i], st) != cudaSuccess) return -1;
+  return i;
+}
+
+struct BPhase {
+  ess_batch* s;
+  cudaStream_t st;
+  int phase, start, launches;
+  BPhase(ess_batch* s_, cudaStream_t st_, int phase_, int launches_ = 1)
+      : s(s_), st(st_), phase(phase_), start(bmark(s_, st_)), launches(launches_) {}
+  ~BPhase() {
+    s->phase_launches[phase] += launches;
+    if (start < 0) return;
+    const int stop = bmark(s, st);
+    if (stop >= 0) s->ev_pending.push_back({phase, {start, stop}});
+  }
+};
+
+void bcollect(ess_batch* s) {
+  for (auto& pe : s->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, s->ev_pool[pe.second.first], s->ev_pool[pe.second.second]) ==
+        cudaSuccess)
+      s->phase_ms[pe.first] += ms;
+  }
+  s->ev_pending.clear();
+  s->ev_used = 0;
+}
+
+void drop_graphs(ess_batch* s) {
+  for (auto& g : s->graphs) cudaGraphExecDestroy(g.exec);
+  s->graphs.clear();
+}
+
+void free_work(ess_batch* s) {
+  drop_graphs(s);
+  bfree(s->desc);
+  bfree(s->items);
+  if (s->X) cudaFree(s->X);
+  if (s->NU) cudaFree(s->NU);
+  if (s->P) cudaFree(s->P);
+  if (s->P2) cudaFree(s->P2);
+  if (s->Q) cudaFree(s->Q);
+  s->X = s->NU = s->P = s->P2 = s->Q = nullptr;
+  bfree(s->P64);
+  bfree(s->ovf);
+  s->cap_n = s->cap_items = 0;
+  s->cap_x = s->cap_p = 0;
+  s->nc.clear();
+  s->n = 0;
+}
+
+// Builds the chain views and GEMM work items for chain counts nc and makes
+// sure the work buffers hold them.
+ess_status prepare(ess_batch* s, const int* nc_in) {
+  std::vector<int> nc(nc_in, nc_in + s->np);
+  for (int p = 0; p < s->np; ++p)
+    if (nc[p] < 0) return bfail(ESS_ERR_ARG, "negative chain count");
+  if (nc == s->nc && s->desc) return ESS_OK;
+  std::vector<ChainDesc> desc;
+  std::vector<BatchItem> items;
+  long long xo = 0, po = 0;
+  for (int p = 0; p < s->np; ++p) {
+    const int d = s->d[p], m = s->m[p];
+    for (int k = 0; k < nc[p]; ++k) {
+      ChainDesc cd{};
+      cd.d = d;
+      cd.m = m;
+      cd.chain = (unsigned)k;
+      cd.problem = (unsigned)p;
+      cd.x_off = xo + (long long)k * d;
+      cd.p_off = po + (long long)k * m;
+      cd.a_off = s->a_off[p];
+      cd.b_off = s->b_off[p];
+      desc.push_back(cd);
+    }
+    for (int c0 = 0; c0 < nc[p]; c0 += ess::kBatchTile)
+      for (int r0 = 0; r0 < m; r0 += ess::kBatchTile) {
+        BatchItem it{};
+        it.row0 = r0;
+        it.rows = std::min(ess::kBatchTile, m - r0);
+        it.chains = std::min(ess::kBatchTile, nc[p] - c0);
+        it.d = d;
+        it.m = m;
+        it.b_off = s->b_off[p];
+        it.a_off = s->a_off[p];
+        it.x_off = xo + (long long)c0 * d;
+        it.p_off = po + (long long)c0 * m;
+        items.push_back(it);
+      }
+    xo += (long long)nc[p] * d;
+    po += (long long)nc[p] * m;
+  }
+  // largest items first: the work queue then ends on small items (LPT order)
+  std::stable_sort(items.begin(), items.end(), [](const BatchItem& a, const BatchItem& b) {
+    return (long long)a.rows * a.chains * a.d > (long long)b.rows * b.chains * b.d;
+  });
+  const int n = (int)desc.size();
+  if (n > s->cap_n || xo > s->cap_x || po > s->cap_p || (int)items.size() > s->cap_items) {
+    free_work(s);
+    const size_t e = belem(s);
+    BESS_CUDA(balloc(&s->desc, std::max<size_t>(1, desc.size())));
+    BESS_CUDA(balloc(&s->items, std::max<size_t>(1, items.size())));
+    BESS_CUDA(cudaMalloc(&s->X, std::max<long long>(1, xo) * e));
+    BESS_CUDA(cudaMalloc(&s->NU, std::max<long long>(1, xo) * e));
+    BESS_CUDA(cudaMalloc(&s->P, std::max<long long>(1, po) * e));
+    BESS_CUDA(cudaMalloc(&s->P2, std::max<long long>(1, po) * e));
+    BESS_CUDA(cudaMalloc(&s->Q, std::max<long long>(1, po) * e));
+    BESS_CUDA(balloc(&s->P64, std::max<long long>(1, po)));
+    BESS_CUDA(balloc(&s->ovf, (size_t)n + 1));
+    s->cap_n = n;
+    s->cap_x = xo;
+    s->cap_p = po;
+    s->cap_items = (int)items.size();
+  }
+  if (!desc.empty())
+    BESS_CUDA(cudaMemcpy(s->desc, desc.data(), sizeof(ChainDesc) * desc.size(), cudaMemcpyHostToDevice));
+  if (!items.empty())
+    BESS_CUDA(cudaMemcpy(s->items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
+  drop_graphs(s);
+  s->nc = nc;
+  s->n = n;
+  s->n_items = (int)items.size();
+  s->total_x = xo;
+  s->total_p = po;
+  ++s->layout_version;
+  return ESS_OK;
+}
+
+ess_status bread_status(ess_batch* s, cudaStream_t st) {
+  int h = 0;
+  BESS_CUDA(cudaMemcpyAsync(&h, s->dstatus, sizeof(int), cudaMemcpyDeviceToHost, st));
+  BESS_CUDA(cudaStreamSynchronize(st));
+  if (h & ess::kStatusInfeasible)
+    return bfail(ESS_ERR_INFEASIBLE_X0, "a chain state violates A x <= b (checked in FP64)");
+  if (h & ess::kStatusNumeric)
+    return bfail(ESS_ERR_NUMERIC, "NaN or Inf in theta or x; affected chains kept their state");
+  if (h & ess::kStatusTimeout) return bfail(ESS_ERR_TIMEOUT, "a bounded device wait gave up");
+  return ESS_OK;
+}
+
+// p = A x for every chain (FP64-class), optionally with drift statistics and
+// the FP64 feasibility check of the states.
+template <typename T>
+ess_status brefresh(ess_batch* s, const T* X, bool drift, bool check, cudaStream_t st) {
+  BESS_CUDA(ess::launch_batch_refresh<T>(s->items, s->n_items, s->queue, s->A64, X,
+                                         static_cast<T*>(s->P), check ? s->P64 : nullptr,
+                                         s->anorm, drift ? &s->dstats->max_drift_bits : nullptr,
+                                         st));
+  if (check) BESS_CUDA(ess::launch_batch_check(s->desc, s->n, s->P64, s->b64, s->dstatus, st));
+  return ESS_OK;
+}
+
+template <typename T>
+ess::ChainParams<T> bparams(ess_batch* s) {
+  ess::ChainParams<T> p{};
+  p.d = s->max_d;
+  p.m = s->max_m;
+  p.n_chains = s->n;
+  p.Q = static_cast<const T*>(s->Q);
+  if constexpr (sizeof(T) == 4) p.b = reinterpret_cast<const T*>(s->b32);
+  else p.b = reinterpret_cast<const T*>(s->b64);
+  p.b64 = s->b64;
+  p.A64 = s->A64;
+  p.anorm = s->anorm;
+  p.slack = static_cast<const T*>(s->slack);
+  p.NU = static_cast<const T*>(s->NU);
+  p.X = static_cast<const T*>(s->X);
+  p.X_out = static_cast<T*>(s->X);
+  p.trim_eps = s->cfg.trim_eps;
+  p.tangent_thresh = s->cfg.tangent_thresh;
+  p.margin = s->cfg.residual_margin;
+  p.stats = s->dstats;
+  p.status = s->dstatus;
+  p.desc = s->desc;
+  return p;
+}
+
+// Chain step of every chain: warp kernel, then the CTA kernel for the chains
+// it listed; reads P, writes P2 (the caller swaps them).
+template <typename T>
+ess_status bchain(ess_batch* s, ess::ChainParams<T> p, cudaStream_t st) {
+  p.P_in = static_cast<const T*>(s->P);
+  p.P_out = static_cast<T*>(s->P2);
+  BESS_CUDA(cudaMemsetAsync(s->ovf, 0, sizeof(int), st));
+  p.overflow_count = s->ovf;
+  p.overflow_list = s->ovf + 1;
+  BESS_CUDA(ess::launch_chain_step_warp<T>(p, st));
+  p.chain_list = s->ovf + 1;
+  p.list_count = s->ovf;
+  p.overflow_count = nullptr;
+  p.overflow_list = nullptr;
+  BESS_CUDA(ess::launch_chain_step<T>(p, s->chain_threads, st));
+  return ESS_OK;
+}
+
+// One step (draw, q, chain step) at step index t (+ *t_dev when t_dev is set).
+template <typename T>
+ess_status bstep(ess_batch* s, uint64_t seed, uint32_t t, const unsigned* t_dev, T* samples,
+                 cudaStream_t st) {
+  {
+    BPhase ph(s, st, ESS_PHASE_DRAW);
+    BESS_CUDA(ess::launch_batch_draw<T>(s->desc, s->n, static_cast<T*>(s->NU), seed, t, t_dev, st));
+  }
+  {
+    BPhase ph(s, st, ESS_PHASE_GEMM);
+    const T* A = bmixed(s) ? reinterpret_cast<const T*>(s->A32) : reinterpret_cast<const T*>(s->A64);
+    BESS_CUDA(ess::launch_batch_q<T>(s->items, s->n_items, s->queue, A,
+                                     static_cast<const T*>(s->NU), static_cast<T*>(s->Q), st));
+  }
+  ess::ChainParams<T> p = bparams<T>(s);
+  p.seed = seed;
+  p.t = t;
+  p.t_dev = t_dev;
+  p.samples = samples;
+  BPhase ph(s, st, ESS_PHASE_CHAIN, 2);
+  ess_status rc = bchain<T>(s, p, st);
+  std::swap(s->P, s->P2);
+  return rc;
+}
+
+// Replays (capturing on first use) the graph of one refresh period that
+// starts at a step index held in *t_dev.
+template <typename T>
+ess_status bgraph_period(ess_batch* s, uint64_t seed, cudaStream_t st) {
+  const int k = s->cfg.refresh_k;
+  ess_batch::GraphEntry* hit = nullptr;
+  for (auto& g : s->graphs)
+    if (g.version == s->layout_version && g.seed == seed && g.p_first == s->P) hit = &g;
+  if (!hit) {
+    if (!s->cap_stream) BESS_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+    void* p_first = s->P;
+    const bool timing = s->timing;
+    s->timing = false;
+    BESS_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    ess_status rc = brefresh<T>(s, static_cast<const T*>(s->X), true, false, s->cap_stream);
+    for (int j = 0; j < k && rc == ESS_OK; ++j)
+      rc = bstep<T>(s, seed, (uint32_t)j, s->t_dev, nullptr, s->cap_stream);
+    if (rc == ESS_OK) {
+      cudaError_t e = ess::launch_advance_t(s->t_dev, (unsigned)k, s->cap_stream);
+      if (e != cudaSuccess) rc = bcuda(e, "advance step index");
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(s->cap_stream, &graph);
+    s->timing = timing;
+    if (rc != ESS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess) return bcuda(ec, "graph capture");
+    cudaGraphExec_t exec = nullptr;
+    ec = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) return bcuda(ec, "graph instantiate");
+    // k is even, so the period leaves P where it found it
+    if (s->P != p_first) std::swap(s->P, s->P2);
+    s->graphs.push_back({s->layout_version, seed, p_first, exec});
+    hit = &s->graphs.back();
+  }
+  BESS_CUDA(cudaGraphLaunch(hit->exec, st));
+  ++s->graph_launches;
+  s->phase_launches[ESS_PHASE_REFRESH] += 1;
+  s->phase_launches[ESS_PHASE_DRAW] += k;
+  s->phase_launches[ESS_PHASE_GEMM] += k;
+  s->phase_launches[ESS_PHASE_CHAIN] += 2 * k;
+  return ESS_OK;
+}
+
+__global__ void set_u32_kernel(unsigned* p, unsigned v) { *p = v; }
+
+template <typename T>
+ess_status brun(ess_batch* s, double* X, int t0, int n_iter, uint64_t seed, void* samples,
+                int record_every, cudaStream_t st) {
+  T* Xw = static_cast<T*>(s->X);
+  BESS_CUDA(cudaMemsetAsync(s->dstatus, 0, sizeof(int), st));
+  BESS_CUDA((ess::launch_convert<double, T>(X, (int)s->total_x, Xw, (int)s->total_x, 1,
+                                            (int)s->total_x, st)));
+  ess_status rc = brefresh<T>(s, Xw, false, true, st);
+  if (rc == ESS_OK) rc = bread_status(s, st);
+  if (rc != ESS_OK) return rc;
+  const int k = s->cfg.refresh_k;
+  const int n_rec = record_every > 0 ? n_iter / record_every : 0;
+  const bool graphs_ok = s->use_graphs && !s->timing && record_every == 0 && k % 2 == 0;
+  int fresh = t0;
+  int it = 0;
+  while (it < n_iter) {
+    const int t = t0 + it;
+    if (graphs_ok && t % k == 0 && t != fresh && n_iter - it >= k) {
+      set_u32_kernel<<<1, 1, 0, st>>>(s->t_dev, (unsigned)t);
+      BESS_CUDA(cudaGetLastError());
+      while (n_iter - it >= k) {
+        rc = bgraph_period<T>(s, seed, st);
+        if (rc != ESS_OK) return rc;
+        it += k;
+      }
+      fresh = t0 + it - k;
+      continue;
+    }
+    if (t % k == 0 && t != fresh) {
+      BPhase ph(s, st, ESS_PHASE_REFRESH);
+      rc = brefresh<T>(s, Xw, true, false, st);
+      if (rc != ESS_OK) return rc;
+      fresh = t;
+    }
+    const bool rec = record_every > 0 && (it + 1) % record_every == 0 &&
+                     (it + 1) / record_every <= n_rec;
+    T* srow = rec ? static_cast<T*>(samples) + (long long)((it + 1) / record_every - 1) * s->total_x
+                  : nullptr;
+    rc = bstep<T>(s, seed, (uint32_t)t, nullptr, srow, st);
+    if (rc != ESS_OK) return rc;
+    ++it;
+  }
+  BESS_CUDA((ess::launch_convert<T, double>(Xw, (int)s->total_x, X, (int)s->total_x, 1,
+                                            (int)s->total_x, st)));
+  s->host_steps += (long long)s->n * n_iter;
+  rc = bread_status(s, st);
+  bcollect(s);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+ess_status ess_batch_create(int n_problems, const int* d, const int* m, const double* A,
+                            const double* b, const ess_config* cfg, ess_batch** out) {
+  ess_internal_set_error("");
+  if (!out) return bfail(ESS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_problems < 1 || !d || !m || !A || !b) return bfail(ESS_ERR_ARG, "bad argument");
+  ess_config c;
+  if (cfg) c = *cfg;
+  else ess_default_config(ESS_PREC_FP64, &c);
+  if (c.precision != ESS_PREC_FP64 && c.precision != ESS_PREC_MIXED)
+    return bfail(ESS_ERR_ARG, "unknown precision");
+  if (c.refresh_k < 1) return bfail(ESS_ERR_ARG, "refresh_k must be >= 1");
+  if (!(c.trim_eps >= 0.0) || !(c.tangent_thresh >= 0.0) || !(c.residual_margin >= 0.0))
+    return bfail(ESS_ERR_ARG, "negative tolerance");
+  ess_batch* s = new ess_batch();
+  s->np = n_problems;
+  s->cfg = c;
+  cudaGetDevice(&s->device);
+  long long ta = 0;
+  int tb = 0;
+  for (int p = 0; p < n_problems; ++p) {
+    if (d[p] < 1 || m[p] < 1) {
+      delete s;
+      return bfail(ESS_ERR_ARG, "need d >= 1 and m >= 1 for every problem");
+    }
+    s->d.push_back(d[p]);
+    s->m.push_back(m[p]);
+    s->a_off.push_back(ta);
+    s->b_off.push_back(tb);
+    ta += (long long)m[p] * d[p];
+    tb += m[p];
+    s->max_d = std::max(s->max_d, d[p]);
+    s->max_m = std::max(s->max_m, m[p]);
+  }
+  for (long long i = 0; i < ta; ++i)
+    if (!std::isfinite(A[i])) {
+      delete s;
+      return bfail(ESS_ERR_ARG, "A has a non-finite entry");
+    }
+  for (int i = 0; i < tb; ++i)
+    if (!std::isfinite(b[i])) {
+      delete s;
+      return bfail(ESS_ERR_ARG, "b has a non-finite entry");
+    }
+  s->chain_threads = ess::chain_threads_for(s->max_m);
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+  const size_t need = bmixed(s) ? ess::chain_smem_bytes<float>(s->chain_threads, s->max_d)
+                                : ess::chain_smem_bytes<double>(s->chain_threads, s->max_d);
+  if (s->chain_threads == 0 || (long long)need > (long long)smem_optin - 1024) {
+    delete s;
+    return bfail(ESS_ERR_UNSUPPORTED, "a problem is larger than the chain-step kernels support");
+  }
+  auto cleanup = [&](cudaError_t e) {
+    ess_batch_destroy(s);
+    return bcuda(e, "ess_batch_create device setup");
+  };
+  BDeviceGuard g(s->device);
+  std::vector<double> norms(tb);
+  for (int p = 0; p < n_problems; ++p)
+    for (int i = 0; i < m[p]; ++i) {
+      const double* a = A + s->a_off[p] + (long long)i * d[p];
+      double acc = 0.0;
+      for (int j = 0; j < d[p]; ++j) acc += a[j] * a[j];
+      norms[s->b_off[p] + i] = std::sqrt(acc);
+    }
+  const size_t esz = belem(s);
+  std::vector<unsigned char> sl(esz * tb);
+  for (int i = 0; i < tb; ++i) {
+    const double v = b[i] - c.residual_margin * norms[i];
+    if (bmixed(s)) {
+      float f = (float)v;
+      if ((double)f > v) f = std::nextafter(f, -INFINITY);
+      std::memcpy(&sl[esz * i], &f, esz);
+    } else {
+      std::memcpy(&sl[esz * i], &v, esz);
+    }
+  }
+  cudaError_t e = balloc(&s->A64, (size_t)ta);
+  if (e == cudaSuccess) e = cudaMemcpy(s->A64, A, sizeof(double) * ta, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = balloc(&s->b64, (size_t)tb);
+  if (e == cudaSuccess) e = cudaMemcpy(s->b64, b, sizeof(double) * tb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = balloc(&s->anorm, (size_t)tb);
+  if (e == cudaSuccess) e = cudaMemcpy(s->anorm, norms.data(), sizeof(double) * tb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&s->slack, esz * tb);
+  if (e == cudaSuccess) e = cudaMemcpy(s->slack, sl.data(), esz * tb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && bmixed(s)) {
+    std::vector<float> a32(ta), b32(tb);
+    for (long long i = 0; i < ta; ++i) a32[i] = (float)A[i];
+    for (int i = 0; i < tb; ++i) b32[i] = (float)b[i];
+    e = balloc(&s->A32, (size_t)ta);
+    if (e == cudaSuccess) e = cudaMemcpy(s->A32, a32.data(), sizeof(float) * ta, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = balloc(&s->b32, (size_t)tb);
+    if (e == cudaSuccess) e = cudaMemcpy(s->b32, b32.data(), sizeof(float) * tb, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = balloc(&s->queue, 1);
+  if (e == cudaSuccess) e = balloc(&s->t_dev, 1);
+  if (e == cudaSuccess) e = balloc(&s->dstats, 1);
+  if (e == cudaSuccess) e = balloc(&s->dstatus, 1);
+  if (e == cudaSuccess) e = cudaMemset(s->dstats, 0, sizeof(DevStats));
+  if (e == cudaSuccess) e = cudaMemset(s->dstatus, 0, sizeof(int));
+  if (e != cudaSuccess) return cleanup(e);
+  *out = s;
+  return ESS_OK;
+}
+
+void ess_batch_destroy(ess_batch* s) {
+  if (!s) return;
+  BDeviceGuard g(s->device);
+  free_work(s);
+  bfree(s->A64);
+  bfree(s->A32);
+  bfree(s->b64);
+  bfree(s->b32);
+  bfree(s->anorm);
+  if (s->slack) cudaFree(s->slack);
+  bfree(s->queue);
+  bfree(s->t_dev);
+  bfree(s->dstats);
+  bfree(s->dstatus);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  delete s;
+}
+
+ess_status ess_batch_run(ess_batch* s, const int* n_chains, double* X, int t0, int n_iter,
+                         uint64_t seed, void* samples, int record_every, void* cuda_stream) {
+  ess_internal_set_error("");
+  if (!s || !n_chains) return bfail(ESS_ERR_ARG, "NULL argument");
+  if (n_iter < 0 || t0 < 0 || record_every < 0) return bfail(ESS_ERR_ARG, "negative size");
+  if ((long long)t0 + n_iter > 0x7fffffffLL) return bfail(ESS_ERR_ARG, "step index overflow");
+  if (record_every > 0 && !samples) return bfail(ESS_ERR_ARG, "samples is NULL");
+  BDeviceGuard g(s->device);
+  ess_status rc = prepare(s, n_chains);
+  if (rc != ESS_OK) return rc;
+  if (s->n == 0) return ESS_OK;
+  if (!X) return bfail(ESS_ERR_ARG, "X is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  return bmixed(s) ? brun<float>(s, X, t0, n_iter, seed, samples, record_every, st)
+                   : brun<double>(s, X, t0, n_iter, seed, samples, record_every, st);
+}
+
+ess_status ess_batch_step_with_draws(ess_batch* s, const int* n_chains, const double* X,
+                                     const double* nu, const double* u, double* X_next,
+                                     double* theta, int* rejected, void* cuda_stream) {
+  ess_internal_set_error("");
+  if (!s || !n_chains) return bfail(ESS_ERR_ARG, "NULL argument");
+  BDeviceGuard g(s->device);
+  ess_status rc = prepare(s, n_chains);
+  if (rc != ESS_OK) return rc;
+  if (s->n == 0) return ESS_OK;
+  if (!X || !nu || !u || !X_next) return bfail(ESS_ERR_ARG, "NULL input");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  BESS_CUDA(cudaMemsetAsync(s->dstatus, 0, sizeof(int), st));
+  const int tx = (int)s->total_x;
+  auto one = [&](auto tag) -> ess_status {
+    using T = decltype(tag);
+    T* Xw = static_cast<T*>(s->X);
+    BESS_CUDA((ess::launch_convert<double, T>(X, tx, Xw, tx, 1, tx, st)));
+    BESS_CUDA((ess::launch_convert<double, T>(nu, tx, static_cast<T*>(s->NU), tx, 1, tx, st)));
+    ess_status r = brefresh<T>(s, Xw, false, true, st);
+    if (r == ESS_OK) r = bread_status(s, st);
+    if (r != ESS_OK) return r;
+    const T* A = bmixed(s) ? reinterpret_cast<const T*>(s->A32) : reinterpret_cast<const T*>(s->A64);
+    BESS_CUDA(ess::launch_batch_q<T>(s->items, s->n_items, s->queue, A,
+                                     static_cast<const T*>(s->NU), static_cast<T*>(s->Q), st));
+    ess::ChainParams<T> p = bparams<T>(s);
+    p.U = u;
+    p.theta_out = theta;
+    p.rejected_out = rejected;
+    r = bchain<T>(s, p, st);
+    std::swap(s->P, s->P2);
+    if (r != ESS_OK) return r;
+    BESS_CUDA((ess::launch_convert<T, double>(Xw, tx, X_next, tx, 1, tx, st)));
+    s->host_steps += s->n;
+    return bread_status(s, st);
+  };
+  return bmixed(s) ? one(float{}) : one(double{});
+}
+
+ess_status ess_batch_products(ess_batch* s, const int* n_chains, const double* X,
+                              const double* nu, double* P, double* Q, void* cuda_stream) {
+  ess_internal_set_error("");
+  if (!s || !n_chains) return bfail(ESS_ERR_ARG, "NULL argument");
+  BDeviceGuard g(s->device);
+  ess_status rc = prepare(s, n_chains);
+  if (rc != ESS_OK) return rc;
+  if (s->n == 0) return ESS_OK;
+  if ((P && !X) || (Q && !nu)) return bfail(ESS_ERR_ARG, "NULL input");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int tx = (int)s->total_x, tp = (int)s->total_p;
+  auto one = [&](auto tag) -> ess_status {
+    using T = decltype(tag);
+    if (P) {
+      BESS_CUDA((ess::launch_convert<double, T>(X, tx, static_cast<T*>(s->X), tx, 1, tx, st)));
+      BESS_CUDA(ess::launch_batch_refresh<T>(s->items, s->n_items, s->queue, s->A64,
+                                             static_cast<const T*>(s->X), nullptr, P, s->anorm,
+                                             nullptr, st));
+    }
+    if (Q) {
+      BESS_CUDA((ess::launch_convert<double, T>(nu, tx, static_cast<T*>(s->NU), tx, 1, tx, st)));
+      const T* A = bmixed(s) ? reinterpret_cast<const T*>(s->A32) : reinterpret_cast<const T*>(s->A64);
+      BESS_CUDA(ess::launch_batch_q<T>(s->items, s->n_items, s->queue, A,
+                                       static_cast<const T*>(s->NU), static_cast<T*>(s->Q), st));
+      BESS_CUDA((ess::launch_convert<T, double>(static_cast<const T*>(s->Q), tp, Q, tp, 1, tp, st)));
+    }
+    BESS_CUDA(cudaStreamSynchronize(st));
+    return ESS_OK;
+  };
+  return bmixed(s) ? one(float{}) : one(double{});
+}
+
+ess_status ess_batch_get_stats(const ess_batch* s, ess_stats* out) {
+  if (!s || !out) return bfail(ESS_ERR_ARG, "NULL argument");
+  BDeviceGuard g(s->device);
+  DevStats h{};
+  BESS_CUDA(cudaMemcpy(&h, s->dstats, sizeof(h), cudaMemcpyDeviceToHost));
+  std::memset(out, 0, sizeof(*out));
+  out->steps = s->host_steps;
+  out->rejections = (long long)h.rejections;
+  out->residual_rechecks = (long long)h.rechecks;
+  out->tangent_fp64 = (long long)h.tangent_fp64;
+  out->numeric_errors = (long long)h.numeric_errors;
+  out->sort_keys = (long long)h.sort_keys;
+  double drift = 0.0;
+  std::memcpy(&drift, &h.max_drift_bits, sizeof(double));
+  out->max_refresh_drift = drift;
+  out->max_residual = h.max_residual_bits ? ess::dec_ordered(h.max_residual_bits) : -INFINITY;
+  return ESS_OK;
+}
+
+ess_status ess_batch_reset_stats(ess_batch* s) {
+  if (!s) return bfail(ESS_ERR_ARG, "NULL argument");
+  BDeviceGuard g(s->device);
+  BESS_CUDA(cudaMemset(s->dstats, 0, sizeof(DevStats)));
+  s->host_steps = 0;
+  return ESS_OK;
+}
+
+ess_status ess_batch_set_graphs(ess_batch* s, int enable) {
+  if (!s) return bfail(ESS_ERR_ARG, "NULL argument");
+  s->use_graphs = enable != 0;
+  return ESS_OK;
+}
+
+ess_status ess_batch_set_timing(ess_batch* s, int enable) {
+  if (!s) return bfail(ESS_ERR_ARG, "NULL argument");
+  s->timing = enable != 0;
+  return ESS_OK;
+}
+
+ess_status ess_batch_get_timing(ess_batch* s, double* ms, long long* launches, int n_phases) {
+  if (!s || n_phases < 0) return bfail(ESS_ERR_ARG, "bad argument");
+  BDeviceGuard g(s->device);
+  BESS_CUDA(cudaDeviceSynchronize());
+  bcollect(s);
+  for (int i = 0; i < n_phases && i < ESS_N_PHASES; ++i) {
+    if (ms) ms[i] = s->phase_ms[i];
+    if (launches) launches[i] = s->phase_launches[i];
+  }
+  return ESS_OK;
+}
+
+ess_status ess_batch_reset_timing(ess_batch* s) {
+  if (!s) return bfail(ESS_ERR_ARG, "NULL argument");
+  BDeviceGuard g(s->device);
+  BESS_CUDA(cudaDeviceSynchronize());
+  bcollect(s);
+  for (int i = 0; i < ESS_N_PHASES; ++i) {
+    s->phase_ms[i] = 0.0;
+    s->phase_launches[i] = 0;
+  }
+  s->graph_launches = 0;
+  return ESS_OK;
+}
+
+ess_status ess_batch_info(const ess_batch* s, long long* total_x, long long* total_p,
+                          int* n_items, long long* graph_launches) {
+  if (!s) return bfail(ESS_ERR_ARG, "NULL argument");
+  if (total_x) *total_x = s->total_x;
+  if (total_p) *total_p = s->total_p;
+  if (n_items) *n_items = s->n_items;
+  if (graph_launches) *graph_launches = s->graph_launches;
+  return ESS_OK;
+}
+
+}  // extern "C"

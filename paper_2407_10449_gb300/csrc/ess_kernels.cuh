@@ -52,6 +52,18 @@ cudaError_t launch_check_feasible_bounded(const double* P, int ldp, const double
                                           int d, int* status, cudaStream_t s);
 
 // ------------------------------------------------------------ chain step ---
+// One chain of a packed batch of problems (uneven d, m and chain counts).
+struct ChainDesc {
+  int d, m;             // the chain's problem size
+  unsigned chain;       // Philox chain counter: the chain's index within its problem
+  unsigned problem;     // Philox problem index
+  long long x_off;      // element offset of the chain's row in X, X_out, NU, samples
+  long long p_off;      // element offset of the chain's row in P_in, P_out, Q
+  long long a_off;      // element offset of the problem's A64 (m x d, row-major)
+  int b_off;            // element offset of the problem's b, b64, anorm, slack
+  int pad_;
+};
+
 template <typename T>
 struct ChainParams {
   int d, m, n_chains;
@@ -88,7 +100,73 @@ struct ChainParams {
   // warp kernel: chains with too many arcs to sort in a warp are appended here
   int* overflow_list;
   int* overflow_count;
+  // batch mode: per-chain problem views (d, m above are then the maxima and
+  // ldx, ldp, chain0, problem, sample_stride are unused)
+  const ChainDesc* desc;
+  // if set, the step index is t + *t_dev (replayable CUDA graphs)
+  const unsigned* t_dev;
 };
+
+// The rows of one chain as a kernel sees them.
+template <typename T>
+struct ChainView {
+  int d, m;
+  const T* P;            // p (m)
+  const T* Q;            // q (m)
+  T* P_out;
+  const T* X;            // x (d)
+  const T* NU;           // nu (d)
+  T* X_out;
+  T* S;                  // sample row or nullptr
+  const T* b;            // problem rows (m each)
+  const double* b64;
+  const double* anorm;
+  const T* slack;
+  const double* A64;     // m x d
+  unsigned chain, problem, t;
+};
+
+template <typename T, bool BATCH>
+__device__ __forceinline__ ChainView<T> chain_view(const ChainParams<T>& prm, int c) {
+  ChainView<T> v;
+  size_t xo, po;
+  if constexpr (BATCH) {
+    const ChainDesc cd = prm.desc[c];
+    v.d = cd.d;
+    v.m = cd.m;
+    xo = (size_t)cd.x_off;
+    po = (size_t)cd.p_off;
+    v.b = prm.b + cd.b_off;
+    v.b64 = prm.b64 + cd.b_off;
+    v.anorm = prm.anorm + cd.b_off;
+    v.slack = prm.slack ? prm.slack + cd.b_off : nullptr;
+    v.A64 = prm.A64 + cd.a_off;
+    v.chain = cd.chain;
+    v.problem = cd.problem;
+    v.S = prm.samples ? prm.samples + xo : nullptr;
+  } else {
+    v.d = prm.d;
+    v.m = prm.m;
+    xo = (size_t)c * prm.ldx;
+    po = (size_t)c * prm.ldp;
+    v.b = prm.b;
+    v.b64 = prm.b64;
+    v.anorm = prm.anorm;
+    v.slack = prm.slack;
+    v.A64 = prm.A64;
+    v.chain = prm.chain0 + (unsigned)c;
+    v.problem = prm.problem;
+    v.S = prm.samples ? prm.samples + (size_t)c * prm.sample_stride : nullptr;
+  }
+  v.P = prm.P_in + po;
+  v.Q = prm.Q + po;
+  v.P_out = prm.P_out + po;
+  v.X = prm.X + xo;
+  v.NU = prm.NU + xo;
+  v.X_out = prm.X_out + xo;
+  v.t = prm.t + (prm.t_dev ? *prm.t_dev : 0u);
+  return v;
+}
 
 template <typename T>
 cudaError_t launch_chain_step(const ChainParams<T>& p, int threads, cudaStream_t s);
@@ -102,6 +180,40 @@ cudaError_t launch_chain_step_warp(const ChainParams<T>& p, cudaStream_t s);
 template <typename T>
 size_t chain_warp_smem_bytes(int m);
 constexpr int kWarpSortCap = 128;
+
+// ---------------------------------------------------------------- batch ---
+// A work item of the grouped GEMMs: rows row0 .. row0 + rows - 1 of one
+// problem's A times `chains` consecutive chains of that problem.
+struct BatchItem {
+  int row0, rows, chains;
+  int d, m;
+  int b_off;           // element offset of the problem's b / anorm
+  long long a_off;     // element offset of the problem's A (row 0)
+  long long x_off;     // element offset of the first chain's row in X / NU
+  long long p_off;     // element offset of the first chain's row in P / Q
+};
+constexpr int kBatchTile = 64;  // rows and chains per item
+
+// nu for every chain of the batch (T = float: float Box-Muller, T = double:
+// 53-bit), written at desc[c].x_off; the step index is t (+ *t_dev if set).
+template <typename T>
+cudaError_t launch_batch_draw(const ChainDesc* desc, int n_chains, T* NU, uint64_t seed,
+                              uint32_t t, const unsigned* t_dev, cudaStream_t s);
+// Q = A nu per item, in T; queue: one int of scratch (reset by the launcher).
+template <typename T>
+cudaError_t launch_batch_q(const BatchItem* items, int n_items, int* queue, const T* A,
+                           const T* NU, T* Q, cudaStream_t s);
+// P = A64 X with FP64-class accuracy (see k_batch.cu); P64 and drift optional.
+template <typename T>
+cudaError_t launch_batch_refresh(const BatchItem* items, int n_items, int* queue,
+                                 const double* A64, const T* X, T* P, double* P64,
+                                 const double* anorm, unsigned long long* drift_bits,
+                                 cudaStream_t s);
+// status |= kStatusInfeasible if any P64 row entry exceeds b.
+cudaError_t launch_batch_check(const ChainDesc* desc, int n_chains, const double* P64,
+                               const double* b64, int* status, cudaStream_t s);
+// *t_dev += by (advances the step index of a replayed CUDA graph).
+cudaError_t launch_advance_t(unsigned* t_dev, unsigned by, cudaStream_t s);
 
 // Threads per chain the chain-step kernel uses for m constraints (0 if m is
 // beyond the supported maximum), and the dynamic shared memory it needs.

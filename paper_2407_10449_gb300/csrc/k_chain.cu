@@ -81,7 +81,7 @@ __device__ __forceinline__ int pad_idx(int e) { return e + (e >> 5); }
 
 constexpr int kBuckets = 64;  // alpha buckets of the domination prune
 
-template <typename T, int NT, int ITEMS>
+template <typename T, int NT, int ITEMS, bool BATCH>
 __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_kernel(ChainParams<T> prm) {
   constexpr int NSLOT = NT * ITEMS;
   constexpr int NPAD = NSLOT + NSLOT / 32;
@@ -101,7 +101,6 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int m = prm.m, d = prm.d;
   const T two_pi = Lim<T>::two_pi();
   const T inf = Lim<T>::inf();
 
@@ -110,6 +109,8 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
   const int n_work = prm.chain_list ? *prm.list_count : prm.n_chains;
   for (int work = blockIdx.x; work < n_work; work += gridDim.x) {
   const int c = prm.chain_list ? prm.chain_list[work] : work;
+  const ChainView<T> v = chain_view<T, BATCH>(prm, c);
+  const int m = v.m, d = v.d;
   __syncthreads();
   if (tid == 0) {
     s_nflag = 0;
@@ -123,8 +124,8 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
   __syncthreads();
 
   // ---- 1. p, q of every row (kept in registers) and approximate arcs --------
-  const T* Prow = prm.P_in + (size_t)c * prm.ldp;
-  const T* Qrow = prm.Q + (size_t)c * prm.ldp;
+  const T* Prow = v.P;
+  const T* Qrow = v.Q;
   T p[ITEMS], q[ITEMS];
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
     if (i < m) {
       nonfinite |= !isfinite(p[r]) || !isfinite(q[r]);
       bool inf_row = false;
-      cls[r] = classify_row<T>(p[r], q[r], prm.b[i], prm.b64[i], tlo, thi, a_ap[r], b_ap[r],
+      cls[r] = classify_row<T>(p[r], q[r], v.b[i], v.b64[i], tlo, thi, a_ap[r], b_ap[r],
                                inf_row);
       infeasible |= inf_row;
       if (cls[r] == kRowApprox) {
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
     const int i = s_flag[k];
     T al, be;
     bool inf_row = false;
-    const bool has = roots(Prow[i], Qrow[i], prm.b[i], prm.b64[i], prm.tangent_thresh, al, be,
+    const bool has = roots(Prow[i], Qrow[i], v.b[i], v.b64[i], prm.tangent_thresh, al, be,
                            inf_row, tangent);
     infeasible |= inf_row;
     s_key[pad_idx(k)] = has ? al : inf;
@@ -337,8 +338,7 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
   const T total = mid_total + tail_len;
 
   // ---- 4. theta ~ U(I_act): inverse CDF ------------------------------------
-  const double u = prm.U ? prm.U[c]
-                         : theta_uniform(prm.seed, prm.chain0 + (uint32_t)c, prm.t, prm.problem);
+  const double u = prm.U ? prm.U[c] : theta_uniform(prm.seed, v.chain, v.t, v.problem);
   const T s = (T)(u * (double)total);
   int cand = -1;
   T cand_theta = T(0);
@@ -403,8 +403,8 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
     sincosf((float)theta, reinterpret_cast<float*>(&sn), reinterpret_cast<float*>(&cs));
   }
   const bool theta_ok = isfinite(theta);
-  const T* xrow = prm.X + (size_t)c * prm.ldx;
-  const T* nurow = prm.NU + (size_t)c * prm.ldx;
+  const T* xrow = v.X;
+  const T* nurow = v.NU;
   bool bad = !theta_ok || nonfinite;
   for (int j = tid; j < d; j += NT) {
     const T xn = xrow[j] * cs + nurow[j] * sn;
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
     const int i = tid + r * NT;
     pn[r] = p[r] * cs + q[r] * sn;
     if (i < m) {
-      const T slack_bound = prm.slack ? prm.slack[i] : (T)(prm.b64[i] - prm.margin * prm.anorm[i]);
+      const T slack_bound = v.slack ? v.slack[i] : (T)(v.b64[i] - prm.margin * v.anorm[i]);
       if (!(pn[r] <= slack_bound)) {  // within the margin (or NaN)
         const int at = atomicAdd(&s_nflag, 1);
         s_flag[at] = i;
@@ -435,12 +435,12 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
   bool violated = false;
   for (int f = warp; f < nflag; f += NW) {
     const int i = s_flag[f];
-    const double* arow = prm.A64 + (size_t)i * d;
+    const double* arow = v.A64 + (size_t)i * d;
     double acc = 0.0;
     for (int j = lane; j < d; j += 32) acc = fma(arow[j], (double)s_x[j], acc);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    const double res = acc - prm.b64[i];
+    const double res = acc - v.b64[i];
     my_maxres = fmax(my_maxres, res);
     violated |= res > 0.0;
   }
@@ -449,13 +449,13 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
   const bool reject = s_reject != 0 || s_bad != 0;
 
   // ---- 7. write back ------------------------------------------------------
-  T* xout = prm.X_out + (size_t)c * prm.ldx;
+  T* xout = v.X_out;
   if (!reject) {
     for (int j = tid; j < d; j += NT) xout[j] = s_x[j];
   } else if (prm.X_out != prm.X) {
     for (int j = tid; j < d; j += NT) xout[j] = xrow[j];
   }
-  T* prow_out = prm.P_out + (size_t)c * prm.ldp;
+  T* prow_out = v.P_out;
   if (!reject) {
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
@@ -469,8 +469,8 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
       if (i < m) prow_out[i] = p[r];
     }
   }
-  if (prm.samples) {
-    T* srow = prm.samples + (size_t)c * prm.sample_stride;
+  if (v.S) {
+    T* srow = v.S;
     for (int j = tid; j < d; j += NT) srow[j] = reject ? xrow[j] : s_x[j];
   }
 
@@ -526,7 +526,8 @@ cudaError_t launch_chain_step(const ChainParams<T>& p, int threads, cudaStream_t
   if (grid.x == 0) return cudaSuccess;
 #define ESS_CHAIN_CASE(NT)                                                              \
   case NT: {                                                                            \
-    auto k = chain_step_kernel<T, NT, kChainItems>;                                     \
+    auto k = p.desc ? chain_step_kernel<T, NT, kChainItems, true>                       \
+                    : chain_step_kernel<T, NT, kChainItems, false>;                     \
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                          (int)smem);                                    \
     if (e != cudaSuccess) return e;                                                     \

@@ -142,12 +142,11 @@ __device__ __forceinline__ void warp_bitonic(T (&key)[kPer], T (&val)[kPer], int
   }
 }
 
-template <typename T, int WARPS>
+template <typename T, int WARPS, bool BATCH>
 __global__ void __launch_bounds__(WARPS * 32, ESS_WARP_MINBLOCKS)
 chain_warp_kernel(ChainParams<T> prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m = prm.m, d = prm.d;
   // per-warp shared memory: two padded bucket arrays, candidates (code,
   // pseudo-beta), survivor rows
   const size_t per_warp = ((size_t)2 * kWBP + 2 * kCand + kCap) * 4;
@@ -166,8 +165,10 @@ chain_warp_kernel(ChainParams<T> prm) {
   int my_sort_keys = 0;
 
   if (c < prm.n_chains) {
-    const T* Prow = prm.P_in + (size_t)c * prm.ldp;
-    const T* Qrow = prm.Q + (size_t)c * prm.ldp;
+    const ChainView<T> v = chain_view<T, BATCH>(prm, c);
+    const int m = v.m, d = v.d;
+    const T* Prow = v.P;
+    const T* Qrow = v.Q;
     for (int k = lane; k < 2 * kWBP; k += 32) bsub[k] = 0u;  // bsub and bfull
     __syncwarp();
     const T tlo = (T)(1.0 - prm.tangent_thresh);
@@ -190,7 +191,7 @@ chain_warp_kernel(ChainParams<T> prm) {
         if (i >= m_sub) continue;
         float pa = 0.f, pb = 0.f;
         bool inf_row = false;
-        if (classify_phi<T>(pv[k], qv[k], prm.b[i], prm.b64[i], tlo, thi, pa, pb, inf_row) ==
+        if (classify_phi<T>(pv[k], qv[k], v.b[i], v.b64[i], tlo, thi, pa, pb, inf_row) ==
             kRowApprox)
           atomicMax(&bsub[bslot(pbucket(pa))], __float_as_uint(pb));
       }
@@ -221,7 +222,7 @@ chain_warp_kernel(ChainParams<T> prm) {
           float pa = 0.f;
           bool inf_row = false;
           const int cls =
-              classify_phi<T>(pv[k], qv[k], prm.b[i], prm.b64[i], tlo, thi, pa, pb, inf_row);
+              classify_phi<T>(pv[k], qv[k], v.b[i], v.b64[i], tlo, thi, pa, pb, inf_row);
           infeasible |= inf_row;
           if (cls == kRowKeep) {
             cand = true;
@@ -290,7 +291,7 @@ chain_warp_kernel(ChainParams<T> prm) {
           const int i = surv[e];
           T al, be;
           bool inf_row = false;
-          const bool has = roots(Prow[i], Qrow[i], prm.b[i], prm.b64[i], prm.tangent_thresh, al,
+          const bool has = roots(Prow[i], Qrow[i], v.b[i], v.b64[i], prm.tangent_thresh, al,
                                  be, inf_row, tangent);
           infeasible |= inf_row;
           if (has) {
@@ -345,8 +346,7 @@ chain_warp_kernel(ChainParams<T> prm) {
       const T total = mid_total + tail_len;
 
       // ---- theta ~ U(I_act): the last positive piece starting at or below s ----
-      const double u = prm.U ? prm.U[c] : theta_uniform(prm.seed, prm.chain0 + (uint32_t)c,
-                                                         prm.t, prm.problem);
+      const double u = prm.U ? prm.U[c] : theta_uniform(prm.seed, v.chain, v.t, v.problem);
       const T s = (T)(u * (double)total);
       int cand = -1;
       T cand_theta = T(0);
@@ -401,9 +401,9 @@ chain_warp_kernel(ChainParams<T> prm) {
       } else {
         sincosf((float)theta, reinterpret_cast<float*>(&sn), reinterpret_cast<float*>(&cs));
       }
-      const T* xrow = prm.X + (size_t)c * prm.ldx;
-      const T* nurow = prm.NU + (size_t)c * prm.ldx;
-      T* prow_out = prm.P_out + (size_t)c * prm.ldp;
+      const T* xrow = v.X;
+      const T* nurow = v.NU;
+      T* prow_out = v.P_out;
       bool bad = nonfinite || !isfinite(theta);
       bool violated = false;
       int rechecks = 0;
@@ -424,7 +424,7 @@ chain_warp_kernel(ChainParams<T> prm) {
             const T pn = pv[k] * cs + qv[k] * sn;
             prow_out[i] = pn;
             const T slack =
-                prm.slack ? prm.slack[i] : (T)(prm.b64[i] - prm.margin * prm.anorm[i]);
+                v.slack ? v.slack[i] : (T)(v.b64[i] - prm.margin * v.anorm[i]);
             if (!(pn <= slack)) flags |= 1u << k;
           }
         }
@@ -435,7 +435,7 @@ chain_warp_kernel(ChainParams<T> prm) {
           const int src = __ffs(ball) - 1;
           ball &= ball - 1;
           const int row = i0 + src + 32 * k;
-          const double* arow = prm.A64 + (size_t)row * d;
+          const double* arow = v.A64 + (size_t)row * d;
           double acc = 0.0;
           for (int jj = lane; jj < d; jj += 32) {
             const T xn = xrow[jj] * cs + nurow[jj] * sn;
@@ -443,7 +443,7 @@ chain_warp_kernel(ChainParams<T> prm) {
           }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-          const double res = acc - prm.b64[row];
+          const double res = acc - v.b64[row];
           maxres = fmax(maxres, res);
           violated |= res > 0.0;
         }
@@ -452,8 +452,8 @@ chain_warp_kernel(ChainParams<T> prm) {
       // x' is finite whenever theta, x and nu are (x_0 passes an FP64 check)
       const bool reject = __any_sync(kFull, violated || bad);
       bad = __any_sync(kFull, bad);
-      T* xout = prm.X_out + (size_t)c * prm.ldx;
-      T* srow = prm.samples ? prm.samples + (size_t)c * prm.sample_stride : nullptr;
+      T* xout = v.X_out;
+      T* srow = v.S;
       if (!reject) {
         for (int j0 = 0; j0 < d; j0 += 32 * kBatch) {
           T xv[kBatch], nv[kBatch];
@@ -515,7 +515,7 @@ cudaError_t launch_chain_step_warp(const ChainParams<T>& p, cudaStream_t s) {
   if (p.n_chains <= 0) return cudaSuccess;
   if (p.P_out == p.P_in || !p.overflow_list || !p.overflow_count) return cudaErrorInvalidValue;
   const size_t smem = chain_warp_smem_bytes<T>(p.m);
-  auto k = chain_warp_kernel<T, kWarps>;
+  auto k = p.desc ? chain_warp_kernel<T, kWarps, true> : chain_warp_kernel<T, kWarps, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((p.n_chains + kWarps - 1) / kWarps);

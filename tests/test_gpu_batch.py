@@ -1,0 +1,197 @@
+"""Batched problems (ess_batch_*): polytopes of uneven d, m and chain counts
+advanced together, against the FP64 oracle run problem by problem.
+
+The batch only changes the work layout (packed states, grouped GEMM work
+items, per-chain problem views, graph replays); every chain must follow the
+one-problem sampler of Alg. 1 with the problem index in its Philox counter.
+Sizes cross the 64-row and 64-chain work-item tiles and the 16-wide K chunk,
+and include d = 1 and a problem with no chains.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2407_10449_gb300 as ess
+import workloads
+from gpu_helpers import dev, host, oracle_steps, feasible_instance
+
+pytestmark = pytest.mark.gpu
+
+# (d, m, chains)
+SPECS = [(1, 2, 3), (3, 5, 4), (10, 20, 16), (17, 60, 70), (40, 130, 9), (64, 64, 0),
+         (33, 100, 65)]
+
+
+def make_batch(seed, specs=SPECS):
+    rng = np.random.default_rng(seed)
+    As, bs, Xs = [], [], []
+    for d, m, n in specs:
+        A, b, X = feasible_instance(rng, d, m, max(n, 1), scale=1.0 / math.sqrt(d),
+                                    slack=(0.1, 1.0))
+        As.append(A)
+        bs.append(b)
+        Xs.append(X[:n])
+    return As, bs, Xs, [n for _, _, n in specs]
+
+
+def test_batch_fp64_run_reproduces_oracle():
+    """20 steps with refresh_k = 8: direct steps, one graph-replayed period,
+    direct steps again; every problem's chains equal the oracle's."""
+    As, bs, Xs, nc = make_batch(1)
+    bs_ = ess.BatchSampler(As, bs, precision=ess.ESS_PREC_FP64, refresh_k=8)
+    try:
+        X = bs_.pack(Xs)
+        bs_.run(nc, X, 20, seed=9)
+        got = bs_.unpack(X, nc)
+        info = ess.ess_batch_info(bs_.batch)
+        st = bs_.stats()
+    finally:
+        bs_.close()
+    assert info["graph_launches"] == 1
+    for p, (A, b, X0) in enumerate(zip(As, bs, Xs)):
+        if X0.shape[0] == 0:
+            continue
+        want, _, rej = oracle.run(A, b, X0, 20, seed=9, problem=p)
+        np.testing.assert_allclose(got[p], want, rtol=0, atol=1e-8, err_msg=f"problem {p}")
+    assert st["numeric_errors"] == 0
+    assert st["steps"] == sum(nc) * 20
+
+
+@pytest.mark.parametrize("form", [ess.ESS_PREC_FP64, ess.ESS_PREC_MIXED])
+def test_batch_graph_replay_is_bit_identical(form):
+    """Graph replays and plain launches give the same bits."""
+    As, bs, Xs, nc = make_batch(2)
+    out = []
+    for graphs in (True, False):
+        bs_ = ess.BatchSampler(As, bs, precision=form, refresh_k=4)
+        try:
+            ess.ess_batch_set_graphs(bs_.batch, graphs)
+            X = bs_.pack(Xs)
+            bs_.run(nc, X, 22, seed=4, t0=2)
+            out.append(host(X))
+            info = ess.ess_batch_info(bs_.batch)
+        finally:
+            bs_.close()
+        assert info["graph_launches"] == (5 if graphs else 0)
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_batch_fp64_step_with_draws():
+    """One step with given draws: theta within 1e-10 rad, x' within 1e-9
+    relative of the oracle's one-step map, for every chain of every problem."""
+    As, bs, Xs, nc = make_batch(3)
+    rng = np.random.default_rng(5)
+    NUs = [rng.standard_normal(X.shape) for X in Xs]
+    U = rng.uniform(size=sum(nc))
+    bs_ = ess.BatchSampler(As, bs, precision=ess.ESS_PREC_FP64)
+    try:
+        Xn, th, rej = bs_.step_with_draws(nc, bs_.pack(Xs), bs_.pack(NUs), dev(U))
+        Xn = bs_.unpack(Xn, nc)
+        th, rej = host(th), host(rej)
+    finally:
+        bs_.close()
+    at = 0
+    for p, (A, b, X, NU) in enumerate(zip(As, bs, Xs, NUs)):
+        ref = oracle_steps(A, b, X, NU, U[at:at + X.shape[0]])
+        for c, r in enumerate(ref):
+            assert abs(th[at + c] - r.theta) <= 1e-10, (p, c, th[at + c], r.theta)
+            assert bool(rej[at + c]) == r.rejected
+            scale = np.maximum(1.0, np.abs(r.x_next))
+            assert np.all(np.abs(Xn[p][c] - r.x_next) <= 1e-9 * scale), (p, c)
+        at += X.shape[0]
+
+
+def test_batch_mixed_step_with_draws():
+    """Mixed form, one step with given draws: theta within 1e-5 rad of the
+    oracle for all but a few ill-conditioned chains; zero infeasible iterates."""
+    As, bs, Xs, nc = make_batch(6)
+    rng = np.random.default_rng(7)
+    Xs = [np.asarray(X, np.float32).astype(np.float64) for X in Xs]
+    NUs = [np.asarray(rng.standard_normal(X.shape), np.float32).astype(np.float64) for X in Xs]
+    U = rng.uniform(size=sum(nc))
+    bs_ = ess.BatchSampler(As, bs, precision=ess.ESS_PREC_MIXED)
+    try:
+        Xn, th, rej = bs_.step_with_draws(nc, bs_.pack(Xs), bs_.pack(NUs), dev(U))
+        Xn = bs_.unpack(Xn, nc)
+        th = host(th)
+    finally:
+        bs_.close()
+    at, bad, total = 0, 0, 0
+    for p, (A, b, X, NU) in enumerate(zip(As, bs, Xs, NUs)):
+        if X.shape[0]:
+            assert np.max(Xn[p] @ A.T - b) <= 0.0, p
+        ref = oracle_steps(A, b, X, NU, U[at:at + X.shape[0]])
+        for c, r in enumerate(ref):
+            bad += abs(th[at + c] - r.theta) > 1e-5
+            total += 1
+        at += X.shape[0]
+    assert bad <= max(2, 0.02 * total), (bad, total)
+
+
+@pytest.mark.parametrize("form", [ess.ESS_PREC_FP64, ess.ESS_PREC_MIXED])
+def test_batch_products(form):
+    """P = A x (refresh path, FP64-class in both forms) and Q = A nu (FP32
+    FMAs in the mixed form: within d 2^-24 sum |a||nu| plus the float
+    rounding of the inputs)."""
+    As, bs, Xs, nc = make_batch(8)
+    rng = np.random.default_rng(9)
+    NUs = [rng.standard_normal(X.shape) for X in Xs]
+    bs_ = ess.BatchSampler(As, bs, precision=form)
+    try:
+        P, Q = bs_.products(nc, bs_.pack(Xs), bs_.pack(NUs))
+        P, Q = bs_.unpack(P, nc, "m"), bs_.unpack(Q, nc, "m")
+    finally:
+        bs_.close()
+    for p, (A, X, NU) in enumerate(zip(As, Xs, NUs)):
+        if form == ess.ESS_PREC_MIXED:
+            X = np.asarray(X, np.float32).astype(np.float64)
+            NU = np.asarray(NU, np.float32).astype(np.float64)
+            A32 = np.asarray(A, np.float32).astype(np.float64)
+            qtol = (A.shape[1] + 2) * 2.0**-24 * (np.abs(NU) @ np.abs(A32).T)
+            np.testing.assert_array_less(np.abs(Q[p] - NU @ A32.T), qtol + 1e-300)
+        else:
+            np.testing.assert_allclose(Q[p], NU @ A.T, rtol=0,
+                                       atol=1e-13 * (1 + np.abs(NU).sum()))
+        ptol = 1e-12 * (np.abs(X) @ np.abs(A).T) + 1e-300
+        np.testing.assert_array_less(np.abs(P[p] - X @ A.T), ptol)
+
+
+@pytest.mark.parametrize("form", [ess.ESS_PREC_FP64, ess.ESS_PREC_MIXED])
+def test_batch_every_iterate_feasible(form):
+    """The uneven-batch workload (reduced): every recorded iterate of every
+    chain satisfies its polytope in FP64."""
+    import torch
+    insts = workloads.batched(seed=3, n_problems=24, n_iter=40, d_range=(8, 96),
+                              c_range=(1, 40))
+    As = [i.A for i in insts]
+    bs = [i.b for i in insts]
+    nc = [i.X0.shape[0] for i in insts]
+    bs_ = ess.BatchSampler(As, bs, precision=form, refresh_k=8)
+    try:
+        X = bs_.pack([i.X0 for i in insts])
+        tx = X.numel()
+        S = torch.zeros((40, tx), dtype=bs_.sample_dtype, device="cuda")
+        bs_.run(nc, X, 40, seed=2, samples=S, record_every=1)
+        S = host(S).astype(np.float64)
+        st = bs_.stats()
+    finally:
+        bs_.close()
+    for r in range(40):
+        rows = bs_.unpack(S[r], nc)
+        for p, inst in enumerate(insts):
+            assert np.max(rows[p] @ inst.A.T - inst.b) <= 0.0, (r, p)
+    assert st["numeric_errors"] == 0
+
+
+def test_batch_infeasible_start_is_refused():
+    As, bs, Xs, nc = make_batch(10)
+    Xs = [X.copy() for X in Xs]
+    Xs[2][3] = 1e3  # far outside problem 2
+    bs_ = ess.BatchSampler(As, bs, precision=ess.ESS_PREC_MIXED)
+    try:
+        with pytest.raises(ess.EssError):
+            bs_.run(nc, bs_.pack(Xs), 5, seed=0)
+    finally:
+        bs_.close()
