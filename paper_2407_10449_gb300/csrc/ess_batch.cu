@@ -77,11 +77,14 @@ struct ess_batch {
   std::vector<int> d, m;
   std::vector<long long> a_off;  // per problem, into A64 / A32
   std::vector<int> b_off;        // per problem, into b, anorm, slack
+  std::vector<long long> at_off; // per problem, into AT (K-major copy, rows padded to 4)
   int max_d = 0, max_m = 0;
   int chain_threads = 0;         // CTA kernel width for max_m
   // constants (device)
   double* A64 = nullptr;
-  float* A32 = nullptr;          // mixed form: A rounded to float (q GEMM)
+  float* A32 = nullptr;          // mixed form: A rounded to float (q GEMM, refresh hi part)
+  float* Alo = nullptr;          // mixed form: A - A32 rounded to float (refresh lo part)
+  void* AT = nullptr;            // K-major A in the step's type (q GEMM operand)
   double* b64 = nullptr;
   float* b32 = nullptr;
   double* anorm = nullptr;
@@ -218,16 +221,21 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
       cd.b_off = s->b_off[p];
       desc.push_back(cd);
     }
-    for (int c0 = 0; c0 < nc[p]; c0 += ess::kBatchTile)
-      for (int r0 = 0; r0 < m; r0 += ess::kBatchTile) {
+    const int ct = ess::batch_ctile(nc[p]), rt = ess::batch_rtile(ct);
+    for (int c0 = 0; c0 < nc[p]; c0 += ct)
+      for (int r0 = 0; r0 < m; r0 += rt) {
         BatchItem it{};
         it.row0 = r0;
-        it.rows = std::min(ess::kBatchTile, m - r0);
-        it.chains = std::min(ess::kBatchTile, nc[p] - c0);
+        it.rows = std::min(rt, m - r0);
+        it.chains = std::min(ct, nc[p] - c0);
+        it.rtile = rt;
+        it.ctile = ct;
         it.d = d;
         it.m = m;
         it.b_off = s->b_off[p];
         it.a_off = s->a_off[p];
+        it.at_off = s->at_off[p];
+        it.mpad = (m + 3) & ~3;
         it.x_off = xo + (long long)c0 * d;
         it.p_off = po + (long long)c0 * m;
         items.push_back(it);
@@ -283,14 +291,21 @@ ess_status bread_status(ess_batch* s, cudaStream_t st) {
   return ESS_OK;
 }
 
+// The hi part of A the refresh reads (A32 in the mixed form; unused in FP64).
+template <typename T>
+const T* ahi(const ess_batch* s) {
+  if constexpr (sizeof(T) == 4) return s->A32;
+  else return s->A64;
+}
+
 // p = A x for every chain (FP64-class), optionally with drift statistics and
 // the FP64 feasibility check of the states.
 template <typename T>
 ess_status brefresh(ess_batch* s, const T* X, bool drift, bool check, cudaStream_t st) {
-  BESS_CUDA(ess::launch_batch_refresh<T>(s->items, s->n_items, s->queue, s->A64, X,
-                                         static_cast<T*>(s->P), check ? s->P64 : nullptr,
-                                         s->anorm, drift ? &s->dstats->max_drift_bits : nullptr,
-                                         st));
+  BESS_CUDA(ess::launch_batch_refresh<T>(s->items, s->n_items, s->queue, ahi<T>(s), s->A64,
+                                         s->Alo, X, static_cast<T*>(s->P),
+                                         check ? s->P64 : nullptr, s->anorm,
+                                         drift ? &s->dstats->max_drift_bits : nullptr, st));
   if (check) BESS_CUDA(ess::launch_batch_check(s->desc, s->n, s->P64, s->b64, s->dstatus, st));
   return ESS_OK;
 }
@@ -348,8 +363,7 @@ ess_status bstep(ess_batch* s, uint64_t seed, uint32_t t, const unsigned* t_dev,
   }
   {
     BPhase ph(s, st, ESS_PHASE_GEMM);
-    const T* A = bmixed(s) ? reinterpret_cast<const T*>(s->A32) : reinterpret_cast<const T*>(s->A64);
-    BESS_CUDA(ess::launch_batch_q<T>(s->items, s->n_items, s->queue, A,
+    BESS_CUDA(ess::launch_batch_q<T>(s->items, s->n_items, s->queue, static_cast<const T*>(s->AT),
                                      static_cast<const T*>(s->NU), static_cast<T*>(s->Q), st));
   }
   ess::ChainParams<T> p = bparams<T>(s);
@@ -484,7 +498,7 @@ ess_status ess_batch_create(int n_problems, const int* d, const int* m, const do
   s->np = n_problems;
   s->cfg = c;
   cudaGetDevice(&s->device);
-  long long ta = 0;
+  long long ta = 0, tat = 0;
   int tb = 0;
   for (int p = 0; p < n_problems; ++p) {
     if (d[p] < 1 || m[p] < 1) {
@@ -495,6 +509,8 @@ ess_status ess_batch_create(int n_problems, const int* d, const int* m, const do
     s->m.push_back(m[p]);
     s->a_off.push_back(ta);
     s->b_off.push_back(tb);
+    s->at_off.push_back(tat);
+    tat += (long long)d[p] * ((m[p] + 3) & ~3);
     ta += (long long)m[p] * d[p];
     tb += m[p];
     s->max_d = std::max(s->max_d, d[p]);
@@ -553,13 +569,38 @@ ess_status ess_batch_create(int n_problems, const int* d, const int* m, const do
   if (e == cudaSuccess) e = cudaMalloc(&s->slack, esz * tb);
   if (e == cudaSuccess) e = cudaMemcpy(s->slack, sl.data(), esz * tb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && bmixed(s)) {
-    std::vector<float> a32(ta), b32(tb);
-    for (long long i = 0; i < ta; ++i) a32[i] = (float)A[i];
+    std::vector<float> a32(ta), alo(ta), b32(tb);
+    for (long long i = 0; i < ta; ++i) {
+      a32[i] = (float)A[i];
+      alo[i] = (float)(A[i] - (double)a32[i]);
+    }
     for (int i = 0; i < tb; ++i) b32[i] = (float)b[i];
     e = balloc(&s->A32, (size_t)ta);
     if (e == cudaSuccess) e = cudaMemcpy(s->A32, a32.data(), sizeof(float) * ta, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = balloc(&s->Alo, (size_t)ta);
+    if (e == cudaSuccess) e = cudaMemcpy(s->Alo, alo.data(), sizeof(float) * ta, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = balloc(&s->b32, (size_t)tb);
     if (e == cudaSuccess) e = cudaMemcpy(s->b32, b32.data(), sizeof(float) * tb, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) {
+    // K-major copy of every A_p (rows padded to a multiple of 4 with zeros)
+    std::vector<unsigned char> at((size_t)tat * esz, 0);
+    for (int p = 0; p < n_problems; ++p) {
+      const int mp = (m[p] + 3) & ~3;
+      for (int i = 0; i < m[p]; ++i)
+        for (int k = 0; k < d[p]; ++k) {
+          const double v = A[s->a_off[p] + (long long)i * d[p] + k];
+          const size_t o = (size_t)(s->at_off[p] + (long long)k * mp + i);
+          if (bmixed(s)) {
+            const float f = (float)v;
+            std::memcpy(&at[o * esz], &f, esz);
+          } else {
+            std::memcpy(&at[o * esz], &v, esz);
+          }
+        }
+    }
+    e = cudaMalloc(&s->AT, std::max<size_t>(1, at.size()));
+    if (e == cudaSuccess) e = cudaMemcpy(s->AT, at.data(), at.size(), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = balloc(&s->queue, 1);
   if (e == cudaSuccess) e = balloc(&s->t_dev, 1);
@@ -578,6 +619,8 @@ void ess_batch_destroy(ess_batch* s) {
   free_work(s);
   bfree(s->A64);
   bfree(s->A32);
+  bfree(s->Alo);
+  if (s->AT) cudaFree(s->AT);
   bfree(s->b64);
   bfree(s->b32);
   bfree(s->anorm);
@@ -629,8 +672,7 @@ ess_status ess_batch_step_with_draws(ess_batch* s, const int* n_chains, const do
     ess_status r = brefresh<T>(s, Xw, false, true, st);
     if (r == ESS_OK) r = bread_status(s, st);
     if (r != ESS_OK) return r;
-    const T* A = bmixed(s) ? reinterpret_cast<const T*>(s->A32) : reinterpret_cast<const T*>(s->A64);
-    BESS_CUDA(ess::launch_batch_q<T>(s->items, s->n_items, s->queue, A,
+    BESS_CUDA(ess::launch_batch_q<T>(s->items, s->n_items, s->queue, static_cast<const T*>(s->AT),
                                      static_cast<const T*>(s->NU), static_cast<T*>(s->Q), st));
     ess::ChainParams<T> p = bparams<T>(s);
     p.U = u;
@@ -661,14 +703,14 @@ ess_status ess_batch_products(ess_batch* s, const int* n_chains, const double* X
     using T = decltype(tag);
     if (P) {
       BESS_CUDA((ess::launch_convert<double, T>(X, tx, static_cast<T*>(s->X), tx, 1, tx, st)));
-      BESS_CUDA(ess::launch_batch_refresh<T>(s->items, s->n_items, s->queue, s->A64,
-                                             static_cast<const T*>(s->X), nullptr, P, s->anorm,
-                                             nullptr, st));
+      BESS_CUDA(ess::launch_batch_refresh<T>(s->items, s->n_items, s->queue, ahi<T>(s), s->A64,
+                                             s->Alo, static_cast<const T*>(s->X), nullptr, P,
+                                             s->anorm, nullptr, st));
     }
     if (Q) {
       BESS_CUDA((ess::launch_convert<double, T>(nu, tx, static_cast<T*>(s->NU), tx, 1, tx, st)));
-      const T* A = bmixed(s) ? reinterpret_cast<const T*>(s->A32) : reinterpret_cast<const T*>(s->A64);
-      BESS_CUDA(ess::launch_batch_q<T>(s->items, s->n_items, s->queue, A,
+      BESS_CUDA(ess::launch_batch_q<T>(s->items, s->n_items, s->queue,
+                                       static_cast<const T*>(s->AT),
                                        static_cast<const T*>(s->NU), static_cast<T*>(s->Q), st));
       BESS_CUDA((ess::launch_convert<T, double>(static_cast<const T*>(s->Q), tp, Q, tp, 1, tp, st)));
     }

@@ -183,32 +183,43 @@ constexpr int kWarpSortCap = 128;
 
 // ---------------------------------------------------------------- batch ---
 // A work item of the grouped GEMMs: rows row0 .. row0 + rows - 1 of one
-// problem's A times `chains` consecutive chains of that problem.
+// problem's A times `chains` consecutive chains of that problem, computed as
+// an rtile x ctile tile (rows <= rtile, chains <= ctile, rtile ctile = 4096).
 struct BatchItem {
   int row0, rows, chains;
+  int rtile, ctile;
   int d, m;
   int b_off;           // element offset of the problem's b / anorm
   long long a_off;     // element offset of the problem's A (row 0)
   long long x_off;     // element offset of the first chain's row in X / NU
   long long p_off;     // element offset of the first chain's row in P / Q
+  long long at_off;    // element offset of the problem's K-major copy of A (q GEMM)
+  int mpad;            // row stride of that copy: m rounded up to 4 (zero padded)
+  int pad_;
 };
-constexpr int kBatchTile = 64;  // rows and chains per item
+// Chain tile of a problem with n chains (16, 32 or 64; larger counts are cut
+// into tiles of 64), and the matching row tile.
+inline int batch_ctile(int n) { return n <= 16 ? 16 : n <= 32 ? 32 : 64; }
+inline int batch_rtile(int ctile) { return 4096 / ctile; }
 
 // nu for every chain of the batch (T = float: float Box-Muller, T = double:
 // 53-bit), written at desc[c].x_off; the step index is t (+ *t_dev if set).
 template <typename T>
 cudaError_t launch_batch_draw(const ChainDesc* desc, int n_chains, T* NU, uint64_t seed,
                               uint32_t t, const unsigned* t_dev, cudaStream_t s);
-// Q = A nu per item, in T; queue: one int of scratch (reset by the launcher).
+// Q = A nu per item, in T; AT holds every problem's A K-major (d x mpad at
+// at_off); queue: one int of scratch (reset by the launcher).
 template <typename T>
-cudaError_t launch_batch_q(const BatchItem* items, int n_items, int* queue, const T* A,
+cudaError_t launch_batch_q(const BatchItem* items, int n_items, int* queue, const T* AT,
                            const T* NU, T* Q, cudaStream_t s);
 // P = A64 X with FP64-class accuracy (see k_batch.cu); P64 and drift optional.
+// T = float reads A64 as Ahi + Alo (A rounded to float and the float
+// remainder), T = double reads A64 (Ahi, Alo unused).
 template <typename T>
 cudaError_t launch_batch_refresh(const BatchItem* items, int n_items, int* queue,
-                                 const double* A64, const T* X, T* P, double* P64,
-                                 const double* anorm, unsigned long long* drift_bits,
-                                 cudaStream_t s);
+                                 const T* Ahi, const double* A64, const float* Alo, const T* X,
+                                 T* P, double* P64, const double* anorm,
+                                 unsigned long long* drift_bits, cudaStream_t s);
 // status |= kStatusInfeasible if any P64 row entry exceeds b.
 cudaError_t launch_batch_check(const ChainDesc* desc, int n_chains, const double* P64,
                                const double* b64, int* status, cudaStream_t s);

@@ -8,11 +8,12 @@
 //   batch_draw_kernel      nu ~ N(0, I_{d_p}) per chain (Alg. 1, "sample nu"),
 //                          the same Philox counters as the one-problem path
 //                          with the problem index in the counter;
-//   batch_q_kernel         q = A_p nu for every chain: a grouped GEMM over work
-//                          items (problem, 64 rows of A_p, <= 64 of its chains)
-//                          taken from a global work queue by a persistent grid;
+//   batch_gemm_kernel      q = A_p nu for every chain: a grouped GEMM over work
+//                          items (problem, a tile of A_p's rows, a tile of its
+//                          chains) taken from a global work queue by a
+//                          persistent grid;
 //   the chain-step kernels (k_chain_warp.cu, k_chain.cu) with per-chain views.
-// Every refresh_k steps batch_refresh_kernel recomputes p = A_p x with
+// Every refresh_k steps the same kernel recomputes p = A_p x with
 // FP64-class accuracy (Sec. 2.2: A x carried forward; the refresh bounds the
 // drift): FP64 FMAs in the FP64 form, double-float sums on the FP32 pipe in
 // the mixed form (a = hi + lo in float, hi x split exactly by an FMA, partial
@@ -25,7 +26,6 @@
 namespace ess {
 namespace {
 
-constexpr int kBT = 64;      // rows of A and chains per work item
 constexpr int kBK = 16;      // K chunk staged in shared memory
 constexpr int kBThreads = 256;
 
@@ -60,65 +60,6 @@ __global__ void batch_draw_kernel(const ChainDesc* __restrict__ desc, int n_chai
   }
 }
 
-// q[c, i] = a_i . nu_c in T (FP32 FMAs in the mixed form, FP64 in the FP64
-// form).  Thread (ty, tx) of a 64 x 64 item owns chains ty + 16 i and rows
-// tx + 16 j.
-template <typename T>
-__global__ void __launch_bounds__(kBThreads)
-batch_q_kernel(const BatchItem* __restrict__ items, int n_items, int* queue,
-               const T* __restrict__ A, const T* __restrict__ NU, T* __restrict__ Q) {
-  __shared__ T As[kBK][kBT + 1];
-  __shared__ T Xs[kBK][kBT + 1];
-  __shared__ int s_item;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (;;) {
-    const int it = next_item(queue, &s_item);
-    if (it >= n_items) break;
-    const BatchItem I = items[it];
-    T acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-    const T* Ab = A + I.a_off + (size_t)I.row0 * I.d;
-    const T* Xb = NU + I.x_off;
-    for (int k0 = 0; k0 < I.d; k0 += kBK) {
-#pragma unroll
-      for (int e = 0; e < kBT * kBK / kBThreads; ++e) {
-        const int idx = tid + e * kBThreads;
-        const int r = idx / kBK, kk = idx % kBK, gk = k0 + kk;
-        As[kk][r] = (r < I.rows && gk < I.d) ? Ab[(size_t)r * I.d + gk] : T(0);
-        Xs[kk][r] = (r < I.chains && gk < I.d) ? Xb[(size_t)r * I.d + gk] : T(0);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < kBK; ++kk) {
-        T xv[4], av[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) xv[i] = Xs[kk][ty + 16 * i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) av[j] = As[kk][tx + 16 * j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(xv[i], av[j], acc[i][j]);
-      }
-      __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int ci = ty + 16 * i;
-      if (ci >= I.chains) continue;
-      T* qrow = Q + I.p_off + (size_t)ci * I.m + I.row0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int rj = tx + 16 * j;
-        if (rj < I.rows) qrow[rj] = acc[i][j];
-      }
-    }
-  }
-}
-
 // Error-free sum: s + e == a + b exactly.
 __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
   s = a + b;
@@ -126,106 +67,247 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   e = (a - (s - bb)) + (b - bb);
 }
 
-// p[c, i] = a_i . x_c with FP64-class accuracy.  T = double: FP64 FMAs.
-// T = float: a_i = hi + lo (floats), hi x exactly as (prod, fma error), the
-// running sum as an error-free (s, c) pair; the result (s + c) has relative
-// error ~2^-44 of sum |a||x|.  Writes P (rounded to T) and, if P64 is set, the
-// double value; with drift set, folds max |P_new - P_old| / ||a_i|| into it.
-template <typename T>
+template <typename V> struct Vec4;
+template <> struct Vec4<float> {
+  __device__ static void load(const float* p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+};
+template <> struct Vec4<double> {
+  __device__ static void load(const double* p, double (&v)[4]) {
+    const double2 t0 = reinterpret_cast<const double2*>(p)[0];
+    const double2 t1 = reinterpret_cast<const double2*>(p)[1];
+    v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+  }
+};
+
+inline unsigned warps_grid(int n) { return (unsigned)(((size_t)n * 32 + 255) / 256); }
+
+int persistent_grid(int n_items) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return std::max(1, std::min(n_items, sms * 6));
+}
+
+enum { kGemmQ = 0, kGemmRefresh = 1 };
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Asynchronous global -> shared copy of one element (4 or 8 bytes); copies
+// zeros when ok is false (no bytes are read then).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_addr(dst)), "l"(src),
+               "n"(BYTES), "r"(ok ? BYTES : 0)
+               : "memory");
+}
+// 16 bytes (both addresses 16-byte aligned), zeros when ok is false.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(ok ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_one() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+// Staged tile sizes (elements): A chunk 16 x (256 + 4), X chunk 16 x (64 + 4);
+// rows padded to 16-byte multiples for the 128-bit shared loads.
+constexpr int kAS = 256 + 4;
+constexpr int kXS = 64 + 4;
+
+template <typename TA, typename TX, bool kDF>
+constexpr size_t gemm_smem_bytes() {
+  return 2 * ((kDF ? 2 : 1) * sizeof(TA) * kBK * kAS + sizeof(TX) * kBK * kXS);
+}
+
+// One grouped-GEMM launch over work items taken from a device queue.  An item
+// is rows row0 .. row0 + rows - 1 of one problem's A times `chains` of its
+// chains, tile shape rtile x ctile (256 x 16, 128 x 32 or 64 x 64, chosen per
+// problem from its chain count).  Thread (tx, ty) owns rows 4 tx .. 4 tx + 3
+// and chains 4 ty .. 4 ty + 3 (4 x 4 register tile, 128-bit shared loads);
+// a warp covers an 8 x 4 block of such threads.
+// K is staged 16 columns at a time by cp.async into two shared-memory
+// buffers, the next chunk's copies in flight while the current one is used.
+//   kGemmQ:       out[c, i] = a_i . nu_c in T (FP32 or FP64 FMAs); A is read
+//                 from its K-major copy (16-byte copies of consecutive rows).
+//   kGemmRefresh: p[c, i] = a_i . x_c with FP64-class accuracy:
+//                 T = double: FP64 FMAs on A64; T = float: A64 = hi + lo with
+//                 hi = Aq (A rounded to float) and lo = Alo (float), hi x
+//                 exactly as (product, FMA error), sums as error-free (s, c)
+//                 pairs (relative error ~2^-44 of sum |a||x|).  Also writes
+//                 P64 and folds max |P_new - P_old| / ||a_i|| into drift_bits.
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kBThreads)
-batch_refresh_kernel(const BatchItem* __restrict__ items, int n_items, int* queue,
-                     const double* __restrict__ A64, const T* __restrict__ X, T* P, double* P64,
-                     const double* __restrict__ anorm, unsigned long long* drift_bits) {
-  constexpr bool kDF = sizeof(T) == 4;
-  using S = typename std::conditional<kDF, float, double>::type;
-  __shared__ S Ah[kBK][kBT + 1];
-  __shared__ S Al[kDF ? kBK : 1][kBT + 1];
-  __shared__ T Xs[kBK][kBT + 1];
+batch_gemm_kernel(const BatchItem* __restrict__ items, int n_items, int* queue,
+                  const T* __restrict__ Aq, const double* __restrict__ A64,
+                  const float* __restrict__ Alo, const T* __restrict__ X, T* out, double* P64,
+                  const double* __restrict__ anorm, unsigned long long* drift_bits) {
+  constexpr bool kDF = MODE == kGemmRefresh && sizeof(T) == 4;  // double-float sums
+  // staged A type: T for q and the double-float refresh, double otherwise
+  using TA = typename std::conditional<MODE == kGemmQ || kDF, T, double>::type;
+  constexpr int kASlices = kDF ? 2 : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TA* As = reinterpret_cast<TA*>(smem_raw);  // [2][kASlices][kBK][kAS]
+  T* Xs = reinterpret_cast<T*>(smem_raw + 2 * kASlices * sizeof(TA) * kBK * kAS);  // [2][kBK][kXS]
   __shared__ int s_item;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x;
+  const TA* Asrc = MODE == kGemmQ || kDF ? reinterpret_cast<const TA*>(Aq)
+                                         : reinterpret_cast<const TA*>(A64);
+  const TA* Alsrc = reinterpret_cast<const TA*>(Alo);
   double drift = 0.0;
   for (;;) {
     const int it = next_item(queue, &s_item);
     if (it >= n_items) break;
     const BatchItem I = items[it];
-    S hi[4][4], lo[4][4];
+    // warp w covers 8 row quads x 4 chain quads (lane & 7, lane >> 3), so a
+    // k step reads 128 bytes of A and 64 bytes of X per warp from shared memory
+    const int wpr = I.rtile >> 5;  // warps across the row quads (rtile / 4 / 8)
+    const int warp = tid >> 5, lane = tid & 31;
+    const int tx = (warp % wpr) * 8 + (lane & 7);
+    const int ty = (warp / wpr) * 4 + (lane >> 3);
+    T hi[4][4], lo[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        hi[i][j] = S(0);
-        lo[i][j] = S(0);
+        hi[i][j] = T(0);
+        lo[i][j] = T(0);
       }
-    const double* Ab = A64 + I.a_off + (size_t)I.row0 * I.d;
+    const TA* Ab = MODE == kGemmQ ? Asrc + I.at_off : Asrc + I.a_off + (size_t)I.row0 * I.d;
+    const TA* Alb = kDF ? Alsrc + I.a_off + (size_t)I.row0 * I.d : nullptr;
     const T* Xb = X + I.x_off;
-    for (int k0 = 0; k0 < I.d; k0 += kBK) {
-#pragma unroll
-      for (int e = 0; e < kBT * kBK / kBThreads; ++e) {
-        const int idx = tid + e * kBThreads;
-        const int r = idx / kBK, kk = idx % kBK, gk = k0 + kk;
-        const double a = (r < I.rows && gk < I.d) ? Ab[(size_t)r * I.d + gk] : 0.0;
-        if constexpr (kDF) {
-          const float h = __double2float_rn(a);
-          Ah[kk][r] = h;
-          Al[kk][r] = __double2float_rn(a - (double)h);
-        } else {
-          Ah[kk][r] = a;
+    const int nchunk = (I.d + kBK - 1) / kBK;
+    // chunk c of A and X into buffer c & 1 (zero fill outside the item);
+    // consecutive threads read consecutive k of one row
+    auto stage = [&](int c) {
+      const int k0 = c * kBK;
+      TA* as = As + (c & 1) * kASlices * kBK * kAS;
+      T* xs = Xs + (c & 1) * kBK * kXS;
+      if constexpr (MODE == kGemmQ) {
+        // K-major A: 16-byte copies of V consecutive rows (zero padding up to mpad)
+        constexpr int V = 16 / sizeof(TA);
+        const int lg = 31 - __clz(I.rtile / V);  // vectors per k-row: a power of two
+        for (int idx = tid; idx < (kBK << lg); idx += kBThreads) {
+          const int kk = idx >> lg, r = V * (idx & ((1 << lg) - 1)), gk = k0 + kk;
+          const bool ok = gk < I.d && I.row0 + r < I.mpad;
+          cp_async16(&as[kk * kAS + r], ok ? Ab + (size_t)gk * I.mpad + I.row0 + r : Ab, ok);
         }
-        Xs[kk][r] = (r < I.chains && gk < I.d) ? Xb[(size_t)r * I.d + gk] : T(0);
+      } else {
+        for (int idx = tid; idx < I.rtile * kBK; idx += kBThreads) {
+          const int r = idx >> 4, kk = idx & 15, gk = k0 + kk;
+          const bool ok = r < I.rows && gk < I.d;
+          const size_t o = ok ? (size_t)r * I.d + gk : 0;
+          cp_async_elem<sizeof(TA)>(&as[kk * kAS + r], Ab + o, ok);
+          if constexpr (kDF) cp_async_elem<sizeof(TA)>(&as[(kBK + kk) * kAS + r], Alb + o, ok);
+        }
       }
-      __syncthreads();
-#pragma unroll 4
-      for (int kk = 0; kk < kBK; ++kk) {
+      for (int idx = tid; idx < I.ctile * kBK; idx += kBThreads) {
+        const int r = idx >> 4, kk = idx & 15, gk = k0 + kk;
+        const bool ok = r < I.chains && gk < I.d;
+        cp_async_elem<sizeof(T)>(&xs[kk * kXS + r], ok ? Xb + (size_t)r * I.d + gk : Xb, ok);
+      }
+    };
+    stage(0);
+    cp_async_commit();
+    for (int c = 0; c < nchunk; ++c) {
+      if (c + 1 < nchunk) stage(c + 1);
+      cp_async_commit();
+      cp_async_wait_one();  // chunk c has landed (this thread's copies)
+      __syncthreads();      // ... and every thread's
+      const TA* as = As + (c & 1) * kASlices * kBK * kAS;
+      const T* xs = Xs + (c & 1) * kBK * kXS;
+      const int kn = min(kBK, I.d - c * kBK);
+      auto kstep = [&](int kk) {
         T xv[4];
-        S ah[4], al[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) xv[i] = Xs[kk][ty + 16 * i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          ah[j] = Ah[kk][tx + 16 * j];
-          al[j] = kDF ? Al[kk][tx + 16 * j] : S(0);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
+        TA av[4];
+        Vec4<T>::load(xs + kk * kXS + 4 * ty, xv);
+        Vec4<TA>::load(as + kk * kAS + 4 * tx, av);
+        if constexpr (kDF) {
+          TA alv[4];
+          Vec4<TA>::load(as + (kBK + kk) * kAS + 4 * tx, alv);
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            if constexpr (kDF) {
-              const float pr = ah[j] * xv[i];
-              const float pe = fmaf(ah[j], xv[i], -pr);  // hi x = pr + pe exactly
-              float s, e;
-              two_sum_f(hi[i][j], pr, s, e);
-              hi[i][j] = s;
-              lo[i][j] += e + pe + al[j] * xv[i];
-            } else {
-              hi[i][j] = fma(ah[j], (double)xv[i], hi[i][j]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const float pr = av[j] * xv[i];
+              const float pe = fmaf(av[j], xv[i], -pr);  // hi x = pr + pe exactly
+              float sum, e;
+              two_sum_f(hi[i][j], pr, sum, e);
+              hi[i][j] = sum;
+              lo[i][j] += e + pe + alv[j] * xv[i];
             }
           }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) hi[i][j] = fma(xv[i], (T)av[j], hi[i][j]);
+        }
+      };
+      if (kn == kBK) {
+#pragma unroll
+        for (int kk = 0; kk < kBK; ++kk) kstep(kk);
+      } else {
+        for (int kk = 0; kk < kn; ++kk) kstep(kk);
       }
-      __syncthreads();
+      __syncthreads();  // buffer c & 1 is free for chunk c + 2
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int ci = ty + 16 * i;
+      const int ci = 4 * ty + i;
       if (ci >= I.chains) continue;
-      const size_t base = I.p_off + (size_t)ci * I.m + I.row0;
+      const size_t base = (size_t)I.p_off + (size_t)ci * I.m + I.row0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int rj = tx + 16 * j;
+        const int rj = 4 * tx + j;
         if (rj >= I.rows) continue;
-        const double v = (double)hi[i][j] + (double)lo[i][j];
-        if (P64) P64[base + rj] = v;
-        if (P) {
-          const T pn = (T)v;
-          if (drift_bits) {
-            const double old = (double)P[base + rj];
-            drift = fmax(drift, fabs((double)pn - old) / anorm[I.b_off + I.row0 + rj]);
+        if constexpr (MODE == kGemmQ) {
+          out[base + rj] = hi[i][j];
+        } else {
+          const double v = (double)hi[i][j] + (double)lo[i][j];
+          if (P64) P64[base + rj] = v;
+          if (out) {
+            const T pn = (T)v;
+            if (drift_bits) {
+              const double old = (double)out[base + rj];
+              drift = fmax(drift, fabs((double)pn - old) / anorm[I.b_off + I.row0 + rj]);
+            }
+            out[base + rj] = pn;
           }
-          P[base + rj] = pn;
         }
       }
     }
   }
   if (drift_bits) atomic_max_nonneg(drift_bits, drift);
+}
+
+template <typename T, int MODE>
+cudaError_t launch_gemm(const BatchItem* items, int n_items, int* queue, const T* Aq,
+                        const double* A64, const float* Alo, const T* X, T* out, double* P64,
+                        const double* anorm, unsigned long long* drift_bits, cudaStream_t s) {
+  constexpr bool kDF = MODE == kGemmRefresh && sizeof(T) == 4;
+  using TA = typename std::conditional<MODE == kGemmQ || kDF, T, double>::type;
+  constexpr size_t smem = gemm_smem_bytes<TA, T, kDF>();
+  auto k = batch_gemm_kernel<T, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(queue, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  k<<<persistent_grid(n_items), kBThreads, smem, s>>>(items, n_items, queue, Aq, A64, Alo, X, out,
+                                                      P64, anorm, drift_bits);
+  return cudaGetLastError();
 }
 
 // status |= kStatusInfeasible where the FP64-class product exceeds b.
@@ -243,19 +325,6 @@ __global__ void batch_check_kernel(const ChainDesc* __restrict__ desc, int n_cha
 
 __global__ void advance_t_kernel(unsigned* t_dev, unsigned by) { *t_dev += by; }
 
-inline unsigned warps_grid(int n) { return (unsigned)(((size_t)n * 32 + 255) / 256); }
-
-int persistent_grid(int n_items) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
-  return std::max(1, std::min(n_items, sms * 6));
-}
-
 }  // namespace
 
 template <typename T>
@@ -270,23 +339,18 @@ template <typename T>
 cudaError_t launch_batch_q(const BatchItem* items, int n_items, int* queue, const T* A,
                            const T* NU, T* Q, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  batch_q_kernel<T><<<persistent_grid(n_items), kBThreads, 0, s>>>(items, n_items, queue, A, NU, Q);
-  return cudaGetLastError();
+  return launch_gemm<T, kGemmQ>(items, n_items, queue, A, nullptr, nullptr, NU, Q, nullptr,
+                                nullptr, nullptr, s);
 }
 
 template <typename T>
 cudaError_t launch_batch_refresh(const BatchItem* items, int n_items, int* queue,
-                                 const double* A64, const T* X, T* P, double* P64,
-                                 const double* anorm, unsigned long long* drift_bits,
-                                 cudaStream_t s) {
+                                 const T* Ahi, const double* A64, const float* Alo, const T* X,
+                                 T* P, double* P64, const double* anorm,
+                                 unsigned long long* drift_bits, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  batch_refresh_kernel<T><<<persistent_grid(n_items), kBThreads, 0, s>>>(
-      items, n_items, queue, A64, X, P, P64, anorm, drift_bits);
-  return cudaGetLastError();
+  return launch_gemm<T, kGemmRefresh>(items, n_items, queue, Ahi, A64, Alo, X, P, P64, anorm,
+                                      drift_bits, s);
 }
 
 cudaError_t launch_batch_check(const ChainDesc* desc, int n_chains, const double* P64,
@@ -309,11 +373,13 @@ template cudaError_t launch_batch_q<float>(const BatchItem*, int, int*, const fl
                                            float*, cudaStream_t);
 template cudaError_t launch_batch_q<double>(const BatchItem*, int, int*, const double*,
                                             const double*, double*, cudaStream_t);
-template cudaError_t launch_batch_refresh<float>(const BatchItem*, int, int*, const double*,
-                                                 const float*, float*, double*, const double*,
+template cudaError_t launch_batch_refresh<float>(const BatchItem*, int, int*, const float*,
+                                                 const double*, const float*, const float*,
+                                                 float*, double*, const double*,
                                                  unsigned long long*, cudaStream_t);
 template cudaError_t launch_batch_refresh<double>(const BatchItem*, int, int*, const double*,
-                                                  const double*, double*, double*, const double*,
+                                                  const double*, const float*, const double*,
+                                                  double*, double*, const double*,
                                                   unsigned long long*, cudaStream_t);
 
 }  // namespace ess

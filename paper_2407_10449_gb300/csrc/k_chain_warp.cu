@@ -169,15 +169,18 @@ chain_warp_kernel(ChainParams<T> prm) {
     const int m = v.m, d = v.d;
     const T* Prow = v.P;
     const T* Qrow = v.Q;
-    for (int k = lane; k < 2 * kWBP; k += 32) bsub[k] = 0u;  // bsub and bfull
+    // clear bsub and bfull (contiguous, 16-byte aligned: 2 kWBP words)
+    for (int k = lane; k < 2 * kWBP / 4; k += 32)
+      reinterpret_cast<uint4*>(bsub)[k] = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
     const T tlo = (T)(1.0 - prm.tangent_thresh);
     const T thi = (T)(1.0 + prm.tangent_thresh);
     bool infeasible = false, nonfinite = false;
 
     // ---- 1a. a first batch of rows builds bucket maxima of beta ---------------
-    const int m_sub = min(m, 32 * kBatch);
-    {
+    // (with m <= kCand every row fits the candidate list: no first batch)
+    const int m_sub = m > kCand ? min(m, 32 * kBatch) : 0;
+    if (m_sub > 0) {
       T pv[kBatch], qv[kBatch];
 #pragma unroll
       for (int k = 0; k < kBatch; ++k) {
@@ -197,7 +200,7 @@ chain_warp_kernel(ChainParams<T> prm) {
       }
     }
     __syncwarp();
-    prefix_max(bsub, lane);
+    if (m_sub > 0) prefix_max(bsub, lane);
     __syncwarp();
 
     // ---- 1b. every row: full bucket maxima, candidates not dominated by an
@@ -229,8 +232,11 @@ chain_warp_kernel(ChainParams<T> prm) {
             code = 0x80000000u | (unsigned)i;
           } else if (cls == kRowApprox) {
             const int bk = pbucket(pa);
-            atomicMax(&bfull[bslot(bk)], __float_as_uint(pb));
             cand = bk < 2 || !(pb + 2.f * kPhiMargin <= __uint_as_float(bsub[bslot(bk - 2)]));
+            // a row dominated by the first batch adds nothing to the full
+            // maxima: the first-batch arc that covers it dominates every arc
+            // it would dominate
+            if (cand) atomicMax(&bfull[bslot(bk)], __float_as_uint(pb));
             code = ((unsigned)bk << 14) | (unsigned)i;
           }
         }
@@ -319,8 +325,13 @@ chain_warp_kernel(ChainParams<T> prm) {
       const T eps = (T)prm.trim_eps;
       T plo[kPer], phi[kPer], plen[kPer], sexcl[kPer];
       T gcarry = T(0), scarry = T(0);
+      const int jn = (n_roots + 31) >> 5;  // register slots holding roots (warp-uniform)
 #pragma unroll
       for (int j = 0; j < kPer; ++j) {
+        if (j >= jn) {
+          plo[j] = phi[j] = plen[j] = sexcl[j] = T(0);
+          continue;
+        }
         const int e = lane + 32 * j;
         const bool valid = e < n_roots;
         const T v = valid ? val[j] : T(0);
