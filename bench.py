@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mixed-only", action="store_true",
                     help="time only the mixed form (profiling runs)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the short runs of the other configurations")
     return ap.parse_args()
 
 
@@ -215,8 +217,12 @@ def phase_rooflines(inst, n_chains, timing, precision, peaks):
                                   peak=FP64_TFLOPS_MEASURED, work_per_launch=flops)
         elif phase == "refresh":
             if mixed:
-                # exact split: K (K + 1) / 2 BF16 slice products (K = 5 at d = 1000)
-                K = 5
+                # exact split: K (K + 1) / 2 bf16 slice products of w-bit slices,
+                # (2^w - 1)^2 d <= 2^24, K = ceil(35 / w) (K = 5 at d = 1000)
+                w = 8
+                while w > 1 and (2 ** w - 1) ** 2 * d > 2 ** 24:
+                    w -= 1
+                K = min(-(-35 // w), 7)
                 flops = K * (K + 1) / 2 * 2.0 * m * d * C
                 out[phase] = dict(bound="tensor", unit="TFLOP/s", achieved=flops / ms / 1e9,
                                   peak=peaks["bf16_tflops_sustained"], work_per_launch=flops,
@@ -247,7 +253,8 @@ def time_form(ess, torch, inst, precision, n_chains, steps, warmup, seed, world,
     prec = ess.ESS_PREC_MIXED if precision == "mixed" else ess.ESS_PREC_FP64
     s = ess.Sampler(inst.A, inst.b, precision=prec)
     stream = torch.cuda.Stream()
-    X = torch.zeros((n_chains, inst.d), dtype=torch.float64, device="cuda")
+    x0 = torch.as_tensor(inst.X0[0], dtype=torch.float64)
+    X = x0.to("cuda").repeat(n_chains, 1).contiguous()
     ess.ess_chains_init(s.state, X, n_chains, 0, stream)
     ess.ess_chains_step(s.state, warmup, seed, stream=stream)
     ess.ess_chains_get(s.state, None, stream)
@@ -274,6 +281,117 @@ def time_form(ess, torch, inst, precision, n_chains, steps, warmup, seed, world,
     stats = s.stats()
     s.close()
     return ms_max, timing, stats, clk
+
+
+# FP32 FMA peak of the GPU at the maximum SM clock (152 SMs x 128 FMA/clk x 2
+# flops x 2.07 GHz on GB300); the batched GEMM runs on the FP32 pipe.
+def fp32_peak_tflops(torch):
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return sms * 128 * 2 * 2.07e9 / 1e12
+
+
+def batch_phase_rooflines(insts, timing, precision, torch, peaks):
+    """Phase rooflines of the batched sampler (work summed over problems)."""
+    mixed = precision == "mixed"
+    esz = 4 if mixed else 8
+    mdC = sum(i.m * i.d * i.n_chains for i in insts)
+    steps = timing.get("draw", {}).get("launches", 0)
+    fp = fp32_peak_tflops(torch) if mixed else FP64_TFLOPS_MEASURED
+    work = {
+        "draw": ("hbm", "GB/s", float(sum(i.d * i.n_chains for i in insts) * esz),
+                 peaks["hbm_gbs"]),
+        "gemm": ("fp32" if mixed else "fp64", "TFLOP/s", 2.0 * mdC, fp),
+        "chain": ("hbm", "GB/s", float(sum(i.n_chains * esz * (3 * i.m + 3 * i.d) for i in insts)),
+                  peaks["hbm_gbs"]),
+        # double-float refresh: ~11 FP32 operations per multiply-add
+        "refresh": ("fp32" if mixed else "fp64", "TFLOP/s", 2.0 * mdC,
+                    fp / 5.5 if mixed else fp),
+    }
+    out = {}
+    total = sum(v["ms"] for v in timing.values()) or 1.0
+    for phase, t in timing.items():
+        if t["launches"] == 0 or t["ms"] <= 0:
+            continue
+        bound, unit, w, peak = work[phase]
+        units = steps if phase == "chain" and steps else t["launches"]
+        ms = t["ms"] / units
+        scale = 1e6 if unit == "GB/s" else 1e9
+        ach = w / ms / scale
+        out[phase] = dict(bound=bound, unit=unit, achieved=ach, peak=peak, frac=ach / peak,
+                          ms_per_launch=ms, work_per_launch=w, launches=t["launches"],
+                          share=t["ms"] / total)
+    return out
+
+
+def time_batch(ess, torch, insts, precision, steps, warmup, seed, peaks):
+    """Batched problems: value from a timed run (CUDA-graph replays), phases
+    from a second run with per-phase events (plain launches)."""
+    prec = ess.ESS_PREC_MIXED if precision == "mixed" else ess.ESS_PREC_FP64
+    As = [i.A for i in insts]
+    bs = [i.b for i in insts]
+    nc = [i.n_chains for i in insts]
+    s = ess.BatchSampler(As, bs, precision=prec)
+    X = s.pack([i.X0 for i in insts])
+    stream = torch.cuda.current_stream()
+    s.run(nc, X, warmup, seed)
+    s.reset_stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.run(nc, X, steps, seed, t0=warmup)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    stats = s.stats()
+    info = ess.ess_batch_info(s.batch)
+    ess.ess_batch_set_timing(s.batch, True)
+    ess.ess_batch_reset_timing(s.batch)
+    s.run(nc, X, steps, seed, t0=warmup + steps)
+    timing = ess.ess_batch_get_timing(s.batch)
+    s.close()
+    n = sum(nc)
+    phases = batch_phase_rooflines(insts, timing, precision, torch, peaks)
+    return {"value": n * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
+            "ms_per_step": ms / steps, "chains": n, "graph_launches": info["graph_launches"],
+            "phases": phases, "stats": stats}
+
+
+def time_configs(ess, torch, workloads, peaks, seed):
+    """The other configurations, both forms, short runs (parity-tested
+    elsewhere; reported here with their phase rooflines)."""
+    from types import SimpleNamespace
+    out = {}
+    singles = [("small_d10_m20_c16", workloads.small(n_chains=1), 16, (200, 200)),
+               ("medium_d100_m200_c1024", workloads.medium(n_chains=1), 1024, (200, 100))]
+    pb = workloads.probit(n_chains=1)
+    Aw, bw = ess.ess_whiten(pb["A0"], pb["b"], pb["mu"], pb["L"])
+    singles.append(("probit_n2000_c4096",
+                    SimpleNamespace(A=Aw, b=bw, X0=pb["X0"], d=Aw.shape[1], m=Aw.shape[0]),
+                    4096, (64, 3)))
+    for name, inst, C, (st_mixed, st_fp64) in singles:
+        entry = {}
+        for form, steps in (("mixed", st_mixed), ("fp64", st_fp64)):
+            ms, timing, stats, _ = time_form(ess, torch, inst, form, C, steps, 3, seed, 1, 0)
+            ph = phase_rooflines(inst, C, timing, form, peaks)
+            dom = max(ph, key=lambda k: ph[k]["share"]) if ph else None
+            entry[form] = {"value": C * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
+                           "ms_per_step": ms / steps,
+                           "dominant": dom, "dominant_frac": ph[dom]["frac"] if dom else None,
+                           "phases": ph, "rejections": stats["rejections"],
+                           "numeric_errors": stats["numeric_errors"]}
+        out[name] = entry
+    insts = workloads.batched()
+    entry = {}
+    for form, steps in (("mixed", 64), ("fp64", 8)):
+        r = time_batch(ess, torch, insts, form, steps, 4, seed, peaks)
+        ph = r["phases"]
+        dom = max(ph, key=lambda k: ph[k]["share"]) if ph else None
+        r["dominant"] = dom
+        r["dominant_frac"] = ph[dom]["frac"] if dom else None
+        entry[form] = r
+    out["batched_512_problems"] = entry
+    return out
 
 
 def time_e2e(ess, torch, inst, n_chains, steps, seed, record_every=10):
@@ -401,6 +519,9 @@ def main():
     cpu = None
     if not args.no_cpu and world >= 1:
         cpu = cpu_baseline(lambda n: workloads.metric(n_chains=n))
+    configs = None
+    if not args.no_configs and not args.mixed_only:
+        configs = time_configs(ess, torch, workloads, peaks, seed)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -421,6 +542,7 @@ def main():
         "clocks": clk,
         "gpu_launches": launches,
         "stats": stats,
+        "configs": configs,
     }
     print(json.dumps(line), flush=True)
     barrier(world)
