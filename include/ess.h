@@ -278,8 +278,8 @@ ess_status ess_step_noalloc(const double *A, const double *b, int d, int m, cons
 /* ---- Batched problems -------------------------------------------------------
  * Many independent polytopes {x : A_p x <= b_p} of uneven sizes d_p x m_p,
  * each with its own chains, advanced together: per step one grouped GEMM for
- * q = A_p nu over all problems (work items of 64 rows x 64 chains taken from a
- * device work queue by a persistent grid), one chain-step launch for all
+ * q = A_p nu over all problems (work items of up to 4096 row-chain pairs taken
+ * from a device work queue by a persistent grid), one chain-step launch for all
  * chains, and whole refresh periods replayed from a CUDA graph.  The sampler
  * of every chain is the one of ess_run (Alg. 1 with the roots of App. B and
  * the intersection of Alg. 3); the batch only changes how the work is laid
