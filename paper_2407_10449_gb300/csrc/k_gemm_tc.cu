@@ -50,13 +50,14 @@ constexpr int kThreads = 192;       // producer warp, MMA warp, 4 epilogue warps
 constexpr int kRefreshBN = 64;      // tile width of the exact refresh
 constexpr int kMaxSlices = 7;       // operand slices of the exact refresh
 constexpr int kMaxPasses = 28;      // products per launch
+// kModeSum: q = A nu (FP16x3).  A stage holds one K block of the two nu
+//   slices and the two A slices; three products go into two accumulators.
+// kModePairs: exact refresh, one (x slice, A slice) pair per stage.
 enum { kModeSum = 0, kModePairs = 1 };
 
-struct PassDesc {
-  unsigned char xi, bi;     // slice indices of the two operands
-  unsigned char group : 7;  // accumulator (sum mode)
-  unsigned char first : 1;  // first product into its accumulator
-  unsigned char shift;      // pairs mode: weight 2^-shift
+struct PassDesc {             // pairs mode: one slice pair per pass
+  unsigned char xi, bi;       // slice indices of the two operands
+  unsigned char shift;        // weight 2^-shift
 };
 
 struct TcMaps {
@@ -229,12 +230,17 @@ constexpr uint32_t tmem_cols_for(int groups) {
          : groups * BN <= 256 ? 256u : 512u;
 }
 
+template <int BN, int MODE>
+constexpr uint32_t stage_bytes() {
+  return (MODE == kModeSum ? 2u : 1u) * (uint32_t)(BM + BN) * BK * 2u;
+}
+
 template <int BN, int STAGES, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcArgs args) {
   constexpr uint32_t A_BYTES = BM * BK * 2;
   constexpr uint32_t B_BYTES = BN * BK * 2;
-  constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+  constexpr uint32_t STAGE_BYTES = stage_bytes<BN, MODE>();
   constexpr int GROUPS = 2;  // sum mode: up to 2 accumulators; pairs mode: 2 buffers
   constexpr uint32_t TMEM_COLS = tmem_cols_for<BN>(GROUPS);
   static_assert(B_BYTES % 1024 == 0, "BN must be a multiple of 8");
@@ -280,8 +286,74 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
   const int npass = args.npass, kblocks = args.kblocks;
   const int total = kblocks * npass;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer ----------------
+  if (warp == 0 && lane == 0 && MODE == kModeSum) {
+    // ---------------- TMA producer (sum mode): 4 tiles per K block ----------------
+    bool loaded[STAGES];
+    uint32_t last_phase[STAGES];
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) loaded[s] = false;
+    int s = 0;
+    uint32_t phase = 0;
+    for (int kb = 0; kb < kblocks; ++kb) {
+      if (kb >= STAGES && !mbar_wait(empty_bar(s), phase ^ 1u)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      const uint32_t sa = sbase + s * STAGE_BYTES;
+      mbar_expect_tx(full_bar(s), STAGE_BYTES);
+      tma_load_2d(sa, &maps.x[0], kb * BK, m0, full_bar(s));
+      tma_load_2d(sa + A_BYTES, &maps.x[1], kb * BK, m0, full_bar(s));
+      tma_load_2d(sa + 2 * A_BYTES, &maps.b[0], kb * BK, n0, full_bar(s));
+      tma_load_2d(sa + 2 * A_BYTES + B_BYTES, &maps.b[1], kb * BK, n0, full_bar(s));
+      loaded[s] = true;
+      last_phase[s] = phase;
+      if (++s == STAGES) {
+        s = 0;
+        phase ^= 1u;
+      }
+    }
+    if (*abort_flag) {
+      // let every copy this thread issued land before the CTA exits
+#pragma unroll
+      for (int j = 0; j < STAGES; ++j)
+        if (loaded[j]) (void)mbar_wait(full_bar(j), last_phase[j]);
+    }
+  } else if (warp == 1 && lane == 0 && MODE == kModeSum) {
+    // ---------------- MMA issuer (sum mode) ----------------
+    // acc 0 (columns 0 .. BN-1): h0.a0; acc 1 (BN .. 2BN-1): h1.a0 + h0.a1
+    constexpr uint32_t idesc = idesc_f16(BM, BN, false);
+    int s = 0;
+    uint32_t phase = 0;
+    for (int kb = 0; kb < kblocks; ++kb) {
+      if (!mbar_wait(full_bar(s), phase)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sa = sbase + s * STAGE_BYTES;
+      const uint64_t x0 = smem_desc_sw128(sa);
+      const uint64_t x1 = smem_desc_sw128(sa + A_BYTES);
+      const uint64_t b0 = smem_desc_sw128(sa + 2 * A_BYTES);
+      const uint64_t b1 = smem_desc_sw128(sa + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k)  // each K = 16 step advances 32 bytes
+        umma_bf16(tmem_d, x0 + 2 * k, b0 + 2 * k, idesc, (kb == 0 && k == 0) ? 0u : 1u);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k)
+        umma_bf16(tmem_d + BN, x1 + 2 * k, b0 + 2 * k, idesc, (kb == 0 && k == 0) ? 0u : 1u);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k)
+        umma_bf16(tmem_d + BN, x0 + 2 * k, b1 + 2 * k, idesc, 1u);
+      umma_commit(empty_bar(s));
+      if (++s == STAGES) {
+        s = 0;
+        phase ^= 1u;
+      }
+    }
+    umma_commit(accf_bar(0));
+  } else if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer (pairs mode) ----------------
     int last_round[STAGES];
 #pragma unroll
     for (int s = 0; s < STAGES; ++s) last_round[s] = -1;
@@ -293,9 +365,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
         break;
       }
       if (*abort_flag) break;
-      int kb, pass;
-      if (MODE == kModeSum) { kb = it / npass; pass = it % npass; }
-      else { pass = it / kblocks; kb = it % kblocks; }
+      const int pass = it / kblocks, kb = it % kblocks;
       const PassDesc pd = args.pass[pass];
       const uint32_t sa = sbase + s * STAGE_BYTES;
       mbar_expect_tx(full_bar(s), STAGE_BYTES);
@@ -310,31 +380,21 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
         if (last_round[s] >= 0) (void)mbar_wait(full_bar(s), (uint32_t)(last_round[s] & 1));
     }
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer ----------------
-    constexpr uint32_t idesc = idesc_f16(BM, BN, MODE == kModePairs);
+    // ---------------- MMA issuer (pairs mode) ----------------
+    constexpr uint32_t idesc = idesc_f16(BM, BN, true);
     for (int it = 0; it < total; ++it) {
       const int s = it % STAGES;
       const int round = it / STAGES;
-      int kb, pass;
-      if (MODE == kModeSum) { kb = it / npass; pass = it % npass; }
-      else { pass = it / kblocks; kb = it % kblocks; }
-      const PassDesc pd = args.pass[pass];
-      uint32_t acc_col;
-      bool fresh;  // first MMA into this accumulator: overwrite instead of add
-      if (MODE == kModeSum) {
-        acc_col = (uint32_t)(pd.group * BN);
-        fresh = kb == 0 && pd.first;
-      } else {
-        const int buf = pass & 1;
-        acc_col = (uint32_t)(buf * BN);
-        fresh = kb == 0;
-        if (kb == 0 && pass >= 2 &&
-            !mbar_wait(acce_bar(buf), (uint32_t)(((pass >> 1) - 1) & 1))) {
-          *abort_flag = 1;
-          break;
-        }
-        if (kb == 0) tc_fence_after();
+      const int pass = it / kblocks, kb = it % kblocks;
+      const int buf = pass & 1;
+      const uint32_t acc_col = (uint32_t)(buf * BN);
+      const bool fresh = kb == 0;  // first MMA into this buffer: overwrite
+      if (kb == 0 && pass >= 2 &&
+          !mbar_wait(acce_bar(buf), (uint32_t)(((pass >> 1) - 1) & 1))) {
+        *abort_flag = 1;
+        break;
       }
+      if (kb == 0) tc_fence_after();
       if (!mbar_wait(full_bar(s), (uint32_t)(round & 1))) {
         *abort_flag = 1;
         break;
@@ -350,9 +410,8 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
                   (fresh && k == 0) ? 0u : 1u);
       }
       umma_commit(empty_bar(s));
-      if (MODE == kModePairs && kb == kblocks - 1) umma_commit(accf_bar(pass & 1));
+      if (kb == kblocks - 1) umma_commit(accf_bar(buf));
     }
-    if (MODE == kModeSum) umma_commit(accf_bar(0));
   } else if (warp >= 2) {
     // ---------------- epilogue warps 2..5: TMEM lane quarter warp % 4 ----------------
     const int quarter = warp & 3;
@@ -564,23 +623,23 @@ cudaError_t make_map(CUtensorMap* map, const void* base, int rows, int cols, int
 
 constexpr int kSmemLimit = 227 * 1024;
 
-template <int BN>
+template <int BN, int MODE = kModeSum>
 constexpr int stages_for() {
-  constexpr int stage = (BM + BN) * BK * 2;
+  constexpr int stage = (int)stage_bytes<BN, MODE>();
   constexpr int s = (kSmemLimit - 1024 - 256) / stage;
   return s > 6 ? 6 : s;
 }
 
-template <int BN>
+template <int BN, int MODE>
 size_t smem_for() {
-  return (size_t)stages_for<BN>() * (BM + BN) * BK * 2 + 1024 + 256;
+  return (size_t)stages_for<BN, MODE>() * stage_bytes<BN, MODE>() + 1024 + 256;
 }
 
 template <int BN, int MODE>
 cudaError_t launch_bn(const TcMaps& maps, const TcArgs& args, cudaStream_t s) {
-  constexpr int ST = stages_for<BN>();
+  constexpr int ST = stages_for<BN, MODE>();
   auto k = tc_gemm_kernel<BN, ST, MODE>;
-  const size_t smem = smem_for<BN>();
+  const size_t smem = smem_for<BN, MODE>();
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((args.n_cols + BN - 1) / BN, (args.n_rows + BM - 1) / BM);
@@ -634,7 +693,14 @@ struct TcGemmPlan {
 void tc_gemm_tile_for(int n_chains, int m, int* bn, int* stages) {
   // Pick the tile width that minimises (waves of tiles) x (tile width): the
   // per-tile time grows with BN, and the last wave is padded to the SM count.
+  // (ESS_Q_BN fixes the width at build time, for tuning sweeps.)
   const int sms = num_sms();
+#ifdef ESS_Q_BN
+  *bn = ESS_Q_BN;
+  if (stages) *stages = 0;
+  (void)sms;
+  return;
+#endif
   const long long mt = (n_chains + BM - 1) / BM;
   int best = 256;
   long long best_cost = -1;
@@ -795,17 +861,9 @@ cudaError_t tc_gemm_q(TcGemmPlan* plan, __half* const nu[2], const float* nu_uns
   a.n_rows = n_chains;
   a.n_cols = plan->m;
   a.kblocks = (plan->d + BK - 1) / BK;
-  // group 0: h0.a0; group 1: h1.a0 and h0.a1 (weight 2^-11 each)
-  const unsigned char order[3][3] = {{0, 0, 0}, {1, 0, 1}, {0, 1, 1}};
+  // accumulator 0: h0.a0; accumulator 1: h1.a0 + h0.a1 (weight 2^-11 each)
   a.npass = 3;
   a.ngroups = 2;
-  for (int i = 0; i < 3; ++i) {
-    a.pass[i].xi = order[i][0];
-    a.pass[i].bi = order[i][1];
-    a.pass[i].group = order[i][2];
-    a.pass[i].first = i < 2 ? 1 : 0;
-    a.pass[i].shift = 0;
-  }
   a.Q = Q;
   a.ldq = ldq;
   a.row_scale = nu_unscale;
@@ -846,8 +904,6 @@ cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
       if (k > K || l > K) continue;
       a.pass[np].xi = (unsigned char)(l - 1);
       a.pass[np].bi = (unsigned char)(k - 1);
-      a.pass[np].group = 0;
-      a.pass[np].first = 1;
       a.pass[np].shift = (unsigned char)(plan->w * sum);
       ++np;
     }
