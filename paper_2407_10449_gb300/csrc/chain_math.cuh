@@ -3,6 +3,7 @@
 // approximate arcs used only to decide which arcs the sort can skip.
 #pragma once
 
+#include <cfloat>
 #include <cmath>
 
 #include "ess_common.cuh"
@@ -166,31 +167,35 @@ __device__ __forceinline__ float diamond_angle(float x, float y) {
 // (App. B: cos tau = p / r, sin tau = q / r, cos h = b / r, sin h = w / r).
 // The row classes match roots(): the no-root and near-tangent decisions are
 // taken only outside a 1e-6 relative slack of the b/r computed here, and rows
-// whose arc would wrap through 0 (boundary points) are always kept.
+// whose arc would wrap through 0 (boundary points) are always kept.  b64
+// points at the exact b_i (read only when r = 0); nonfinite is set when p or
+// q is NaN or infinite (r^2 is then not finite).
 template <typename T>
-__device__ __forceinline__ int classify_phi(T p, T q, T b, double b64, T tlo, T thi, float& pa,
-                                            float& pb, bool& infeasible) {
-  float ratio;
+__device__ __forceinline__ int classify_phi(T p, T q, T b, const double* b64, T tlo, T thi,
+                                            float& pa, float& pb, bool& infeasible,
+                                            bool& nonfinite) {
   const float pf = (float)p, qf = (float)q, bf = (float)b;
   if constexpr (sizeof(T) == 4) {
     const float r2 = fmaf(p, p, q * q);
+    nonfinite |= !(r2 <= FLT_MAX);  // NaN or Inf in p or q
     if (r2 == 0.0f) {
-      infeasible = b64 < 0.0;
+      infeasible = *b64 < 0.0;
       return kRowNone;
     }
-    ratio = b * rsqrtf(r2);
+    const float ratio = b * rsqrtf(r2);
     if (ratio >= thi * 1.000001f) return kRowNone;
     if (fabsf(ratio) > tlo * 0.999999f) return kRowKeep;
   } else {
-    const double r = sqrt(p * p + q * q);
+    const double r2 = p * p + q * q;
+    nonfinite |= !(r2 <= DBL_MAX);
+    const double r = sqrt(r2);
     if (r == 0.0) {
-      infeasible = b64 < 0.0;
+      infeasible = b < 0.0;
       return kRowNone;
     }
-    const double rd = b64 / r;
+    const double rd = b / r;
     if (rd >= 1.0) return kRowNone;
     if (fabs(rd) > tlo || r < 1e-30 || r > 1e30) return kRowKeep;
-    ratio = (float)rd;
   }
   const float r2f = fmaf(pf, pf, qf * qf);
   const float w2 = fmaf(-bf, bf, r2f);
@@ -198,7 +203,6 @@ __device__ __forceinline__ int classify_phi(T p, T q, T b, double b64, T tlo, T 
   const float w = w2 * rsqrtf(w2);
   pa = diamond_angle(fmaf(pf, bf, qf * w), fmaf(qf, bf, -pf * w));
   pb = diamond_angle(fmaf(pf, bf, -qf * w), fmaf(qf, bf, pf * w));
-  (void)ratio;
   return pa < pb ? kRowApprox : kRowKeep;
 }
 

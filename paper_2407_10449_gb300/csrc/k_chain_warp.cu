@@ -47,6 +47,7 @@ constexpr int kWBP = kWB + kWB / 32;      // padded bucket array: bucket j at j 
 #define ESS_WARP_MINBLOCKS 4
 #endif
 constexpr int kBatch = ESS_WARP_BATCH;    // rows per lane in flight per loop trip
+constexpr int kFirst = 256;               // rows of the first batch
 
 // Bucket j lives at j + j / 32: a lane's consecutive buckets then sit on
 // different banks.
@@ -179,24 +180,27 @@ chain_warp_kernel(ChainParams<T> prm) {
 
     // ---- 1a. a first batch of rows builds bucket maxima of beta ---------------
     // (with m <= kCand every row fits the candidate list: no first batch)
-    const int m_sub = m > kCand ? min(m, 32 * kBatch) : 0;
+    const int m_sub = m > kCand ? min(m, kFirst) : 0;
     if (m_sub > 0) {
-      T pv[kBatch], qv[kBatch];
+      for (int i0 = 0; i0 < m_sub; i0 += 32 * kBatch) {
+        T pv[kBatch], qv[kBatch], bv[kBatch];
 #pragma unroll
-      for (int k = 0; k < kBatch; ++k) {
-        const int i = lane + 32 * k;
-        pv[k] = i < m_sub ? Prow[i] : T(0);
-        qv[k] = i < m_sub ? Qrow[i] : T(0);
-      }
+        for (int k = 0; k < kBatch; ++k) {
+          const int i = i0 + lane + 32 * k;
+          pv[k] = i < m_sub ? Prow[i] : T(0);
+          qv[k] = i < m_sub ? Qrow[i] : T(0);
+          bv[k] = i < m_sub ? v.b[i] : T(0);
+        }
 #pragma unroll
-      for (int k = 0; k < kBatch; ++k) {
-        const int i = lane + 32 * k;
-        if (i >= m_sub) continue;
-        float pa = 0.f, pb = 0.f;
-        bool inf_row = false;
-        if (classify_phi<T>(pv[k], qv[k], v.b[i], v.b64[i], tlo, thi, pa, pb, inf_row) ==
-            kRowApprox)
-          atomicMax(&bsub[bslot(pbucket(pa))], __float_as_uint(pb));
+        for (int k = 0; k < kBatch; ++k) {
+          const int i = i0 + lane + 32 * k;
+          if (i >= m_sub) continue;
+          float pa = 0.f, pb = 0.f;
+          bool inf_row = false, nf = false;
+          if (classify_phi<T>(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb, inf_row, nf) ==
+              kRowApprox)
+            atomicMax(&bsub[bslot(pbucket(pa))], __float_as_uint(pb));
+        }
       }
     }
     __syncwarp();
@@ -207,12 +211,13 @@ chain_warp_kernel(ChainParams<T> prm) {
     //          arc of the first batch ------------------------------------------
     int n_cand = 0;
     for (int i0 = 0; i0 < m; i0 += 32 * kBatch) {
-      T pv[kBatch], qv[kBatch];
+      T pv[kBatch], qv[kBatch], bv[kBatch];
 #pragma unroll
       for (int k = 0; k < kBatch; ++k) {
         const int i = i0 + lane + 32 * k;
         pv[k] = i < m ? Prow[i] : T(0);
         qv[k] = i < m ? Qrow[i] : T(0);
+        bv[k] = i < m ? v.b[i] : T(0);
       }
 #pragma unroll
       for (int k = 0; k < kBatch; ++k) {
@@ -221,11 +226,10 @@ chain_warp_kernel(ChainParams<T> prm) {
         unsigned code = 0u;
         float pb = 0.f;
         if (i < m) {
-          nonfinite |= !isfinite(pv[k]) || !isfinite(qv[k]);
           float pa = 0.f;
           bool inf_row = false;
-          const int cls =
-              classify_phi<T>(pv[k], qv[k], v.b[i], v.b64[i], tlo, thi, pa, pb, inf_row);
+          const int cls = classify_phi<T>(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb,
+                                          inf_row, nonfinite);
           infeasible |= inf_row;
           if (cls == kRowKeep) {
             cand = true;
@@ -420,12 +424,14 @@ chain_warp_kernel(ChainParams<T> prm) {
       int rechecks = 0;
       double maxres = -INFINITY;
       for (int i0 = 0; i0 < m; i0 += 32 * kBatch) {
-        T pv[kBatch], qv[kBatch];
+        T pv[kBatch], qv[kBatch], sv[kBatch];
 #pragma unroll
         for (int k = 0; k < kBatch; ++k) {
           const int i = i0 + lane + 32 * k;
           pv[k] = i < m ? Prow[i] : T(0);
           qv[k] = i < m ? Qrow[i] : T(0);
+          sv[k] = i < m ? (v.slack ? v.slack[i] : (T)(v.b64[i] - prm.margin * v.anorm[i]))
+                        : T(0);
         }
         unsigned flags = 0u;
 #pragma unroll
@@ -434,9 +440,7 @@ chain_warp_kernel(ChainParams<T> prm) {
           if (i < m) {
             const T pn = pv[k] * cs + qv[k] * sn;
             prow_out[i] = pn;
-            const T slack =
-                v.slack ? v.slack[i] : (T)(v.b64[i] - prm.margin * v.anorm[i]);
-            if (!(pn <= slack)) flags |= 1u << k;
+            if (!(pn <= sv[k])) flags |= 1u << k;
           }
         }
         for (int k = 0; k < kBatch; ++k) {
