@@ -249,7 +249,10 @@ def phase_rooflines(inst, n_chains, timing, precision, peaks):
 
 
 def time_form(ess, torch, inst, precision, n_chains, steps, warmup, seed, world, rank,
-              clocks=None):
+              clocks=None, phase_steps=None):
+    """K steps through ess_chains_step on the run's stream as a user runs them
+    (refresh periods replayed from CUDA graphs), timed by CUDA events; then a
+    second pass with per-phase events (plain launches) for the phase table."""
     prec = ess.ESS_PREC_MIXED if precision == "mixed" else ess.ESS_PREC_FP64
     s = ess.Sampler(inst.A, inst.b, precision=prec)
     stream = torch.cuda.Stream()
@@ -259,7 +262,6 @@ def time_form(ess, torch, inst, precision, n_chains, steps, warmup, seed, world,
     ess.ess_chains_step(s.state, warmup, seed, stream=stream)
     ess.ess_chains_get(s.state, None, stream)
     ess.ess_reset_timing(s.state)
-    ess.ess_set_timing(s.state, True)
     s.reset_stats()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -277,10 +279,18 @@ def time_form(ess, torch, inst, precision, n_chains, steps, warmup, seed, world,
     ess.ess_chains_get(s.state, None, stream)
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(world, ms)
-    timing = ess.ess_get_timing(s.state)
+    launches = sum(t["launches"] for t in ess.ess_get_timing(s.state).values())
+    graphs = ess.ess_graph_launches(s.state)
     stats = s.stats()
+    # phase table: per-phase events around plain launches
+    ps = phase_steps or steps
+    ess.ess_reset_timing(s.state)
+    ess.ess_set_timing(s.state, True)
+    ess.ess_chains_step(s.state, ps, seed, stream=stream)
+    ess.ess_chains_get(s.state, None, stream)
+    timing = ess.ess_get_timing(s.state)
     s.close()
-    return ms_max, timing, stats, clk
+    return ms_max, timing, stats, clk, {"gpu_launches": launches, "graph_launches": graphs}
 
 
 # FP32 FMA peak of the GPU at the maximum SM clock (152 SMs x 128 FMA/clk x 2
@@ -372,13 +382,14 @@ def time_configs(ess, torch, workloads, peaks, seed):
     for name, inst, C, (st_mixed, st_fp64) in singles:
         entry = {}
         for form, steps in (("mixed", st_mixed), ("fp64", st_fp64)):
-            ms, timing, stats, _ = time_form(ess, torch, inst, form, C, steps, 3, seed, 1, 0)
+            ms, timing, stats, _, lc = time_form(ess, torch, inst, form, C, steps, 3, seed, 1, 0)
             ph = phase_rooflines(inst, C, timing, form, peaks)
             dom = max(ph, key=lambda k: ph[k]["share"]) if ph else None
             entry[form] = {"value": C * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
                            "ms_per_step": ms / steps,
                            "dominant": dom, "dominant_frac": ph[dom]["frac"] if dom else None,
-                           "phases": ph, "rejections": stats["rejections"],
+                           "phases": ph, "graph_launches": lc["graph_launches"],
+                           "rejections": stats["rejections"],
                            "numeric_errors": stats["numeric_errors"]}
         out[name] = entry
     insts = workloads.batched()
@@ -483,14 +494,14 @@ def main():
     seed = args.seed + 1000003 * rank
 
     clocks = ClockSampler(local) if rank == 0 else None
-    ms, timing, stats, clk = time_form(ess, torch, inst, "mixed", C, args.steps, args.warmup,
-                                       seed, world, rank, clocks)
+    ms, timing, stats, clk, lc = time_form(ess, torch, inst, "mixed", C, args.steps, args.warmup,
+                                           seed, world, rank, clocks)
     value = world * C * args.steps / (ms / 1e3)
     if args.mixed_only:
         ms64, timing64, stats64, value64 = float("nan"), {}, {}, None
     else:
-        ms64, timing64, stats64, _ = time_form(ess, torch, inst, "fp64", C, args.fp64_steps, 3,
-                                               seed, world, rank, None)
+        ms64, timing64, stats64, _, _ = time_form(ess, torch, inst, "fp64", C, args.fp64_steps,
+                                                  3, seed, world, rank, None)
         value64 = world * C * args.fp64_steps / (ms64 / 1e3)
 
     if rank != 0:
@@ -511,7 +522,7 @@ def main():
                 "traffic": traffic, "work_per_launch": dom["work_per_launch"],
                 "peak_source": peaks["source"] if dom["bound"] in ("hbm", "tensor") else
                 "DFMA microbenchmark on this pool"}
-    launches = sum(t["launches"] for t in timing.values())
+    launches = lc["gpu_launches"]
 
     e2e = None
     if not args.no_e2e:
@@ -541,6 +552,7 @@ def main():
         "cpu_baseline": cpu,
         "clocks": clk,
         "gpu_launches": launches,
+        "graph_launches": lc["graph_launches"],
         "stats": stats,
         "configs": configs,
     }

@@ -275,6 +275,18 @@ ess_status ess_step_noalloc(const double *A, const double *b, int d, int m, cons
                             const double *nu, const double *u, int n_chains, double *X_next,
                             double *theta, int *rejected, void *cuda_stream);
 
+/*
+ * CUDA-graph replay of whole refresh periods in ess_chains_step / ess_run
+ * (on by default).  A period -- the A x refresh and refresh_k steps -- is
+ * captured once per (chain count, seed, p buffer) and replayed, the step index
+ * coming from a device counter that the graph advances; it applies when
+ * refresh_k is even, no samples are recorded and phase timing is off.  The
+ * chains are bit-identical with and without graphs.  ess_graph_launches
+ * reports the replays since the state was created.
+ */
+ess_status ess_set_graphs(ess_state *state, int enable);
+ess_status ess_graph_launches(const ess_state *state, long long *launches);
+
 /* ---- Batched problems -------------------------------------------------------
  * Many independent polytopes {x : A_p x <= b_p} of uneven sizes d_p x m_p,
  * each with its own chains, advanced together: per step one grouped GEMM for

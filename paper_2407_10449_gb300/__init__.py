@@ -43,6 +43,7 @@ EXPORTED = ("ess_default_config", "ess_create", "ess_destroy", "ess_limits", "es
             "ess_draw_normals",
             "ess_set_timing", "ess_get_timing", "ess_reset_timing",
             "ess_get_stats", "ess_reset_stats", "ess_whiten", "ess_unwhiten", "ess_step_noalloc",
+            "ess_set_graphs", "ess_graph_launches",
             "ess_batch_create", "ess_batch_destroy", "ess_batch_run", "ess_batch_step_with_draws",
             "ess_batch_products", "ess_batch_get_stats", "ess_batch_reset_stats",
             "ess_batch_set_graphs", "ess_batch_set_timing", "ess_batch_get_timing",
@@ -126,6 +127,8 @@ def load(build_if_missing: bool = True):
             "ess_unwhiten": ([_dp, _dp, c_int, c_int, _dp, _dp], c_int),
             "ess_step_noalloc": ([_vp, _vp, c_int, c_int, _vp, _vp, _vp, c_int, _vp, _vp, _vp,
                                   _vp], c_int),
+            "ess_set_graphs": ([_vp, c_int], c_int),
+            "ess_graph_launches": ([_vp, ctypes.POINTER(ctypes.c_longlong)], c_int),
             "ess_batch_create": ([c_int, _vp, _vp, _dp, _dp, ctypes.POINTER(ess_config),
                                   ctypes.POINTER(_vp)], c_int),
             "ess_batch_destroy": ([_vp], None),
@@ -314,6 +317,16 @@ def ess_step_noalloc(A, b, X, nu, u, X_next, theta=None, rejected=None, stream=N
     _check(load().ess_step_noalloc(_ptr(A), _ptr(b), d, m, _ptr(X), _ptr(nu), _ptr(u), n,
                                    _ptr(X_next), _ptr(theta), _ptr(rejected),
                                    _stream_ptr(stream)))
+
+
+def ess_set_graphs(state, enable=True):
+    _check(load().ess_set_graphs(state, 1 if enable else 0))
+
+
+def ess_graph_launches(state) -> int:
+    n = ctypes.c_longlong()
+    _check(load().ess_graph_launches(state, ctypes.byref(n)))
+    return n.value
 
 
 def ess_batch_create(As, bs, cfg: ess_config | None = None):

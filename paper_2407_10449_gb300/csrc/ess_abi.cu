@@ -94,6 +94,19 @@ struct ess_state {
   DevStats* dstats = nullptr;
   int* dstatus = nullptr;
   ess::TcGemmPlan* tc_plan = nullptr;  // tensor-core GEMMs (q = A nu, exact refresh)
+  // CUDA graphs of one refresh period (refresh + refresh_k steps), keyed by
+  // chain count, seed and the p buffer the period starts from
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  unsigned* t_dev = nullptr;  // step index base of a replayed period
+  struct GraphEntry {
+    int n;
+    uint64_t seed;
+    void* p_first;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+  long long graph_launches = 0;
   // optional per-phase device timing (CUDA events on the run's stream)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -149,7 +162,13 @@ void timing_collect(ess_state* s) {
 }
 size_t elem(const ess_state* s) { return mixed(s) ? sizeof(float) : sizeof(double); }
 
+void drop_graphs(ess_state* s) {
+  for (auto& g : s->graphs) cudaGraphExecDestroy(g.exec);
+  s->graphs.clear();
+}
+
 void free_work(ess_state* s) {
+  drop_graphs(s);
   if (s->P) cudaFree(s->P);
   if (s->P2) cudaFree(s->P2);
   s->P2 = nullptr;
@@ -335,6 +354,89 @@ struct DeviceGuard {
 
 }  // namespace
 
+namespace {
+
+// One step of every loaded chain at step index t (+ *t_dev when t_dev is
+// set): draw nu, q = A nu, chain step (p buffers swapped).
+template <typename T>
+ess_status step_one(ess_state* s, uint64_t seed, uint32_t t, const unsigned* t_dev, T* samples,
+                    long long sample_stride, cudaStream_t st) {
+  const int n = s->n_loaded, d = s->d;
+  {
+    PhaseScope ps(s, st, ESS_PHASE_DRAW);
+    if constexpr (sizeof(T) == 4)
+      ESS_CUDA(ess::launch_draw_nu_f32(static_cast<float*>(s->NU), d, s->NU_h, s->ld16, n, d,
+                                       seed, t, 0u, 0u, st, t_dev));
+    else
+      ESS_CUDA(ess::launch_draw_nu_f64(static_cast<double*>(s->NU), n, d, d, seed, t, 0u, 0u, st,
+                                       t_dev));
+  }
+  {
+    PhaseScope ps(s, st, ESS_PHASE_GEMM);
+    ess_status rc = compute_q(s, n, st);
+    if (rc != ESS_OK) return rc;
+  }
+  ess::ChainParams<T> p = base_params<T>(s, n);
+  p.X = static_cast<const T*>(chain_states(s));
+  p.X_out = static_cast<T*>(const_cast<void*>(chain_states(s)));
+  p.seed = seed;
+  p.t = t;
+  p.t_dev = t_dev;
+  p.samples = samples;
+  p.sample_stride = sample_stride;
+  PhaseScope ps(s, st, ESS_PHASE_CHAIN, s->cfg.sort_threads > 0 ? 1 : 2);
+  return launch_step<T>(s, p, st);
+}
+
+// Replays (capturing on first use) one refresh period -- refresh, then
+// refresh_k steps -- starting at the step index held in *t_dev.
+template <typename T>
+ess_status graph_period(ess_state* s, uint64_t seed, cudaStream_t st) {
+  const int k = s->cfg.refresh_k;
+  ess_state::GraphEntry* hit = nullptr;
+  for (auto& g : s->graphs)
+    if (g.n == s->n_loaded && g.seed == seed && g.p_first == s->P) hit = &g;
+  if (!hit) {
+    if (!s->cap_stream) ESS_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+    void* p_first = s->P;
+    const bool timing = s->timing;
+    s->timing = false;
+    ESS_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    ess_status rc = refresh_p(s, s->n_loaded, chain_states(s), true, false, s->cap_stream);
+    for (int j = 0; j < k && rc == ESS_OK; ++j)
+      rc = step_one<T>(s, seed, (uint32_t)j, s->t_dev, nullptr, 0, s->cap_stream);
+    if (rc == ESS_OK) {
+      cudaError_t e = ess::launch_advance_t(s->t_dev, (unsigned)k, s->cap_stream);
+      if (e != cudaSuccess) rc = cuda_fail(e, "advance step index");
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(s->cap_stream, &graph);
+    s->timing = timing;
+    if (rc != ESS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess) return cuda_fail(ec, "graph capture");
+    cudaGraphExec_t exec = nullptr;
+    ec = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) return cuda_fail(ec, "graph instantiate");
+    // refresh_k is even, so the period leaves the p buffers where it found them
+    if (s->P != p_first) std::swap(s->P, s->P2);
+    s->graphs.push_back({s->n_loaded, seed, p_first, exec});
+    hit = &s->graphs.back();
+  }
+  ESS_CUDA(cudaGraphLaunch(hit->exec, st));
+  ++s->graph_launches;
+  s->phase_launches[ESS_PHASE_REFRESH] += 1;
+  s->phase_launches[ESS_PHASE_DRAW] += k;
+  s->phase_launches[ESS_PHASE_GEMM] += k;
+  s->phase_launches[ESS_PHASE_CHAIN] += (long long)k * (s->cfg.sort_threads > 0 ? 1 : 2);
+  return ESS_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 ess_status ess_default_config(int precision, ess_config* cfg) {
@@ -431,6 +533,7 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
   }
   if (e == cudaSuccess) e = dev_alloc(&s->dstats, 1);
   if (e == cudaSuccess) e = dev_alloc(&s->dstatus, 1);
+  if (e == cudaSuccess) e = dev_alloc(&s->t_dev, 1);
   if (e == cudaSuccess) e = cudaMemset(s->dstats, 0, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMemset(s->dstatus, 0, sizeof(int));
   if (e == cudaSuccess && c.precision == ESS_PREC_MIXED) {
@@ -459,6 +562,8 @@ void ess_destroy(ess_state* s) {
   dev_free(s->dstatus);
   ess::tc_gemm_destroy(s->tc_plan);
   s->tc_plan = nullptr;
+  dev_free(s->t_dev);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   delete s;
 }
@@ -513,67 +618,55 @@ ess_status ess_chains_step(ess_state* s, int n_iter, uint64_t seed, void* sample
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int n = s->n_loaded, d = s->d;
   const int n_rec = record_every > 0 ? n_iter / record_every : 0;
-  const uint32_t k = (uint32_t)s->cfg.refresh_k;
-  for (int it = 0; it < n_iter; ++it) {
-    const uint32_t t = (uint32_t)(s->t_next + it);
-    if (t % k == 0 && (int)t != s->p_fresh_t) {
+  const int k = s->cfg.refresh_k;
+  // whole refresh periods replay from a CUDA graph (not with sample recording
+  // or per-phase timing, whose pointers and events change from step to step)
+  const bool graphs_ok = s->use_graphs && !s->timing && record_every == 0 && k % 2 == 0;
+  int it = 0;
+  while (it < n_iter) {
+    const int t = s->t_next + it;
+    if (graphs_ok && t % k == 0 && t != s->p_fresh_t && n_iter - it >= k) {
+      ESS_CUDA(ess::launch_set_t(s->t_dev, (unsigned)t, st));
+      while (n_iter - it >= k) {
+        ess_status rc = mixed(s) ? graph_period<float>(s, seed, st) : graph_period<double>(s, seed, st);
+        if (rc != ESS_OK) return rc;
+        it += k;
+      }
+      s->p_fresh_t = s->t_next + it - k;
+      continue;
+    }
+    if (t % k == 0 && t != s->p_fresh_t) {
       PhaseScope ps(s, st, ESS_PHASE_REFRESH);
       ess_status rc = refresh_p(s, n, chain_states(s), true, false, st);
       if (rc != ESS_OK) return rc;
-      s->p_fresh_t = (int)t;
+      s->p_fresh_t = t;
     }
     const bool rec = record_every > 0 && (it + 1) % record_every == 0 &&
                      (it + 1) / record_every <= n_rec;
     const long long rec_off = rec ? (long long)((it + 1) / record_every - 1) * d : 0;
-    if (mixed(s)) {
-      {
-        PhaseScope ps(s, st, ESS_PHASE_DRAW);
-        ESS_CUDA(ess::launch_draw_nu_f32(static_cast<float*>(s->NU), d, s->NU_h, s->ld16, n, d,
-                                         seed, t, 0u, 0u, st));
-      }
-      {
-        PhaseScope ps(s, st, ESS_PHASE_GEMM);
-        ess_status rc = compute_q(s, n, st);
-        if (rc != ESS_OK) return rc;
-      }
-      ess::ChainParams<float> p = base_params<float>(s, n);
-      p.X = s->Xw;
-      p.X_out = s->Xw;
-      p.seed = seed;
-      p.t = t;
-      if (rec) {
-        p.samples = static_cast<float*>(samples) + rec_off;
-        p.sample_stride = (long long)n_rec * d;
-      }
-      PhaseScope ps(s, st, ESS_PHASE_CHAIN, s->cfg.sort_threads > 0 ? 1 : 2);
-      ess_status rc = launch_step<float>(s, p, st);
-      if (rc != ESS_OK) return rc;
-    } else {
-      {
-        PhaseScope ps(s, st, ESS_PHASE_DRAW);
-        ESS_CUDA(ess::launch_draw_nu_f64(static_cast<double*>(s->NU), n, d, d, seed, t, 0u, 0u, st));
-      }
-      {
-        PhaseScope ps(s, st, ESS_PHASE_GEMM);
-        ess_status rc = compute_q(s, n, st);
-        if (rc != ESS_OK) return rc;
-      }
-      ess::ChainParams<double> p = base_params<double>(s, n);
-      p.X = s->Xd;
-      p.X_out = s->Xd;
-      p.seed = seed;
-      p.t = t;
-      if (rec) {
-        p.samples = static_cast<double*>(samples) + rec_off;
-        p.sample_stride = (long long)n_rec * d;
-      }
-      PhaseScope ps(s, st, ESS_PHASE_CHAIN, s->cfg.sort_threads > 0 ? 1 : 2);
-      ess_status rc = launch_step<double>(s, p, st);
-      if (rc != ESS_OK) return rc;
-    }
+    const long long stride = (long long)n_rec * d;
+    ess_status rc = mixed(s)
+        ? step_one<float>(s, seed, (uint32_t)t, nullptr,
+                          rec ? static_cast<float*>(samples) + rec_off : nullptr, stride, st)
+        : step_one<double>(s, seed, (uint32_t)t, nullptr,
+                           rec ? static_cast<double*>(samples) + rec_off : nullptr, stride, st);
+    if (rc != ESS_OK) return rc;
+    ++it;
   }
   s->t_next += n_iter;
   s->host_steps += (long long)n * n_iter;
+  return ESS_OK;
+}
+
+ess_status ess_set_graphs(ess_state* s, int enable) {
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  s->use_graphs = enable != 0;
+  return ESS_OK;
+}
+
+ess_status ess_graph_launches(const ess_state* s, long long* launches) {
+  if (!s || !launches) return fail(ESS_ERR_ARG, "NULL argument");
+  *launches = s->graph_launches;
   return ESS_OK;
 }
 

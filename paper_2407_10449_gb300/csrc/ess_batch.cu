@@ -424,8 +424,6 @@ ess_status bgraph_period(ess_batch* s, uint64_t seed, cudaStream_t st) {
   return ESS_OK;
 }
 
-__global__ void set_u32_kernel(unsigned* p, unsigned v) { *p = v; }
-
 template <typename T>
 ess_status brun(ess_batch* s, double* X, int t0, int n_iter, uint64_t seed, void* samples,
                 int record_every, cudaStream_t st) {
@@ -444,8 +442,7 @@ ess_status brun(ess_batch* s, double* X, int t0, int n_iter, uint64_t seed, void
   while (it < n_iter) {
     const int t = t0 + it;
     if (graphs_ok && t % k == 0 && t != fresh && n_iter - it >= k) {
-      set_u32_kernel<<<1, 1, 0, st>>>(s->t_dev, (unsigned)t);
-      BESS_CUDA(cudaGetLastError());
+      BESS_CUDA(ess::launch_set_t(s->t_dev, (unsigned)t, st));
       while (n_iter - it >= k) {
         rc = bgraph_period<T>(s, seed, st);
         if (rc != ESS_OK) return rc;

@@ -11,15 +11,17 @@
 namespace ess {
 
 // ---------------------------------------------------------------- draws ----
-// nu[c, j] for chains chain0 .. chain0 + n_chains - 1 at step t (row stride ld).
+// nu[c, j] for chains chain0 .. chain0 + n_chains - 1 at step t (row stride ld);
+// with t_dev set the step index is t + *t_dev (replayable CUDA graphs).
 cudaError_t launch_draw_nu_f64(double* nu, int n_chains, int d, int ld, uint64_t seed,
-                               uint32_t t, uint32_t problem, uint32_t chain0, cudaStream_t s);
+                               uint32_t t, uint32_t problem, uint32_t chain0, cudaStream_t s,
+                               const unsigned* t_dev = nullptr);
 // float nu plus (if split != nullptr) the two-way fp16 split of nu * kNuSplitScale
 // (h0 = fp16(y), h1 = fp16(y - h0)), rows of ld16 elements; columns
 // d .. ld16 - 1 of the split are left untouched.
 cudaError_t launch_draw_nu_f32(float* nu, int ld, __half* const split[2], int ld16, int n_chains,
                                int d, uint64_t seed, uint32_t t, uint32_t problem, uint32_t chain0,
-                               cudaStream_t s);
+                               cudaStream_t s, const unsigned* t_dev = nullptr);
 cudaError_t launch_philox_blocks(uint64_t seed, uint32_t chain, uint32_t t, uint32_t problem,
                                  uint32_t stream, int n_blocks, uint32_t* out, cudaStream_t s);
 
@@ -223,8 +225,9 @@ cudaError_t launch_batch_refresh(const BatchItem* items, int n_items, int* queue
 // status |= kStatusInfeasible if any P64 row entry exceeds b.
 cudaError_t launch_batch_check(const ChainDesc* desc, int n_chains, const double* P64,
                                const double* b64, int* status, cudaStream_t s);
-// *t_dev += by (advances the step index of a replayed CUDA graph).
+// *t_dev += by (advances the step index of a replayed CUDA graph); *t_dev = v.
 cudaError_t launch_advance_t(unsigned* t_dev, unsigned by, cudaStream_t s);
+cudaError_t launch_set_t(unsigned* t_dev, unsigned v, cudaStream_t s);
 
 // Threads per chain the chain-step kernel uses for m constraints (0 if m is
 // beyond the supported maximum), and the dynamic shared memory it needs.

@@ -324,6 +324,7 @@ __global__ void batch_check_kernel(const ChainDesc* __restrict__ desc, int n_cha
 }
 
 __global__ void advance_t_kernel(unsigned* t_dev, unsigned by) { *t_dev += by; }
+__global__ void set_t_kernel(unsigned* t_dev, unsigned v) { *t_dev = v; }
 
 }  // namespace
 
@@ -362,6 +363,11 @@ cudaError_t launch_batch_check(const ChainDesc* desc, int n_chains, const double
 
 cudaError_t launch_advance_t(unsigned* t_dev, unsigned by, cudaStream_t s) {
   advance_t_kernel<<<1, 1, 0, s>>>(t_dev, by);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_t(unsigned* t_dev, unsigned v, cudaStream_t s) {
+  set_t_kernel<<<1, 1, 0, s>>>(t_dev, v);
   return cudaGetLastError();
 }
 

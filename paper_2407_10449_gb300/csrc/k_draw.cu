@@ -14,10 +14,12 @@ __device__ __forceinline__ uint2 pack4(const __half (&v)[4]) {
 
 // One thread per (chain, Philox block): 4 consecutive coordinates.
 __global__ void draw_nu_f64_kernel(double* __restrict__ nu, int n_chains, int d, int ld,
-                                   uint64_t seed, uint32_t t, uint32_t problem, uint32_t chain0) {
+                                   uint64_t seed, uint32_t t, const unsigned* t_dev,
+                                   uint32_t problem, uint32_t chain0) {
   const int nblk = (d + 3) >> 2;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long long)n_chains * nblk) return;
+  if (t_dev) t += *t_dev;
   const int c = (int)(gid / nblk), n = (int)(gid % nblk);
   uint32_t r[4];
   rng_block(seed, (uint32_t)n, chain0 + (uint32_t)c, t, problem, 0u, r);
@@ -35,10 +37,12 @@ __global__ void draw_nu_f64_kernel(double* __restrict__ nu, int n_chains, int d,
 
 __global__ void draw_nu_f32_kernel(float* __restrict__ nu, int ld, __half* __restrict__ h0,
                                    __half* __restrict__ h1, int ld16, int n_chains, int d,
-                                   uint64_t seed, uint32_t t, uint32_t problem, uint32_t chain0) {
+                                   uint64_t seed, uint32_t t, const unsigned* t_dev,
+                                   uint32_t problem, uint32_t chain0) {
   const int nblk = (d + 3) >> 2;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long long)n_chains * nblk) return;
+  if (t_dev) t += *t_dev;
   const int c = (int)(gid / nblk), n = (int)(gid % nblk);
   uint32_t r[4];
   rng_block(seed, (uint32_t)n, chain0 + (uint32_t)c, t, problem, 0u, r);
@@ -135,22 +139,24 @@ inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block 
 }  // namespace
 
 cudaError_t launch_draw_nu_f64(double* nu, int n_chains, int d, int ld, uint64_t seed, uint32_t t,
-                               uint32_t problem, uint32_t chain0, cudaStream_t s) {
+                               uint32_t problem, uint32_t chain0, cudaStream_t s,
+                               const unsigned* t_dev) {
   const long long n = (long long)n_chains * ((d + 3) / 4);
   if (n == 0) return cudaSuccess;
-  draw_nu_f64_kernel<<<grid_for(n, 256), 256, 0, s>>>(nu, n_chains, d, ld, seed, t, problem, chain0);
+  draw_nu_f64_kernel<<<grid_for(n, 256), 256, 0, s>>>(nu, n_chains, d, ld, seed, t, t_dev,
+                                                      problem, chain0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_draw_nu_f32(float* nu, int ld, __half* const split[2], int ld16, int n_chains,
                                int d, uint64_t seed, uint32_t t, uint32_t problem, uint32_t chain0,
-                               cudaStream_t s) {
+                               cudaStream_t s, const unsigned* t_dev) {
   const long long n = (long long)n_chains * ((d + 3) / 4);
   if (n == 0) return cudaSuccess;
   __half* h0 = split ? split[0] : nullptr;
   __half* h1 = split ? split[1] : nullptr;
   draw_nu_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(nu, ld, h0, h1, ld16, n_chains, d, seed, t,
-                                                      problem, chain0);
+                                                      t_dev, problem, chain0);
   return cudaGetLastError();
 }
 

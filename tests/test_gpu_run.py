@@ -79,6 +79,28 @@ def test_split_run_is_bit_identical(form):
 
 
 @pytest.mark.parametrize("form", FORMS)
+def test_graph_replay_is_bit_identical(form):
+    """Refresh periods replayed from a CUDA graph give the chains of plain
+    launches, bit for bit (start off a period boundary, end inside one)."""
+    inst = workloads.medium(n_chains=96)
+    out = []
+    for graphs in (True, False):
+        s = ess.Sampler(inst.A, inst.b, precision=form, refresh_k=8)
+        try:
+            ess.ess_set_graphs(s.state, graphs)
+            X = dev(inst.X0)
+            s.run(X, 45, seed=7, t0=3)
+            out.append(host(X))
+            n_graph = ess.ess_graph_launches(s.state)
+        finally:
+            s.close()
+        # steps 3..47: steps 3..7 run plain, the periods starting at 8, 16, 24,
+        # 32 and 40 replay
+        assert n_graph == (5 if graphs else 0)
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("form", FORMS)
 def test_every_iterate_feasible(form):
     inst = workloads.medium(n_chains=128)
     import torch
