@@ -49,15 +49,27 @@ constexpr int BK = 64;              // 16-bit elements per 128-byte swizzle row
 constexpr int kThreads = 192;       // producer warp, MMA warp, 4 epilogue warps
 constexpr int kRefreshBN = 64;      // tile width of the exact refresh
 constexpr int kMaxSlices = 7;       // operand slices of the exact refresh
-constexpr int kMaxPasses = 28;      // products per launch
+constexpr int kMaxRounds = 4;       // refresh rounds (<= 8 slice pairs each)
+// shared memory of one refresh stage: the x and A slice tiles of one round
+constexpr uint32_t kRefreshStage = 112u * 1024u;
 // kModeSum: q = A nu (FP16x3).  A stage holds one K block of the two nu
 //   slices and the two A slices; three products go into two accumulators.
-// kModePairs: exact refresh, one (x slice, A slice) pair per stage.
+// kModePairs: exact refresh in rounds of up to 8 slice pairs, each pair in its
+//   own 64-column TMEM accumulator; a stage holds one K block of every slice
+//   tile the round needs.
 enum { kModeSum = 0, kModePairs = 1 };
 
-struct PassDesc {             // pairs mode: one slice pair per pass
-  unsigned char xi, bi;       // slice indices of the two operands
-  unsigned char shift;        // weight 2^-shift
+// Pairs mode: one MMA of x slice tile xs with the na A slice tiles a0 ..
+// a0 + na - 1 stacked as one N = 64 na operand, into accumulator blocks
+// col .. col + na - 1 (64 columns each; one block per slice pair).
+struct RefreshGroup {
+  unsigned char xs, a0, na, col;
+};
+struct RefreshRound {
+  unsigned char nx, na, ngroups, npairs;  // x tiles, A tiles (slices 0 .. na-1), groups, pairs
+  unsigned char x[kMaxSlices];            // x slice of each loaded x tile
+  RefreshGroup g[8];
+  unsigned char shift[8];                 // accumulator block j holds a pair of weight 2^-shift
 };
 
 struct TcMaps {
@@ -66,8 +78,9 @@ struct TcMaps {
 };
 
 struct TcArgs {
-  int n_rows, n_cols, kblocks, npass, ngroups;
-  PassDesc pass[kMaxPasses];
+  int n_rows, n_cols, kblocks, ngroups;
+  int nrounds;                // pairs mode
+  RefreshRound round[kMaxRounds];
   float* Q;                   // sum mode output
   int ldq;
   const float* row_scale;     // t_c per chain (sum mode: 1 / t_c, or nullptr: row_const)
@@ -232,7 +245,7 @@ constexpr uint32_t tmem_cols_for(int groups) {
 
 template <int BN, int MODE>
 constexpr uint32_t stage_bytes() {
-  return (MODE == kModeSum ? 2u : 1u) * (uint32_t)(BM + BN) * BK * 2u;
+  return MODE == kModeSum ? 2u * (uint32_t)(BM + BN) * BK * 2u : kRefreshStage;
 }
 
 template <int BN, int STAGES, int MODE>
@@ -241,8 +254,8 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
   constexpr uint32_t A_BYTES = BM * BK * 2;
   constexpr uint32_t B_BYTES = BN * BK * 2;
   constexpr uint32_t STAGE_BYTES = stage_bytes<BN, MODE>();
-  constexpr int GROUPS = 2;  // sum mode: up to 2 accumulators; pairs mode: 2 buffers
-  constexpr uint32_t TMEM_COLS = tmem_cols_for<BN>(GROUPS);
+  // sum mode: 2 accumulators of BN columns; pairs mode: 8 blocks of 64 columns
+  constexpr uint32_t TMEM_COLS = MODE == kModeSum ? tmem_cols_for<BN>(2) : 512u;
   static_assert(B_BYTES % 1024 == 0, "BN must be a multiple of 8");
   static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "BN in {32, ..., 256}, multiple of 32");
 
@@ -283,8 +296,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_d = *tmem_slot;
-  const int npass = args.npass, kblocks = args.kblocks;
-  const int total = kblocks * npass;
+  const int kblocks = args.kblocks;
 
   if (warp == 0 && lane == 0 && MODE == kModeSum) {
     // ---------------- TMA producer (sum mode): 4 tiles per K block ----------------
@@ -353,64 +365,83 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
     }
     umma_commit(accf_bar(0));
   } else if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer (pairs mode) ----------------
-    int last_round[STAGES];
+    // ---------------- TMA producer (pairs mode): one round after another ----------------
+    bool loaded[STAGES];
+    uint32_t last_phase[STAGES];
 #pragma unroll
-    for (int s = 0; s < STAGES; ++s) last_round[s] = -1;
-    for (int it = 0; it < total; ++it) {
-      const int s = it % STAGES;
-      const int round = it / STAGES;
-      if (round > 0 && !mbar_wait(empty_bar(s), (uint32_t)((round - 1) & 1))) {
-        *abort_flag = 1;
-        break;
+    for (int j = 0; j < STAGES; ++j) loaded[j] = false;
+    int s = 0, count = 0;
+    uint32_t phase = 0;
+    for (int r = 0; r < args.nrounds && !*abort_flag; ++r) {
+      const RefreshRound& R = args.round[r];
+      const uint32_t bytes = R.nx * A_BYTES + R.na * B_BYTES;
+      for (int kb = 0; kb < kblocks; ++kb, ++count) {
+        if (count >= STAGES && !mbar_wait(empty_bar(s), phase ^ 1u)) {
+          *abort_flag = 1;
+          break;
+        }
+        if (*abort_flag) break;
+        const uint32_t sa = sbase + s * STAGE_BYTES;
+        mbar_expect_tx(full_bar(s), bytes);
+        for (int i = 0; i < R.nx; ++i)
+          tma_load_2d(sa + i * A_BYTES, &maps.x[R.x[i]], kb * BK, m0, full_bar(s));
+        for (int j = 0; j < R.na; ++j)
+          tma_load_2d(sa + R.nx * A_BYTES + j * B_BYTES, &maps.b[j], kb * BK, n0, full_bar(s));
+        loaded[s] = true;
+        last_phase[s] = phase;
+        if (++s == STAGES) {
+          s = 0;
+          phase ^= 1u;
+        }
       }
-      if (*abort_flag) break;
-      const int pass = it / kblocks, kb = it % kblocks;
-      const PassDesc pd = args.pass[pass];
-      const uint32_t sa = sbase + s * STAGE_BYTES;
-      mbar_expect_tx(full_bar(s), STAGE_BYTES);
-      tma_load_2d(sa, &maps.x[pd.xi], kb * BK, m0, full_bar(s));
-      tma_load_2d(sa + A_BYTES, &maps.b[pd.bi], kb * BK, n0, full_bar(s));
-      last_round[s] = round;
     }
     if (*abort_flag) {
       // let every copy this thread issued land before the CTA exits
 #pragma unroll
-      for (int s = 0; s < STAGES; ++s)
-        if (last_round[s] >= 0) (void)mbar_wait(full_bar(s), (uint32_t)(last_round[s] & 1));
+      for (int j = 0; j < STAGES; ++j)
+        if (loaded[j]) (void)mbar_wait(full_bar(j), last_phase[j]);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer (pairs mode) ----------------
-    constexpr uint32_t idesc = idesc_f16(BM, BN, true);
-    for (int it = 0; it < total; ++it) {
-      const int s = it % STAGES;
-      const int round = it / STAGES;
-      const int pass = it / kblocks, kb = it % kblocks;
-      const int buf = pass & 1;
-      const uint32_t acc_col = (uint32_t)(buf * BN);
-      const bool fresh = kb == 0;  // first MMA into this buffer: overwrite
-      if (kb == 0 && pass >= 2 &&
-          !mbar_wait(acce_bar(buf), (uint32_t)(((pass >> 1) - 1) & 1))) {
-        *abort_flag = 1;
-        break;
-      }
-      if (kb == 0) tc_fence_after();
-      if (!mbar_wait(full_bar(s), (uint32_t)(round & 1))) {
+    int s = 0;
+    uint32_t phase = 0;
+    for (int r = 0; r < args.nrounds; ++r) {
+      const RefreshRound& R = args.round[r];
+      // the epilogue must have read round r - 1 out of TMEM
+      if (r > 0 && !mbar_wait(acce_bar(0), (uint32_t)((r - 1) & 1))) {
         *abort_flag = 1;
         break;
       }
       tc_fence_after();
-      const uint32_t sa = sbase + s * STAGE_BYTES;
-      const uint64_t adesc = smem_desc_sw128(sa);
-      const uint64_t bdesc = smem_desc_sw128(sa + A_BYTES);
+      bool ok = true;
+      for (int kb = 0; kb < kblocks; ++kb) {
+        if (!mbar_wait(full_bar(s), phase)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = sbase + s * STAGE_BYTES;
+        for (int g = 0; g < R.ngroups; ++g) {
+          const RefreshGroup G = R.g[g];
+          const uint64_t adesc = smem_desc_sw128(sa + G.xs * A_BYTES);
+          const uint64_t bdesc = smem_desc_sw128(sa + R.nx * A_BYTES + G.a0 * B_BYTES);
+          const uint32_t idesc = idesc_f16(BM, BN * G.na, true);
 #pragma unroll
-      for (int k = 0; k < BK / 16; ++k) {
-        // each K = 16 step advances 32 bytes inside the swizzled row
-        umma_bf16(tmem_d + acc_col, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc,
-                  (fresh && k == 0) ? 0u : 1u);
+          for (int k = 0; k < BK / 16; ++k)  // each K = 16 step advances 32 bytes
+            umma_bf16(tmem_d + (uint32_t)(G.col * BN), adesc + (uint64_t)(2 * k),
+                      bdesc + (uint64_t)(2 * k), idesc, (kb == 0 && k == 0) ? 0u : 1u);
+        }
+        umma_commit(empty_bar(s));
+        if (++s == STAGES) {
+          s = 0;
+          phase ^= 1u;
+        }
       }
-      umma_commit(empty_bar(s));
-      if (kb == kblocks - 1) umma_commit(accf_bar(buf));
+      if (!ok) {
+        *abort_flag = 1;
+        break;
+      }
+      umma_commit(accf_bar(0));
     }
   } else if (warp >= 2) {
     // ---------------- epilogue warps 2..5: TMEM lane quarter warp % 4 ----------------
@@ -458,38 +489,41 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
         }
       }
     } else {
-      // exact integer products of one slice pair per buffer, accumulated
-      // error-free into (hi, lo) float pairs with the pair's power-of-two weight
+      // exact integer products of the slice pairs, one 64-column block each,
+      // accumulated error-free into (hi, lo) float pairs with the pair's
+      // power-of-two weight, round by round
       float hi[BN], lo[BN];
 #pragma unroll
       for (int j = 0; j < BN; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
       bool ok = true;
-      for (int pass = 0; pass < npass; ++pass) {
-        const int buf = pass & 1;
-        if (*abort_flag || !mbar_wait(accf_bar(buf), (uint32_t)((pass >> 1) & 1))) {
+      for (int r = 0; r < args.nrounds; ++r) {
+        if (*abort_flag || !mbar_wait(accf_bar(0), (uint32_t)(r & 1))) {
           *abort_flag = 1;
           ok = false;
           break;
         }
         tc_fence_after();
-        // 2^-shift as a float (shift <= 126)
-        const float w = __uint_as_float((uint32_t)(127 - args.pass[pass].shift) << 23);
+        const RefreshRound& R = args.round[r];
+        for (int pj = 0; pj < R.npairs; ++pj) {
+          // 2^-shift as a float (shift <= 126)
+          const float w = __uint_as_float((uint32_t)(127 - R.shift[pj]) << 23);
 #pragma unroll
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-          uint32_t v[32];
-          tmem_ld_32cols(lane_base + (uint32_t)(buf * BN + c0), v);
-          tmem_ld_wait();
+          for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld_32cols(lane_base + (uint32_t)(pj * BN + c0), v);
+            tmem_ld_wait();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            float sum, err;
-            two_sum(hi[c0 + j], __uint_as_float(v[j]) * w, sum, err);
-            hi[c0 + j] = sum;
-            lo[c0 + j] += err;
+            for (int j = 0; j < 32; ++j) {
+              float sum, err;
+              two_sum(hi[c0 + j], __uint_as_float(v[j]) * w, sum, err);
+              hi[c0 + j] = sum;
+              lo[c0 + j] += err;
+            }
           }
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(acce_bar(buf));
+        if (lane == 0) mbar_arrive(acce_bar(0));
       }
       if (ok && row < args.n_rows) {
         const float rs = args.row_scale[row];
@@ -862,7 +896,6 @@ cudaError_t tc_gemm_q(TcGemmPlan* plan, __half* const nu[2], const float* nu_uns
   a.n_cols = plan->m;
   a.kblocks = (plan->d + BK - 1) / BK;
   // accumulator 0: h0.a0; accumulator 1: h1.a0 + h0.a1 (weight 2^-11 each)
-  a.npass = 3;
   a.ngroups = 2;
   a.Q = Q;
   a.ldq = ldq;
@@ -896,19 +929,44 @@ cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
   a.n_rows = n_chains;
   a.n_cols = plan->m;
   a.kblocks = (plan->d + BK - 1) / BK;
-  // slice pairs (k, l), k + l <= K + 1 (1-based), smallest weight first
-  int np = 0;
-  for (int sum = K + 1; sum >= 2; --sum)
-    for (int k = 1; k < sum; ++k) {
-      const int l = sum - k;
-      if (k > K || l > K) continue;
-      a.pass[np].xi = (unsigned char)(l - 1);
-      a.pass[np].bi = (unsigned char)(k - 1);
-      a.pass[np].shift = (unsigned char)(plan->w * sum);
-      ++np;
+  // slice pairs (x slice l, A slice k), k + l <= K + 1 (1-based), grouped into
+  // rounds of at most 8 pairs whose tiles fit one stage; within a round the
+  // pairs of one x slice with consecutive A slices share one MMA (N <= 256)
+  int nr = 0;
+  auto open_round = [&]() {
+    std::memset(&a.round[nr], 0, sizeof(RefreshRound));
+    ++nr;
+  };
+  open_round();
+  for (int l = 1; l <= K; ++l)
+    for (int k = 1; k + l <= K + 1; ++k) {
+      RefreshRound* R = &a.round[nr - 1];
+      const bool new_x = R->nx == 0 || R->x[R->nx - 1] != (unsigned char)(l - 1);
+      const int nx = R->nx + (new_x ? 1 : 0);
+      const int na = std::max<int>(R->na, k);
+      const uint32_t bytes = (uint32_t)nx * BM * BK * 2 + (uint32_t)na * kRefreshBN * BK * 2;
+      if (R->npairs == 8 || bytes > kRefreshStage) {
+        if (nr == kMaxRounds) return cudaErrorInvalidValue;
+        open_round();
+        R = &a.round[nr - 1];
+      }
+      if (R->nx == 0 || R->x[R->nx - 1] != (unsigned char)(l - 1)) R->x[R->nx++] = (unsigned char)(l - 1);
+      R->na = (unsigned char)std::max<int>(R->na, k);
+      const int col = R->npairs++;
+      R->shift[col] = (unsigned char)(plan->w * (k + l));
+      RefreshGroup* G = R->ngroups ? &R->g[R->ngroups - 1] : nullptr;
+      if (G && G->xs == R->nx - 1 && G->a0 + G->na == k - 1 && G->na < 4 && G->col + G->na == col) {
+        ++G->na;
+      } else {
+        G = &R->g[R->ngroups++];
+        G->xs = (unsigned char)(R->nx - 1);
+        G->a0 = (unsigned char)(k - 1);
+        G->na = 1;
+        G->col = (unsigned char)col;
+      }
     }
-  a.npass = np;
-  a.ngroups = np;
+  a.nrounds = nr;
+  a.ngroups = 0;
   a.row_scale = row_scale;
   a.col_scale = plan->col_scale;
   a.P32 = P32;
