@@ -443,25 +443,28 @@ chain_warp_kernel(ChainParams<T> prm) {
             if (!(pn <= sv[k])) flags |= 1u << k;
           }
         }
-        for (int k = 0; k < kBatch; ++k) {
-        unsigned ball = __ballot_sync(kFull, (flags >> k) & 1u);
-        rechecks += __popc(ball);
-        while (ball) {
-          const int src = __ffs(ball) - 1;
-          ball &= ball - 1;
-          const int row = i0 + src + 32 * k;
-          const double* arow = v.A64 + (size_t)row * d;
-          double acc = 0.0;
-          for (int jj = lane; jj < d; jj += 32) {
-            const T xn = xrow[jj] * cs + nurow[jj] * sn;
-            acc = fma(arow[jj], (double)xn, acc);
-          }
+        // rows near their bound are rare: one vote per batch, then per slot
+        if (__any_sync(kFull, flags != 0u)) {
+          for (int k = 0; k < kBatch; ++k) {
+            unsigned ball = __ballot_sync(kFull, (flags >> k) & 1u);
+            rechecks += __popc(ball);
+            while (ball) {
+              const int src = __ffs(ball) - 1;
+              ball &= ball - 1;
+              const int row = i0 + src + 32 * k;
+              const double* arow = v.A64 + (size_t)row * d;
+              double acc = 0.0;
+              for (int jj = lane; jj < d; jj += 32) {
+                const T xn = xrow[jj] * cs + nurow[jj] * sn;
+                acc = fma(arow[jj], (double)xn, acc);
+              }
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-          const double res = acc - v.b64[row];
-          maxres = fmax(maxres, res);
-          violated |= res > 0.0;
-        }
+              for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+              const double res = acc - v.b64[row];
+              maxres = fmax(maxres, res);
+              violated |= res > 0.0;
+            }
+          }
         }
       }
       // x' is finite whenever theta, x and nu are (x_0 passes an FP64 check)
