@@ -367,6 +367,39 @@ def time_batch(ess, torch, insts, precision, steps, warmup, seed, peaks):
             "phases": phases, "stats": stats}
 
 
+def time_unwhiten(ess, torch, pb, n, peaks, reps=10):
+    """App. A map x = L u + mu on the GPU for one record of n samples (d x d L)."""
+    d = pb["L"].shape[0]
+    w = ess.Whitener(pb["L"], pb["mu"])
+    out = {}
+    g = torch.Generator(device="cuda").manual_seed(0)
+    for name, dt in (("float", torch.float32), ("double", torch.float64)):
+        U = torch.randn((n, d), generator=g, device="cuda", dtype=dt)
+        X = torch.empty_like(U)
+        for _ in range(3):
+            ess.ess_whitener_apply(w._w, U, X)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            ess.ess_whitener_apply(w._w, U, X)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        if dt == torch.float32:
+            flops = 3 * 2.0 * n * d * d  # three fp16 products (FP16x3)
+            peak = peaks["bf16_tflops_sustained"]
+        else:
+            flops = 2.0 * n * d * d
+            peak = FP64_TFLOPS_MEASURED
+        ach = flops / ms / 1e9
+        out[name] = {"ms": ms, "samples_per_s": n / (ms / 1e3), "achieved_tflops": ach,
+                     "peak_tflops": peak, "frac": ach / peak}
+    w.close()
+    return out
+
+
 def time_configs(ess, torch, workloads, peaks, seed):
     """The other configurations, both forms, short runs (parity-tested
     elsewhere; reported here with their phase rooflines)."""
@@ -392,6 +425,7 @@ def time_configs(ess, torch, workloads, peaks, seed):
                            "rejections": stats["rejections"],
                            "numeric_errors": stats["numeric_errors"]}
         out[name] = entry
+    out["probit_n2000_c4096"]["unwhiten"] = time_unwhiten(ess, torch, pb, 4096, peaks)
     insts = workloads.batched()
     entry = {}
     for form, steps in (("mixed", 64), ("fp64", 8)):

@@ -253,6 +253,25 @@ ess_status ess_unwhiten(const double *L, const double *mu, int d, int n, const d
                         double *X);
 
 /*
+ * App. A map x = L u + mu on the GPU for many samples (e.g. the recorded
+ * samples of a run in whitened coordinates).  ess_whitener_create copies L
+ * (host, d x d row-major, any square matrix) and mu (host, d, or NULL) to the
+ * current device; ess_whitener_apply computes X = U L^T + mu row by row for
+ * n rows of U (device, n x d, row-major):
+ *   u_double = 0: U and X float; the product runs on the tensor cores as the
+ *                 scaled FP16x3 GEMM of q = A nu (|error| <= (16 + d / 16)
+ *                 2^-24 sum_j |L_ij| |u_j| before the FP32 rounding of + mu);
+ *   u_double = 1: U and X double; FP64 fused multiply-adds.
+ * X must not overlap U.  Synchronous.  Errors: ESS_ERR_ARG for bad sizes or
+ * non-finite L or mu, ESS_ERR_TIMEOUT if a bounded device wait gave up.
+ */
+typedef struct ess_whitener ess_whitener;
+ess_status ess_whitener_create(const double *L, const double *mu, int d, ess_whitener **out);
+void ess_whitener_destroy(ess_whitener *whitener);
+ess_status ess_whitener_apply(ess_whitener *whitener, const void *U, int u_double, int n,
+                              void *X, void *cuda_stream);
+
+/*
  * One FP64 chain step that allocates no device memory (the paper has no
  * counterpart; this is a service for callers that may not call cudaMalloc,
  * e.g. plugins whose host framework owns the device-memory budget, request

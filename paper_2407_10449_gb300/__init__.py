@@ -44,6 +44,7 @@ EXPORTED = ("ess_default_config", "ess_create", "ess_destroy", "ess_limits", "es
             "ess_set_timing", "ess_get_timing", "ess_reset_timing",
             "ess_get_stats", "ess_reset_stats", "ess_whiten", "ess_unwhiten", "ess_step_noalloc",
             "ess_set_graphs", "ess_graph_launches",
+            "ess_whitener_create", "ess_whitener_destroy", "ess_whitener_apply",
             "ess_batch_create", "ess_batch_destroy", "ess_batch_run", "ess_batch_step_with_draws",
             "ess_batch_products", "ess_batch_get_stats", "ess_batch_reset_stats",
             "ess_batch_set_graphs", "ess_batch_set_timing", "ess_batch_get_timing",
@@ -127,6 +128,9 @@ def load(build_if_missing: bool = True):
             "ess_unwhiten": ([_dp, _dp, c_int, c_int, _dp, _dp], c_int),
             "ess_step_noalloc": ([_vp, _vp, c_int, c_int, _vp, _vp, _vp, c_int, _vp, _vp, _vp,
                                   _vp], c_int),
+            "ess_whitener_create": ([_dp, _dp, c_int, ctypes.POINTER(_vp)], c_int),
+            "ess_whitener_destroy": ([_vp], None),
+            "ess_whitener_apply": ([_vp, _vp, c_int, c_int, _vp, _vp], c_int),
             "ess_set_graphs": ([_vp, c_int], c_int),
             "ess_graph_launches": ([_vp, ctypes.POINTER(ctypes.c_longlong)], c_int),
             "ess_batch_create": ([c_int, _vp, _vp, _dp, _dp, ctypes.POINTER(ess_config),
@@ -317,6 +321,58 @@ def ess_step_noalloc(A, b, X, nu, u, X_next, theta=None, rejected=None, stream=N
     _check(load().ess_step_noalloc(_ptr(A), _ptr(b), d, m, _ptr(X), _ptr(nu), _ptr(u), n,
                                    _ptr(X_next), _ptr(theta), _ptr(rejected),
                                    _stream_ptr(stream)))
+
+
+def ess_whitener_create(L, mu=None):
+    L = _np64(L)
+    d = L.shape[0]
+    mu_p = None if mu is None else _np64(mu)
+    w = _vp()
+    _check(load().ess_whitener_create(L.ctypes.data_as(_dp),
+                                      None if mu_p is None else mu_p.ctypes.data_as(_dp), d,
+                                      ctypes.byref(w)))
+    return w
+
+
+def ess_whitener_destroy(w):
+    load().ess_whitener_destroy(w)
+
+
+def ess_whitener_apply(w, U, X, stream=None):
+    """X = U L^T + mu for CUDA tensors U, X (n x d, both float32 or both float64)."""
+    import torch
+    u_double = 1 if U.dtype == torch.float64 else 0
+    if X.dtype != U.dtype:
+        raise ValueError("U and X must have the same dtype")
+    n = U.shape[0] if U.dim() > 1 else 1
+    _check(load().ess_whitener_apply(w, _ptr(U), u_double, n, _ptr(X), _stream_ptr(stream)))
+
+
+class Whitener:
+    """x = L u + mu on the GPU (App. A) for batches of samples."""
+
+    def __init__(self, L, mu=None):
+        self.L = _np64(L)
+        self.d = self.L.shape[0]
+        self._w = ess_whitener_create(self.L, mu)
+
+    def close(self):
+        if self._w is not None:
+            ess_whitener_destroy(self._w)
+            self._w = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __call__(self, U, stream=None):
+        import torch
+        U = U.reshape(-1, self.d).contiguous()
+        X = torch.empty_like(U)
+        ess_whitener_apply(self._w, U, X, stream)
+        return X
 
 
 def ess_set_graphs(state, enable=True):
