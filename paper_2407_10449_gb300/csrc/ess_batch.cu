@@ -84,7 +84,11 @@ struct ess_batch {
   double* A64 = nullptr;
   float* A32 = nullptr;          // mixed form: A rounded to float (q GEMM, refresh hi part)
   float* Alo = nullptr;          // mixed form: A - A32 rounded to float (refresh lo part)
-  void* AT = nullptr;            // K-major A in the step's type (q GEMM operand)
+  void* AT = nullptr;            // FP64 form: K-major A (operand of the FMA q GEMM)
+  __half* Ah[2] = {nullptr, nullptr};  // mixed form: fp16 splits of A s_i (rows of dpad)
+  float* arow_unscale = nullptr;       // mixed form: 1 / s_i per row
+  std::vector<long long> ah_off;       // per problem, into Ah
+  std::vector<int> dpad;               // per problem: d rounded up to 8
   double* b64 = nullptr;
   float* b32 = nullptr;
   double* anorm = nullptr;
@@ -96,6 +100,8 @@ struct ess_batch {
   ChainDesc* desc = nullptr;
   BatchItem* items = nullptr;
   int n_items = 0;
+  BatchItem* mitems = nullptr;   // mixed form: items of the tensor-core q GEMM
+  int n_mitems = 0;
   int layout_version = 0;
   // work buffers (device)
   int cap_n = 0, cap_items = 0;
@@ -105,6 +111,9 @@ struct ess_batch {
   void* P = nullptr;
   void* P2 = nullptr;
   void* Q = nullptr;
+  __half* H[2] = {nullptr, nullptr};  // mixed form: fp16 splits of nu (rows of dpad)
+  float* chain_unscale = nullptr;     // per chain 1 / t of caller-supplied nu
+  long long cap_h = 0;
   double* P64 = nullptr;
   int* ovf = nullptr;            // [0] overflow count, [1..] overflow chains
   int* queue = nullptr;          // work-queue head of the grouped GEMMs
@@ -183,12 +192,17 @@ void free_work(ess_batch* s) {
   drop_graphs(s);
   bfree(s->desc);
   bfree(s->items);
+  bfree(s->mitems);
   if (s->X) cudaFree(s->X);
   if (s->NU) cudaFree(s->NU);
   if (s->P) cudaFree(s->P);
   if (s->P2) cudaFree(s->P2);
   if (s->Q) cudaFree(s->Q);
   s->X = s->NU = s->P = s->P2 = s->Q = nullptr;
+  bfree(s->H[0]);
+  bfree(s->H[1]);
+  bfree(s->chain_unscale);
+  s->cap_h = 0;
   bfree(s->P64);
   bfree(s->ovf);
   s->cap_n = s->cap_items = 0;
@@ -205,10 +219,11 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
     if (nc[p] < 0) return bfail(ESS_ERR_ARG, "negative chain count");
   if (nc == s->nc && s->desc) return ESS_OK;
   std::vector<ChainDesc> desc;
-  std::vector<BatchItem> items;
-  long long xo = 0, po = 0;
+  std::vector<BatchItem> items, mitems;
+  long long xo = 0, po = 0, ho = 0;
   for (int p = 0; p < s->np; ++p) {
-    const int d = s->d[p], m = s->m[p];
+    const int d = s->d[p], m = s->m[p], dp = s->dpad[p];
+    const int c_first = (int)desc.size();
     for (int k = 0; k < nc[p]; ++k) {
       ChainDesc cd{};
       cd.d = d;
@@ -219,6 +234,8 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
       cd.p_off = po + (long long)k * m;
       cd.a_off = s->a_off[p];
       cd.b_off = s->b_off[p];
+      cd.dpad = dp;
+      cd.h_off = ho + (long long)k * dp;
       desc.push_back(cd);
     }
     const int ct = ess::batch_ctile(nc[p]), rt = ess::batch_rtile(ct);
@@ -238,21 +255,51 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
         it.mpad = (m + 3) & ~3;
         it.x_off = xo + (long long)c0 * d;
         it.p_off = po + (long long)c0 * m;
+        it.dpad = dp;
+        it.ah_off = bmixed(s) ? s->ah_off[p] : 0;
+        it.xh_off = ho + (long long)c0 * dp;
+        it.c_first = c_first + c0;
         items.push_back(it);
       }
+    if (bmixed(s)) {
+      const int mrt = ess::batch_mma_rtile(ct);
+      for (int c0 = 0; c0 < nc[p]; c0 += ct)
+        for (int r0 = 0; r0 < m; r0 += mrt) {
+          BatchItem it{};
+          it.row0 = r0;
+          it.rows = std::min(mrt, m - r0);
+          it.chains = std::min(ct, nc[p] - c0);
+          it.rtile = mrt;
+          it.ctile = ct;
+          it.d = d;
+          it.m = m;
+          it.b_off = s->b_off[p];
+          it.p_off = po + (long long)c0 * m;
+          it.dpad = dp;
+          it.ah_off = s->ah_off[p];
+          it.xh_off = ho + (long long)c0 * dp;
+          it.c_first = c_first + c0;
+          mitems.push_back(it);
+        }
+    }
     xo += (long long)nc[p] * d;
     po += (long long)nc[p] * m;
+    ho += (long long)nc[p] * dp;
   }
   // largest items first: the work queue then ends on small items (LPT order)
-  std::stable_sort(items.begin(), items.end(), [](const BatchItem& a, const BatchItem& b) {
+  auto by_cost = [](const BatchItem& a, const BatchItem& b) {
     return (long long)a.rows * a.chains * a.d > (long long)b.rows * b.chains * b.d;
-  });
+  };
+  std::stable_sort(items.begin(), items.end(), by_cost);
+  std::stable_sort(mitems.begin(), mitems.end(), by_cost);
   const int n = (int)desc.size();
-  if (n > s->cap_n || xo > s->cap_x || po > s->cap_p || (int)items.size() > s->cap_items) {
+  if (n > s->cap_n || xo > s->cap_x || po > s->cap_p ||
+      (int)std::max(items.size(), mitems.size()) > s->cap_items || (bmixed(s) && ho > s->cap_h)) {
     free_work(s);
     const size_t e = belem(s);
     BESS_CUDA(balloc(&s->desc, std::max<size_t>(1, desc.size())));
-    BESS_CUDA(balloc(&s->items, std::max<size_t>(1, items.size())));
+    BESS_CUDA(balloc(&s->items, std::max<size_t>(1, std::max(items.size(), mitems.size()))));
+    BESS_CUDA(balloc(&s->mitems, std::max<size_t>(1, std::max(items.size(), mitems.size()))));
     BESS_CUDA(cudaMalloc(&s->X, std::max<long long>(1, xo) * e));
     BESS_CUDA(cudaMalloc(&s->NU, std::max<long long>(1, xo) * e));
     BESS_CUDA(cudaMalloc(&s->P, std::max<long long>(1, po) * e));
@@ -260,19 +307,31 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
     BESS_CUDA(cudaMalloc(&s->Q, std::max<long long>(1, po) * e));
     BESS_CUDA(balloc(&s->P64, std::max<long long>(1, po)));
     BESS_CUDA(balloc(&s->ovf, (size_t)n + 1));
+    if (bmixed(s)) {
+      for (auto& h : s->H) {
+        BESS_CUDA(balloc(&h, (size_t)std::max<long long>(1, ho)));
+        // the padding columns d .. dpad - 1 of every row stay zero
+        BESS_CUDA(cudaMemset(h, 0, sizeof(__half) * (size_t)std::max<long long>(1, ho)));
+      }
+      BESS_CUDA(balloc(&s->chain_unscale, std::max<size_t>(1, (size_t)n)));
+      s->cap_h = ho;
+    }
     s->cap_n = n;
     s->cap_x = xo;
     s->cap_p = po;
-    s->cap_items = (int)items.size();
+    s->cap_items = (int)std::max(items.size(), mitems.size());
   }
   if (!desc.empty())
     BESS_CUDA(cudaMemcpy(s->desc, desc.data(), sizeof(ChainDesc) * desc.size(), cudaMemcpyHostToDevice));
   if (!items.empty())
     BESS_CUDA(cudaMemcpy(s->items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
+  if (!mitems.empty())
+    BESS_CUDA(cudaMemcpy(s->mitems, mitems.data(), sizeof(BatchItem) * mitems.size(), cudaMemcpyHostToDevice));
   drop_graphs(s);
   s->nc = nc;
   s->n = n;
   s->n_items = (int)items.size();
+  s->n_mitems = (int)mitems.size();
   s->total_x = xo;
   s->total_p = po;
   ++s->layout_version;
@@ -307,6 +366,26 @@ ess_status brefresh(ess_batch* s, const T* X, bool drift, bool check, cudaStream
                                          check ? s->P64 : nullptr, s->anorm,
                                          drift ? &s->dstats->max_drift_bits : nullptr, st));
   if (check) BESS_CUDA(ess::launch_batch_check(s->desc, s->n, s->P64, s->b64, s->dstatus, st));
+  return ESS_OK;
+}
+
+// q = A nu for every chain.  Mixed form: FP16x3 on the tensor cores (the nu
+// splits come from the draw kernel, or from a per-chain split of a
+// caller-supplied nu when user_nu); FP64 form: FP64 FMAs.
+template <typename T>
+ess_status bq(ess_batch* s, bool user_nu, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (user_nu)
+      BESS_CUDA(ess::launch_batch_split(s->desc, s->n, static_cast<const float*>(s->NU), s->H[0],
+                                        s->H[1], s->chain_unscale, st));
+    BESS_CUDA(ess::launch_batch_q_mma(s->mitems, s->n_mitems, s->queue, s->Ah[0], s->Ah[1],
+                                      s->arow_unscale, s->H[0], s->H[1],
+                                      user_nu ? s->chain_unscale : nullptr,
+                                      static_cast<float*>(s->Q), st));
+  } else {
+    BESS_CUDA(ess::launch_batch_q<T>(s->items, s->n_items, s->queue, static_cast<const T*>(s->AT),
+                                     static_cast<const T*>(s->NU), static_cast<T*>(s->Q), st));
+  }
   return ESS_OK;
 }
 
@@ -359,12 +438,13 @@ ess_status bstep(ess_batch* s, uint64_t seed, uint32_t t, const unsigned* t_dev,
                  cudaStream_t st) {
   {
     BPhase ph(s, st, ESS_PHASE_DRAW);
-    BESS_CUDA(ess::launch_batch_draw<T>(s->desc, s->n, static_cast<T*>(s->NU), seed, t, t_dev, st));
+    BESS_CUDA(ess::launch_batch_draw<T>(s->desc, s->n, static_cast<T*>(s->NU), seed, t, t_dev, st,
+                                        s->H[0], s->H[1]));
   }
   {
     BPhase ph(s, st, ESS_PHASE_GEMM);
-    BESS_CUDA(ess::launch_batch_q<T>(s->items, s->n_items, s->queue, static_cast<const T*>(s->AT),
-                                     static_cast<const T*>(s->NU), static_cast<T*>(s->Q), st));
+    ess_status rc = bq<T>(s, false, st);
+    if (rc != ESS_OK) return rc;
   }
   ess::ChainParams<T> p = bparams<T>(s);
   p.seed = seed;
@@ -495,7 +575,7 @@ ess_status ess_batch_create(int n_problems, const int* d, const int* m, const do
   s->np = n_problems;
   s->cfg = c;
   cudaGetDevice(&s->device);
-  long long ta = 0, tat = 0;
+  long long ta = 0, tat = 0, tah = 0;
   int tb = 0;
   for (int p = 0; p < n_problems; ++p) {
     if (d[p] < 1 || m[p] < 1) {
@@ -508,6 +588,9 @@ ess_status ess_batch_create(int n_problems, const int* d, const int* m, const do
     s->b_off.push_back(tb);
     s->at_off.push_back(tat);
     tat += (long long)d[p] * ((m[p] + 3) & ~3);
+    s->dpad.push_back((d[p] + 7) & ~7);
+    s->ah_off.push_back(tah);
+    tah += (long long)m[p] * ((d[p] + 7) & ~7);
     ta += (long long)m[p] * d[p];
     tb += m[p];
     s->max_d = std::max(s->max_d, d[p]);
@@ -579,7 +662,39 @@ ess_status ess_batch_create(int n_problems, const int* d, const int* m, const do
     if (e == cudaSuccess) e = balloc(&s->b32, (size_t)tb);
     if (e == cudaSuccess) e = cudaMemcpy(s->b32, b32.data(), sizeof(float) * tb, cudaMemcpyHostToDevice);
   }
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && bmixed(s)) {
+    // fp16 splits of every row a_i s_i, s_i = 2^(15 - e_i) with max_j |a_ij| in
+    // [2^(e_i - 1), 2^e_i) (A rounded to float first), rows padded to dpad
+    std::vector<__half> h0((size_t)std::max<long long>(1, tah), __float2half_rn(0.f)), h1 = h0;
+    std::vector<float> ru(tb);
+    for (int p = 0; p < n_problems; ++p)
+      for (int i = 0; i < m[p]; ++i) {
+        const double* a = A + s->a_off[p] + (long long)i * d[p];
+        float mx = 0.f;
+        for (int j = 0; j < d[p]; ++j) mx = std::fmax(mx, std::fabs((float)a[j]));
+        int ex = 0;
+        if (mx > 0.f) (void)std::frexp(mx, &ex);
+        const float t = mx > 0.f ? std::ldexp(1.f, 15 - ex) : 1.f;
+        ru[s->b_off[p] + i] = mx > 0.f ? std::ldexp(1.f, ex - 15) : 0.f;
+        const size_t o = (size_t)(s->ah_off[p] + (long long)i * s->dpad[p]);
+        for (int j = 0; j < d[p]; ++j) {
+          const float y = (float)a[j] * t;
+          const __half hv = __float2half_rn(y);
+          h0[o + j] = hv;
+          h1[o + j] = __float2half_rn(y - __half2float(hv));
+        }
+      }
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = balloc(&s->Ah[k], h0.size());
+      if (e == cudaSuccess)
+        e = cudaMemcpy(s->Ah[k], (k ? h1 : h0).data(), sizeof(__half) * h0.size(),
+                       cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = balloc(&s->arow_unscale, (size_t)tb);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(s->arow_unscale, ru.data(), sizeof(float) * tb, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess && !bmixed(s)) {
     // K-major copy of every A_p (rows padded to a multiple of 4 with zeros)
     std::vector<unsigned char> at((size_t)tat * esz, 0);
     for (int p = 0; p < n_problems; ++p) {
@@ -618,6 +733,9 @@ void ess_batch_destroy(ess_batch* s) {
   bfree(s->A32);
   bfree(s->Alo);
   if (s->AT) cudaFree(s->AT);
+  bfree(s->Ah[0]);
+  bfree(s->Ah[1]);
+  bfree(s->arow_unscale);
   bfree(s->b64);
   bfree(s->b32);
   bfree(s->anorm);
@@ -669,8 +787,8 @@ ess_status ess_batch_step_with_draws(ess_batch* s, const int* n_chains, const do
     ess_status r = brefresh<T>(s, Xw, false, true, st);
     if (r == ESS_OK) r = bread_status(s, st);
     if (r != ESS_OK) return r;
-    BESS_CUDA(ess::launch_batch_q<T>(s->items, s->n_items, s->queue, static_cast<const T*>(s->AT),
-                                     static_cast<const T*>(s->NU), static_cast<T*>(s->Q), st));
+    r = bq<T>(s, true, st);
+    if (r != ESS_OK) return r;
     ess::ChainParams<T> p = bparams<T>(s);
     p.U = u;
     p.theta_out = theta;
@@ -706,9 +824,8 @@ ess_status ess_batch_products(ess_batch* s, const int* n_chains, const double* X
     }
     if (Q) {
       BESS_CUDA((ess::launch_convert<double, T>(nu, tx, static_cast<T*>(s->NU), tx, 1, tx, st)));
-      BESS_CUDA(ess::launch_batch_q<T>(s->items, s->n_items, s->queue,
-                                       static_cast<const T*>(s->AT),
-                                       static_cast<const T*>(s->NU), static_cast<T*>(s->Q), st));
+      ess_status r = bq<T>(s, true, st);
+      if (r != ESS_OK) return r;
       BESS_CUDA((ess::launch_convert<T, double>(static_cast<const T*>(s->Q), tp, Q, tp, 1, tp, st)));
     }
     BESS_CUDA(cudaStreamSynchronize(st));

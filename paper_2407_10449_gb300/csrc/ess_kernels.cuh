@@ -63,7 +63,8 @@ struct ChainDesc {
   long long p_off;      // element offset of the chain's row in P_in, P_out, Q
   long long a_off;      // element offset of the problem's A64 (m x d, row-major)
   int b_off;            // element offset of the problem's b, b64, anorm, slack
-  int pad_;
+  int dpad;             // row stride of the fp16 nu slices (d rounded up to 8)
+  long long h_off;      // element offset of the chain's row in the fp16 nu slices
 };
 
 template <typename T>
@@ -197,18 +198,43 @@ struct BatchItem {
   long long p_off;     // element offset of the first chain's row in P / Q
   long long at_off;    // element offset of the problem's K-major copy of A (q GEMM)
   int mpad;            // row stride of that copy: m rounded up to 4 (zero padded)
+  int dpad;            // row stride of the fp16 splits of A and nu (d rounded up to 8)
+  long long ah_off;    // element offset of the problem's fp16 A splits (row 0)
+  long long xh_off;    // element offset of the first chain's row in the fp16 nu splits
+  int c_first;         // index of the first chain in the whole batch
   int pad_;
 };
 // Chain tile of a problem with n chains (16, 32 or 64; larger counts are cut
 // into tiles of 64), and the matching row tile.
 inline int batch_ctile(int n) { return n <= 16 ? 16 : n <= 32 ? 32 : 64; }
 inline int batch_rtile(int ctile) { return 4096 / ctile; }
+#ifndef ESS_BQ_WARPS
+#define ESS_BQ_WARPS 4
+#endif
+constexpr int kBatchMmaTile = 512 * ESS_BQ_WARPS;  // 4 blocks of 16 x 8 per warp
+inline int batch_mma_rtile(int ctile) { return kBatchMmaTile / ctile; }
 
 // nu for every chain of the batch (T = float: float Box-Muller, T = double:
 // 53-bit), written at desc[c].x_off; the step index is t (+ *t_dev if set).
+// T = float with H0, H1 set also writes the fp16 split of nu * kNuSplitScale
+// at desc[c].h_off (rows of desc[c].dpad).
 template <typename T>
 cudaError_t launch_batch_draw(const ChainDesc* desc, int n_chains, T* NU, uint64_t seed,
-                              uint32_t t, const unsigned* t_dev, cudaStream_t s);
+                              uint32_t t, const unsigned* t_dev, cudaStream_t s,
+                              __half* H0 = nullptr, __half* H1 = nullptr);
+// Scaled fp16 split of caller-supplied float nu rows (per chain: t = 2^(15-e)
+// with max |nu| in [2^(e-1), 2^e); unscale[c] = 1 / t).
+cudaError_t launch_batch_split(const ChainDesc* desc, int n_chains, const float* NU, __half* H0,
+                               __half* H1, float* unscale, cudaStream_t s);
+// Mixed form: Q = A nu per item on the tensor cores (mma.sync, FP16x3), items
+// of rtile x ctile = kBatchMmaTile (batch_mma_rtile):
+// A0, A1 the fp16 splits of A s_i (rows of dpad at ah_off), arow_unscale[i] =
+// 1 / s_i (indexed by b_off + row), H0, H1 the nu splits, chain_unscale[c] =
+// 1 / t_c per chain (nullptr: 1 / kNuSplitScale).
+cudaError_t launch_batch_q_mma(const BatchItem* items, int n_items, int* queue, const __half* A0,
+                               const __half* A1, const float* arow_unscale, const __half* H0,
+                               const __half* H1, const float* chain_unscale, float* Q,
+                               cudaStream_t s);
 // Q = A nu per item, in T; AT holds every problem's A K-major (d x mpad at
 // at_off); queue: one int of scratch (reset by the launcher).
 template <typename T>

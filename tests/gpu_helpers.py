@@ -67,3 +67,20 @@ def feasible_instance(rng, d, m, n_chains, scale=1.0, slack=(0.0, 1.0)):
     X = rng.standard_normal((n_chains, d)) * 0.3
     b = (X @ A.T).max(axis=0) + rng.uniform(*slack, size=m)
     return A, b, X
+
+
+def fp16x3_bound(A, NU):
+    """Bound on |q - a.nu| per chain (row of NU) and row of A for the scaled
+    FP16x3 products: row i of A (rounded to float) is scaled by s_i so that its
+    largest entry lies in [2^14, 2^15), chain c of nu by t_c likewise (or by
+    2^12 for drawn nu), each split as v = h0 + h1 + r with fp16 h0, h1:
+    |r| <= 2^-22 |v| + 2^-25 (the second term when h1 is subnormal).  The two
+    residuals and the dropped h1.a1 product give 12 x 2^-24 relative to
+    |a||nu|; the FP32 accumulation over K/16 tensor-core steps and the final
+    addition of the two accumulators add K/16 + 2.  Unscaled, the subnormal
+    terms are below 2^-38 max|nu_c| per |a_j| and 2^-38 max|a_i| per |nu_j|."""
+    absdot = np.abs(NU) @ np.abs(A).T
+    k = A.shape[1]
+    sub = 2.0**-38 * (np.abs(NU).max(axis=1)[:, None] * np.abs(A).sum(axis=1)[None, :]
+                      + np.abs(NU).sum(axis=1)[:, None] * np.abs(A).max(axis=1)[None, :])
+    return absdot * (16 + k / 16) * 2.0**-24 + sub

@@ -15,7 +15,7 @@ import pytest
 import oracle
 import paper_2407_10449_gb300 as ess
 import workloads
-from gpu_helpers import dev, host, oracle_steps, feasible_instance
+from gpu_helpers import dev, host, oracle_steps, feasible_instance, fp16x3_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -132,9 +132,8 @@ def test_batch_mixed_step_with_draws():
 
 @pytest.mark.parametrize("form", [ess.ESS_PREC_FP64, ess.ESS_PREC_MIXED])
 def test_batch_products(form):
-    """P = A x (refresh path, FP64-class in both forms) and Q = A nu (FP32
-    FMAs in the mixed form: within d 2^-24 sum |a||nu| plus the float
-    rounding of the inputs)."""
+    """P = A x (refresh path, FP64-class in both forms) and Q = A nu (the
+    tensor-core FP16x3 products in the mixed form, within their bound)."""
     As, bs, Xs, nc = make_batch(8)
     rng = np.random.default_rng(9)
     NUs = [rng.standard_normal(X.shape) for X in Xs]
@@ -149,8 +148,11 @@ def test_batch_products(form):
             X = np.asarray(X, np.float32).astype(np.float64)
             NU = np.asarray(NU, np.float32).astype(np.float64)
             A32 = np.asarray(A, np.float32).astype(np.float64)
-            qtol = (A.shape[1] + 2) * 2.0**-24 * (np.abs(NU) @ np.abs(A32).T)
+            qtol = fp16x3_bound(A32, NU)
             np.testing.assert_array_less(np.abs(Q[p] - NU @ A32.T), qtol + 1e-300)
+            # a wrong operand layout would not stay far inside the bound
+            if Q[p].size:
+                assert np.median(np.abs(Q[p] - NU @ A32.T) / (qtol + 1e-300)) < 0.2
         else:
             np.testing.assert_allclose(Q[p], NU @ A.T, rtol=0,
                                        atol=1e-13 * (1 + np.abs(NU).sum()))

@@ -16,7 +16,7 @@ import pytest
 
 import oracle
 import paper_2407_10449_gb300 as ess
-from gpu_helpers import dev, host, oracle_steps, positive_pieces, feasible_instance, \
+from gpu_helpers import dev, host, oracle_steps, positive_pieces, feasible_instance, fp16x3_bound, \
     sym_diff_measure
 
 pytestmark = pytest.mark.gpu
@@ -29,20 +29,8 @@ def f32(a):
 
 
 def q_error_bound(A, NU):
-    """Bound on |q - a.nu| per row and chain for the FP16x3 GEMM.  Row i of A
-    (rounded to float: 2^-24 relative) is scaled by s_i so that its largest
-    entry lies in [2^14, 2^15), chain c of nu by t_c likewise, and each is split
-    as v = h0 + h1 + r with fp16 h0, h1: |r| <= 2^-22 |v| + 2^-25 (the second
-    term when h1 is subnormal).  The two residuals and the dropped h1.a1
-    product give 12 x 2^-24 relative to |a||nu|; the FP32 accumulation over
-    K/16 tensor-core steps and the final addition of the two accumulators add
-    K/16 + 2.  Unscaled, the subnormal terms are below 2^-38 max|nu_c| per
-    |a_j| and 2^-38 max|a_i| per |nu_j|."""
-    absdot = np.abs(NU) @ np.abs(A).T
-    k = A.shape[1]
-    sub = 2.0**-38 * (np.abs(NU).max(axis=1)[:, None] * np.abs(A).sum(axis=1)[None, :]
-                      + np.abs(NU).sum(axis=1)[:, None] * np.abs(A).max(axis=1)[None, :])
-    return absdot * (16 + k / 16) * 2.0**-24 + sub
+    """The FP16x3 GEMM's bound (see gpu_helpers.fp16x3_bound)."""
+    return fp16x3_bound(A, NU)
 
 
 @pytest.mark.parametrize("n,m,d", [(1, 20, 10), (130, 300, 137), (256, 448, 64),
