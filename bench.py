@@ -153,13 +153,25 @@ def barrier(world):
 
 
 def max_over_ranks(world, value):
+    """Largest value over the ranks (the job's time is its slowest rank's)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_seed(seed, rank):
+    """Seed of a rank's replica: the replicas draw disjoint Philox streams."""
+    return seed + 1000003 * rank
+
+
+def job_throughput(world, chains_per_rank, steps, ms_max):
+    """Whole-job chain-iterations per second from the slowest rank's time."""
+    return world * chains_per_rank * steps / (ms_max / 1e3)
 
 
 def source_hash(*names):
@@ -525,18 +537,18 @@ def main():
     peaks = load_peaks()
     C = args.chains
     inst = workloads.metric(n_chains=1)
-    seed = args.seed + 1000003 * rank
+    seed = rank_seed(args.seed, rank)
 
     clocks = ClockSampler(local) if rank == 0 else None
     ms, timing, stats, clk, lc = time_form(ess, torch, inst, "mixed", C, args.steps, args.warmup,
                                            seed, world, rank, clocks)
-    value = world * C * args.steps / (ms / 1e3)
+    value = job_throughput(world, C, args.steps, ms)
     if args.mixed_only:
         ms64, timing64, stats64, value64 = float("nan"), {}, {}, None
     else:
         ms64, timing64, stats64, _, _ = time_form(ess, torch, inst, "fp64", C, args.fp64_steps,
                                                   3, seed, world, rank, None)
-        value64 = world * C * args.fp64_steps / (ms64 / 1e3)
+        value64 = job_throughput(world, C, args.fp64_steps, ms64)
 
     if rank != 0:
         barrier(world)
