@@ -82,8 +82,15 @@ typedef struct {
     int sort_threads;           /* 0 (default): one warp per chain, with a
                                    CTA per chain for chains that keep more than
                                    128 arcs after the domination prune;
-                                   > 0: a CTA per chain for every chain */
-    int reserved[8];
+                                   > 0: a CTA per chain for every chain, of
+                                   sort_threads threads rounded up to a power
+                                   of two (at least the width that holds m
+                                   arcs, at most 1024) */
+    int autotune;               /* 0 (default): tile widths and the sort path
+                                   from a cost model; 1: ess_chains_init times
+                                   the candidates on the loaded chains and keeps
+                                   the fastest (see ess_get_tuning) */
+    int reserved[7];
 } ess_config;
 
 typedef struct {
@@ -304,6 +311,20 @@ ess_status ess_step_noalloc(const double *A, const double *b, int d, int m, cons
  * reports the replays since the state was created.
  */
 ess_status ess_set_graphs(ess_state *state, int enable);
+
+/*
+ * Autotuner (cfg.autotune = 1): when chains are loaded, ess_chains_init
+ * (and so ess_run) times, on the loaded chains and their first draw,
+ *   - every tile width of the q = A nu tensor-core GEMM (mixed form), and
+ *   - the chain-step kernels: one warp per chain with the CTA-per-chain
+ *     fallback, or a CTA per chain for every chain at the minimum and at twice
+ *     the minimum width,
+ * without advancing any chain, and keeps the fastest for that chain count.
+ * Different choices can change results in the last bits (different sums), so
+ * the tuning is opt-in.  ess_get_tuning reports the choice in use: the q GEMM
+ * width (0 in the FP64 form) and sort_threads (0: warp per chain).
+ */
+ess_status ess_get_tuning(const ess_state *state, int *q_width, int *sort_threads);
 ess_status ess_graph_launches(const ess_state *state, long long *launches);
 
 /* ---- Batched problems -------------------------------------------------------

@@ -43,7 +43,7 @@ EXPORTED = ("ess_default_config", "ess_create", "ess_destroy", "ess_limits", "es
             "ess_draw_normals",
             "ess_set_timing", "ess_get_timing", "ess_reset_timing",
             "ess_get_stats", "ess_reset_stats", "ess_whiten", "ess_unwhiten", "ess_step_noalloc",
-            "ess_set_graphs", "ess_graph_launches",
+            "ess_set_graphs", "ess_graph_launches", "ess_get_tuning",
             "ess_whitener_create", "ess_whitener_destroy", "ess_whitener_apply",
             "ess_batch_create", "ess_batch_destroy", "ess_batch_run", "ess_batch_step_with_draws",
             "ess_batch_products", "ess_batch_get_stats", "ess_batch_reset_stats",
@@ -66,7 +66,8 @@ class ess_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("refresh_k", ctypes.c_int),
                 ("refresh_mode", ctypes.c_int), ("tangent_thresh", ctypes.c_double),
                 ("trim_eps", ctypes.c_double), ("residual_margin", ctypes.c_double),
-                ("sort_threads", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("sort_threads", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 class ess_stats(ctypes.Structure):
@@ -132,6 +133,7 @@ def load(build_if_missing: bool = True):
             "ess_whitener_destroy": ([_vp], None),
             "ess_whitener_apply": ([_vp, _vp, c_int, c_int, _vp, _vp], c_int),
             "ess_set_graphs": ([_vp, c_int], c_int),
+            "ess_get_tuning": ([_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)], c_int),
             "ess_graph_launches": ([_vp, ctypes.POINTER(ctypes.c_longlong)], c_int),
             "ess_batch_create": ([c_int, _vp, _vp, _dp, _dp, ctypes.POINTER(ess_config),
                                   ctypes.POINTER(_vp)], c_int),
@@ -377,6 +379,13 @@ class Whitener:
 
 def ess_set_graphs(state, enable=True):
     _check(load().ess_set_graphs(state, 1 if enable else 0))
+
+
+def ess_get_tuning(state):
+    """(q GEMM tile width, sort_threads) in use (width 0 in the FP64 form)."""
+    w, t = ctypes.c_int(), ctypes.c_int()
+    _check(load().ess_get_tuning(state, ctypes.byref(w), ctypes.byref(t)))
+    return w.value, t.value
 
 
 def ess_graph_launches(state) -> int:

@@ -67,6 +67,8 @@ struct ess_state {
   int device = 0;
   int ld16 = 0;           // row stride of the 16-bit operands (d rounded up to 8)
   int chain_threads = 0;  // threads per chain of the step kernel
+  int min_chain_threads = 0;  // the narrowest CTA width that holds m arcs
+  int tuned_n = 0;            // chain count the autotuner last tuned for
   // constants (device)
   double* A64 = nullptr;
   double* b64 = nullptr;
@@ -356,6 +358,127 @@ struct DeviceGuard {
 
 namespace {
 
+// Times the candidate q GEMM widths and chain-step paths on the loaded chains
+// (their first draw), writing x' to scratch so that no chain moves, and keeps
+// the fastest.
+ess_status autotune(ess_state* s, int t0, cudaStream_t st) {
+  const int n = s->n_loaded, d = s->d;
+  cudaEvent_t e0, e1;
+  ESS_CUDA(cudaEventCreate(&e0));
+  ESS_CUDA(cudaEventCreate(&e1));
+  auto timed = [&](auto&& launch, float* ms) -> ess_status {
+    ess_status rc = launch();  // warm-up
+    if (rc != ESS_OK) return rc;
+    ESS_CUDA(cudaEventRecord(e0, st));
+    for (int r = 0; r < 3 && rc == ESS_OK; ++r) rc = launch();
+    ESS_CUDA(cudaEventRecord(e1, st));
+    ESS_CUDA(cudaEventSynchronize(e1));
+    if (rc != ESS_OK) return rc;
+    ESS_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    return ESS_OK;
+  };
+  const bool timing = s->timing;
+  s->timing = false;
+  ess_status rc = ESS_OK;
+  // the trial steps must not count in the statistics
+  DevStats saved{};
+  ESS_CUDA(cudaMemcpyAsync(&saved, s->dstats, sizeof(saved), cudaMemcpyDeviceToHost, st));
+  ESS_CUDA(cudaStreamSynchronize(st));
+  // the first draw of the loaded chains (nu and, in the mixed form, its splits)
+  if (mixed(s))
+    ESS_CUDA(ess::launch_draw_nu_f32(static_cast<float*>(s->NU), d, s->NU_h, s->ld16, n, d, 0,
+                                     (uint32_t)t0, 0u, 0u, st));
+  else
+    ESS_CUDA(ess::launch_draw_nu_f64(static_cast<double*>(s->NU), n, d, d, 0, (uint32_t)t0, 0u,
+                                     0u, st));
+  if (mixed(s)) {
+    int best = 0;
+    float best_ms = 0.f;
+    for (int w : ess::kTcWidths) {
+      ESS_CUDA(ess::tc_gemm_set_width(s->tc_plan, w));
+      float ms = 0.f;
+      rc = timed([&]() { return compute_q(s, n, st); }, &ms);
+      if (rc != ESS_OK) break;
+      if (best == 0 || ms < best_ms) {
+        best = w;
+        best_ms = ms;
+      }
+    }
+    if (rc == ESS_OK) ESS_CUDA(ess::tc_gemm_set_width(s->tc_plan, best));
+  }
+  if (rc == ESS_OK) rc = compute_q(s, n, st);
+  // chain step: x' to scratch, p' to the second buffer (P is left intact)
+  void* scratch = nullptr;
+  if (rc == ESS_OK) ESS_CUDA(cudaMalloc(&scratch, (size_t)n * d * elem(s)));
+  const int saved_sort = s->cfg.sort_threads, saved_threads = s->chain_threads;
+  int cands[3][2] = {{0, s->min_chain_threads}, {s->min_chain_threads, s->min_chain_threads},
+                     {2 * s->min_chain_threads, 2 * s->min_chain_threads}};
+  int best = -1;
+  float best_ms = 0.f;
+  for (int c = 0; c < 3 && rc == ESS_OK; ++c) {
+    if (cands[c][1] > ess::kChainMaxThreads) continue;
+    const size_t smem = mixed(s) ? ess::chain_smem_bytes<float>(cands[c][1], d)
+                                 : ess::chain_smem_bytes<double>(cands[c][1], d);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+    if (smem + 1024 > (size_t)optin) continue;
+    s->cfg.sort_threads = cands[c][0];
+    s->chain_threads = cands[c][1];
+    float ms = 0.f;
+    void* P_keep = s->P;
+    void* P2_keep = s->P2;
+    auto launch = [&]() -> ess_status {
+      s->P = P_keep;
+      s->P2 = P2_keep;
+      ess_status r;
+      if (mixed(s)) {
+        ess::ChainParams<float> p = base_params<float>(s, n);
+        p.X = s->Xw;
+        p.X_out = static_cast<float*>(scratch);
+        p.t = (uint32_t)t0;
+        r = launch_step<float>(s, p, st);
+      } else {
+        ess::ChainParams<double> p = base_params<double>(s, n);
+        p.X = s->Xd;
+        p.X_out = static_cast<double*>(scratch);
+        p.t = (uint32_t)t0;
+        r = launch_step<double>(s, p, st);
+      }
+      s->P = P_keep;
+      s->P2 = P2_keep;
+      return r;
+    };
+    rc = timed(launch, &ms);
+    if (rc == ESS_OK && (best < 0 || ms < best_ms)) {
+      best = c;
+      best_ms = ms;
+    }
+  }
+  if (scratch) {
+    cudaStreamSynchronize(st);
+    cudaFree(scratch);
+  }
+  ESS_CUDA(cudaMemcpyAsync(s->dstats, &saved, sizeof(saved), cudaMemcpyHostToDevice, st));
+  ESS_CUDA(cudaStreamSynchronize(st));
+  if (best >= 0) {
+    s->cfg.sort_threads = cands[best][0];
+    s->chain_threads = cands[best][1];
+  } else {
+    s->cfg.sort_threads = saved_sort;
+    s->chain_threads = saved_threads;
+  }
+  s->timing = timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  drop_graphs(s);  // captured with the previous choices
+  if (rc == ESS_OK) s->tuned_n = n;
+  return rc;
+}
+
+}  // namespace
+
+namespace {
+
 // One step of every loaded chain at step index t (+ *t_dev when t_dev is
 // set): draw nu, q = A nu, chain step (p buffers swapped).
 template <typename T>
@@ -476,9 +599,12 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
       !(c.residual_margin >= 0.0))
     return fail(ESS_ERR_ARG, "tangent_thresh in [0, 1), trim_eps >= 0, residual_margin >= 0");
 
-  const int threads = ess::chain_threads_for(m);
-  if (threads == 0)
+  const int min_threads = ess::chain_threads_for(m);
+  if (min_threads == 0)
     return fail(ESS_ERR_UNSUPPORTED, "m exceeds the per-chain shared-memory sort limit (8192)");
+  // a CTA per chain: at least the minimum width, wider if sort_threads asks
+  int threads = min_threads;
+  while (threads < c.sort_threads && threads < ess::kChainMaxThreads) threads <<= 1;
   const size_t smem = c.precision == ESS_PREC_MIXED ? ess::chain_smem_bytes<float>(threads, d)
                                                     : ess::chain_smem_bytes<double>(threads, d);
   int dev = 0;
@@ -495,6 +621,7 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
   s->device = dev;
   s->ld16 = (d + 7) & ~7;
   s->chain_threads = threads;
+  s->min_chain_threads = min_threads;
 
   auto cleanup = [&](ess_status st) {
     ess_destroy(s);
@@ -603,6 +730,17 @@ ess_status ess_chains_init(ess_state* s, const double* X, int n_chains, int t0,
   s->n_loaded = n;
   s->t_next = t0;
   s->p_fresh_t = t0;
+  if (s->cfg.autotune && s->tuned_n != n) {
+    rc = autotune(s, t0, st);
+    if (rc != ESS_OK) return rc;
+  }
+  return ESS_OK;
+}
+
+ess_status ess_get_tuning(const ess_state* s, int* q_width, int* sort_threads) {
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  if (q_width) *q_width = mixed(s) ? ess::tc_gemm_width(s->tc_plan, std::max(1, s->n_loaded)) : 0;
+  if (sort_threads) *sort_threads = s->cfg.sort_threads;
   return ESS_OK;
 }
 

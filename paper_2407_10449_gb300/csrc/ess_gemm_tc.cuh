@@ -55,5 +55,10 @@ const float* tc_refresh_col_scale(const TcGemmPlan* plan);
 
 // Tile width (constraints per CTA) and pipeline depth chosen for a shape.
 void tc_gemm_tile_for(int n_chains, int m, int* bn, int* stages);
+// Tile widths the q GEMM supports, and a fixed width for a plan (0: the cost
+// model of tc_gemm_tile_for); the width tc_gemm_q uses for n_chains.
+extern const int kTcWidths[6];
+cudaError_t tc_gemm_set_width(TcGemmPlan* plan, int bn);
+int tc_gemm_width(const TcGemmPlan* plan, int n_chains);
 
 }  // namespace ess

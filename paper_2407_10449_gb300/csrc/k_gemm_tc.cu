@@ -721,6 +721,7 @@ struct TcGemmPlan {
   __nv_bfloat16* aK = nullptr;      // K slices, m x ld_bf each
   float* col_scale = nullptr;       // s_i
   CUtensorMap rmaps[kMaxSlices];
+  int bn_fixed = 0;                 // q GEMM tile width set by the autotuner (0: cost model)
   double bound_factor = 0.0;        // |p_exact - p| <= bound_factor * s_i * t_c
 };
 
@@ -862,6 +863,22 @@ void tc_gemm_destroy(TcGemmPlan* plan) {
   delete plan;
 }
 
+const int kTcWidths[6] = {64, 128, 160, 192, 224, 256};
+
+cudaError_t tc_gemm_set_width(TcGemmPlan* plan, int bn) {
+  if (!plan) return cudaErrorInvalidValue;
+  if (bn != 0 && std::find(kWidths, kWidths + 6, bn) == kWidths + 6) return cudaErrorInvalidValue;
+  plan->bn_fixed = bn;
+  return cudaSuccess;
+}
+
+int tc_gemm_width(const TcGemmPlan* plan, int n_chains) {
+  if (plan->bn_fixed) return plan->bn_fixed;
+  int bn = 0;
+  tc_gemm_tile_for(n_chains, plan->m, &bn, nullptr);
+  return bn;
+}
+
 int tc_refresh_num_slices(const TcGemmPlan* plan) { return plan->K; }
 double tc_refresh_bound_factor(const TcGemmPlan* plan) { return plan->bound_factor; }
 const float* tc_refresh_col_scale(const TcGemmPlan* plan) { return plan->col_scale; }
@@ -879,8 +896,7 @@ cudaError_t tc_gemm_q(TcGemmPlan* plan, __half* const nu[2], const float* nu_uns
   if (!plan) return cudaErrorInvalidValue;
   if (n_chains == 0) return cudaSuccess;
   if (ld16 != plan->ld16) return cudaErrorInvalidValue;
-  int bn = 0;
-  tc_gemm_tile_for(n_chains, plan->m, &bn, nullptr);
+  const int bn = tc_gemm_width(plan, n_chains);
   int wi = 0;
   while (kWidths[wi] != bn) ++wi;
   TcMaps maps;

@@ -101,6 +101,35 @@ def test_graph_replay_is_bit_identical(form):
 
 
 @pytest.mark.parametrize("form", FORMS)
+def test_autotune_keeps_the_chains(form):
+    """The autotuner times its candidates without moving any chain: a tuned
+    run equals an untuned run with the same sort path (the q GEMM's tile
+    width does not change any element's sums)."""
+    inst = workloads.medium(n_chains=200)
+    s = ess.Sampler(inst.A, inst.b, precision=form, autotune=1)
+    try:
+        Xa = dev(inst.X0)
+        s.run(Xa, 12, seed=4)
+        width, sort_threads = ess.ess_get_tuning(s.state)
+        st = s.stats()
+    finally:
+        s.close()
+    if form == ess.ESS_PREC_MIXED:
+        assert width in (64, 128, 160, 192, 224, 256)
+    else:
+        assert width == 0
+    assert sort_threads in (0, 32, 64, 128)
+    assert st["steps"] == 200 * 12
+    s = ess.Sampler(inst.A, inst.b, precision=form, sort_threads=sort_threads)
+    try:
+        Xb = dev(inst.X0)
+        s.run(Xb, 12, seed=4)
+    finally:
+        s.close()
+    np.testing.assert_array_equal(host(Xa), host(Xb))
+
+
+@pytest.mark.parametrize("form", FORMS)
 def test_every_iterate_feasible(form):
     inst = workloads.medium(n_chains=128)
     import torch
