@@ -206,5 +206,30 @@ __device__ __forceinline__ int classify_phi(T p, T q, T b, const double* b64, T 
   return pa < pb ? kRowApprox : kRowKeep;
 }
 
+// Branch-free float form of classify_phi (same classes and pseudo-angles):
+// every quantity is computed and the class picked by selects, so the rows of a
+// batch are straight-line code that the compiler can interleave.  pa and pb
+// are meaningful only for kRowApprox.
+__device__ __forceinline__ int classify_phi_nb(float p, float q, float b, const double* b64,
+                                               float tlo, float thi, float& pa, float& pb,
+                                               bool& infeasible, bool& nonfinite) {
+  const float r2 = fmaf(p, p, q * q);
+  nonfinite |= !(r2 <= FLT_MAX);  // NaN or Inf in p or q
+  const float ratio = b * rsqrtf(r2);
+  const float w2 = fmaf(-b, b, r2);
+  const float w = w2 * rsqrtf(fmaxf(w2, FLT_MIN));
+  pa = diamond_angle(fmaf(p, b, q * w), fmaf(q, b, -p * w));
+  pb = diamond_angle(fmaf(p, b, -q * w), fmaf(q, b, p * w));
+  int cls = pa < pb ? kRowApprox : kRowKeep;
+  cls = w2 > 0.f ? cls : kRowKeep;
+  cls = fabsf(ratio) > tlo * 0.999999f ? kRowKeep : cls;
+  cls = ratio >= thi * 1.000001f ? kRowNone : cls;
+  if (r2 == 0.0f) {  // rare: read the exact b only here
+    infeasible = *b64 < 0.0;
+    cls = kRowNone;
+  }
+  return cls;
+}
+
 }  // namespace chainmath
 }  // namespace ess

@@ -197,9 +197,12 @@ chain_warp_kernel(ChainParams<T> prm) {
           if (i >= m_sub) continue;
           float pa = 0.f, pb = 0.f;
           bool inf_row = false, nf = false;
-          if (classify_phi<T>(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb, inf_row, nf) ==
-              kRowApprox)
-            atomicMax(&bsub[bslot(pbucket(pa))], __float_as_uint(pb));
+          int cls;
+          if constexpr (sizeof(T) == 4)
+            cls = classify_phi_nb(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb, inf_row, nf);
+          else
+            cls = classify_phi<T>(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb, inf_row, nf);
+          if (cls == kRowApprox) atomicMax(&bsub[bslot(pbucket(pa))], __float_as_uint(pb));
         }
       }
     }
@@ -228,20 +231,36 @@ chain_warp_kernel(ChainParams<T> prm) {
         if (i < m) {
           float pa = 0.f;
           bool inf_row = false;
-          const int cls = classify_phi<T>(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb,
-                                          inf_row, nonfinite);
-          infeasible |= inf_row;
-          if (cls == kRowKeep) {
-            cand = true;
-            code = 0x80000000u | (unsigned)i;
-          } else if (cls == kRowApprox) {
-            const int bk = pbucket(pa);
-            cand = bk < 2 || !(pb + 2.f * kPhiMargin <= __uint_as_float(bsub[bslot(bk - 2)]));
+          if constexpr (sizeof(T) == 4) {
+            // straight-line form: class, bucket test and candidate code by
+            // selects (the rows of the batch interleave)
+            const int cls = classify_phi_nb(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb,
+                                            inf_row, nonfinite);
+            infeasible |= inf_row;
+            const int bk = pbucket(fminf(fmaxf(pa, 0.f), 4.f));
+            const float dom = __uint_as_float(bsub[bslot(max(bk - 2, 0))]);
+            const bool undominated = bk < 2 || !(pb + 2.f * kPhiMargin <= dom);
+            const bool approx = cls == kRowApprox;
+            cand = cls == kRowKeep || (approx && undominated);
             // a row dominated by the first batch adds nothing to the full
             // maxima: the first-batch arc that covers it dominates every arc
             // it would dominate
-            if (cand) atomicMax(&bfull[bslot(bk)], __float_as_uint(pb));
-            code = ((unsigned)bk << 14) | (unsigned)i;
+            if (approx && undominated) atomicMax(&bfull[bslot(bk)], __float_as_uint(pb));
+            code = cls == kRowKeep ? (0x80000000u | (unsigned)i)
+                                   : (((unsigned)bk << 14) | (unsigned)i);
+          } else {
+            const int cls = classify_phi<T>(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb,
+                                            inf_row, nonfinite);
+            infeasible |= inf_row;
+            if (cls == kRowKeep) {
+              cand = true;
+              code = 0x80000000u | (unsigned)i;
+            } else if (cls == kRowApprox) {
+              const int bk = pbucket(pa);
+              cand = bk < 2 || !(pb + 2.f * kPhiMargin <= __uint_as_float(bsub[bslot(bk - 2)]));
+              if (cand) atomicMax(&bfull[bslot(bk)], __float_as_uint(pb));
+              code = ((unsigned)bk << 14) | (unsigned)i;
+            }
           }
         }
         const unsigned ball = __ballot_sync(kFull, cand);
