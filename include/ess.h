@@ -90,7 +90,15 @@ typedef struct {
                                    from a cost model; 1: ess_chains_init times
                                    the candidates on the loaded chains and keeps
                                    the fastest (see ess_get_tuning) */
-    int reserved[7];
+    int q_tile;                 /* mixed form, tile of the q = A nu GEMM:
+                                   0 (default): cost model (or the autotuner);
+                                   BN in {64, 128, 160, 192, 224, 256}: one SM
+                                   per tile of 128 chains x BN rows of A;
+                                   2000 + BN, BN in {128, ..., 256}: a pair of
+                                   SMs (tcgen05 cta_group::2) per tile of 256
+                                   chains x BN rows.  Any other value is
+                                   ESS_ERR_ARG. */
+    int reserved[6];
 } ess_config;
 
 typedef struct {
@@ -322,7 +330,8 @@ ess_status ess_set_graphs(ess_state *state, int enable);
  * without advancing any chain, and keeps the fastest for that chain count.
  * Different choices can change results in the last bits (different sums), so
  * the tuning is opt-in.  ess_get_tuning reports the choice in use: the q GEMM
- * width (0 in the FP64 form) and sort_threads (0: warp per chain).
+ * tile code as in ess_config.q_tile (0 in the FP64 form) and sort_threads
+ * (0: warp per chain).
  */
 ess_status ess_get_tuning(const ess_state *state, int *q_width, int *sort_threads);
 ess_status ess_graph_launches(const ess_state *state, long long *launches);

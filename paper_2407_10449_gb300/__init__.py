@@ -67,7 +67,7 @@ class ess_config(ctypes.Structure):
                 ("refresh_mode", ctypes.c_int), ("tangent_thresh", ctypes.c_double),
                 ("trim_eps", ctypes.c_double), ("residual_margin", ctypes.c_double),
                 ("sort_threads", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("q_tile", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class ess_stats(ctypes.Structure):

@@ -4,6 +4,7 @@
 // state, and the per-step launch sequence
 //   [refresh p = A x]  ->  draw nu  ->  q = A nu  ->  chain step
 // on the caller's stream.  All arithmetic of the step runs in the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -230,7 +231,7 @@ ess_status refresh_p(ess_state* s, int n, const void* Xcur, bool with_drift, boo
     const float* Xf = static_cast<const float*>(Xcur);
     ESS_CUDA(ess::tc_refresh(s->tc_plan, Xf, s->d, n, s->x_slices, (size_t)n * s->ld16,
                              s->row_scale, static_cast<float*>(s->P), check ? s->P64 : nullptr,
-                             s->m, s->anorm, with_drift ? &s->dstats->max_drift_bits : nullptr,
+                             s->m, with_drift ? &s->dstats->max_drift_bits : nullptr,
                              s->dstatus, st));
     if (check) {
       ESS_CUDA(ess::launch_check_feasible_bounded(
@@ -598,6 +599,9 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
   if (!(c.tangent_thresh >= 0.0 && c.tangent_thresh < 1.0) || !(c.trim_eps >= 0.0) ||
       !(c.residual_margin >= 0.0))
     return fail(ESS_ERR_ARG, "tangent_thresh in [0, 1), trim_eps >= 0, residual_margin >= 0");
+  if (c.q_tile != 0 &&
+      std::find(ess::kTcWidths, ess::kTcWidths + 11, c.q_tile) == ess::kTcWidths + 11)
+    return fail(ESS_ERR_ARG, "q_tile: 0, 64/128/160/192/224/256, or 2000 + 128/160/192/224/256");
 
   const int min_threads = ess::chain_threads_for(m);
   if (min_threads == 0)
@@ -669,6 +673,7 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
     e = dev_alloc(&s->b32, (size_t)m);
     if (e == cudaSuccess) e = cudaMemcpy(s->b32, bf.data(), sizeof(float) * m, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = ess::tc_gemm_create(&s->tc_plan, A, m, d);
+    if (e == cudaSuccess && c.q_tile) e = ess::tc_gemm_set_width(s->tc_plan, c.q_tile);
   }
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "ess_create device setup"));
   *out = s;

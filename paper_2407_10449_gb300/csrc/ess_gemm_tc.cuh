@@ -39,13 +39,14 @@ cudaError_t tc_split2_rows(const float* src, int ld, int rows, int cols, __half*
 // pairs are combined error-free in (hi, lo) float pairs.  The result differs
 // from A x by at most bound_factor * s_i * t_c (truncated slices and dropped
 // pairs).  Writes P32 (rounded once to float) and/or P64; if drift_bits is
-// set, folds max |P32_new - P32_old| / anorm_i into it.  x_slices needs
+// set, folds max |P32_new - P32_old| / ||a_i|| (evaluated in FP32) into it
+// (the bits of a non-negative double).  x_slices needs
 // K x slice_stride bf16 (slice_stride >= n_chains * ld16) and row_scale
 // n_chains floats of scratch.
 cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
                        __nv_bfloat16* x_slices, size_t slice_stride, float* row_scale,
-                       float* P32, double* P64, int ldp, const double* anorm,
-                       unsigned long long* drift_bits, int* status, cudaStream_t s);
+                       float* P32, double* P64, int ldp, unsigned long long* drift_bits,
+                       int* status, cudaStream_t s);
 
 // Slice count K and width w of the refresh for dimension d.
 int tc_refresh_slices(int d, int* w);
@@ -53,11 +54,13 @@ int tc_refresh_num_slices(const TcGemmPlan* plan);
 double tc_refresh_bound_factor(const TcGemmPlan* plan);
 const float* tc_refresh_col_scale(const TcGemmPlan* plan);
 
-// Tile width (constraints per CTA) and pipeline depth chosen for a shape.
+// Tile of the q GEMM chosen for a shape: BN for one-SM tiles of 128 chains x
+// BN rows of A, 2000 + BN for SM-pair tiles (tcgen05 cta_group::2) of 256
+// chains x BN rows.  *stages (if given) is set to 0.
 void tc_gemm_tile_for(int n_chains, int m, int* bn, int* stages);
-// Tile widths the q GEMM supports, and a fixed width for a plan (0: the cost
-// model of tc_gemm_tile_for); the width tc_gemm_q uses for n_chains.
-extern const int kTcWidths[6];
+// Tile codes the q GEMM supports, and a fixed code for a plan (0: the cost
+// model of tc_gemm_tile_for); the code tc_gemm_q uses for n_chains.
+extern const int kTcWidths[11];
 cudaError_t tc_gemm_set_width(TcGemmPlan* plan, int bn);
 int tc_gemm_width(const TcGemmPlan* plan, int n_chains);
 

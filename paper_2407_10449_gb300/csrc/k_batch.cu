@@ -218,6 +218,7 @@ batch_gemm_kernel(const BatchItem* __restrict__ items, int n_items, int* queue,
                                          : reinterpret_cast<const TA*>(A64);
   const TA* Alsrc = reinterpret_cast<const TA*>(Alo);
   double drift = 0.0;
+  float driftf = 0.f;
   for (;;) {
     const int it = next_item(queue, &s_item);
     if (it >= n_items) break;
@@ -315,6 +316,23 @@ batch_gemm_kernel(const BatchItem* __restrict__ items, int n_items, int* queue,
       }
       __syncthreads();  // buffer c & 1 is free for chunk c + 2
     }
+    // refresh with drift: every old value is loaded before the first store,
+    // so the loads are in flight together
+    T old[4][4];
+    if constexpr (MODE != kGemmQ) {
+      if (out && drift_bits) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int ci = 4 * ty + i;
+          const size_t base = (size_t)I.p_off + (size_t)ci * I.m + I.row0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int rj = 4 * tx + j;
+            old[i][j] = ci < I.chains && rj < I.rows ? out[base + rj] : T(0);
+          }
+        }
+      }
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int ci = 4 * ty + i;
@@ -332,8 +350,15 @@ batch_gemm_kernel(const BatchItem* __restrict__ items, int n_items, int* queue,
           if (out) {
             const T pn = (T)v;
             if (drift_bits) {
-              const double old = (double)out[base + rj];
-              drift = fmax(drift, fabs((double)pn - old) / anorm[I.b_off + I.row0 + rj]);
+              if constexpr (sizeof(T) == 4) {
+                // the drift statistic in FP32: a diagnostic, far coarser than FP32
+                const float dv = __fdividef(fabsf(pn - old[i][j]),
+                                            (float)anorm[I.b_off + I.row0 + rj]);
+                driftf = fmaxf(driftf, dv);
+              } else {
+                drift = fmax(drift, fabs((double)pn - (double)old[i][j]) /
+                                        anorm[I.b_off + I.row0 + rj]);
+              }
             }
             out[base + rj] = pn;
           }
@@ -341,7 +366,7 @@ batch_gemm_kernel(const BatchItem* __restrict__ items, int n_items, int* queue,
       }
     }
   }
-  if (drift_bits) atomic_max_nonneg(drift_bits, drift);
+  if (drift_bits) atomic_max_nonneg(drift_bits, fmax(drift, (double)driftf));
 }
 
 template <typename T, int MODE>

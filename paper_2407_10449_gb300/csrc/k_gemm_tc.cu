@@ -89,7 +89,7 @@ struct TcArgs {
   float* P32;                 // pairs mode outputs (either may be null)
   double* P64;
   int ldp;
-  const double* anorm;        // drift normalisation
+  const float* inv_anorm;     // drift normalisation: 1 / ||a_i|| (0 for a zero row)
   unsigned long long* drift_bits;
   int* status;
 };
@@ -528,25 +528,65 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
       if (ok && row < args.n_rows) {
         const float rs = args.row_scale[row];
         const size_t base = (size_t)row * args.ldp;
-        double drift = 0.0;
+        const bool full = n0 + BN <= args.n_cols;
+        if (args.P64) {
 #pragma unroll
-        for (int j = 0; j < BN; ++j) {
-          const int col = n0 + j;
-          if (col < args.n_cols) {
-            const float cs = args.col_scale[col];
-            if (args.P64) args.P64[base + col] = ((double)hi[j] + (double)lo[j]) * (double)rs * (double)cs;
-            if (args.P32) {
-              const float pnew = (hi[j] + lo[j]) * rs * cs;
-              if (args.drift_bits) {
-                const float old = args.P32[base + col];
-                drift = fmax(drift, fabs((double)pnew - (double)old) / args.anorm[col]);
-              }
-              args.P32[base + col] = pnew;
-            }
+          for (int j = 0; j < BN; ++j) {
+            const int col = n0 + j;
+            if (col < args.n_cols)
+              args.P64[base + col] =
+                  ((double)hi[j] + (double)lo[j]) * (double)rs * (double)args.col_scale[col];
           }
         }
-        if (args.drift_bits && drift > 0.0)
-          atomicMax(args.drift_bits, (unsigned long long)__double_as_longlong(drift));
+        if (args.P32) {
+          // p rounded once to float (the scales are powers of two), kept in hi
+#pragma unroll
+          for (int j = 0; j < BN; ++j) {
+            const int col = n0 + j;
+            hi[j] = (hi[j] + lo[j]) * rs * (col < args.n_cols ? args.col_scale[col] : 0.f);
+          }
+          // the drift statistic in FP32 (a diagnostic, far coarser than FP32);
+          // every old value is loaded before the first store, so the loads
+          // are in flight together
+          float* prow = args.P32 + base + n0;
+          const bool vec = full && (args.ldp & 3) == 0 && (n0 & 3) == 0 &&
+                           (reinterpret_cast<uintptr_t>(args.P32) & 15) == 0;
+          float drift = 0.f;
+          if (vec) {
+            float4* p4 = reinterpret_cast<float4*>(prow);
+            if (args.drift_bits) {
+              float4 old[BN / 4];
+#pragma unroll
+              for (int j = 0; j < BN / 4; ++j) old[j] = p4[j];
+#pragma unroll
+              for (int j = 0; j < BN / 4; ++j) {
+                const float* ia = args.inv_anorm + n0 + 4 * j;
+                drift = fmaxf(drift, fabsf(hi[4 * j] - old[j].x) * ia[0]);
+                drift = fmaxf(drift, fabsf(hi[4 * j + 1] - old[j].y) * ia[1]);
+                drift = fmaxf(drift, fabsf(hi[4 * j + 2] - old[j].z) * ia[2]);
+                drift = fmaxf(drift, fabsf(hi[4 * j + 3] - old[j].w) * ia[3]);
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < BN / 4; ++j)
+              p4[j] = make_float4(hi[4 * j], hi[4 * j + 1], hi[4 * j + 2], hi[4 * j + 3]);
+          } else {
+            if (args.drift_bits) {
+#pragma unroll
+              for (int j = 0; j < BN; ++j)
+                lo[j] = n0 + j < args.n_cols ? prow[j] : 0.f;
+#pragma unroll
+              for (int j = 0; j < BN; ++j)
+                if (n0 + j < args.n_cols)
+                  drift = fmaxf(drift, fabsf(hi[j] - lo[j]) * args.inv_anorm[n0 + j]);
+            }
+#pragma unroll
+            for (int j = 0; j < BN; ++j)
+              if (n0 + j < args.n_cols) prow[j] = hi[j];
+          }
+          if (args.drift_bits && drift > 0.f)
+            atomicMax(args.drift_bits, (unsigned long long)__double_as_longlong((double)drift));
+        }
       }
     }
   }
@@ -556,6 +596,266 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
   if (warp == 0) tmem_dealloc(tmem_d, TMEM_COLS);
 }
 
+
+// ---- q = A nu on SM pairs (tcgen05 cta_group::2) --------------------------------
+// The same FP16x3 sum as tc_gemm_kernel's sum mode, with one 256 x BN output
+// tile per cluster of two CTAs on two SMs.  CTA rank r holds chains
+// m0 + 128 r .. m0 + 128 r + 127 (its half of the MMA's M = 256) and rows
+// n0 + (BN / 2) r .. of A (its half of N); the leader (rank 0) issues
+// tcgen05.mma.cta_group::2, which reads both CTAs' shared memory at the same
+// offsets and writes each CTA's 128 accumulator lanes to its own TMEM.  Per
+// SM this loads (2 x 128 + BN) x 64 x 2 bytes per K block for a 128 x BN
+// output, against (2 x 128 + 2 BN) x 64 x 2 in the one-SM form: the L2 reads
+// and the tensor core's shared-memory reads of A fall by half.
+//   both CTAs, warp 0 / lane 0: TMA producer of the CTA's own tiles; every
+//     copy signals the leader's "full" barrier (the leader arms it with the
+//     bytes of both CTAs); a stage is refilled after the MMA's commit has
+//     arrived on the CTA's own "empty" barrier (multicast to both CTAs);
+//   leader, warp 1 / lane 0: MMA issuer; commits multicast to both CTAs;
+//   both CTAs, warps 2..5: epilogue of the CTA's 128 chains (as in the
+//     one-SM form).
+// Waits are bounded as in tc_gemm_kernel; on expiry the CTA sets
+// kStatusTimeout, the leader waits (bounded) for the copies it armed, and both
+// CTAs meet at a cluster barrier before TMEM is freed.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank) {
+  uint32_t a;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(local), "r"(rank));
+  return a;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+
+// TMA load into this CTA's shared memory, completion counted on the barrier at
+// cluster address bar (the leader's, for cta_group::2 consumers).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int x,
+                                                 int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_f16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive once on the barrier at the same shared-memory offset in both CTAs of
+// the pair when this thread's earlier MMAs have completed.
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
+  asm volatile(
+      "{\n\t.reg .b16 m;\n\tmov.b16 m, 3;\n\t"
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], m;\n\t}\n" ::"r"(bar)
+      : "memory");
+}
+
+template <int BN>
+constexpr uint32_t pair_stage_bytes() {
+  return 2u * (uint32_t)BM * BK * 2u + 2u * (uint32_t)(BN / 2) * BK * 2u;
+}
+
+template <int BN, int STAGES>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+tc_gemm_pair_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcArgs args) {
+  constexpr uint32_t A_BYTES = BM * BK * 2;                 // one chain-side slice tile
+  constexpr uint32_t B_BYTES = (BN / 2) * BK * 2;           // this CTA's half of an A slice tile
+  constexpr uint32_t STAGE_BYTES = pair_stage_bytes<BN>();
+  constexpr uint32_t TMEM_COLS = tmem_cols_for<BN>(2);
+  static_assert(B_BYTES % 1024 == 0, "BN / 2 must be a multiple of 8");
+  static_assert(BN % 32 == 0 && BN >= 64 && BN <= 256, "BN in {64, ..., 256}, multiple of 32");
+
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  unsigned char* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  const uint32_t sbase = smem_u32(smem);
+  // a spare half tile after the stages keeps every operand read of the last
+  // stage inside the tile area
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + B_BYTES);
+  // bars: [0, S) full (used in the leader), [S, 2S) empty, 2S accumulator full
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto full_bar = [&](int s) { return smem_u32(bars + s); };
+  auto empty_bar = [&](int s) { return smem_u32(bars + STAGES + s); };
+  const uint32_t accf = smem_u32(bars + 2 * STAGES);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int n0 = (blockIdx.x >> 1) * BN;
+  const int m0 = blockIdx.y * (2 * BM) + (int)rank * BM;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    mbar_init(accf, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    // one warp of each CTA of the pair allocates (the same columns in both)
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  cluster_sync_all();  // barriers of both CTAs initialised, TMEM address visible
+  tc_fence_after();
+  const uint32_t tmem_d = *tmem_slot;
+  const int kblocks = args.kblocks;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer (both CTAs) ----------------
+    const uint32_t full0 = cluster_addr(full_bar(0), 0);  // the leader's barriers
+    bool armed[STAGES];
+    uint32_t armed_phase[STAGES];
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) armed[s] = false;
+    int s = 0;
+    uint32_t phase = 0;
+    for (int kb = 0; kb < kblocks; ++kb) {
+      if (kb >= STAGES && !mbar_wait(empty_bar(s), phase ^ 1u)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      const uint32_t sa = sbase + s * STAGE_BYTES;
+      const uint32_t fb = full0 + (uint32_t)s * 8u;
+      if (leader) {
+        mbar_expect_tx(full_bar(s), 2u * STAGE_BYTES);
+        armed[s] = true;
+        armed_phase[s] = phase;
+      }
+      tma_load_2d_pair(sa, &maps.x[0], kb * BK, m0, fb);
+      tma_load_2d_pair(sa + A_BYTES, &maps.x[1], kb * BK, m0, fb);
+      tma_load_2d_pair(sa + 2 * A_BYTES, &maps.b[0], kb * BK, n0 + (int)rank * (BN / 2), fb);
+      tma_load_2d_pair(sa + 2 * A_BYTES + B_BYTES, &maps.b[1], kb * BK, n0 + (int)rank * (BN / 2),
+                       fb);
+      if (++s == STAGES) {
+        s = 0;
+        phase ^= 1u;
+      }
+    }
+    if (*abort_flag && leader) {
+      // the copies of both CTAs complete on the leader's barriers
+#pragma unroll
+      for (int j = 0; j < STAGES; ++j)
+        if (armed[j]) (void)mbar_wait(full_bar(j), armed_phase[j]);
+    }
+  } else if (warp == 1 && lane == 0 && leader) {
+    // ---------------- MMA issuer (leader) ----------------
+    // acc 0 (columns 0 .. BN-1): h0.a0; acc 1 (BN .. 2BN-1): h1.a0 + h0.a1
+    constexpr uint32_t idesc = idesc_f16(2 * BM, BN, false);
+    int s = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int kb = 0; kb < kblocks; ++kb) {
+      if (!mbar_wait(full_bar(s), phase)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sa = sbase + s * STAGE_BYTES;
+      const uint64_t x0 = smem_desc_sw128(sa);
+      const uint64_t x1 = smem_desc_sw128(sa + A_BYTES);
+      const uint64_t b0 = smem_desc_sw128(sa + 2 * A_BYTES);
+      const uint64_t b1 = smem_desc_sw128(sa + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k)  // each K = 16 step advances 32 bytes
+        umma_f16_pair(tmem_d, x0 + 2 * k, b0 + 2 * k, idesc, (kb == 0 && k == 0) ? 0u : 1u);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k)
+        umma_f16_pair(tmem_d + BN, x1 + 2 * k, b0 + 2 * k, idesc, (kb == 0 && k == 0) ? 0u : 1u);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k)
+        umma_f16_pair(tmem_d + BN, x0 + 2 * k, b1 + 2 * k, idesc, 1u);
+      umma_commit_pair(empty_bar(s));
+      if (++s == STAGES) {
+        s = 0;
+        phase ^= 1u;
+      }
+    }
+    if (ok) umma_commit_pair(accf);
+    else *abort_flag = 1;
+  } else if (warp >= 2) {
+    // ---------------- epilogue warps 2..5: TMEM lane quarter warp % 4 ----------------
+    const int quarter = warp & 3;
+    const int row = m0 + quarter * 32 + lane;
+    const uint32_t lane_base = tmem_d + ((uint32_t)(quarter * 32) << 16);
+    const bool ready = mbar_wait(accf, 0);
+    tc_fence_after();
+    if (!ready) *abort_flag = 1;
+    const bool row_ok = row < args.n_rows && ready && !*abort_flag;
+    float* qrow = args.Q + (size_t)(row_ok ? row : 0) * args.ldq;
+    const bool vec_ok = (args.ldq & 3) == 0 && ((reinterpret_cast<uintptr_t>(args.Q) & 15) == 0);
+    const float rsc = args.row_scale ? args.row_scale[row_ok ? row : 0] : args.row_const;
+    if (ready) {
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld_32cols(lane_base + (uint32_t)c0, v);
+        tmem_ld_wait();
+        float f[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]);
+        tmem_ld_32cols(lane_base + (uint32_t)(BN + c0), v);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) f[j] += __uint_as_float(v[j]);
+        if (!row_ok) continue;
+        const int col = n0 + c0;
+        if (vec_ok && col + 32 <= args.n_cols) {
+          // unscale by powers of two (exact): 1 / s_i per column, 1 / t_c per row
+          const float4* cs4 = reinterpret_cast<const float4*>(args.col_scale + col);
+          float4* dst = reinterpret_cast<float4*>(qrow + col);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 cs = __ldg(cs4 + j);
+            dst[j] = make_float4(f[4 * j] * cs.x * rsc, f[4 * j + 1] * cs.y * rsc,
+                                 f[4 * j + 2] * cs.z * rsc, f[4 * j + 3] * cs.w * rsc);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (col + j < args.n_cols) qrow[col + j] = f[j] * args.col_scale[col + j] * rsc;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag) {
+    // a copy of this CTA may still target its shared memory (the leader's
+    // drain above covers only the stages it armed): give it time to land
+    if (threadIdx.x == 0) atomicOr(args.status, kStatusTimeout);
+    for (int i = 0; i < 1000; ++i) __nanosleep(1000);
+  }
+  cluster_sync_all();  // the leader's MMAs no longer read the peer's shared memory
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_d),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
 
 // Fixed-point slices of the chain states for the exact refresh: per row c,
 // t_c = 2^e with max_j |x_cj| < t_c, and x_cj / t_c = sum_l e_l 2^(-w l) + r,
@@ -682,6 +982,47 @@ cudaError_t launch_bn(const TcMaps& maps, const TcArgs& args, cudaStream_t s) {
 }
 
 const int kWidths[6] = {64, 128, 160, 192, 224, 256};
+// SM-pair tiles: 256 chains x BN rows of A, reported as kPairCode + BN
+constexpr int kPairCode = 2000;
+const int kPairWidths[5] = {128, 160, 192, 224, 256};
+
+// Shared memory of the pair kernel: the stages, then one spare half tile of A
+// (BN / 2 rows), then the barriers.
+template <int BN>
+constexpr size_t pair_smem_bytes(int stages) {
+  return (size_t)stages * pair_stage_bytes<BN>() + (size_t)(BN / 2) * BK * 2 + 1024 + 256;
+}
+
+template <int BN>
+constexpr int pair_stages() {
+  constexpr int s = (kSmemLimit - 1024 - 256 - (BN / 2) * BK * 2) / (int)pair_stage_bytes<BN>();
+  return s > 6 ? 6 : s;
+}
+
+template <int BN>
+cudaError_t launch_pair_bn(const TcMaps& maps, const TcArgs& args, cudaStream_t s) {
+  constexpr int ST = pair_stages<BN>();
+  auto k = tc_gemm_pair_kernel<BN, ST>;
+  const size_t smem = pair_smem_bytes<BN>(ST);
+  static_assert(pair_smem_bytes<BN>(ST) <= (size_t)kSmemLimit, "pair kernel shared memory");
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // x: two CTAs (one cluster) per column tile; y: 256 chains per cluster
+  dim3 grid(2 * ((args.n_cols + BN - 1) / BN), (args.n_rows + 2 * BM - 1) / (2 * BM));
+  k<<<grid, kThreads, smem, s>>>(maps, args);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair(int bn, const TcMaps& maps, const TcArgs& args, cudaStream_t s) {
+  switch (bn) {
+    case 128: return launch_pair_bn<128>(maps, args, s);
+    case 160: return launch_pair_bn<160>(maps, args, s);
+    case 192: return launch_pair_bn<192>(maps, args, s);
+    case 224: return launch_pair_bn<224>(maps, args, s);
+    case 256: return launch_pair_bn<256>(maps, args, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_sum(int bn, const TcMaps& maps, const TcArgs& args, cudaStream_t s) {
   switch (bn) {
@@ -716,49 +1057,48 @@ struct TcGemmPlan {
   __half* a2[2] = {nullptr, nullptr};
   float* q_col_scale = nullptr;     // 1 / s_i
   CUtensorMap qmaps[6][2];
+  CUtensorMap pmaps[5][2];          // boxes of BN / 2 rows for the SM-pair tiles
   // exact refresh: fixed-point slices of A (per-row power-of-two scale)
   int w = 7, K = 5;
   __nv_bfloat16* aK = nullptr;      // K slices, m x ld_bf each
   float* col_scale = nullptr;       // s_i
+  float* inv_anorm = nullptr;       // 1 / ||a_i|| (drift statistic of the refresh)
   CUtensorMap rmaps[kMaxSlices];
   int bn_fixed = 0;                 // q GEMM tile width set by the autotuner (0: cost model)
   double bound_factor = 0.0;        // |p_exact - p| <= bound_factor * s_i * t_c
 };
 
 void tc_gemm_tile_for(int n_chains, int m, int* bn, int* stages) {
-  // Pick the tile width that minimises (waves of tiles) x (tile width): the
-  // per-tile time grows with BN, and the last wave is padded to the SM count.
-  // (ESS_Q_BN fixes the width at build time, for tuning sweeps.)
+  // One-SM tiles (128 chains x BN rows of A, code BN) or SM-pair tiles (256
+  // chains x BN, code kPairCode + BN).  With at least 256 chains the pair form
+  // is taken: per product it reads ~40 % fewer bytes from L2 and from shared
+  // memory.  Within a form, pick the width that minimises (waves of tiles) x
+  // (tile width): the per-tile time grows with BN, and the last wave is padded
+  // to the number of tile slots (SMs, or SM pairs).
+  // (ESS_Q_BN fixes the code at build time, for tuning sweeps.)
   const int sms = num_sms();
+  if (stages) *stages = 0;
 #ifdef ESS_Q_BN
   *bn = ESS_Q_BN;
-  if (stages) *stages = 0;
   (void)sms;
   return;
 #endif
-  const long long mt = (n_chains + BM - 1) / BM;
+  const bool pair = n_chains >= 2 * BM;
+  const int slots = pair ? std::max(1, sms / 2) : sms;
+  const long long mt = pair ? (n_chains + 2 * BM - 1) / (2 * BM) : (n_chains + BM - 1) / BM;
   int best = 256;
   long long best_cost = -1;
   for (int w : kWidths) {
+    if (pair && std::find(kPairWidths, kPairWidths + 5, w) == kPairWidths + 5) continue;
     const long long tiles = mt * ((m + w - 1) / w);
-    const long long waves = (tiles + sms - 1) / sms;
+    const long long waves = (tiles + slots - 1) / slots;
     const long long cost = waves * w;
     if (best_cost < 0 || cost < best_cost || (cost == best_cost && w > best)) {
       best_cost = cost;
       best = w;
     }
   }
-  *bn = best;
-  if (stages) {
-    switch (best) {
-      case 64: *stages = stages_for<64>(); break;
-      case 128: *stages = stages_for<128>(); break;
-      case 160: *stages = stages_for<160>(); break;
-      case 192: *stages = stages_for<192>(); break;
-      case 224: *stages = stages_for<224>(); break;
-      default: *stages = stages_for<256>(); break;
-    }
-  }
+  *bn = pair ? kPairCode + best : best;
 }
 
 int tc_refresh_slices(int d, int* w_out) {
@@ -814,6 +1154,9 @@ cudaError_t tc_gemm_create(TcGemmPlan** plan, const double* A, int m, int d) {
   for (int i = 0; i < 6 && e == cudaSuccess; ++i)
     for (int k = 0; k < 2 && e == cudaSuccess; ++k)
       e = make_map(&p->qmaps[i][k], p->a2[k], m, d, ld, kWidths[i], false);
+  for (int i = 0; i < 5 && e == cudaSuccess; ++i)
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+      e = make_map(&p->pmaps[i][k], p->a2[k], m, d, ld, kPairWidths[i] / 2, false);
   if (e != cudaSuccess) return fail(e);
 
   // --- exact refresh operands: fixed-point slices of A in FP64 on the host
@@ -843,6 +1186,17 @@ cudaError_t tc_gemm_create(TcGemmPlan** plan, const double* A, int m, int d) {
     e = cudaMemcpy(p->aK, slices.data(), sizeof(__nv_bfloat16) * slices.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&p->col_scale, sizeof(float) * m);
   if (e == cudaSuccess) e = cudaMemcpy(p->col_scale, cs.data(), sizeof(float) * m, cudaMemcpyHostToDevice);
+  {
+    std::vector<float> ia(m);
+    for (int i = 0; i < m; ++i) {
+      double nn = 0.0;
+      for (int j = 0; j < d; ++j) nn += A[(size_t)i * d + j] * A[(size_t)i * d + j];
+      ia[i] = nn > 0.0 ? (float)(1.0 / std::sqrt(nn)) : 0.f;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&p->inv_anorm, sizeof(float) * m);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->inv_anorm, ia.data(), sizeof(float) * m, cudaMemcpyHostToDevice);
+  }
   for (int k = 0; k < K && e == cudaSuccess; ++k)
     e = make_map(&p->rmaps[k], p->aK + (size_t)k * m * ld, m, d, ld, kRefreshBN);
   if (e != cudaSuccess) return fail(e);
@@ -860,14 +1214,18 @@ void tc_gemm_destroy(TcGemmPlan* plan) {
   if (plan->q_col_scale) cudaFree(plan->q_col_scale);
   if (plan->aK) cudaFree(plan->aK);
   if (plan->col_scale) cudaFree(plan->col_scale);
+  if (plan->inv_anorm) cudaFree(plan->inv_anorm);
   delete plan;
 }
 
-const int kTcWidths[6] = {64, 128, 160, 192, 224, 256};
+const int kTcWidths[11] = {64, 128, 160, 192, 224, 256,
+                           kPairCode + 128, kPairCode + 160, kPairCode + 192, kPairCode + 224,
+                           kPairCode + 256};
 
 cudaError_t tc_gemm_set_width(TcGemmPlan* plan, int bn) {
   if (!plan) return cudaErrorInvalidValue;
-  if (bn != 0 && std::find(kWidths, kWidths + 6, bn) == kWidths + 6) return cudaErrorInvalidValue;
+  if (bn != 0 && std::find(kTcWidths, kTcWidths + 11, bn) == kTcWidths + 11)
+    return cudaErrorInvalidValue;
   plan->bn_fixed = bn;
   return cudaSuccess;
 }
@@ -896,15 +1254,20 @@ cudaError_t tc_gemm_q(TcGemmPlan* plan, __half* const nu[2], const float* nu_uns
   if (!plan) return cudaErrorInvalidValue;
   if (n_chains == 0) return cudaSuccess;
   if (ld16 != plan->ld16) return cudaErrorInvalidValue;
-  const int bn = tc_gemm_width(plan, n_chains);
+  const int code = tc_gemm_width(plan, n_chains);
+  const bool pair = code > kPairCode;
+  const int bn = pair ? code - kPairCode : code;
+  const int* widths = pair ? kPairWidths : kWidths;
+  const int nw = pair ? 5 : 6;
   int wi = 0;
-  while (kWidths[wi] != bn) ++wi;
+  while (wi < nw && widths[wi] != bn) ++wi;
+  if (wi == nw) return cudaErrorInvalidValue;
   TcMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   for (int k = 0; k < 2; ++k) {
     cudaError_t e = make_map(&maps.x[k], nu[k], n_chains, plan->d, ld16, BM, false);
     if (e != cudaSuccess) return e;
-    maps.b[k] = plan->qmaps[wi][k];
+    maps.b[k] = pair ? plan->pmaps[wi][k] : plan->qmaps[wi][k];
   }
   TcArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -919,13 +1282,13 @@ cudaError_t tc_gemm_q(TcGemmPlan* plan, __half* const nu[2], const float* nu_uns
   a.row_const = 1.f / kNuSplitScale;
   a.col_scale = plan->q_col_scale;
   a.status = status;
-  return launch_sum(bn, maps, a, s);
+  return pair ? launch_pair(bn, maps, a, s) : launch_sum(bn, maps, a, s);
 }
 
 cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
                        __nv_bfloat16* x_slices, size_t slice_stride, float* row_scale,
-                       float* P32, double* P64, int ldp, const double* anorm,
-                       unsigned long long* drift_bits, int* status, cudaStream_t s) {
+                       float* P32, double* P64, int ldp, unsigned long long* drift_bits,
+                       int* status, cudaStream_t s) {
   if (!plan) return cudaErrorInvalidValue;
   if (n_chains == 0) return cudaSuccess;
   const int K = plan->K, ld = plan->ld16;
@@ -988,7 +1351,7 @@ cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
   a.P32 = P32;
   a.P64 = P64;
   a.ldp = ldp;
-  a.anorm = anorm;
+  a.inv_anorm = plan->inv_anorm;
   a.drift_bits = drift_bits;
   a.status = status;
   return launch_bn<kRefreshBN, kModePairs>(maps, a, s);

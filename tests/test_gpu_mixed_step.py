@@ -62,6 +62,39 @@ def test_products_tensor_core_gemm(n, m, d):
     assert np.all(np.abs(P - p_ref) <= tol), float(np.max(np.abs(P - p_ref) / tol))
 
 
+Q_TILES = [64, 128, 160, 192, 224, 256, 2128, 2160, 2192, 2224, 2256]
+
+
+@pytest.mark.parametrize("q_tile", Q_TILES)
+@pytest.mark.parametrize("n,m,d", [(513, 1000, 333), (256, 448, 64), (40, 300, 1000)])
+def test_q_gemm_every_tile(q_tile, n, m, d):
+    """Every tile form of the q GEMM (one SM per 128-chain tile, or an SM pair
+    per 256-chain tile with tcgen05 cta_group::2) within the FP16x3 bound, on
+    ragged chain counts (a cluster row with one live chain), ragged m and K."""
+    rng = np.random.default_rng(n + m + q_tile)
+    A = rng.standard_normal((m, d)) / math.sqrt(d)
+    NU = f32(rng.standard_normal((n, d)))
+    X = np.zeros((n, d))
+    s = ess.Sampler(A, np.ones(m), precision=ess.ESS_PREC_MIXED, q_tile=q_tile)
+    try:
+        _, Q = s.products(dev(X), dev(NU))
+        Q = host(Q)
+    finally:
+        s.close()
+    A32 = f32(A)
+    q_ref = NU @ A32.T
+    err = np.abs(Q - q_ref)
+    bound = q_error_bound(A32, NU)
+    assert np.all(err <= bound), float((err / bound).max())
+    assert np.median(err / np.maximum(bound, 1e-300)) < 0.2
+
+
+def test_q_tile_rejects_unknown_codes():
+    for bad in (1, 96, 2064, 2000, 3000, -1):
+        with pytest.raises(ess.EssError):
+            ess.Sampler(np.eye(3), np.ones(3), precision=ess.ESS_PREC_MIXED, q_tile=bad)
+
+
 def refresh_bound(A, X):
     """|p_refresh - A x| bound of the exact-split refresh: w-bit slices with
     (2^w - 1)^2 d <= 2^24, K = ceil(35 / w) slices per operand, per-row and
