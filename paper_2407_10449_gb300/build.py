@@ -25,6 +25,11 @@ LIB_PATH = os.path.join(HERE, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+# Per-file flags.  The warp-per-chain step kernel flushes FP32 subnormals to
+# zero: its float operands (p, q, b, angles) are O(1) quantities, and the
+# flush drops the subnormal fix-ups around rsqrt and the reciprocals of the
+# per-row classification.
+FILE_FLAGS = {"k_chain_warp.cu": ["-ftz=true"]}
 
 
 def nvcc() -> str:
@@ -59,7 +64,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *ARCH, *flags, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *flags, *FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -150,14 +150,17 @@ __device__ __forceinline__ int classify_row(T p, T q, T b, double b64, T tlo, T 
 }
 
 
-// Pseudo-angle of a nonzero vector (x, y): a strictly increasing function of
-// its polar angle in [0, 2 pi), with values in [0, 4) ("diamond angle", one
-// unit per quadrant).  Comparisons of pseudo-angles are comparisons of angles.
-// With yn = y / (|x| + |y|): quadrant I gives yn, II and III give 2 - yn,
-// IV gives 4 + yn (continuous across the quadrant boundaries).
-__device__ __forceinline__ float diamond_angle(float x, float y) {
-  const float yn = __fdividef(y, fabsf(x) + fabsf(y));
-  return x >= 0.f ? (y >= 0.f ? yn : 4.f + yn) : 2.f - yn;
+// Pseudo-angle of a nonzero vector (x, y): a non-decreasing function of its
+// polar angle in [0, 2 pi), with values in [0, 4], computed without
+// trigonometry.  With xn = x / (|x| + |y|) (in [-1, 1], decreasing in the
+// angle on [0, pi] and increasing on [pi, 2 pi]):
+//   y >= 0:  1 - xn   (0 at angle 0, 1 at pi / 2, 2 at pi)
+//   y <  0:  3 + xn   (2 at pi, 3 at 3 pi / 2, 4 at 2 pi)
+// i.e. 2 - copysign(1 + xn, y).  Comparisons of pseudo-angles are
+// comparisons of angles; its slope lies between 1/2 and 1 per radian.
+// inv is 1 / (|x| + |y|).
+__device__ __forceinline__ float pseudo_angle(float x, float y, float inv) {
+  return 2.f - copysignf(fmaf(x, inv, 1.f), y);
 }
 
 // Pseudo-angles of the two roots: with w = sqrt(r^2 - b^2), the points of the
@@ -165,65 +168,61 @@ __device__ __forceinline__ float diamond_angle(float x, float y) {
 //   u_alpha = (p b + q w, q b - p w)   (= r^2 (cos(tau - h), sin(tau - h)))
 //   u_beta  = (p b - q w, q b + p w)   (= r^2 (cos(tau + h), sin(tau + h)))
 // (App. B: cos tau = p / r, sin tau = q / r, cos h = b / r, sin h = w / r).
-// The row classes match roots(): the no-root and near-tangent decisions are
-// taken only outside a 1e-6 relative slack of the b/r computed here, and rows
-// whose arc would wrap through 0 (boundary points) are always kept.  b64
-// points at the exact b_i (read only when r = 0); nonfinite is set when p or
-// q is NaN or infinite (r^2 is then not finite).
-template <typename T>
-__device__ __forceinline__ int classify_phi(T p, T q, T b, const double* b64, T tlo, T thi,
-                                            float& pa, float& pb, bool& infeasible,
-                                            bool& nonfinite) {
-  const float pf = (float)p, qf = (float)q, bf = (float)b;
-  if constexpr (sizeof(T) == 4) {
-    const float r2 = fmaf(p, p, q * q);
-    nonfinite |= !(r2 <= FLT_MAX);  // NaN or Inf in p or q
-    if (r2 == 0.0f) {
-      infeasible = *b64 < 0.0;
-      return kRowNone;
-    }
-    const float ratio = b * rsqrtf(r2);
-    if (ratio >= thi * 1.000001f) return kRowNone;
-    if (fabsf(ratio) > tlo * 0.999999f) return kRowKeep;
-  } else {
-    const double r2 = p * p + q * q;
-    nonfinite |= !(r2 <= DBL_MAX);
-    const double r = sqrt(r2);
-    if (r == 0.0) {
-      infeasible = b < 0.0;
-      return kRowNone;
-    }
-    const double rd = b / r;
-    if (rd >= 1.0) return kRowNone;
-    if (fabs(rd) > tlo || r < 1e-30 || r > 1e30) return kRowKeep;
+__device__ __forceinline__ void root_pseudo_angles(float p, float q, float b, float w, float& pa,
+                                                   float& pb) {
+  const float pbv = p * b, qbv = q * b;
+  const float ax = fmaf(q, w, pbv), ay = fmaf(-p, w, qbv);
+  const float bx = fmaf(-q, w, pbv), by = fmaf(p, w, qbv);
+  pa = pseudo_angle(ax, ay, __fdividef(1.f, fabsf(ax) + fabsf(ay)));
+  pb = pseudo_angle(bx, by, __fdividef(1.f, fabsf(bx) + fabsf(by)));
+}
+
+// Row classes of the prune (FP64 chains): the no-root and near-tangent
+// decisions are the ones roots_dp takes; rows whose arc would wrap through 0
+// (boundary points) are always kept.  b64 points at the exact b_i; nonfinite
+// is set when p or q is NaN or infinite.
+__device__ __forceinline__ int classify_phi(double p, double q, double b, const double* b64,
+                                            double tlo, double thi, float& pa, float& pb,
+                                            bool& infeasible, bool& nonfinite) {
+  (void)b64;
+  (void)thi;
+  const double r2 = p * p + q * q;
+  nonfinite |= !(r2 <= DBL_MAX);
+  const double r = sqrt(r2);
+  if (r == 0.0) {
+    infeasible = b < 0.0;
+    return kRowNone;
   }
+  const double rd = b / r;
+  if (rd >= 1.0) return kRowNone;
+  if (fabs(rd) > tlo || r < 1e-30 || r > 1e30) return kRowKeep;
+  const float pf = (float)p, qf = (float)q, bf = (float)b;
   const float r2f = fmaf(pf, pf, qf * qf);
   const float w2 = fmaf(-bf, bf, r2f);
   if (!(w2 > 0.f)) return kRowKeep;
-  const float w = w2 * rsqrtf(w2);
-  pa = diamond_angle(fmaf(pf, bf, qf * w), fmaf(qf, bf, -pf * w));
-  pb = diamond_angle(fmaf(pf, bf, -qf * w), fmaf(qf, bf, pf * w));
+  root_pseudo_angles(pf, qf, bf, w2 * rsqrtf(w2), pa, pb);
   return pa < pb ? kRowApprox : kRowKeep;
 }
 
-// Branch-free float form of classify_phi (same classes and pseudo-angles):
-// every quantity is computed and the class picked by selects, so the rows of a
-// batch are straight-line code that the compiler can interleave.  pa and pb
-// are meaningful only for kRowApprox.
+// Row classes of the prune (float chains), branch-free so that the rows of a
+// batch interleave.  The no-root and near-tangent decisions compare b^2 with
+// r^2 times the squared thresholds, which carry a 1e-6 relative slack beyond
+// the ones roots() applies to b / r: only decisions that hold with that slack
+// are taken here, rows inside it are kept and get the exact test in roots().
+//   tlo2 = ((1 - thresh) (1 - 1e-6))^2,  thi2 = ((1 + thresh) (1 + 1e-6))^2.
+// pa and pb are meaningful only for kRowApprox.
 __device__ __forceinline__ int classify_phi_nb(float p, float q, float b, const double* b64,
-                                               float tlo, float thi, float& pa, float& pb,
+                                               float tlo2, float thi2, float& pa, float& pb,
                                                bool& infeasible, bool& nonfinite) {
   const float r2 = fmaf(p, p, q * q);
   nonfinite |= !(r2 <= FLT_MAX);  // NaN or Inf in p or q
-  const float ratio = b * rsqrtf(r2);
+  const float b2 = b * b;
   const float w2 = fmaf(-b, b, r2);
-  const float w = w2 * rsqrtf(fmaxf(w2, FLT_MIN));
-  pa = diamond_angle(fmaf(p, b, q * w), fmaf(q, b, -p * w));
-  pb = diamond_angle(fmaf(p, b, -q * w), fmaf(q, b, p * w));
+  root_pseudo_angles(p, q, b, w2 * rsqrtf(fmaxf(w2, FLT_MIN)), pa, pb);
   int cls = pa < pb ? kRowApprox : kRowKeep;
   cls = w2 > 0.f ? cls : kRowKeep;
-  cls = fabsf(ratio) > tlo * 0.999999f ? kRowKeep : cls;
-  cls = ratio >= thi * 1.000001f ? kRowNone : cls;
+  cls = b2 > tlo2 * r2 ? kRowKeep : cls;                 // |b / r| > 1 - thresh (with slack)
+  cls = b >= 0.f && b2 >= thi2 * r2 ? kRowNone : cls;    // b / r >= 1 + thresh (with slack)
   if (r2 == 0.0f) {  // rare: read the exact b only here
     infeasible = *b64 < 0.0;
     cls = kRowNone;

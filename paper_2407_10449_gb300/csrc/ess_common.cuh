@@ -79,16 +79,20 @@ __device__ __forceinline__ void box_muller4(const uint32_t r[4], float z[4]) {
   const float inv32 = 2.3283064365386963e-10f;  // 2^-32
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    // ln u1 with u1 = (r + 1) / 2^32: for u1 <= 1/2 directly; for u1 > 1/2 as
-    // log1p(-v) with v = 1 - u1 = (2^32 - 1 - r) / 2^32, so that the rounding
-    // of r to 24 bits never dominates a logarithm close to zero
+    // ln u1 with u1 = (r + 1) / 2^32: for u1 <= 1/2 directly, by the fast
+    // hardware logarithm (ln u1 <= -ln 2 there, so its relative error stays
+    // below 2^-21); for u1 > 1/2 as log1p(-v) with v = 1 - u1 =
+    // (2^32 - 1 - r) / 2^32, so that the rounding of r to 24 bits never
+    // dominates a logarithm close to zero
     const uint32_t r0 = r[2 * k];
-    const float lnu = r0 < 0x80000000u ? logf(fmaf((float)r0, inv32, inv32))
+    const float lnu = r0 < 0x80000000u ? __logf(fmaf((float)r0, inv32, inv32))
                                        : log1pf(-(float)(~r0) * inv32);
-    float u2 = (float)r[2 * k + 1] * inv32;
-    float rad = sqrtf(-2.0f * lnu);
+    const float u2 = (float)r[2 * k + 1] * inv32;
+    const float rad = sqrtf(-2.0f * lnu);
+    // cos and sin of 2 pi u2 by the hardware approximations on the reduced
+    // angle 2 pi (u2 - rint(u2)) in [-pi, pi] (absolute error below 2^-21)
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
+    __sincosf(6.28318530717958648f * (u2 - rintf(u2)), &s, &c);
     z[2 * k] = rad * c;
     z[2 * k + 1] = rad * s;
   }

@@ -53,9 +53,14 @@ constexpr int kFirst = 256;               // rows of the first batch
 // different banks.
 __device__ __forceinline__ int bslot(int j) { return j + (j >> 5); }
 
-// Bucket of a pseudo-angle in [0, 4).
+// Bucket of a pseudo-angle in [0, 4]: pa * kWB / 4 rounded to the nearest
+// integer by the float add-and-round idiom (2^23 + 2^22 added, the integer
+// read from the low mantissa bits), clamped to [0, kWB - 1].  Any
+// non-decreasing map would do: the prune only needs bucket(a) < bucket(b) to
+// imply a < b.  NaN pseudo-angles (non-finite rows) land in a valid bucket.
 __device__ __forceinline__ int pbucket(float pa) {
-  return min(kWB - 1, (int)(pa * (kWB / 4.0f)));
+  const int k = __float_as_int(fmaf(pa, kWB / 4.0f, 12582912.0f)) - 0x4B400000;
+  return min(max(k, 0), kWB - 1);
 }
 
 // In-place inclusive prefix max of kWB bucket maxima (float bits, >= 0).
@@ -176,6 +181,10 @@ chain_warp_kernel(ChainParams<T> prm) {
     __syncwarp();
     const T tlo = (T)(1.0 - prm.tangent_thresh);
     const T thi = (T)(1.0 + prm.tangent_thresh);
+    // squared thresholds of the float classification (1e-6 relative slack)
+    const float tlo_s = (float)((1.0 - prm.tangent_thresh) * 0.999999);
+    const float thi_s = (float)((1.0 + prm.tangent_thresh) * 1.000001);
+    const float tlo2 = tlo_s * tlo_s, thi2 = thi_s * thi_s;
     bool infeasible = false, nonfinite = false;
 
     // ---- 1a. a first batch of rows builds bucket maxima of beta ---------------
@@ -199,9 +208,9 @@ chain_warp_kernel(ChainParams<T> prm) {
           bool inf_row = false, nf = false;
           int cls;
           if constexpr (sizeof(T) == 4)
-            cls = classify_phi_nb(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb, inf_row, nf);
+            cls = classify_phi_nb(pv[k], qv[k], bv[k], v.b64 + i, tlo2, thi2, pa, pb, inf_row, nf);
           else
-            cls = classify_phi<T>(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb, inf_row, nf);
+            cls = classify_phi(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb, inf_row, nf);
           if (cls == kRowApprox) atomicMax(&bsub[bslot(pbucket(pa))], __float_as_uint(pb));
         }
       }
@@ -234,10 +243,10 @@ chain_warp_kernel(ChainParams<T> prm) {
           if constexpr (sizeof(T) == 4) {
             // straight-line form: class, bucket test and candidate code by
             // selects (the rows of the batch interleave)
-            const int cls = classify_phi_nb(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb,
+            const int cls = classify_phi_nb(pv[k], qv[k], bv[k], v.b64 + i, tlo2, thi2, pa, pb,
                                             inf_row, nonfinite);
             infeasible |= inf_row;
-            const int bk = pbucket(fminf(fmaxf(pa, 0.f), 4.f));
+            const int bk = pbucket(pa);
             const float dom = __uint_as_float(bsub[bslot(max(bk - 2, 0))]);
             const bool undominated = bk < 2 || !(pb + 2.f * kPhiMargin <= dom);
             const bool approx = cls == kRowApprox;
@@ -249,8 +258,8 @@ chain_warp_kernel(ChainParams<T> prm) {
             code = cls == kRowKeep ? (0x80000000u | (unsigned)i)
                                    : (((unsigned)bk << 14) | (unsigned)i);
           } else {
-            const int cls = classify_phi<T>(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb,
-                                            inf_row, nonfinite);
+            const int cls = classify_phi(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb,
+                                         inf_row, nonfinite);
             infeasible |= inf_row;
             if (cls == kRowKeep) {
               cand = true;

@@ -6,10 +6,8 @@
 namespace ess {
 namespace {
 
-__device__ __forceinline__ uint2 pack4(const __half (&v)[4]) {
-  const uint32_t lo = (uint32_t)__half_as_ushort(v[0]) | ((uint32_t)__half_as_ushort(v[1]) << 16);
-  const uint32_t hi = (uint32_t)__half_as_ushort(v[2]) | ((uint32_t)__half_as_ushort(v[3]) << 16);
-  return make_uint2(lo, hi);
+__device__ __forceinline__ uint32_t h2_bits(__half2 v) {
+  return *reinterpret_cast<const uint32_t*>(&v);
 }
 
 // One thread per (chain, Philox block): 4 consecutive coordinates.
@@ -57,23 +55,25 @@ __global__ void draw_nu_f32_kernel(float* __restrict__ nu, int ld, __half* __res
   }
   if (h0 != nullptr) {
     // two-way fp16 split of nu * 2^12 (|nu| < 6.67 keeps it below 2^15):
-    // y = a + b + r with a = fp16(y), b = fp16(y - a)
-    __half a[4], b[4];
+    // y = a + b + r with a = fp16(y), b = fp16(y - a), two values per
+    // conversion instruction
+    __half2 a[2], b[2];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float y = z[k] * kNuSplitScale;
-      a[k] = __float2half_rn(y);
-      b[k] = __float2half_rn(y - __half2float(a[k]));
+    for (int k = 0; k < 2; ++k) {
+      const float2 y = make_float2(z[2 * k] * kNuSplitScale, z[2 * k + 1] * kNuSplitScale);
+      a[k] = __float22half2_rn(y);
+      const float2 af = __half22float2(a[k]);
+      b[k] = __float22half2_rn(make_float2(y.x - af.x, y.y - af.y));
     }
     const size_t o = (size_t)c * ld16 + 4 * n;
     if (left >= 4 && (o & 3) == 0) {
       // 8-byte stores of four fp16 values (ld16 is a multiple of 8)
-      *reinterpret_cast<uint2*>(h0 + o) = pack4(a);
-      *reinterpret_cast<uint2*>(h1 + o) = pack4(b);
+      *reinterpret_cast<uint2*>(h0 + o) = make_uint2(h2_bits(a[0]), h2_bits(a[1]));
+      *reinterpret_cast<uint2*>(h1 + o) = make_uint2(h2_bits(b[0]), h2_bits(b[1]));
     } else {
       for (int k = 0; k < 4 && k < left; ++k) {
-        h0[o + k] = a[k];
-        h1[o + k] = b[k];
+        h0[o + k] = (k & 1) ? __high2half(a[k >> 1]) : __low2half(a[k >> 1]);
+        h1[o + k] = (k & 1) ? __high2half(b[k >> 1]) : __low2half(b[k >> 1]);
       }
     }
   }
