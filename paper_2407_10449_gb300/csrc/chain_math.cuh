@@ -210,10 +210,12 @@ __device__ __forceinline__ int classify_phi(double p, double q, double b, const 
 // the ones roots() applies to b / r: only decisions that hold with that slack
 // are taken here, rows inside it are kept and get the exact test in roots().
 //   tlo2 = ((1 - thresh) (1 - 1e-6))^2,  thi2 = ((1 + thresh) (1 + 1e-6))^2.
-// pa and pb are meaningful only for kRowApprox.
-__device__ __forceinline__ int classify_phi_nb(float p, float q, float b, const double* b64,
-                                               float tlo2, float thi2, float& pa, float& pb,
-                                               bool& infeasible, bool& nonfinite) {
+// pa and pb are meaningful only for kRowApprox.  A row with r = 0 has no
+// root; it sets *zero, and the caller decides infeasibility from the exact b_i
+// (b_i < 0) outside the hot loop.
+__device__ __forceinline__ int classify_phi_nb(float p, float q, float b, float tlo2, float thi2,
+                                               float& pa, float& pb, bool& zero,
+                                               bool& nonfinite) {
   const float r2 = fmaf(p, p, q * q);
   nonfinite |= !(r2 <= FLT_MAX);  // NaN or Inf in p or q
   const float b2 = b * b;
@@ -223,11 +225,8 @@ __device__ __forceinline__ int classify_phi_nb(float p, float q, float b, const 
   cls = w2 > 0.f ? cls : kRowKeep;
   cls = b2 > tlo2 * r2 ? kRowKeep : cls;                 // |b / r| > 1 - thresh (with slack)
   cls = b >= 0.f && b2 >= thi2 * r2 ? kRowNone : cls;    // b / r >= 1 + thresh (with slack)
-  if (r2 == 0.0f) {  // rare: read the exact b only here
-    infeasible = *b64 < 0.0;
-    cls = kRowNone;
-  }
-  return cls;
+  zero = r2 == 0.0f;
+  return zero ? kRowNone : cls;
 }
 
 }  // namespace chainmath

@@ -208,7 +208,7 @@ chain_warp_kernel(ChainParams<T> prm) {
           bool inf_row = false, nf = false;
           int cls;
           if constexpr (sizeof(T) == 4)
-            cls = classify_phi_nb(pv[k], qv[k], bv[k], v.b64 + i, tlo2, thi2, pa, pb, inf_row, nf);
+            cls = classify_phi_nb(pv[k], qv[k], bv[k], tlo2, thi2, pa, pb, inf_row, nf);
           else
             cls = classify_phi(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb, inf_row, nf);
           if (cls == kRowApprox) atomicMax(&bsub[bslot(pbucket(pa))], __float_as_uint(pb));
@@ -231,6 +231,7 @@ chain_warp_kernel(ChainParams<T> prm) {
         qv[k] = i < m ? Qrow[i] : T(0);
         bv[k] = i < m ? v.b[i] : T(0);
       }
+      unsigned zmask = 0u;  // float rows of the batch with r = 0 (no root)
 #pragma unroll
       for (int k = 0; k < kBatch; ++k) {
         const int i = i0 + lane + 32 * k;
@@ -243,9 +244,10 @@ chain_warp_kernel(ChainParams<T> prm) {
           if constexpr (sizeof(T) == 4) {
             // straight-line form: class, bucket test and candidate code by
             // selects (the rows of the batch interleave)
-            const int cls = classify_phi_nb(pv[k], qv[k], bv[k], v.b64 + i, tlo2, thi2, pa, pb,
-                                            inf_row, nonfinite);
-            infeasible |= inf_row;
+            bool zero = false;
+            const int cls = classify_phi_nb(pv[k], qv[k], bv[k], tlo2, thi2, pa, pb, zero,
+                                            nonfinite);
+            zmask |= (zero ? 1u : 0u) << k;
             const int bk = pbucket(pa);
             const float dom = __uint_as_float(bsub[bslot(max(bk - 2, 0))]);
             const bool undominated = bk < 2 || !(pb + 2.f * kPhiMargin <= dom);
@@ -279,6 +281,11 @@ chain_warp_kernel(ChainParams<T> prm) {
           candb[at] = pb;
         }
         n_cand += __popc(ball);
+      }
+      // rare: r = 0 with b_i < 0 means x violates row i (App. B)
+      if (zmask) {
+        for (int k = 0; k < kBatch; ++k)
+          if ((zmask >> k) & 1u) infeasible |= v.b64[i0 + lane + 32 * k] < 0.0;
       }
     }
     __syncwarp();
@@ -458,8 +465,12 @@ chain_warp_kernel(ChainParams<T> prm) {
           const int i = i0 + lane + 32 * k;
           pv[k] = i < m ? Prow[i] : T(0);
           qv[k] = i < m ? Qrow[i] : T(0);
-          sv[k] = i < m ? (v.slack ? v.slack[i] : (T)(v.b64[i] - prm.margin * v.anorm[i]))
-                        : T(0);
+          if constexpr (sizeof(T) == 4) {
+            sv[k] = i < m ? v.slack[i] : T(0);  // float chains always carry the thresholds
+          } else {
+            sv[k] = i < m ? (v.slack ? v.slack[i] : (T)(v.b64[i] - prm.margin * v.anorm[i]))
+                          : T(0);
+          }
         }
         unsigned flags = 0u;
 #pragma unroll
@@ -560,6 +571,7 @@ template <typename T>
 cudaError_t launch_chain_step_warp(const ChainParams<T>& p, cudaStream_t s) {
   if (p.n_chains <= 0) return cudaSuccess;
   if (p.P_out == p.P_in || !p.overflow_list || !p.overflow_count) return cudaErrorInvalidValue;
+  if (sizeof(T) == 4 && p.slack == nullptr) return cudaErrorInvalidValue;
   const size_t smem = chain_warp_smem_bytes<T>(p.m);
   auto k = p.desc ? chain_warp_kernel<T, kWarps, true> : chain_warp_kernel<T, kWarps, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
