@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 #include "chain_math.cuh"
 #include "ess_kernels.cuh"
@@ -55,12 +56,14 @@ __device__ __forceinline__ int bslot(int j) { return j + (j >> 5); }
 
 // Bucket of a pseudo-angle in [0, 4]: pa * kWB / 4 rounded to the nearest
 // integer by the float add-and-round idiom (2^23 + 2^22 added, the integer
-// read from the low mantissa bits), clamped to [0, kWB - 1].  Any
+// read from the low mantissa bits), clamped to [0, kWB - 3].  Any
 // non-decreasing map would do: the prune only needs bucket(a) < bucket(b) to
 // imply a < b.  NaN pseudo-angles (non-finite rows) land in a valid bucket.
+// The maxima of bucket j are kept in slot j + 2, so that after the prefix
+// max, slot j holds the maxima of the buckets up to j - 2 (zero for j < 2).
 __device__ __forceinline__ int pbucket(float pa) {
   const int k = __float_as_int(fmaf(pa, kWB / 4.0f, 12582912.0f)) - 0x4B400000;
-  return min(max(k, 0), kWB - 1);
+  return min(max(k, 0), kWB - 3);
 }
 
 // In-place inclusive prefix max of kWB bucket maxima (float bits, >= 0).
@@ -211,7 +214,7 @@ chain_warp_kernel(ChainParams<T> prm) {
             cls = classify_phi_nb(pv[k], qv[k], bv[k], tlo2, thi2, pa, pb, inf_row, nf);
           else
             cls = classify_phi(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb, inf_row, nf);
-          if (cls == kRowApprox) atomicMax(&bsub[bslot(pbucket(pa))], __float_as_uint(pb));
+          if (cls == kRowApprox) atomicMax(&bsub[bslot(pbucket(pa) + 2)], __float_as_uint(pb));
         }
       }
     }
@@ -222,44 +225,83 @@ chain_warp_kernel(ChainParams<T> prm) {
     // ---- 1b. every row: full bucket maxima, candidates not dominated by an
     //          arc of the first batch ------------------------------------------
     int n_cand = 0;
-    for (int i0 = 0; i0 < m; i0 += 32 * kBatch) {
-      T pv[kBatch], qv[kBatch], bv[kBatch];
-#pragma unroll
-      for (int k = 0; k < kBatch; ++k) {
-        const int i = i0 + lane + 32 * k;
-        pv[k] = i < m ? Prow[i] : T(0);
-        qv[k] = i < m ? Qrow[i] : T(0);
-        bv[k] = i < m ? v.b[i] : T(0);
+    // candidate compaction of one row slot of the batch
+    auto push = [&](bool cand, unsigned code, float pb) {
+      const unsigned ball = __ballot_sync(kFull, cand);
+      const int at = n_cand + __popc(ball & ((1u << lane) - 1u));
+      if (cand && at < kCand) {
+        candc[at] = code;
+        candb[at] = pb;
       }
-      unsigned zmask = 0u;  // float rows of the batch with r = 0 (no root)
+      n_cand += __popc(ball);
+    };
+    if constexpr (sizeof(T) == 4) {
+      // One batch of 32 kBatch rows in straight-line form (class, bucket test
+      // and candidate code by selects, so the rows interleave); FULL batches
+      // skip the bounds checks.
+      auto batch = [&](int i0, auto full_tag) {
+        constexpr bool FULL = decltype(full_tag)::value;
+        float pv[kBatch], qv[kBatch], bv[kBatch];
 #pragma unroll
-      for (int k = 0; k < kBatch; ++k) {
-        const int i = i0 + lane + 32 * k;
-        bool cand = false;
-        unsigned code = 0u;
-        float pb = 0.f;
-        if (i < m) {
-          float pa = 0.f;
-          bool inf_row = false;
-          if constexpr (sizeof(T) == 4) {
-            // straight-line form: class, bucket test and candidate code by
-            // selects (the rows of the batch interleave)
-            bool zero = false;
-            const int cls = classify_phi_nb(pv[k], qv[k], bv[k], tlo2, thi2, pa, pb, zero,
-                                            nonfinite);
-            zmask |= (zero ? 1u : 0u) << k;
-            const int bk = pbucket(pa);
-            const float dom = __uint_as_float(bsub[bslot(max(bk - 2, 0))]);
-            const bool undominated = bk < 2 || !(pb + 2.f * kPhiMargin <= dom);
-            const bool approx = cls == kRowApprox;
-            cand = cls == kRowKeep || (approx && undominated);
-            // a row dominated by the first batch adds nothing to the full
-            // maxima: the first-batch arc that covers it dominates every arc
-            // it would dominate
-            if (approx && undominated) atomicMax(&bfull[bslot(bk)], __float_as_uint(pb));
-            code = cls == kRowKeep ? (0x80000000u | (unsigned)i)
-                                   : (((unsigned)bk << 14) | (unsigned)i);
-          } else {
+        for (int k = 0; k < kBatch; ++k) {
+          const int i = i0 + lane + 32 * k;
+          pv[k] = FULL || i < m ? Prow[i] : 0.f;
+          qv[k] = FULL || i < m ? Qrow[i] : 0.f;
+          bv[k] = FULL || i < m ? v.b[i] : 0.f;
+        }
+        unsigned zmask = 0u;  // rows of the batch with r = 0 (no root)
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+          const int i = i0 + lane + 32 * k;
+          float pa = 0.f, pb = 0.f;
+          bool zero = false;
+          int cls = classify_phi_nb(pv[k], qv[k], bv[k], tlo2, thi2, pa, pb, zero, nonfinite);
+          if (!FULL) {
+            // padding slots past the last row (p = q = 0) are no rows at all
+            cls = i < m ? cls : kRowNone;
+            zero = zero && i < m;
+          }
+          zmask |= (zero ? 1u : 0u) << k;
+          const int bk = pbucket(pa);
+          // bucket maxima sit two slots up: slot bk holds the maxima of the
+          // arcs that start at least two buckets earlier
+          const bool undominated = !(pb + 2.f * kPhiMargin <= __uint_as_float(bsub[bslot(bk)]));
+          const bool approx = cls == kRowApprox;
+          // a row dominated by the first batch adds nothing to the full
+          // maxima: the first-batch arc that covers it dominates every arc
+          // it would dominate
+          if (approx && undominated) atomicMax(&bfull[bslot(bk + 2)], __float_as_uint(pb));
+          push(cls == kRowKeep || (approx && undominated),
+               cls == kRowKeep ? (0x80000000u | (unsigned)i) : (((unsigned)bk << 14) | (unsigned)i),
+               pb);
+        }
+        // rare: r = 0 with b_i < 0 means x violates row i (App. B)
+        if (zmask) {
+          for (int k = 0; k < kBatch; ++k)
+            if ((zmask >> k) & 1u) infeasible |= v.b64[i0 + lane + 32 * k] < 0.0;
+        }
+      };
+      int i0 = 0;
+      for (; i0 + 32 * kBatch <= m; i0 += 32 * kBatch) batch(i0, std::true_type{});
+      if (i0 < m) batch(i0, std::false_type{});
+    } else {
+      for (int i0 = 0; i0 < m; i0 += 32 * kBatch) {
+        T pv[kBatch], qv[kBatch], bv[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+          const int i = i0 + lane + 32 * k;
+          pv[k] = i < m ? Prow[i] : T(0);
+          qv[k] = i < m ? Qrow[i] : T(0);
+          bv[k] = i < m ? v.b[i] : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+          const int i = i0 + lane + 32 * k;
+          bool cand = false;
+          unsigned code = 0u;
+          float pa = 0.f, pb = 0.f;
+          if (i < m) {
+            bool inf_row = false;
             const int cls = classify_phi(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb,
                                          inf_row, nonfinite);
             infeasible |= inf_row;
@@ -268,24 +310,13 @@ chain_warp_kernel(ChainParams<T> prm) {
               code = 0x80000000u | (unsigned)i;
             } else if (cls == kRowApprox) {
               const int bk = pbucket(pa);
-              cand = bk < 2 || !(pb + 2.f * kPhiMargin <= __uint_as_float(bsub[bslot(bk - 2)]));
-              if (cand) atomicMax(&bfull[bslot(bk)], __float_as_uint(pb));
+              cand = !(pb + 2.f * kPhiMargin <= __uint_as_float(bsub[bslot(bk)]));
+              if (cand) atomicMax(&bfull[bslot(bk + 2)], __float_as_uint(pb));
               code = ((unsigned)bk << 14) | (unsigned)i;
             }
           }
+          push(cand, code, pb);
         }
-        const unsigned ball = __ballot_sync(kFull, cand);
-        const int at = n_cand + __popc(ball & ((1u << lane) - 1u));
-        if (cand && at < kCand) {
-          candc[at] = code;
-          candb[at] = pb;
-        }
-        n_cand += __popc(ball);
-      }
-      // rare: r = 0 with b_i < 0 means x violates row i (App. B)
-      if (zmask) {
-        for (int k = 0; k < kBatch; ++k)
-          if ((zmask >> k) & 1u) infeasible |= v.b64[i0 + lane + 32 * k] < 0.0;
       }
     }
     __syncwarp();
@@ -306,7 +337,7 @@ chain_warp_kernel(ChainParams<T> prm) {
             keep = true;
           } else {
             const int bk = (int)((code >> 14) & 0x3FFu);
-            keep = bk < 2 || !(candb[e] + 2.f * kPhiMargin <= __uint_as_float(bfull[bslot(bk - 2)]));
+            keep = !(candb[e] + 2.f * kPhiMargin <= __uint_as_float(bfull[bslot(bk)]));
           }
         }
         const unsigned ball = __ballot_sync(kFull, keep);
