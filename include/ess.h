@@ -96,8 +96,11 @@ typedef struct {
                                    per tile of 128 chains x BN rows of A;
                                    2000 + BN, BN in {128, ..., 256}: a pair of
                                    SMs (tcgen05 cta_group::2) per tile of 256
-                                   chains x BN rows.  Any other value is
-                                   ESS_ERR_ARG. */
+                                   chains x BN rows, one launch per tile;
+                                   3000 + BN: the same tiles in a persistent
+                                   kernel, one cluster per SM pair (when m is
+                                   not a multiple of 4, 2000 + BN runs).  Any
+                                   other value is ESS_ERR_ARG. */
     int reserved[6];
 } ess_config;
 

@@ -600,8 +600,9 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
       !(c.residual_margin >= 0.0))
     return fail(ESS_ERR_ARG, "tangent_thresh in [0, 1), trim_eps >= 0, residual_margin >= 0");
   if (c.q_tile != 0 &&
-      std::find(ess::kTcWidths, ess::kTcWidths + 11, c.q_tile) == ess::kTcWidths + 11)
-    return fail(ESS_ERR_ARG, "q_tile: 0, 64/128/160/192/224/256, or 2000 + 128/160/192/224/256");
+      std::find(ess::kTcWidths, ess::kTcWidths + 16, c.q_tile) == ess::kTcWidths + 16)
+    return fail(ESS_ERR_ARG,
+                "q_tile: 0, 64/128/160/192/224/256, or 2000/3000 + 128/160/192/224/256");
 
   const int min_threads = ess::chain_threads_for(m);
   if (min_threads == 0)

@@ -56,11 +56,14 @@ const float* tc_refresh_col_scale(const TcGemmPlan* plan);
 
 // Tile of the q GEMM chosen for a shape: BN for one-SM tiles of 128 chains x
 // BN rows of A, 2000 + BN for SM-pair tiles (tcgen05 cta_group::2) of 256
-// chains x BN rows.  *stages (if given) is set to 0.
+// chains x BN rows with one launch per tile, 3000 + BN for the same tiles in a
+// persistent kernel (one cluster per SM pair, TMA-stored Q; used when the Q
+// row stride is a multiple of 4 floats, else 2000 + BN).  *stages (if given)
+// is set to 0.
 void tc_gemm_tile_for(int n_chains, int m, int* bn, int* stages);
 // Tile codes the q GEMM supports, and a fixed code for a plan (0: the cost
 // model of tc_gemm_tile_for); the code tc_gemm_q uses for n_chains.
-extern const int kTcWidths[11];
+extern const int kTcWidths[16];
 cudaError_t tc_gemm_set_width(TcGemmPlan* plan, int bn);
 int tc_gemm_width(const TcGemmPlan* plan, int n_chains);
 

@@ -75,6 +75,7 @@ struct RefreshRound {
 struct TcMaps {
   CUtensorMap x[kMaxSlices];  // chain-side operand slices (M = chains)
   CUtensorMap b[kMaxSlices];  // constraint-side operand slices (N = rows of A)
+  CUtensorMap q;              // Q, 32 x 32 fp32 blocks (persistent pair form)
 };
 
 struct TcArgs {
@@ -857,6 +858,259 @@ tc_gemm_pair_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__
                  : "memory");
 }
 
+// ---- q = A nu on SM pairs, persistent ---------------------------------------------
+// The SM-pair form of tc_gemm_pair_kernel with one cluster per SM pair looping
+// over the 256 x BN output tiles (tile cid, cid + nclusters, ...).  The
+// producers stream the K blocks of consecutive tiles through the stage ring
+// without a break; the MMA issuer starts a tile as soon as both CTAs'
+// epilogues have read the previous accumulators out of TMEM (the leader's
+// "accumulator empty" barrier, one arrival per epilogue warp of either CTA);
+// the epilogue writes each 32 x 32 block of Q through a 128-byte-swizzled
+// shared staging buffer (two per warp) and a TMA store, so that its global
+// writes overlap the next tile's loads and MMAs.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(src)
+      : "memory");
+}
+
+constexpr uint32_t kStageQ = 32u * 32u * 4u;  // one 32 x 32 fp32 block of Q
+
+template <int BN, int STAGES>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+tc_gemm_pair_persistent_kernel(const __grid_constant__ TcMaps maps,
+                               const __grid_constant__ TcArgs args) {
+  constexpr uint32_t A_BYTES = BM * BK * 2;
+  constexpr uint32_t B_BYTES = (BN / 2) * BK * 2;
+  constexpr uint32_t STAGE_BYTES = pair_stage_bytes<BN>();
+  constexpr uint32_t TMEM_COLS = tmem_cols_for<BN>(2);
+  static_assert(B_BYTES % 1024 == 0, "BN / 2 must be a multiple of 8");
+  static_assert(BN % 32 == 0 && BN >= 64 && BN <= 256, "BN in {64, ..., 256}, multiple of 32");
+
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  unsigned char* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  const uint32_t sbase = smem_u32(smem);
+  // [stages][4 warps x 2 Q staging blocks][barriers]
+  const uint32_t qstage = sbase + STAGES * STAGE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + 8 * kStageQ);
+  // bars: [0, S) full (leader), [S, 2S) empty, 2S accumulator full, 2S + 1 accumulator empty (leader)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto full_bar = [&](int s) { return smem_u32(bars + s); };
+  auto empty_bar = [&](int s) { return smem_u32(bars + STAGES + s); };
+  const uint32_t accf = smem_u32(bars + 2 * STAGES);
+  const uint32_t acce = smem_u32(bars + 2 * STAGES + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int cid = blockIdx.x >> 1, nclusters = gridDim.x >> 1;
+  const int ncol = (args.n_cols + BN - 1) / BN;
+  const int ntiles = ncol * ((args.n_rows + 2 * BM - 1) / (2 * BM));
+  const int kblocks = args.kblocks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(acce, 8);  // 4 epilogue warps in each CTA of the pair
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  cluster_sync_all();
+  tc_fence_after();
+  const uint32_t tmem_d = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer (both CTAs), K blocks of every tile ----------------
+    const uint32_t full0 = cluster_addr(full_bar(0), 0);
+    bool armed[STAGES];
+    uint32_t armed_phase[STAGES];
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) armed[s] = false;
+    int s = 0, count = 0;
+    uint32_t phase = 0;
+    for (int t = cid; t < ntiles && !*abort_flag; t += nclusters) {
+      const int m0 = (t / ncol) * (2 * BM) + (int)rank * BM;
+      const int nb = (t % ncol) * BN + (int)rank * (BN / 2);
+      for (int kb = 0; kb < kblocks; ++kb, ++count) {
+        if (count >= STAGES && !mbar_wait(empty_bar(s), phase ^ 1u)) {
+          *abort_flag = 1;
+          break;
+        }
+        const uint32_t sa = sbase + s * STAGE_BYTES;
+        const uint32_t fb = full0 + (uint32_t)s * 8u;
+        if (leader) {
+          mbar_expect_tx(full_bar(s), 2u * STAGE_BYTES);
+          armed[s] = true;
+          armed_phase[s] = phase;
+        }
+        tma_load_2d_pair(sa, &maps.x[0], kb * BK, m0, fb);
+        tma_load_2d_pair(sa + A_BYTES, &maps.x[1], kb * BK, m0, fb);
+        tma_load_2d_pair(sa + 2 * A_BYTES, &maps.b[0], kb * BK, nb, fb);
+        tma_load_2d_pair(sa + 2 * A_BYTES + B_BYTES, &maps.b[1], kb * BK, nb, fb);
+        if (++s == STAGES) {
+          s = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+    if (*abort_flag && leader) {
+#pragma unroll
+      for (int j = 0; j < STAGES; ++j)
+        if (armed[j]) (void)mbar_wait(full_bar(j), armed_phase[j]);
+    }
+  } else if (warp == 1 && lane == 0 && leader) {
+    // ---------------- MMA issuer (leader) ----------------
+    constexpr uint32_t idesc = idesc_f16(2 * BM, BN, false);
+    int s = 0, j = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int t = cid; t < ntiles && ok; t += nclusters, ++j) {
+      // both epilogues have read tile j - 1 out of TMEM
+      if (j > 0 && !mbar_wait(acce, (uint32_t)((j - 1) & 1))) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      for (int kb = 0; kb < kblocks; ++kb) {
+        if (!mbar_wait(full_bar(s), phase)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = sbase + s * STAGE_BYTES;
+        const uint64_t x0 = smem_desc_sw128(sa);
+        const uint64_t x1 = smem_desc_sw128(sa + A_BYTES);
+        const uint64_t b0 = smem_desc_sw128(sa + 2 * A_BYTES);
+        const uint64_t b1 = smem_desc_sw128(sa + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k)
+          umma_f16_pair(tmem_d, x0 + 2 * k, b0 + 2 * k, idesc, (kb == 0 && k == 0) ? 0u : 1u);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k)
+          umma_f16_pair(tmem_d + BN, x1 + 2 * k, b0 + 2 * k, idesc,
+                        (kb == 0 && k == 0) ? 0u : 1u);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k)
+          umma_f16_pair(tmem_d + BN, x0 + 2 * k, b1 + 2 * k, idesc, 1u);
+        umma_commit_pair(empty_bar(s));
+        if (++s == STAGES) {
+          s = 0;
+          phase ^= 1u;
+        }
+      }
+      if (ok) umma_commit_pair(accf);
+    }
+    if (!ok) *abort_flag = 1;
+  } else if (warp >= 2) {
+    // ---------------- epilogue warps 2..5: TMEM lane quarter warp % 4 ----------------
+    const int quarter = warp & 3;
+    const uint32_t lane_base = tmem_d + ((uint32_t)(quarter * 32) << 16);
+    const uint32_t acce0 = cluster_addr(acce, 0);
+    const uint32_t my_q = qstage + (uint32_t)(warp - 2) * 2u * kStageQ;
+    const uint32_t sw = (uint32_t)(lane & 7);  // 128-byte swizzle of row `lane`
+    int j = 0, buf = 0;
+    for (int t = cid; t < ntiles; t += nclusters, ++j) {
+      const bool ready = !*abort_flag && mbar_wait(accf, (uint32_t)(j & 1));
+      tc_fence_after();
+      if (!ready) {
+        *abort_flag = 1;
+        break;
+      }
+      const int r0 = (t / ncol) * (2 * BM) + (int)rank * BM + quarter * 32;
+      const int n0 = (t % ncol) * BN;
+      const int row = r0 + lane;
+      const float rsc = args.row_scale ? args.row_scale[row < args.n_rows ? row : 0]
+                                       : args.row_const;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t v[32], w[32];
+        tmem_ld_32cols(lane_base + (uint32_t)c0, v);
+        tmem_ld_32cols(lane_base + (uint32_t)(BN + c0), w);
+        tmem_ld_wait();
+        if (c0 + 32 >= BN) {
+          // the accumulators of this tile are in registers: release TMEM
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cluster(acce0);
+        }
+        // the staging block written two chunks ago has been read by its TMA store
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncwarp();
+        const uint32_t dst = my_q + (uint32_t)buf * kStageQ + (uint32_t)lane * 128u;
+        const int col = n0 + c0;
+#pragma unroll
+        for (int q4 = 0; q4 < 8; ++q4) {
+          // 1 / s_i per column (zero past the last row of A), 1 / t_c per row:
+          // powers of two, so the scaling is exact
+          float4 cs;
+          const int cq = col + 4 * q4;
+          if (cq + 4 <= args.n_cols) {
+            cs = __ldg(reinterpret_cast<const float4*>(args.col_scale + col) + q4);
+          } else {
+            cs.x = cq < args.n_cols ? args.col_scale[cq] : 0.f;
+            cs.y = cq + 1 < args.n_cols ? args.col_scale[cq + 1] : 0.f;
+            cs.z = cq + 2 < args.n_cols ? args.col_scale[cq + 2] : 0.f;
+            cs.w = cq + 3 < args.n_cols ? args.col_scale[cq + 3] : 0.f;
+          }
+          const float o0 = (__uint_as_float(v[4 * q4]) + __uint_as_float(w[4 * q4])) * cs.x * rsc;
+          const float o1 =
+              (__uint_as_float(v[4 * q4 + 1]) + __uint_as_float(w[4 * q4 + 1])) * cs.y * rsc;
+          const float o2 =
+              (__uint_as_float(v[4 * q4 + 2]) + __uint_as_float(w[4 * q4 + 2])) * cs.z * rsc;
+          const float o3 =
+              (__uint_as_float(v[4 * q4 + 3]) + __uint_as_float(w[4 * q4 + 3])) * cs.w * rsc;
+          const uint32_t a = dst + (((uint32_t)q4 ^ sw) << 4);
+          asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(o0), "f"(o1),
+                       "f"(o2), "f"(o3)
+                       : "memory");
+        }
+        // make the generic-proxy writes visible to the TMA engine, then store
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          tma_store_2d(&maps.q, col, r0, my_q + (uint32_t)buf * kStageQ);
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+        buf ^= 1;
+      }
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    __syncwarp();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag) {
+    if (threadIdx.x == 0) atomicOr(args.status, kStatusTimeout);
+    for (int i = 0; i < 1000; ++i) __nanosleep(1000);
+  }
+  cluster_sync_all();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_d),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
+
 // Fixed-point slices of the chain states for the exact refresh: per row c,
 // t_c = 2^e with max_j |x_cj| < t_c, and x_cj / t_c = sum_l e_l 2^(-w l) + r,
 // e_l integers in (-2^w, 2^w) stored exactly as bf16.  One warp per row.
@@ -955,6 +1209,23 @@ cudaError_t make_map(CUtensorMap* map, const void* base, int rows, int cols, int
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// 2-D tensor map of a float matrix (rows x cols, row stride ld elements) for
+// TMA stores of 32 x 32 blocks with the 128-byte swizzle.
+cudaError_t make_map_q(CUtensorMap* map, void* base, int rows, int cols, int ld) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld * 4) % 16 != 0)
+    return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 constexpr int kSmemLimit = 227 * 1024;
 
 template <int BN, int MODE = kModeSum>
@@ -1011,6 +1282,68 @@ cudaError_t launch_pair_bn(const TcMaps& maps, const TcArgs& args, cudaStream_t 
   dim3 grid(2 * ((args.n_cols + BN - 1) / BN), (args.n_rows + 2 * BM - 1) / (2 * BM));
   k<<<grid, kThreads, smem, s>>>(maps, args);
   return cudaGetLastError();
+}
+
+int num_sms();
+
+// Persistent SM-pair form: one cluster of two CTAs per co-resident slot.
+constexpr int kPersistCode = 3000;
+
+template <int BN>
+constexpr int persist_stages() {
+  constexpr int s = (kSmemLimit - 1024 - 256 - 8 * (int)kStageQ) / (int)pair_stage_bytes<BN>();
+  return s > 6 ? 6 : s;
+}
+
+template <int BN>
+constexpr size_t persist_smem_bytes() {
+  return (size_t)persist_stages<BN>() * pair_stage_bytes<BN>() + 8 * kStageQ + 1024 + 256;
+}
+
+template <int BN>
+cudaError_t launch_persist_bn(const TcMaps& maps, const TcArgs& args, cudaStream_t s) {
+  constexpr int ST = persist_stages<BN>();
+  static_assert(persist_smem_bytes<BN>() <= (size_t)kSmemLimit, "persistent pair shared memory");
+  auto k = tc_gemm_pair_persistent_kernel<BN, ST>;
+  const size_t smem = persist_smem_bytes<BN>();
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int ntiles = ((args.n_cols + BN - 1) / BN) * ((args.n_rows + 2 * BM - 1) / (2 * BM));
+  // co-resident clusters of this configuration (cached per width)
+  static int max_clusters = 0;
+  if (max_clusters == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess || n < 1) {
+      (void)cudaGetLastError();
+      n = std::max(1, num_sms() / 2);
+    }
+    max_clusters = n;
+  }
+  const int nclusters = std::max(1, std::min(ntiles, max_clusters));
+  k<<<dim3(2 * nclusters), kThreads, smem, s>>>(maps, args);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_persist(int bn, const TcMaps& maps, const TcArgs& args, cudaStream_t s) {
+  switch (bn) {
+    case 128: return launch_persist_bn<128>(maps, args, s);
+    case 160: return launch_persist_bn<160>(maps, args, s);
+    case 192: return launch_persist_bn<192>(maps, args, s);
+    case 224: return launch_persist_bn<224>(maps, args, s);
+    case 256: return launch_persist_bn<256>(maps, args, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_pair(int bn, const TcMaps& maps, const TcArgs& args, cudaStream_t s) {
@@ -1070,11 +1403,13 @@ struct TcGemmPlan {
 
 void tc_gemm_tile_for(int n_chains, int m, int* bn, int* stages) {
   // One-SM tiles (128 chains x BN rows of A, code BN) or SM-pair tiles (256
-  // chains x BN, code kPairCode + BN).  With at least 256 chains the pair form
-  // is taken: per product it reads ~40 % fewer bytes from L2 and from shared
-  // memory.  Within a form, pick the width that minimises (waves of tiles) x
-  // (tile width): the per-tile time grows with BN, and the last wave is padded
-  // to the number of tile slots (SMs, or SM pairs).
+  // chains x BN), run by the persistent kernel (code kPersistCode + BN; the
+  // one-launch-per-tile pair kernel is code kPairCode + BN).  With at least
+  // 256 chains the persistent pair form is taken: per product it reads ~40 %
+  // fewer bytes from L2 and from shared memory, and its epilogue overlaps the
+  // next tile.  Within a form, pick the width that minimises (tiles per slot)
+  // x (tile width): the per-tile time grows with BN, and the last round is
+  // padded to the number of tile slots (SMs, or SM pairs).
   // (ESS_Q_BN fixes the code at build time, for tuning sweeps.)
   const int sms = num_sms();
   if (stages) *stages = 0;
@@ -1098,7 +1433,7 @@ void tc_gemm_tile_for(int n_chains, int m, int* bn, int* stages) {
       best = w;
     }
   }
-  *bn = pair ? kPairCode + best : best;
+  *bn = pair ? kPersistCode + best : best;
 }
 
 int tc_refresh_slices(int d, int* w_out) {
@@ -1218,13 +1553,15 @@ void tc_gemm_destroy(TcGemmPlan* plan) {
   delete plan;
 }
 
-const int kTcWidths[11] = {64, 128, 160, 192, 224, 256,
+const int kTcWidths[16] = {64, 128, 160, 192, 224, 256,
                            kPairCode + 128, kPairCode + 160, kPairCode + 192, kPairCode + 224,
-                           kPairCode + 256};
+                           kPairCode + 256,
+                           kPersistCode + 128, kPersistCode + 160, kPersistCode + 192,
+                           kPersistCode + 224, kPersistCode + 256};
 
 cudaError_t tc_gemm_set_width(TcGemmPlan* plan, int bn) {
   if (!plan) return cudaErrorInvalidValue;
-  if (bn != 0 && std::find(kTcWidths, kTcWidths + 11, bn) == kTcWidths + 11)
+  if (bn != 0 && std::find(kTcWidths, kTcWidths + 16, bn) == kTcWidths + 16)
     return cudaErrorInvalidValue;
   plan->bn_fixed = bn;
   return cudaSuccess;
@@ -1255,8 +1592,9 @@ cudaError_t tc_gemm_q(TcGemmPlan* plan, __half* const nu[2], const float* nu_uns
   if (n_chains == 0) return cudaSuccess;
   if (ld16 != plan->ld16) return cudaErrorInvalidValue;
   const int code = tc_gemm_width(plan, n_chains);
+  const bool persist = code > kPersistCode;
   const bool pair = code > kPairCode;
-  const int bn = pair ? code - kPairCode : code;
+  const int bn = persist ? code - kPersistCode : pair ? code - kPairCode : code;
   const int* widths = pair ? kPairWidths : kWidths;
   const int nw = pair ? 5 : 6;
   int wi = 0;
@@ -1269,6 +1607,10 @@ cudaError_t tc_gemm_q(TcGemmPlan* plan, __half* const nu[2], const float* nu_uns
     if (e != cudaSuccess) return e;
     maps.b[k] = pair ? plan->pmaps[wi][k] : plan->qmaps[wi][k];
   }
+  // the persistent form stores Q by TMA: rows of 16-byte multiples
+  bool use_persist = persist && (ldq & 3) == 0 && (reinterpret_cast<uintptr_t>(Q) & 15) == 0;
+  if (use_persist && make_map_q(&maps.q, Q, n_chains, plan->m, ldq) != cudaSuccess)
+    use_persist = false;
   TcArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n_rows = n_chains;
@@ -1282,7 +1624,9 @@ cudaError_t tc_gemm_q(TcGemmPlan* plan, __half* const nu[2], const float* nu_uns
   a.row_const = 1.f / kNuSplitScale;
   a.col_scale = plan->q_col_scale;
   a.status = status;
-  return pair ? launch_pair(bn, maps, a, s) : launch_sum(bn, maps, a, s);
+  return use_persist ? launch_persist(bn, maps, a, s)
+         : pair      ? launch_pair(bn, maps, a, s)
+                     : launch_sum(bn, maps, a, s);
 }
 
 cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,

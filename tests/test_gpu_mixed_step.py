@@ -62,15 +62,19 @@ def test_products_tensor_core_gemm(n, m, d):
     assert np.all(np.abs(P - p_ref) <= tol), float(np.max(np.abs(P - p_ref) / tol))
 
 
-Q_TILES = [64, 128, 160, 192, 224, 256, 2128, 2160, 2192, 2224, 2256]
+Q_TILES = [64, 128, 160, 192, 224, 256, 2128, 2160, 2192, 2224, 2256,
+           3128, 3160, 3192, 3224, 3256]
 
 
 @pytest.mark.parametrize("q_tile", Q_TILES)
-@pytest.mark.parametrize("n,m,d", [(513, 1000, 333), (256, 448, 64), (40, 300, 1000)])
+@pytest.mark.parametrize("n,m,d", [(513, 1000, 333), (256, 448, 64), (40, 300, 1000),
+                                   (1300, 1001, 77)])
 def test_q_gemm_every_tile(q_tile, n, m, d):
-    """Every tile form of the q GEMM (one SM per 128-chain tile, or an SM pair
-    per 256-chain tile with tcgen05 cta_group::2) within the FP16x3 bound, on
-    ragged chain counts (a cluster row with one live chain), ragged m and K."""
+    """Every tile form of the q GEMM (one SM per 128-chain tile; an SM pair per
+    256-chain tile with tcgen05 cta_group::2, one launch per tile or the
+    persistent kernel with TMA-stored Q) within the FP16x3 bound, on ragged
+    chain counts (a cluster row with one live chain), ragged m and K; m = 1001
+    (rows of Q not a multiple of 16 bytes) takes the per-tile launch."""
     rng = np.random.default_rng(n + m + q_tile)
     A = rng.standard_normal((m, d)) / math.sqrt(d)
     NU = f32(rng.standard_normal((n, d)))
@@ -90,7 +94,7 @@ def test_q_gemm_every_tile(q_tile, n, m, d):
 
 
 def test_q_tile_rejects_unknown_codes():
-    for bad in (1, 96, 2064, 2000, 3000, -1):
+    for bad in (1, 96, 2064, 2000, 3000, 3064, 4224, -1):
         with pytest.raises(ess.EssError):
             ess.Sampler(np.eye(3), np.ones(3), precision=ess.ESS_PREC_MIXED, q_tile=bad)
 

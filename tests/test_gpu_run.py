@@ -115,7 +115,8 @@ def test_autotune_keeps_the_chains(form):
     finally:
         s.close()
     if form == ess.ESS_PREC_MIXED:
-        assert width in (64, 128, 160, 192, 224, 256, 2128, 2160, 2192, 2224, 2256)
+        assert width in (64, 128, 160, 192, 224, 256, 2128, 2160, 2192, 2224, 2256,
+                         3128, 3160, 3192, 3224, 3256)
     else:
         assert width == 0
     assert sort_threads in (0, 32, 64, 128)
