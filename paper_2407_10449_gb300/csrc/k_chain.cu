@@ -7,10 +7,17 @@
 //      (tau - h, tau + h) with tau shifted into [0, 2 pi)); rows with
 //      b/r >= 1 or r = 0 are dropped instead of padded (Sec. 3.2: such a
 //      constraint "can be simply ignored").
-//   2. Alg. 3: sort the left endpoints alpha with beta as payload (register
-//      bitonic network per thread, then merge-path merges in shared memory),
-//      cumulative max gamma_k of beta (warp-shuffle scan), and the pieces
-//      [0, alpha_(1)], [gamma_(k-1), alpha_(k)], [gamma_(n), 2 pi] of Prop. 1.
+//   2. Alg. 3 on the kept arcs, sorted by alpha.  The arcs are first merged
+//      per bucket of alpha (up to 2048 buckets of width w, 512 for double): an arc in bucket j = [j w, (j + 1) w] that reaches (j + 1) w
+//      contains that point, so all such arcs of one bucket overlap and their
+//      union is the single interval [min alpha, max beta]; the bucket
+//      intervals are already in ascending order of alpha, and Alg. 3 on them
+//      gives the same union of arcs (hence I_act) as on the arcs themselves,
+//      without a sort.  If any kept arc is shorter than its bucket, the arcs
+//      are sorted instead (register bitonic network per thread, then
+//      merge-path merges in shared memory).  Then the cumulative max gamma_k
+//      of beta (warp-shuffle scan), and the pieces [0, alpha_(1)],
+//      [gamma_(k-1), alpha_(k)], [gamma_(n), 2 pi] of Prop. 1.
 //   3. theta ~ U(I_act) by the inverse CDF over the piece lengths (prefix sum).
 //   4. x' = x cos(theta) + nu sin(theta) (Alg. 1), p' = p cos(theta) +
 //      q sin(theta) (A x carried forward), and the Sec. 3.3 safeguard: rows
@@ -24,6 +31,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 #include "chain_math.cuh"
 #include "ess_kernels.cuh"
@@ -80,29 +88,46 @@ __device__ V block_exclusive_scan(V v, V identity, Op op, V* tmp, V& total) {
 __device__ __forceinline__ int pad_idx(int e) { return e + (e >> 5); }
 
 constexpr int kBuckets = 64;  // alpha buckets of the domination prune
+// Alpha buckets of the interval merge (at most): 2048 for float chains; 512
+// for double chains, whose larger arrays would otherwise cost the CTA kernel
+// half its residency at m = 2000.
+template <typename T>
+constexpr int merge_buckets() { return sizeof(T) == 8 ? 512 : 2048; }
 
 template <typename T, int NT, int ITEMS, bool BATCH>
 __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_kernel(ChainParams<T> prm) {
   constexpr int NSLOT = NT * ITEMS;
   constexpr int NPAD = NSLOT + NSLOT / 32;
   constexpr int NW = NT / 32;
+  constexpr int NB = NSLOT < merge_buckets<T>() ? NSLOT : merge_buckets<T>();  // merge buckets
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s_key = reinterpret_cast<T*>(smem_raw);
   T* s_val = s_key + NPAD;
   T* s_x = s_val + NPAD;
   int* s_flag = reinterpret_cast<int*>(s_x + ((prm.d + 1) & ~1));
+  // per alpha bucket: min alpha and max beta as ordered bit patterns
+  // (non-negative floating-point values compare like their bits)
+  using Bits = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned>::type;
+  Bits* s_bmin = reinterpret_cast<Bits*>(s_flag + NSLOT);
+  Bits* s_bmaxb = s_bmin + NB;
 
   __shared__ int s_itmp[NW];
   __shared__ T s_ttmp[NW];
   __shared__ unsigned int s_bmax[kBuckets];  // max approximate beta (bits) per alpha bucket
   __shared__ float s_gearly[kBuckets];       // max approximate beta over buckets <= j - 2
-  __shared__ int s_nflag, s_reject, s_best, s_bad, s_tangent, s_noroot;
+  __shared__ int s_nflag, s_reject, s_best, s_bad, s_tangent, s_noroot, s_slow;
   __shared__ T s_theta;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const T two_pi = Lim<T>::two_pi();
   const T inf = Lim<T>::inf();
+  // the bucket arrays exist only if the launch provided their shared memory
+  uint32_t dyn_smem;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
+  const bool can_merge =
+      (size_t)dyn_smem >= 2 * NPAD * sizeof(T) + (size_t)((prm.d + 1) & ~1) * sizeof(T) +
+                              NSLOT * sizeof(int) + 2 * NB * sizeof(T);
 
   // one chain per CTA, or (list mode) the chains of prm.chain_list, strided
   // over the grid
@@ -119,8 +144,13 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
     s_bad = 0;
     s_tangent = 0;
     s_noroot = 0;
+    s_slow = can_merge ? 0 : 1;
   }
   for (int k = tid; k < kBuckets; k += NT) s_bmax[k] = 0;
+  for (int k = tid; k < NB && can_merge; k += NT) {
+    s_bmin[k] = sizeof(T) == 8 ? (Bits)0x7FF0000000000000ull : (Bits)0x7F800000u;  // +inf
+    s_bmaxb[k] = 0;
+  }
   __syncthreads();
 
   // ---- 1. p, q of every row (kept in registers) and approximate arcs --------
@@ -203,8 +233,11 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
   }
   __syncthreads();
 
-  // ---- exact roots of the kept rows (App. B, Sec. 3.2) ------------------------
+  // ---- exact roots of the kept rows (App. B, Sec. 3.2), merged per bucket ----
   int tangent = 0, no_root = 0;
+  const T bucket_w = two_pi / (T)NB;
+  const T to_slot = (T)NB / two_pi;
+  bool slow = false;
   for (int k = tid; k < n_keep; k += NT) {
     const int i = s_flag[k];
     T al, be;
@@ -215,7 +248,31 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
     s_key[pad_idx(k)] = has ? al : inf;
     s_val[pad_idx(k)] = has ? be : T(0);
     no_root += has ? 0 : 1;
+    if (has && can_merge) {
+      // bucket j = [lo_j, hi_j], lo_j = j w, hi_j = (j + 1) w (2 pi for the
+      // last); the same expressions for every arc, so hi_j == lo_(j+1)
+      int j = min(max((int)(al * to_slot), 0), NB - 1);
+      auto lo_of = [&](int b) { return (T)b * bucket_w; };
+      auto hi_of = [&](int b) { return b + 1 == NB ? two_pi : (T)(b + 1) * bucket_w; };
+      if (j > 0 && al < lo_of(j)) --j;
+      else if (j + 1 < NB && al > hi_of(j)) ++j;
+      if (al >= lo_of(j) && al <= hi_of(j) && be >= hi_of(j)) {
+        Bits ab, bb;
+        if constexpr (sizeof(T) == 8) {
+          ab = (Bits)__double_as_longlong((double)al) & 0x7FFFFFFFFFFFFFFFull;  // +0 for -0
+          bb = (Bits)__double_as_longlong((double)be) & 0x7FFFFFFFFFFFFFFFull;
+        } else {
+          ab = (Bits)__float_as_uint((float)al) & 0x7FFFFFFFu;
+          bb = (Bits)__float_as_uint((float)be) & 0x7FFFFFFFu;
+        }
+        atomicMin(&s_bmin[j], ab);
+        atomicMax(&s_bmaxb[j], bb);
+      } else {
+        slow = true;  // shorter than its bucket: this chain's arcs are sorted
+      }
+    }
   }
+  if (slow) s_slow = 1;
   if (tangent) atomicAdd(&s_tangent, tangent);
   if (no_root) atomicAdd(&s_noroot, no_root);
   const int n_active_slots = ((n_keep + ITEMS - 1) / ITEMS) * ITEMS;
@@ -224,14 +281,50 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
     s_val[pad_idx(k)] = T(0);
   }
   __syncthreads();
-  const int n_roots = n_keep - s_noroot;  // rows without roots sort to the end (+inf)
-
-  // ---- 2. Alg. 3: sort alpha ascending, beta as payload -----------------
+  int n_roots = n_keep - s_noroot;  // rows without roots sort to the end (+inf)
+  const int base = tid * ITEMS;
+  T key[ITEMS], val[ITEMS];
+  if (!s_slow) {
+    // ---- 2a. bucket intervals in ascending order of alpha -------------------
+    int my_n = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      key[i] = inf;
+      val[i] = T(0);
+      if (base + i < NB) {
+        const Bits ab = s_bmin[base + i];
+        key[i] = sizeof(T) == 8 ? (T)__longlong_as_double((long long)ab)
+                                : (T)__uint_as_float((unsigned)ab);
+        const Bits bb = s_bmaxb[base + i];
+        val[i] = sizeof(T) == 8 ? (T)__longlong_as_double((long long)bb)
+                                : (T)__uint_as_float((unsigned)bb);
+      }
+      my_n += key[i] < inf ? 1 : 0;
+    }
+    int n_int;
+    int at = block_exclusive_scan<NT>(my_n, 0, OpAdd(), s_itmp, n_int);
+    // compact the non-empty buckets to the front, in bucket order
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      if (key[i] < inf) {
+        s_key[pad_idx(at)] = key[i];
+        s_val[pad_idx(at)] = val[i];
+        ++at;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const bool in = base + i < n_int;
+      key[i] = in ? s_key[pad_idx(base + i)] : inf;
+      val[i] = in ? s_val[pad_idx(base + i)] : T(0);
+    }
+    n_roots = n_int;
+  } else {
+  // ---- 2b. Alg. 3: sort alpha ascending, beta as payload -----------------
   // Only the first n_active_slots positions hold arcs; the rest is padding
   // (+inf keys) that the sort never needs to touch.
-  const int base = tid * ITEMS;
   const bool owns = base < n_active_slots;
-  T key[ITEMS], val[ITEMS];
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     key[i] = owns ? s_key[pad_idx(base + i)] : inf;
@@ -295,6 +388,7 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
       }
     }
   }
+  }  // sorted arcs
 
   // ---- 3. Alg. 3: gamma_k = cumulative max of beta ----------------------
   T g[ITEMS];
@@ -511,12 +605,18 @@ template <typename T>
 size_t chain_smem_bytes(int threads, int d) {
   const size_t nslot = (size_t)threads * kChainItems;
   const size_t npad = nslot + nslot / 32;
+  // keys, values, x', flags (the launch adds the merge buckets when they fit)
   return 2 * npad * sizeof(T) + (size_t)((d + 1) & ~1) * sizeof(T) + nslot * sizeof(int);
 }
 
 template <typename T>
 cudaError_t launch_chain_step(const ChainParams<T>& p, int threads, cudaStream_t s) {
-  const size_t smem = chain_smem_bytes<T>(threads, p.d);
+  // the per-bucket interval merge needs two more arrays of min(threads *
+  // kChainItems, merge_buckets<T>()) values; without them the kernel sorts
+  size_t smem = chain_smem_bytes<T>(threads, p.d);
+  const size_t merge =
+      2 * std::min((size_t)threads * kChainItems, (size_t)merge_buckets<T>()) * sizeof(T);
+  if (smem + merge <= (size_t)227 * 1024) smem += merge;
   int sms = 1, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -203,3 +203,34 @@ def test_both_step_kernels(sort_threads):
     X2 = np.tile(z, (32, 1))
     check_fp64(A2, b2, X2, rng.standard_normal((32, 200)), rng.uniform(size=32),
                sort_threads=sort_threads)
+
+
+@pytest.mark.parametrize("sort_threads", [0, 256])
+def test_cta_kernel_short_arcs(sort_threads):
+    """Arcs shorter than a bucket of the CTA kernel's interval merge (half-width
+    1e-3 rad against buckets of 2 pi / 512 in FP64) make it sort the arcs instead; the
+    step still equals the oracle's.  The other chains' arcs are merged per
+    bucket (long arcs only)."""
+    rng = np.random.default_rng(33)
+    d, m_long, m_short, n = 12, 300, 24, 8
+    x = rng.standard_normal(d) * 0.2
+    nu = rng.standard_normal(d)
+    A_long = rng.standard_normal((m_long, d))
+    b_long = A_long @ x + rng.uniform(0.2, 1.0, size=m_long)
+    A_short, b_short = [], []
+    while len(A_short) < m_short:
+        a = rng.standard_normal(d)
+        p, q = a @ x, a @ nu
+        r = math.hypot(p, q)
+        bb = r * math.cos(1e-3)
+        if p < bb - 1e-9 * r:  # x strictly feasible: the short arc avoids 0
+            A_short.append(a)
+            b_short.append(bb)
+    A = np.vstack([A_long, np.array(A_short)])
+    b = np.concatenate([b_long, np.array(b_short)])
+    X = np.tile(x, (n, 1))
+    NU = np.tile(nu, (n, 1))
+    U = np.linspace(0.05, 0.95, n)
+    check_fp64(A, b, X, NU, U, sort_threads=sort_threads)
+    # the long-arc rows alone take the bucket merge in the CTA kernel
+    check_fp64(A_long, b_long, X, NU, U, sort_threads=sort_threads)
