@@ -182,7 +182,11 @@ ess_status ess_chains_step(ess_state *state, int n_iter, uint64_t seed, void *sa
 ess_status ess_chains_get(ess_state *state, double *X, void *cuda_stream);
 
 /* Same as ess_run with X and samples in HOST memory: copies X to the device,
- * runs, and copies the final states (and samples) back. */
+ * runs, and copies the final states (and samples) back.  Each record is copied
+ * to the host (from one of two device slots, on a stream of its own) while the
+ * next record_every steps run; with pinned host buffers the copies overlap the
+ * steps.  The device buffers are kept in the state for the next call.  Returns
+ * after every copy has finished. */
 ess_status ess_run_host(ess_state *state, double *X_host, int n_chains, int t0, int n_iter,
                         uint64_t seed, void *samples_host, int record_every,
                         void *cuda_stream);

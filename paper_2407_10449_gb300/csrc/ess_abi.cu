@@ -117,6 +117,13 @@ struct ess_state {
   int ev_used = 0;
   double phase_ms[ESS_N_PHASES] = {0};
   long long phase_launches[ESS_N_PHASES] = {0};
+  // ess_run_host: device copy of X, two sample slots whose copies to the host
+  // overlap the next steps (on their own stream), kept across calls
+  int host_cap = 0;
+  double* host_x = nullptr;
+  void* host_slot[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t slot_ready[2] = {nullptr, nullptr}, slot_free[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -698,6 +705,13 @@ void ess_destroy(ess_state* s) {
   dev_free(s->t_dev);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  dev_free(s->host_x);
+  for (int k = 0; k < 2; ++k) {
+    if (s->host_slot[k]) cudaFree(s->host_slot[k]);
+    if (s->slot_ready[k]) cudaEventDestroy(s->slot_ready[k]);
+    if (s->slot_free[k]) cudaEventDestroy(s->slot_free[k]);
+  }
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   delete s;
 }
 
@@ -885,32 +899,62 @@ ess_status ess_run_host(ess_state* s, double* X_host, int n_chains, int t0, int 
   if (record_every > 0 && !samples_host) return fail(ESS_ERR_ARG, "samples is NULL");
   DeviceGuard g(s->device);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  const size_t xbytes = sizeof(double) * (size_t)n_chains * s->d;
+  const int d = s->d;
+  const size_t xbytes = sizeof(double) * (size_t)n_chains * d;
   const int n_rec = record_every > 0 ? n_iter / record_every : 0;
-  const size_t sbytes = elem(s) * (size_t)n_chains * n_rec * s->d;
-  double* Xd = nullptr;
-  void* Sd = nullptr;
-  ESS_CUDA(cudaMalloc(&Xd, xbytes));
-  if (sbytes) {
-    cudaError_t e = cudaMalloc(&Sd, sbytes);
-    if (e != cudaSuccess) {
-      cudaFree(Xd);
-      return cuda_fail(e, "samples buffer");
-    }
+  const size_t row = elem(s) * (size_t)d;         // one chain's state
+  const size_t slot_bytes = row * (size_t)n_chains;  // one record of every chain
+  // device buffers and the copy stream, kept across calls (grow only)
+  if (n_chains > s->host_cap) {
+    dev_free(s->host_x);
+    for (auto& p : s->host_slot)
+      if (p) {
+        cudaFree(p);
+        p = nullptr;
+      }
+    s->host_cap = 0;
+    ESS_CUDA(dev_alloc(&s->host_x, (size_t)n_chains * d));
+    for (auto& p : s->host_slot) ESS_CUDA(cudaMalloc(&p, slot_bytes));
+    s->host_cap = n_chains;
   }
-  ess_status rc = ESS_OK;
-  cudaError_t e = cudaMemcpyAsync(Xd, X_host, xbytes, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) rc = cuda_fail(e, "copy X to device");
-  if (rc == ESS_OK) rc = ess_run(s, Xd, n_chains, t0, n_iter, seed, Sd, record_every, cuda_stream);
+  if (!s->copy_stream) ESS_CUDA(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
+  for (int k = 0; k < 2; ++k) {
+    if (!s->slot_ready[k])
+      ESS_CUDA(cudaEventCreateWithFlags(&s->slot_ready[k], cudaEventDisableTiming));
+    if (!s->slot_free[k])
+      ESS_CUDA(cudaEventCreateWithFlags(&s->slot_free[k], cudaEventDisableTiming));
+  }
+  ESS_CUDA(cudaMemcpyAsync(s->host_x, X_host, xbytes, cudaMemcpyHostToDevice, st));
+  ess_status rc = ess_chains_init(s, s->host_x, n_chains, t0, cuda_stream);
+  // record r: record_every steps, then a device copy of the states into slot
+  // r % 2 and its copy to the host (chain-major rows of n_rec records) on the
+  // copy stream while the next steps run; a slot is refilled only after its
+  // previous copy to the host has finished
+  for (int r = 0; r < n_rec && rc == ESS_OK; ++r) {
+    rc = ess_chains_step(s, record_every, seed, nullptr, 0, cuda_stream);
+    if (rc != ESS_OK) break;
+    const int k = r & 1;
+    if (r >= 2) ESS_CUDA(cudaStreamWaitEvent(st, s->slot_free[k], 0));
+    ESS_CUDA(cudaMemcpyAsync(s->host_slot[k], chain_states(s), slot_bytes,
+                             cudaMemcpyDeviceToDevice, st));
+    ESS_CUDA(cudaEventRecord(s->slot_ready[k], st));
+    ESS_CUDA(cudaStreamWaitEvent(s->copy_stream, s->slot_ready[k], 0));
+    ESS_CUDA(cudaMemcpy2DAsync(static_cast<char*>(samples_host) + (size_t)r * row,
+                               row * (size_t)n_rec, s->host_slot[k], row, row, (size_t)n_chains,
+                               cudaMemcpyDeviceToHost, s->copy_stream));
+    ESS_CUDA(cudaEventRecord(s->slot_free[k], s->copy_stream));
+  }
+  const int rest = n_iter - n_rec * record_every;
+  if (rc == ESS_OK && rest > 0) rc = ess_chains_step(s, rest, seed, nullptr, 0, cuda_stream);
+  if (rc == ESS_OK) rc = ess_chains_get(s, s->host_x, cuda_stream);
   if (rc == ESS_OK || rc == ESS_ERR_NUMERIC) {
-    e = cudaMemcpyAsync(X_host, Xd, xbytes, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && sbytes)
-      e = cudaMemcpyAsync(samples_host, Sd, sbytes, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(X_host, s->host_x, xbytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess && rc == ESS_OK) rc = cuda_fail(e, "copy results to host");
   }
-  cudaFree(Xd);
-  if (Sd) cudaFree(Sd);
+  // the sample copies have finished before the call returns
+  const cudaError_t e = cudaStreamSynchronize(s->copy_stream);
+  if (e != cudaSuccess && rc == ESS_OK) rc = cuda_fail(e, "copy samples to host");
   return rc;
 }
 

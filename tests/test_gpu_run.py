@@ -223,3 +223,32 @@ def test_run_host_matches_device_run():
         np.testing.assert_array_equal(host(Xd), Xh)
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("n_iter,record_every", [(70, 10), (40, 7), (33, 40), (64, 32)])
+def test_run_host_records_like_device_run(form, n_iter, record_every):
+    """ess_run_host (host buffers; each record copied to the host from a device
+    slot while the next steps run) gives the same final states and the same
+    recorded samples, bit for bit, as ess_run on device buffers (samples
+    written by the step kernel), for record intervals that do and do not
+    divide refresh_k = 32."""
+    import torch
+    inst = workloads.medium(n_chains=300)
+    n, d = 300, inst.d
+    n_rec = n_iter // record_every
+    dt = torch.float64 if form == ess.ESS_PREC_FP64 else torch.float32
+    s = ess.Sampler(inst.A, inst.b, precision=form)
+    try:
+        Xd = dev(inst.X0)
+        Sd = torch.zeros((n, max(n_rec, 1), d), dtype=dt, device="cuda")
+        ess.ess_run(s.state, Xd, n, 3, n_iter, 9, Sd if n_rec else None, record_every if n_rec else 0)
+        Xh = np.array(inst.X0, dtype=np.float64, order="C")
+        Sh = torch.zeros((n, max(n_rec, 1), d), dtype=dt).pin_memory()
+        ess.ess_run_host(s.state, Xh, n, 3, n_iter, 9, Sh.numpy() if n_rec else None,
+                         record_every if n_rec else 0)
+    finally:
+        s.close()
+    np.testing.assert_array_equal(host(Xd), Xh)
+    if n_rec:
+        np.testing.assert_array_equal(host(Sd), Sh.numpy())
