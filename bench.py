@@ -322,7 +322,14 @@ def batch_phase_rooflines(insts, timing, precision, torch, peaks):
     work = {
         "draw": ("hbm", "GB/s", float(sum(i.d * i.n_chains for i in insts) * esz),
                  peaks["hbm_gbs"]),
-        "gemm": ("fp32" if mixed else "fp64", "TFLOP/s", 2.0 * mdC, fp),
+        # mixed: the tcgen05 grouped GEMM streams each problem's fp16 A splits
+        # once (4 B per element of A), its chains' nu splits once per 128-row
+        # tile and writes Q: HBM-bound (arithmetic intensity ~1.5 N flops per
+        # byte of A for N chains); FP64 form: DFMAs
+        "gemm": (("hbm", "GB/s",
+                  float(sum(4 * i.m * i.d + 4 * i.n_chains * i.d * (-(-i.m // 128))
+                            + 4 * i.n_chains * i.m for i in insts)),
+                  peaks["hbm_gbs"]) if mixed else ("fp64", "TFLOP/s", 2.0 * mdC, fp)),
         "chain": ("hbm", "GB/s", float(sum(i.n_chains * esz * (3 * i.m + 3 * i.d) for i in insts)),
                   peaks["hbm_gbs"]),
         # double-float refresh: ~11 FP32 operations per multiply-add

@@ -19,6 +19,7 @@
 
 #include "ess.h"
 #include "ess_kernels.cuh"
+#include "ess_gemm_tc.cuh"
 
 void ess_internal_set_error(const std::string& msg);  // ess_abi.cu
 
@@ -100,8 +101,9 @@ struct ess_batch {
   ChainDesc* desc = nullptr;
   BatchItem* items = nullptr;
   int n_items = 0;
-  BatchItem* mitems = nullptr;   // mixed form: items of the tensor-core q GEMM
-  int n_mitems = 0;
+  ess::TcBatchItem* titems = nullptr;  // mixed form: items of the tensor-core q GEMM
+  int n_titems = 0, cap_titems = 0;
+  CUtensorMap* tmaps = nullptr;  // mixed form: 4 operand maps per problem (A and nu splits)
   int layout_version = 0;
   // work buffers (device)
   int cap_n = 0, cap_items = 0;
@@ -192,7 +194,10 @@ void free_work(ess_batch* s) {
   drop_graphs(s);
   bfree(s->desc);
   bfree(s->items);
-  bfree(s->mitems);
+  bfree(s->titems);
+  s->cap_titems = 0;
+  if (s->tmaps) cudaFree(s->tmaps);
+  s->tmaps = nullptr;
   if (s->X) cudaFree(s->X);
   if (s->NU) cudaFree(s->NU);
   if (s->P) cudaFree(s->P);
@@ -219,7 +224,10 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
     if (nc[p] < 0) return bfail(ESS_ERR_ARG, "negative chain count");
   if (nc == s->nc && s->desc) return ESS_OK;
   std::vector<ChainDesc> desc;
-  std::vector<BatchItem> items, mitems;
+  std::vector<BatchItem> items;
+  std::vector<ess::TcBatchItem> titems;
+  std::vector<long long> ho_of(s->np, 0);  // per problem: offset of its rows in the nu splits
+  std::vector<int> ntile_of(s->np, 16);    // per problem: chain tile of the q GEMM
   long long xo = 0, po = 0, ho = 0;
   for (int p = 0; p < s->np; ++p) {
     const int d = s->d[p], m = s->m[p], dp = s->dpad[p];
@@ -261,25 +269,27 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
         it.c_first = c_first + c0;
         items.push_back(it);
       }
-    if (bmixed(s)) {
-      const int mrt = ess::batch_mma_rtile(ct);
-      for (int c0 = 0; c0 < nc[p]; c0 += ct)
-        for (int r0 = 0; r0 < m; r0 += mrt) {
-          BatchItem it{};
+    if (bmixed(s) && nc[p] > 0) {
+      // tensor-core items: 128 rows of A_p x up to 64 of its chains (N = the
+      // problem's chain count rounded up to 16, at most 64)
+      const int nt = std::min(64, (nc[p] + 15) / 16 * 16);
+      ho_of[p] = ho;
+      ntile_of[p] = nt;
+      for (int c0 = 0; c0 < nc[p]; c0 += 64)
+        for (int r0 = 0; r0 < m; r0 += 128) {
+          ess::TcBatchItem it{};
+          it.problem = p;
           it.row0 = r0;
-          it.rows = std::min(mrt, m - r0);
-          it.chains = std::min(ct, nc[p] - c0);
-          it.rtile = mrt;
-          it.ctile = ct;
-          it.d = d;
+          it.rows = std::min(128, m - r0);
+          it.chain0 = c0;
+          it.chains = std::min(64, nc[p] - c0);
+          it.ntile = nt;
+          it.kblocks = (d + 63) / 64;
           it.m = m;
-          it.b_off = s->b_off[p];
-          it.p_off = po + (long long)c0 * m;
-          it.dpad = dp;
-          it.ah_off = s->ah_off[p];
-          it.xh_off = ho + (long long)c0 * dp;
+          it.q_off = po + (long long)c0 * m;
+          it.urow = s->b_off[p] + r0;
           it.c_first = c_first + c0;
-          mitems.push_back(it);
+          titems.push_back(it);
         }
     }
     xo += (long long)nc[p] * d;
@@ -291,15 +301,22 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
     return (long long)a.rows * a.chains * a.d > (long long)b.rows * b.chains * b.d;
   };
   std::stable_sort(items.begin(), items.end(), by_cost);
-  std::stable_sort(mitems.begin(), mitems.end(), by_cost);
+  // persistent tensor-core kernel: CTA b takes items b, b + G, ...; largest first
+  std::stable_sort(titems.begin(), titems.end(),
+                   [](const ess::TcBatchItem& a, const ess::TcBatchItem& b) {
+                     return (long long)a.rows * a.ntile * a.kblocks >
+                            (long long)b.rows * b.ntile * b.kblocks;
+                   });
   const int n = (int)desc.size();
   if (n > s->cap_n || xo > s->cap_x || po > s->cap_p ||
-      (int)std::max(items.size(), mitems.size()) > s->cap_items || (bmixed(s) && ho > s->cap_h)) {
+      (int)items.size() > s->cap_items || (int)titems.size() > s->cap_titems ||
+      (bmixed(s) && ho > s->cap_h)) {
     free_work(s);
     const size_t e = belem(s);
     BESS_CUDA(balloc(&s->desc, std::max<size_t>(1, desc.size())));
-    BESS_CUDA(balloc(&s->items, std::max<size_t>(1, std::max(items.size(), mitems.size()))));
-    BESS_CUDA(balloc(&s->mitems, std::max<size_t>(1, std::max(items.size(), mitems.size()))));
+    BESS_CUDA(balloc(&s->items, std::max<size_t>(1, items.size())));
+    BESS_CUDA(balloc(&s->titems, std::max<size_t>(1, titems.size())));
+    s->cap_titems = (int)titems.size();
     BESS_CUDA(cudaMalloc(&s->X, std::max<long long>(1, xo) * e));
     BESS_CUDA(cudaMalloc(&s->NU, std::max<long long>(1, xo) * e));
     BESS_CUDA(cudaMalloc(&s->P, std::max<long long>(1, po) * e));
@@ -319,19 +336,37 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
     s->cap_n = n;
     s->cap_x = xo;
     s->cap_p = po;
-    s->cap_items = (int)std::max(items.size(), mitems.size());
+    s->cap_items = (int)items.size();
   }
   if (!desc.empty())
     BESS_CUDA(cudaMemcpy(s->desc, desc.data(), sizeof(ChainDesc) * desc.size(), cudaMemcpyHostToDevice));
   if (!items.empty())
     BESS_CUDA(cudaMemcpy(s->items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
-  if (!mitems.empty())
-    BESS_CUDA(cudaMemcpy(s->mitems, mitems.data(), sizeof(BatchItem) * mitems.size(), cudaMemcpyHostToDevice));
+  if (!titems.empty())
+    BESS_CUDA(cudaMemcpy(s->titems, titems.data(), sizeof(ess::TcBatchItem) * titems.size(),
+                         cudaMemcpyHostToDevice));
+  if (bmixed(s)) {
+    // operand maps of the tensor-core q GEMM (the nu splits may have moved)
+    std::vector<CUtensorMap> maps((size_t)4 * s->np);
+    std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+    for (int p = 0; p < s->np; ++p) {
+      if (nc[p] == 0) continue;
+      const int d = s->d[p], m = s->m[p], dp = s->dpad[p];
+      for (int k = 0; k < 2; ++k) {
+        BESS_CUDA(ess::tc_batch_map(&maps[4 * p + k], s->Ah[k] + s->ah_off[p], m, d, dp, 128));
+        BESS_CUDA(ess::tc_batch_map(&maps[4 * p + 2 + k], s->H[k] + ho_of[p], nc[p], d, dp,
+                                    ntile_of[p]));
+      }
+    }
+    if (!s->tmaps) BESS_CUDA(cudaMalloc(&s->tmaps, sizeof(CUtensorMap) * maps.size()));
+    BESS_CUDA(cudaMemcpy(s->tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                         cudaMemcpyHostToDevice));
+  }
   drop_graphs(s);
   s->nc = nc;
   s->n = n;
   s->n_items = (int)items.size();
-  s->n_mitems = (int)mitems.size();
+  s->n_titems = (int)titems.size();
   s->total_x = xo;
   s->total_p = po;
   ++s->layout_version;
@@ -378,10 +413,9 @@ ess_status bq(ess_batch* s, bool user_nu, cudaStream_t st) {
     if (user_nu)
       BESS_CUDA(ess::launch_batch_split(s->desc, s->n, static_cast<const float*>(s->NU), s->H[0],
                                         s->H[1], s->chain_unscale, st));
-    BESS_CUDA(ess::launch_batch_q_mma(s->mitems, s->n_mitems, s->queue, s->Ah[0], s->Ah[1],
-                                      s->arow_unscale, s->H[0], s->H[1],
-                                      user_nu ? s->chain_unscale : nullptr,
-                                      static_cast<float*>(s->Q), st));
+    BESS_CUDA(ess::tc_batch_q(s->titems, s->n_titems, s->tmaps, s->arow_unscale,
+                              user_nu ? s->chain_unscale : nullptr, static_cast<float*>(s->Q),
+                              s->dstatus, st));
   } else {
     BESS_CUDA(ess::launch_batch_q<T>(s->items, s->n_items, s->queue, static_cast<const T*>(s->AT),
                                      static_cast<const T*>(s->NU), static_cast<T*>(s->Q), st));

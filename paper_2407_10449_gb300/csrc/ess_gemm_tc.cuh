@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstddef>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -46,6 +47,29 @@ cudaError_t tc_split2_rows(const float* src, int ld, int rows, int cols, __half*
 cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
                        __nv_bfloat16* x_slices, size_t slice_stride, float* row_scale,
                        float* P32, double* P64, int ldp, unsigned long long* drift_bits,
+                       int* status, cudaStream_t s);
+
+// ---- q = A_p nu for a batch of problems (mixed form) -------------------------
+// One work item: rows row0 .. row0 + rows - 1 (rows <= 128) of problem
+// `problem`'s A against its chains chain0 .. chain0 + chains - 1 (chains <= 64,
+// ntile = chains rounded up to 16), over kblocks = ceil(d / 64) K blocks.  The
+// operands come from maps[4 problem + k]: k = 0, 1 the scaled fp16 splits of
+// A_p (m_p x d, row stride dpad, boxes of 128 rows x 64), k = 2, 3 those of the
+// problem's nu rows (its chains x d, boxes of ntile rows x 64).
+// Q[q_off + c m + row0 + r] = (h0.a0 + h1.a0 + h0.a1)(r, c) * arow_unscale[urow + r]
+//   * (chain_unscale ? chain_unscale[c_first + c] : 1 / kNuSplitScale).
+struct TcBatchItem {
+  int problem, row0, rows, chain0, chains, ntile, kblocks, m;
+  long long q_off;   // element offset of chain chain0's row of Q
+  int urow;          // offset of row row0 in arow_unscale
+  int c_first;       // batch index of chain chain0 (chain_unscale)
+};
+// 2-D map of a 16-bit operand (rows x cols, row stride ld elements) with boxes
+// of box_rows x 64 elements, 128-byte swizzle, zero fill out of bounds.
+cudaError_t tc_batch_map(CUtensorMap* map, const __half* base, int rows, int cols, int ld,
+                         int box_rows);
+cudaError_t tc_batch_q(const TcBatchItem* items, int n_items, const CUtensorMap* maps,
+                       const float* arow_unscale, const float* chain_unscale, float* Q,
                        int* status, cudaStream_t s);
 
 // Slice count K and width w of the refresh for dimension d.

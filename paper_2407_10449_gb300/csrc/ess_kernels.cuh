@@ -208,11 +208,6 @@ struct BatchItem {
 // into tiles of 64), and the matching row tile.
 inline int batch_ctile(int n) { return n <= 16 ? 16 : n <= 32 ? 32 : 64; }
 inline int batch_rtile(int ctile) { return 4096 / ctile; }
-#ifndef ESS_BQ_WARPS
-#define ESS_BQ_WARPS 4
-#endif
-constexpr int kBatchMmaTile = 512 * ESS_BQ_WARPS;  // 4 blocks of 16 x 8 per warp
-inline int batch_mma_rtile(int ctile) { return kBatchMmaTile / ctile; }
 
 // nu for every chain of the batch (T = float: float Box-Muller, T = double:
 // 53-bit), written at desc[c].x_off; the step index is t (+ *t_dev if set).
@@ -226,15 +221,6 @@ cudaError_t launch_batch_draw(const ChainDesc* desc, int n_chains, T* NU, uint64
 // with max |nu| in [2^(e-1), 2^e); unscale[c] = 1 / t).
 cudaError_t launch_batch_split(const ChainDesc* desc, int n_chains, const float* NU, __half* H0,
                                __half* H1, float* unscale, cudaStream_t s);
-// Mixed form: Q = A nu per item on the tensor cores (mma.sync, FP16x3), items
-// of rtile x ctile = kBatchMmaTile (batch_mma_rtile):
-// A0, A1 the fp16 splits of A s_i (rows of dpad at ah_off), arow_unscale[i] =
-// 1 / s_i (indexed by b_off + row), H0, H1 the nu splits, chain_unscale[c] =
-// 1 / t_c per chain (nullptr: 1 / kNuSplitScale).
-cudaError_t launch_batch_q_mma(const BatchItem* items, int n_items, int* queue, const __half* A0,
-                               const __half* A1, const float* arow_unscale, const __half* H0,
-                               const __half* H1, const float* chain_unscale, float* Q,
-                               cudaStream_t s);
 // Q = A nu per item, in T; AT holds every problem's A K-major (d x mpad at
 // at_off); queue: one int of scratch (reset by the launcher).
 template <typename T>

@@ -386,179 +386,6 @@ cudaError_t launch_gemm(const BatchItem* items, int n_items, int* queue, const T
   return cudaGetLastError();
 }
 
-// ---- tensor-core grouped q (mixed form) ----------------------------------------
-// q = A nu with warp-level mma.sync m16n8k16 (f16 inputs, f32 accumulation) and
-// the scaled FP16x3 splits of the one-problem path (tc_gemm_q): row i of A is
-// scaled by s_i and split as a0 + a1, nu by t (2^12 for drawn nu) as h0 + h1;
-// q = (h0.a0 + (h1.a0 + h0.a1)) / (s_i t).  M = rows of A, N = chains, K = d.
-// An item's rtile x ctile tile (rtile ctile = 512 per warp) is made of 16 x 8
-// blocks; each of the CTA's warps owns 4 of them (CT = 16: 2 row blocks x 2
-// chain blocks, 32 and 64: 1 x 4).  K is staged 32 at a time (rows padded to
-// 80 bytes: ldmatrix without bank conflicts) in a three-buffer cp.async
-// pipeline; small CTAs keep several items in flight per SM.
-constexpr int kQK = 32;
-constexpr int kQRow = 40;                              // halves per staged row
-#ifndef ESS_BQ_STAGES
-#define ESS_BQ_STAGES 2
-#endif
-#ifndef ESS_BQ_WARPS
-#define ESS_BQ_WARPS 4
-#endif
-constexpr int kQStages = ESS_BQ_STAGES;
-constexpr int kQWarps = ESS_BQ_WARPS;
-constexpr int kQThreads = 32 * kQWarps;
-constexpr int kQTile = 512 * kQWarps;                           // rtile x ctile of an item
-constexpr int kQStageHalves = 2 * (kQTile / 16 + 16) * kQRow;  // largest rtile + ctile
-static_assert(kQTile == kBatchMmaTile, "item shape of the host and the kernel differ");
-constexpr size_t kQSmem = (size_t)kQStages * kQStageHalves * sizeof(__half);
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait_n() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const __half* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_addr(p)));
-}
-
-__device__ __forceinline__ void ldmatrix_x2(uint32_t (&r)[2], const __half* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];"
-               : "=r"(r[0]), "=r"(r[1])
-               : "r"(smem_addr(p)));
-}
-
-__device__ __forceinline__ void mma_f16(float (&c)[4], const uint32_t (&a)[4],
-                                        const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-      "{%8, %9}, {%0, %1, %2, %3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-template <int CT>
-__device__ __forceinline__ void q_mma_item(const BatchItem& I, __half* sm, const __half* A0,
-                                           const __half* A1, const float* arow_unscale,
-                                           const __half* H0, const __half* H1,
-                                           const float* chain_unscale, float* Q) {
-  constexpr int RT = kQTile / CT;
-  constexpr int NBW = CT / 8 < 4 ? CT / 8 : 4;  // chain blocks per warp
-  constexpr int MBW = 4 / NBW;                  // row blocks per warp
-  constexpr int WN = (CT / 8) / NBW;            // warps along the chains
-  static_assert(RT % 16 == 0 && WN * ((RT / 16) / MBW) == kQWarps,
-                "the item's 16 x 8 blocks must split evenly over the warps");
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int mb0 = (warp / WN) * MBW, nb0 = (warp % WN) * NBW;
-  float acc0[MBW][NBW][4], acc1[MBW][NBW][4];
-#pragma unroll
-  for (int i = 0; i < MBW; ++i)
-#pragma unroll
-    for (int j = 0; j < NBW; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        acc0[i][j][e] = 0.f;
-        acc1[i][j][e] = 0.f;
-      }
-  const int nchunk = (I.dpad + kQK - 1) / kQK;
-  // chunk c into buffer buf: A (RT rows) and nu (CT rows), two slices each,
-  // four 16-byte copies per row and slice
-  auto stage = [&](int c, int buf) {
-    __half* as = sm + buf * kQStageHalves;
-    __half* xs = as + 2 * RT * kQRow;
-    const int k0 = c * kQK;
-    for (int idx = tid; idx < RT * 8; idx += kQThreads) {
-      const int r = idx >> 3, sl = (idx >> 2) & 1, ch = idx & 3, k = k0 + ch * 8;
-      const bool ok = r < I.rows && k < I.dpad;
-      const __half* src = (sl ? A1 : A0) + I.ah_off + (size_t)(I.row0 + r) * I.dpad + k;
-      cp_async16(as + (sl * RT + r) * kQRow + ch * 8, ok ? src : A0, ok);
-    }
-    for (int idx = tid; idx < CT * 8; idx += kQThreads) {
-      const int r = idx >> 3, sl = (idx >> 2) & 1, ch = idx & 3, k = k0 + ch * 8;
-      const bool ok = r < I.chains && k < I.dpad;
-      const __half* src = (sl ? H1 : H0) + I.xh_off + (size_t)r * I.dpad + k;
-      cp_async16(xs + (sl * CT + r) * kQRow + ch * 8, ok ? src : H0, ok);
-    }
-  };
-#pragma unroll
-  for (int c = 0; c < kQStages - 1; ++c) {
-    if (c < nchunk) stage(c, c);
-    cp_async_commit();
-  }
-  for (int c = 0; c < nchunk; ++c) {
-    cp_async_wait_n<kQStages - 2>();  // this thread's copies of chunk c have landed
-    __syncthreads();                  // everyone's; buffer (c - 1) % S is free again
-    if (c + kQStages - 1 < nchunk) stage(c + kQStages - 1, (c + kQStages - 1) % kQStages);
-    cp_async_commit();
-    const __half* as = sm + (c % kQStages) * kQStageHalves;
-    const __half* xs = as + 2 * RT * kQRow;
-#pragma unroll
-    for (int ks = 0; ks < kQK / 16; ++ks) {
-      uint32_t af[MBW][2][4], bf[NBW][2][2];
-#pragma unroll
-      for (int i = 0; i < MBW; ++i)
-#pragma unroll
-        for (int sl = 0; sl < 2; ++sl)
-          ldmatrix_x4(af[i][sl], as + (sl * RT + (mb0 + i) * 16 + (lane & 15)) * kQRow + ks * 16 +
-                                     (lane >> 4) * 8);
-#pragma unroll
-      for (int j = 0; j < NBW; ++j)
-#pragma unroll
-        for (int sl = 0; sl < 2; ++sl)
-          ldmatrix_x2(bf[j][sl], xs + (sl * CT + (nb0 + j) * 8 + (lane & 7)) * kQRow + ks * 16 +
-                                     ((lane >> 3) & 1) * 8);
-#pragma unroll
-      for (int i = 0; i < MBW; ++i)
-#pragma unroll
-        for (int j = 0; j < NBW; ++j) {
-          mma_f16(acc0[i][j], af[i][0], bf[j][0]);  // a0 h0
-          mma_f16(acc1[i][j], af[i][0], bf[j][1]);  // a0 h1
-          mma_f16(acc1[i][j], af[i][1], bf[j][0]);  // a1 h0
-        }
-    }
-  }
-  // epilogue: c0, c1 at (row g, chains 2t, 2t + 1), c2, c3 at row g + 8
-  const int g = lane >> 2, t4 = lane & 3;
-#pragma unroll
-  for (int i = 0; i < MBW; ++i)
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      const int r = (mb0 + i) * 16 + g + 8 * hh;
-      if (r >= I.rows) continue;
-      const float ru = arow_unscale[I.b_off + I.row0 + r];
-#pragma unroll
-      for (int j = 0; j < NBW; ++j)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int cc = (nb0 + j) * 8 + 2 * t4 + e;
-          if (cc >= I.chains) continue;
-          const float cu = chain_unscale ? chain_unscale[I.c_first + cc] : 1.f / kNuSplitScale;
-          const float qv = acc0[i][j][2 * hh + e] + acc1[i][j][2 * hh + e];
-          Q[I.p_off + (size_t)cc * I.m + I.row0 + r] = qv * ru * cu;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kQThreads)
-batch_q_mma_kernel(const BatchItem* __restrict__ items, int n_items, int* queue,
-                   const __half* __restrict__ A0, const __half* __restrict__ A1,
-                   const float* __restrict__ arow_unscale, const __half* __restrict__ H0,
-                   const __half* __restrict__ H1, const float* __restrict__ chain_unscale,
-                   float* __restrict__ Q) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __half* sm = reinterpret_cast<__half*>(smem_raw);
-  __shared__ int s_item;
-  for (;;) {
-    const int it = next_item(queue, &s_item);
-    if (it >= n_items) break;
-    const BatchItem I = items[it];
-    if (I.ctile == 16) q_mma_item<16>(I, sm, A0, A1, arow_unscale, H0, H1, chain_unscale, Q);
-    else if (I.ctile == 32) q_mma_item<32>(I, sm, A0, A1, arow_unscale, H0, H1, chain_unscale, Q);
-    else q_mma_item<64>(I, sm, A0, A1, arow_unscale, H0, H1, chain_unscale, Q);
-  }
-}
-
 // status |= kStatusInfeasible where the FP64-class product exceeds b.
 __global__ void batch_check_kernel(const ChainDesc* __restrict__ desc, int n_chains,
                                    const double* __restrict__ P64, const double* __restrict__ b64,
@@ -594,21 +421,6 @@ cudaError_t launch_batch_split(const ChainDesc* desc, int n_chains, const float*
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_q_mma(const BatchItem* items, int n_items, int* queue, const __half* A0,
-                               const __half* A1, const float* arow_unscale, const __half* H0,
-                               const __half* H1, const float* chain_unscale, float* Q,
-                               cudaStream_t s) {
-  if (n_items <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(batch_q_mma_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQSmem);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(queue, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  static const int per_sm = resident_per_sm(batch_q_mma_kernel, kQThreads, kQSmem);
-  batch_q_mma_kernel<<<persistent_grid(n_items, per_sm), kQThreads, kQSmem, s>>>(
-      items, n_items, queue, A0, A1, arow_unscale, H0, H1, chain_unscale, Q);
-  return cudaGetLastError();
-}
 
 template <typename T>
 cudaError_t launch_batch_q(const BatchItem* items, int n_items, int* queue, const T* A,

@@ -1111,6 +1111,198 @@ tc_gemm_pair_persistent_kernel(const __grid_constant__ TcMaps maps,
                  : "memory");
 }
 
+// ---- q = A_p nu for a batch of problems (tcgen05, one SM per work item) --------
+// Work item: rows row0 .. row0 + 127 of one problem's A_p against one group of
+// up to 64 of its chains (N = the group's chain count rounded up to 16).  The
+// FP16x3 products of the one-problem form (h0.a0 into one accumulator,
+// h1.a0 + h0.a1 into a second) with the roles swapped: the MMA's M side is the
+// rows of A_p (TMEM lane = row), its N side the chains, so that the epilogue
+// writes each chain's q as 32 consecutive floats per warp.  One persistent CTA
+// per SM walks the items b, b + G, b + 2G, ... (the host sorts them largest
+// first); the producer streams the K blocks of consecutive items through a
+// ring of stages without a break, and two TMEM accumulator pairs let the
+// epilogue of one item overlap the MMAs of the next.  Operand tiles come from
+// per-problem tensor maps (128-byte swizzle, zero fill past d_p, m_p and the
+// chain count).
+constexpr int kBqStageBytes = 2 * 128 * 64 * 2 + 2 * 64 * 64 * 2;  // two A and two nu tiles
+constexpr int kBqStages = 4;
+
+__global__ void __launch_bounds__(kThreads, 1)
+tc_batch_q_kernel(const TcBatchItem* __restrict__ items, int n_items,
+                  const CUtensorMap* __restrict__ maps, const float* __restrict__ arow_unscale,
+                  const float* __restrict__ chain_unscale, float* __restrict__ Q, int* status) {
+  constexpr uint32_t A_BYTES = 128 * 64 * 2;
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  unsigned char* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  const uint32_t sbase = smem_u32(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBqStages * kBqStageBytes);
+  // bars: [0, S) full, [S, 2S) empty, 2S + {0, 1} accumulator full, 2S + {2, 3} accumulator empty
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kBqStages + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto full_bar = [&](int s) { return smem_u32(bars + s); };
+  auto empty_bar = [&](int s) { return smem_u32(bars + kBqStages + s); };
+  auto accf_bar = [&](int b) { return smem_u32(bars + 2 * kBqStages + b); };
+  auto acce_bar = [&](int b) { return smem_u32(bars + 2 * kBqStages + 2 + b); };
+  constexpr uint32_t TMEM_COLS = 256;  // two buffers x (two accumulators x 64 columns)
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kBqStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf_bar(b), 1);
+      mbar_init(acce_bar(b), 4);  // one arrival per epilogue warp
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_d = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    bool loaded[kBqStages];
+    uint32_t last_phase[kBqStages];
+#pragma unroll
+    for (int j = 0; j < kBqStages; ++j) loaded[j] = false;
+    int s = 0, count = 0;
+    uint32_t phase = 0;
+    for (int it = blockIdx.x; it < n_items && !*abort_flag; it += gridDim.x) {
+      const TcBatchItem I = items[it];
+      const CUtensorMap* mp = maps + 4 * I.problem;
+      const uint32_t bytes = 2u * A_BYTES + 2u * (uint32_t)I.ntile * 128u;
+      for (int kb = 0; kb < I.kblocks; ++kb, ++count) {
+        if (count >= kBqStages && !mbar_wait(empty_bar(s), phase ^ 1u)) {
+          *abort_flag = 1;
+          break;
+        }
+        const uint32_t sa = sbase + s * kBqStageBytes;
+        mbar_expect_tx(full_bar(s), bytes);
+        tma_load_2d(sa, mp + 0, kb * BK, I.row0, full_bar(s));
+        tma_load_2d(sa + A_BYTES, mp + 1, kb * BK, I.row0, full_bar(s));
+        tma_load_2d(sa + 2 * A_BYTES, mp + 2, kb * BK, I.chain0, full_bar(s));
+        tma_load_2d(sa + 2 * A_BYTES + (uint32_t)I.ntile * 128u, mp + 3, kb * BK, I.chain0,
+                    full_bar(s));
+        loaded[s] = true;
+        last_phase[s] = phase;
+        if (++s == kBqStages) {
+          s = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+    if (*abort_flag) {
+#pragma unroll
+      for (int j = 0; j < kBqStages; ++j)
+        if (loaded[j]) (void)mbar_wait(full_bar(j), last_phase[j]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    int s = 0, j = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++j) {
+      const TcBatchItem I = items[it];
+      const int buf = j & 1;
+      // the epilogue has read this buffer's previous item (item j - 2)
+      if (j >= 2 && !mbar_wait(acce_bar(buf), (uint32_t)(((j - 2) >> 1) & 1))) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t idesc = idesc_f16(128, I.ntile, false);
+      const uint32_t acc0 = tmem_d + (uint32_t)(buf * 128), acc1 = acc0 + 64;
+      for (int kb = 0; kb < I.kblocks; ++kb) {
+        if (!mbar_wait(full_bar(s), phase)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = sbase + s * kBqStageBytes;
+        const uint64_t a0 = smem_desc_sw128(sa);
+        const uint64_t a1 = smem_desc_sw128(sa + A_BYTES);
+        const uint64_t h0 = smem_desc_sw128(sa + 2 * A_BYTES);
+        const uint64_t h1 = smem_desc_sw128(sa + 2 * A_BYTES + (uint32_t)I.ntile * 128u);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k)
+          umma_bf16(acc0, a0 + 2 * k, h0 + 2 * k, idesc, (kb == 0 && k == 0) ? 0u : 1u);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k)
+          umma_bf16(acc1, a1 + 2 * k, h0 + 2 * k, idesc, (kb == 0 && k == 0) ? 0u : 1u);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k)
+          umma_bf16(acc1, a0 + 2 * k, h1 + 2 * k, idesc, 1u);
+        umma_commit(empty_bar(s));
+        if (++s == kBqStages) {
+          s = 0;
+          phase ^= 1u;
+        }
+      }
+      if (ok) umma_commit(accf_bar(buf));
+    }
+    if (!ok) *abort_flag = 1;
+  } else if (warp >= 2) {
+    // ---------------- epilogue warps 2..5: TMEM lane quarter warp % 4 ----------------
+    const int quarter = warp & 3;
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    int j = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++j) {
+      const int buf = j & 1;
+      const bool ready = !*abort_flag && mbar_wait(accf_bar(buf), (uint32_t)((j >> 1) & 1));
+      tc_fence_after();
+      if (!ready) {
+        *abort_flag = 1;
+        break;
+      }
+      const TcBatchItem I = items[it];
+      const int r = quarter * 32 + lane;  // row within the item
+      const bool row_ok = r < I.rows;
+      const float ru = row_ok ? arow_unscale[I.urow + r] : 0.f;
+      const uint32_t acc0 = tmem_d + lane_off + (uint32_t)(buf * 128), acc1 = acc0 + 64;
+      // all of this item's accumulators in registers first (<= 64 columns)
+      float qv[64];
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 32) {
+        if (c0 < I.ntile) {
+          uint32_t v[32], w[32];
+          tmem_ld_32cols(acc0 + (uint32_t)c0, v);
+          tmem_ld_32cols(acc1 + (uint32_t)c0, w);
+          tmem_ld_wait();
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) qv[c0 + jj] = __uint_as_float(v[jj]) + __uint_as_float(w[jj]);
+        }
+      }
+      // TMEM buffer free for the item after next
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce_bar(buf));
+      if (row_ok) {
+        float* qrow = Q + I.q_off + I.row0 + r;  // chain c of the item at qrow[c * m]
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+          if (c < I.chains) {
+            const float cu = chain_unscale ? chain_unscale[I.c_first + c] : 1.f / kNuSplitScale;
+            qrow[(size_t)c * I.m] = qv[c] * ru * cu;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(status, kStatusTimeout);
+  if (warp == 0) tmem_dealloc(tmem_d, TMEM_COLS);
+}
+
 // Fixed-point slices of the chain states for the exact refresh: per row c,
 // t_c = 2^e with max_j |x_cj| < t_c, and x_cj / t_c = sum_l e_l 2^(-w l) + r,
 // e_l integers in (-2^w, 2^w) stored exactly as bf16.  One warp per row.
@@ -1699,6 +1891,25 @@ cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
   a.drift_bits = drift_bits;
   a.status = status;
   return launch_bn<kRefreshBN, kModePairs>(maps, a, s);
+}
+
+cudaError_t tc_batch_map(CUtensorMap* map, const __half* base, int rows, int cols, int ld,
+                         int box_rows) {
+  return make_map(map, base, rows, cols, ld, box_rows, false);
+}
+
+cudaError_t tc_batch_q(const TcBatchItem* items, int n_items, const CUtensorMap* maps,
+                       const float* arow_unscale, const float* chain_unscale, float* Q,
+                       int* status, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  const size_t smem = (size_t)kBqStages * kBqStageBytes + 1024 + 256;
+  cudaError_t e = cudaFuncSetAttribute(tc_batch_q_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(n_items, num_sms());
+  tc_batch_q_kernel<<<grid, kThreads, smem, s>>>(items, n_items, maps, arow_unscale,
+                                                  chain_unscale, Q, status);
+  return cudaGetLastError();
 }
 
 }  // namespace ess
