@@ -64,6 +64,21 @@ typedef enum {
                                    error-free fixed-point split, rounded once */
 } ess_refresh_mode;
 
+typedef enum {
+    ESS_PRODUCTS_DFMA = 0,      /* FP64 form: q = A nu and p = A x with FP64
+                                   fused multiply-adds (plain FP64) */
+    ESS_PRODUCTS_SPLIT = 1      /* FP64 form: both products on BF16 tensor
+                                   cores from 56-bit fixed-point splits of both
+                                   operands (integer slices of w <= 8 bits,
+                                   every slice product exact in the FP32
+                                   accumulator, the pairs combined error-free,
+                                   rounded once to double): error below
+                                   d (3 + K(K-1)/2) 2^-(wK) max|a_i| max|x|
+                                   (e.g. 4e-13 relative to that at d = 1000)
+                                   plus N^2 2^-48 sum_j |a_ij x_j| for the
+                                   N = K(K+1)/2 slice products */
+} ess_products_mode;
+
 typedef struct {
     int precision;              /* ess_precision; default ESS_PREC_FP64 */
     int refresh_k;              /* p = A x recomputed when t % refresh_k == 0;
@@ -101,7 +116,10 @@ typedef struct {
                                    kernel, one cluster per SM pair (when m is
                                    not a multiple of 4, 2000 + BN runs).  Any
                                    other value is ESS_ERR_ARG. */
-    int reserved[6];
+    int fp64_products;          /* FP64 form: ess_products_mode; default
+                                   ESS_PRODUCTS_DFMA (ignored by the mixed
+                                   form) */
+    int reserved[5];
 } ess_config;
 
 typedef struct {

@@ -32,6 +32,8 @@ ESS_PREC_FP64 = 0
 ESS_PREC_MIXED = 1
 ESS_REFRESH_FP64 = 0
 ESS_REFRESH_SPLIT = 1
+ESS_PRODUCTS_DFMA = 0
+ESS_PRODUCTS_SPLIT = 1
 
 _STATUS_NAMES = {0: "ESS_OK", 1: "ESS_ERR_ARG", 2: "ESS_ERR_INFEASIBLE_X0", 3: "ESS_ERR_CUDA",
                  4: "ESS_ERR_NUMERIC", 5: "ESS_ERR_TIMEOUT", 6: "ESS_ERR_OOM",
@@ -67,7 +69,8 @@ class ess_config(ctypes.Structure):
                 ("refresh_mode", ctypes.c_int), ("tangent_thresh", ctypes.c_double),
                 ("trim_eps", ctypes.c_double), ("residual_margin", ctypes.c_double),
                 ("sort_threads", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("q_tile", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("q_tile", ctypes.c_int), ("fp64_products", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class ess_stats(ctypes.Structure):

@@ -129,6 +129,13 @@ struct ess_state {
 namespace {
 
 bool mixed(const ess_state* s) { return s->cfg.precision == ESS_PREC_MIXED; }
+// FP64 form with its products from exact splits on the tensor cores
+bool split64(const ess_state* s) {
+  return s->cfg.precision == ESS_PREC_FP64 && s->cfg.fp64_products == ESS_PRODUCTS_SPLIT;
+}
+// bits of the fixed-point splits of the FP64 form's operands (a double's 53
+// plus room for the per-row power-of-two scaling)
+constexpr int kSplit64Bits = 56;
 
 // Records an event for phase timing; returns its pool index or -1.
 int timing_mark(ess_state* s, cudaStream_t st) {
@@ -223,6 +230,13 @@ ess_status ensure_capacity(ess_state* s, int n) {
     }
   } else {
     ESS_CUDA(dev_alloc(&s->Xd, (size_t)n * s->d));
+    if (split64(s)) {
+      // slices of x (refresh) or nu (q), one at a time
+      const int K = ess::tc_refresh_num_slices(s->tc_plan);
+      ESS_CUDA(dev_alloc(&s->x_slices, (size_t)K * n * s->ld16));
+      ESS_CUDA(cudaMemset(s->x_slices, 0, (size_t)K * n * s->ld16 * sizeof(__nv_bfloat16)));
+      ESS_CUDA(dev_alloc(&s->row_scale, (size_t)n));
+    }
   }
   s->cap = n;
   return ESS_OK;
@@ -261,6 +275,19 @@ ess_status refresh_p(ess_state* s, int n, const void* Xcur, bool with_drift, boo
       cudaFree(P64);
       if (e != cudaSuccess) return cuda_fail(e, "feasibility check");
     }
+  } else if (split64(s)) {
+    // FP64 products from exact 56-bit splits on the tensor cores
+    const double* Xd = static_cast<const double*>(Xcur);
+    ESS_CUDA(ess::tc_exact_f64(s->tc_plan, Xd, s->d, n, s->x_slices, (size_t)n * s->ld16,
+                               s->row_scale, static_cast<double*>(s->P), s->m,
+                               with_drift ? &s->dstats->max_drift_bits : nullptr, s->dstatus, st));
+    if (check) {
+      // entries within the split's bound of b_i are decided by FP64 FMAs
+      ESS_CUDA(ess::launch_check_feasible_bounded(
+          static_cast<const double*>(s->P), s->m, s->b64, n, s->m, s->row_scale,
+          ess::tc_refresh_col_scale(s->tc_plan), ess::tc_refresh_bound_factor(s->tc_plan), Xd,
+          s->d, s->A64, s->d, s->dstatus, st));
+    }
   } else {
     ESS_CUDA((ess::launch_gemm_nt_f64<double, double>(static_cast<const double*>(Xcur), s->d,
                                                        s->A64, s->d, static_cast<double*>(s->P),
@@ -279,6 +306,10 @@ ess_status compute_q(ess_state* s, int n, cudaStream_t st, bool drawn = true) {
     cudaError_t e = ess::tc_gemm_q(s->tc_plan, s->NU_h, drawn ? nullptr : s->nu_unscale, s->ld16,
                                    n, static_cast<float*>(s->Q), s->m, s->dstatus, st);
     if (e != cudaSuccess) return cuda_fail(e, "FP16x3 tensor-core GEMM");
+  } else if (split64(s)) {
+    ESS_CUDA(ess::tc_exact_f64(s->tc_plan, static_cast<const double*>(s->NU), s->d, n,
+                               s->x_slices, (size_t)n * s->ld16, s->row_scale,
+                               static_cast<double*>(s->Q), s->m, nullptr, s->dstatus, st));
   } else {
     ESS_CUDA((ess::launch_gemm_nt_f64<double, double>(static_cast<const double*>(s->NU), s->d,
                                                        s->A64, s->d, static_cast<double*>(s->Q),
@@ -606,6 +637,8 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
   if (!(c.tangent_thresh >= 0.0 && c.tangent_thresh < 1.0) || !(c.trim_eps >= 0.0) ||
       !(c.residual_margin >= 0.0))
     return fail(ESS_ERR_ARG, "tangent_thresh in [0, 1), trim_eps >= 0, residual_margin >= 0");
+  if (c.fp64_products != ESS_PRODUCTS_DFMA && c.fp64_products != ESS_PRODUCTS_SPLIT)
+    return fail(ESS_ERR_ARG, "unknown fp64_products");
   if (c.q_tile != 0 &&
       std::find(ess::kTcWidths, ess::kTcWidths + 16, c.q_tile) == ess::kTcWidths + 16)
     return fail(ESS_ERR_ARG,
@@ -683,6 +716,8 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
     if (e == cudaSuccess) e = ess::tc_gemm_create(&s->tc_plan, A, m, d);
     if (e == cudaSuccess && c.q_tile) e = ess::tc_gemm_set_width(s->tc_plan, c.q_tile);
   }
+  if (e == cudaSuccess && c.precision == ESS_PREC_FP64 && c.fp64_products == ESS_PRODUCTS_SPLIT)
+    e = ess::tc_gemm_create(&s->tc_plan, A, m, d, kSplit64Bits, false);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "ess_create device setup"));
   *out = s;
   return ESS_OK;

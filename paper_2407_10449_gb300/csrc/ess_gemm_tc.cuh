@@ -12,10 +12,12 @@ namespace ess {
 struct TcGemmPlan;
 
 // Prepares the constant operand A (host, m x d row-major doubles): the scaled
-// two-way fp16 split of A rounded to float (for q = A nu) and the fixed-point
-// slices of A with per-row power-of-two scales (for the exact refresh).
-// Operand rows are padded to a multiple of 8 elements.
-cudaError_t tc_gemm_create(TcGemmPlan** plan, const double* A, int m, int d);
+// two-way fp16 split of A rounded to float (for q = A nu; only if with_q) and
+// the fixed-point slices of A with per-row power-of-two scales (for the exact
+// products: ceil(exact_bits / w) slices of w bits).  Operand rows are padded
+// to a multiple of 8 elements.
+cudaError_t tc_gemm_create(TcGemmPlan** plan, const double* A, int m, int d,
+                           int exact_bits = 35, bool with_q = true);
 void tc_gemm_destroy(TcGemmPlan* plan);
 
 // Q[c, i] = a_i . nu_c from the scaled fp16 splits nu_c t_c = h0 + h1 (rows of
@@ -72,8 +74,21 @@ cudaError_t tc_batch_q(const TcBatchItem* items, int n_items, const CUtensorMap*
                        const float* arow_unscale, const float* chain_unscale, float* Q,
                        int* status, cudaStream_t s);
 
-// Slice count K and width w of the refresh for dimension d.
-int tc_refresh_slices(int d, int* w);
+// FP64 products P64 = A x for double rows X with the same exact split (the
+// plan's slices; with 56 bits the truncation leaves d (3 + K(K-1)/2) 2^-(wK)
+// s_i t_c, e.g. 4e-13 s_i t_c at d = 1000), the N = K(K+1)/2 exact slice
+// products summed into (hi, lo) float pairs (every addition error-free, the
+// low parts summed in float: at most N^2 2^-48 sum_j |a_ij x_j| more) and
+// rounded once to double; with drift_bits, max |P64_new - P64_old| / ||a_i||
+// is folded in.
+cudaError_t tc_exact_f64(TcGemmPlan* plan, const double* X, int ldx, int n_chains,
+                         __nv_bfloat16* x_slices, size_t slice_stride, float* row_scale,
+                         double* P64, int ldp, unsigned long long* drift_bits, int* status,
+                         cudaStream_t s);
+
+// Slice count K and width w of the exact products for dimension d and a
+// budget of `bits` bits per operand.
+int tc_refresh_slices(int d, int* w, int bits = 35);
 int tc_refresh_num_slices(const TcGemmPlan* plan);
 double tc_refresh_bound_factor(const TcGemmPlan* plan);
 const float* tc_refresh_col_scale(const TcGemmPlan* plan);

@@ -46,11 +46,12 @@ cudaError_t launch_gemm_nt_f64(const TX* X, int ldx, const double* A, int lda, T
 cudaError_t launch_check_feasible(const double* P, int ldp, const double* b, int rows, int m,
                                   int* status, cudaStream_t s);
 
-// Feasibility of float states X from a product P known to within
+// Feasibility of states X (float or double) from a product P known to within
 // bound * row_scale[r] * col_scale[i]; undecided entries recomputed in FP64.
+template <typename TX>
 cudaError_t launch_check_feasible_bounded(const double* P, int ldp, const double* b, int rows,
                                           int m, const float* row_scale, const float* col_scale,
-                                          double bound, const float* X, int ldx, const double* A,
+                                          double bound, const TX* X, int ldx, const double* A,
                                           int d, int* status, cudaStream_t s);
 
 // ------------------------------------------------------------ chain step ---

@@ -112,11 +112,12 @@ __global__ void check_feasible_kernel(const double* __restrict__ P, int ldp,
 // Feasibility of float states from an exact-split product P (error at most
 // bound * s_i * t_c): certain violations and certain passes are decided from
 // P; the few entries within the bound are recomputed with FP64 FMAs.
+template <typename TX>
 __global__ void check_feasible_bounded_kernel(const double* __restrict__ P, int ldp,
                                               const double* __restrict__ b, int rows, int m,
                                               const float* __restrict__ row_scale,
                                               const float* __restrict__ col_scale, double bound,
-                                              const float* __restrict__ X, int ldx,
+                                              const TX* __restrict__ X, int ldx,
                                               const double* __restrict__ A, int d, int* status) {
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long long)rows * m) return;
@@ -126,7 +127,7 @@ __global__ void check_feasible_bounded_kernel(const double* __restrict__ P, int 
   if (!(v <= b[i] + e)) {
     atomicOr(status, kStatusInfeasible);
   } else if (v > b[i] - e) {
-    const float* x = X + (size_t)r * ldx;
+    const TX* x = X + (size_t)r * ldx;
     const double* a = A + (size_t)i * d;
     double acc = 0.0;
     for (int j = 0; j < d; ++j) acc = fma(a[j], (double)x[j], acc);
@@ -185,17 +186,27 @@ cudaError_t launch_check_feasible(const double* P, int ldp, const double* b, int
   return cudaGetLastError();
 }
 
+template <typename TX>
 cudaError_t launch_check_feasible_bounded(const double* P, int ldp, const double* b, int rows,
                                           int m, const float* row_scale, const float* col_scale,
-                                          double bound, const float* X, int ldx, const double* A,
+                                          double bound, const TX* X, int ldx, const double* A,
                                           int d, int* status, cudaStream_t s) {
   const long long n = (long long)rows * m;
   if (n == 0) return cudaSuccess;
-  check_feasible_bounded_kernel<<<grid_for(n, 256), 256, 0, s>>>(P, ldp, b, rows, m, row_scale,
+  check_feasible_bounded_kernel<TX><<<grid_for(n, 256), 256, 0, s>>>(P, ldp, b, rows, m, row_scale,
                                                                  col_scale, bound, X, ldx, A, d,
                                                                  status);
   return cudaGetLastError();
 }
+
+template cudaError_t launch_check_feasible_bounded<float>(const double*, int, const double*, int,
+                                                         int, const float*, const float*, double,
+                                                         const float*, int, const double*, int,
+                                                         int*, cudaStream_t);
+template cudaError_t launch_check_feasible_bounded<double>(const double*, int, const double*, int,
+                                                          int, const float*, const float*, double,
+                                                          const double*, int, const double*, int,
+                                                          int*, cudaStream_t);
 
 template cudaError_t launch_convert<double, float>(const double*, int, float*, int, int, int,
                                                    cudaStream_t);

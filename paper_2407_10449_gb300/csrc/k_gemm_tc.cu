@@ -48,8 +48,8 @@ constexpr int BM = 128;             // chains per tile (MMA M)
 constexpr int BK = 64;              // 16-bit elements per 128-byte swizzle row
 constexpr int kThreads = 192;       // producer warp, MMA warp, 4 epilogue warps
 constexpr int kRefreshBN = 64;      // tile width of the exact refresh
-constexpr int kMaxSlices = 7;       // operand slices of the exact refresh
-constexpr int kMaxRounds = 4;       // refresh rounds (<= 8 slice pairs each)
+constexpr int kMaxSlices = 12;      // operand slices of the exact products
+constexpr int kMaxRounds = 16;      // rounds of the exact products (<= 8 slice pairs each)
 // shared memory of one refresh stage: the x and A slice tiles of one round.
 // 64 KB packs the 15 slice pairs of K = 5 into rounds of 5, 7 and 3 pairs and
 // leaves room for three stages (the same bytes per tile as two rounds of up
@@ -70,8 +70,9 @@ struct RefreshGroup {
   unsigned char xs, a0, na, col;
 };
 struct RefreshRound {
-  unsigned char nx, na, ngroups, npairs;  // x tiles, A tiles (slices 0 .. na-1), groups, pairs
+  unsigned char nx, na, ngroups, npairs;  // x tiles, A tiles, groups, pairs
   unsigned char x[kMaxSlices];            // x slice of each loaded x tile
+  unsigned char a[kMaxSlices];            // A slice of each loaded A tile
   RefreshGroup g[8];
   unsigned char shift[8];                 // accumulator block j holds a pair of weight 2^-shift
 };
@@ -391,7 +392,8 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
         for (int i = 0; i < R.nx; ++i)
           tma_load_2d(sa + i * A_BYTES, &maps.x[R.x[i]], kb * BK, m0, full_bar(s));
         for (int j = 0; j < R.na; ++j)
-          tma_load_2d(sa + R.nx * A_BYTES + j * B_BYTES, &maps.b[j], kb * BK, n0, full_bar(s));
+          tma_load_2d(sa + R.nx * A_BYTES + j * B_BYTES, &maps.b[R.a[j]], kb * BK, n0,
+                      full_bar(s));
         loaded[s] = true;
         last_phase[s] = phase;
         if (++s == STAGES) {
@@ -535,13 +537,32 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
         const size_t base = (size_t)row * args.ldp;
         const bool full = n0 + BN <= args.n_cols;
         if (args.P64) {
+          // FP64 product (hi + lo exact in double, scales are powers of two);
+          // without a float copy the drift statistic compares the FP64 values,
+          // 16 columns at a time (old values loaded before the stores)
+          const bool d64 = args.drift_bits != nullptr && args.P32 == nullptr;
+          double* prow64 = args.P64 + base + n0;
+          double drift64 = 0.0;
 #pragma unroll
-          for (int j = 0; j < BN; ++j) {
-            const int col = n0 + j;
-            if (col < args.n_cols)
-              args.P64[base + col] =
-                  ((double)hi[j] + (double)lo[j]) * (double)rs * (double)args.col_scale[col];
+          for (int j0 = 0; j0 < BN; j0 += 16) {
+            double old[16];
+            if (d64) {
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) old[jj] = n0 + j0 + jj < args.n_cols ? prow64[j0 + jj] : 0.0;
+            }
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const int col = n0 + j0 + jj;
+              if (col < args.n_cols) {
+                const double v = ((double)hi[j0 + jj] + (double)lo[j0 + jj]) * (double)rs *
+                                 (double)args.col_scale[col];
+                if (d64) drift64 = fmax(drift64, fabs(v - old[jj]) * (double)args.inv_anorm[col]);
+                prow64[j0 + jj] = v;
+              }
+            }
           }
+          if (d64 && drift64 > 0.0)
+            atomicMax(args.drift_bits, (unsigned long long)__double_as_longlong(drift64));
         }
         if (args.P32) {
           // p rounded once to float (the scales are powers of two), kept in hi
@@ -1310,29 +1331,30 @@ tc_batch_q_kernel(const TcBatchItem* __restrict__ items, int n_items,
 // Fixed-point slices of the chain states for the exact refresh: per row c,
 // t_c = 2^e with max_j |x_cj| < t_c, and x_cj / t_c = sum_l e_l 2^(-w l) + r,
 // e_l integers in (-2^w, 2^w) stored exactly as bf16.  One warp per row.
-__global__ void slice_rows_kernel(const float* __restrict__ X, int ldx, int rows, int d, int w,
+template <typename TI>
+__global__ void slice_rows_kernel(const TI* __restrict__ X, int ldx, int rows, int d, int w,
                                   int K, __nv_bfloat16* __restrict__ slices, int ld_bf,
                                   size_t slice_stride, float* __restrict__ row_scale) {
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= rows) return;
-  const float* x = X + (size_t)row * ldx;
-  float mx = 0.f;
-  for (int j = lane; j < d; j += 32) mx = fmaxf(mx, fabsf(x[j]));
+  const TI* x = X + (size_t)row * ldx;
+  TI mx = TI(0);
+  for (int j = lane; j < d; j += 32) mx = fmax(mx, fabs(x[j]));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   int e = 0;
-  if (mx > 0.f) (void)frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1): mx < 2^e
-  const float inv_t = ldexpf(1.f, -e);
-  if (lane == 0) row_scale[row] = mx > 0.f ? ldexpf(1.f, e) : 0.f;
-  const float up = ldexpf(1.f, w);
+  if (mx > TI(0)) (void)frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): mx < 2^e
+  const TI inv_t = ldexp(TI(1), -e);
+  if (lane == 0) row_scale[row] = mx > TI(0) ? ldexpf(1.f, e) : 0.f;
+  const TI up = ldexp(TI(1), w);
   for (int j = lane; j < d; j += 32) {
-    float y = x[j] * inv_t;  // exact: power-of-two scaling
+    TI y = x[j] * inv_t;  // exact: power-of-two scaling
     for (int l = 0; l < K; ++l) {
       y *= up;
-      const float c = truncf(y);
+      const TI c = trunc(y);  // an integer of at most w bits: exact in bf16
       y -= c;
-      slices[(size_t)l * slice_stride + (size_t)row * ld_bf + j] = __float2bfloat16_rn(c);
+      slices[(size_t)l * slice_stride + (size_t)row * ld_bf + j] = __float2bfloat16_rn((float)c);
     }
   }
 }
@@ -1632,17 +1654,19 @@ void tc_gemm_tile_for(int n_chains, int m, int* bn, int* stages) {
   *bn = pair ? kPersistCode + best : best;
 }
 
-int tc_refresh_slices(int d, int* w_out) {
-  // widest slice w with (2^w - 1)^2 d <= 2^24 (exact FP32 sums), at most 8 bits
+int tc_refresh_slices(int d, int* w_out, int bits) {
+  // widest slice w with (2^w - 1)^2 d <= 2^24 (exact FP32 sums), at most 8 bits;
+  // K = ceil(bits / w) slices per operand
   int w = 8;
   while (w > 1 && (double)((1 << w) - 1) * ((1 << w) - 1) * d > 16777216.0) --w;
-  int K = (35 + w - 1) / w;
+  int K = (bits + w - 1) / w;
   if (K > kMaxSlices) K = kMaxSlices;
   if (w_out) *w_out = w;
   return K;
 }
 
-cudaError_t tc_gemm_create(TcGemmPlan** plan, const double* A, int m, int d) {
+cudaError_t tc_gemm_create(TcGemmPlan** plan, const double* A, int m, int d, int exact_bits,
+                           bool with_q) {
   *plan = nullptr;
   TcGemmPlan* p = new TcGemmPlan();
   p->m = m;
@@ -1653,6 +1677,8 @@ cudaError_t tc_gemm_create(TcGemmPlan** plan, const double* A, int m, int d) {
     tc_gemm_destroy(p);
     return e;
   };
+  cudaError_t e = cudaSuccess;
+  if (with_q) {
   // --- FP16x3 operands: A rounded to float, row i scaled by s_i = 2^(15 - e_i)
   // (max_j |a_ij| in [2^(e_i - 1), 2^e_i)) and split as a s_i = a0 + a1
   std::vector<__half> h0((size_t)m * ld, __float2half_rn(0.f)), h1 = h0;
@@ -1671,7 +1697,6 @@ cudaError_t tc_gemm_create(TcGemmPlan** plan, const double* A, int m, int d) {
       h1[(size_t)i * ld + j] = __float2half_rn(y - __half2float(a));
     }
   }
-  cudaError_t e = cudaSuccess;
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
     e = cudaMalloc(&p->a2[k], sizeof(__half) * (size_t)m * ld);
     if (e == cudaSuccess)
@@ -1689,9 +1714,10 @@ cudaError_t tc_gemm_create(TcGemmPlan** plan, const double* A, int m, int d) {
     for (int k = 0; k < 2 && e == cudaSuccess; ++k)
       e = make_map(&p->pmaps[i][k], p->a2[k], m, d, ld, kPairWidths[i] / 2, false);
   if (e != cudaSuccess) return fail(e);
+  }  // with_q
 
-  // --- exact refresh operands: fixed-point slices of A in FP64 on the host
-  p->K = tc_refresh_slices(d, &p->w);
+  // --- exact products: fixed-point slices of A in FP64 on the host
+  p->K = tc_refresh_slices(d, &p->w, exact_bits);
   const int w = p->w, K = p->K;
   std::vector<__nv_bfloat16> slices((size_t)K * m * ld, __float2bfloat16_rn(0.f));
   std::vector<float> cs(m);
@@ -1825,14 +1851,16 @@ cudaError_t tc_gemm_q(TcGemmPlan* plan, __half* const nu[2], const float* nu_uns
                      : launch_sum(bn, maps, a, s);
 }
 
-cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
-                       __nv_bfloat16* x_slices, size_t slice_stride, float* row_scale,
-                       float* P32, double* P64, int ldp, unsigned long long* drift_bits,
-                       int* status, cudaStream_t s) {
+namespace {
+template <typename TI>
+cudaError_t exact_product(TcGemmPlan* plan, const TI* X, int ldx, int n_chains,
+                          __nv_bfloat16* x_slices, size_t slice_stride, float* row_scale,
+                          float* P32, double* P64, int ldp, unsigned long long* drift_bits,
+                          int* status, cudaStream_t s) {
   if (!plan) return cudaErrorInvalidValue;
   if (n_chains == 0) return cudaSuccess;
   const int K = plan->K, ld = plan->ld16;
-  slice_rows_kernel<<<grid_for((long long)n_chains * 32, 256), 256, 0, s>>>(
+  slice_rows_kernel<TI><<<grid_for((long long)n_chains * 32, 256), 256, 0, s>>>(
       X, ldx, n_chains, plan->d, plan->w, K, x_slices, ld, slice_stride, row_scale);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1849,8 +1877,16 @@ cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
   a.n_cols = plan->m;
   a.kblocks = (plan->d + BK - 1) / BK;
   // slice pairs (x slice l, A slice k), k + l <= K + 1 (1-based), grouped into
-  // rounds of at most 8 pairs whose tiles fit one stage; within a round the
-  // pairs of one x slice with consecutive A slices share one MMA (N <= 256)
+  // rounds of at most 8 pairs whose x and A tiles (each loaded once per round)
+  // fit one stage; within a round the pairs of one x tile with A tiles that
+  // sit next to each other in the stage share one MMA (N <= 256)
+  constexpr uint32_t kXTile = (uint32_t)BM * BK * 2, kATile = (uint32_t)kRefreshBN * BK * 2;
+  static_assert(kXTile + kATile <= kRefreshStage, "one slice pair must fit a stage");
+  auto pos_of = [](const unsigned char* arr, int n, int v) {
+    for (int i = 0; i < n; ++i)
+      if (arr[i] == (unsigned char)v) return i;
+    return -1;
+  };
   int nr = 0;
   auto open_round = [&]() {
     std::memset(&a.round[nr], 0, sizeof(RefreshRound));
@@ -1860,30 +1896,40 @@ cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
   for (int l = 1; l <= K; ++l)
     for (int k = 1; k + l <= K + 1; ++k) {
       RefreshRound* R = &a.round[nr - 1];
-      const bool new_x = R->nx == 0 || R->x[R->nx - 1] != (unsigned char)(l - 1);
-      const int nx = R->nx + (new_x ? 1 : 0);
-      const int na = std::max<int>(R->na, k);
-      const uint32_t bytes = (uint32_t)nx * BM * BK * 2 + (uint32_t)na * kRefreshBN * BK * 2;
+      int xi = pos_of(R->x, R->nx, l - 1), ai = pos_of(R->a, R->na, k - 1);
+      const uint32_t bytes = (uint32_t)(R->nx + (xi < 0 ? 1 : 0)) * kXTile +
+                             (uint32_t)(R->na + (ai < 0 ? 1 : 0)) * kATile;
       if (R->npairs == 8 || bytes > kRefreshStage) {
         if (nr == kMaxRounds) return cudaErrorInvalidValue;
         open_round();
         R = &a.round[nr - 1];
+        xi = ai = -1;
       }
-      if (R->nx == 0 || R->x[R->nx - 1] != (unsigned char)(l - 1)) R->x[R->nx++] = (unsigned char)(l - 1);
-      R->na = (unsigned char)std::max<int>(R->na, k);
+      if (xi < 0) {
+        xi = R->nx;
+        R->x[R->nx++] = (unsigned char)(l - 1);
+      }
+      if (ai < 0) {
+        ai = R->na;
+        R->a[R->na++] = (unsigned char)(k - 1);
+      }
       const int col = R->npairs++;
       R->shift[col] = (unsigned char)(plan->w * (k + l));
       RefreshGroup* G = R->ngroups ? &R->g[R->ngroups - 1] : nullptr;
-      if (G && G->xs == R->nx - 1 && G->a0 + G->na == k - 1 && G->na < 4 && G->col + G->na == col) {
+      if (G && G->xs == xi && G->a0 + G->na == ai && G->na < 4 && G->col + G->na == col) {
         ++G->na;
       } else {
         G = &R->g[R->ngroups++];
-        G->xs = (unsigned char)(R->nx - 1);
-        G->a0 = (unsigned char)(k - 1);
+        G->xs = (unsigned char)xi;
+        G->a0 = (unsigned char)ai;
         G->na = 1;
         G->col = (unsigned char)col;
       }
     }
+  // every round's tiles fit a stage (the copies of a stage land inside it)
+  for (int r = 0; r < nr; ++r)
+    if ((uint32_t)a.round[r].nx * kXTile + (uint32_t)a.round[r].na * kATile > kRefreshStage)
+      return cudaErrorInvalidValue;
   a.nrounds = nr;
   a.ngroups = 0;
   a.row_scale = row_scale;
@@ -1895,6 +1941,23 @@ cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
   a.drift_bits = drift_bits;
   a.status = status;
   return launch_bn<kRefreshBN, kModePairs>(maps, a, s);
+}
+}  // namespace
+
+cudaError_t tc_refresh(TcGemmPlan* plan, const float* X, int ldx, int n_chains,
+                       __nv_bfloat16* x_slices, size_t slice_stride, float* row_scale,
+                       float* P32, double* P64, int ldp, unsigned long long* drift_bits,
+                       int* status, cudaStream_t s) {
+  return exact_product<float>(plan, X, ldx, n_chains, x_slices, slice_stride, row_scale, P32,
+                              P64, ldp, drift_bits, status, s);
+}
+
+cudaError_t tc_exact_f64(TcGemmPlan* plan, const double* X, int ldx, int n_chains,
+                         __nv_bfloat16* x_slices, size_t slice_stride, float* row_scale,
+                         double* P64, int ldp, unsigned long long* drift_bits, int* status,
+                         cudaStream_t s) {
+  return exact_product<double>(plan, X, ldx, n_chains, x_slices, slice_stride, row_scale,
+                               nullptr, P64, ldp, drift_bits, status, s);
 }
 
 cudaError_t tc_batch_map(CUtensorMap* map, const __half* base, int rows, int cols, int ld,
