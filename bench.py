@@ -44,6 +44,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--fp64-split-steps", type=int, default=40)
     ap.add_argument("--chains", type=int, default=8192)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -204,8 +205,19 @@ def phase_rooflines(inst, n_chains, timing, precision, peaks):
     """Achieved vs peak for each phase of the timed region (per launch)."""
     d, m, C = inst.d, inst.m, n_chains
     mixed = precision == "mixed"
+    split = precision == "fp64_split"
     esz = 4 if mixed else 8
     out = {}
+
+    def slice_pairs(bits):
+        # exact split: K (K + 1) / 2 bf16 slice products of w-bit slices,
+        # (2^w - 1)^2 d <= 2^24, K = ceil(bits / w)
+        w = 8
+        while w > 1 and (2 ** w - 1) ** 2 * d > 2 ** 24:
+            w -= 1
+        K = min(-(-bits // w), 12)
+        return K * (K + 1) / 2
+
     steps = timing.get("draw", {}).get("launches", 0)
     for phase, t in timing.items():
         if t["launches"] == 0 or t["ms"] <= 0:
@@ -223,19 +235,21 @@ def phase_rooflines(inst, n_chains, timing, precision, peaks):
                 peak = peaks["bf16_tflops_sustained"]
                 out[phase] = dict(bound="tensor", unit="TFLOP/s", achieved=flops / ms / 1e9,
                                   peak=peak, work_per_launch=flops, useful_flops=flops / 3)
+            elif split:
+                # FP64 products from 56-bit splits: the slice products issued
+                flops = slice_pairs(56) * 2.0 * m * d * C
+                out[phase] = dict(bound="tensor", unit="TFLOP/s", achieved=flops / ms / 1e9,
+                                  peak=peaks["bf16_tflops_sustained"], work_per_launch=flops,
+                                  useful_flops=2.0 * m * d * C)
             else:
                 flops = 2.0 * m * d * C
                 out[phase] = dict(bound="fp64", unit="TFLOP/s", achieved=flops / ms / 1e9,
                                   peak=FP64_TFLOPS_MEASURED, work_per_launch=flops)
         elif phase == "refresh":
-            if mixed:
-                # exact split: K (K + 1) / 2 bf16 slice products of w-bit slices,
-                # (2^w - 1)^2 d <= 2^24, K = ceil(35 / w) (K = 5 at d = 1000)
-                w = 8
-                while w > 1 and (2 ** w - 1) ** 2 * d > 2 ** 24:
-                    w -= 1
-                K = min(-(-35 // w), 7)
-                flops = K * (K + 1) / 2 * 2.0 * m * d * C
+            if mixed or split:
+                # exact split (35 bits mixed, 56 bits for the FP64 form; K = 5
+                # and 8 slices per operand at d = 1000)
+                flops = slice_pairs(35 if mixed else 56) * 2.0 * m * d * C
                 out[phase] = dict(bound="tensor", unit="TFLOP/s", achieved=flops / ms / 1e9,
                                   peak=peaks["bf16_tflops_sustained"], work_per_launch=flops,
                                   useful_flops=2.0 * m * d * C)
@@ -266,7 +280,8 @@ def time_form(ess, torch, inst, precision, n_chains, steps, warmup, seed, world,
     (refresh periods replayed from CUDA graphs), timed by CUDA events; then a
     second pass with per-phase events (plain launches) for the phase table."""
     prec = ess.ESS_PREC_MIXED if precision == "mixed" else ess.ESS_PREC_FP64
-    s = ess.Sampler(inst.A, inst.b, precision=prec)
+    cfg = {"fp64_products": ess.ESS_PRODUCTS_SPLIT} if precision == "fp64_split" else {}
+    s = ess.Sampler(inst.A, inst.b, precision=prec, **cfg)
     stream = torch.cuda.Stream()
     x0 = torch.as_tensor(inst.X0[0], dtype=torch.float64)
     X = x0.to("cuda").repeat(n_chains, 1).contiguous()
@@ -433,7 +448,8 @@ def time_configs(ess, torch, workloads, peaks, seed):
                     4096, (64, 3)))
     for name, inst, C, (st_mixed, st_fp64) in singles:
         entry = {}
-        for form, steps in (("mixed", st_mixed), ("fp64", st_fp64)):
+        for form, steps in (("mixed", st_mixed), ("fp64", st_fp64),
+                            ("fp64_split", max(st_fp64, min(st_mixed, 40)))):
             ms, timing, stats, _, lc = time_form(ess, torch, inst, form, C, steps, 3, seed, 1, 0)
             ph = phase_rooflines(inst, C, timing, form, peaks)
             dom = max(ph, key=lambda k: ph[k]["share"]) if ph else None
@@ -556,6 +572,10 @@ def main():
         ms64, timing64, stats64, _, _ = time_form(ess, torch, inst, "fp64", C, args.fp64_steps,
                                                   3, seed, world, rank, None)
         value64 = job_throughput(world, C, args.fp64_steps, ms64)
+        ms64s, timing64s, stats64s, _, _ = time_form(ess, torch, inst, "fp64_split", C,
+                                                     args.fp64_split_steps, 3, seed, world,
+                                                     rank, None)
+        value64s = job_throughput(world, C, args.fp64_split_steps, ms64s)
 
     if rank != 0:
         barrier(world)
@@ -563,6 +583,7 @@ def main():
 
     roof = phase_rooflines(inst, C, timing, "mixed", peaks)
     roof64 = phase_rooflines(inst, C, timing64, "fp64", peaks) if timing64 else {}
+    roof64s = phase_rooflines(inst, C, timing64s, "fp64_split", peaks) if timing64 else {}
     dominant = max(roof, key=lambda k: roof[k]["share"])
     dom = roof[dominant]
     kernel_src = {"gemm": ("k_gemm_tc.cu",),
@@ -599,6 +620,12 @@ def main():
             "value": value64, "unit": UNIT, "steps": args.fp64_steps,
             "ms_per_step": ms64 / args.fp64_steps, "dtype": "f64",
             "phases": roof64, "stats": stats64},
+        # the FP64 form with q = A nu and p = A x from exact 56-bit splits on the
+        # tensor cores (FP64-class products, ess_config.fp64_products = 1)
+        "fp64_split": None if args.mixed_only else {
+            "value": value64s, "unit": UNIT, "steps": args.fp64_split_steps,
+            "ms_per_step": ms64s / args.fp64_split_steps, "dtype": "f64 (products: bf16 slices)",
+            "phases": roof64s, "stats": stats64s},
         "roofline": roofline,
         "phases": roof,
         "e2e": e2e,
