@@ -177,32 +177,15 @@ __device__ __forceinline__ void root_pseudo_angles(float p, float q, float b, fl
   pb = pseudo_angle(bx, by, __fdividef(1.f, fabsf(bx) + fabsf(by)));
 }
 
-// Row classes of the prune (FP64 chains): the no-root and near-tangent
-// decisions are the ones roots_dp takes; rows whose arc would wrap through 0
-// (boundary points) are always kept.  b64 points at the exact b_i; nonfinite
-// is set when p or q is NaN or infinite.
-__device__ __forceinline__ int classify_phi(double p, double q, double b, const double* b64,
-                                            double tlo, double thi, float& pa, float& pb,
-                                            bool& infeasible, bool& nonfinite) {
-  (void)b64;
-  (void)thi;
-  const double r2 = p * p + q * q;
-  nonfinite |= !(r2 <= DBL_MAX);
-  const double r = sqrt(r2);
-  if (r == 0.0) {
-    infeasible = b < 0.0;
-    return kRowNone;
-  }
-  const double rd = b / r;
-  if (rd >= 1.0) return kRowNone;
-  if (fabs(rd) > tlo || r < 1e-30 || r > 1e30) return kRowKeep;
-  const float pf = (float)p, qf = (float)q, bf = (float)b;
-  const float r2f = fmaf(pf, pf, qf * qf);
-  const float w2 = fmaf(-bf, bf, r2f);
-  if (!(w2 > 0.f)) return kRowKeep;
-  root_pseudo_angles(pf, qf, bf, w2 * rsqrtf(w2), pa, pb);
-  return pa < pb ? kRowApprox : kRowKeep;
-}
+// Row classes of the prune for FP64 chains, taken in FP32 (GB300's FP64 pipe
+// is narrow): the float classification of the rounded p, q, b keeps every row
+// whose no-root or near-tangent decision lies within its slack, and the rows
+// it cannot classify (r = 0 or non-finite in float: underflow or overflow of
+// the rounding) are kept too; every kept row gets the exact FP64 roots.
+// Non-finite doubles are detected from their exponent bits.
+__device__ __forceinline__ int classify_phi_d(double p, double q, double b, float tlo2,
+                                              float thi2, float& pa, float& pb,
+                                              bool& nonfinite);
 
 // Row classes of the prune (float chains), branch-free so that the rows of a
 // batch interleave.  The no-root and near-tangent decisions compare b^2 with
@@ -227,6 +210,16 @@ __device__ __forceinline__ int classify_phi_nb(float p, float q, float b, float 
   cls = b >= 0.f && b2 >= thi2 * r2 ? kRowNone : cls;    // b / r >= 1 + thresh (with slack)
   zero = r2 == 0.0f;
   return zero ? kRowNone : cls;
+}
+
+__device__ __forceinline__ int classify_phi_d(double p, double q, double b, float tlo2,
+                                              float thi2, float& pa, float& pb,
+                                              bool& nonfinite) {
+  nonfinite |= (__double2hiint(p) & 0x7FF00000) == 0x7FF00000 ||
+               (__double2hiint(q) & 0x7FF00000) == 0x7FF00000;
+  bool zero = false, nf = false;
+  const int cls = classify_phi_nb((float)p, (float)q, (float)b, tlo2, thi2, pa, pb, zero, nf);
+  return zero || nf ? kRowKeep : cls;
 }
 
 }  // namespace chainmath

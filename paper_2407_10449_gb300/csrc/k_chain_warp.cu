@@ -213,7 +213,7 @@ chain_warp_kernel(ChainParams<T> prm) {
           if constexpr (sizeof(T) == 4)
             cls = classify_phi_nb(pv[k], qv[k], bv[k], tlo2, thi2, pa, pb, inf_row, nf);
           else
-            cls = classify_phi(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb, inf_row, nf);
+            cls = classify_phi_d(pv[k], qv[k], bv[k], tlo2, thi2, pa, pb, nf);
           if (cls == kRowApprox) atomicMax(&bsub[bslot(pbucket(pa) + 2)], __float_as_uint(pb));
         }
       }
@@ -301,10 +301,9 @@ chain_warp_kernel(ChainParams<T> prm) {
           unsigned code = 0u;
           float pa = 0.f, pb = 0.f;
           if (i < m) {
-            bool inf_row = false;
-            const int cls = classify_phi(pv[k], qv[k], bv[k], v.b64 + i, tlo, thi, pa, pb,
-                                         inf_row, nonfinite);
-            infeasible |= inf_row;
+            // FP32 classification (rows it cannot decide are kept; r = 0 rows
+            // get their infeasibility test from the exact roots)
+            const int cls = classify_phi_d(pv[k], qv[k], bv[k], tlo2, thi2, pa, pb, nonfinite);
             if (cls == kRowKeep) {
               cand = true;
               code = 0x80000000u | (unsigned)i;
