@@ -1877,9 +1877,12 @@ cudaError_t exact_product(TcGemmPlan* plan, const TI* X, int ldx, int n_chains,
   a.n_cols = plan->m;
   a.kblocks = (plan->d + BK - 1) / BK;
   // slice pairs (x slice l, A slice k), k + l <= K + 1 (1-based), grouped into
-  // rounds of at most 8 pairs whose x and A tiles (each loaded once per round)
-  // fit one stage; within a round the pairs of one x tile with A tiles that
-  // sit next to each other in the stage share one MMA (N <= 256)
+  // rounds of at most kMaxPairs pairs whose x and A tiles (each loaded once per
+  // round) fit one stage; within a round the pairs of one x tile with A tiles
+  // that sit next to each other in the stage share one MMA (N <= 256).  The
+  // pairs are taken row by row (x slice by x slice) or in 2 x 2 blocks of
+  // (x, A) slices, whichever loads fewer tile bytes per K block.
+  constexpr int kMaxPairs = 8;
   constexpr uint32_t kXTile = (uint32_t)BM * BK * 2, kATile = (uint32_t)kRefreshBN * BK * 2;
   static_assert(kXTile + kATile <= kRefreshStage, "one slice pair must fit a stage");
   auto pos_of = [](const unsigned char* arr, int n, int v) {
@@ -1887,22 +1890,28 @@ cudaError_t exact_product(TcGemmPlan* plan, const TI* X, int ldx, int n_chains,
       if (arr[i] == (unsigned char)v) return i;
     return -1;
   };
-  int nr = 0;
-  auto open_round = [&]() {
-    std::memset(&a.round[nr], 0, sizeof(RefreshRound));
-    ++nr;
-  };
-  open_round();
-  for (int l = 1; l <= K; ++l)
-    for (int k = 1; k + l <= K + 1; ++k) {
-      RefreshRound* R = &a.round[nr - 1];
+  // fills t.round / t.nrounds; returns the tile bytes of all rounds per K
+  // block, or 0 if the pairs need more than kMaxRounds rounds
+  auto build = [&](TcArgs& t, bool blocks) -> uint32_t {
+    int nr = 0;
+    bool overflow = false;
+    auto open_round = [&]() {
+      std::memset(&t.round[nr], 0, sizeof(RefreshRound));
+      ++nr;
+    };
+    auto add = [&](int l, int k) {
+      if (overflow) return;
+      RefreshRound* R = &t.round[nr - 1];
       int xi = pos_of(R->x, R->nx, l - 1), ai = pos_of(R->a, R->na, k - 1);
       const uint32_t bytes = (uint32_t)(R->nx + (xi < 0 ? 1 : 0)) * kXTile +
                              (uint32_t)(R->na + (ai < 0 ? 1 : 0)) * kATile;
-      if (R->npairs == 8 || bytes > kRefreshStage) {
-        if (nr == kMaxRounds) return cudaErrorInvalidValue;
+      if (R->npairs == kMaxPairs || bytes > kRefreshStage) {
+        if (nr == kMaxRounds) {
+          overflow = true;
+          return;
+        }
         open_round();
-        R = &a.round[nr - 1];
+        R = &t.round[nr - 1];
         xi = ai = -1;
       }
       if (xi < 0) {
@@ -1925,12 +1934,36 @@ cudaError_t exact_product(TcGemmPlan* plan, const TI* X, int ldx, int n_chains,
         G->na = 1;
         G->col = (unsigned char)col;
       }
+    };
+    open_round();
+    if (blocks) {
+      for (int lb = 1; lb <= K; lb += 2)
+        for (int kb = 1; kb <= K; kb += 2)
+          for (int l = lb; l <= lb + 1 && l <= K; ++l)
+            for (int k = kb; k <= kb + 1 && k <= K; ++k)
+              if (k + l <= K + 1) add(l, k);
+    } else {
+      for (int l = 1; l <= K; ++l)
+        for (int k = 1; k + l <= K + 1; ++k) add(l, k);
     }
-  // every round's tiles fit a stage (the copies of a stage land inside it)
-  for (int r = 0; r < nr; ++r)
-    if ((uint32_t)a.round[r].nx * kXTile + (uint32_t)a.round[r].na * kATile > kRefreshStage)
-      return cudaErrorInvalidValue;
-  a.nrounds = nr;
+    if (overflow) return 0u;
+    // every round's tiles fit a stage (the copies of a stage land inside it)
+    uint32_t total = 0;
+    for (int r = 0; r < nr; ++r) {
+      const uint32_t b = (uint32_t)t.round[r].nx * kXTile + (uint32_t)t.round[r].na * kATile;
+      if (b > kRefreshStage) return 0u;
+      total += b;
+    }
+    t.nrounds = nr;
+    return total;
+  };
+  {
+    TcArgs alt = a;
+    const uint32_t rows_bytes = build(a, false);
+    const uint32_t block_bytes = build(alt, true);
+    if (rows_bytes == 0u && block_bytes == 0u) return cudaErrorInvalidValue;
+    if (block_bytes != 0u && (rows_bytes == 0u || block_bytes < rows_bytes)) a = alt;
+  }
   a.ngroups = 0;
   a.row_scale = row_scale;
   a.col_scale = plan->col_scale;

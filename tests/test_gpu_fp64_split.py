@@ -61,12 +61,15 @@ def products(A, X, NU):
 
 
 @pytest.mark.parametrize("n,m,d", [(1, 20, 10), (130, 300, 137), (64, 2001, 1000),
-                                   (33, 500, 2000)])
+                                   (33, 500, 2000), (300, 130, 137), (513, 2001, 1000),
+                                   (260, 200, 2000)])
 def test_split_products_exact_inputs(n, m, d):
     """Entries on a 2^-12 grid below 8 in magnitude: every product and every
     sum of up to 2000 of them is exact in double, so the reference is the exact
     value; the 56-bit slices hold such entries exactly, so only the final
-    rounding of the (hi, lo) float pair to double remains."""
+    rounding of the (hi, lo) float pair to double remains.  The sizes leave
+    ragged chain and constraint tails; at d = 2000 the slices are 6 bits wide
+    (10 per operand, 55 slice pairs)."""
     rng = np.random.default_rng(n + 5 * m + d)
     grid = lambda shape: np.round(rng.uniform(-7.9, 7.9, size=shape) * 4096) / 4096
     A, X, NU = grid((m, d)), grid((n, d)), grid((n, d))

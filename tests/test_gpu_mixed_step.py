@@ -34,7 +34,8 @@ def q_error_bound(A, NU):
 
 
 @pytest.mark.parametrize("n,m,d", [(1, 20, 10), (130, 300, 137), (256, 448, 64),
-                                   (200, 1000, 333), (128, 2000, 1000), (77, 4100, 50)])
+                                   (200, 1000, 333), (128, 2000, 1000), (77, 4100, 50),
+                                   (300, 130, 137), (513, 2001, 1000)])
 def test_products_tensor_core_gemm(n, m, d):
     """q = A nu from the tcgen05 FP16x3 GEMM vs FP64, and p = A x (refresh) vs FP64."""
     rng = np.random.default_rng(n * 7 + m)
