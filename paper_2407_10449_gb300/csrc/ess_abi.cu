@@ -90,6 +90,10 @@ struct ess_state {
   int p_fresh_t = -1;      // step index at which p was last recomputed from x
   long long host_steps = 0;  // chain-steps enqueued since the last stats reset
   __half* NU_h[2] = {nullptr, nullptr};  // scaled fp16 split of nu (tensor-core q)
+  // second nu buffers: in a replayed refresh period the draw of step j + 1
+  // runs on a low-priority side stream while step j's GEMM runs
+  void* NU_alt = nullptr;
+  __half* NU_h_alt[2] = {nullptr, nullptr};
   float* nu_unscale = nullptr;           // 1 / t_c of caller-supplied nu (scanned per chain)
   __nv_bfloat16* x_slices = nullptr;  // refresh: fixed-point slices of the states
   float* row_scale = nullptr;         // refresh: per-chain power-of-two scales
@@ -100,7 +104,9 @@ struct ess_state {
   // CUDA graphs of one refresh period (refresh + refresh_k steps), keyed by
   // chain count, seed and the p buffer the period starts from
   bool use_graphs = true;
-  cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_stream = nullptr;   // capture stream (highest priority)
+  cudaStream_t side_stream = nullptr;  // capture side stream of the draws (lowest priority)
+  cudaEvent_t ev_drawn = nullptr, ev_done = nullptr;
   unsigned* t_dev = nullptr;  // step index base of a replayed period
   struct GraphEntry {
     int n;
@@ -192,10 +198,12 @@ void free_work(ess_state* s) {
   dev_free(s->ovf);
   if (s->Q) cudaFree(s->Q);
   if (s->NU) cudaFree(s->NU);
-  s->P = s->Q = s->NU = nullptr;
+  if (s->NU_alt) cudaFree(s->NU_alt);
+  s->P = s->Q = s->NU = s->NU_alt = nullptr;
   dev_free(s->Xw);
   dev_free(s->Xd);
   for (auto& p : s->NU_h) dev_free(p);
+  for (auto& p : s->NU_h_alt) dev_free(p);
   dev_free(s->nu_unscale);
   dev_free(s->x_slices);
   dev_free(s->row_scale);
@@ -213,9 +221,11 @@ ess_status ensure_capacity(ess_state* s, int n) {
   ESS_CUDA(dev_alloc(&s->ovf, (size_t)n + 1));
   ESS_CUDA(cudaMalloc(&s->Q, (size_t)n * s->m * e));
   ESS_CUDA(cudaMalloc(&s->NU, (size_t)n * s->d * e));
+  ESS_CUDA(cudaMalloc(&s->NU_alt, (size_t)n * s->d * e));
   if (mixed(s)) {
     ESS_CUDA(dev_alloc(&s->Xw, (size_t)n * s->d));
-    for (auto& p : s->NU_h) {
+    for (int k = 0; k < 4; ++k) {
+      __half*& p = k < 2 ? s->NU_h[k] : s->NU_h_alt[k - 2];
       ESS_CUDA(dev_alloc(&p, (size_t)n * s->ld16));
       // the padding columns d .. ld16 - 1 stay zero
       ESS_CUDA(cudaMemset(p, 0, (size_t)n * s->ld16 * sizeof(__half)));
@@ -518,20 +528,32 @@ ess_status autotune(ess_state* s, int t0, cudaStream_t st) {
 
 namespace {
 
+// nu of step t (+ *t_dev when t_dev is set) for every loaded chain into nu
+// (and its fp16 split nu_h, mixed form).
+template <typename T>
+ess_status draw_step_nu(ess_state* s, uint64_t seed, uint32_t t, const unsigned* t_dev, void* nu,
+                        __half* const nu_h[2], cudaStream_t st) {
+  const int n = s->n_loaded, d = s->d;
+  if constexpr (sizeof(T) == 4)
+    ESS_CUDA(ess::launch_draw_nu_f32(static_cast<float*>(nu), d, nu_h, s->ld16, n, d, seed, t,
+                                     0u, 0u, st, t_dev));
+  else
+    ESS_CUDA(ess::launch_draw_nu_f64(static_cast<double*>(nu), n, d, d, seed, t, 0u, 0u, st,
+                                     t_dev));
+  return ESS_OK;
+}
+
 // One step of every loaded chain at step index t (+ *t_dev when t_dev is
-// set): draw nu, q = A nu, chain step (p buffers swapped).
+// set): draw nu (unless it is already in s->NU), q = A nu, chain step (p
+// buffers swapped).
 template <typename T>
 ess_status step_one(ess_state* s, uint64_t seed, uint32_t t, const unsigned* t_dev, T* samples,
-                    long long sample_stride, cudaStream_t st) {
-  const int n = s->n_loaded, d = s->d;
-  {
+                    long long sample_stride, cudaStream_t st, bool draw = true) {
+  const int n = s->n_loaded;
+  if (draw) {
     PhaseScope ps(s, st, ESS_PHASE_DRAW);
-    if constexpr (sizeof(T) == 4)
-      ESS_CUDA(ess::launch_draw_nu_f32(static_cast<float*>(s->NU), d, s->NU_h, s->ld16, n, d,
-                                       seed, t, 0u, 0u, st, t_dev));
-    else
-      ESS_CUDA(ess::launch_draw_nu_f64(static_cast<double*>(s->NU), n, d, d, seed, t, 0u, 0u, st,
-                                       t_dev));
+    ess_status rc = draw_step_nu<T>(s, seed, t, t_dev, s->NU, s->NU_h, st);
+    if (rc != ESS_OK) return rc;
   }
   {
     PhaseScope ps(s, st, ESS_PHASE_GEMM);
@@ -559,20 +581,57 @@ ess_status graph_period(ess_state* s, uint64_t seed, cudaStream_t st) {
   for (auto& g : s->graphs)
     if (g.n == s->n_loaded && g.seed == seed && g.p_first == s->P) hit = &g;
   if (!hit) {
-    if (!s->cap_stream) ESS_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+    if (!s->cap_stream) {
+      // the steps at the highest priority, the draws ahead of them at the
+      // lowest: a draw fills the SMs' room beside the GEMM instead of
+      // delaying it
+      int least = 0, greatest = 0;
+      ESS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      ESS_CUDA(cudaStreamCreateWithPriority(&s->cap_stream, cudaStreamNonBlocking, greatest));
+      ESS_CUDA(cudaStreamCreateWithPriority(&s->side_stream, cudaStreamNonBlocking, least));
+      ESS_CUDA(cudaEventCreateWithFlags(&s->ev_drawn, cudaEventDisableTiming));
+      ESS_CUDA(cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming));
+    }
     void* p_first = s->P;
     const bool timing = s->timing;
     s->timing = false;
-    ESS_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-    ess_status rc = refresh_p(s, s->n_loaded, chain_states(s), true, false, s->cap_stream);
-    for (int j = 0; j < k && rc == ESS_OK; ++j)
-      rc = step_one<T>(s, seed, (uint32_t)j, s->t_dev, nullptr, 0, s->cap_stream);
+    cudaStream_t cs = s->cap_stream, ss = s->side_stream;
+    ESS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    // Step j's nu is drawn on the side stream into the buffer pair that step
+    // j - 1 does not use: draw 0 beside the refresh, draw j + 1 beside step j
+    // once step j - 1 (the last reader of that pair) is done.  Every side
+    // operation is joined back before the step that reads it, and refresh_k
+    // is even, so the period leaves the nu buffers where it found them.
+    ess_status rc = ESS_OK;
+    auto cap_ok = [&](cudaError_t e, const char* what) {
+      if (rc == ESS_OK && e != cudaSuccess) rc = cuda_fail(e, what);
+      return rc == ESS_OK;
+    };
+    if (cap_ok(cudaEventRecord(s->ev_done, cs), "graph fork") &&
+        cap_ok(cudaStreamWaitEvent(ss, s->ev_done, 0), "graph fork")) {
+      rc = draw_step_nu<T>(s, seed, 0u, s->t_dev, s->NU, s->NU_h, ss);
+      if (rc == ESS_OK) cap_ok(cudaEventRecord(s->ev_drawn, ss), "graph draw");
+    }
+    if (rc == ESS_OK) rc = refresh_p(s, s->n_loaded, chain_states(s), true, false, cs);
+    for (int j = 0; j < k && rc == ESS_OK; ++j) {
+      if (!cap_ok(cudaStreamWaitEvent(cs, s->ev_drawn, 0), "graph join")) break;
+      if (j + 1 < k) {
+        if (j > 0 && !cap_ok(cudaStreamWaitEvent(ss, s->ev_done, 0), "graph fork")) break;
+        rc = draw_step_nu<T>(s, seed, (uint32_t)(j + 1), s->t_dev, s->NU_alt, s->NU_h_alt, ss);
+        if (rc != ESS_OK || !cap_ok(cudaEventRecord(s->ev_drawn, ss), "graph draw")) break;
+      }
+      rc = step_one<T>(s, seed, (uint32_t)j, s->t_dev, nullptr, 0, cs, false);
+      if (rc != ESS_OK || !cap_ok(cudaEventRecord(s->ev_done, cs), "graph step")) break;
+      std::swap(s->NU, s->NU_alt);
+      std::swap(s->NU_h[0], s->NU_h_alt[0]);
+      std::swap(s->NU_h[1], s->NU_h_alt[1]);
+    }
     if (rc == ESS_OK) {
-      cudaError_t e = ess::launch_advance_t(s->t_dev, (unsigned)k, s->cap_stream);
+      cudaError_t e = ess::launch_advance_t(s->t_dev, (unsigned)k, cs);
       if (e != cudaSuccess) rc = cuda_fail(e, "advance step index");
     }
     cudaGraph_t graph = nullptr;
-    cudaError_t ec = cudaStreamEndCapture(s->cap_stream, &graph);
+    cudaError_t ec = cudaStreamEndCapture(cs, &graph);
     s->timing = timing;
     if (rc != ESS_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -580,7 +639,7 @@ ess_status graph_period(ess_state* s, uint64_t seed, cudaStream_t st) {
     }
     if (ec != cudaSuccess) return cuda_fail(ec, "graph capture");
     cudaGraphExec_t exec = nullptr;
-    ec = cudaGraphInstantiate(&exec, graph, 0);
+    ec = cudaGraphInstantiateWithFlags(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     if (ec != cudaSuccess) return cuda_fail(ec, "graph instantiate");
     // refresh_k is even, so the period leaves the p buffers where it found them
@@ -739,6 +798,9 @@ void ess_destroy(ess_state* s) {
   s->tc_plan = nullptr;
   dev_free(s->t_dev);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->side_stream) cudaStreamDestroy(s->side_stream);
+  if (s->ev_drawn) cudaEventDestroy(s->ev_drawn);
+  if (s->ev_done) cudaEventDestroy(s->ev_done);
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   dev_free(s->host_x);
   for (int k = 0; k < 2; ++k) {
