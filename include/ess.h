@@ -188,6 +188,12 @@ ess_status ess_run(ess_state *state, double *X, int n_chains, int t0, int n_iter
  *   ess_chains_step  enqueues n_iter steps of the loaded chains on the stream
  *                    and returns without waiting (samples as in ess_run).
  *                    Device-side errors surface in the next ess_chains_get.
+ *                    Unless per-phase timing is on, the steps run on two
+ *                    internal streams of the state (the draw of step t + 1
+ *                    beside step t), forked from the stream at the call and
+ *                    joined back into it before the call returns: work the
+ *                    caller enqueues on the stream afterwards runs after
+ *                    them, as with plain launches.
  *   ess_chains_get   copies the current states to X (device doubles, may be
  *                    NULL) and reports device-side errors.  Synchronous.
  * ess_step_with_draws and ess_products reuse the work buffers and unload the

@@ -104,9 +104,10 @@ struct ess_state {
   // CUDA graphs of one refresh period (refresh + refresh_k steps), keyed by
   // chain count, seed and the p buffer the period starts from
   bool use_graphs = true;
-  cudaStream_t cap_stream = nullptr;   // capture stream (highest priority)
-  cudaStream_t side_stream = nullptr;  // capture side stream of the draws (lowest priority)
-  cudaEvent_t ev_drawn = nullptr, ev_done = nullptr;
+  cudaStream_t cap_stream = nullptr;   // graph capture: the steps (highest priority)
+  cudaStream_t work_stream = nullptr;  // plain launches: the steps (highest priority)
+  cudaStream_t side_stream = nullptr;  // the draws one step ahead (lowest priority)
+  cudaEvent_t ev_drawn = nullptr, ev_done = nullptr, ev_fork = nullptr, ev_join = nullptr;
   unsigned* t_dev = nullptr;  // step index base of a replayed period
   struct GraphEntry {
     int n;
@@ -572,6 +573,21 @@ ess_status step_one(ess_state* s, uint64_t seed, uint32_t t, const unsigned* t_d
   return launch_step<T>(s, p, st);
 }
 
+// The internal streams and events of the draws made one step ahead: the steps
+// at the highest priority, the draws at the lowest, so that a draw fills the
+// SMs' room beside the q GEMM instead of delaying it.
+ess_status ensure_streams(ess_state* s) {
+  if (s->cap_stream) return ESS_OK;
+  int least = 0, greatest = 0;
+  ESS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  ESS_CUDA(cudaStreamCreateWithPriority(&s->cap_stream, cudaStreamNonBlocking, greatest));
+  ESS_CUDA(cudaStreamCreateWithPriority(&s->work_stream, cudaStreamNonBlocking, greatest));
+  ESS_CUDA(cudaStreamCreateWithPriority(&s->side_stream, cudaStreamNonBlocking, least));
+  for (cudaEvent_t* e : {&s->ev_drawn, &s->ev_done, &s->ev_fork, &s->ev_join})
+    ESS_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  return ESS_OK;
+}
+
 // Replays (capturing on first use) one refresh period -- refresh, then
 // refresh_k steps -- starting at the step index held in *t_dev.
 template <typename T>
@@ -581,17 +597,8 @@ ess_status graph_period(ess_state* s, uint64_t seed, cudaStream_t st) {
   for (auto& g : s->graphs)
     if (g.n == s->n_loaded && g.seed == seed && g.p_first == s->P) hit = &g;
   if (!hit) {
-    if (!s->cap_stream) {
-      // the steps at the highest priority, the draws ahead of them at the
-      // lowest: a draw fills the SMs' room beside the GEMM instead of
-      // delaying it
-      int least = 0, greatest = 0;
-      ESS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-      ESS_CUDA(cudaStreamCreateWithPriority(&s->cap_stream, cudaStreamNonBlocking, greatest));
-      ESS_CUDA(cudaStreamCreateWithPriority(&s->side_stream, cudaStreamNonBlocking, least));
-      ESS_CUDA(cudaEventCreateWithFlags(&s->ev_drawn, cudaEventDisableTiming));
-      ESS_CUDA(cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming));
-    }
+    ess_status rs = ensure_streams(s);
+    if (rs != ESS_OK) return rs;
     void* p_first = s->P;
     const bool timing = s->timing;
     s->timing = false;
@@ -799,8 +806,9 @@ void ess_destroy(ess_state* s) {
   dev_free(s->t_dev);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   if (s->side_stream) cudaStreamDestroy(s->side_stream);
-  if (s->ev_drawn) cudaEventDestroy(s->ev_drawn);
-  if (s->ev_done) cudaEventDestroy(s->ev_done);
+  if (s->work_stream) cudaStreamDestroy(s->work_stream);
+  for (cudaEvent_t e : {s->ev_drawn, s->ev_done, s->ev_fork, s->ev_join})
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   dev_free(s->host_x);
   for (int k = 0; k < 2; ++k) {
@@ -861,26 +869,30 @@ ess_status ess_get_tuning(const ess_state* s, int* q_width, int* sort_threads) {
   return ESS_OK;
 }
 
-ess_status ess_chains_step(ess_state* s, int n_iter, uint64_t seed, void* samples,
-                           int record_every, void* cuda_stream) {
-  g_err.clear();
-  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
-  if (n_iter < 0 || record_every < 0) return fail(ESS_ERR_ARG, "negative size");
-  if (s->n_loaded < 1) return fail(ESS_ERR_ARG, "no chains loaded (call ess_chains_init)");
-  if (record_every > 0 && !samples) return fail(ESS_ERR_ARG, "samples is NULL");
-  if ((long long)s->t_next + n_iter > 0x7fffffffLL) return fail(ESS_ERR_ARG, "step index overflow");
-  DeviceGuard g(s->device);
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+namespace {
+
+// The steps of ess_chains_step on stream st.  With `ahead`, each plain step
+// t that another plain step follows draws nu of step t + 1 on the side
+// stream into the second nu buffers, once step t - 1 (their last reader) is
+// done, so that the draw runs beside step t; graph-replayed periods do the
+// same inside the graph.
+ess_status chains_step_on(ess_state* s, int n_iter, uint64_t seed, void* samples,
+                          int record_every, cudaStream_t st, bool ahead) {
   const int n = s->n_loaded, d = s->d;
   const int n_rec = record_every > 0 ? n_iter / record_every : 0;
   const int k = s->cfg.refresh_k;
   // whole refresh periods replay from a CUDA graph (not with sample recording
   // or per-phase timing, whose pointers and events change from step to step)
   const bool graphs_ok = s->use_graphs && !s->timing && record_every == 0 && k % 2 == 0;
+  auto graph_at = [&](int it_) {
+    const int t_ = s->t_next + it_;
+    return graphs_ok && t_ % k == 0 && t_ != s->p_fresh_t && n_iter - it_ >= k;
+  };
+  bool drawn = false;  // s->NU holds nu of step t, drawn on the side stream
   int it = 0;
   while (it < n_iter) {
     const int t = s->t_next + it;
-    if (graphs_ok && t % k == 0 && t != s->p_fresh_t && n_iter - it >= k) {
+    if (graph_at(it)) {
       ESS_CUDA(ess::launch_set_t(s->t_dev, (unsigned)t, st));
       while (n_iter - it >= k) {
         ess_status rc = mixed(s) ? graph_period<float>(s, seed, st) : graph_period<double>(s, seed, st);
@@ -889,6 +901,19 @@ ess_status ess_chains_step(ess_state* s, int n_iter, uint64_t seed, void* sample
       }
       s->p_fresh_t = s->t_next + it - k;
       continue;
+    }
+    const bool next = ahead && it + 1 < n_iter && !graph_at(it + 1);
+    if (next) {
+      ESS_CUDA(cudaEventRecord(s->ev_done, st));  // step t - 1 is done here
+      ESS_CUDA(cudaStreamWaitEvent(s->side_stream, s->ev_done, 0));
+      ess_status rc = mixed(s)
+          ? draw_step_nu<float>(s, seed, (uint32_t)(t + 1), nullptr, s->NU_alt, s->NU_h_alt,
+                                s->side_stream)
+          : draw_step_nu<double>(s, seed, (uint32_t)(t + 1), nullptr, s->NU_alt, s->NU_h_alt,
+                                 s->side_stream);
+      if (rc != ESS_OK) return rc;
+      s->phase_launches[ESS_PHASE_DRAW] += 1;
+      ESS_CUDA(cudaEventRecord(s->ev_drawn, s->side_stream));
     }
     if (t % k == 0 && t != s->p_fresh_t) {
       PhaseScope ps(s, st, ESS_PHASE_REFRESH);
@@ -902,15 +927,57 @@ ess_status ess_chains_step(ess_state* s, int n_iter, uint64_t seed, void* sample
     const long long stride = (long long)n_rec * d;
     ess_status rc = mixed(s)
         ? step_one<float>(s, seed, (uint32_t)t, nullptr,
-                          rec ? static_cast<float*>(samples) + rec_off : nullptr, stride, st)
+                          rec ? static_cast<float*>(samples) + rec_off : nullptr, stride, st,
+                          !drawn)
         : step_one<double>(s, seed, (uint32_t)t, nullptr,
-                           rec ? static_cast<double*>(samples) + rec_off : nullptr, stride, st);
+                           rec ? static_cast<double*>(samples) + rec_off : nullptr, stride, st,
+                           !drawn);
     if (rc != ESS_OK) return rc;
+    if (next) {
+      // step t + 1 reads the buffers just drawn, after the draw
+      std::swap(s->NU, s->NU_alt);
+      std::swap(s->NU_h[0], s->NU_h_alt[0]);
+      std::swap(s->NU_h[1], s->NU_h_alt[1]);
+      ESS_CUDA(cudaStreamWaitEvent(st, s->ev_drawn, 0));
+    }
+    drawn = next;
     ++it;
   }
   s->t_next += n_iter;
   s->host_steps += (long long)n * n_iter;
   return ESS_OK;
+}
+
+}  // namespace
+
+ess_status ess_chains_step(ess_state* s, int n_iter, uint64_t seed, void* samples,
+                           int record_every, void* cuda_stream) {
+  g_err.clear();
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  if (n_iter < 0 || record_every < 0) return fail(ESS_ERR_ARG, "negative size");
+  if (s->n_loaded < 1) return fail(ESS_ERR_ARG, "no chains loaded (call ess_chains_init)");
+  if (record_every > 0 && !samples) return fail(ESS_ERR_ARG, "samples is NULL");
+  if ((long long)s->t_next + n_iter > 0x7fffffffLL) return fail(ESS_ERR_ARG, "step index overflow");
+  DeviceGuard g(s->device);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // Without per-phase timing the steps run on the internal high-priority
+  // stream, forked from and joined back into the caller's stream (the join
+  // also covers every draw on the side stream, each of which a later step
+  // waited for).
+  const bool ahead = !s->timing && n_iter > 1;
+  if (!ahead) return chains_step_on(s, n_iter, seed, samples, record_every, st, false);
+  ess_status rc = ensure_streams(s);
+  if (rc != ESS_OK) return rc;
+  ESS_CUDA(cudaEventRecord(s->ev_fork, st));
+  ESS_CUDA(cudaStreamWaitEvent(s->work_stream, s->ev_fork, 0));
+  rc = chains_step_on(s, n_iter, seed, samples, record_every, s->work_stream, true);
+  // join even after an error: no internal work may outlive the call's stream order
+  cudaError_t e = cudaEventRecord(s->ev_join, s->work_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->ev_join, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_join, s->side_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->ev_join, 0);
+  if (e != cudaSuccess && rc == ESS_OK) rc = cuda_fail(e, "join internal streams");
+  return rc;
 }
 
 ess_status ess_set_graphs(ess_state* s, int enable) {

@@ -101,6 +101,27 @@ def test_graph_replay_is_bit_identical(form):
 
 
 @pytest.mark.parametrize("form", FORMS)
+def test_draws_ahead_are_bit_identical(form):
+    """nu of step t + 1 drawn on a side stream beside step t (plain launches
+    and replayed periods) gives the chains of strictly sequential launches
+    (per-phase timing on: every draw in line), bit for bit."""
+    inst = workloads.medium(n_chains=80)
+    out = []
+    for timing, graphs in ((True, False), (False, False), (False, True)):
+        s = ess.Sampler(inst.A, inst.b, precision=form, refresh_k=8)
+        try:
+            ess.ess_set_graphs(s.state, graphs)
+            ess.ess_set_timing(s.state, timing)
+            X = dev(inst.X0)
+            s.run(X, 37, seed=11, t0=5)
+            out.append(host(X))
+        finally:
+            s.close()
+    np.testing.assert_array_equal(out[0], out[1])
+    np.testing.assert_array_equal(out[0], out[2])
+
+
+@pytest.mark.parametrize("form", FORMS)
 def test_autotune_keeps_the_chains(form):
     """The autotuner times its candidates without moving any chain: a tuned
     run equals an untuned run with the same sort path (the q GEMM's tile
