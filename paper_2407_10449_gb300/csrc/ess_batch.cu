@@ -104,6 +104,7 @@ struct ess_batch {
   ess::TcBatchItem* titems = nullptr;  // mixed form: items of the tensor-core q GEMM
   int n_titems = 0, cap_titems = 0;
   CUtensorMap* tmaps = nullptr;  // mixed form: 4 operand maps per problem (A and nu splits)
+  CUtensorMap* tmaps_alt = nullptr;  // the same maps over the second nu splits
   int layout_version = 0;
   // work buffers (device)
   int cap_n = 0, cap_items = 0;
@@ -114,6 +115,9 @@ struct ess_batch {
   void* P2 = nullptr;
   void* Q = nullptr;
   __half* H[2] = {nullptr, nullptr};  // mixed form: fp16 splits of nu (rows of dpad)
+  // second nu buffers: the draw of step t + 1 runs beside step t
+  void* NU_alt = nullptr;
+  __half* H_alt[2] = {nullptr, nullptr};
   float* chain_unscale = nullptr;     // per chain 1 / t of caller-supplied nu
   long long cap_h = 0;
   double* P64 = nullptr;
@@ -125,7 +129,10 @@ struct ess_batch {
   long long host_steps = 0;
   // CUDA graphs of one refresh period, keyed by layout, seed and P parity
   bool use_graphs = true;
-  cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_stream = nullptr;   // graph capture: the steps (highest priority)
+  cudaStream_t work_stream = nullptr;  // plain launches: the steps (highest priority)
+  cudaStream_t side_stream = nullptr;  // the draws one step ahead (lowest priority)
+  cudaEvent_t ev_drawn = nullptr, ev_done = nullptr, ev_fork = nullptr, ev_join = nullptr;
   struct GraphEntry {
     int version;
     uint64_t seed;
@@ -197,15 +204,18 @@ void free_work(ess_batch* s) {
   bfree(s->titems);
   s->cap_titems = 0;
   if (s->tmaps) cudaFree(s->tmaps);
-  s->tmaps = nullptr;
+  if (s->tmaps_alt) cudaFree(s->tmaps_alt);
+  s->tmaps = s->tmaps_alt = nullptr;
   if (s->X) cudaFree(s->X);
   if (s->NU) cudaFree(s->NU);
+  if (s->NU_alt) cudaFree(s->NU_alt);
+  s->NU_alt = nullptr;
   if (s->P) cudaFree(s->P);
   if (s->P2) cudaFree(s->P2);
   if (s->Q) cudaFree(s->Q);
   s->X = s->NU = s->P = s->P2 = s->Q = nullptr;
-  bfree(s->H[0]);
-  bfree(s->H[1]);
+  for (auto& h : s->H) bfree(h);
+  for (auto& h : s->H_alt) bfree(h);
   bfree(s->chain_unscale);
   s->cap_h = 0;
   bfree(s->P64);
@@ -319,13 +329,15 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
     s->cap_titems = (int)titems.size();
     BESS_CUDA(cudaMalloc(&s->X, std::max<long long>(1, xo) * e));
     BESS_CUDA(cudaMalloc(&s->NU, std::max<long long>(1, xo) * e));
+    BESS_CUDA(cudaMalloc(&s->NU_alt, std::max<long long>(1, xo) * e));
     BESS_CUDA(cudaMalloc(&s->P, std::max<long long>(1, po) * e));
     BESS_CUDA(cudaMalloc(&s->P2, std::max<long long>(1, po) * e));
     BESS_CUDA(cudaMalloc(&s->Q, std::max<long long>(1, po) * e));
     BESS_CUDA(balloc(&s->P64, std::max<long long>(1, po)));
     BESS_CUDA(balloc(&s->ovf, (size_t)n + 1));
     if (bmixed(s)) {
-      for (auto& h : s->H) {
+      for (int k = 0; k < 4; ++k) {
+        __half*& h = k < 2 ? s->H[k] : s->H_alt[k - 2];
         BESS_CUDA(balloc(&h, (size_t)std::max<long long>(1, ho)));
         // the padding columns d .. dpad - 1 of every row stay zero
         BESS_CUDA(cudaMemset(h, 0, sizeof(__half) * (size_t)std::max<long long>(1, ho)));
@@ -346,21 +358,26 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
     BESS_CUDA(cudaMemcpy(s->titems, titems.data(), sizeof(ess::TcBatchItem) * titems.size(),
                          cudaMemcpyHostToDevice));
   if (bmixed(s)) {
-    // operand maps of the tensor-core q GEMM (the nu splits may have moved)
-    std::vector<CUtensorMap> maps((size_t)4 * s->np);
-    std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
-    for (int p = 0; p < s->np; ++p) {
-      if (nc[p] == 0) continue;
-      const int d = s->d[p], m = s->m[p], dp = s->dpad[p];
-      for (int k = 0; k < 2; ++k) {
-        BESS_CUDA(ess::tc_batch_map(&maps[4 * p + k], s->Ah[k] + s->ah_off[p], m, d, dp, 128));
-        BESS_CUDA(ess::tc_batch_map(&maps[4 * p + 2 + k], s->H[k] + ho_of[p], nc[p], d, dp,
-                                    ntile_of[p]));
+    // operand maps of the tensor-core q GEMM (the nu splits may have moved),
+    // one set per nu split buffer pair
+    for (int set = 0; set < 2; ++set) {
+      __half* const* hs = set == 0 ? s->H : s->H_alt;
+      std::vector<CUtensorMap> maps((size_t)4 * s->np);
+      std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+      for (int p = 0; p < s->np; ++p) {
+        if (nc[p] == 0) continue;
+        const int d = s->d[p], m = s->m[p], dp = s->dpad[p];
+        for (int k = 0; k < 2; ++k) {
+          BESS_CUDA(ess::tc_batch_map(&maps[4 * p + k], s->Ah[k] + s->ah_off[p], m, d, dp, 128));
+          BESS_CUDA(ess::tc_batch_map(&maps[4 * p + 2 + k], hs[k] + ho_of[p], nc[p], d, dp,
+                                      ntile_of[p]));
+        }
       }
+      CUtensorMap*& dst = set == 0 ? s->tmaps : s->tmaps_alt;
+      if (!dst) BESS_CUDA(cudaMalloc(&dst, sizeof(CUtensorMap) * maps.size()));
+      BESS_CUDA(cudaMemcpy(dst, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                           cudaMemcpyHostToDevice));
     }
-    if (!s->tmaps) BESS_CUDA(cudaMalloc(&s->tmaps, sizeof(CUtensorMap) * maps.size()));
-    BESS_CUDA(cudaMemcpy(s->tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
-                         cudaMemcpyHostToDevice));
   }
   drop_graphs(s);
   s->nc = nc;
@@ -466,11 +483,45 @@ ess_status bchain(ess_batch* s, ess::ChainParams<T> p, cudaStream_t st) {
   return ESS_OK;
 }
 
-// One step (draw, q, chain step) at step index t (+ *t_dev when t_dev is set).
+// The internal streams and events of the draws made one step ahead: the steps
+// at the highest priority, the draws at the lowest, so that a draw fills the
+// SMs' room beside the q GEMM instead of delaying it.
+ess_status bensure_streams(ess_batch* s) {
+  if (s->cap_stream) return ESS_OK;
+  int least = 0, greatest = 0;
+  BESS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  BESS_CUDA(cudaStreamCreateWithPriority(&s->cap_stream, cudaStreamNonBlocking, greatest));
+  BESS_CUDA(cudaStreamCreateWithPriority(&s->work_stream, cudaStreamNonBlocking, greatest));
+  BESS_CUDA(cudaStreamCreateWithPriority(&s->side_stream, cudaStreamNonBlocking, least));
+  for (cudaEvent_t* e : {&s->ev_drawn, &s->ev_done, &s->ev_fork, &s->ev_join})
+    BESS_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  return ESS_OK;
+}
+
+// The second nu buffers become the current ones (and the reverse).
+void bswap_nu(ess_batch* s) {
+  std::swap(s->NU, s->NU_alt);
+  std::swap(s->H[0], s->H_alt[0]);
+  std::swap(s->H[1], s->H_alt[1]);
+  std::swap(s->tmaps, s->tmaps_alt);
+}
+
+// nu of step t (+ *t_dev when t_dev is set) of every chain into the second
+// nu buffers (and their fp16 splits, mixed form).
+template <typename T>
+ess_status bdraw_alt(ess_batch* s, uint64_t seed, uint32_t t, const unsigned* t_dev,
+                     cudaStream_t st) {
+  BESS_CUDA(ess::launch_batch_draw<T>(s->desc, s->n, static_cast<T*>(s->NU_alt), seed, t, t_dev,
+                                      st, s->H_alt[0], s->H_alt[1]));
+  return ESS_OK;
+}
+
+// One step (draw, q, chain step) at step index t (+ *t_dev when t_dev is set);
+// without `draw`, nu of step t is already in the current buffers.
 template <typename T>
 ess_status bstep(ess_batch* s, uint64_t seed, uint32_t t, const unsigned* t_dev, T* samples,
-                 cudaStream_t st) {
-  {
+                 cudaStream_t st, bool draw = true) {
+  if (draw) {
     BPhase ph(s, st, ESS_PHASE_DRAW);
     BESS_CUDA(ess::launch_batch_draw<T>(s->desc, s->n, static_cast<T*>(s->NU), seed, t, t_dev, st,
                                         s->H[0], s->H[1]));
@@ -500,20 +551,47 @@ ess_status bgraph_period(ess_batch* s, uint64_t seed, cudaStream_t st) {
   for (auto& g : s->graphs)
     if (g.version == s->layout_version && g.seed == seed && g.p_first == s->P) hit = &g;
   if (!hit) {
-    if (!s->cap_stream) BESS_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+    ess_status rs = bensure_streams(s);
+    if (rs != ESS_OK) return rs;
     void* p_first = s->P;
     const bool timing = s->timing;
     s->timing = false;
-    BESS_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-    ess_status rc = brefresh<T>(s, static_cast<const T*>(s->X), true, false, s->cap_stream);
-    for (int j = 0; j < k && rc == ESS_OK; ++j)
-      rc = bstep<T>(s, seed, (uint32_t)j, s->t_dev, nullptr, s->cap_stream);
+    cudaStream_t cs = s->cap_stream, ss = s->side_stream;
+    BESS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    // step j's nu is drawn on the side stream one step ahead (draw 0 beside
+    // the refresh, draw j + 1 beside step j once step j - 1 is done); every
+    // side operation is joined back before the step that reads it, and k is
+    // even, so the period leaves the nu buffers where it found them
+    ess_status rc = ESS_OK;
+    auto cap_ok = [&](cudaError_t e, const char* what) {
+      if (rc == ESS_OK && e != cudaSuccess) rc = bcuda(e, what);
+      return rc == ESS_OK;
+    };
+    if (cap_ok(cudaEventRecord(s->ev_done, cs), "graph fork") &&
+        cap_ok(cudaStreamWaitEvent(ss, s->ev_done, 0), "graph fork")) {
+      bswap_nu(s);
+      rc = bdraw_alt<T>(s, seed, 0u, s->t_dev, ss);  // into the current buffers
+      bswap_nu(s);
+      if (rc == ESS_OK) cap_ok(cudaEventRecord(s->ev_drawn, ss), "graph draw");
+    }
+    if (rc == ESS_OK) rc = brefresh<T>(s, static_cast<const T*>(s->X), true, false, cs);
+    for (int j = 0; j < k && rc == ESS_OK; ++j) {
+      if (!cap_ok(cudaStreamWaitEvent(cs, s->ev_drawn, 0), "graph join")) break;
+      if (j + 1 < k) {
+        if (j > 0 && !cap_ok(cudaStreamWaitEvent(ss, s->ev_done, 0), "graph fork")) break;
+        rc = bdraw_alt<T>(s, seed, (uint32_t)(j + 1), s->t_dev, ss);
+        if (rc != ESS_OK || !cap_ok(cudaEventRecord(s->ev_drawn, ss), "graph draw")) break;
+      }
+      rc = bstep<T>(s, seed, (uint32_t)j, s->t_dev, nullptr, cs, false);
+      if (rc != ESS_OK || !cap_ok(cudaEventRecord(s->ev_done, cs), "graph step")) break;
+      bswap_nu(s);
+    }
     if (rc == ESS_OK) {
-      cudaError_t e = ess::launch_advance_t(s->t_dev, (unsigned)k, s->cap_stream);
+      cudaError_t e = ess::launch_advance_t(s->t_dev, (unsigned)k, cs);
       if (e != cudaSuccess) rc = bcuda(e, "advance step index");
     }
     cudaGraph_t graph = nullptr;
-    cudaError_t ec = cudaStreamEndCapture(s->cap_stream, &graph);
+    cudaError_t ec = cudaStreamEndCapture(cs, &graph);
     s->timing = timing;
     if (rc != ESS_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -521,7 +599,7 @@ ess_status bgraph_period(ess_batch* s, uint64_t seed, cudaStream_t st) {
     }
     if (ec != cudaSuccess) return bcuda(ec, "graph capture");
     cudaGraphExec_t exec = nullptr;
-    ec = cudaGraphInstantiate(&exec, graph, 0);
+    ec = cudaGraphInstantiateWithFlags(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     if (ec != cudaSuccess) return bcuda(ec, "graph instantiate");
     // k is even, so the period leaves P where it found it
@@ -551,34 +629,80 @@ ess_status brun(ess_batch* s, double* X, int t0, int n_iter, uint64_t seed, void
   const int k = s->cfg.refresh_k;
   const int n_rec = record_every > 0 ? n_iter / record_every : 0;
   const bool graphs_ok = s->use_graphs && !s->timing && record_every == 0 && k % 2 == 0;
-  int fresh = t0;
-  int it = 0;
-  while (it < n_iter) {
-    const int t = t0 + it;
-    if (graphs_ok && t % k == 0 && t != fresh && n_iter - it >= k) {
-      BESS_CUDA(ess::launch_set_t(s->t_dev, (unsigned)t, st));
-      while (n_iter - it >= k) {
-        rc = bgraph_period<T>(s, seed, st);
-        if (rc != ESS_OK) return rc;
-        it += k;
-      }
-      fresh = t0 + it - k;
-      continue;
-    }
-    if (t % k == 0 && t != fresh) {
-      BPhase ph(s, st, ESS_PHASE_REFRESH);
-      rc = brefresh<T>(s, Xw, true, false, st);
-      if (rc != ESS_OK) return rc;
-      fresh = t;
-    }
-    const bool rec = record_every > 0 && (it + 1) % record_every == 0 &&
-                     (it + 1) / record_every <= n_rec;
-    T* srow = rec ? static_cast<T*>(samples) + (long long)((it + 1) / record_every - 1) * s->total_x
-                  : nullptr;
-    rc = bstep<T>(s, seed, (uint32_t)t, nullptr, srow, st);
+  // Unless per-phase timing is on, the steps run on the internal high-priority
+  // work stream and each plain step t that another plain step follows draws
+  // nu of step t + 1 on the low-priority side stream beside it; both streams
+  // are forked from st here and joined back after the loop.
+  const bool ahead = !s->timing && n_iter > 1;
+  cudaStream_t wst = st;
+  if (ahead) {
+    rc = bensure_streams(s);
     if (rc != ESS_OK) return rc;
-    ++it;
+    BESS_CUDA(cudaEventRecord(s->ev_fork, st));
+    BESS_CUDA(cudaStreamWaitEvent(s->work_stream, s->ev_fork, 0));
+    wst = s->work_stream;
   }
+  int fresh = t0;
+  auto graph_at = [&](int it_) {
+    const int t_ = t0 + it_;
+    return graphs_ok && t_ % k == 0 && t_ != fresh && n_iter - it_ >= k;
+  };
+  auto loop = [&]() -> ess_status {
+    bool drawn = false;  // the current nu buffers hold step t's draw
+    int it = 0;
+    while (it < n_iter) {
+      const int t = t0 + it;
+      if (graph_at(it)) {
+        BESS_CUDA(ess::launch_set_t(s->t_dev, (unsigned)t, wst));
+        while (n_iter - it >= k) {
+          ess_status r = bgraph_period<T>(s, seed, wst);
+          if (r != ESS_OK) return r;
+          it += k;
+        }
+        fresh = t0 + it - k;
+        continue;
+      }
+      const bool next = ahead && it + 1 < n_iter && !graph_at(it + 1);
+      if (next) {
+        BESS_CUDA(cudaEventRecord(s->ev_done, wst));  // step t - 1 is done here
+        BESS_CUDA(cudaStreamWaitEvent(s->side_stream, s->ev_done, 0));
+        ess_status r = bdraw_alt<T>(s, seed, (uint32_t)(t + 1), nullptr, s->side_stream);
+        if (r != ESS_OK) return r;
+        s->phase_launches[ESS_PHASE_DRAW] += 1;
+        BESS_CUDA(cudaEventRecord(s->ev_drawn, s->side_stream));
+      }
+      if (t % k == 0 && t != fresh) {
+        BPhase ph(s, wst, ESS_PHASE_REFRESH);
+        ess_status r = brefresh<T>(s, Xw, true, false, wst);
+        if (r != ESS_OK) return r;
+        fresh = t;
+      }
+      const bool rec = record_every > 0 && (it + 1) % record_every == 0 &&
+                       (it + 1) / record_every <= n_rec;
+      T* srow = rec ? static_cast<T*>(samples) + (long long)((it + 1) / record_every - 1) * s->total_x
+                    : nullptr;
+      ess_status r = bstep<T>(s, seed, (uint32_t)t, nullptr, srow, wst, !drawn);
+      if (r != ESS_OK) return r;
+      if (next) {
+        // step t + 1 reads the buffers just drawn, after the draw
+        bswap_nu(s);
+        BESS_CUDA(cudaStreamWaitEvent(wst, s->ev_drawn, 0));
+      }
+      drawn = next;
+      ++it;
+    }
+    return ESS_OK;
+  };
+  rc = loop();
+  if (ahead) {
+    // join even after an error: no internal work may outlive st's order
+    cudaError_t e = cudaEventRecord(s->ev_join, s->work_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->ev_join, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev_join, s->side_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->ev_join, 0);
+    if (e != cudaSuccess && rc == ESS_OK) rc = bcuda(e, "join internal streams");
+  }
+  if (rc != ESS_OK) return rc;
   BESS_CUDA((ess::launch_convert<T, double>(Xw, (int)s->total_x, X, (int)s->total_x, 1,
                                             (int)s->total_x, st)));
   s->host_steps += (long long)s->n * n_iter;
@@ -778,7 +902,10 @@ void ess_batch_destroy(ess_batch* s) {
   bfree(s->t_dev);
   bfree(s->dstats);
   bfree(s->dstatus);
-  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  for (cudaStream_t q : {s->cap_stream, s->work_stream, s->side_stream})
+    if (q) cudaStreamDestroy(q);
+  for (cudaEvent_t e : {s->ev_drawn, s->ev_done, s->ev_fork, s->ev_join})
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   delete s;
 }

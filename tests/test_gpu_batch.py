@@ -78,6 +78,32 @@ def test_batch_graph_replay_is_bit_identical(form):
     np.testing.assert_array_equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("form", [ess.ESS_PREC_FP64, ess.ESS_PREC_MIXED])
+def test_batch_draws_ahead_are_bit_identical(form):
+    """nu of step t + 1 drawn on a side stream beside step t (plain launches
+    and graph replays) gives the bits of strictly sequential launches
+    (per-phase timing on), with a layout change between runs (the second
+    runs swap which nu buffers and operand maps are current)."""
+    As, bs, Xs, nc = make_batch(3)
+    nc2 = [max(0, n - 3) for n in nc]
+    out = []
+    for timing, graphs in ((True, False), (False, False), (False, True)):
+        bs_ = ess.BatchSampler(As, bs, precision=form, refresh_k=4)
+        try:
+            ess.ess_batch_set_graphs(bs_.batch, graphs)
+            ess.ess_batch_set_timing(bs_.batch, timing)
+            X = bs_.pack(Xs)
+            bs_.run(nc, X, 19, seed=6, t0=1)
+            X2 = bs_.pack([x[:n] for x, n in zip(Xs, nc2)])
+            bs_.run(nc2, X2, 13, seed=6, t0=3)
+            out.append((host(X), host(X2)))
+        finally:
+            bs_.close()
+    for o in out[1:]:
+        np.testing.assert_array_equal(out[0][0], o[0])
+        np.testing.assert_array_equal(out[0][1], o[1])
+
+
 def test_batch_fp64_step_with_draws():
     """One step with given draws: theta within 1e-10 rad, x' within 1e-9
     relative of the oracle's one-step map, for every chain of every problem."""
