@@ -47,7 +47,18 @@ constexpr int kWBP = kWB + kWB / 32;      // padded bucket array: bucket j at j 
 #ifndef ESS_WARP_MINBLOCKS
 #define ESS_WARP_MINBLOCKS 4
 #endif
-constexpr int kBatch = ESS_WARP_BATCH;    // rows per lane in flight per loop trip
+// FP64 chains: their double p, q and thresholds take twice the registers per
+// row in flight; 4 rows per lane and trip keep them out of local memory at 4
+// CTAs per SM (measured at d = 1000, m = 2000, 8192 chains: 0.516 ms per step
+// against 0.551 with 8 rows, 0.551 with 4 rows at 3 CTAs, 0.586 with 8 rows
+// at 2 CTAs)
+#ifndef ESS_WARP_BATCH_F64
+#define ESS_WARP_BATCH_F64 4
+#endif
+#ifndef ESS_WARP_MINBLOCKS_F64
+#define ESS_WARP_MINBLOCKS_F64 4
+#endif
+constexpr int kBatchF32 = ESS_WARP_BATCH;  // rows per lane in flight per loop trip (float)
 constexpr int kFirst = 256;               // rows of the first batch
 
 // Bucket j lives at j + j / 32: a lane's consecutive buckets then sit on
@@ -152,8 +163,10 @@ __device__ __forceinline__ void warp_bitonic(T (&key)[kPer], T (&val)[kPer], int
 }
 
 template <typename T, int WARPS, bool BATCH>
-__global__ void __launch_bounds__(WARPS * 32, ESS_WARP_MINBLOCKS)
+__global__ void __launch_bounds__(WARPS * 32,
+                                  sizeof(T) == 4 ? ESS_WARP_MINBLOCKS : ESS_WARP_MINBLOCKS_F64)
 chain_warp_kernel(ChainParams<T> prm) {
+  constexpr int kBatch = sizeof(T) == 4 ? kBatchF32 : ESS_WARP_BATCH_F64;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // per-warp shared memory: two padded bucket arrays, candidates (code,
