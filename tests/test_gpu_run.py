@@ -122,6 +122,38 @@ def test_draws_ahead_are_bit_identical(form):
 
 
 @pytest.mark.parametrize("form", FORMS)
+def test_steps_capture_into_a_cuda_graph(form):
+    """ess_chains_step enqueued while the caller captures its stream (the
+    internal work and draw streams fork from it and join back): one replay of
+    the captured steps, across a refresh boundary, gives the chains of the
+    same steps launched directly."""
+    import torch
+    inst = workloads.medium(n_chains=64)
+    out = []
+    for capture in (False, True):
+        s = ess.Sampler(inst.A, inst.b, precision=form, refresh_k=8)
+        try:
+            ess.ess_set_graphs(s.state, False)
+            st = torch.cuda.Stream()
+            X = dev(inst.X0)
+            ess.ess_chains_init(s.state, X, 64, 3, stream=st)
+            ess.ess_chains_step(s.state, 2, 9, stream=st)  # steps 3, 4
+            if capture:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=st):
+                    ess.ess_chains_step(s.state, 4, 9, stream=st)  # steps 5 .. 8
+                g.replay()
+            else:
+                ess.ess_chains_step(s.state, 4, 9, stream=st)
+            torch.cuda.synchronize()
+            ess.ess_chains_get(s.state, X, stream=st)
+            out.append(host(X))
+        finally:
+            s.close()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("form", FORMS)
 def test_autotune_keeps_the_chains(form):
     """The autotuner times its candidates without moving any chain: a tuned
     run equals an untuned run with the same sort path (the q GEMM's tile
