@@ -413,7 +413,10 @@ void ess_batch_destroy(ess_batch *batch);
  *             run's precision (float in the mixed form, double in FP64).
  * Steps t0 .. t0 + n_iter - 1; p = A x is recomputed when t % refresh_k == 0.
  * Without sample recording and with refresh_k even, full refresh periods run
- * as CUDA-graph replays.  Synchronous on return.  Reference: Alg. 1. */
+ * as CUDA-graph replays.  Unless per-phase timing is on, the steps run on two
+ * internal streams (the draw of step t + 1 beside step t), forked from
+ * cuda_stream and joined back into it.  Synchronous on return.
+ * Reference: Alg. 1. */
 ess_status ess_batch_run(ess_batch *batch, const int *n_chains, double *X, int t0, int n_iter,
                          uint64_t seed, void *samples, int record_every, void *cuda_stream);
 
