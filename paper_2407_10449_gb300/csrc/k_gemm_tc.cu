@@ -1347,6 +1347,27 @@ __global__ void slice_rows_kernel(const TI* __restrict__ X, int ldx, int rows, i
   if (mx > TI(0)) (void)frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): mx < 2^e
   const TI inv_t = ldexp(TI(1), -e);
   if (lane == 0) row_scale[row] = mx > TI(0) ? ldexpf(1.f, e) : 0.f;
+  if constexpr (sizeof(TI) == 8) {
+    if (w * K <= 63) {
+      // FP64 rows: |y| < 1, so |y| 2^63 converts exactly to an integer in its
+      // top 60 bits (the bits below 2^-63 are below every slice), and slice l
+      // is the bit field [63 - w (l + 1), 63 - w l) of it with the sign of y:
+      // the same integers as the loop below, with one FP64 conversion per
+      // entry instead of three FP64 operations per slice
+      const unsigned long long mask = (1ull << w) - 1ull;
+      for (int j = lane; j < d; j += 32) {
+        const double y = x[j] * inv_t;  // exact: power-of-two scaling
+        const unsigned long long Y = (unsigned long long)(fabs(y) * 9223372036854775808.0);
+        const bool neg = y < 0.0;
+        for (int l = 0; l < K; ++l) {
+          const int v = (int)((Y >> (63 - w * (l + 1))) & mask);
+          slices[(size_t)l * slice_stride + (size_t)row * ld_bf + j] =
+              __float2bfloat16_rn((float)(neg ? -v : v));
+        }
+      }
+      return;
+    }
+  }
   const TI up = ldexp(TI(1), w);
   for (int j = lane; j < d; j += 32) {
     TI y = x[j] * inv_t;  // exact: power-of-two scaling
