@@ -212,13 +212,35 @@ __device__ __forceinline__ int classify_phi_nb(float p, float q, float b, float 
   return zero ? kRowNone : cls;
 }
 
+// A double rounded to float by integer operations on its two halves, so that
+// the FP64 chains' classification (three conversions per row) leaves the
+// narrow FP64 pipe to the FP64 work proper.  Values in float's normal range
+// are rounded to nearest (ties away from zero: error at most half an ulp,
+// 2^-24 relative); values below it become zero, finite values above it
+// become infinity, and NaN stays NaN.  The classification keeps rows whose
+// float p, q or b is zero or non-finite where that decides the class (r = 0 or
+// a non-finite r^2).
+__device__ __forceinline__ float dbl_to_flt_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned dexp = (hi >> 20) & 0x7FFu;
+  const int e = (int)dexp - 896;  // float exponent field for normal values
+  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  unsigned bits = (sign | ((unsigned)e << 23) | mant) + ((lo >> 28) & 1u);
+  bits = e <= 0 ? sign : bits;
+  bits = e >= 255 ? (sign | 0x7F800000u) : bits;
+  bits = dexp == 0x7FFu && ((hi & 0xFFFFFu) | lo) != 0u ? 0x7FC00000u : bits;
+  return __uint_as_float(bits);
+}
+
 __device__ __forceinline__ int classify_phi_d(double p, double q, double b, float tlo2,
                                               float thi2, float& pa, float& pb,
                                               bool& nonfinite) {
   nonfinite |= (__double2hiint(p) & 0x7FF00000) == 0x7FF00000 ||
                (__double2hiint(q) & 0x7FF00000) == 0x7FF00000;
   bool zero = false, nf = false;
-  const int cls = classify_phi_nb((float)p, (float)q, (float)b, tlo2, thi2, pa, pb, zero, nf);
+  const int cls = classify_phi_nb(dbl_to_flt_bits(p), dbl_to_flt_bits(q), dbl_to_flt_bits(b),
+                                  tlo2, thi2, pa, pb, zero, nf);
   return zero || nf ? kRowKeep : cls;
 }
 
