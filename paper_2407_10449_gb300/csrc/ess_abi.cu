@@ -75,6 +75,7 @@ struct ess_state {
   double* b64 = nullptr;
   double* anorm = nullptr;
   float* b32 = nullptr;
+  double* bm_tab = nullptr;  // FP64 Box-Muller tables (ess::bm_table_fill)
   void* slack = nullptr;   // m thresholds b_i - margin ||a_i|| (T, rounded down)
   // work buffers (device), sized for `cap` chains
   int cap = 0;
@@ -440,7 +441,7 @@ ess_status autotune(ess_state* s, int t0, cudaStream_t st) {
                                      (uint32_t)t0, 0u, 0u, st));
   else
     ESS_CUDA(ess::launch_draw_nu_f64(static_cast<double*>(s->NU), n, d, d, 0, (uint32_t)t0, 0u,
-                                     0u, st));
+                                     0u, s->bm_tab, st));
   if (mixed(s)) {
     int best = 0;
     float best_ms = 0.f;
@@ -539,8 +540,8 @@ ess_status draw_step_nu(ess_state* s, uint64_t seed, uint32_t t, const unsigned*
     ESS_CUDA(ess::launch_draw_nu_f32(static_cast<float*>(nu), d, nu_h, s->ld16, n, d, seed, t,
                                      0u, 0u, st, t_dev));
   else
-    ESS_CUDA(ess::launch_draw_nu_f64(static_cast<double*>(nu), n, d, d, seed, t, 0u, 0u, st,
-                                     t_dev));
+    ESS_CUDA(ess::launch_draw_nu_f64(static_cast<double*>(nu), n, d, d, seed, t, 0u, 0u,
+                                     s->bm_tab, st, t_dev));
   return ESS_OK;
 }
 
@@ -772,6 +773,13 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
   if (e == cudaSuccess) e = dev_alloc(&s->dstats, 1);
   if (e == cudaSuccess) e = dev_alloc(&s->dstatus, 1);
   if (e == cudaSuccess) e = dev_alloc(&s->t_dev, 1);
+  if (e == cudaSuccess) {
+    std::vector<double> tab(ess::kBmTableSize);
+    ess::bm_table_fill(tab.data());
+    e = dev_alloc(&s->bm_tab, tab.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(s->bm_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMemset(s->dstats, 0, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMemset(s->dstatus, 0, sizeof(int));
   if (e == cudaSuccess && c.precision == ESS_PREC_MIXED) {
@@ -799,6 +807,7 @@ void ess_destroy(ess_state* s) {
   if (s->slack) cudaFree(s->slack);
   s->slack = nullptr;
   dev_free(s->b32);
+  dev_free(s->bm_tab);
   dev_free(s->dstats);
   dev_free(s->dstatus);
   ess::tc_gemm_destroy(s->tc_plan);
@@ -1252,7 +1261,7 @@ ess_status ess_draw_normals(const ess_state* s, int n_chains, int t, uint64_t se
                                      s->d, seed, (uint32_t)t, 0u, 0u, st));
   else
     ESS_CUDA(ess::launch_draw_nu_f64(static_cast<double*>(out), n_chains, s->d, s->d, seed,
-                                     (uint32_t)t, 0u, 0u, st));
+                                     (uint32_t)t, 0u, 0u, s->bm_tab, st));
   ESS_CUDA(cudaStreamSynchronize(st));
   return ESS_OK;
 }

@@ -92,6 +92,7 @@ struct ess_batch {
   std::vector<int> dpad;               // per problem: d rounded up to 8
   double* b64 = nullptr;
   float* b32 = nullptr;
+  double* bm_tab = nullptr;      // FP64 Box-Muller tables (ess::bm_table_fill)
   double* anorm = nullptr;
   void* slack = nullptr;         // b - margin ||a||, rounded down in the step's type
   // current chain layout
@@ -512,7 +513,7 @@ template <typename T>
 ess_status bdraw_alt(ess_batch* s, uint64_t seed, uint32_t t, const unsigned* t_dev,
                      cudaStream_t st) {
   BESS_CUDA(ess::launch_batch_draw<T>(s->desc, s->n, static_cast<T*>(s->NU_alt), seed, t, t_dev,
-                                      st, s->H_alt[0], s->H_alt[1]));
+                                      s->bm_tab, st, s->H_alt[0], s->H_alt[1]));
   return ESS_OK;
 }
 
@@ -523,8 +524,8 @@ ess_status bstep(ess_batch* s, uint64_t seed, uint32_t t, const unsigned* t_dev,
                  cudaStream_t st, bool draw = true) {
   if (draw) {
     BPhase ph(s, st, ESS_PHASE_DRAW);
-    BESS_CUDA(ess::launch_batch_draw<T>(s->desc, s->n, static_cast<T*>(s->NU), seed, t, t_dev, st,
-                                        s->H[0], s->H[1]));
+    BESS_CUDA(ess::launch_batch_draw<T>(s->desc, s->n, static_cast<T*>(s->NU), seed, t, t_dev,
+                                        s->bm_tab, st, s->H[0], s->H[1]));
   }
   {
     BPhase ph(s, st, ESS_PHASE_GEMM);
@@ -874,6 +875,13 @@ ess_status ess_batch_create(int n_problems, const int* d, const int* m, const do
   }
   if (e == cudaSuccess) e = balloc(&s->queue, 1);
   if (e == cudaSuccess) e = balloc(&s->t_dev, 1);
+  if (e == cudaSuccess) {
+    std::vector<double> tab(ess::kBmTableSize);
+    ess::bm_table_fill(tab.data());
+    e = balloc(&s->bm_tab, tab.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(s->bm_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = balloc(&s->dstats, 1);
   if (e == cudaSuccess) e = balloc(&s->dstatus, 1);
   if (e == cudaSuccess) e = cudaMemset(s->dstats, 0, sizeof(DevStats));
@@ -900,6 +908,7 @@ void ess_batch_destroy(ess_batch* s) {
   if (s->slack) cudaFree(s->slack);
   bfree(s->queue);
   bfree(s->t_dev);
+  bfree(s->bm_tab);
   bfree(s->dstats);
   bfree(s->dstatus);
   for (cudaStream_t q : {s->cap_stream, s->work_stream, s->side_stream})

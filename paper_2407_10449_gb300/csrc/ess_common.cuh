@@ -8,6 +8,7 @@
 // [0, 1); the theta draw uses a 53-bit uniform from block 0 of stream 1.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -59,86 +60,100 @@ __device__ __forceinline__ void rng_block(uint64_t seed, uint32_t n, uint32_t ch
                 (uint32_t)(seed >> 32), out);
 }
 
-// ln u1 for u1 = x / 2^32, x an integer in [1, 2^32], in double precision
-// without the general-purpose logarithm (GB300's FP64 pipe is narrow): with
-// x = 2^e m, m in [0.75, 1.5) (e and m from integer operations),
-//   ln u1 = (e - 32) ln 2 + ln m,  ln m = 2 atanh(f),  f = (m - 1) / (m + 1),
-// f in [-1/7, 1/5], and the atanh series 2 f (1 + f^2/3 + ... + f^20/21), whose
-// next term is below 2^-54 of the sum.  Near u1 = 1 (e = 32) m - 1 is exact,
-// so the result keeps its relative accuracy there.
-__device__ __forceinline__ double ln_u32(uint64_t x) {
+// FP64 Box-Muller without the general-purpose logarithm and sine / cosine
+// (GB300's FP64 pipe is narrow), from small tables built on the host
+// (bm_table_fill) and short series on reduced arguments.  Table layout
+// (kBmTableSize doubles):
+//   [0, 97)      c_j = 1 / (1 + (j - 32) / 128) rounded to float, j = 0 .. 96
+//                (c_32 = 1 exactly);
+//   [97, 194)    -ln c_j;
+//   [194, 450)   sin(2 pi k / 256), k = 0 .. 255;
+//   [450, 706)   cos(2 pi k / 256).
+constexpr int kBmLnC = 0, kBmLnT = 97, kBmSin = 194, kBmCos = 450, kBmTableSize = 706;
+
+// ln u1 for u1 = x / 2^32, x an integer in [1, 2^32]: x = 2^e m with
+// m in [0.75, 1.5) (e, m and the table index from integer operations),
+// ln u1 = (e - 32) ln 2 - ln c_j + ln(1 + r), r = m c_j - 1 for the table
+// entry j nearest m (|r| < 0.0053), ln(1 + r) by its series through r^8 (the
+// next term is below 2^-55 of the sum).  Near u1 = 1, c_j = 1 and r = m - 1
+// exactly, so the result keeps its relative accuracy there.
+__device__ __forceinline__ double ln_u32(uint64_t x, const double* __restrict__ tab) {
   constexpr double kLn2Hi = 0.6931471805599452862267639829951804131269;  // ln 2 rounded
   constexpr double kLn2Lo = 2.3190468138462996154948555e-17;               // ln 2 - kLn2Hi
   const int lz = __clzll((long long)x);
   int e = 63 - lz;
-  const uint64_t frac = ((x << lz) << 1) >> 12;  // the bits below the leading one
-  double m = __longlong_as_double((long long)(0x3FF0000000000000ull | frac));  // [1, 2)
-  if (m >= 1.5) {
-    m *= 0.5;
+  const uint64_t frac = ((x << lz) << 1) >> 12;  // the 52 bits below the leading one
+  uint64_t mbits = 0x3FF0000000000000ull | frac;  // m in [1, 2)
+  int j;
+  if (frac >= (1ull << 51)) {
+    // m in [1.5, 2): use m / 2 in [0.75, 1), entry round((m / 2 - 1) 128)
+    mbits -= 1ull << 52;
     ++e;
+    j = (int)((frac + (1ull << 45)) >> 46) - 64;
+  } else {
+    j = (int)((frac + (1ull << 44)) >> 45);  // round((m - 1) 128)
   }
-  const double f = (m - 1.0) / (m + 1.0);
-  const double f2 = f * f;
-  double sum = 1.0 / 21.0;
-  sum = fma(sum, f2, 1.0 / 19.0);
-  sum = fma(sum, f2, 1.0 / 17.0);
-  sum = fma(sum, f2, 1.0 / 15.0);
-  sum = fma(sum, f2, 1.0 / 13.0);
-  sum = fma(sum, f2, 1.0 / 11.0);
-  sum = fma(sum, f2, 1.0 / 9.0);
-  sum = fma(sum, f2, 1.0 / 7.0);
-  sum = fma(sum, f2, 1.0 / 5.0);
-  sum = fma(sum, f2, 1.0 / 3.0);
-  const double lnm = fma(f * f2, sum, f) * 2.0;  // 2 (f + f^3 (1/3 + ...))
+  j += 32;
+  const double m = __longlong_as_double((long long)mbits);
+  const double r = fma(m, __ldg(tab + kBmLnC + j), -1.0);
+  // ln(1 + r) = r (1 - r/2 + r^2/3 - ... - r^7/8)
+  double sum = -1.0 / 8.0;
+  sum = fma(sum, r, 1.0 / 7.0);
+  sum = fma(sum, r, -1.0 / 6.0);
+  sum = fma(sum, r, 1.0 / 5.0);
+  sum = fma(sum, r, -1.0 / 4.0);
+  sum = fma(sum, r, 1.0 / 3.0);
+  sum = fma(sum, r, -1.0 / 2.0);
+  const double l1p = fma(r * r, sum, r);
   const double n = (double)(e - 32);
-  return fma(n, kLn2Hi, fma(n, kLn2Lo, lnm));
+  return fma(n, kLn2Hi, fma(n, kLn2Lo, __ldg(tab + kBmLnT + j) + l1p));
 }
 
-// cos and sin of 2 pi r / 2^32 for a 32-bit r: the quadrant k = round(r / 2^30)
-// is taken exactly in integers, the rest t = 2 pi (r - k 2^30) / 2^32 lies in
-// [-pi/4, pi/4], where the Taylor series of sin through t^17 and of cos
-// through t^16 leave a truncation below 2^-54.
-__device__ __forceinline__ void sincos_2pi_u32(uint32_t r, double& s, double& c) {
+// cos and sin of 2 pi r / 2^32 for a 32-bit r: k = round(r / 2^24) (mod 256)
+// taken exactly in integers, the rest t = 2 pi (r - k 2^24) / 2^32 in
+// [-pi/256, pi/256], Taylor sin t through t^7 and cos t through t^6 (the next
+// terms are below 2^-60), and the angle-sum formulas with the table's sin and
+// cos of 2 pi k / 256.
+__device__ __forceinline__ void sincos_2pi_u32(uint32_t r, const double* __restrict__ tab,
+                                               double& s, double& c) {
   constexpr double kStep = kTwoPi * 2.3283064365386962890625e-10;  // 2 pi / 2^32
-  const uint32_t k = ((r + 0x20000000u) >> 30) & 3u;  // r near 2^32 wraps to quadrant 0
-  const int f = (int)(r - (k << 30));                // in [-2^29, 2^29)
+  const uint32_t k = ((r + 0x800000u) >> 24) & 255u;  // r near 2^32 wraps to entry 0
+  const int f = (int)(r - (k << 24));                // in [-2^23, 2^23)
   const double t = (double)f * kStep;
   const double t2 = t * t;
-  // sin t = t + t^3 P(t^2),  P = -1/3! + t^2/5! - ... + t^14/17!
-  double ps = 1.0 / 355687428096000.0;       // 1/17!
-  ps = fma(ps, t2, -1.0 / 1307674368000.0);  // 1/15!
-  ps = fma(ps, t2, 1.0 / 6227020800.0);      // 1/13!
-  ps = fma(ps, t2, -1.0 / 39916800.0);       // 1/11!
-  ps = fma(ps, t2, 1.0 / 362880.0);          // 1/9!
-  ps = fma(ps, t2, -1.0 / 5040.0);           // 1/7!
-  ps = fma(ps, t2, 1.0 / 120.0);             // 1/5!
-  ps = fma(ps, t2, -1.0 / 6.0);              // 1/3!
-  const double st = fma(t * t2, ps, t);
-  // cos t = 1 + t^2 Q(t^2),  Q = -1/2! + t^2/4! - ... + t^14/16!
-  double pc = 1.0 / 20922789888000.0;        // 1/16!
-  pc = fma(pc, t2, -1.0 / 87178291200.0);    // 1/14!
-  pc = fma(pc, t2, 1.0 / 479001600.0);       // 1/12!
-  pc = fma(pc, t2, -1.0 / 3628800.0);        // 1/10!
-  pc = fma(pc, t2, 1.0 / 40320.0);           // 1/8!
-  pc = fma(pc, t2, -1.0 / 720.0);            // 1/6!
-  pc = fma(pc, t2, 1.0 / 24.0);              // 1/4!
-  pc = fma(pc, t2, -0.5);                    // 1/2!
-  const double ct = fma(t2, pc, 1.0);
-  // rotate by k quarter turns
-  const double sa = (k & 1u) ? ct : st, ca = (k & 1u) ? st : ct;
-  s = (k & 2u) ? -sa : sa;
-  c = ((k + 1u) & 2u) ? -ca : ca;
+  const double st = fma(t * t2, fma(t2, fma(t2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), t);
+  const double ct = fma(t2, fma(t2, fma(t2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+  const double sk = __ldg(tab + kBmSin + k), ck = __ldg(tab + kBmCos + k);
+  s = fma(sk, ct, ck * st);
+  c = fma(ck, ct, -(sk * st));
 }
 
-// Box-Muller, double precision: 4 normals from one block.
-__device__ __forceinline__ void box_muller4(const uint32_t r[4], double z[4]) {
+// Box-Muller, double precision: 4 normals from one block (tab: the tables
+// above, in device memory).
+__device__ __forceinline__ void box_muller4(const uint32_t r[4], double z[4],
+                                            const double* __restrict__ tab) {
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const double rad = sqrt(-2.0 * ln_u32((uint64_t)r[2 * k] + 1u));
+    const double rad = sqrt(-2.0 * ln_u32((uint64_t)r[2 * k] + 1u, tab));
     double s, c;
-    sincos_2pi_u32(r[2 * k + 1], s, c);
+    sincos_2pi_u32(r[2 * k + 1], tab, s, c);
     z[2 * k] = rad * c;
     z[2 * k + 1] = rad * s;
+  }
+}
+
+// Host: the tables of the FP64 Box-Muller, from long-double library values
+// rounded once to double.
+inline void bm_table_fill(double* tab) {
+  const long double two_pi = 2.0L * acosl(-1.0L);
+  for (int j = 0; j < 97; ++j) {
+    const float cj = (float)(1.0L / (1.0L + (long double)(j - 32) / 128.0L));
+    tab[kBmLnC + j] = (double)cj;
+    tab[kBmLnT + j] = (double)(-logl((long double)cj));
+  }
+  for (int k = 0; k < 256; ++k) {
+    tab[kBmSin + k] = (double)sinl(two_pi * (long double)k / 256.0L);
+    tab[kBmCos + k] = (double)cosl(two_pi * (long double)k / 256.0L);
   }
 }
 
@@ -166,9 +181,10 @@ __device__ __forceinline__ void box_muller4(const uint32_t r[4], float z[4]) {
   }
 }
 
-__device__ __forceinline__ void box_muller4(const uint32_t r[4], double* out, int n) {
+__device__ __forceinline__ void box_muller4(const uint32_t r[4], double* out, int n,
+                                            const double* __restrict__ tab) {
   double z[4];
-  box_muller4(r, z);
+  box_muller4(r, z, tab);
   for (int k = 0; k < n; ++k) out[k] = z[k];
 }
 

@@ -12,9 +12,11 @@ namespace ess {
 
 // ---------------------------------------------------------------- draws ----
 // nu[c, j] for chains chain0 .. chain0 + n_chains - 1 at step t (row stride ld);
-// with t_dev set the step index is t + *t_dev (replayable CUDA graphs).
+// with t_dev set the step index is t + *t_dev (replayable CUDA graphs);
+// bm_tab: the FP64 Box-Muller tables (bm_table_fill) in device memory.
 cudaError_t launch_draw_nu_f64(double* nu, int n_chains, int d, int ld, uint64_t seed,
-                               uint32_t t, uint32_t problem, uint32_t chain0, cudaStream_t s,
+                               uint32_t t, uint32_t problem, uint32_t chain0,
+                               const double* bm_tab, cudaStream_t s,
                                const unsigned* t_dev = nullptr);
 // float nu plus (if split != nullptr) the two-way fp16 split of nu * kNuSplitScale
 // (h0 = fp16(y), h1 = fp16(y - h0)), rows of ld16 elements; columns
@@ -214,10 +216,11 @@ inline int batch_rtile(int ctile) { return 4096 / ctile; }
 // 53-bit), written at desc[c].x_off; the step index is t (+ *t_dev if set).
 // T = float with H0, H1 set also writes the fp16 split of nu * kNuSplitScale
 // at desc[c].h_off (rows of desc[c].dpad).
+// bm_tab: the FP64 Box-Muller tables (T = double; unused for float).
 template <typename T>
 cudaError_t launch_batch_draw(const ChainDesc* desc, int n_chains, T* NU, uint64_t seed,
-                              uint32_t t, const unsigned* t_dev, cudaStream_t s,
-                              __half* H0 = nullptr, __half* H1 = nullptr);
+                              uint32_t t, const unsigned* t_dev, const double* bm_tab,
+                              cudaStream_t s, __half* H0 = nullptr, __half* H1 = nullptr);
 // Scaled fp16 split of caller-supplied float nu rows (per chain: t = 2^(15-e)
 // with max |nu| in [2^(e-1), 2^e); unscale[c] = 1 / t).
 cudaError_t launch_batch_split(const ChainDesc* desc, int n_chains, const float* NU, __half* H0,

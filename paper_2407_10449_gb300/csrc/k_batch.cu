@@ -40,8 +40,8 @@ __device__ __forceinline__ int next_item(int* queue, int* s_item) {
 template <typename T>
 __global__ void batch_draw_kernel(const ChainDesc* __restrict__ desc, int n_chains,
                                   T* __restrict__ NU, uint64_t seed, uint32_t t,
-                                  const unsigned* t_dev, __half* __restrict__ H0,
-                                  __half* __restrict__ H1) {
+                                  const unsigned* t_dev, const double* __restrict__ bm_tab,
+                                  __half* __restrict__ H0, __half* __restrict__ H1) {
   const int c = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (c >= n_chains) return;
@@ -53,7 +53,10 @@ __global__ void batch_draw_kernel(const ChainDesc* __restrict__ desc, int n_chai
     uint32_t r[4];
     rng_block(seed, (uint32_t)n, cd.chain, tt, cd.problem, 0u, r);
     T z[4];
-    box_muller4(r, z);
+    if constexpr (sizeof(T) == 8)
+      box_muller4(r, z, bm_tab);
+    else
+      box_muller4(r, z);
     const int left = cd.d - 4 * n;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -406,11 +409,12 @@ __global__ void set_t_kernel(unsigned* t_dev, unsigned v) { *t_dev = v; }
 
 template <typename T>
 cudaError_t launch_batch_draw(const ChainDesc* desc, int n_chains, T* NU, uint64_t seed,
-                              uint32_t t, const unsigned* t_dev, cudaStream_t s, __half* H0,
-                              __half* H1) {
+                              uint32_t t, const unsigned* t_dev, const double* bm_tab,
+                              cudaStream_t s, __half* H0, __half* H1) {
   if (n_chains <= 0) return cudaSuccess;
+  if (sizeof(T) == 8 && bm_tab == nullptr) return cudaErrorInvalidValue;
   batch_draw_kernel<T><<<warps_grid(n_chains), 256, 0, s>>>(desc, n_chains, NU, seed, t, t_dev,
-                                                            H0, H1);
+                                                            bm_tab, H0, H1);
   return cudaGetLastError();
 }
 
@@ -458,9 +462,11 @@ cudaError_t launch_set_t(unsigned* t_dev, unsigned v, cudaStream_t s) {
 }
 
 template cudaError_t launch_batch_draw<float>(const ChainDesc*, int, float*, uint64_t, uint32_t,
-                                              const unsigned*, cudaStream_t, __half*, __half*);
+                                              const unsigned*, const double*, cudaStream_t,
+                                              __half*, __half*);
 template cudaError_t launch_batch_draw<double>(const ChainDesc*, int, double*, uint64_t, uint32_t,
-                                               const unsigned*, cudaStream_t, __half*, __half*);
+                                               const unsigned*, const double*, cudaStream_t,
+                                               __half*, __half*);
 template cudaError_t launch_batch_q<float>(const BatchItem*, int, int*, const float*, const float*,
                                            float*, cudaStream_t);
 template cudaError_t launch_batch_q<double>(const BatchItem*, int, int*, const double*,

@@ -13,7 +13,8 @@ __device__ __forceinline__ uint32_t h2_bits(__half2 v) {
 // One thread per (chain, Philox block): 4 consecutive coordinates.
 __global__ void draw_nu_f64_kernel(double* __restrict__ nu, int n_chains, int d, int ld,
                                    uint64_t seed, uint32_t t, const unsigned* t_dev,
-                                   uint32_t problem, uint32_t chain0) {
+                                   uint32_t problem, uint32_t chain0,
+                                   const double* __restrict__ bm_tab) {
   const int nblk = (d + 3) >> 2;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long long)n_chains * nblk) return;
@@ -22,7 +23,7 @@ __global__ void draw_nu_f64_kernel(double* __restrict__ nu, int n_chains, int d,
   uint32_t r[4];
   rng_block(seed, (uint32_t)n, chain0 + (uint32_t)c, t, problem, 0u, r);
   double z[4];
-  box_muller4(r, z);
+  box_muller4(r, z, bm_tab);
   double* row = nu + (size_t)c * ld + 4 * n;
   const int left = d - 4 * n;
   if (left >= 4 && ((reinterpret_cast<uintptr_t>(row) & 15) == 0)) {
@@ -140,12 +141,13 @@ inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block 
 }  // namespace
 
 cudaError_t launch_draw_nu_f64(double* nu, int n_chains, int d, int ld, uint64_t seed, uint32_t t,
-                               uint32_t problem, uint32_t chain0, cudaStream_t s,
-                               const unsigned* t_dev) {
+                               uint32_t problem, uint32_t chain0, const double* bm_tab,
+                               cudaStream_t s, const unsigned* t_dev) {
   const long long n = (long long)n_chains * ((d + 3) / 4);
   if (n == 0) return cudaSuccess;
+  if (bm_tab == nullptr) return cudaErrorInvalidValue;
   draw_nu_f64_kernel<<<grid_for(n, 256), 256, 0, s>>>(nu, n_chains, d, ld, seed, t, t_dev,
-                                                      problem, chain0);
+                                                      problem, chain0, bm_tab);
   return cudaGetLastError();
 }
 
