@@ -243,6 +243,36 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// The float f times 2^sh as a double, built from f's bits (exact; no FP64
+// instruction): f must be zero or normal and f 2^sh inside double's normal
+// range.
+__device__ __forceinline__ double f2d_shifted(float f, int sh) {
+  const unsigned u = __float_as_uint(f);
+  if ((u & 0x7FFFFFFFu) == 0u) return 0.0;
+  const unsigned dexp = ((u >> 23) & 0xFFu) + 896u + (unsigned)sh;
+  const unsigned hiw = (u & 0x80000000u) | (dexp << 20) | ((u & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hiw, (int)(u << 29));
+}
+
+// (hi + lo) rs cs rounded once to double, where rs and cs are powers of two
+// (or zero) and hi, lo the error-free float pair of an exact product: every
+// nonzero hi, lo is a multiple of 2^-63 (integers times 2^-shift), hence a
+// normal float.  With normal rs and cs the scales go into the exponents by
+// integer operations and one FP64 addition rounds (the same double as
+// ((double)hi + (double)lo) * rs * cs, whose multiplications are exact);
+// otherwise that expression is evaluated as written.  The FP64 pipe of
+// GB300 is narrow, and this runs for every entry of an FP64 product.
+__device__ __forceinline__ double scaled_pair_sum(float hi, float lo, float rs, float cs) {
+  const unsigned ur = __float_as_uint(rs), uc = __float_as_uint(cs);
+  const unsigned er = (ur >> 23) & 0xFFu, ec = (uc >> 23) & 0xFFu;
+  if (er == 0u || ec == 0u || er == 0xFFu || ec == 0xFFu || (ur & 0x7FFFFFu) != 0u ||
+      (uc & 0x7FFFFFu) != 0u)
+    return ((double)hi + (double)lo) * (double)rs * (double)cs;
+  const int sh = (int)er + (int)ec - 254;  // log2 |rs cs|
+  const double v = f2d_shifted(hi, sh) + f2d_shifted(lo, sh);
+  return ((ur ^ uc) & 0x80000000u) ? -v : v;
+}
+
 template <int BN>
 constexpr uint32_t tmem_cols_for(int groups) {
   return groups * BN <= 32 ? 32u : groups * BN <= 64 ? 64u : groups * BN <= 128 ? 128u
@@ -554,8 +584,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ TcAr
             for (int jj = 0; jj < 16; ++jj) {
               const int col = n0 + j0 + jj;
               if (col < args.n_cols) {
-                const double v = ((double)hi[j0 + jj] + (double)lo[j0 + jj]) * (double)rs *
-                                 (double)args.col_scale[col];
+                const double v = scaled_pair_sum(hi[j0 + jj], lo[j0 + jj], rs, args.col_scale[col]);
                 if (d64) drift64 = fmax(drift64, fabs(v - old[jj]) * (double)args.inv_anorm[col]);
                 prow64[j0 + jj] = v;
               }
