@@ -138,11 +138,13 @@ __device__ __forceinline__ int classify_row(T p, T q, T b, double b64, T tlo, T 
     }
     ratio = b64 / r;
     if (ratio >= 1.0) return kRowNone;
-    if (fabs(ratio) > tlo || r < 1e-30) return kRowKeep;
+    // rows whose p, q do not fit float's normal range are kept (exact roots)
+    if (fabs(ratio) > tlo || r < 1e-30 || r > 1e30) return kRowKeep;
   }
   float tau = atan2_poly((float)q, (float)p);
   if (tau < 0.f) tau += kTwoPiF;
-  if (tau < 0.02f || tau > kTwoPiF - 0.02f) return kRowKeep;
+  // (written so that a NaN angle keeps the row)
+  if (!(tau >= 0.02f && tau <= kTwoPiF - 0.02f)) return kRowKeep;
   const float h = acos_poly((float)ratio);
   a_ap = fmaxf(0.f, tau - h);
   b_ap = fminf(kTwoPiF, tau + h);

@@ -146,6 +146,24 @@ def test_sort_reduction_through_kernel():
     np.testing.assert_allclose(got[1:-1, 0], order[:-1] + eps, atol=1e-12)
 
 
+def test_rows_beyond_float_range():
+    """FP64 chains classify rows in FP32 (integer double-to-float rounding):
+    rows scaled by 1e40 (p, q, b overflow float) and by 1e-41 (they vanish
+    in float) are kept for exact FP64 roots, so the step still equals the
+    oracle's; the halfspaces are the unscaled ones, so the pieces are too."""
+    rng = np.random.default_rng(41)
+    d, m, n = 7, 60, 40
+    A, b, X = feasible_instance(rng, d, m, n)
+    A[:12] *= 1e40
+    b[:12] *= 1e40
+    A[12:24] *= 1e-41
+    b[12:24] *= 1e-41
+    NU = rng.standard_normal((n, d))
+    U = rng.uniform(size=n)
+    for sort_threads in (0, 256):
+        check_fp64(A, b, X, NU, U, sort_threads=sort_threads)
+
+
 def test_single_chain_and_trim():
     rng = np.random.default_rng(13)
     A, b, X = feasible_instance(rng, 12, 40, 1)
