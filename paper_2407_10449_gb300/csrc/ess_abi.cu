@@ -706,6 +706,12 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
     return fail(ESS_ERR_ARG, "tangent_thresh in [0, 1), trim_eps >= 0, residual_margin >= 0");
   if (c.fp64_products != ESS_PRODUCTS_DFMA && c.fp64_products != ESS_PRODUCTS_SPLIT)
     return fail(ESS_ERR_ARG, "unknown fp64_products");
+  if ((c.precision == ESS_PREC_MIXED || c.fp64_products == ESS_PRODUCTS_SPLIT) &&
+      !ess::rows_fit_float_scales(A, b, m, d, c.precision == ESS_PREC_MIXED))
+    return fail(ESS_ERR_ARG,
+                "a row of A (or an entry of b) is outside the float scaling range of the mixed "
+                "form and of split products (nonzero row maxima in [2^-100, 2^100], |b| <= "
+                "2^100); the FP64 form with DFMA products takes any finite values");
   if (c.q_tile != 0 &&
       std::find(ess::kTcWidths, ess::kTcWidths + 16, c.q_tile) == ess::kTcWidths + 16)
     return fail(ESS_ERR_ARG,

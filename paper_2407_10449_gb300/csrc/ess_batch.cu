@@ -765,6 +765,14 @@ ess_status ess_batch_create(int n_problems, const int* d, const int* m, const do
       delete s;
       return bfail(ESS_ERR_ARG, "b has a non-finite entry");
     }
+  if (bmixed(s))
+    for (int p = 0; p < n_problems; ++p)
+      if (!ess::rows_fit_float_scales(A + s->a_off[p], b + s->b_off[p], m[p], d[p], true)) {
+        delete s;
+        return bfail(ESS_ERR_ARG,
+                     "a row of A or an entry of b is outside the mixed form's float scaling "
+                     "range (nonzero row maxima in [2^-100, 2^100], |b| <= 2^100)");
+      }
   s->chain_threads = ess::chain_threads_for(s->max_m);
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);

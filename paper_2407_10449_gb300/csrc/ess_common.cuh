@@ -23,6 +23,22 @@ constexpr float kTwoPiF = 6.28318548202514648f;  // 2 pi rounded to float (upwar
 // nu * 2^12 stays below 2^15, inside the fp16 range, with no per-chain scan.
 constexpr float kNuSplitScale = 4096.f;
 
+// Host: whether the m x d rows of A (and, with check_b, the entries of b) fit
+// the float power-of-two scalings of the mixed form and of the split FP64
+// products: every nonzero row's largest |a_ij| in [2^-100, 2^100], and
+// |b_i| <= 2^100 when check_b.
+inline bool rows_fit_float_scales(const double* A, const double* b, long long m, long long d,
+                                  bool check_b) {
+  const double lo = 7.888609052210118e-31, hi = 1.2676506002282294e30;  // 2^-100, 2^100
+  for (long long i = 0; i < m; ++i) {
+    double mx = 0.0;
+    for (long long j = 0; j < d; ++j) mx = std::fmax(mx, std::fabs(A[i * d + j]));
+    if (mx != 0.0 && (mx < lo || mx > hi)) return false;
+    if (check_b && std::fabs(b[i]) > hi) return false;
+  }
+  return true;
+}
+
 // Device-side counters of one launch sequence (accumulated over a run).
 struct DevStats {
   unsigned long long steps;

@@ -73,3 +73,34 @@ def test_argument_errors_without_gpu():
     with pytest.raises(ess.EssError) as e:
         ess.ess_whiten(np.zeros((0, 3)), np.zeros(0), None, np.eye(3))
     assert e.value.status == ess.ESS_ERR_ARG
+
+
+def test_float_scaling_range_is_checked_without_gpu():
+    """The mixed form (A and b in float with power-of-two row scales) and the
+    FP64 form's split products (row scales kept as floats) refuse rows whose
+    largest entry lies outside [2^-100, 2^100] (and, for the mixed form, b
+    beyond 2^100) before touching the GPU; the batched mixed form likewise."""
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((6, 4))
+    b = np.ones(6)
+    cases = []
+    for scale in (1e40, 1e-41):
+        A2 = A.copy()
+        A2[2] *= scale
+        cases += [(A2, b, dict(precision=ess.ESS_PREC_MIXED)),
+                  (A2, b, dict(precision=ess.ESS_PREC_FP64,
+                               fp64_products=ess.ESS_PRODUCTS_SPLIT))]
+    b2 = b.copy()
+    b2[4] = 1e35
+    cases.append((A, b2, dict(precision=ess.ESS_PREC_MIXED)))
+    for Ax, bx, cfg in cases:
+        with pytest.raises(ess.EssError) as e:
+            ess.Sampler(Ax, bx, **cfg)
+        assert e.value.status == ess.ESS_ERR_ARG
+        assert "float scaling range" in str(e.value)
+    A3 = A.copy()
+    A3[1] *= 1e40
+    with pytest.raises(ess.EssError) as e:
+        ess.BatchSampler([A, A3], [b, b], precision=ess.ESS_PREC_MIXED)
+    assert e.value.status == ess.ESS_ERR_ARG
+
