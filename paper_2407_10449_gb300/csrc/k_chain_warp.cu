@@ -77,6 +77,14 @@ __device__ __forceinline__ int pbucket(float pa) {
   return min(max(k, 0), kWB - 3);
 }
 
+// A double's bits as a signed integer in the order of the values (negative
+// values mirrored below zero): x < y for finite x, y exactly when
+// ordered_bits(x) < ordered_bits(y), except that -0 orders below +0.
+__device__ __forceinline__ long long ordered_bits(double x) {
+  const long long v = __double_as_longlong(x);
+  return v < 0 ? v ^ 0x7FFFFFFFFFFFFFFFll : v;
+}
+
 // In-place inclusive prefix max of kWB bucket maxima (float bits, >= 0).
 __device__ __forceinline__ void prefix_max(unsigned* b, int lane) {
   unsigned run = 0u;
@@ -522,7 +530,14 @@ chain_warp_kernel(ChainParams<T> prm) {
           if (i < m) {
             const T pn = pv[k] * cs + qv[k] * sn;
             prow_out[i] = pn;
-            if (!(pn <= sv[k])) flags |= 1u << k;
+            if constexpr (sizeof(T) == 8) {
+              // pn > sv on the doubles' bits mapped to ordered integers (no
+              // FP64 instruction); a NaN pn also marks the chain bad, which
+              // rejects the move
+              if (ordered_bits(pn) > ordered_bits(sv[k])) flags |= 1u << k;
+            } else {
+              if (!(pn <= sv[k])) flags |= 1u << k;
+            }
           }
         }
         // rows near their bound are rare: one vote per batch, then per slot
