@@ -706,12 +706,16 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
     return fail(ESS_ERR_ARG, "tangent_thresh in [0, 1), trim_eps >= 0, residual_margin >= 0");
   if (c.fp64_products != ESS_PRODUCTS_DFMA && c.fp64_products != ESS_PRODUCTS_SPLIT)
     return fail(ESS_ERR_ARG, "unknown fp64_products");
-  if ((c.precision == ESS_PREC_MIXED || c.fp64_products == ESS_PRODUCTS_SPLIT) &&
-      !ess::rows_fit_float_scales(A, b, m, d, c.precision == ESS_PREC_MIXED))
+  if (c.precision == ESS_PREC_MIXED && !ess::rows_fit_float_scales(A, b, m, d, true, 30))
     return fail(ESS_ERR_ARG,
-                "a row of A (or an entry of b) is outside the float scaling range of the mixed "
-                "form and of split products (nonzero row maxima in [2^-100, 2^100], |b| <= "
-                "2^100); the FP64 form with DFMA products takes any finite values");
+                "a row of A or an entry of b is outside the mixed form's float scaling range "
+                "(nonzero row maxima in [2^-30, 2^30], |b| <= 2^30); the FP64 form takes any "
+                "finite values");
+  if (c.precision == ESS_PREC_FP64 && c.fp64_products == ESS_PRODUCTS_SPLIT &&
+      !ess::rows_fit_float_scales(A, b, m, d, false, 100))
+    return fail(ESS_ERR_ARG,
+                "a row of A is outside the float scaling range of split products (nonzero row "
+                "maxima in [2^-100, 2^100]); DFMA products take any finite values");
   if (c.q_tile != 0 &&
       std::find(ess::kTcWidths, ess::kTcWidths + 16, c.q_tile) == ess::kTcWidths + 16)
     return fail(ESS_ERR_ARG,

@@ -767,11 +767,11 @@ ess_status ess_batch_create(int n_problems, const int* d, const int* m, const do
     }
   if (bmixed(s))
     for (int p = 0; p < n_problems; ++p)
-      if (!ess::rows_fit_float_scales(A + s->a_off[p], b + s->b_off[p], m[p], d[p], true)) {
+      if (!ess::rows_fit_float_scales(A + s->a_off[p], b + s->b_off[p], m[p], d[p], true, 30)) {
         delete s;
         return bfail(ESS_ERR_ARG,
                      "a row of A or an entry of b is outside the mixed form's float scaling "
-                     "range (nonzero row maxima in [2^-100, 2^100], |b| <= 2^100)");
+                     "range (nonzero row maxima in [2^-30, 2^30], |b| <= 2^30)");
       }
   s->chain_threads = ess::chain_threads_for(s->max_m);
   int smem_optin = 0;

@@ -23,13 +23,14 @@ constexpr float kTwoPiF = 6.28318548202514648f;  // 2 pi rounded to float (upwar
 // nu * 2^12 stays below 2^15, inside the fp16 range, with no per-chain scan.
 constexpr float kNuSplitScale = 4096.f;
 
-// Host: whether the m x d rows of A (and, with check_b, the entries of b) fit
-// the float power-of-two scalings of the mixed form and of the split FP64
-// products: every nonzero row's largest |a_ij| in [2^-100, 2^100], and
-// |b_i| <= 2^100 when check_b.
+// Host: whether every nonzero row of the m x d matrix A has its largest |a_ij|
+// in [2^-e, 2^e] (and, with check_b, |b_i| <= 2^e).  The split FP64 products
+// keep per-row power-of-two scales as floats (e = 100).  The mixed form keeps
+// A, b, p and q in float and compares b^2 with p^2 + q^2, which must neither
+// overflow nor flush to zero for |x| and |nu| of the order of 1 (e = 30).
 inline bool rows_fit_float_scales(const double* A, const double* b, long long m, long long d,
-                                  bool check_b) {
-  const double lo = 7.888609052210118e-31, hi = 1.2676506002282294e30;  // 2^-100, 2^100
+                                  bool check_b, int e) {
+  const double hi = std::ldexp(1.0, e), lo = std::ldexp(1.0, -e);
   for (long long i = 0; i < m; ++i) {
     double mx = 0.0;
     for (long long j = 0; j < d; ++j) mx = std::fmax(mx, std::fabs(A[i * d + j]));

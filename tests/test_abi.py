@@ -76,10 +76,11 @@ def test_argument_errors_without_gpu():
 
 
 def test_float_scaling_range_is_checked_without_gpu():
-    """The mixed form (A and b in float with power-of-two row scales) and the
-    FP64 form's split products (row scales kept as floats) refuse rows whose
-    largest entry lies outside [2^-100, 2^100] (and, for the mixed form, b
-    beyond 2^100) before touching the GPU; the batched mixed form likewise."""
+    """The mixed form (A, b, p, q in float; b^2 against p^2 + q^2) refuses
+    rows whose largest entry lies outside [2^-30, 2^30] and b beyond 2^30;
+    the FP64 form's split products (row scales kept as floats) refuse rows
+    outside [2^-100, 2^100].  Both before touching the GPU; the batched
+    mixed form likewise."""
     rng = np.random.default_rng(3)
     A = rng.standard_normal((6, 4))
     b = np.ones(6)
@@ -91,13 +92,16 @@ def test_float_scaling_range_is_checked_without_gpu():
                   (A2, b, dict(precision=ess.ESS_PREC_FP64,
                                fp64_products=ess.ESS_PRODUCTS_SPLIT))]
     b2 = b.copy()
-    b2[4] = 1e35
+    b2[4] = 1e10
     cases.append((A, b2, dict(precision=ess.ESS_PREC_MIXED)))
+    A4 = A.copy()
+    A4[0] *= 1e12  # inside the split products' range, outside the mixed form's
+    cases.append((A4, b, dict(precision=ess.ESS_PREC_MIXED)))
     for Ax, bx, cfg in cases:
         with pytest.raises(ess.EssError) as e:
             ess.Sampler(Ax, bx, **cfg)
         assert e.value.status == ess.ESS_ERR_ARG
-        assert "float scaling range" in str(e.value)
+        assert "scaling range" in str(e.value)
     A3 = A.copy()
     A3[1] *= 1e40
     with pytest.raises(ess.EssError) as e:
