@@ -109,6 +109,27 @@ __device__ __forceinline__ float acos_poly(float x) {  // x in [-1, 1]
   return x < 0.f ? 3.1415927f - v : v;
 }
 
+// A double rounded to float by integer operations on its two halves, so that
+// the FP64 chains' classification (three conversions per row) leaves the
+// narrow FP64 pipe to the FP64 work proper.  Values in float's normal range
+// are rounded to nearest (ties away from zero: error at most half an ulp,
+// 2^-24 relative); values below it become zero, finite values above it
+// become infinity, and NaN stays NaN.  The classification keeps rows whose
+// float p, q or b is zero or non-finite where that decides the class (r = 0 or
+// a non-finite r^2).
+__device__ __forceinline__ float dbl_to_flt_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned dexp = (hi >> 20) & 0x7FFu;
+  const int e = (int)dexp - 896;  // float exponent field for normal values
+  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  unsigned bits = (sign | ((unsigned)e << 23) | mant) + ((lo >> 28) & 1u);
+  bits = e <= 0 ? sign : bits;
+  bits = e >= 255 ? (sign | 0x7F800000u) : bits;
+  bits = dexp == 0x7FFu && ((hi & 0xFFFFFu) | lo) != 0u ? 0x7FC00000u : bits;
+  return __uint_as_float(bits);
+}
+
 // Row classification of the prune: the has-root decision is exactly the one
 // roots() takes; rows near tangency (where arccos is ill-conditioned) or with
 // tau close to the 0 / 2 pi cut are never dropped.
@@ -117,8 +138,10 @@ enum : int { kRowNone = 0, kRowApprox = 1, kRowKeep = 2 };
 template <typename T>
 __device__ __forceinline__ int classify_row(T p, T q, T b, double b64, T tlo, T thi, float& a_ap,
                                             float& b_ap, bool& infeasible) {
-  T ratio;
+  float pf, qf, ratio;
   if constexpr (sizeof(T) == 4) {
+    pf = p;
+    qf = q;
     const float r2 = fmaf(p, p, q * q);
     if (r2 == 0.0f) {
       infeasible = b64 < 0.0;
@@ -131,21 +154,24 @@ __device__ __forceinline__ int classify_row(T p, T q, T b, double b64, T tlo, T 
     if (ratio >= thi * 1.000001f) return kRowNone;
     if (fabsf(ratio) > tlo * 0.999999f) return kRowKeep;
   } else {
-    const double r = sqrt(p * p + q * q);
-    if (r == 0.0) {
-      infeasible = b64 < 0.0;
-      return kRowNone;
-    }
-    ratio = b64 / r;
-    if (ratio >= 1.0) return kRowNone;
-    // rows whose p, q do not fit float's normal range are kept (exact roots)
-    if (fabs(ratio) > tlo || r < 1e-30 || r > 1e30) return kRowKeep;
+    // FP64 chains: the same float decisions on p, q, b rounded by integer
+    // operations (no FP64 instruction; the rounding adds at most 2^-23 to the
+    // error of b / r, well inside the 1e-6 slack).  Rows whose r^2 leaves
+    // [1e-30, 1e30] in float -- including r = 0, decided by the exact roots --
+    // are kept.
+    pf = dbl_to_flt_bits(p);
+    qf = dbl_to_flt_bits(q);
+    const float r2 = fmaf(pf, pf, qf * qf);
+    if (!(r2 >= 1e-30f && r2 <= 1e30f)) return kRowKeep;
+    ratio = dbl_to_flt_bits(b) * rsqrtf(r2);
+    if (ratio >= (float)thi * 1.000001f) return kRowNone;
+    if (fabsf(ratio) > (float)tlo * 0.999999f) return kRowKeep;
   }
-  float tau = atan2_poly((float)q, (float)p);
+  float tau = atan2_poly(qf, pf);
   if (tau < 0.f) tau += kTwoPiF;
   // (written so that a NaN angle keeps the row)
   if (!(tau >= 0.02f && tau <= kTwoPiF - 0.02f)) return kRowKeep;
-  const float h = acos_poly((float)ratio);
+  const float h = acos_poly(ratio);
   a_ap = fmaxf(0.f, tau - h);
   b_ap = fminf(kTwoPiF, tau + h);
   return kRowApprox;
@@ -212,27 +238,6 @@ __device__ __forceinline__ int classify_phi_nb(float p, float q, float b, float 
   cls = b >= 0.f && b2 >= thi2 * r2 ? kRowNone : cls;    // b / r >= 1 + thresh (with slack)
   zero = r2 == 0.0f;
   return zero ? kRowNone : cls;
-}
-
-// A double rounded to float by integer operations on its two halves, so that
-// the FP64 chains' classification (three conversions per row) leaves the
-// narrow FP64 pipe to the FP64 work proper.  Values in float's normal range
-// are rounded to nearest (ties away from zero: error at most half an ulp,
-// 2^-24 relative); values below it become zero, finite values above it
-// become infinity, and NaN stays NaN.  The classification keeps rows whose
-// float p, q or b is zero or non-finite where that decides the class (r = 0 or
-// a non-finite r^2).
-__device__ __forceinline__ float dbl_to_flt_bits(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  const unsigned sign = hi & 0x80000000u;
-  const unsigned dexp = (hi >> 20) & 0x7FFu;
-  const int e = (int)dexp - 896;  // float exponent field for normal values
-  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-  unsigned bits = (sign | ((unsigned)e << 23) | mant) + ((lo >> 28) & 1u);
-  bits = e <= 0 ? sign : bits;
-  bits = e >= 255 ? (sign | 0x7F800000u) : bits;
-  bits = dexp == 0x7FFu && ((hi & 0xFFFFFu) | lo) != 0u ? 0x7FC00000u : bits;
-  return __uint_as_float(bits);
 }
 
 __device__ __forceinline__ int classify_phi_d(double p, double q, double b, float tlo2,
