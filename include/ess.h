@@ -320,20 +320,26 @@ ess_status ess_whitener_apply(ess_whitener *whitener, const void *U, int u_doubl
 /*
  * One FP64 chain step that allocates no device memory (the paper has no
  * counterpart; this is a service for callers that may not call cudaMalloc,
- * e.g. plugins whose host framework owns the device-memory budget, request
- * paths that must stay off the allocator, or threads whose stream is being
- * captured).  Same map and results as ess_step_with_draws in the FP64 form,
- * without an ess_state:
- *   A, b        device, m x d and m doubles (the polytope A x <= b).
- *   X, nu, u    device inputs as in ess_step_with_draws.
- *   X_next      device output, n_chains x d doubles.
- *   theta, rejected   device outputs or NULL.
+ * e.g. plugins whose host framework owns the device-memory budget, or request
+ * paths that must stay off the allocator and its implicit synchronization).
+ * Same map and results as ess_step_with_draws in the FP64 form, without an
+ * ess_state:
+ *   A, b        device, m x d row-major and m doubles (the polytope A x <= b).
+ *   X, nu, u    device inputs as in ess_step_with_draws (n_chains x d, n_chains x d,
+ *               n_chains doubles, row-major, contiguous).
+ *   X_next      device output, n_chains x d doubles (must not overlap X).
+ *   theta, rejected   device outputs (n_chains doubles / ints) or NULL.
  * All scratch lives in one library-owned device array of
  * ESS_NOALLOC_SCRATCH_BYTES per GPU (allocated when the library is loaded,
- * kept until exit): 16 * n_chains * m + 8 * m bytes (plus 512) must fit, else
- * ESS_ERR_ARG.  Calls share that array: calls that overlap on the GPU race, so
- * serialize them.  The first call on a device looks up the array's device
- * address; make it before any stream capture.  Synchronous.
+ * kept until exit), every region rounded up to 256 bytes: with r(v) = v
+ * rounded up to a multiple of 256, 512 + r(8 m) + 2 r(8 n_chains m) bytes
+ * must fit (e.g. 512 chains at m = 2000), else ESS_ERR_ARG.  m > 8192, or a d
+ * whose x' does not fit the chain-step kernel's shared memory beside the
+ * arcs, gives ESS_ERR_UNSUPPORTED (as in ess_create).  Calls share that
+ * array: calls that overlap on the GPU race, so serialize them.  The start
+ * points are checked in FP64 first: an infeasible X gives
+ * ESS_ERR_INFEASIBLE_X0 with X_next, theta and rejected untouched.
+ * Synchronous (reads a status word back and waits for cuda_stream).
  */
 #define ESS_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 ess_status ess_step_noalloc(const double *A, const double *b, int d, int m, const double *X,

@@ -317,15 +317,40 @@ def ess_step_noalloc(A, b, X, nu, u, X_next, theta=None, rejected=None, stream=N
     """FP64 one-step map without any device allocation (see include/ess.h).
 
     For callers that may not allocate device memory at call time (a host
-    framework owning the memory budget, an allocation-free request path, a
-    thread whose stream is being captured).  A, b, X, nu, u, X_next (and the
-    optional theta, rejected) are CUDA tensors; scratch comes from a fixed
-    16 MiB array inside the library, so calls must not overlap on the GPU."""
+    framework owning the memory budget, an allocation-free request path).
+    A (m, d), b (m,), X, nu, X_next (n, d), u (n,) and the optional theta (n,)
+    and rejected (n, int32) are contiguous float64 CUDA tensors on one device;
+    scratch comes from a fixed 16 MiB array inside the library, so calls must
+    not overlap on the GPU.  Synchronous."""
+    import torch
+    if A.dim() != 2:
+        raise ValueError("A must be (m, d)")
     m, d = A.shape
-    n = X.shape[0]
-    _check(load().ess_step_noalloc(_ptr(A), _ptr(b), d, m, _ptr(X), _ptr(nu), _ptr(u), n,
-                                   _ptr(X_next), _ptr(theta), _ptr(rejected),
-                                   _stream_ptr(stream)))
+    n = X.shape[0] if X.dim() == 2 else -1
+    want = [("A", A, (m, d)), ("b", b, (m,)), ("X", X, (n, d)), ("nu", nu, (n, d)),
+            ("u", u, (n,)), ("X_next", X_next, (n, d))]
+    if theta is not None:
+        want.append(("theta", theta, (n,)))
+    if rejected is not None:
+        want.append(("rejected", rejected, (n,)))
+    devices = set()
+    for name, t, shape in want:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        dtype = torch.int32 if name == "rejected" else torch.float64
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype}")
+        if tuple(t.shape) != shape:
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {shape}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        devices.add(t.device)
+    if len(devices) != 1:
+        raise ValueError("all tensors must be on one device")
+    with torch.cuda.device(devices.pop()):
+        _check(load().ess_step_noalloc(_ptr(A), _ptr(b), d, m, _ptr(X), _ptr(nu), _ptr(u), n,
+                                       _ptr(X_next), _ptr(theta), _ptr(rejected),
+                                       _stream_ptr(stream)))
 
 
 def ess_whitener_create(L, mu=None):

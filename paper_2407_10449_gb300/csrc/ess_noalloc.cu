@@ -2,10 +2,10 @@
 //
 // Who needs this: callers that are not allowed to call cudaMalloc at the point
 // where they want a step -- a plugin running inside a host framework that owns
-// the whole device-memory budget and forbids allocations after start-up, a
+// the whole device-memory budget and forbids allocations after start-up, or a
 // latency-critical service that must keep the allocator (and its implicit
-// device synchronization) off its request path, or code running in a thread
-// whose CUDA stream is being captured, where allocation calls are an error.
+// device synchronization) off its request path.  The call is synchronous: it
+// reads a status word back to the host and waits for the caller's stream.
 // ess_step_noalloc gives them the FP64 one-step map of ess_step_with_draws
 // without an ess_state: the caller passes A, b and every input and output as
 // device pointers, and all scratch (the row norms of A, the products p = A x
@@ -22,7 +22,16 @@
 // Host code cannot use the array's name as a device address (on the host it
 // names a host-side stand-in).  The address is looked up once per device with
 // cudaGetSymbolAddress, with that device current, the first time the entry
-// point runs on it; make that first call before any stream capture begins.
+// point runs on it.
+//
+// Scratch layout, every region starting on a 256-byte boundary (r(v) = v
+// rounded up to a multiple of 256):
+//   status word              256 bytes
+//   counters (DevStats)      r(sizeof(DevStats)) = 256 bytes
+//   row norms of A           r(8 m)
+//   P = A x                  r(8 n m)
+//   Q = A nu                 r(8 n m)
+// so a call needs 512 + r(8 m) + 2 r(8 n m) <= ESS_NOALLOC_SCRATCH_BYTES.
 #include <mutex>
 #include <string>
 
@@ -101,12 +110,22 @@ extern "C" ess_status ess_step_noalloc(const double* A, const double* b, int d, 
   const size_t pq = round_up(sizeof(double) * (size_t)n_chains * (size_t)m);
   const size_t need = off_p + 2 * pq;
   if (need > kScratchBytes)
-    return fail(ESS_ERR_ARG, "n_chains * m too large for the fixed scratch of ess_step_noalloc "
-                             "(2 * 8 * n_chains * m + 8 * m bytes must fit in 16 MiB)");
+    return fail(ESS_ERR_ARG,
+                "n_chains * m too large for the fixed scratch of ess_step_noalloc: "
+                "512 + r(8 m) + 2 r(8 n_chains m) bytes must fit in 16 MiB, r(v) = v rounded "
+                "up to a multiple of 256 (need " + std::to_string(need) + ")");
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  // the CTA-per-chain kernel keeps x' (d values) beside the arcs in shared
+  // memory: the same limit as ess_create
+  int smem_optin = 0;
+  e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+  if (ess::chain_smem_bytes<double>(threads, d) + 1024 > (size_t)smem_optin)
+    return fail(ESS_ERR_UNSUPPORTED, "d too large for the chain-step kernel's shared memory");
+
   unsigned char* base = nullptr;
   e = scratch_address(dev, &base);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
@@ -116,17 +135,23 @@ extern "C" ess_status ess_step_noalloc(const double* A, const double* b, int d, 
   double* P = reinterpret_cast<double*>(base + off_p);
   double* Q = reinterpret_cast<double*>(base + off_p + pq);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int h = 0;
 
   // the array keeps the previous call's contents: clear what must start at zero
   e = cudaMemsetAsync(base, 0, off_norm, st);
-  if (e == cudaSuccess) {
-    noalloc_row_norms<<<(m * 32 + 255) / 256, 256, 0, st>>>(A, d, m, anorm);
-    e = cudaGetLastError();
-  }
   if (e == cudaSuccess)
     e = ess::launch_gemm_nt_f64<double, double>(X, d, A, d, P, m, n_chains, m, d, nullptr,
                                                 nullptr, st);
   if (e == cudaSuccess) e = ess::launch_check_feasible(P, m, b, n_chains, m, status, st);
+  // the start points are checked before anything is written to the outputs
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "ess_step_noalloc (start-point check)");
+  if (h & ess::kStatusInfeasible)
+    return fail(ESS_ERR_INFEASIBLE_X0, "a chain state violates A x <= b (checked in FP64)");
+
+  noalloc_row_norms<<<(m * 32 + 255) / 256, 256, 0, st>>>(A, d, m, anorm);
+  e = cudaGetLastError();
   if (e == cudaSuccess)
     e = ess::launch_gemm_nt_f64<double, double>(nu, d, A, d, Q, m, n_chains, m, d, nullptr,
                                                 nullptr, st);
@@ -158,7 +183,6 @@ extern "C" ess_status ess_step_noalloc(const double* A, const double* b, int d, 
     e = ess::launch_chain_step<double>(p, threads, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "ess_step_noalloc launch");
-  int h = 0;
   e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "ess_step_noalloc");
