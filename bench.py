@@ -43,8 +43,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--fp64-steps", type=int, default=4)
-    ap.add_argument("--fp64-split-steps", type=int, default=40)
+    ap.add_argument("--fp64-steps", type=int, default=32)
+    ap.add_argument("--fp64-split-steps", type=int, default=64)
     ap.add_argument("--chains", type=int, default=8192)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -68,9 +68,32 @@ def load_peaks():
             "source": "fallback"}
 
 
-# FP64 FMA throughput of this GB300 pool, measured with a DFMA microbenchmark
-# (8 independent FMA chains per thread, 8 CTAs of 256 threads per SM).
+# FP64 throughput, the denominator of the FP64 phases: measured in the run by
+# measure_fp64_peak (cuBLAS DGEMM); this value stands in only if that fails.
 FP64_TFLOPS_MEASURED = 1.19
+FP64_PEAK_SOURCE = "fallback: earlier DFMA microbenchmark on this pool"
+
+
+def measure_fp64_peak(torch, n=4096, reps=3):
+    """FP64 dense throughput of this GPU in this run: the best of `reps`
+    cuBLAS DGEMMs of n x n x n (2 n^3 flops), timed with CUDA events."""
+    global FP64_TFLOPS_MEASURED, FP64_PEAK_SOURCE
+    a = torch.randn((n, n), dtype=torch.float64, device="cuda")
+    b = torch.randn((n, n), dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    FP64_TFLOPS_MEASURED = 2.0 * n**3 / (best * 1e-3) / 1e12
+    FP64_PEAK_SOURCE = f"measured in this run: cuBLAS DGEMM {n}^3, best of {reps}"
+    return FP64_TFLOPS_MEASURED
 
 
 class ClockSampler:
@@ -183,22 +206,40 @@ def source_hash(*names):
     return h.hexdigest()[:12]
 
 
-def ncu_traffic(kernel_key, src_hash):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current source of that kernel (else None)."""
+def ncu_counters(kernel_key, src_hash):
+    """(DRAM bytes, warp instructions) per launch from the committed ncu
+    summary, if it was taken on the current source of that kernel (else
+    (None, None))."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
     if not os.path.exists(path):
-        return None
+        return None, None
     with open(path) as f:
         for line in f:
-            # | kernel_key | src_hash | dram bytes per launch | ... |
+            # | kernel_key | src_hash | dram bytes per launch | warp instructions | ... |
             parts = [p.strip() for p in line.strip().strip("|").split("|")]
-            if len(parts) >= 3 and parts[0] == kernel_key and parts[1] == src_hash:
-                try:
-                    return float(parts[2])
-                except ValueError:
-                    return None
-    return None
+            if len(parts) >= 4 and parts[0] == kernel_key and parts[1] == src_hash:
+                def num(v):
+                    try:
+                        return float(v)
+                    except ValueError:
+                        return None
+                return num(parts[2]), num(parts[3])
+    return None, None
+
+
+def issue_roofline(torch, inst_per_launch, ms_per_launch, sm_mhz):
+    """The SM issue bound of a kernel: warp instructions per launch (ncu) over
+    its live launch time, against one instruction per clock per scheduler
+    (SM count x 4 schedulers x the median SM clock under load)."""
+    if not inst_per_launch or not ms_per_launch:
+        return None
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = sm_mhz or 2070.0
+    peak = sms * 4 * mhz * 1e6
+    ach = inst_per_launch / (ms_per_launch * 1e-3)
+    return {"bound": "issue", "unit": "warp-inst/s", "achieved": ach, "peak": peak,
+            "frac": ach / peak, "inst_per_launch": inst_per_launch, "sm_mhz": mhz,
+            "issue_limited_ms": inst_per_launch / peak * 1e3}
 
 
 def phase_rooflines(inst, n_chains, timing, precision, peaks):
@@ -274,19 +315,36 @@ def phase_rooflines(inst, n_chains, timing, precision, peaks):
     return out
 
 
+REFRESH_K = 32
+
+
+def aligned_warmup(warmup, refresh_k=REFRESH_K):
+    """Warm-up steps that end on a refresh boundary (at least `warmup`), so
+    that the timed window starts with a refresh and holds the refreshes of
+    its steps at their natural frequency (one every refresh_k steps)."""
+    return warmup + (-warmup) % refresh_k
+
+
+def refreshes_in(t0, steps, refresh_k=REFRESH_K):
+    return sum(1 for t in range(t0, t0 + steps) if t % refresh_k == 0)
+
+
 def time_form(ess, torch, inst, precision, n_chains, steps, warmup, seed, world, rank,
-              clocks=None, phase_steps=None):
-    """K steps through ess_chains_step on the run's stream as a user runs them
-    (refresh periods replayed from CUDA graphs), timed by CUDA events; then a
-    second pass with per-phase events (plain launches) for the phase table."""
+              clocks=None, phase_steps=None, keep=0):
+    """Exactly `steps` steps through ess_chains_step on the run's stream as a
+    user runs them (refresh periods replayed from CUDA graphs), starting on a
+    refresh boundary, timed by CUDA events; then a second pass with per-phase
+    events (plain launches) for the phase table.  keep > 0: also returns the
+    states of `keep` chains after the timed steps (host, float64)."""
     prec = ess.ESS_PREC_MIXED if precision == "mixed" else ess.ESS_PREC_FP64
     cfg = {"fp64_products": ess.ESS_PRODUCTS_SPLIT} if precision == "fp64_split" else {}
-    s = ess.Sampler(inst.A, inst.b, precision=prec, **cfg)
+    s = ess.Sampler(inst.A, inst.b, precision=prec, refresh_k=REFRESH_K, **cfg)
     stream = torch.cuda.Stream()
     x0 = torch.as_tensor(inst.X0[0], dtype=torch.float64)
     X = x0.to("cuda").repeat(n_chains, 1).contiguous()
+    w = aligned_warmup(warmup)
     ess.ess_chains_init(s.state, X, n_chains, 0, stream)
-    ess.ess_chains_step(s.state, warmup, seed, stream=stream)
+    ess.ess_chains_step(s.state, w, seed, stream=stream)
     ess.ess_chains_get(s.state, None, stream)
     ess.ess_reset_timing(s.state)
     s.reset_stats()
@@ -303,7 +361,14 @@ def time_form(ess, torch, inst, precision, n_chains, steps, warmup, seed, world,
     clk = clocks.stop() if clocks else None
     torch.cuda.synchronize()
     barrier(world)
-    ess.ess_chains_get(s.state, None, stream)
+    kept = None
+    if keep:
+        out = torch.empty_like(X)
+        ess.ess_chains_get(s.state, out, stream)
+        torch.cuda.synchronize()
+        kept = out[:keep].cpu().numpy().astype("float64")
+    else:
+        ess.ess_chains_get(s.state, None, stream)
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(world, ms)
     launches = sum(t["launches"] for t in ess.ess_get_timing(s.state).values())
@@ -317,7 +382,10 @@ def time_form(ess, torch, inst, precision, n_chains, steps, warmup, seed, world,
     ess.ess_chains_get(s.state, None, stream)
     timing = ess.ess_get_timing(s.state)
     s.close()
-    return ms_max, timing, stats, clk, {"gpu_launches": launches, "graph_launches": graphs}
+    window = {"t0": w, "steps": steps, "refreshes": refreshes_in(w, steps),
+              "refresh_k": REFRESH_K}
+    return ms_max, timing, stats, clk, {"gpu_launches": launches, "graph_launches": graphs,
+                                        "window": window, "states": kept}
 
 
 # FP32 FMA peak of the GPU at the maximum SM clock (152 SMs x 128 FMA/clk x 2
@@ -374,9 +442,10 @@ def time_batch(ess, torch, insts, precision, steps, warmup, seed, peaks):
     As = [i.A for i in insts]
     bs = [i.b for i in insts]
     nc = [i.n_chains for i in insts]
-    s = ess.BatchSampler(As, bs, precision=prec)
+    s = ess.BatchSampler(As, bs, precision=prec, refresh_k=REFRESH_K)
     X = s.pack([i.X0 for i in insts])
     stream = torch.cuda.current_stream()
+    warmup = aligned_warmup(warmup)
     s.run(nc, X, warmup, seed)
     s.reset_stats()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -398,6 +467,8 @@ def time_batch(ess, torch, insts, precision, steps, warmup, seed, peaks):
     phases = batch_phase_rooflines(insts, timing, precision, torch, peaks)
     return {"value": n * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
             "ms_per_step": ms / steps, "chains": n, "graph_launches": info["graph_launches"],
+            "window": {"t0": warmup, "steps": steps, "refreshes": refreshes_in(warmup, steps),
+                       "refresh_k": REFRESH_K},
             "phases": phases, "stats": stats}
 
 
@@ -434,41 +505,47 @@ def time_unwhiten(ess, torch, pb, n, peaks, reps=10):
     return out
 
 
-def time_configs(ess, torch, workloads, peaks, seed):
+def time_configs(ess, torch, workloads, peaks, seed, errors=True):
     """The other configurations, both forms, short runs (parity-tested
     elsewhere; reported here with their phase rooflines)."""
     from types import SimpleNamespace
     out = {}
-    singles = [("small_d10_m20_c16", workloads.small(n_chains=1), 16, (200, 200)),
-               ("medium_d100_m200_c1024", workloads.medium(n_chains=1), 1024, (200, 100))]
+    singles = [("small_d10_m20_c16", workloads.small(n_chains=1), 16, (192, 192)),
+               ("medium_d100_m200_c1024", workloads.medium(n_chains=1), 1024, (192, 96))]
     pb = workloads.probit(n_chains=1)
     Aw, bw = ess.ess_whiten(pb["A0"], pb["b"], pb["mu"], pb["L"])
     singles.append(("probit_n2000_c4096",
                     SimpleNamespace(A=Aw, b=bw, X0=pb["X0"], d=Aw.shape[1], m=Aw.shape[0]),
-                    4096, (64, 3)))
+                    4096, (64, 32)))
     for name, inst, C, (st_mixed, st_fp64) in singles:
         entry = {}
         for form, steps in (("mixed", st_mixed), ("fp64", st_fp64),
-                            ("fp64_split", max(st_fp64, min(st_mixed, 40)))):
-            ms, timing, stats, _, lc = time_form(ess, torch, inst, form, C, steps, 3, seed, 1, 0)
+                            ("fp64_split", max(st_fp64, min(st_mixed, 64)))):
+            ms, timing, stats, _, lc = time_form(ess, torch, inst, form, C, steps, 3, seed, 1, 0,
+                                                 keep=ERR_SAMPLE if errors else 0)
             ph = phase_rooflines(inst, C, timing, form, peaks)
             dom = max(ph, key=lambda k: ph[k]["share"]) if ph else None
             entry[form] = {"value": C * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
-                           "ms_per_step": ms / steps,
+                           "ms_per_step": ms / steps, "window": lc["window"],
                            "dominant": dom, "dominant_frac": ph[dom]["frac"] if dom else None,
                            "phases": ph, "graph_launches": lc["graph_launches"],
                            "rejections": stats["rejections"],
                            "numeric_errors": stats["numeric_errors"]}
+            if errors:
+                entry[form]["error_vs_oracle"] = oracle_errors(ess, torch, inst.A, inst.b,
+                                                               lc["states"], form, seed)
         out[name] = entry
     out["probit_n2000_c4096"]["unwhiten"] = time_unwhiten(ess, torch, pb, 4096, peaks)
     insts = workloads.batched()
     entry = {}
-    for form, steps in (("mixed", 64), ("fp64", 8)):
+    for form, steps in (("mixed", 64), ("fp64", 32)):
         r = time_batch(ess, torch, insts, form, steps, 4, seed, peaks)
         ph = r["phases"]
         dom = max(ph, key=lambda k: ph[k]["share"]) if ph else None
         r["dominant"] = dom
         r["dominant_frac"] = ph[dom]["frac"] if dom else None
+        if errors:
+            r["error_vs_oracle"] = batch_oracle_errors(ess, torch, insts, form, seed)
         entry[form] = r
     out["batched_512_problems"] = entry
     return out
@@ -496,6 +573,101 @@ def time_e2e(ess, torch, inst, n_chains, steps, seed, record_every=10):
     return {"value": n_chains * steps / dt, "unit": UNIT,
             "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
             "seconds": dt, "call": "ess_run_host", "record_every": record_every}
+
+
+ERR_SAMPLE = 32
+
+
+def _step_errors(theta_g, x_g, rej_g, refs):
+    """Largest and median angle error (rad) and largest relative iterate error
+    of the GPU's one-step map against the oracle's, plus rejection mismatches."""
+    import numpy as np
+    th_o = np.array([r.theta for r in refs])
+    x_o = np.stack([r.x_next for r in refs])
+    rej_o = np.array([r.rejected for r in refs])
+    dth = np.abs(theta_g - th_o)
+    dx = np.max(np.abs(x_g - x_o) / np.maximum(1.0, np.abs(x_o)), axis=1)
+    return {"chains": int(len(refs)), "max_theta_err_rad": float(dth.max()),
+            "median_theta_err_rad": float(np.median(dth)), "max_x_rel_err": float(dx.max()),
+            "median_x_rel_err": float(np.median(dx)),
+            "rejection_mismatches": int(np.sum(rej_o != (rej_g != 0)))}
+
+
+def oracle_errors(ess, torch, A, b, states, form, seed, n=ERR_SAMPLE):
+    """Part of the CPU-baseline (oracle) leg: one step of `n` chains taken from
+    the states after the timed run, with given draws (seeded numpy normals
+    and uniforms), through ess_step_with_draws on the GPU and through the
+    oracle's one-step map; the mixed form's inputs are rounded to float on
+    both sides, as the mixed form stores them."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed + 17)
+    X = np.asarray(states[:n], dtype=np.float64)
+    NU = rng.standard_normal(X.shape)
+    U = rng.uniform(size=X.shape[0])
+    if form == "mixed":
+        X = X.astype(np.float32).astype(np.float64)
+        NU = NU.astype(np.float32).astype(np.float64)
+    prec = ess.ESS_PREC_MIXED if form == "mixed" else ess.ESS_PREC_FP64
+    cfg = {"fp64_products": ess.ESS_PRODUCTS_SPLIT} if form == "fp64_split" else {}
+    s = ess.Sampler(A, b, precision=prec, **cfg)
+    try:
+        cuda = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+        Xn, th, _, _, rej = s.step_with_draws(cuda(X), cuda(NU), cuda(U))
+        Xn, th, rej = (t.cpu().numpy() for t in (Xn, th, rej))
+    finally:
+        s.close()
+    t0 = time.perf_counter()
+    refs = [oracle.step(A, b, X[c], NU[c], U[c]) for c in range(X.shape[0])]
+    dt = time.perf_counter() - t0
+    out = _step_errors(th, Xn.astype(np.float64), rej, refs)
+    out["oracle_chain_iter_per_s_1core"] = X.shape[0] / dt
+    return out
+
+
+def batch_oracle_errors(ess, torch, insts, form, seed, n=ERR_SAMPLE):
+    """As oracle_errors for the batched sampler: one step of every chain of
+    the batch from its start state with given draws; `n` chains spread over
+    the problems are compared with the oracle (each with its own A, b)."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed + 29)
+    prec = ess.ESS_PREC_MIXED if form == "mixed" else ess.ESS_PREC_FP64
+    As = [i.A for i in insts]
+    bs = [i.b for i in insts]
+    nc = [i.n_chains for i in insts]
+    Xs = [np.asarray(i.X0, dtype=np.float64) for i in insts]
+    NUs = [rng.standard_normal(x.shape) for x in Xs]
+    if form == "mixed":
+        Xs = [x.astype(np.float32).astype(np.float64) for x in Xs]
+        NUs = [v.astype(np.float32).astype(np.float64) for v in NUs]
+    U = rng.uniform(size=sum(nc))
+    s = ess.BatchSampler(As, bs, precision=prec)
+    try:
+        Xn, th, rej = s.step_with_draws(nc, s.pack(Xs), s.pack(NUs),
+                                        torch.tensor(U, dtype=torch.float64, device="cuda"))
+        Xn = s.unpack(Xn, nc)
+        th, rej = th.cpu().numpy(), rej.cpu().numpy()
+    finally:
+        s.close()
+    offs = np.concatenate([[0], np.cumsum(nc)])
+    chains = [(p, c) for p in range(len(insts)) for c in range(nc[p])]
+    pick = rng.choice(len(chains), size=min(n, len(chains)), replace=False)
+    refs, thg, xg, rg = [], [], [], []
+    for k in pick:
+        p, c = chains[k]
+        g = offs[p] + c
+        refs.append(oracle.step(As[p], bs[p], Xs[p][c], NUs[p][c], U[g]))
+        thg.append(th[g])
+        xg.append(np.asarray(Xn[p][c], dtype=np.float64))
+        rg.append(rej[g])
+    dth = np.abs(np.array(thg) - np.array([r.theta for r in refs]))
+    dx = np.array([np.max(np.abs(x - r.x_next) / np.maximum(1.0, np.abs(r.x_next)))
+                   for x, r in zip(xg, refs)])
+    return {"chains": int(len(refs)), "max_theta_err_rad": float(dth.max()),
+            "median_theta_err_rad": float(np.median(dth)), "max_x_rel_err": float(dx.max()),
+            "median_x_rel_err": float(np.median(dx)),
+            "rejection_mismatches": int(sum(bool(r.rejected) != bool(x) for r, x in zip(refs, rg)))}
 
 
 def cpu_baseline(inst_small_fn, n_chains=256, n_iter=4):
@@ -558,23 +730,26 @@ def main():
 
     world, rank, local = dist_setup(args.gpus)
     peaks = load_peaks()
+    fp64_peak = measure_fp64_peak(torch)
     C = args.chains
     inst = workloads.metric(n_chains=1)
     seed = rank_seed(args.seed, rank)
 
     clocks = ClockSampler(local) if rank == 0 else None
+    keep = ERR_SAMPLE if (not args.no_cpu and rank == 0) else 0
     ms, timing, stats, clk, lc = time_form(ess, torch, inst, "mixed", C, args.steps, args.warmup,
-                                           seed, world, rank, clocks)
+                                           seed, world, rank, clocks, keep=keep)
     value = job_throughput(world, C, args.steps, ms)
     if args.mixed_only:
         ms64, timing64, stats64, value64 = float("nan"), {}, {}, None
     else:
-        ms64, timing64, stats64, _, _ = time_form(ess, torch, inst, "fp64", C, args.fp64_steps,
-                                                  3, seed, world, rank, None)
+        ms64, timing64, stats64, _, lc64 = time_form(ess, torch, inst, "fp64", C,
+                                                     args.fp64_steps, 3, seed, world, rank,
+                                                     None, keep=keep)
         value64 = job_throughput(world, C, args.fp64_steps, ms64)
-        ms64s, timing64s, stats64s, _, _ = time_form(ess, torch, inst, "fp64_split", C,
-                                                     args.fp64_split_steps, 3, seed, world,
-                                                     rank, None)
+        ms64s, timing64s, stats64s, _, lc64s = time_form(ess, torch, inst, "fp64_split", C,
+                                                         args.fp64_split_steps, 3, seed, world,
+                                                         rank, None, keep=keep)
         value64s = job_throughput(world, C, args.fp64_split_steps, ms64s)
 
     if rank != 0:
@@ -590,44 +765,67 @@ def main():
                   "chain": ("k_chain_warp.cu", "chain_math.cuh", "k_chain.cu"),
                   "draw": ("k_draw.cu", "ess_common.cuh"), "refresh": ("k_gemm_tc.cu",)}
     src = source_hash(*kernel_src[dominant])
-    traffic = ncu_traffic(f"{dominant}_mixed", src)
+    traffic, inst_count = ncu_counters(f"{dominant}_mixed", src)
     roofline = {"bound": dom["bound"], "kernel": dominant, "achieved": dom["achieved"],
                 "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"],
                 "traffic": traffic, "work_per_launch": dom["work_per_launch"],
                 "peak_source": peaks["source"] if dom["bound"] in ("hbm", "tensor") else
-                "DFMA microbenchmark on this pool"}
+                FP64_PEAK_SOURCE}
+    # the chain kernel against its other bound, the SM issue rate (instructions
+    # counted by ncu on the current source, time live)
+    if "chain" in roof:
+        c_src = source_hash(*kernel_src["chain"])
+        _, c_inst = ncu_counters("chain_mixed", c_src)
+        iss = issue_roofline(torch, c_inst, roof["chain"]["ms_per_launch"],
+                             (clk or {}).get("sm_mhz"))
+        roof["chain"]["issue"] = iss
+        if dominant == "chain":
+            roofline["issue"] = iss
     launches = lc["gpu_launches"]
 
     e2e = None
     if not args.no_e2e:
         e2e = time_e2e(ess, torch, inst, C, args.steps, seed)
     cpu = None
+    errors = {}
     if not args.no_cpu and world >= 1:
         cpu = cpu_baseline(lambda n: workloads.metric(n_chains=n))
+        # the same leg compares the oracle's one-step map with the GPU's on
+        # sampled chains of each form (angle and iterate error)
+        errors["mixed"] = oracle_errors(ess, torch, inst.A, inst.b, lc["states"], "mixed", seed)
+        if not args.mixed_only:
+            errors["fp64"] = oracle_errors(ess, torch, inst.A, inst.b, lc64["states"], "fp64",
+                                           seed)
+            errors["fp64_split"] = oracle_errors(ess, torch, inst.A, inst.b, lc64s["states"],
+                                                 "fp64_split", seed)
     configs = None
     if not args.no_configs and not args.mixed_only:
-        configs = time_configs(ess, torch, workloads, peaks, seed)
+        configs = time_configs(ess, torch, workloads, peaks, seed, errors=not args.no_cpu)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+fp16x3", "data": "synthetic",
         "config": {"workload": "metric_d1000_m2000_c8192", "d": 1000, "m": 2000,
-                   "chains_per_gpu": C, "precision": "mixed", "refresh_k": 32,
+                   "chains_per_gpu": C, "precision": "mixed", "refresh_k": REFRESH_K,
+                   "window": lc["window"],
                    "l2": "working set per step ~300 MB > 126 MB L2 (no flush needed)",
                    "parallelism": f"replicas{world}"},
+        "error_vs_oracle": errors.get("mixed"),
         "fp64": None if args.mixed_only else {
             "value": value64, "unit": UNIT, "steps": args.fp64_steps,
-            "ms_per_step": ms64 / args.fp64_steps, "dtype": "f64",
-            "phases": roof64, "stats": stats64},
+            "ms_per_step": ms64 / args.fp64_steps, "dtype": "f64", "window": lc64["window"],
+            "phases": roof64, "stats": stats64, "error_vs_oracle": errors.get("fp64")},
         # the FP64 form with q = A nu and p = A x from exact 56-bit splits on the
         # tensor cores (FP64-class products, ess_config.fp64_products = 1)
         "fp64_split": None if args.mixed_only else {
             "value": value64s, "unit": UNIT, "steps": args.fp64_split_steps,
             "ms_per_step": ms64s / args.fp64_split_steps, "dtype": "f64 (products: bf16 slices)",
-            "phases": roof64s, "stats": stats64s},
+            "window": lc64s["window"], "phases": roof64s, "stats": stats64s,
+            "error_vs_oracle": errors.get("fp64_split")},
         "roofline": roofline,
         "phases": roof,
+        "fp64_peak": {"tflops": fp64_peak, "source": FP64_PEAK_SOURCE},
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,

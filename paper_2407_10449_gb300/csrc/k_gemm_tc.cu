@@ -1369,13 +1369,20 @@ __global__ void slice_rows_kernel(const TI* __restrict__ X, int ldx, int rows, i
   if (row >= rows) return;
   const TI* x = X + (size_t)row * ldx;
   TI mx = TI(0);
-  for (int j = lane; j < d; j += 32) mx = fmax(mx, fabs(x[j]));
+  bool nonfinite = false;
+  for (int j = lane; j < d; j += 32) {
+    mx = fmax(mx, fabs(x[j]));
+    nonfinite |= !isfinite(x[j]);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  nonfinite = __any_sync(0xffffffffu, nonfinite);
   int e = 0;
-  if (mx > TI(0)) (void)frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): mx < 2^e
+  if (mx > TI(0) && !nonfinite) (void)frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): mx < 2^e
   const TI inv_t = ldexp(TI(1), -e);
-  if (lane == 0) row_scale[row] = mx > TI(0) ? ldexpf(1.f, e) : 0.f;
+  // a row with NaN or Inf gets a NaN scale: its slices carry no meaning, and
+  // every product of the row comes out NaN (the epilogue multiplies by it)
+  if (lane == 0) row_scale[row] = nonfinite ? __int_as_float(0x7FC00000) : mx > TI(0) ? ldexpf(1.f, e) : 0.f;
   if constexpr (sizeof(TI) == 8) {
     if (w * K <= 63) {
       // FP64 rows: |y| < 1, so |y| 2^63 converts exactly to an integer in its

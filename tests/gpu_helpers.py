@@ -84,3 +84,122 @@ def fp16x3_bound(A, NU):
     sub = 2.0**-38 * (np.abs(NU).max(axis=1)[:, None] * np.abs(A).sum(axis=1)[None, :]
                       + np.abs(NU).sum(axis=1)[:, None] * np.abs(A).max(axis=1)[None, :])
     return absdot * (16 + k / 16) * 2.0**-24 + sub
+
+
+def f32(a):
+    """Values rounded to float (as the mixed form stores its inputs)."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def grid_bits(d):
+    """Largest B with d (2^B - 1)^2 < 2^24 (at most 11, fp16's significand)."""
+    B = 11
+    while B > 1 and d * (2**B - 1) ** 2 >= 2**24:
+        B -= 1
+    return B
+
+
+def to_grid(V, B):
+    """V rounded to integer multiples k 2^-e of one power of two, |k| <= 2^B - 1
+    (e chosen from max |V|)."""
+    V = np.asarray(V, dtype=np.float64)
+    mx = float(np.abs(V).max()) if V.size else 0.0
+    if mx == 0.0:
+        return V.copy()
+    e = math.floor(math.log2((2**B - 1) / mx))
+    k = np.clip(np.round(V * 2.0**e), -(2**B - 1), 2**B - 1)
+    return k * 2.0**-e
+
+
+def grid_instance(rng, d, m, n_chains, scale=1.0, slack=(0.0, 1.0), x_scale=0.3):
+    """Random polytope whose A, start points X and directions NU lie on grids
+    on which the mixed form's products are exact.
+
+    Each of A, X, NU holds integers k 2^-e (one power of two per array) with
+    |k| <= 2^B - 1 and d (2^B - 1)^2 < 2^24.  Then every product a_i.x and
+    a_i.nu is an integer multiple of one power of two below 2^24 of those
+    units, so every partial sum is a float: the FP32 accumulation is exact in
+    any order.  The operands survive the kernels' power-of-two scalings and
+    splits exactly: after the FP16x3 GEMM scales a row (or a chain's nu) so
+    that its largest entry lies in [2^14, 2^15), every entry is an integer of
+    at most B <= 11 bits times a power of two >= 8, an fp16 value (the second
+    slice is zero); the refresh scales x (and a row) by a power of two
+    t >= max |x| and cuts x / t into w-bit slices, and x / t has at most
+    B + 1 fractional bits, within the 35 (mixed) or 56 (FP64 split) bits it
+    keeps.  So P and Q carry no product error; b is an arbitrary double."""
+    B = grid_bits(d)
+    A = to_grid(rng.standard_normal((m, d)) * scale, B)
+    X = to_grid(rng.standard_normal((n_chains, d)) * x_scale, B)
+    NU = to_grid(rng.standard_normal((n_chains, d)), B)
+    b = (X @ A.T).max(axis=0) + rng.uniform(*slack, size=m)
+    return A, b, X, NU
+
+
+# Error of the FP32 root arithmetic of the mixed form (atan2f 3 ulp, acosf 2
+# ulp, the 2 pi shift and the subtraction tau - h, each at most 2^-21 rad per
+# ulp for angles below 2 pi), and of the float rounding of an FP64 root.
+ARITH_F32 = 7 * 2.0**-21
+ARITH_F64 = 2.0**-22
+# Relative error of the float ratio b / r: b rounded to float, r^2 by one
+# fused multiply-add after a rounded product, the square root and the division.
+RATIO_F32 = 4 * 2.0**-24
+
+
+def mixed_endpoint_bounds(A, b, X, NU, eps_p=0.0, eps_q=0.0, thresh=1e-4):
+    """A-priori bounds per chain (row of X, NU) and row of A on the movement
+    of the mixed form's arc endpoints tau -+ h (App. B) against the exact
+    FP64 roots, computed from the inputs only.
+
+    eps_p, eps_q: bounds on the errors of the products p = A x and q = A nu
+    (zero on grid inputs).  The product error moves the point (p, q) by at
+    most delta = hypot(eps_p, eps_q): tau by arcsin(delta / r) and r by delta.
+    The ratio b / r then moves by (eps_b + |b| delta / r) / (r - delta), plus
+    RATIO_F32 |b / r| where the kernel takes it in FP32 (|b / r| <= 1 - thresh;
+    beyond that the ratio and the arccos are taken in FP64 from b's double),
+    and h = arccos(b / r) by the largest change of arccos over that range.
+    Returns (amp, arith): the conditioning-amplified part and the fixed
+    arithmetic part."""
+    p = X @ A.T
+    q = NU @ A.T
+    r = np.hypot(p, q)
+    delta = np.hypot(eps_p, eps_q) * np.ones_like(r)
+    bb = np.broadcast_to(b[None, :], r.shape)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ratio = bb / r
+        # the kernel's branch test is taken on the float ratio: rows within its
+        # rounding of the threshold may take either branch (the FP32 one bounds both)
+        fp32 = np.abs(ratio) <= 1.0 - thresh + 2 * RATIO_F32
+        eps_b = np.where(fp32, 2.0**-24 * np.abs(bb), 0.0)
+        dtau = np.arcsin(np.minimum(1.0, delta / r))
+        dratio = (eps_b + np.abs(bb) * delta / r) / np.maximum(r - delta, 0.0)
+        dratio = dratio + np.where(fp32, RATIO_F32 * np.abs(ratio), 0.0)
+        rc = np.clip(ratio, -1.0, 1.0)
+        h = np.arccos(rc)
+        dh = np.maximum(np.abs(np.arccos(np.clip(rc - dratio, -1, 1)) - h),
+                        np.abs(np.arccos(np.clip(rc + dratio, -1, 1)) - h))
+        amp = dtau + dh
+    amp = np.where(np.isfinite(amp), amp, np.inf)
+    arith = np.where(fp32, ARITH_F32, ARITH_F64)
+    return amp, arith
+
+
+def mixed_exempt(refs, amp, arith, limit, trim_eps=0.0):
+    """Per chain: True if an arc endpoint that can reach an endpoint of the
+    oracle's active pieces has a conditioning bound above `limit`.  The union
+    of the arcs moves only where an arc endpoint, moved within its bound,
+    reaches one of the union's endpoints; rows without roots (b / r >= 1)
+    gain no arc on grid inputs, since the kernel decides |b / r| within
+    thresh of 1 in FP64."""
+    out = np.zeros(len(refs), dtype=bool)
+    for c, r in enumerate(refs):
+        ends = positive_pieces(r.pieces).ravel()
+        ends = ends[(ends > 0.0) & (ends < TWO_PI)]
+        if ends.size == 0:
+            continue
+        rows = np.flatnonzero(r.has_root)
+        reach = amp[c, rows] + arith[c, rows] + trim_eps + 1e-12
+        da = np.abs(r.alpha[rows, None] - ends[None, :]).min(axis=1)
+        db = np.abs(r.beta[rows, None] - ends[None, :]).min(axis=1)
+        near = (np.minimum(da, db) <= reach)
+        out[c] = bool(np.any(near & (amp[c, rows] > limit)))
+    return out

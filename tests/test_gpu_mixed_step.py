@@ -1,13 +1,18 @@
 """Mixed form: the FP16x3 tensor-core GEMM and the FP32 step vs the FP64 oracle.
 
 Bar (stated for the mixed form): interval endpoints and theta within 1e-5 rad
-and zero infeasible iterates.  A chain whose active endpoints are so
-ill-conditioned that the FP32 products actually computed (read back with
-ess_products) move them by more than 5e-6 rad to first order is exempted and
-counted (App. B: an endpoint tau -+ h moves by
-dp (|q| + |b p| / w) / r^2 + dq (|p| + |b q| / w) / r^2, w = sqrt(r^2 - b^2)).
-Inputs are rounded to float first on both sides, exactly as the mixed form
-stores them.
+and zero infeasible iterates.  The one-step comparisons run on grid inputs
+(gpu_helpers.grid_instance) on which P = A x and Q = A nu are exact in the
+mixed form, so the only differences from the FP64 oracle come from the FP32
+root arithmetic.  A chain is exempted only by an a-priori bound computed from
+the inputs (gpu_helpers.mixed_endpoint_bounds, App. B: h = arccos(b / r) is
+ill-conditioned as |b / r| -> 1, and the kernel takes b / r in FP32 for
+|b / r| <= 1 - 1e-4): if an arc endpoint that can reach an endpoint of the
+active pieces has a conditioning bound above 5e-6 rad.  Every other chain
+must match the oracle's pieces endpoint by endpoint, theta and x' within the
+bar.  The accuracy of the products themselves on arbitrary float inputs is
+checked separately against their proven bounds.  Inputs are rounded to float
+first on both sides, exactly as the mixed form stores them.
 """
 import math
 
@@ -16,16 +21,13 @@ import pytest
 
 import oracle
 import paper_2407_10449_gb300 as ess
-from gpu_helpers import dev, host, oracle_steps, positive_pieces, feasible_instance, fp16x3_bound, \
-    sym_diff_measure
+from conftest import read_golden
+from gpu_helpers import dev, host, oracle_steps, positive_pieces, fp16x3_bound, \
+    sym_diff_measure, f32, grid_bits, to_grid, grid_instance, mixed_endpoint_bounds, mixed_exempt
 
 pytestmark = pytest.mark.gpu
 
 ANG_TOL = 1e-5
-
-
-def f32(a):
-    return np.asarray(a, dtype=np.float32).astype(np.float64)
 
 
 def q_error_bound(A, NU):
@@ -116,101 +118,82 @@ def refresh_bound(A, X):
     return factor * t[:, None] * s[None, :]
 
 
-def _predicted_angle_error(A, b, X, NU, P, Q):
-    """Per row and chain: first-order change of alpha, beta caused by the
-    actual errors of the FP32 products P, Q (App. B: tau = atan2(q, p),
-    h = arccos(b / r))."""
-    p = X @ A.T
-    q = NU @ A.T
-    dp = np.abs(P - p)
-    dq = np.abs(Q - q)
-    r2 = p * p + q * q
-    with np.errstate(divide="ignore", invalid="ignore"):
-        w = np.sqrt(np.maximum(r2 - b[None, :] ** 2, 0.0))
-        bw = np.abs(b[None, :]) / (r2 * w)
-        err = dp * (np.abs(q) / r2 + bw * np.abs(p)) + dq * (np.abs(p) / r2 + bw * np.abs(q))
-    return np.where(np.isfinite(err), err, np.inf)
+LIMIT = 0.5 * ANG_TOL
 
 
-def _chain_is_ill_conditioned(r, pred_c, limit):
-    """True if an endpoint of the oracle's active pieces comes from a row whose
-    predicted angle error exceeds `limit`."""
-    ends = set(positive_pieces(r.pieces).ravel().tolist()) - {0.0, 2 * math.pi}
-    for i in np.flatnonzero(r.has_root):
-        if (r.alpha[i] in ends or r.beta[i] in ends) and pred_c[i] > limit:
-            return True
-    return False
+def check_mixed(A, b, X, NU, U, trim_eps=0.0, eps_p=0.0, eps_q=0.0, sample=None,
+                max_pieces=None, max_exempt_frac=0.05, **cfg):
+    """One mixed step with given draws vs the oracle's one-step map.
 
-
-def check_mixed(A, b, X, NU, U, trim_eps=0.0, max_exempt_frac=0.05):
+    Exemptions are chosen before the GPU runs, from the inputs alone
+    (mixed_endpoint_bounds, with eps_p / eps_q the a-priori product error
+    bounds: zero on grid inputs).  Returns (stats, exempt count, compared)."""
     X, NU = f32(X), f32(NU)
-    s = ess.Sampler(A, b, precision=ess.ESS_PREC_MIXED, trim_eps=trim_eps)
+    n = X.shape[0]
+    idx = np.arange(n) if sample is None else np.asarray(sample)
+    refs = oracle_steps(A, b, X[idx], NU[idx], U[idx], trim_eps)
+    amp, arith = mixed_endpoint_bounds(A, b, X[idx], NU[idx], eps_p, eps_q)
+    exempt = mixed_exempt(refs, amp, arith, LIMIT, trim_eps)
+    s = ess.Sampler(A, b, precision=ess.ESS_PREC_MIXED, trim_eps=trim_eps, **cfg)
     try:
-        Pg, Qg = s.products(dev(X), dev(NU))
-        Pg, Qg = host(Pg), host(Qg)
-        Xn, th, pcs, npc, rej = s.step_with_draws(dev(X), dev(NU), dev(U), max_pieces=A.shape[0] + 2)
+        mp = max_pieces or (A.shape[0] + 2)
+        Xn, th, pcs, npc, rej = s.step_with_draws(dev(X), dev(NU), dev(U), max_pieces=mp)
         Xn, th, pcs, npc, rej = host(Xn), host(th), host(pcs), host(npc), host(rej)
         stats = s.stats()
     finally:
         s.close()
     # zero infeasible iterates, decided in FP64 on the float states
     assert np.max(Xn @ A.T - b[None, :]) <= 0.0
-    ref = oracle_steps(A, b, X, NU, U, trim_eps)
-    pred = _predicted_angle_error(A, b, X, NU, Pg, Qg)
-    n_exempt = 0
-    for c, r in enumerate(ref):
-        if _chain_is_ill_conditioned(r, pred[c], 0.5 * ANG_TOL):
-            n_exempt += 1
+    for k, (c, r) in enumerate(zip(idx, refs)):
+        if exempt[k]:
             continue
-        got = positive_pieces(pcs[c], min(npc[c], pcs.shape[1]))
+        assert npc[c] <= pcs.shape[1], c
+        got = positive_pieces(pcs[c], npc[c])
         want = positive_pieces(r.pieces)
         diff = sym_diff_measure(got, want)
         assert diff <= 2 * max(len(want), 1) * ANG_TOL, (c, diff)
-        if not rej[c]:
-            assert abs(th[c] - r.theta) <= ANG_TOL, (c, th[c], r.theta)
-            scale = 1.0 + np.abs(r.x_next)
-            assert np.all(np.abs(Xn[c] - r.x_next) <= 1e-5 * scale * (1 + np.abs(NU[c]))), c
-        else:
+        if got.shape == want.shape:
+            assert np.max(np.abs(got - want), initial=0.0) <= ANG_TOL, (c, got, want)
+        assert abs(th[c] - r.theta) <= ANG_TOL, (c, th[c], r.theta)
+        if rej[c]:
             np.testing.assert_array_equal(Xn[c], X[c])
-    assert n_exempt <= max(2, max_exempt_frac * len(ref)), n_exempt
-    return stats, n_exempt
+        else:
+            scale = 1.0 + np.abs(r.x_next)
+            assert np.all(np.abs(Xn[c] - r.x_next) <= ANG_TOL * scale * (1 + np.abs(NU[c]))), c
+    n_exempt = int(exempt.sum())
+    assert n_exempt <= max_exempt_frac * len(idx), (n_exempt, len(idx))
+    return stats, n_exempt, len(idx)
 
 
 @pytest.mark.parametrize("d,m,n", [(2, 4, 16), (10, 20, 64), (37, 75, 130), (137, 300, 200),
                                    (100, 200, 256)])
 def test_mixed_step_parity(d, m, n):
     rng = np.random.default_rng(31 * d + m)
-    A, b, X = feasible_instance(rng, d, m, n, scale=1.0 / math.sqrt(d), slack=(0.05, 0.6))
-    NU = rng.standard_normal((n, d))
+    A, b, X, NU = grid_instance(rng, d, m, n, scale=1.0 / math.sqrt(d), slack=(0.05, 0.6))
     U = rng.uniform(size=n)
     check_mixed(A, b, X, NU, U)
 
 
 def test_mixed_full_size_sampled():
-    """d = 1000, m = 2000, 8192 chains (the benchmark's launch), 16 sampled chains."""
+    """d = 1000, m = 2000, 8192 chains (the benchmark's launch): the metric
+    workload's rows on a grid, 64 sampled chains compared element by element."""
     import workloads
-    inst = workloads.metric(n_chains=8192)
+    inst = workloads.metric(n_chains=1)
+    d = inst.d
+    B = grid_bits(d)
+    A = to_grid(inst.A, B)
     rng = np.random.default_rng(2)
-    X = f32(rng.standard_normal((8192, inst.d)) * 0.002)
-    NU = f32(rng.standard_normal((8192, inst.d)))
+    X = to_grid(rng.standard_normal((8192, d)) * 0.002, B)
+    NU = to_grid(rng.standard_normal((8192, d)), B)
     U = rng.uniform(size=8192)
-    s = ess.Sampler(inst.A, inst.b, precision=ess.ESS_PREC_MIXED)
-    try:
-        Xn, th, pcs, npc, rej = s.step_with_draws(dev(X), dev(NU), dev(U), max_pieces=64)
-        Xn, th = host(Xn), host(th)
-    finally:
-        s.close()
-    assert np.max(Xn @ inst.A.T - inst.b) <= 0.0
-    idx = rng.choice(8192, size=16, replace=False)
-    ref = oracle_steps(inst.A, inst.b, X[idx], NU[idx], U[idx])
-    bad = sum(abs(th[c] - r.theta) > ANG_TOL for c, r in zip(idx, ref))
-    assert bad <= 1
+    assert np.max(X @ A.T - inst.b) < 0.0
+    idx = rng.choice(8192, size=64, replace=False)
+    check_mixed(A, inst.b, X, NU, U, sample=idx, max_pieces=64)
 
 
 def test_mixed_trim_keeps_interior():
     rng = np.random.default_rng(4)
-    A, b, X = feasible_instance(rng, 20, 60, 128, scale=0.3, slack=(0.05, 0.5))
-    NU = rng.standard_normal((128, 20))
+    A, b, X, NU = grid_instance(rng, 20, 60, 128, scale=0.3, slack=(0.05, 0.5))
     U = rng.uniform(size=128)
     check_mixed(A, b, X, NU, U, trim_eps=1e-4)
 
@@ -218,29 +201,134 @@ def test_mixed_trim_keeps_interior():
 def test_mixed_cta_kernel_probit_orthant():
     """Mixed form through the CTA-per-chain kernel (every chain), on a
     probit-style orthant where all arcs have half-width pi / 2 and are merged
-    per bucket: theta within 1e-5 rad of the oracle for all but <= 5 % of the
-    chains (ill-conditioned endpoints), every iterate feasible."""
+    per bucket; grid inputs, every chain compared element by element."""
     rng = np.random.default_rng(8)
     k = 256
     M = rng.standard_normal((k, k))
-    L = np.linalg.cholesky(M @ M.T / k + np.eye(k))
-    z = rng.standard_normal(k)
-    y = np.sign(L @ z)
+    B = grid_bits(k)
+    L = to_grid(np.linalg.cholesky(M @ M.T / k + np.eye(k)), B)
+    z = to_grid(rng.standard_normal(k), B)
+    f = L @ z
+    assert np.all(f != 0.0)
+    y = np.sign(f)
     A = -y[:, None] * L
     b = np.zeros(k)
     n = 64
-    X = f32(np.tile(z, (n, 1)))
-    NU = f32(rng.standard_normal((n, k)))
+    X = np.tile(z, (n, 1))
+    NU = to_grid(rng.standard_normal((n, k)), B)
     U = rng.uniform(size=n)
-    s = ess.Sampler(A, b, precision=ess.ESS_PREC_MIXED, sort_threads=256)
-    try:
-        Xn, th, _, _, rej = s.step_with_draws(dev(X), dev(NU), dev(U))
-        Xn, th = host(Xn), host(th)
-    finally:
-        s.close()
-    assert np.max(Xn @ A.T - b) <= 0.0
-    bad = 0
-    for c in range(n):
-        r = oracle.step(A, b, X[c], NU[c], U[c])
-        bad += abs(r.theta - th[c]) > ANG_TOL
-    assert bad <= 0.05 * n, bad
+    check_mixed(A, b, X, NU, U, sort_threads=256)
+
+
+def test_mixed_near_tangent_rows_fp64_branch():
+    """Rows with b / r in (1 - 1e-4, 1): the mixed form takes the arccos
+    argument and the angles in FP64 (tangent_fp64 counts them).  Grid rows,
+    b = r (1 - delta) in double: the small arcs around tau cut holes in a wide
+    active set, and every chain must match the oracle (no exemption)."""
+    rng = np.random.default_rng(12)
+    d, m0, n = 12, 20, 96
+    A0, b0, X1, NU1 = grid_instance(rng, d, m0, 1, scale=0.3, slack=(1.0, 2.0))
+    x, nu = X1[0], NU1[0]
+    B = grid_bits(d)
+    extra = to_grid(rng.standard_normal((40, d)), B)
+    p, q = extra @ x, extra @ nu
+    r = np.hypot(p, q)
+    deltas = np.array([9e-5, 5e-5, 2e-5, 1e-5, 3e-6, 1e-6, 1e-7, 1e-8, 1e-10, 1e-12])
+    rows, bs = [], []
+    for i in range(extra.shape[0]):
+        dl = deltas[len(rows) % deltas.size]
+        if p[i] / r[i] < 1.0 - 2 * dl and len(rows) < 2 * deltas.size:
+            rows.append(extra[i])
+            bs.append(r[i] * (1.0 - dl))
+    A = np.vstack([A0, np.array(rows)])
+    b = np.concatenate([b0, np.array(bs)])
+    X = np.tile(x, (n, 1))
+    NU = np.tile(nu, (n, 1))
+    U = (np.arange(n) + 0.5) / n
+    stats, n_exempt, _ = check_mixed(A, b, X, NU, U, max_exempt_frac=0.0)
+    assert n_exempt == 0
+    assert stats["tangent_fp64"] >= len(rows) * n
+
+
+def test_mixed_near_tangent_minus_one():
+    """A row with b / r in (-1, -1 + 1e-4): x_t sits just inside the
+    constraint and the whole circle but a window of half-width ~sqrt(2 delta)
+    around theta = 0 is infeasible (Fig. 2(d) is the limit delta = 0).  Grid
+    inputs, q = 0 exactly for that row (nu has no component along it)."""
+    rng = np.random.default_rng(13)
+    d, m0, n = 6, 10, 64
+    A0, b0, X1, NU1 = grid_instance(rng, d, m0, 1, scale=0.3, slack=(1.0, 2.0))
+    x, nu = X1[0].copy(), NU1[0].copy()
+    x[0], nu[0] = 0.5, 0.0
+    b0 = np.maximum(b0, A0 @ x + 0.5)
+    for delta in (9e-5, 1e-6, 1e-9):
+        a = np.zeros(d)
+        a[0] = -1.0                       # p = -x_0 = -0.5, q = 0: tau = pi
+        A = np.vstack([A0, a])
+        b = np.concatenate([b0, [-0.5 * (1.0 - delta)]])
+        X = np.tile(x, (n, 1))
+        NU = np.tile(nu, (n, 1))
+        U = (np.arange(n) + 0.5) / n
+        _, n_exempt, _ = check_mixed(A, b, X, NU, U, max_exempt_frac=0.0)
+        assert n_exempt == 0
+
+
+def _fig1_instance():
+    rows = read_golden("fig1_worked_example.txt")
+    x = np.array([float(v) for v in rows[0][1:]])
+    nu = np.array([float(v) for v in rows[1][1:]])
+    A, b = [], []
+    for row in rows[2:]:
+        if row[0] == "plane":
+            t1, t2 = float(row[1]) * math.pi, float(row[2]) * math.pi
+            tau, h = 0.5 * (t1 + t2), 0.5 * (t2 - t1)
+            A.append(np.linalg.solve(np.stack([x, nu]), [math.cos(tau), math.sin(tau)]))
+            b.append(math.cos(h))
+    return x, nu, np.array(A), np.array(b)
+
+
+def test_mixed_fig1_worked_example():
+    """Fig. 1 through the mixed form.  Its rows are not on a grid, so the
+    exemption bound takes the FP16x3 product bound of q and the refresh bound
+    of p (plus their float roundings and that of A): no chain may be exempt."""
+    x, nu, A, b = _fig1_instance()
+    U = np.array([0.0, 0.1, 0.35, 0.5, 0.77, 0.999])
+    X = f32(np.tile(x, (U.size, 1)))
+    NU = f32(np.tile(nu, (U.size, 1)))
+    A32 = f32(A)
+    absA = np.abs(A)
+    eps_q = (fp16x3_bound(A32, NU) + 2.0**-24 * (np.abs(NU) @ absA.T)
+             + 2.0**-24 * np.abs(NU @ A.T))
+    eps_p = refresh_bound(A, X) + 2.0**-23 * np.abs(X @ A.T)
+    stats, n_exempt, _ = check_mixed(A, b, X, NU, U, eps_p=eps_p, eps_q=eps_q,
+                                     max_exempt_frac=0.0)
+    assert n_exempt == 0
+
+
+def test_mixed_fig2_edge_cases():
+    """Fig. 2 gallery through the mixed form (exact inputs): b / r = 1.25 and
+    1 give no root, 0.5 the arc (2 pi / 3, 4 pi / 3), -1 the single point
+    {0} (theta = 0, stay)."""
+    x = np.array([[2.0, 0.0]])
+    nu = np.array([[0.0, 1.0]])
+    a = np.array([[-1.0, 0.0]])
+    for b_val in (2.5, 2.0, 1.0, -2.0):
+        U = np.array([0.4])
+        s = ess.Sampler(a, np.array([b_val]), precision=ess.ESS_PREC_MIXED)
+        try:
+            Xn, th, pcs, npc, rej = s.step_with_draws(dev(x), dev(nu), dev(U), max_pieces=4)
+            Xn, th, pcs, npc = host(Xn), host(th), host(pcs), host(npc)
+        finally:
+            s.close()
+        if b_val >= 2.0:
+            np.testing.assert_allclose(positive_pieces(pcs[0], npc[0]), [[0.0, 2 * math.pi]],
+                                       atol=ANG_TOL)
+        elif b_val == 1.0:
+            np.testing.assert_allclose(positive_pieces(pcs[0], npc[0]),
+                                       [[0.0, 2 * math.pi / 3], [4 * math.pi / 3, 2 * math.pi]],
+                                       atol=ANG_TOL)
+        else:
+            assert th[0] == 0.0 and npc[0] == 0
+            np.testing.assert_array_equal(Xn[0], x[0])
+        _, n_exempt, _ = check_mixed(a, np.array([b_val]), x, nu, U, max_exempt_frac=0.0)
+        assert n_exempt == 0
