@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--chain-kernel", choices=["auto", "warp", "stream"], default="auto",
+                    help="float chain-step kernel (ess_set_chain_kernel)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="time only the mixed form (profiling runs)")
     ap.add_argument("--no-configs", action="store_true",
@@ -329,6 +331,9 @@ def refreshes_in(t0, steps, refresh_k=REFRESH_K):
     return sum(1 for t in range(t0, t0 + steps) if t % refresh_k == 0)
 
 
+CHAIN_KERNEL = "auto"
+
+
 def time_form(ess, torch, inst, precision, n_chains, steps, warmup, seed, world, rank,
               clocks=None, phase_steps=None, keep=0):
     """Exactly `steps` steps through ess_chains_step on the run's stream as a
@@ -339,6 +344,9 @@ def time_form(ess, torch, inst, precision, n_chains, steps, warmup, seed, world,
     prec = ess.ESS_PREC_MIXED if precision == "mixed" else ess.ESS_PREC_FP64
     cfg = {"fp64_products": ess.ESS_PRODUCTS_SPLIT} if precision == "fp64_split" else {}
     s = ess.Sampler(inst.A, inst.b, precision=prec, refresh_k=REFRESH_K, **cfg)
+    if CHAIN_KERNEL != "auto":
+        ess.ess_set_chain_kernel(s.state, {"warp": ess.ESS_CHAIN_WARP,
+                                           "stream": ess.ESS_CHAIN_STREAM}[CHAIN_KERNEL])
     stream = torch.cuda.Stream()
     x0 = torch.as_tensor(inst.X0[0], dtype=torch.float64)
     X = x0.to("cuda").repeat(n_chains, 1).contiguous()
@@ -728,6 +736,8 @@ def main():
     import paper_2407_10449_gb300 as ess
     import workloads
 
+    global CHAIN_KERNEL
+    CHAIN_KERNEL = args.chain_kernel
     world, rank, local = dist_setup(args.gpus)
     peaks = load_peaks()
     fp64_peak = measure_fp64_peak(torch)
@@ -762,7 +772,7 @@ def main():
     dominant = max(roof, key=lambda k: roof[k]["share"])
     dom = roof[dominant]
     kernel_src = {"gemm": ("k_gemm_tc.cu",),
-                  "chain": ("k_chain_warp.cu", "chain_math.cuh", "k_chain.cu"),
+                  "chain": ("k_chain_warp.cu", "chain_math.cuh", "chain_warp_ops.cuh", "k_chain.cu"),
                   "draw": ("k_draw.cu", "ess_common.cuh"), "refresh": ("k_gemm_tc.cu",)}
     src = source_hash(*kernel_src[dominant])
     traffic, inst_count = ncu_counters(f"{dominant}_mixed", src)

@@ -358,6 +358,30 @@ ess_status ess_step_noalloc(const double *A, const double *b, int d, int m, cons
 ess_status ess_set_graphs(ess_state *state, int enable);
 
 /*
+ * The chain-step kernel of ess_chains_step / ess_run / ess_step_with_draws
+ * when ess_config.sort_threads = 0 (the paper has no counterpart: this is the
+ * GPU layout of the per-chain work of Alg. 1, roots of App. B and Alg. 3).
+ *   ESS_CHAIN_AUTO (default): one warp per chain, rows read from global
+ *       memory (the fastest form measured at d = 1000, m = 2000, 8192 chains;
+ *       the autotuner of ess_config.autotune times both forms).
+ *   ESS_CHAIN_WARP: the same kernel, chosen explicitly.
+ *   ESS_CHAIN_STREAM: in the mixed form, when m and d are multiples of 4 and
+ *       m is at most 4096, one warp per chain with the chain's p and q rows
+ *       streamed through shared memory in chunks by 1-D bulk copies (for the
+ *       classification and again, with x and nu, for the move); other shapes
+ *       and the FP64 form use the warp kernel.
+ * In both, chains with more than 128 arcs left after the domination prune go
+ * to the CTA-per-chain kernel.  The kernels compute the same map; their
+ * results can differ in the last bits (the order of FP32 roundings).
+ * ess_get_chain_kernel reports the kernel in use: ESS_CHAIN_STREAM,
+ * ESS_CHAIN_WARP, or ESS_CHAIN_CTA (sort_threads > 0: a CTA per chain).
+ * Changing the kernel drops the captured CUDA graphs.  Errors: ESS_ERR_ARG.
+ */
+enum { ESS_CHAIN_AUTO = 0, ESS_CHAIN_WARP = 1, ESS_CHAIN_STREAM = 2, ESS_CHAIN_CTA = 3 };
+ess_status ess_set_chain_kernel(ess_state *state, int kind);
+ess_status ess_get_chain_kernel(const ess_state *state, int *kind);
+
+/*
  * Autotuner (cfg.autotune = 1): when chains are loaded, ess_chains_init
  * (and so ess_run) times, on the loaded chains and their first draw,
  *   - every tile width of the q = A nu tensor-core GEMM (mixed form), and

@@ -46,6 +46,7 @@ EXPORTED = ("ess_default_config", "ess_create", "ess_destroy", "ess_limits", "es
             "ess_set_timing", "ess_get_timing", "ess_reset_timing",
             "ess_get_stats", "ess_reset_stats", "ess_whiten", "ess_unwhiten", "ess_step_noalloc",
             "ess_set_graphs", "ess_graph_launches", "ess_get_tuning",
+            "ess_set_chain_kernel", "ess_get_chain_kernel",
             "ess_whitener_create", "ess_whitener_destroy", "ess_whitener_apply",
             "ess_batch_create", "ess_batch_destroy", "ess_batch_run", "ess_batch_step_with_draws",
             "ess_batch_products", "ess_batch_get_stats", "ess_batch_reset_stats",
@@ -136,6 +137,8 @@ def load(build_if_missing: bool = True):
             "ess_whitener_destroy": ([_vp], None),
             "ess_whitener_apply": ([_vp, _vp, c_int, c_int, _vp, _vp], c_int),
             "ess_set_graphs": ([_vp, c_int], c_int),
+            "ess_set_chain_kernel": ([_vp, c_int], c_int),
+            "ess_get_chain_kernel": ([_vp, ctypes.POINTER(c_int)], c_int),
             "ess_get_tuning": ([_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)], c_int),
             "ess_graph_launches": ([_vp, ctypes.POINTER(ctypes.c_longlong)], c_int),
             "ess_batch_create": ([c_int, _vp, _vp, _dp, _dp, ctypes.POINTER(ess_config),
@@ -403,6 +406,22 @@ class Whitener:
         X = torch.empty_like(U)
         ess_whitener_apply(self._w, U, X, stream)
         return X
+
+
+ESS_CHAIN_AUTO = 0
+ESS_CHAIN_WARP = 1
+ESS_CHAIN_STREAM = 2
+ESS_CHAIN_CTA = 3
+
+
+def ess_set_chain_kernel(state, kind):
+    _check(load().ess_set_chain_kernel(state, int(kind)))
+
+
+def ess_get_chain_kernel(state) -> int:
+    k = ctypes.c_int()
+    _check(load().ess_get_chain_kernel(state, ctypes.byref(k)))
+    return k.value
 
 
 def ess_set_graphs(state, enable=True):

@@ -240,6 +240,28 @@ __device__ __forceinline__ int classify_phi_nb(float p, float q, float b, float 
   return zero ? kRowNone : cls;
 }
 
+// The row classes of classify_phi_nb with fewer operations, for the streamed
+// warp kernel:
+//   no root   : b >= 0 and b^2 >= thi2 r^2 (this also takes r = 0 with b >= 0);
+//   keep      : otherwise, if b^2 > tlo2 r^2 (near tangency; it includes
+//               w^2 <= 0 and r = 0 with b < 0, which the exact roots then
+//               report as infeasible) or the pseudo-angles do not increase
+//               (an arc through the 0 / 2 pi cut, or NaN);
+//   arc       : otherwise, placed by its pseudo-angles pa < pb.
+// nf accumulates r^2 * 0: it turns NaN once p or q is non-finite (or r^2
+// overflows), so one test after the rows finds non-finite input.
+__device__ __forceinline__ int classify_lean(float p, float q, float b, float tlo2, float thi2,
+                                             float& pa, float& pb, float& nf) {
+  const float r2 = fmaf(p, p, q * q);
+  nf = fmaf(r2, 0.f, nf);
+  const float w2 = fmaf(-b, b, r2);
+  root_pseudo_angles(p, q, b, w2 * rsqrtf(fmaxf(w2, FLT_MIN)), pa, pb);
+  const float b2 = b * b;
+  const bool none = b >= 0.f && b2 >= thi2 * r2;
+  const bool keep = b2 > tlo2 * r2 || !(pa < pb);
+  return none ? kRowNone : keep ? kRowKeep : kRowApprox;
+}
+
 __device__ __forceinline__ int classify_phi_d(double p, double q, double b, float tlo2,
                                               float thi2, float& pa, float& pb,
                                               bool& nonfinite) {

@@ -81,7 +81,9 @@ struct ess_state {
   int cap = 0;
   void* P = nullptr;       // n x m, T: p = A x of the current states
   void* P2 = nullptr;      // n x m, T: next p (double buffer; swapped after each step)
-  int* ovf = nullptr;      // n + 1 ints: [0] count, [1..] chains left to the CTA kernel
+  int* ovf = nullptr;      // n + 2 ints: [0] count, [1] chain tickets of the streamed
+                           // kernel, [2..] chains left to the CTA kernel
+  int chain_kernel = ESS_CHAIN_AUTO;  // the float chain-step kernel (ess_set_chain_kernel)
   void* Q = nullptr;       // n x m, T
   void* NU = nullptr;      // n x d, T
   float* Xw = nullptr;     // n x d, mixed-form working states (the loaded chains)
@@ -220,7 +222,7 @@ ess_status ensure_capacity(ess_state* s, int n) {
   const size_t e = elem(s);
   ESS_CUDA(cudaMalloc(&s->P, (size_t)n * s->m * e));
   ESS_CUDA(cudaMalloc(&s->P2, (size_t)n * s->m * e));
-  ESS_CUDA(dev_alloc(&s->ovf, (size_t)n + 1));
+  ESS_CUDA(dev_alloc(&s->ovf, (size_t)n + 2));
   ESS_CUDA(cudaMalloc(&s->Q, (size_t)n * s->m * e));
   ESS_CUDA(cudaMalloc(&s->NU, (size_t)n * s->d * e));
   ESS_CUDA(cudaMalloc(&s->NU_alt, (size_t)n * s->d * e));
@@ -370,11 +372,20 @@ ess_status launch_step(ess_state* s, ess::ChainParams<T> p, cudaStream_t st) {
   if (s->cfg.sort_threads > 0) {
     ESS_CUDA(ess::launch_chain_step<T>(p, s->chain_threads, st));
   } else {
-    ESS_CUDA(cudaMemsetAsync(s->ovf, 0, sizeof(int), st));
+    ESS_CUDA(cudaMemsetAsync(s->ovf, 0, 2 * sizeof(int), st));
     p.overflow_count = s->ovf;
-    p.overflow_list = s->ovf + 1;
-    ESS_CUDA(ess::launch_chain_step_warp<T>(p, st));
-    p.chain_list = s->ovf + 1;
+    p.overflow_list = s->ovf + 2;
+    bool streamed = false;
+    if constexpr (sizeof(T) == 4) {
+      streamed = s->chain_kernel == ESS_CHAIN_STREAM && ess::chain_stream_supported(s->m, s->d) &&
+                 ess::chain_stream_aligned(p);
+      if (streamed) {
+        p.work_counter = s->ovf + 1;
+        ESS_CUDA(ess::launch_chain_step_stream(p, st));
+      }
+    }
+    if (!streamed) ESS_CUDA(ess::launch_chain_step_warp<T>(p, st));
+    p.chain_list = s->ovf + 2;
     p.list_count = s->ovf;
     ESS_CUDA(ess::launch_chain_step<T>(p, s->chain_threads, st));
   }
@@ -462,12 +473,19 @@ ess_status autotune(ess_state* s, int t0, cudaStream_t st) {
   void* scratch = nullptr;
   if (rc == ESS_OK) ESS_CUDA(cudaMalloc(&scratch, (size_t)n * d * elem(s)));
   const int saved_sort = s->cfg.sort_threads, saved_threads = s->chain_threads;
-  int cands[3][2] = {{0, s->min_chain_threads}, {s->min_chain_threads, s->min_chain_threads},
-                     {2 * s->min_chain_threads, 2 * s->min_chain_threads}};
+  const int saved_kernel = s->chain_kernel;
+  // (sort_threads, CTA width of the fallback or of every chain, float kernel)
+  int cands[4][3] = {{0, s->min_chain_threads, ESS_CHAIN_STREAM},
+                     {0, s->min_chain_threads, ESS_CHAIN_WARP},
+                     {s->min_chain_threads, s->min_chain_threads, ESS_CHAIN_AUTO},
+                     {2 * s->min_chain_threads, 2 * s->min_chain_threads, ESS_CHAIN_AUTO}};
   int best = -1;
   float best_ms = 0.f;
-  for (int c = 0; c < 3 && rc == ESS_OK; ++c) {
+  for (int c = 0; c < 4 && rc == ESS_OK; ++c) {
     if (cands[c][1] > ess::kChainMaxThreads) continue;
+    // the streamed kernel exists for float chains with supported shapes
+    if (c == 0 && !(mixed(s) && ess::chain_stream_supported(s->m, s->d))) continue;
+    s->chain_kernel = cands[c][2];
     const size_t smem = mixed(s) ? ess::chain_smem_bytes<float>(cands[c][1], d)
                                  : ess::chain_smem_bytes<double>(cands[c][1], d);
     int optin = 0;
@@ -514,9 +532,11 @@ ess_status autotune(ess_state* s, int t0, cudaStream_t st) {
   if (best >= 0) {
     s->cfg.sort_threads = cands[best][0];
     s->chain_threads = cands[best][1];
+    s->chain_kernel = cands[best][2];
   } else {
     s->cfg.sort_threads = saved_sort;
     s->chain_threads = saved_threads;
+    s->chain_kernel = saved_kernel;
   }
   s->timing = timing;
   cudaEventDestroy(e0);
@@ -997,6 +1017,24 @@ ess_status ess_chains_step(ess_state* s, int n_iter, uint64_t seed, void* sample
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->ev_join, 0);
   if (e != cudaSuccess && rc == ESS_OK) rc = cuda_fail(e, "join internal streams");
   return rc;
+}
+
+ess_status ess_set_chain_kernel(ess_state* s, int kind) {
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  if (kind != ESS_CHAIN_AUTO && kind != ESS_CHAIN_WARP && kind != ESS_CHAIN_STREAM)
+    return fail(ESS_ERR_ARG, "kind: ESS_CHAIN_AUTO, ESS_CHAIN_WARP or ESS_CHAIN_STREAM");
+  if (kind != s->chain_kernel) drop_graphs(s);  // captured periods hold the old kernel
+  s->chain_kernel = kind;
+  return ESS_OK;
+}
+
+ess_status ess_get_chain_kernel(const ess_state* s, int* kind) {
+  if (!s || !kind) return fail(ESS_ERR_ARG, "NULL argument");
+  if (s->cfg.sort_threads > 0) *kind = ESS_CHAIN_CTA;
+  else if (mixed(s) && s->chain_kernel == ESS_CHAIN_STREAM && ess::chain_stream_supported(s->m, s->d))
+    *kind = ESS_CHAIN_STREAM;
+  else *kind = ESS_CHAIN_WARP;
+  return ESS_OK;
 }
 
 ess_status ess_set_graphs(ess_state* s, int enable) {

@@ -111,6 +111,8 @@ struct ChainParams {
   const ChainDesc* desc;
   // if set, the step index is t + *t_dev (replayable CUDA graphs)
   const unsigned* t_dev;
+  // streamed warp kernel: chain tickets (zero before each launch)
+  int* work_counter;
 };
 
 // The rows of one chain as a kernel sees them.
@@ -186,6 +188,18 @@ cudaError_t launch_chain_step_warp(const ChainParams<T>& p, cudaStream_t s);
 template <typename T>
 size_t chain_warp_smem_bytes(int m);
 constexpr int kWarpSortCap = 128;
+
+// One warp per chain, warps taking chains from *p.work_counter (zeroed before
+// the launch), each chain's p and q rows streamed through shared memory in
+// chunks by 1-D bulk copies (for the classification and again for the move).
+// Float chains of one problem with m, d multiples of 4, m <= 4096 and 16-byte
+// aligned rows (chain_stream_supported / chain_stream_aligned); chains with
+// more than kWarpSortCap surviving arcs are appended to p.overflow_list
+// (untouched) for launch_chain_step in list mode.  p.P_out must differ from
+// p.P_in.
+bool chain_stream_supported(int m, int d);
+bool chain_stream_aligned(const ChainParams<float>& p);
+cudaError_t launch_chain_step_stream(const ChainParams<float>& p, cudaStream_t s);
 
 // ---------------------------------------------------------------- batch ---
 // A work item of the grouped GEMMs: rows row0 .. row0 + rows - 1 of one

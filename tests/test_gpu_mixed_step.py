@@ -122,7 +122,7 @@ LIMIT = 0.5 * ANG_TOL
 
 
 def check_mixed(A, b, X, NU, U, trim_eps=0.0, eps_p=0.0, eps_q=0.0, sample=None,
-                max_pieces=None, max_exempt_frac=0.05, **cfg):
+                max_pieces=None, max_exempt_frac=0.05, chain_kernel=None, **cfg):
     """One mixed step with given draws vs the oracle's one-step map.
 
     Exemptions are chosen before the GPU runs, from the inputs alone
@@ -136,6 +136,8 @@ def check_mixed(A, b, X, NU, U, trim_eps=0.0, eps_p=0.0, eps_q=0.0, sample=None,
     exempt = mixed_exempt(refs, amp, arith, LIMIT, trim_eps)
     s = ess.Sampler(A, b, precision=ess.ESS_PREC_MIXED, trim_eps=trim_eps, **cfg)
     try:
+        if chain_kernel is not None:
+            ess.ess_set_chain_kernel(s.state, chain_kernel)
         mp = max_pieces or (A.shape[0] + 2)
         Xn, th, pcs, npc, rej = s.step_with_draws(dev(X), dev(NU), dev(U), max_pieces=mp)
         Xn, th, pcs, npc, rej = host(Xn), host(th), host(pcs), host(npc), host(rej)
