@@ -347,6 +347,31 @@ ess_status ess_step_noalloc(const double *A, const double *b, int d, int m, cons
                             double *theta, int *rejected, void *cuda_stream);
 
 /*
+ * A few FP64 chains (1 to 16) of the state's polytope for n_iter steps of
+ * Alg. 1, every step in one persistent cooperative kernel (the paper's
+ * single-chain and ten-chain experiments of Sec. 4.2).  The map and the draws
+ * are those of ess_run in the FP64 form (Philox counters (chain, step), the
+ * App. B roots, Alg. 3, the Sec. 3.3 rejection), laid out for few chains:
+ * all SMs stream the rows of A once per step for q = A nu of every chain
+ * and take the exact roots of every row, arcs are merged per angle bucket,
+ * one CTA per chain sweeps the merged arcs (Alg. 3) and draws theta, grid
+ * barriers separate the phases.  p = A x is recomputed at step t0 and whenever t % refresh_k
+ * == 0.
+ *   X          device, n_chains x d doubles: start points in, final states
+ *              out.
+ *   samples    device or NULL; with record_every > 0, n_chains x
+ *              (n_iter / record_every) x d doubles: the state after every
+ *              record_every-th step.
+ * Synchronous.  Errors: ESS_ERR_UNSUPPORTED for the mixed form or m > 6144,
+ * ESS_ERR_ARG for n_chains outside 1..16, ESS_ERR_INFEASIBLE_X0 for a start
+ * point outside the polytope (checked in FP64 at step t0; X unchanged),
+ * ESS_ERR_NUMERIC if NaN/Inf appeared (that chain stays), ESS_ERR_TIMEOUT if
+ * a grid barrier waited more than 2 s.
+ */
+ess_status ess_run_few(ess_state *state, double *X, int n_chains, int t0, int n_iter,
+                       uint64_t seed, double *samples, int record_every, void *cuda_stream);
+
+/*
  * CUDA-graph replay of whole refresh periods in ess_chains_step / ess_run
  * (on by default).  A period -- the A x refresh and refresh_k steps -- is
  * captured once per (chain count, seed, p buffer) and replayed, the step index

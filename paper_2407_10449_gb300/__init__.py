@@ -41,7 +41,7 @@ _STATUS_NAMES = {0: "ESS_OK", 1: "ESS_ERR_ARG", 2: "ESS_ERR_INFEASIBLE_X0", 3: "
 
 # every symbol include/ess.h declares
 EXPORTED = ("ess_default_config", "ess_create", "ess_destroy", "ess_limits", "ess_run",
-            "ess_chains_init", "ess_chains_step", "ess_chains_get", "ess_run_host", "ess_step_with_draws", "ess_products", "ess_philox_blocks",
+            "ess_chains_init", "ess_chains_step", "ess_chains_get", "ess_run_host", "ess_run_few", "ess_step_with_draws", "ess_products", "ess_philox_blocks",
             "ess_draw_normals",
             "ess_set_timing", "ess_get_timing", "ess_reset_timing",
             "ess_get_stats", "ess_reset_stats", "ess_whiten", "ess_unwhiten", "ess_step_noalloc",
@@ -119,6 +119,7 @@ def load(build_if_missing: bool = True):
             "ess_chains_step": ([_vp, c_int, c_u64, _vp, c_int, _vp], c_int),
             "ess_chains_get": ([_vp, _vp, _vp], c_int),
             "ess_run_host": ([_vp, _vp, c_int, c_int, c_int, c_u64, _vp, c_int, _vp], c_int),
+            "ess_run_few": ([_vp, _vp, c_int, c_int, c_int, c_u64, _vp, c_int, _vp], c_int),
             "ess_step_with_draws": ([_vp, _vp, _vp, _vp, c_int, _vp, _vp, _vp, c_int, _vp, _vp,
                                      _vp], c_int),
             "ess_products": ([_vp, _vp, _vp, c_int, _vp, _vp, _vp], c_int),
@@ -234,6 +235,14 @@ def ess_chains_step(state, n_iter, seed, samples=None, record_every=0, stream=No
 
 def ess_chains_get(state, X=None, stream=None):
     _check(load().ess_chains_get(state, _ptr(X), _stream_ptr(stream)))
+
+
+def ess_run_few(state, X, n_chains, t0, n_iter, seed, samples=None, record_every=0, stream=None):
+    """1 to 16 FP64 chains, all steps in one persistent kernel (see include/ess.h).
+    X: CUDA float64 (n_chains, d), updated in place; samples: CUDA float64
+    (n_chains, n_iter // record_every, d) or None."""
+    _check(load().ess_run_few(state, _ptr(X), n_chains, t0, n_iter, seed, _ptr(samples),
+                              record_every, _stream_ptr(stream)))
 
 
 def ess_run_host(state, X, n_chains, t0, n_iter, seed, samples=None, record_every=0, stream=None):

@@ -134,6 +134,16 @@ struct ess_state {
   void* host_slot[2] = {nullptr, nullptr};
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t slot_ready[2] = {nullptr, nullptr}, slot_free[2] = {nullptr, nullptr};
+  // ess_run_few: buffers of the persistent few-chain kernel (kMaxFew chains)
+  double* few_x = nullptr;    // 2 x kMaxFew x d
+  double* few_nu = nullptr;   // 2 x kMaxFew x d
+  double* few_p = nullptr;    // 2 x kMaxFew x m
+  double* few_q = nullptr;    // kMaxFew x m
+  double* few_short = nullptr; // kMaxFew x m x 2
+  double* few_th = nullptr;   // 3 x kMaxFew: theta, cos, sin
+  unsigned long long* few_bkt = nullptr;  // 2 x kMaxFew x kFewBuckets: min alpha, max beta
+  int* few_int = nullptr;     // 7 x kMaxFew: rej[2], cur[2], nshort, bad, bad_prev
+  unsigned* few_bar = nullptr;   // barrier (2) and abort flag (1)
 };
 
 namespace {
@@ -856,6 +866,15 @@ void ess_destroy(ess_state* s) {
     if (s->slot_free[k]) cudaEventDestroy(s->slot_free[k]);
   }
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+  dev_free(s->few_x);
+  dev_free(s->few_nu);
+  dev_free(s->few_p);
+  dev_free(s->few_q);
+  dev_free(s->few_short);
+  dev_free(s->few_th);
+  dev_free(s->few_bkt);
+  dev_free(s->few_int);
+  dev_free(s->few_bar);
   delete s;
 }
 
@@ -1108,6 +1127,90 @@ ess_status ess_run(ess_state* s, double* X, int n_chains, int t0, int n_iter, ui
   if (rc == ESS_OK) rc = ess_chains_step(s, n_iter, seed, samples, record_every, cuda_stream);
   if (rc == ESS_OK) rc = ess_chains_get(s, X, cuda_stream);
   return rc;
+}
+
+ess_status ess_run_few(ess_state* s, double* X, int n_chains, int t0, int n_iter, uint64_t seed,
+                       double* samples, int record_every, void* cuda_stream) {
+  g_err.clear();
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  if (s->cfg.precision != ESS_PREC_FP64)
+    return fail(ESS_ERR_UNSUPPORTED, "ess_run_few runs the FP64 form");
+  if (n_chains < 1 || n_chains > ess::kMaxFew)
+    return fail(ESS_ERR_ARG, "ess_run_few takes 1 to 16 chains");
+  if (n_iter < 0 || t0 < 0 || record_every < 0) return fail(ESS_ERR_ARG, "negative size");
+  if (!X) return fail(ESS_ERR_ARG, "X is NULL");
+  if (record_every > 0 && !samples) return fail(ESS_ERR_ARG, "samples is NULL");
+  if (s->m > ess::kFewMaxM) return fail(ESS_ERR_UNSUPPORTED, "ess_run_few takes m <= 6144");
+  if ((long long)t0 + n_iter > 0x7fffffffLL) return fail(ESS_ERR_ARG, "step index overflow");
+  if (n_iter == 0) return ESS_OK;
+  DeviceGuard g(s->device);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int d = s->d, m = s->m, F = ess::kMaxFew;
+  if (!s->few_x) {
+    ESS_CUDA(dev_alloc(&s->few_x, (size_t)2 * F * d));
+    ESS_CUDA(dev_alloc(&s->few_nu, (size_t)2 * F * d));
+    ESS_CUDA(dev_alloc(&s->few_p, (size_t)2 * F * m));
+    ESS_CUDA(dev_alloc(&s->few_q, (size_t)F * m));
+    ESS_CUDA(dev_alloc(&s->few_short, (size_t)2 * F * m));
+    ESS_CUDA(dev_alloc(&s->few_th, (size_t)3 * F));
+    ESS_CUDA(dev_alloc(&s->few_bkt, (size_t)2 * F * ess::kFewBuckets));
+    ESS_CUDA(dev_alloc(&s->few_int, (size_t)7 * F));
+    ESS_CUDA(dev_alloc(&s->few_bar, (size_t)4));
+  }
+  // rej[(t0 - 1) & 1] = 1 and cur = 0: step t0 starts from buffer 0
+  int init[7 * ess::kMaxFew] = {0};
+  for (int c = 0; c < F; ++c) init[((t0 + 1) & 1) * F + c] = 1;
+  ESS_CUDA(cudaMemcpyAsync(s->few_int, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  ESS_CUDA(cudaMemsetAsync(s->few_bar, 0, sizeof(unsigned) * 4, st));
+  ESS_CUDA(cudaMemsetAsync(s->dstatus, 0, sizeof(int), st));
+  ess::FewArgs a{};
+  a.A = s->A64;
+  a.b = s->b64;
+  a.anorm = s->anorm;
+  a.bm_tab = s->bm_tab;
+  a.d = d;
+  a.m = m;
+  a.C = n_chains;
+  a.chunk = ess::few_chains_chunk(n_chains, d);
+  for (int k = 0; k < 2; ++k) {
+    a.X[k] = s->few_x + (size_t)k * F * d;
+    a.NU[k] = s->few_nu + (size_t)k * F * d;
+    a.P[k] = s->few_p + (size_t)k * F * m;
+    a.rej[k] = s->few_int + (size_t)k * F;
+    a.cur[k] = s->few_int + (size_t)(2 + k) * F;
+  }
+  a.Q = s->few_q;
+  a.bmin = s->few_bkt;
+  a.bmax = s->few_bkt + (size_t)F * ess::kFewBuckets;
+  a.shorts = s->few_short;
+  a.nshort = s->few_int + (size_t)4 * F;
+  a.bad = s->few_int + (size_t)5 * F;
+  a.bad_prev = s->few_int + (size_t)6 * F;
+  a.theta = s->few_th;
+  a.cth = s->few_th + F;
+  a.sth = s->few_th + 2 * F;
+  a.bar = s->few_bar;
+  a.abort_flag = reinterpret_cast<int*>(s->few_bar + 2);
+  a.X_user = X;
+  a.samples = record_every > 0 ? samples : nullptr;
+  a.record_every = record_every > 0 ? record_every : 1;
+  a.n_rec = record_every > 0 ? n_iter / record_every : 0;
+  a.t0 = t0;
+  a.n_iter = n_iter;
+  a.refresh_k = s->cfg.refresh_k;
+  a.seed = seed;
+  a.trim_eps = s->cfg.trim_eps;
+  a.margin = s->cfg.residual_margin;
+  a.stats = s->dstats;
+  a.status = s->dstatus;
+  const size_t smem = ess::few_chains_smem(n_chains, m, a.chunk);
+  int optin = 0;
+  ESS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
+  if (smem + 2048 > (size_t)optin)
+    return fail(ESS_ERR_UNSUPPORTED, "m too large for the few-chain kernel's shared memory");
+  ESS_CUDA(ess::launch_few_chains(a, st));
+  s->host_steps += (long long)n_chains * n_iter;
+  return read_status(s, st);
 }
 
 ess_status ess_run_host(ess_state* s, double* X_host, int n_chains, int t0, int n_iter,

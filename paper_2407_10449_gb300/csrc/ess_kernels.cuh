@@ -201,6 +201,59 @@ bool chain_stream_supported(int m, int d);
 bool chain_stream_aligned(const ChainParams<float>& p);
 cudaError_t launch_chain_step_stream(const ChainParams<float>& p, cudaStream_t s);
 
+// ------------------------------------------------------------ few chains ---
+// FP64 chains of one polytope, 1 .. kMaxFew at a time: all steps of a run in
+// one cooperative persistent kernel (k_few.cu).  Buffers (device):
+//   X[2], NU[2]: C x d; P[2]: C x m; Q: C x m; bmin, bmax: C x kFewBuckets
+//   (double bits); shorts: C x m x 2; nshort, rej[2], cur[2], bad, bad_prev:
+//   C ints; theta, cth, sth: C doubles; bar: 2 unsigned (zero), abort_flag:
+//   1 int (zero).
+// Before the launch: bmin all kEmptyBucket, bmax, nshort, bad, bad_prev zero;
+// cur[(t0 - 1) & 1] zero and rej[(t0 - 1) & 1] one (so that step t0 starts
+// from buffer 0).  X_user holds the start points and receives the final
+// states; samples (or null): C x n_rec x d, the state after every
+// record_every-th step.
+constexpr int kMaxFew = 16;
+constexpr int kFewMaxM = 6144;
+constexpr int kFewBuckets = 2048;
+constexpr unsigned long long kEmptyBucket = 0x7FF0000000000000ull;  // +inf
+struct FewArgs {
+  const double* A;
+  const double* b;
+  const double* anorm;
+  const double* bm_tab;
+  int d, m, C, chunk;
+  double* X[2];
+  double* P[2];
+  double* Q;
+  double* NU[2];
+  unsigned long long* bmin;
+  unsigned long long* bmax;
+  double* shorts;
+  int* nshort;
+  double* theta;
+  double* cth;
+  double* sth;
+  int* rej[2];
+  int* cur[2];
+  int* bad;
+  int* bad_prev;
+  unsigned* bar;
+  int* abort_flag;
+  double* X_user;
+  double* samples;
+  int record_every, n_rec;
+  int t0, n_iter, refresh_k;
+  uint64_t seed;
+  double trim_eps, margin;
+  DevStats* stats;
+  int* status;
+};
+// chunk of d staged per round in shared memory, and the dynamic shared memory
+size_t few_chains_smem(int C, int m, int chunk);
+int few_chains_chunk(int C, int d);
+cudaError_t launch_few_chains(const FewArgs& args, cudaStream_t s);
+
 // ---------------------------------------------------------------- batch ---
 // A work item of the grouped GEMMs: rows row0 .. row0 + rows - 1 of one
 // problem's A times `chains` consecutive chains of that problem, computed as
