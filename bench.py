@@ -30,6 +30,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -513,6 +515,30 @@ def time_unwhiten(ess, torch, pb, n, peaks, reps=10):
     return out
 
 
+def time_cholesky(ess, torch, K, reps=3):
+    """L = chol(K) on the GPU (ess_cholesky, FP64): the best of `reps` timed
+    factorisations (CUDA events; the matrix copied in before each); n^3 / 3
+    multiply-adds against the FP64 peak measured in the run."""
+    n = K.shape[0]
+    src = torch.tensor(np.ascontiguousarray(K), dtype=torch.float64, device="cuda")
+    A = torch.empty_like(src)
+    best = float("inf")
+    for _ in range(reps + 1):
+        A.copy_(src)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ess.ess_cholesky(A)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    flops = n ** 3 / 3.0
+    L = torch.tril(A).cpu().numpy()
+    return {"n": n, "ms": best, "achieved_tflops": flops / (best * 1e-3) / 1e12,
+            "peak_tflops": FP64_TFLOPS_MEASURED,
+            "frac": flops / (best * 1e-3) / 1e12 / FP64_TFLOPS_MEASURED, "L": L}
+
+
 def time_configs(ess, torch, workloads, peaks, seed, errors=True):
     """The other configurations, both forms, short runs (parity-tested
     elsewhere; reported here with their phase rooflines)."""
@@ -521,6 +547,9 @@ def time_configs(ess, torch, workloads, peaks, seed, errors=True):
     singles = [("small_d10_m20_c16", workloads.small(n_chains=1), 16, (192, 192)),
                ("medium_d100_m200_c1024", workloads.medium(n_chains=1), 1024, (192, 96))]
     pb = workloads.probit(n_chains=1)
+    # App. A's factor of K on the GPU (FP64 blocked Cholesky), then the whitening
+    chol = time_cholesky(ess, torch, pb["K"])
+    pb["L"] = chol.pop("L")
     Aw, bw = ess.ess_whiten(pb["A0"], pb["b"], pb["mu"], pb["L"])
     singles.append(("probit_n2000_c4096",
                     SimpleNamespace(A=Aw, b=bw, X0=pb["X0"], d=Aw.shape[1], m=Aw.shape[0]),
@@ -544,6 +573,7 @@ def time_configs(ess, torch, workloads, peaks, seed, errors=True):
                                                                lc["states"], form, seed)
         out[name] = entry
     out["probit_n2000_c4096"]["unwhiten"] = time_unwhiten(ess, torch, pb, 4096, peaks)
+    out["probit_n2000_c4096"]["cholesky"] = chol
     insts = workloads.batched()
     entry = {}
     for form, steps in (("mixed", 64), ("fp64", 32)):
@@ -556,6 +586,54 @@ def time_configs(ess, torch, workloads, peaks, seed, errors=True):
             r["error_vs_oracle"] = batch_oracle_errors(ess, torch, insts, form, seed)
         entry[form] = r
     out["batched_512_problems"] = entry
+    out.update(time_paper_hd(ess, torch, workloads, peaks, seed))
+    return out
+
+
+def time_paper_hd(ess, torch, workloads, peaks, seed):
+    """Sec. 4.2 family (A d x d iid N(0, 1), b = A x0 + U[0, 1], m = d) with 1
+    and 10 chains: the few-chain FP64 path (ess_run_few, one persistent
+    kernel per run), with A read once per step (8 m d bytes) against the HBM
+    peak, and the generic mixed path on the same chains for context."""
+    out = {}
+    for d in (1000, 2000, 4000):
+        for C, steps in ((1, 200), (10, 50)):
+            inst = workloads.paper_hd(d=d, n_chains=C)
+            s = ess.Sampler(inst.A, inst.b, precision=ess.ESS_PREC_FP64)
+            X = torch.tensor(inst.X0, dtype=torch.float64, device="cuda")
+            ess.ess_run_few(s.state, X, C, 0, 8, seed)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ess.ess_run_few(s.state, X, C, 8, steps, seed)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            st = s.stats()
+            s.close()
+            a_gbs = 8.0 * d * d / (ms / steps * 1e-3) / 1e9
+            entry = {"value": C * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
+                     "us_per_step": 1e3 * ms / steps, "dtype": "f64", "call": "ess_run_few",
+                     "roofline": {"bound": "hbm", "achieved": a_gbs, "peak": peaks["hbm_gbs"],
+                                  "unit": "GB/s", "frac": a_gbs / peaks["hbm_gbs"],
+                                  "work_per_step": 8.0 * d * d},
+                     "arcs_per_chain_step": st["sort_keys"] / max(1, st["steps"])}
+            # the generic path's mixed form on the same chains
+            sm = ess.Sampler(inst.A, inst.b, precision=ess.ESS_PREC_MIXED)
+            Xm = torch.tensor(inst.X0, dtype=torch.float64, device="cuda")
+            ess.ess_chains_init(sm.state, Xm, C, 0)
+            ess.ess_chains_step(sm.state, 32, seed)
+            torch.cuda.synchronize()
+            e0.record()
+            ess.ess_chains_step(sm.state, steps, seed)
+            e1.record()
+            e1.synchronize()
+            msm = e0.elapsed_time(e1)
+            sm.close()
+            entry["generic_mixed"] = {"value": C * steps / (msm / 1e3),
+                                      "us_per_step": 1e3 * msm / steps}
+            out[f"paper_hd_d{d}_c{C}"] = entry
     return out
 
 

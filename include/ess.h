@@ -372,6 +372,19 @@ ess_status ess_run_few(ess_state *state, double *X, int n_chains, int t0, int n_
                        uint64_t seed, double *samples, int record_every, void *cuda_stream);
 
 /*
+ * App. A's factor on the GPU: the lower Cholesky factor L of a symmetric
+ * positive definite Sigma = L L^T (the change of variables x = L u + mu).
+ *   A     device, n x n row-major doubles with leading dimension lda >= n;
+ *         only the lower triangle is read, and it is overwritten with L (the
+ *         strict upper triangle is left as it is).
+ *   info  host int or NULL: 0, or the 1-based row whose pivot is not positive.
+ * Blocked FP64 factorisation (64 x 64 blocks: diagonal block, panel solve,
+ * trailing update).  Synchronous.  Errors: ESS_ERR_ARG for bad sizes or a
+ * matrix that is not positive definite (A then holds a partial factor).
+ */
+ess_status ess_cholesky(double *A, int n, int lda, int *info, void *cuda_stream);
+
+/*
  * CUDA-graph replay of whole refresh periods in ess_chains_step / ess_run
  * (on by default).  A period -- the A x refresh and refresh_k steps -- is
  * captured once per (chain count, seed, p buffer) and replayed, the step index

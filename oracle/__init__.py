@@ -19,6 +19,7 @@ Each wrapper names the part of the paper it follows:
   trimming and rejection.
 * ``run``: many independent chains (Alg. 1 loop) with the oracle's own RNG.
 * ``whiten`` / ``unwhiten``: App. A.
+* ``cholesky``: App. A's factor Sigma = L L^T (Cholesky-Banachiewicz).
 
 Parity of the Philox bit stream with the published known-answer vectors is
 unpinned here (the vectors are not available offline); it is pinned by
@@ -94,6 +95,8 @@ def _load():
         lib.orc_run.restype = ctypes.c_int
         lib.orc_whiten.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp]
         lib.orc_unwhiten.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp]
+        lib.orc_cholesky.argtypes = [_dp, ctypes.c_int, _dp]
+        lib.orc_cholesky.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -273,3 +276,16 @@ def unwhiten(L, mu, U):
     X = np.zeros((n, d))
     lib.orc_unwhiten(_ptr(L), _ptr(mu), d, n, _ptr(U), _ptr(X))
     return X
+
+
+def cholesky(S):
+    """App. A: the lower factor L with S = L L^T (only S's lower triangle is
+    read).  Raises ValueError naming the row whose pivot is not positive."""
+    lib = _load()
+    S = _f64(S)
+    n = S.shape[0]
+    L = np.zeros((n, n))
+    info = lib.orc_cholesky(_ptr(S), n, _ptr(L))
+    if info != 0:
+        raise ValueError(f"not positive definite: pivot of row {info - 1}")
+    return L

@@ -25,6 +25,8 @@
  *   - Sec. 3.3 (robustness):       optional trimming of constraint endpoints
  *                                   by eps; rejection of an infeasible x_{t+1}.
  *   - App. A (whitening):          A' = A L, b' = b - A mu; x = L u + mu.
+ *   - App. A (the factor L):       Sigma = L L^T by the Cholesky-Banachiewicz
+ *                                   recurrence, row by row.
  *
  * Readings taken where the paper is silent (each one is also listed in the
  * design notes of the repository):
@@ -477,4 +479,29 @@ void orc_unwhiten(const double *L, const double *mu, int d, int n, const double 
             x[i] = s + (mu ? mu[i] : 0.0);
         }
     }
+}
+
+/* App. A needs a factor L with Sigma = L L^T.  Cholesky-Banachiewicz, row by
+ * row: L_ij = (S_ij - sum_{k<j} L_ik L_jk) / L_jj for j < i, and
+ * L_ii = sqrt(S_ii - sum_{k<i} L_ik^2).  S is n x n row-major (only its lower
+ * triangle is read); L is n x n row-major with zeros above the diagonal.
+ * Returns 0, or i + 1 if the pivot of row i is not positive (S is not
+ * positive definite). */
+int orc_cholesky(const double *S, int n, double *L)
+{
+    for (size_t k = 0; k < (size_t)n * (size_t)n; ++k) L[k] = 0.0;
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = S[(size_t)i * (size_t)n + (size_t)j];
+            for (int k = 0; k < j; ++k)
+                s -= L[(size_t)i * (size_t)n + (size_t)k] * L[(size_t)j * (size_t)n + (size_t)k];
+            if (j < i) {
+                L[(size_t)i * (size_t)n + (size_t)j] = s / L[(size_t)j * (size_t)n + (size_t)j];
+            } else {
+                if (!(s > 0.0)) return i + 1;
+                L[(size_t)i * (size_t)n + (size_t)i] = sqrt(s);
+            }
+        }
+    }
+    return 0;
 }

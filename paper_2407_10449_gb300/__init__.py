@@ -45,6 +45,7 @@ EXPORTED = ("ess_default_config", "ess_create", "ess_destroy", "ess_limits", "es
             "ess_draw_normals",
             "ess_set_timing", "ess_get_timing", "ess_reset_timing",
             "ess_get_stats", "ess_reset_stats", "ess_whiten", "ess_unwhiten", "ess_step_noalloc",
+            "ess_cholesky",
             "ess_set_graphs", "ess_graph_launches", "ess_get_tuning",
             "ess_set_chain_kernel", "ess_get_chain_kernel",
             "ess_whitener_create", "ess_whitener_destroy", "ess_whitener_apply",
@@ -120,6 +121,7 @@ def load(build_if_missing: bool = True):
             "ess_chains_get": ([_vp, _vp, _vp], c_int),
             "ess_run_host": ([_vp, _vp, c_int, c_int, c_int, c_u64, _vp, c_int, _vp], c_int),
             "ess_run_few": ([_vp, _vp, c_int, c_int, c_int, c_u64, _vp, c_int, _vp], c_int),
+            "ess_cholesky": ([_vp, c_int, c_int, ctypes.POINTER(c_int), _vp], c_int),
             "ess_step_with_draws": ([_vp, _vp, _vp, _vp, c_int, _vp, _vp, _vp, c_int, _vp, _vp,
                                      _vp], c_int),
             "ess_products": ([_vp, _vp, _vp, c_int, _vp, _vp, _vp], c_int),
@@ -363,6 +365,30 @@ def ess_step_noalloc(A, b, X, nu, u, X_next, theta=None, rejected=None, stream=N
         _check(load().ess_step_noalloc(_ptr(A), _ptr(b), d, m, _ptr(X), _ptr(nu), _ptr(u), n,
                                        _ptr(X_next), _ptr(theta), _ptr(rejected),
                                        _stream_ptr(stream)))
+
+
+def ess_cholesky(A, stream=None):
+    """In place: the lower triangle of the CUDA float64 (n, n) tensor A becomes
+    its Cholesky factor L (see include/ess.h).  Returns A."""
+    import torch
+    if not (isinstance(A, torch.Tensor) and A.is_cuda and A.dtype == torch.float64 and A.dim() == 2
+            and A.shape[0] == A.shape[1] and A.stride(1) == 1):
+        raise ValueError("A must be a square CUDA float64 tensor with contiguous rows")
+    info = ctypes.c_int()
+    with torch.cuda.device(A.device):
+        _check(load().ess_cholesky(_ptr(A), A.shape[0], A.stride(0), ctypes.byref(info),
+                                   _stream_ptr(stream)))
+    return A
+
+
+def cholesky(S):
+    """Lower Cholesky factor of S (numpy or CUDA tensor) on the GPU, as a new
+    CUDA float64 tensor with zeros above the diagonal."""
+    import torch
+    A = torch.as_tensor(np.ascontiguousarray(S, dtype=np.float64) if isinstance(S, np.ndarray)
+                        else S, dtype=torch.float64).to("cuda").contiguous().clone()
+    ess_cholesky(A)
+    return torch.tril(A)
 
 
 def ess_whitener_create(L, mu=None):

@@ -1213,6 +1213,27 @@ ess_status ess_run_few(ess_state* s, double* X, int n_chains, int t0, int n_iter
   return read_status(s, st);
 }
 
+ess_status ess_cholesky(double* A, int n, int lda, int* info, void* cuda_stream) {
+  g_err.clear();
+  if (info) *info = 0;
+  if (!A || n < 1 || lda < n) return fail(ESS_ERR_ARG, "need A, n >= 1 and lda >= n");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int* dinfo = nullptr;
+  ESS_CUDA(dev_alloc(&dinfo, (size_t)1));
+  int h = 0;
+  cudaError_t e = cudaMemsetAsync(dinfo, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = ess::launch_cholesky(A, n, lda, dinfo, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dinfo);
+  if (e != cudaSuccess) return cuda_fail(e, "Cholesky factorisation");
+  if (info) *info = h;
+  if (h != 0)
+    return fail(ESS_ERR_ARG, "matrix is not positive definite (pivot of row " +
+                                 std::to_string(h - 1) + ")");
+  return ESS_OK;
+}
+
 ess_status ess_run_host(ess_state* s, double* X_host, int n_chains, int t0, int n_iter,
                         uint64_t seed, void* samples_host, int record_every, void* cuda_stream) {
   g_err.clear();

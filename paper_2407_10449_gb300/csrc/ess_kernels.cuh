@@ -254,6 +254,13 @@ size_t few_chains_smem(int C, int m, int chunk);
 int few_chains_chunk(int C, int d);
 cudaError_t launch_few_chains(const FewArgs& args, cudaStream_t s);
 
+// --------------------------------------------------------------- Cholesky ---
+// Lower Cholesky factor of the row-major n x n matrix A (leading dimension
+// lda), in place on its lower triangle (the strict upper triangle is left as
+// it is); *info (device, zero on entry) receives the 1-based row of the first
+// pivot that is not positive.
+cudaError_t launch_cholesky(double* A, int n, int lda, int* info, cudaStream_t s);
+
 // ---------------------------------------------------------------- batch ---
 // A work item of the grouped GEMMs: rows row0 .. row0 + rows - 1 of one
 // problem's A times `chains` consecutive chains of that problem, computed as

@@ -1,6 +1,6 @@
 """App. A on the GPU: x = L u + mu for batches of samples (ess_whitener_*).
 
-* FP64 samples: FP64 FMAs, within a few ulps of the exact product.
+* FP64 samples: FP64 FMAs, within a few ulps of the oracle's x = L u + mu.
 * float samples: the scaled FP16x3 tensor-core GEMM, within its stated bound
   (16 + d/16) 2^-24 sum_j |L_ij||u_j| plus the FP32 rounding of the result.
 * A run in whitened coordinates (App. A) mapped back on the GPU satisfies the
@@ -38,7 +38,7 @@ def test_whitener_fp64(d, n, with_mu):
         X = host(w(dev(U)))
     finally:
         w.close()
-    want = U @ L.T + (mu if mu is not None else 0.0)
+    want = oracle.unwhiten(L, mu, U)
     tol = 1e-13 * (np.abs(U) @ np.abs(L).T + (np.abs(mu) if mu is not None else 0.0)) + 1e-300
     assert np.all(np.abs(X - want) <= tol)
 

@@ -85,7 +85,8 @@ def probit(seed=0, n=2000, n_chains=4096, n_iter=500, lengthscale=0.2, jitter=1e
     Points U[0,1]^2, K = RBF(lengthscale) + jitter I, L = chol(K), z* ~ N(0, I),
     f* = L z*, y = sign(f*).  The posterior of the latent f ~ N(0, K) given
     y_i f_i >= 0 is the truncation of N(0, K) by A0 f <= 0 with
-    A0 = -diag(y).  Returned: (A0, b = 0, L, mu = 0, X0 = z* per chain).
+    A0 = -diag(y).  Returned: (A0, b = 0, K, L, mu = 0, X0 = z* per chain);
+    L (numpy's factor) draws the labels, and a sampler may factor K itself.
     The sampler runs in whitened coordinates (App. A): A = A0 L, b' = b.
     """
     rng = np.random.default_rng(seed)
@@ -99,7 +100,7 @@ def probit(seed=0, n=2000, n_chains=4096, n_iter=500, lengthscale=0.2, jitter=1e
     A0 = np.ascontiguousarray(-np.diag(y))
     b = np.zeros(n)
     X0 = np.tile(z, (n_chains, 1))
-    return dict(A0=A0, b=b, L=np.ascontiguousarray(L), mu=np.zeros(n), X0=X0,
+    return dict(A0=A0, b=b, K=K, L=np.ascontiguousarray(L), mu=np.zeros(n), X0=X0,
                 n_iter=n_iter, name=f"probit_n{n}")
 
 
