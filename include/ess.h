@@ -119,7 +119,12 @@ typedef struct {
     int fp64_products;          /* FP64 form: ess_products_mode; default
                                    ESS_PRODUCTS_DFMA (ignored by the mixed
                                    form) */
-    int reserved[5];
+    int wait_limit_us;          /* bounded device waits of the persistent
+                                   few-chain kernel (ess_run_few): a grid
+                                   barrier gives up after this many
+                                   microseconds and the call returns
+                                   ESS_ERR_TIMEOUT; 0 (default): 2 s */
+    int reserved[4];
 } ess_config;
 
 typedef struct {
@@ -128,7 +133,10 @@ typedef struct {
     long long residual_rechecks;/* rows whose FP64 residual was recomputed */
     long long tangent_fp64;     /* near-tangent roots evaluated in FP64 */
     double max_refresh_drift;   /* max |p_carried - p_refresh| / ||a_i|| seen */
-    double max_residual;        /* max a_i.x - b_i over emitted iterates (rechecked rows) */
+    double max_residual;        /* max a_i.x' - b_i over the candidate moves whose row was
+                                   rechecked in FP64, including moves the check then
+                                   rejected (a positive value means a rejection, not
+                                   an infeasible emitted iterate) */
     long long numeric_errors;   /* chains that produced NaN/Inf */
     long long sort_keys;        /* arcs left to sort after dropping dominated ones */
 } ess_stats;
@@ -385,6 +393,17 @@ ess_status ess_run_few(ess_state *state, double *X, int n_chains, int t0, int n_
 ess_status ess_cholesky(double *A, int n, int lda, int *info, void *cuda_stream);
 
 /*
+ * Self-test of the bounded waits (the paper has no counterpart): runs the
+ * persistent few-chain kernel of ess_run_few on the state with one chain of
+ * zeros and one CTA withholding its arrival at the first grid barrier (a
+ * dependency nothing releases).  Every CTA's wait runs out after
+ * cfg.wait_limit_us, the kernel returns, and so must this call, with
+ * ESS_ERR_TIMEOUT; the device stays usable.  FP64 states only
+ * (ESS_ERR_UNSUPPORTED otherwise).
+ */
+ess_status ess_selftest_wait(ess_state *state);
+
+/*
  * CUDA-graph replay of whole refresh periods in ess_chains_step / ess_run
  * (on by default).  A period -- the A x refresh and refresh_k steps -- is
  * captured once per (chain count, seed, p buffer) and replayed, the step index
@@ -453,12 +472,13 @@ ess_status ess_graph_launches(const ess_state *state, long long *launches);
  * index p, so its trajectory is the one-problem trajectory with that
  * problem index.
  *
- * Precision.  cfg->precision as for ess_create.  Mixed form: q = A nu with
- * FP32 fused multiply-adds (d_p <= a few hundred keeps the FP32 dot products
- * within ~d_p 2^-24 of sum |a||nu|), FP32 step, near-tangent roots, the
- * refresh of p = A x (every refresh_k steps, in double-float arithmetic on the
- * FP32 pipe, FP64-class accuracy) and the feasibility residual as in
- * ess_create.  FP64 form: everything in double.  cfg->sort_threads and
+ * Precision.  cfg->precision as for ess_create.  Mixed form: q = A nu on the
+ * tensor cores, the scaled FP16x3 products of ess_create (tcgen05, FP32
+ * accumulation in tensor memory; within (16 + d_p / 16) 2^-24 sum |a||nu|),
+ * FP32 step, near-tangent roots, the refresh of p = A x (every refresh_k
+ * steps, in double-float arithmetic on the FP32 pipe, FP64-class accuracy)
+ * and the feasibility residual as in ess_create.  FP64 form: everything in
+ * double (q by FP64 fused multiply-adds).  cfg->sort_threads and
  * cfg->refresh_mode are ignored.
  */
 typedef struct ess_batch ess_batch;

@@ -45,7 +45,7 @@ EXPORTED = ("ess_default_config", "ess_create", "ess_destroy", "ess_limits", "es
             "ess_draw_normals",
             "ess_set_timing", "ess_get_timing", "ess_reset_timing",
             "ess_get_stats", "ess_reset_stats", "ess_whiten", "ess_unwhiten", "ess_step_noalloc",
-            "ess_cholesky",
+            "ess_cholesky", "ess_selftest_wait",
             "ess_set_graphs", "ess_graph_launches", "ess_get_tuning",
             "ess_set_chain_kernel", "ess_get_chain_kernel",
             "ess_whitener_create", "ess_whitener_destroy", "ess_whitener_apply",
@@ -72,7 +72,7 @@ class ess_config(ctypes.Structure):
                 ("trim_eps", ctypes.c_double), ("residual_margin", ctypes.c_double),
                 ("sort_threads", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("q_tile", ctypes.c_int), ("fp64_products", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("wait_limit_us", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class ess_stats(ctypes.Structure):
@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True):
             "ess_run_host": ([_vp, _vp, c_int, c_int, c_int, c_u64, _vp, c_int, _vp], c_int),
             "ess_run_few": ([_vp, _vp, c_int, c_int, c_int, c_u64, _vp, c_int, _vp], c_int),
             "ess_cholesky": ([_vp, c_int, c_int, ctypes.POINTER(c_int), _vp], c_int),
+            "ess_selftest_wait": ([_vp], c_int),
             "ess_step_with_draws": ([_vp, _vp, _vp, _vp, c_int, _vp, _vp, _vp, c_int, _vp, _vp,
                                      _vp], c_int),
             "ess_products": ([_vp, _vp, _vp, c_int, _vp, _vp, _vp], c_int),
@@ -365,6 +366,12 @@ def ess_step_noalloc(A, b, X, nu, u, X_next, theta=None, rejected=None, stream=N
         _check(load().ess_step_noalloc(_ptr(A), _ptr(b), d, m, _ptr(X), _ptr(nu), _ptr(u), n,
                                        _ptr(X_next), _ptr(theta), _ptr(rejected),
                                        _stream_ptr(stream)))
+
+
+def ess_selftest_wait(state):
+    """Bounded-wait self-test (see include/ess.h): raises EssError with
+    ESS_ERR_TIMEOUT when the waits gave up as they should."""
+    _check(load().ess_selftest_wait(state))
 
 
 def ess_cholesky(A, stream=None):

@@ -736,6 +736,7 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
     return fail(ESS_ERR_ARG, "tangent_thresh in [0, 1), trim_eps >= 0, residual_margin >= 0");
   if (c.fp64_products != ESS_PRODUCTS_DFMA && c.fp64_products != ESS_PRODUCTS_SPLIT)
     return fail(ESS_ERR_ARG, "unknown fp64_products");
+  if (c.wait_limit_us < 0) return fail(ESS_ERR_ARG, "wait_limit_us must be >= 0");
   if (c.precision == ESS_PREC_MIXED && !ess::rows_fit_float_scales(A, b, m, d, true, 30))
     return fail(ESS_ERR_ARG,
                 "a row of A or an entry of b is outside the mixed form's float scaling range "
@@ -1129,8 +1130,33 @@ ess_status ess_run(ess_state* s, double* X, int n_chains, int t0, int n_iter, ui
   return rc;
 }
 
+namespace {
+ess_status run_few_impl(ess_state* s, double* X, int n_chains, int t0, int n_iter, uint64_t seed,
+                        double* samples, int record_every, void* cuda_stream, bool hold);
+}  // namespace
+
 ess_status ess_run_few(ess_state* s, double* X, int n_chains, int t0, int n_iter, uint64_t seed,
                        double* samples, int record_every, void* cuda_stream) {
+  return run_few_impl(s, X, n_chains, t0, n_iter, seed, samples, record_every, cuda_stream, false);
+}
+
+ess_status ess_selftest_wait(ess_state* s) {
+  g_err.clear();
+  if (!s) return fail(ESS_ERR_ARG, "state is NULL");
+  if (s->cfg.precision != ESS_PREC_FP64)
+    return fail(ESS_ERR_UNSUPPORTED, "the self-test runs the FP64 few-chain kernel");
+  DeviceGuard g(s->device);
+  double* X = nullptr;
+  ESS_CUDA(dev_alloc(&X, (size_t)s->d));
+  ESS_CUDA(cudaMemset(X, 0, sizeof(double) * s->d));
+  const ess_status rc = run_few_impl(s, X, 1, 0, 1, 0, nullptr, 0, nullptr, true);
+  cudaFree(X);
+  return rc;
+}
+
+namespace {
+ess_status run_few_impl(ess_state* s, double* X, int n_chains, int t0, int n_iter, uint64_t seed,
+                        double* samples, int record_every, void* cuda_stream, bool hold) {
   g_err.clear();
   if (!s) return fail(ESS_ERR_ARG, "state is NULL");
   if (s->cfg.precision != ESS_PREC_FP64)
@@ -1203,6 +1229,9 @@ ess_status ess_run_few(ess_state* s, double* X, int n_chains, int t0, int n_iter
   a.margin = s->cfg.residual_margin;
   a.stats = s->dstats;
   a.status = s->dstatus;
+  a.wait_ns = s->cfg.wait_limit_us > 0 ? 1000ull * (unsigned long long)s->cfg.wait_limit_us
+                                       : 2000000000ull;
+  a.hold = hold ? 1 : 0;
   const size_t smem = ess::few_chains_smem(n_chains, m, a.chunk);
   int optin = 0;
   ESS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
@@ -1212,6 +1241,7 @@ ess_status ess_run_few(ess_state* s, double* X, int n_chains, int t0, int n_iter
   s->host_steps += (long long)n_chains * n_iter;
   return read_status(s, st);
 }
+}  // namespace
 
 ess_status ess_cholesky(double* A, int n, int lda, int* info, void* cuda_stream) {
   g_err.clear();

@@ -248,6 +248,8 @@ struct FewArgs {
   double trim_eps, margin;
   DevStats* stats;
   int* status;
+  unsigned long long wait_ns;  // bound of a grid-barrier wait
+  int hold;                    // self-test: CTA 0 never arrives at the first barrier
 };
 // chunk of d staged per round in shared memory, and the dynamic shared memory
 size_t few_chains_smem(int C, int m, int chunk);

@@ -45,7 +45,6 @@ constexpr int kFT = 512;            // threads per CTA
 constexpr int kFW = kFT / 32;       // warps per CTA
 constexpr int kFB = kFewBuckets;    // angle buckets per chain
 constexpr double kFewW = kTwoPi / kFB;  // their width
-constexpr unsigned long long kFewWaitNs = 2000000000ull;  // 2 s per barrier
 
 __device__ __forceinline__ unsigned long long few_now() {
   unsigned long long t;
@@ -55,9 +54,11 @@ __device__ __forceinline__ unsigned long long few_now() {
 
 // Grid barrier over all CTAs of the cooperative launch (all co-resident):
 // arrivals counted in bar[0], release by bumping the generation in bar[1].  A
-// wait longer than kFewWaitNs sets the time-out status and the abort flag.
+// wait longer than wait_ns sets the time-out status and the abort flag.
+// withhold: this CTA waits without arriving (the self-test of the bound).
 // Returns false if the run is aborted (every CTA then leaves at this point).
-__device__ bool grid_barrier(unsigned* bar, int* abort_flag, int* status) {
+__device__ bool grid_barrier(unsigned* bar, int* abort_flag, int* status,
+                             unsigned long long wait_ns, bool withhold = false) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -65,7 +66,7 @@ __device__ bool grid_barrier(unsigned* bar, int* abort_flag, int* status) {
     const unsigned g = *gen;
     __threadfence();
     bool ok = true;
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+    if (!withhold && atomicAdd(bar, 1u) == gridDim.x - 1) {
       bar[0] = 0u;
       __threadfence();
       atomicAdd(bar + 1, 1u);
@@ -73,9 +74,10 @@ __device__ bool grid_barrier(unsigned* bar, int* abort_flag, int* status) {
       const unsigned long long t0 = few_now();
       int spins = 0;
       while (*gen == g) {
-        if (++spins == 256) {
+        if (++spins == 64) {
           spins = 0;
-          if (few_now() - t0 > kFewWaitNs) {
+          if (few_now() - t0 > wait_ns ||
+              *reinterpret_cast<volatile int*>(abort_flag) != 0) {
             ok = false;
             break;
           }
@@ -131,7 +133,8 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
     rng_block(a.seed, (uint32_t)n, (uint32_t)c, (uint32_t)a.t0, 0u, 0u, r);
     box_muller4(r, a.NU[a.t0 & 1] + (size_t)c * d + 4 * n, min(4, d - 4 * n), a.bm_tab);
   }
-  if (!grid_barrier(a.bar, a.abort_flag, a.status)) return;
+  if (!grid_barrier(a.bar, a.abort_flag, a.status, a.wait_ns, a.hold != 0 && blockIdx.x == 0))
+    return;
 
   long long rejections = 0, rechecks = 0, sort_keys = 0;
   for (int t = a.t0; t < a.t0 + a.n_iter; ++t) {
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
         }
       }
     }
-    if (!grid_barrier(a.bar, a.abort_flag, a.status)) return;
+    if (!grid_barrier(a.bar, a.abort_flag, a.status, a.wait_ns)) return;
     if (t == a.t0 && (*reinterpret_cast<volatile int*>(a.status) & kStatusInfeasible)) return;
 
     // ---- D: one CTA per chain: sort the arcs, Alg. 3 sweep, theta ----------------
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
       }
       __syncthreads();
     }
-    if (!grid_barrier(a.bar, a.abort_flag, a.status)) return;
+    if (!grid_barrier(a.bar, a.abort_flag, a.status, a.wait_ns)) return;
 
     // ---- E: move, FP64 recheck, nu of the next step, per-step state cleared ------
     {
@@ -482,7 +485,7 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
         }
       }
     }
-    if (!grid_barrier(a.bar, a.abort_flag, a.status)) return;
+    if (!grid_barrier(a.bar, a.abort_flag, a.status, a.wait_ns)) return;
   }
 
   // ---- end: the final states (and the last record) ------------------------------

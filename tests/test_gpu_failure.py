@@ -62,3 +62,30 @@ def test_non_finite_nu_rejects_and_reports(name, prec, cfg):
         assert max(abs(float(t) - r.theta) for t, r in zip(host(th2), refs)) <= tol
     finally:
         s.close()
+
+
+def test_bounded_wait_runs_out_and_the_device_stays_usable():
+    """A grid barrier of the persistent few-chain kernel whose dependency is
+    never released (one CTA withholds its arrival) gives up after the
+    configured limit: the call returns ESS_ERR_TIMEOUT, nothing hangs or
+    faults, and the same state then runs the oracle's chains."""
+    import time
+
+    import oracle
+    import workloads
+    inst = workloads.paper_hd(d=64, n_chains=3, seed=3)
+    s = ess.Sampler(inst.A, inst.b, precision=ess.ESS_PREC_FP64, wait_limit_us=20000)
+    try:
+        t0 = time.perf_counter()
+        with pytest.raises(ess.EssError) as e:
+            ess.ess_selftest_wait(s.state)
+        assert e.value.status == ess.ESS_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 10.0
+        X = dev(inst.X0)
+        ess.ess_run_few(s.state, X, 3, 0, 6, 2)
+        want = oracle.run(inst.A, inst.b, inst.X0, 6, seed=2)[0]
+        np.testing.assert_allclose(host(X), want, rtol=0, atol=1e-9 * (1 + np.abs(want).max()))
+    finally:
+        s.close()
+    with pytest.raises(ess.EssError):
+        ess.Sampler(inst.A, inst.b, precision=ess.ESS_PREC_FP64, wait_limit_us=-1)
