@@ -100,7 +100,9 @@ typedef struct {
                                    > 0: a CTA per chain for every chain, of
                                    sort_threads threads rounded up to a power
                                    of two (at least the width that holds m
-                                   arcs, at most 1024) */
+                                   arcs, at most 1024).  For m > 8192 the CTA
+                                   per chain is the wide-row kernel (512
+                                   threads, rows streamed), whatever the value */
     int autotune;               /* 0 (default): tile widths and the sort path
                                    from a cost model; 1: ess_chains_init times
                                    the candidates on the loaded chains and keeps
@@ -160,7 +162,12 @@ ess_status ess_create(const double *A, const double *b, int d, int m,
 /* Releases the state and all its device memory.  NULL is ignored. */
 void ess_destroy(ess_state *state);
 
-/* Largest supported m and d for the state's precision. */
+/*
+ * Largest supported m and d for the state's precision and row count: m up to
+ * 2^22 rows; d bounded by the shared memory of the chain-step kernel that
+ * takes the state's m (m <= 8192: the CTA-per-chain kernel; larger m: the
+ * wide-row kernel, which streams the rows).
+ */
 ess_status ess_limits(const ess_state *state, int *max_m, int *max_d);
 
 /*

@@ -69,6 +69,12 @@ struct ess_state {
   int ld16 = 0;           // row stride of the 16-bit operands (d rounded up to 8)
   int chain_threads = 0;  // threads per chain of the step kernel
   int min_chain_threads = 0;  // the narrowest CTA width that holds m arcs
+  // m beyond the CTA kernel's 8192 arcs: the wide-row kernel takes the chains
+  // the warp kernel leaves (or every chain when sort_threads > 0)
+  bool wide = false;
+  void* wide_scratch = nullptr;  // wide_slots x 4 x wide_cap elements of T
+  long long wide_cap = 0;
+  int wide_slots = 0;
   int tuned_n = 0;            // chain count the autotuner last tuned for
   // constants (device)
   double* A64 = nullptr;
@@ -379,6 +385,25 @@ template <typename T>
 ess_status launch_step(ess_state* s, ess::ChainParams<T> p, cudaStream_t st) {
   p.P_in = static_cast<const T*>(s->P);
   p.P_out = static_cast<T*>(s->P2);
+  if (s->wide) {
+    // m beyond the CTA kernel: the warp kernel, then the wide-row kernel for
+    // the chains it leaves (every chain when sort_threads > 0)
+    p.wide_scratch = static_cast<T*>(s->wide_scratch);
+    p.wide_cap = s->wide_cap;
+    if (s->cfg.sort_threads > 0) {
+      ESS_CUDA(ess::launch_chain_step_wide<T>(p, s->wide_slots, st));
+    } else {
+      ESS_CUDA(cudaMemsetAsync(s->ovf, 0, 2 * sizeof(int), st));
+      p.overflow_count = s->ovf;
+      p.overflow_list = s->ovf + 2;
+      ESS_CUDA(ess::launch_chain_step_warp<T>(p, st));
+      p.chain_list = s->ovf + 2;
+      p.list_count = s->ovf;
+      ESS_CUDA(ess::launch_chain_step_wide<T>(p, s->wide_slots, st));
+    }
+    std::swap(s->P, s->P2);
+    return ESS_OK;
+  }
   if (s->cfg.sort_threads > 0) {
     ESS_CUDA(ess::launch_chain_step<T>(p, s->chain_threads, st));
   } else {
@@ -493,6 +518,8 @@ ess_status autotune(ess_state* s, int t0, cudaStream_t st) {
   float best_ms = 0.f;
   for (int c = 0; c < 4 && rc == ESS_OK; ++c) {
     if (cands[c][1] > ess::kChainMaxThreads) continue;
+    // wide rows: the warp kernel with the wide-row kernel behind it
+    if (s->wide && c != 1) continue;
     // the streamed kernel exists for float chains with supported shapes
     if (c == 0 && !(mixed(s) && ess::chain_stream_supported(s->m, s->d))) continue;
     s->chain_kernel = cands[c][2];
@@ -500,7 +527,7 @@ ess_status autotune(ess_state* s, int t0, cudaStream_t st) {
                                  : ess::chain_smem_bytes<double>(cands[c][1], d);
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
-    if (smem + 1024 > (size_t)optin) continue;
+    if (!s->wide && smem + 1024 > (size_t)optin) continue;
     s->cfg.sort_threads = cands[c][0];
     s->chain_threads = cands[c][1];
     float ms = 0.f;
@@ -752,14 +779,19 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
     return fail(ESS_ERR_ARG,
                 "q_tile: 0, 64/128/160/192/224/256, or 2000/3000 + 128/160/192/224/256");
 
+  if (m > ess::kMaxRows)
+    return fail(ESS_ERR_UNSUPPORTED, "m exceeds the chain step's row limit (2^22)");
+  // m beyond the CTA kernel's shared-memory sort (8192 arcs): wide rows
   const int min_threads = ess::chain_threads_for(m);
-  if (min_threads == 0)
-    return fail(ESS_ERR_UNSUPPORTED, "m exceeds the per-chain shared-memory sort limit (8192)");
+  const bool wide = min_threads == 0;
   // a CTA per chain: at least the minimum width, wider if sort_threads asks
   int threads = min_threads;
-  while (threads < c.sort_threads && threads < ess::kChainMaxThreads) threads <<= 1;
-  const size_t smem = c.precision == ESS_PREC_MIXED ? ess::chain_smem_bytes<float>(threads, d)
-                                                    : ess::chain_smem_bytes<double>(threads, d);
+  while (!wide && threads < c.sort_threads && threads < ess::kChainMaxThreads) threads <<= 1;
+  const size_t smem =
+      wide ? (c.precision == ESS_PREC_MIXED ? ess::chain_wide_smem_bytes<float>(d)
+                                            : ess::chain_wide_smem_bytes<double>(d))
+           : (c.precision == ESS_PREC_MIXED ? ess::chain_smem_bytes<float>(threads, d)
+                                            : ess::chain_smem_bytes<double>(threads, d));
   int dev = 0;
   ESS_CUDA(cudaGetDevice(&dev));
   int smem_optin = 0;
@@ -775,6 +807,7 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
   s->ld16 = (d + 7) & ~7;
   s->chain_threads = threads;
   s->min_chain_threads = min_threads;
+  s->wide = wide;
 
   auto cleanup = [&](ess_status st) {
     ess_destroy(s);
@@ -814,6 +847,14 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
   if (e == cudaSuccess) e = dev_alloc(&s->dstats, 1);
   if (e == cudaSuccess) e = dev_alloc(&s->dstatus, 1);
   if (e == cudaSuccess) e = dev_alloc(&s->t_dev, 1);
+  if (e == cudaSuccess && wide) {
+    // scratch slots of the wide-row kernel (one per CTA of its launch)
+    s->wide_slots = ess::chain_wide_slots(dev);
+    s->wide_cap = c.precision == ESS_PREC_MIXED ? ess::chain_wide_cap<float>(m)
+                                                : ess::chain_wide_cap<double>(m);
+    const size_t esz = c.precision == ESS_PREC_MIXED ? sizeof(float) : sizeof(double);
+    e = cudaMalloc(&s->wide_scratch, (size_t)s->wide_slots * 4 * (size_t)s->wide_cap * esz);
+  }
   if (e == cudaSuccess) {
     std::vector<double> tab(ess::kBmTableSize);
     ess::bm_table_fill(tab.data());
@@ -867,6 +908,8 @@ void ess_destroy(ess_state* s) {
     if (s->slot_free[k]) cudaEventDestroy(s->slot_free[k]);
   }
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+  if (s->wide_scratch) cudaFree(s->wide_scratch);
+  s->wide_scratch = nullptr;
   dev_free(s->few_x);
   dev_free(s->few_nu);
   dev_free(s->few_p);
@@ -881,12 +924,16 @@ void ess_destroy(ess_state* s) {
 
 ess_status ess_limits(const ess_state* s, int* max_m, int* max_d) {
   if (!s || !max_m || !max_d) return fail(ESS_ERR_ARG, "NULL argument");
-  *max_m = ess::kChainMaxThreads * ess::kChainItems;
+  *max_m = ess::kMaxRows;
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
   const size_t esz = mixed(s) ? sizeof(float) : sizeof(double);
-  const size_t base = mixed(s) ? ess::chain_smem_bytes<float>(s->chain_threads, 0)
-                               : ess::chain_smem_bytes<double>(s->chain_threads, 0);
+  // d is bounded by the shared memory of the kernel that takes this state's m
+  const size_t base =
+      s->wide ? (mixed(s) ? ess::chain_wide_smem_bytes<float>(0)
+                          : ess::chain_wide_smem_bytes<double>(0))
+              : (mixed(s) ? ess::chain_smem_bytes<float>(s->chain_threads, 0)
+                          : ess::chain_smem_bytes<double>(s->chain_threads, 0));
   long long room = (long long)smem_optin - 1024 - (long long)base;
   *max_d = room > 0 ? (int)(room / (long long)esz) - 1 : 0;
   return ESS_OK;

@@ -113,6 +113,10 @@ struct ChainParams {
   const unsigned* t_dev;
   // streamed warp kernel: chain tickets (zero before each launch)
   int* work_counter;
+  // wide-row kernel: per-CTA scratch slots of 4 wide_cap elements (arcs and
+  // their merge-sort buffer, used when a chain's arcs outgrow shared memory)
+  T* wide_scratch;
+  long long wide_cap;
 };
 
 // The rows of one chain as a kernel sees them.
@@ -200,6 +204,24 @@ constexpr int kWarpSortCap = 128;
 bool chain_stream_supported(int m, int d);
 bool chain_stream_aligned(const ChainParams<float>& p);
 cudaError_t launch_chain_step_stream(const ChainParams<float>& p, cudaStream_t s);
+
+// ------------------------------------------------------------ wide rows ----
+// One CTA per chain for any m up to kMaxRows: the rows are streamed (three
+// passes), the exact arcs merged per alpha bucket, short arcs and the sort
+// spilled to a per-CTA scratch slot when they outgrow shared memory
+// (k_chain_wide.cu).  All chains of p (chain_list == nullptr) or, in list
+// mode, the chains of p.chain_list[0 .. *p.list_count).  Single-problem
+// chains only (p.desc == nullptr); p.P_out must differ from p.P_in.
+// p.wide_scratch holds `slots` slots of 4 chain_wide_cap<T>(m) elements; the
+// launch uses at most `slots` CTAs.
+constexpr int kMaxRows = 1 << 22;  // rows a chain step takes (warp kernel's row code)
+template <typename T>
+size_t chain_wide_smem_bytes(int d);
+template <typename T>
+long long chain_wide_cap(int m);
+int chain_wide_slots(int device);
+template <typename T>
+cudaError_t launch_chain_step_wide(const ChainParams<T>& p, int slots, cudaStream_t s);
 
 // ------------------------------------------------------------ few chains ---
 // FP64 chains of one polytope, 1 .. kMaxFew at a time: all steps of a run in

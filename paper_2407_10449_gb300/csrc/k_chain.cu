@@ -33,6 +33,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "chain_block_ops.cuh"
 #include "chain_math.cuh"
 #include "ess_kernels.cuh"
 
@@ -40,53 +41,9 @@ namespace ess {
 namespace {
 
 using namespace chainmath;
-
-// ---- block scans ---------------------------------------------------------
-struct OpAdd {
-  template <typename V> __device__ V operator()(V a, V b) const { return a + b; }
-};
-struct OpMax {
-  template <typename V> __device__ V operator()(V a, V b) const { return a > b ? a : b; }
-};
-
-// Exclusive block scan; returns the exclusive prefix of `v`, sets `total`.
-// `tmp` holds NT/32 values.  Contains __syncthreads (call uniformly).
-template <int NT, typename V, typename Op>
-__device__ V block_exclusive_scan(V v, V identity, Op op, V* tmp, V& total) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  constexpr int NW = NT / 32;
-  V x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    V y = __shfl_up_sync(kFull, x, o);
-    if (lane >= o) x = op(x, y);
-  }
-  if (lane == 31) tmp[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    V t = lane < NW ? tmp[lane] : identity;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      V y = __shfl_up_sync(kFull, t, o);
-      if (lane >= o) t = op(t, y);
-    }
-    if (lane < NW) tmp[lane] = t;
-  }
-  __syncthreads();
-  V warp_prefix = w > 0 ? tmp[w - 1] : identity;
-  total = tmp[NW - 1];
-  // exclusive within the warp
-  V incl_prev = __shfl_up_sync(kFull, x, 1);
-  V excl = lane > 0 ? op(warp_prefix, incl_prev) : warp_prefix;
-  __syncthreads();
-  return excl;
-}
+using namespace blockops;
 
 // ---- kernel ----------------------------------------------------------------
-// Shared-memory slot of sorted position e: one padding word per 32 keeps the
-// per-thread chunks (stride ITEMS) on distinct banks.
-__device__ __forceinline__ int pad_idx(int e) { return e + (e >> 5); }
-
 constexpr int kBuckets = 64;  // alpha buckets of the domination prune
 // Alpha buckets of the interval merge (at most): 2048 for float chains; 512
 // for double chains, whose larger arrays would otherwise cost the CTA kernel
@@ -330,64 +287,7 @@ __global__ void __launch_bounds__(NT, (768 / NT > 0 ? 768 / NT : 1)) chain_step_
     key[i] = owns ? s_key[pad_idx(base + i)] : inf;
     val[i] = owns ? s_val[pad_idx(base + i)] : T(0);
   }
-  // bitonic network over the thread's ITEMS registers
-#pragma unroll
-  for (int kk = 2; kk <= ITEMS; kk <<= 1) {
-#pragma unroll
-    for (int j = kk >> 1; j > 0; j >>= 1) {
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        const int l = i ^ j;
-        if (l > i) {
-          const bool up = (i & kk) == 0;
-          if ((key[i] > key[l]) == up) {
-            T tk = key[i]; key[i] = key[l]; key[l] = tk;
-            T tv = val[i]; val[i] = val[l]; val[l] = tv;
-          }
-        }
-      }
-    }
-  }
-  // merge-path merges of sorted runs of width ITEMS, 2 ITEMS, ... until one
-  // run holds every arc
-  for (int w = ITEMS; w < n_active_slots; w <<= 1) {
-    __syncthreads();
-    if (owns) {
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        s_key[pad_idx(base + i)] = key[i];
-        s_val[pad_idx(base + i)] = val[i];
-      }
-    }
-    __syncthreads();
-    if (owns) {
-      const int start = base & ~(2 * w - 1);
-      const int diag = base - start;
-      // runs [start, start + w) and [start + w, start + 2w), clipped to the arcs
-      const int a_end = min(w, n_active_slots - start);
-      const int b_len = max(0, min(w, n_active_slots - start - w));
-      int lo = diag - b_len > 0 ? diag - b_len : 0;
-      int hi = diag < a_end ? diag : a_end;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (!(s_key[pad_idx(start + w + diag - 1 - mid)] < s_key[pad_idx(start + mid)])) lo = mid + 1;
-        else hi = mid;
-      }
-      int ia = lo, ib = diag - lo;
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        const bool a_ok = ia < a_end;
-        const bool b_ok = ib < b_len;
-        const T ka = a_ok ? s_key[pad_idx(start + ia)] : inf;
-        const T kb = b_ok ? s_key[pad_idx(start + w + ib)] : inf;
-        const bool take_a = a_ok && (!b_ok || !(kb < ka));
-        key[i] = take_a ? ka : kb;
-        val[i] = take_a ? s_val[pad_idx(start + ia)] : (b_ok ? s_val[pad_idx(start + w + ib)] : T(0));
-        ia += take_a ? 1 : 0;
-        ib += take_a ? 0 : 1;
-      }
-    }
-  }
+  block_sort_arcs<ITEMS, T>(key, val, n_active_slots, s_key, s_val, inf);
   }  // sorted arcs
 
   // ---- 3. Alg. 3: gamma_k = cumulative max of beta ----------------------

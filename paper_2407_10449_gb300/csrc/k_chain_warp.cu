@@ -53,6 +53,11 @@ constexpr int kWarps = 8;                 // chains per CTA
 #define ESS_WARP_MINBLOCKS_F64 4
 #endif
 constexpr int kBatchF32 = ESS_WARP_BATCH;  // rows per lane in flight per loop trip (float)
+// Candidate codes: a kept row is 0x80000000 | i; an arc is bucket << kRowBits
+// | i (buckets < kWB = 2^9 fill bits 22 .. 30), so rows up to 2^22.
+constexpr int kRowBits = 22;
+constexpr unsigned kRowMask = (1u << kRowBits) - 1u;
+static_assert(kWB <= 512, "bucket field of the candidate code");
 
 template <typename T, int WARPS, bool BATCH>
 __global__ void __launch_bounds__(WARPS * 32,
@@ -176,7 +181,7 @@ chain_warp_kernel(ChainParams<T> prm) {
           // it would dominate
           if (approx && undominated) atomicMax(&bfull[bslot(bk + 2)], __float_as_uint(pb));
           push(cls == kRowKeep || (approx && undominated),
-               cls == kRowKeep ? (0x80000000u | (unsigned)i) : (((unsigned)bk << 14) | (unsigned)i),
+               cls == kRowKeep ? (0x80000000u | (unsigned)i) : (((unsigned)bk << kRowBits) | (unsigned)i),
                pb);
         }
         // rare: r = 0 with b_i < 0 means x violates row i (App. B)
@@ -215,7 +220,7 @@ chain_warp_kernel(ChainParams<T> prm) {
               const int bk = pbucket(pa);
               cand = !(pb + 2.f * kPhiMargin <= __uint_as_float(bsub[bslot(bk)]));
               if (cand) atomicMax(&bfull[bslot(bk + 2)], __float_as_uint(pb));
-              code = ((unsigned)bk << 14) | (unsigned)i;
+              code = ((unsigned)bk << kRowBits) | (unsigned)i;
             }
           }
           push(cand, code, pb);
@@ -235,11 +240,11 @@ chain_warp_kernel(ChainParams<T> prm) {
         int row = 0;
         if (e < n_cand) {
           const unsigned code = candc[e];
-          row = (int)(code & 0x3FFFu);
+          row = (int)(code & kRowMask);
           if (code & 0x80000000u) {
             keep = true;
           } else {
-            const int bk = (int)((code >> 14) & 0x3FFu);
+            const int bk = (int)((code >> kRowBits) & 0x1FFu);
             keep = !(candb[e] + 2.f * kPhiMargin <= __uint_as_float(bfull[bslot(bk)]));
           }
         }
