@@ -587,6 +587,37 @@ def time_configs(ess, torch, workloads, peaks, seed, errors=True):
         entry[form] = r
     out["batched_512_problems"] = entry
     out.update(time_paper_hd(ess, torch, workloads, peaks, seed))
+    out.update(time_wide(ess, torch, workloads, peaks, seed, errors))
+    return out
+
+
+def time_wide(ess, torch, workloads, peaks, seed, errors=True):
+    """m beyond the CTA kernel's 8192 arcs: the metric family at m = 16384
+    (the warp kernel keeps nearly every chain) and a probit-style orthant at
+    m = 16384, d = 256 (every arc survives the prune: every chain goes to the
+    wide-row kernel), both forms, with the phase rooflines of time_configs."""
+    out = {}
+    cases = [("metric_d1000_m16384_c8192", workloads.metric(n_chains=1, m=16384), 8192,
+              (("mixed", 64), ("fp64", 32))),
+             ("probit_features_d256_m16384_c2048", workloads.probit_features(n_chains=1), 2048,
+              (("mixed", 64), ("fp64", 32)))]
+    for name, inst, C, forms in cases:
+        entry = {"m": inst.m, "d": inst.d, "chains": C}
+        for form, steps in forms:
+            ms, timing, stats, _, lc = time_form(ess, torch, inst, form, C, steps, 3, seed, 1, 0,
+                                                 keep=ERR_SAMPLE if errors else 0)
+            ph = phase_rooflines(inst, C, timing, form, peaks)
+            dom = max(ph, key=lambda k: ph[k]["share"]) if ph else None
+            entry[form] = {"value": C * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
+                           "ms_per_step": ms / steps, "window": lc["window"],
+                           "dominant": dom, "dominant_frac": ph[dom]["frac"] if dom else None,
+                           "phases": ph, "rejections": stats["rejections"],
+                           "numeric_errors": stats["numeric_errors"],
+                           "arcs_per_chain_step": stats["sort_keys"] / max(1, stats["steps"])}
+            if errors:
+                entry[form]["error_vs_oracle"] = oracle_errors(ess, torch, inst.A, inst.b,
+                                                               lc["states"], form, seed)
+        out[name] = entry
     return out
 
 

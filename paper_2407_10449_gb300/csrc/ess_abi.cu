@@ -386,11 +386,13 @@ ess_status launch_step(ess_state* s, ess::ChainParams<T> p, cudaStream_t st) {
   p.P_in = static_cast<const T*>(s->P);
   p.P_out = static_cast<T*>(s->P2);
   if (s->wide) {
-    // m beyond the CTA kernel: the warp kernel, then the wide-row kernel for
-    // the chains it leaves (every chain when sort_threads > 0)
+    // m beyond the CTA kernel: the wide-row kernel for every chain (measured
+    // faster at m = 12000 and 16384, where most chains keep more arcs than a
+    // warp sorts), or with ESS_CHAIN_WARP the warp kernel first and the
+    // wide-row kernel for the chains it leaves
     p.wide_scratch = static_cast<T*>(s->wide_scratch);
     p.wide_cap = s->wide_cap;
-    if (s->cfg.sort_threads > 0) {
+    if (s->cfg.sort_threads > 0 || s->chain_kernel != ESS_CHAIN_WARP) {
       ESS_CUDA(ess::launch_chain_step_wide<T>(p, s->wide_slots, st));
     } else {
       ESS_CUDA(cudaMemsetAsync(s->ovf, 0, 2 * sizeof(int), st));
@@ -518,8 +520,9 @@ ess_status autotune(ess_state* s, int t0, cudaStream_t st) {
   float best_ms = 0.f;
   for (int c = 0; c < 4 && rc == ESS_OK; ++c) {
     if (cands[c][1] > ess::kChainMaxThreads) continue;
-    // wide rows: the warp kernel with the wide-row kernel behind it
-    if (s->wide && c != 1) continue;
+    // wide rows: the wide-row kernel for every chain, or the warp kernel
+    // with the wide-row kernel behind it
+    if (s->wide && c != 1 && c != 2) continue;
     // the streamed kernel exists for float chains with supported shapes
     if (c == 0 && !(mixed(s) && ess::chain_stream_supported(s->m, s->d))) continue;
     s->chain_kernel = cands[c][2];
@@ -1097,7 +1100,8 @@ ess_status ess_set_chain_kernel(ess_state* s, int kind) {
 
 ess_status ess_get_chain_kernel(const ess_state* s, int* kind) {
   if (!s || !kind) return fail(ESS_ERR_ARG, "NULL argument");
-  if (s->cfg.sort_threads > 0) *kind = ESS_CHAIN_CTA;
+  if (s->cfg.sort_threads > 0 || (s->wide && s->chain_kernel != ESS_CHAIN_WARP))
+    *kind = ESS_CHAIN_CTA;
   else if (mixed(s) && s->chain_kernel == ESS_CHAIN_STREAM && ess::chain_stream_supported(s->m, s->d))
     *kind = ESS_CHAIN_STREAM;
   else *kind = ESS_CHAIN_WARP;

@@ -5,9 +5,15 @@
 // edge cases, Alg. 3 sort and cumulative-max sweep, inverse-CDF theta, move
 // and the Sec. 3.3 safeguard); only the storage differs, so that m is bounded
 // by memory instead of by one CTA's registers and shared memory:
-//   1. a pass over the rows: approximate arcs give the maximum beta per alpha
-//      bucket (64 buckets) for the domination prune;
-//   2. a second pass: every row that is not dominated gets its exact roots,
+//   1. a pass over the rows: each row's arc is placed by the pseudo-angles of
+//      its two roots (a monotone stand-in for the angle, without
+//      trigonometry) in one of 512 buckets, for the domination prune of the
+//      warp kernel (an arc that lies inside an arc starting two buckets
+//      earlier changes no piece): a first batch of rows gives bucket maxima,
+//      the later rows that no first-batch arc covers become candidates;
+//   2. the first batch and the candidates (or, when the candidates overflow
+//      their list, all rows again) are tested against the full maxima, and
+//      every row that is not dominated gets its exact roots,
 //      merged into its alpha bucket (NB buckets of width 2 pi / NB): an arc
 //      that reaches the end of its bucket contains that point, so all such
 //      arcs of a bucket overlap and their union is [min alpha, max beta]; a
@@ -32,6 +38,7 @@
 
 #include "chain_block_ops.cuh"
 #include "chain_math.cuh"
+#include "chain_warp_ops.cuh"
 #include "ess_kernels.cuh"
 
 namespace ess {
@@ -39,16 +46,38 @@ namespace {
 
 using namespace chainmath;
 using namespace blockops;
+using warpops::bslot;
+using warpops::kPhiMargin;
+using warpops::kWBP;
+using warpops::pbucket;
+using warpops::prefix_max;
 
-constexpr int kWT = 512;                       // threads per CTA
+#ifndef ESS_WIDE_THREADS
+#define ESS_WIDE_THREADS 512
+#endif
+#ifndef ESS_WIDE_MINBLOCKS
+#define ESS_WIDE_MINBLOCKS 2
+#endif
+#ifndef ESS_WIDE_ROWS
+#define ESS_WIDE_ROWS 2
+#endif
+constexpr int kWT = ESS_WIDE_THREADS;          // threads per CTA
 constexpr int kWW = kWT / 32;                  // warps per CTA
-constexpr int kWItems = 8;                     // sorted arcs per thread
-constexpr int kWSlots = kWT * kWItems;         // arcs sorted at once (4096)
+constexpr int kWSlots = 4096;                  // arcs sorted at once in shared memory
+constexpr int kWItems = kWSlots / kWT;         // sorted arcs per thread
 constexpr int kWPad = kWSlots + kWSlots / 32;  // padded shared arrays
-constexpr int kWU = 4;                         // rows per thread per pass trip
+constexpr int kWU = ESS_WIDE_ROWS;             // rows per thread per pass trip
 constexpr int kWTrip = kWT * kWU;              // rows per pass trip
 constexpr int kWFlag = 2 * kWTrip;             // flagged rows held before a recheck batch
-constexpr int kWPB = 64;                       // buckets of the domination prune
+constexpr int kWFirst = 2048;                  // rows of the prune's first batch
+// Candidate rows held after the first batch: 2048 (float chains), 1024
+// (double chains: two CTAs per SM at d = 1000).
+template <typename T>
+constexpr int wide_cand() { return sizeof(T) == 8 ? 1024 : 2048; }
+// Candidate codes: a kept row is 0x80000000 | i; an arc is bucket << kWRowBits
+// | i (buckets below 512 in bits 22 .. 30), so rows up to 2^22.
+constexpr int kWRowBits = 22;
+constexpr unsigned kWRowMask = (1u << kWRowBits) - 1u;
 
 // Merge buckets: 2048 for float chains, 1024 for double chains (whose wider
 // entries would otherwise cost a CTA per SM at d = 1000).
@@ -237,9 +266,11 @@ __device__ void global_sort_arcs(T* k0, T* v0, T* k1, T* v1, int n, T* s_key, T*
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kWT, 2) chain_wide_kernel(ChainParams<T> prm) {
+__global__ void __launch_bounds__(kWT, ESS_WIDE_MINBLOCKS) chain_wide_kernel(ChainParams<T> prm) {
   constexpr int NB = wide_buckets<T>();
   constexpr int NSH = wide_short_smem<T>();
+  constexpr int NC = wide_cand<T>();
+  static_assert(NC <= kWFlag, "candidate codes share the recheck list");
   constexpr int BPT = NB / kWT;  // buckets per thread
   using Bits = BitsOf<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -248,13 +279,20 @@ __global__ void __launch_bounds__(kWT, 2) chain_wide_kernel(ChainParams<T> prm) 
   Bits* s_bmin = reinterpret_cast<Bits*>(s_val + kWPad);
   Bits* s_bmax = s_bmin + NB;
   int* s_flag = reinterpret_cast<int*>(s_bmax + NB);
-  T* s_x = reinterpret_cast<T*>(s_flag + kWFlag);
+  // candidate rows of the prune (codes in the recheck list's space, which is
+  // free until the move) and their pseudo-beta
+  unsigned* s_ccode = reinterpret_cast<unsigned*>(s_flag);
+  float* s_cpb = reinterpret_cast<float*>(s_flag + kWFlag);
+  T* s_x = reinterpret_cast<T*>(s_cpb + NC);
 
-  __shared__ unsigned s_pmax[kWPB];  // max approximate beta (bits) per prune bucket
-  __shared__ float s_gearly[kWPB];   // max approximate beta over buckets <= j - 2
+  // prune buckets: the max pseudo-beta (bits) of the arcs of pseudo-alpha
+  // bucket j sits in slot bslot(j + 2); after the prefix max, slot bslot(j)
+  // holds the max over the buckets <= j - 2
+  __shared__ __align__(16) unsigned s_pbk[kWBP];
+  __shared__ __align__(16) unsigned s_pbf[kWBP];  // the later rows' maxima, then the full ones
   __shared__ int s_itmp[kWW];
   __shared__ T s_ttmp[kWW];
-  __shared__ int s_nshort, s_nflag, s_reject, s_bad, s_tangent, s_best, s_infeasible;
+  __shared__ int s_ncand, s_nshort, s_nflag, s_reject, s_bad, s_tangent, s_best, s_infeasible;
   __shared__ T s_theta;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -275,6 +313,7 @@ __global__ void __launch_bounds__(kWT, 2) chain_wide_kernel(ChainParams<T> prm) 
     const T* Qrow = v.Q;
     __syncthreads();
     if (tid == 0) {
+      s_ncand = 0;
       s_nshort = 0;
       s_nflag = 0;
       s_reject = 0;
@@ -283,20 +322,68 @@ __global__ void __launch_bounds__(kWT, 2) chain_wide_kernel(ChainParams<T> prm) 
       s_best = -1;
       s_infeasible = 0;
     }
-    for (int k = tid; k < kWPB; k += kWT) s_pmax[k] = 0u;
+    for (int k = tid; k < kWBP; k += kWT) {
+      s_pbk[k] = 0u;
+      s_pbf[k] = 0u;
+    }
     for (int k = tid; k < NB; k += kWT) {
       s_bmin[k] = empty_bits<T>();
       s_bmax[k] = 0;
     }
     __syncthreads();
 
-    const T tlo = (T)(1.0 - prm.tangent_thresh);
-    const T thi = (T)(1.0 + prm.tangent_thresh);
-    const float to_pbucket = (float)(kWPB / kTwoPi);
+    // squared thresholds of the float classification (1e-6 relative slack
+    // around the exact test of roots())
+    const float tlo_s = (float)((1.0 - prm.tangent_thresh) * 0.999999);
+    const float thi_s = (float)((1.0 + prm.tangent_thresh) * 1.000001);
+    const float tlo2 = tlo_s * tlo_s, thi2 = thi_s * thi_s;
     bool infeasible = false, nonfinite = false;
+    // class and pseudo-angles of one row (a row with r = 0 has no root; x
+    // violates it iff b_i < 0, read from the exact b in that rare case)
+    auto classify = [&](T p, T q, T b, int i, float& pa, float& pb, bool& inf_row) {
+      if constexpr (sizeof(T) == 4) {
+        bool zero = false;
+        const int cls = classify_phi_nb(p, q, b, tlo2, thi2, pa, pb, zero, nonfinite);
+        if (zero) inf_row |= v.b64[i] < 0.0;
+        return cls;
+      } else {
+        (void)i;
+        (void)inf_row;
+        return classify_phi_d(p, q, b, tlo2, thi2, pa, pb, nonfinite);
+      }
+    };
 
-    // ---- 1. approximate arcs: max beta per prune bucket ----------------------
-    for (int i0 = 0; i0 < m; i0 += kWTrip) {
+    // ---- 1. pseudo-angle arcs: the domination prune ----------------------------
+    // A first batch of rows gives per-bucket maxima (s_pbk, then prefix-maxed);
+    // every later row is tested against them: a row whose arc lies inside a
+    // first-batch arc starting two buckets earlier is dropped, the others add
+    // to the full maxima (s_pbf) and join the candidate list.  (A dropped row
+    // adds nothing to the full maxima: the first-batch arc that covers it
+    // dominates every arc it would dominate.)
+    const int m_first = min(m, kWFirst);
+    for (int i0 = 0; i0 < m_first; i0 += kWTrip) {
+      T pv[kWU], qv[kWU], bv[kWU];
+#pragma unroll
+      for (int k = 0; k < kWU; ++k) {
+        const int i = i0 + tid + k * kWT;
+        pv[k] = i < m_first ? Prow[i] : T(0);
+        qv[k] = i < m_first ? Qrow[i] : T(0);
+        bv[k] = i < m_first ? v.b[i] : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < kWU; ++k) {
+        const int i = i0 + tid + k * kWT;
+        if (i < m_first) {
+          float pa = 0.f, pb = 0.f;
+          const int cls = classify(pv[k], qv[k], bv[k], i, pa, pb, infeasible);
+          if (cls == kRowApprox) atomicMax(&s_pbk[bslot(pbucket(pa) + 2)], __float_as_uint(pb));
+        }
+      }
+    }
+    __syncthreads();
+    if (warp == 0) prefix_max(s_pbk, lane);
+    __syncthreads();
+    for (int i0 = m_first; i0 < m; i0 += kWTrip) {
       T pv[kWU], qv[kWU], bv[kWU];
 #pragma unroll
       for (int k = 0; k < kWU; ++k) {
@@ -308,93 +395,122 @@ __global__ void __launch_bounds__(kWT, 2) chain_wide_kernel(ChainParams<T> prm) 
 #pragma unroll
       for (int k = 0; k < kWU; ++k) {
         const int i = i0 + tid + k * kWT;
+        bool cand = false;
+        unsigned code = 0u;
+        float pb = 0.f;
         if (i < m) {
-          nonfinite |= !isfinite(pv[k]) || !isfinite(qv[k]);
-          float a_ap = 0.f, b_ap = 0.f;
-          bool inf_row = false;
-          const int cls = classify_row<T>(pv[k], qv[k], bv[k], v.b64[i], tlo, thi, a_ap, b_ap,
-                                          inf_row);
-          infeasible |= inf_row;
-          if (cls == kRowApprox)
-            atomicMax(&s_pmax[min(kWPB - 1, (int)(a_ap * to_pbucket))], __float_as_uint(b_ap));
+          float pa = 0.f;
+          const int cls = classify(pv[k], qv[k], bv[k], i, pa, pb, infeasible);
+          const int bk = pbucket(pa);
+          const bool undominated =
+              !(pb + 2.f * kPhiMargin <= __uint_as_float(s_pbk[bslot(bk)]));
+          if (cls == kRowApprox && undominated)
+            atomicMax(&s_pbf[bslot(bk + 2)], __float_as_uint(pb));
+          cand = cls == kRowKeep || (cls == kRowApprox && undominated);
+          code = cls == kRowKeep ? (0x80000000u | (unsigned)i)
+                                 : (((unsigned)bk << kWRowBits) | (unsigned)i);
+        }
+        // candidate list: one shared atomic per warp
+        const unsigned ball = __ballot_sync(kFull, cand);
+        if (ball) {
+          const int leader = __ffs(ball) - 1;
+          int base = 0;
+          if (lane == leader) base = atomicAdd(&s_ncand, __popc(ball));
+          base = __shfl_sync(kFull, base, leader);
+          const int at = base + __popc(ball & ((1u << lane) - 1u));
+          if (cand && at < NC) {
+            s_ccode[at] = code;
+            s_cpb[at] = pb;
+          }
         }
       }
     }
     __syncthreads();
-    // max over the prune buckets <= j - 2 (an arc from there that reaches
-    // further than arc i contains it; see chain_step_kernel)
-    if (warp == 0) {
-      const float b0 = __uint_as_float(s_pmax[2 * lane]);
-      const float b1 = __uint_as_float(s_pmax[2 * lane + 1]);
-      float incl = fmaxf(b0, b1);
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const float y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl = fmaxf(y, incl);
-      }
-      const float incl1 = __shfl_up_sync(kFull, incl, 1);
-      const float incl2 = __shfl_up_sync(kFull, incl, 2);
-      const float b0_prev = __shfl_up_sync(kFull, b0, 1);
-      s_gearly[2 * lane] = lane == 0 ? -1.f : (lane == 1 ? b0_prev : fmaxf(incl2, b0_prev));
-      s_gearly[2 * lane + 1] = lane == 0 ? -1.f : incl1;
-    }
+    // full maxima: prefix max of the later rows' maxima, joined with the first batch's
+    if (warp == 0) prefix_max(s_pbf, lane);
+    __syncthreads();
+    for (int k = tid; k < kWBP; k += kWT) s_pbf[k] = max(s_pbf[k], s_pbk[k]);
     __syncthreads();
 
     // ---- 2. exact roots of the rows not dominated, merged per bucket -----------
     int tangent = 0;
     const T bucket_w = two_pi / (T)NB;
     const T to_slot = (T)NB / two_pi;
-    for (int i0 = 0; i0 < m; i0 += kWTrip) {
-      T pv[kWU], qv[kWU], bv[kWU];
-#pragma unroll
-      for (int k = 0; k < kWU; ++k) {
-        const int i = i0 + tid + k * kWT;
-        pv[k] = i < m ? Prow[i] : T(0);
-        qv[k] = i < m ? Qrow[i] : T(0);
-        bv[k] = i < m ? v.b[i] : T(0);
-      }
-#pragma unroll
-      for (int k = 0; k < kWU; ++k) {
-        const int i = i0 + tid + k * kWT;
-        if (i >= m) continue;
-        float a_ap = 0.f, b_ap = 0.f;
-        bool inf_row = false;
-        const double b64 = v.b64[i];
-        const int cls = classify_row<T>(pv[k], qv[k], bv[k], b64, tlo, thi, a_ap, b_ap, inf_row);
-        bool keep = cls == kRowKeep;
-        if (cls == kRowApprox) {
-          const int bk = min(kWPB - 1, (int)(a_ap * to_pbucket));
-          keep = !(b_ap + 2.f * kPruneMargin <= s_gearly[bk]);
-        }
-        if (!keep) continue;
-        T al, be;
-        bool inf_root = false;
-        const bool has = roots(pv[k], qv[k], bv[k], b64, prm.tangent_thresh, al, be, inf_root,
-                               tangent);
-        infeasible |= inf_root;
-        if (!has) continue;
-        // bucket j = [lo_j, hi_j], lo_j = j w, hi_j = (j + 1) w (2 pi for the
-        // last); the same expressions for every arc, so hi_j == lo_(j+1)
-        int j = min(max((int)(al * to_slot), 0), NB - 1);
-        auto lo_of = [&](int b) { return (T)b * bucket_w; };
-        auto hi_of = [&](int b) { return b + 1 == NB ? two_pi : (T)(b + 1) * bucket_w; };
-        if (j > 0 && al < lo_of(j)) --j;
-        else if (j + 1 < NB && al > hi_of(j)) ++j;
-        if (al >= lo_of(j) && al <= hi_of(j) && be >= hi_of(j)) {
-          atomicMin(&s_bmin[j], abs_bits<T>(al));
-          atomicMax(&s_bmax[j], abs_bits<T>(be));
+    // exact roots of one kept row (App. B, Sec. 3.2), merged into its bucket
+    auto exact_merge = [&](T p, T q, T b, double b64) {
+      T al, be;
+      bool inf_root = false;
+      const bool has = roots(p, q, b, b64, prm.tangent_thresh, al, be, inf_root, tangent);
+      infeasible |= inf_root;
+      if (!has) return;
+      // bucket j = [lo_j, hi_j], lo_j = j w, hi_j = (j + 1) w (2 pi for the
+      // last); the same expressions for every arc, so hi_j == lo_(j+1)
+      int j = min(max((int)(al * to_slot), 0), NB - 1);
+      auto lo_of = [&](int bb) { return (T)bb * bucket_w; };
+      auto hi_of = [&](int bb) { return bb + 1 == NB ? two_pi : (T)(bb + 1) * bucket_w; };
+      if (j > 0 && al < lo_of(j)) --j;
+      else if (j + 1 < NB && al > hi_of(j)) ++j;
+      if (al >= lo_of(j) && al <= hi_of(j) && be >= hi_of(j)) {
+        atomicMin(&s_bmin[j], abs_bits<T>(al));
+        atomicMax(&s_bmax[j], abs_bits<T>(be));
+      } else {
+        // shorter than its bucket: to the short list
+        const int at = atomicAdd(&s_nshort, 1);
+        if (at < NSH) {
+          s_key[pad_idx(at)] = al;
+          s_val[pad_idx(at)] = be;
         } else {
-          // shorter than its bucket: to the short list
-          const int at = atomicAdd(&s_nshort, 1);
-          if (at < NSH) {
-            s_key[pad_idx(at)] = al;
-            s_val[pad_idx(at)] = be;
-          } else {
-            gk0[at - NSH] = al;
-            gv0[at - NSH] = be;
-          }
+          gk0[at - NSH] = al;
+          gv0[at - NSH] = be;
         }
       }
+    };
+    // rows [r0, r1) streamed: classified again and tested against the full maxima
+    auto stream_rows = [&](int r0, int r1) {
+      for (int i0 = r0; i0 < r1; i0 += kWTrip) {
+        // every operand of the trip's rows is loaded up front (exact b too:
+        // the near-tangent roots take it), so that the loads overlap
+        T pv[kWU], qv[kWU], bv[kWU];
+        double b64v[kWU];
+#pragma unroll
+        for (int k = 0; k < kWU; ++k) {
+          const int i = i0 + tid + k * kWT;
+          pv[k] = i < r1 ? Prow[i] : T(0);
+          qv[k] = i < r1 ? Qrow[i] : T(0);
+          bv[k] = i < r1 ? v.b[i] : T(0);
+          if constexpr (sizeof(T) == 8) b64v[k] = bv[k];  // double chains: b is exact b
+          else b64v[k] = i < r1 ? v.b64[i] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < kWU; ++k) {
+          const int i = i0 + tid + k * kWT;
+          if (i >= r1) continue;
+          float pa = 0.f, pb = 0.f;
+          const int cls = classify(pv[k], qv[k], bv[k], i, pa, pb, infeasible);
+          // dominated: inside an arc of a bucket at least two earlier
+          const bool keep =
+              cls == kRowKeep ||
+              (cls == kRowApprox &&
+               !(pb + 2.f * kPhiMargin <= __uint_as_float(s_pbf[bslot(pbucket(pa))])));
+          if (keep) exact_merge(pv[k], qv[k], bv[k], b64v[k]);
+        }
+      }
+    };
+    const int n_cand = s_ncand;
+    if (n_cand <= NC) {
+      // the first batch, then the candidates (rows read where they lie)
+      stream_rows(0, m_first);
+      for (int e = tid; e < n_cand; e += kWT) {
+        const unsigned code = s_ccode[e];
+        const int i = (int)(code & kWRowMask);
+        const bool keep =
+            (code & 0x80000000u) != 0u ||
+            !(s_cpb[e] + 2.f * kPhiMargin <=
+              __uint_as_float(s_pbf[bslot((int)((code >> kWRowBits) & 0x1FFu))]));
+        if (keep) exact_merge(Prow[i], Qrow[i], v.b[i], v.b64[i]);
+      }
+    } else {
+      stream_rows(0, m);
     }
     if (tangent) atomicAdd(&s_tangent, tangent);
     if (infeasible) s_infeasible = 1;
@@ -626,7 +742,8 @@ template <typename T>
 size_t chain_wide_smem_bytes(int d) {
   using Bits = BitsOf<T>;
   return 2 * (size_t)kWPad * sizeof(T) + 2 * (size_t)wide_buckets<T>() * sizeof(Bits) +
-         (size_t)kWFlag * sizeof(int) + (size_t)((d + 1) & ~1) * sizeof(T);
+         (size_t)kWFlag * sizeof(int) + (size_t)wide_cand<T>() * sizeof(float) +
+         (size_t)((d + 1) & ~1) * sizeof(T);
 }
 
 template <typename T>

@@ -52,9 +52,15 @@ def _sym_diff(p1, p2):
     return meas(a) + meas(b) - 2.0 * inter
 
 
-def _run(A, b, X, NU, U, precision, max_pieces, **cfg):
+def _run(A, b, X, NU, U, precision, max_pieces, warp_first=False, **cfg):
     s = ess.Sampler(A, b, precision=precision, **cfg)
     try:
+        if warp_first:
+            ess.ess_set_chain_kernel(s.state, ess.ESS_CHAIN_WARP)
+            assert ess.ess_get_chain_kernel(s.state) == (
+                ess.ESS_CHAIN_CTA if cfg.get("sort_threads") else ess.ESS_CHAIN_WARP)
+        else:
+            assert ess.ess_get_chain_kernel(s.state) == ess.ESS_CHAIN_CTA
         Xn, th, pcs, npc, rej = s.step_with_draws(dev(X), dev(NU), dev(U), max_pieces=max_pieces)
         out = host(Xn), host(th), host(pcs), host(npc), host(rej), s.stats()
         m_max, _ = ess.ess_limits(s.state)
@@ -64,8 +70,9 @@ def _run(A, b, X, NU, U, precision, max_pieces, **cfg):
     return out
 
 
-def check_fp64(A, b, X, NU, U, max_pieces, **cfg):
-    Xn, th, pcs, npc, rej, st = _run(A, b, X, NU, U, ess.ESS_PREC_FP64, max_pieces, **cfg)
+def check_fp64(A, b, X, NU, U, max_pieces, warp_first=False, **cfg):
+    Xn, th, pcs, npc, rej, st = _run(A, b, X, NU, U, ess.ESS_PREC_FP64, max_pieces, warp_first,
+                                     **cfg)
     refs = oracle_steps(A, b, X, NU, U)
     for c, r in enumerate(refs):
         want = positive_pieces(r.pieces)
@@ -80,12 +87,13 @@ def check_fp64(A, b, X, NU, U, max_pieces, **cfg):
     return st
 
 
-def check_mixed(A, b, X, NU, U, max_pieces, max_exempt_frac=0.05, **cfg):
+def check_mixed(A, b, X, NU, U, max_pieces, max_exempt_frac=0.05, warp_first=False, **cfg):
     X, NU = f32(X), f32(NU)
     refs = oracle_steps(A, b, X, NU, U)
     amp, arith = mixed_endpoint_bounds(A, b, X, NU)
     exempt = mixed_exempt(refs, amp, arith, 0.5 * ANG32)
-    Xn, th, pcs, npc, rej, st = _run(A, b, X, NU, U, ess.ESS_PREC_MIXED, max_pieces, **cfg)
+    Xn, th, pcs, npc, rej, st = _run(A, b, X, NU, U, ess.ESS_PREC_MIXED, max_pieces, warp_first,
+                                     **cfg)
     assert np.max(Xn @ A.T - b) <= 0.0
     for c, r in enumerate(refs):
         if exempt[c]:
@@ -137,22 +145,29 @@ def _circle(rng, m, h=2e-4, grid=False):
     return A[keep], b[keep]
 
 
-@pytest.mark.parametrize("sort_threads", [0, 256])
-def test_wide_fp64_random_polytope(sort_threads):
+# (sort_threads, warp_first): the wide-row kernel for every chain (the
+# default), the warp kernel first with the wide-row kernel for the chains it
+# leaves, and sort_threads > 0
+PATHS = [(0, False), (0, True), (256, False)]
+
+
+@pytest.mark.parametrize("sort_threads,warp_first", PATHS)
+def test_wide_fp64_random_polytope(sort_threads, warp_first):
     rng = np.random.default_rng(1)
     d, m, n = 24, 17001, 40
     A, b, X = feasible_instance(rng, d, m, n, scale=1.0 / math.sqrt(d), slack=(0.05, 0.6))
     NU = rng.standard_normal((n, d))
     U = rng.uniform(size=n)
-    check_fp64(A, b, X, NU, U, max_pieces=256, sort_threads=sort_threads)
+    check_fp64(A, b, X, NU, U, max_pieces=256, sort_threads=sort_threads, warp_first=warp_first)
 
 
-@pytest.mark.parametrize("sort_threads", [0, 256])
-def test_wide_fp64_cones_every_arc_survives(sort_threads):
+@pytest.mark.parametrize("sort_threads,warp_first", PATHS)
+def test_wide_fp64_cones_every_arc_survives(sort_threads, warp_first):
     rng = np.random.default_rng(2)
     A, b, X, NU = _cones(rng, 16, 12000, 12)
     U = rng.uniform(size=X.shape[0])
-    st = check_fp64(A, b, X, NU, U, max_pieces=64, sort_threads=sort_threads)
+    st = check_fp64(A, b, X, NU, U, max_pieces=64, sort_threads=sort_threads,
+                    warp_first=warp_first)
     # every arc reached the interval merge (no arc contains another)
     assert st["sort_keys"] >= X.shape[0]
 
@@ -192,15 +207,16 @@ def test_wide_fp64_short_and_long_arcs_smem():
     check_fp64(A, b, X, NUt, U, max_pieces=512)
 
 
-@pytest.mark.parametrize("sort_threads", [0, 256])
-def test_wide_mixed_cones(sort_threads):
+@pytest.mark.parametrize("sort_threads,warp_first", PATHS)
+def test_wide_mixed_cones(sort_threads, warp_first):
     rng = np.random.default_rng(5)
     A, b, X, NU = _cones(rng, 16, 10000, 16, grid=True)
     U = rng.uniform(size=X.shape[0])
-    check_mixed(A, b, X, NU, U, max_pieces=64, sort_threads=sort_threads)
+    check_mixed(A, b, X, NU, U, max_pieces=64, sort_threads=sort_threads, warp_first=warp_first)
 
 
-def test_wide_mixed_random_grid():
+@pytest.mark.parametrize("warp_first", [False, True])
+def test_wide_mixed_random_grid(warp_first):
     rng = np.random.default_rng(6)
     d, m, n = 32, 20011, 64
     B = grid_bits(d)
@@ -209,7 +225,7 @@ def test_wide_mixed_random_grid():
     NU = to_grid(rng.standard_normal((n, d)), B)
     b = (X @ A.T).max(axis=0) + rng.uniform(0.05, 0.6, size=m)
     U = rng.uniform(size=n)
-    check_mixed(A, b, X, NU, U, max_pieces=256)
+    check_mixed(A, b, X, NU, U, max_pieces=256, warp_first=warp_first)
 
 
 def test_wide_mixed_short_arcs_global_sort():

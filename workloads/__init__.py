@@ -104,6 +104,24 @@ def probit(seed=0, n=2000, n_chains=4096, n_iter=500, lengthscale=0.2, jitter=1e
                 n_iter=n_iter, name=f"probit_n{n}")
 
 
+def probit_features(seed=0, d=256, m=16384, n_chains=2048, n_iter=200) -> Instance:
+    """Probit-style orthant with m observations of d features: y_i phi_i . x
+    >= 0 for all i, i.e. A = -diag(y) Phi, b = 0, Phi iid N(0, 1) / sqrt(d),
+    y_i = sign(phi_i . x0) for a start x0 ~ N(0, I).  Every arc then has
+    half-width pi / 2 (b = 0) and none contains another, so no row drops out
+    of the domination prune: the many-arc case at m well beyond d."""
+    rng = np.random.default_rng(seed)
+    Phi = rng.standard_normal((m, d)) / np.sqrt(d)
+    x0 = rng.standard_normal(d)
+    y = np.sign(Phi @ x0)
+    y[y == 0] = 1.0
+    A = -y[:, None] * Phi
+    keep = A @ x0 < 0.0
+    A = np.ascontiguousarray(A[keep])
+    return Instance(f"probit_features_d{d}_m{m}", A, np.zeros(A.shape[0]),
+                    np.tile(x0, (n_chains, 1)), n_iter)
+
+
 def batched(seed=0, n_problems=512, n_iter=1000, d_range=(8, 256), c_range=(8, 64)):
     """Uneven batch: d ~ U{8..256}, m ~ U{d..4d}, chains ~ U{8..64} per polytope."""
     rng = np.random.default_rng(seed)
