@@ -289,3 +289,88 @@ def cholesky(S):
     if info != 0:
         raise ValueError(f"not positive definite: pivot of row {info - 1}")
     return L
+
+
+# ---------------------------------------------------------------------------
+# Normal probability of the domain, Z = P(A x <= b) for x ~ N(0, I) (the
+# normaliser of the target of Sec. 2), by the Holmes-Diaconis-Ross (HDR)
+# splitting estimator driven by the sampler -- the use the paper cites in its
+# introduction and related work (Gessner et al. 2020).  The paper gives no
+# algorithm for it; the steps below restate the published method:
+#   nested domains D_t = {x : A x <= b + gamma_t}, gamma_1 > ... > gamma_T = 0;
+#   Z = P(D_1) prod_t P(D_t | D_(t-1)), each factor estimated by the fraction
+#   of n samples of the truncated normal on D_(t-1) that lie in D_t, the
+#   samples of level t drawn by elliptical slice sampling on D_(t-1) started
+#   from the samples of level t - 1 that lie in D_(t-1) ("splitting").
+# The shifts come from a first stage (subset simulation): gamma_t sits
+# between the k-th and (k+1)-th smallest level values, k = ceil(rho n), so
+# that a fraction rho of the samples falls in each next domain; the second
+# stage (HDR proper) repeats the levels with fresh draws at those fixed shifts.
+# Random numbers: the start samples of a stage are Philox normals of (seed,
+# chain j, t = 0, problem 1); level t's chains take the steps (t - 1) k_b ..
+# t k_b - 1 of run() with problem 0, k_b = n_between.  Stage 1 uses seed,
+# stage 2 seed + 1.
+# ---------------------------------------------------------------------------
+
+def hdr_level(A, b, X):
+    """g(x) = max_i (a_i . x - b_i) per row of X: x lies in {A x <= b + gamma}
+    exactly when g(x) <= gamma."""
+    return np.max(np.asarray(X) @ _f64(A).T - _f64(b)[None, :], axis=1)
+
+
+def hdr_start(seed, n, d):
+    """The n start samples of a stage: independent N(0, I_d) draws."""
+    return np.stack([draw_nu(seed, j, 0, d, problem=1) for j in range(n)])
+
+
+def hdr_stage(A, b, n_samples, rho, n_between, seed, shifts=None, max_levels=64):
+    """One stage of the estimator; returns (shifts, counts) per level.
+
+    shifts None: subset simulation -- level t's shift is the midpoint of the
+    k-th and (k + 1)-th smallest g over the level's samples (k = ceil(rho n)),
+    or 0 once the k-th smallest is <= 0 (the last level).  Otherwise the given
+    shifts (the last must be 0) are used in turn; a level with no sample
+    inside ends the stage (Z estimate 0)."""
+    A = _f64(A)
+    b = _f64(b)
+    m, d = A.shape
+    n = int(n_samples)
+    k = int(np.ceil(rho * n))
+    if not (1 <= k <= n - 1):
+        raise ValueError("need 1 <= ceil(rho n) <= n - 1")
+    X = hdr_start(seed, n, d)
+    out_shifts, counts = [], []
+    while True:
+        level = len(out_shifts)
+        g = hdr_level(A, b, X)
+        if shifts is None:
+            gs = np.sort(g)
+            gamma = 0.0 if gs[k - 1] <= 0.0 else gs[k - 1] + (gs[k] - gs[k - 1]) / 2.0
+        else:
+            gamma = float(shifts[level])
+        inside = g <= gamma
+        cnt = int(inside.sum())
+        out_shifts.append(gamma)
+        counts.append(cnt)
+        if gamma == 0.0 or cnt == 0:
+            break
+        if len(out_shifts) >= max_levels:
+            raise RuntimeError("no level reached the domain within max_levels")
+        seeds = X[inside]
+        X0 = seeds[np.arange(n) % cnt]
+        X = run(A, b + gamma, X0, n_between, seed, t0=level * n_between)[0]
+    return np.array(out_shifts), np.array(counts)
+
+
+def hdr(A, b, n_samples, rho=0.5, n_between=8, seed=0, max_levels=64):
+    """Z = P(A x <= b), x ~ N(0, I): subset simulation for the shifts, then
+    HDR at those shifts.  Returns a dict with log_z (HDR), the shifts and
+    per-level counts of both stages, and log_z_ss (the subset-simulation
+    estimate of stage 1)."""
+    s1, c1 = hdr_stage(A, b, n_samples, rho, n_between, seed, None, max_levels)
+    s2, c2 = hdr_stage(A, b, n_samples, rho, n_between, seed + 1, s1, max_levels)
+    n = float(n_samples)
+    with np.errstate(divide="ignore"):
+        log_z = float(np.sum(np.log(c2 / n))) if len(c2) == len(s1) else -np.inf
+        log_z_ss = float(np.sum(np.log(c1 / n)))
+    return dict(log_z=log_z, shifts=s1, counts=c2, counts_ss=c1, log_z_ss=log_z_ss)
