@@ -588,7 +588,43 @@ def time_configs(ess, torch, workloads, peaks, seed, errors=True):
     out["batched_512_problems"] = entry
     out.update(time_paper_hd(ess, torch, workloads, peaks, seed))
     out.update(time_wide(ess, torch, workloads, peaks, seed, errors))
+    out.update(time_hdr(ess, torch, workloads, seed))
     return out
+
+
+def time_hdr(ess, torch, workloads, seed):
+    """Normal probability of a rotated box (d = 200, m = 400, exact log Z =
+    200 log(Phi(1.5) - Phi(-1))) by ess_hdr: 8192 samples per level, rho =
+    1/2, 8 chain steps between levels, both stages; the whole call timed by
+    CUDA events, its chain steps counted for a throughput in the metric's unit."""
+    inst = workloads.rotated_box()
+    want = inst.meta["log_z"]
+    n, rho, kb = 8192, 0.5, 8
+    out = {}
+    for form, prec in (("mixed", ess.ESS_PREC_MIXED), ("fp64", ess.ESS_PREC_FP64)):
+        s = ess.Sampler(inst.A, inst.b, precision=prec)
+        try:
+            ess.ess_hdr(s.state, 1024, rho, 2, seed + 7)  # warm-up (allocations, kernels)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = ess.ess_hdr(s.state, n, rho, kb, seed)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+        finally:
+            s.close()
+        T = len(r["shifts"])
+        # chain steps: stage 1 runs T - 1 level transitions, stage 2 as many
+        steps = 2 * (T - 1) * kb
+        p = r["counts"] / n
+        se = float(np.sqrt(np.sum((1 - p) / (n * p))))
+        out[form] = {"ms_per_estimate": ms, "levels": T, "log_z": r["log_z"],
+                     "log_z_ss": r["log_z_ss"], "log_z_exact": want,
+                     "error": r["log_z"] - want, "naive_se": se,
+                     "chain_iter_per_s": n * steps / (ms / 1e3), "unit": UNIT}
+    return {"hdr_rotated_box_d200_m400": out}
 
 
 def time_wide(ess, torch, workloads, peaks, seed, errors=True):

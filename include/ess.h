@@ -163,6 +163,47 @@ ess_status ess_create(const double *A, const double *b, int d, int m,
 void ess_destroy(ess_state *state);
 
 /*
+ * Normal probability Z = P(A x <= b) of the state's polytope for x ~ N(0, I_d)
+ * (the normaliser of the truncated normal of Sec. 2), by the
+ * Holmes-Diaconis-Ross splitting estimator driven by the chain steps (the use
+ * of the sampler the paper cites; the paper gives no algorithm, the steps
+ * follow the published method).  Nested domains D_t = {x : A x <= b +
+ * gamma_t}, gamma_1 > ... > gamma_T = 0, and Z = prod_t P(D_t | D_(t-1)),
+ * each factor estimated by the fraction of n_samples samples of the
+ * truncated normal on D_(t-1) lying in D_t; level t's samples come from
+ * n_between chain steps on D_(t-1) started from level t - 1's samples inside
+ * it (sample j restarts from the (j mod count)-th of them).
+ *   Stage 1 (subset simulation) sets the shifts: gamma_t is the midpoint of
+ *   the k-th and (k + 1)-th smallest level value g(x) = max_i (a_i.x - b_i)
+ *   (k = ceil(rho n_samples)), or 0 once the k-th is <= 0 (the last level).
+ *   Stage 2 (HDR) repeats the levels at those shifts with fresh draws.
+ * Random numbers: a stage's start samples are the normals of (seed_s, chain
+ * j, t = 0, problem 1) of ess_draw_normals' generator; the chains of the step
+ * from level t (0-based) take the steps t n_between .. (t + 1) n_between - 1
+ * of ess_run's map; seed_s = seed (stage 1), seed + 1 (stage 2).  g is taken
+ * in FP64 from FP64 products A x (the exact split of the refresh in the mixed
+ * form).
+ *   n_samples   samples per level, >= 2, with 1 <= ceil(rho n_samples) <= n_samples - 1
+ *   rho         target fraction of samples inside each next domain, 0 < rho < 1
+ *   n_between   chain steps between levels, >= 1
+ *   max_levels  capacity of shifts / counts / counts_ss
+ *   shifts      host, out: gamma_1 .. gamma_T
+ *   counts      host, out (or NULL): stage 2's samples inside each level
+ *   counts_ss   host, out (or NULL): stage 1's counts
+ *   n_levels    host, out: T
+ *   log_z       host, out: log of the HDR estimate, sum_t log(counts_t / n_samples)
+ *               (-inf if a level held no sample)
+ *   log_z_ss    host, out (or NULL): log of stage 1's estimate
+ * The state's loaded chains are dropped (load new ones with ess_chains_init);
+ * b is restored on return.  Errors: ESS_ERR_ARG; ESS_ERR_UNSUPPORTED when no
+ * level reaches the domain within max_levels (the domain may be empty);
+ * ESS_ERR_NUMERIC from the chain steps; ESS_ERR_OOM / ESS_ERR_CUDA.
+ */
+ess_status ess_hdr(ess_state *state, int n_samples, double rho, int n_between, uint64_t seed,
+                   int max_levels, double *shifts, int *counts, int *counts_ss, int *n_levels,
+                   double *log_z, double *log_z_ss, void *cuda_stream);
+
+/*
  * Largest supported m and d for the state's precision and row count: m up to
  * 2^22 rows; d bounded by the shared memory of the chain-step kernel that
  * takes the state's m (m <= 8192: the CTA-per-chain kernel; larger m: the

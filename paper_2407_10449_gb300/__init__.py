@@ -45,7 +45,7 @@ EXPORTED = ("ess_default_config", "ess_create", "ess_destroy", "ess_limits", "es
             "ess_draw_normals",
             "ess_set_timing", "ess_get_timing", "ess_reset_timing",
             "ess_get_stats", "ess_reset_stats", "ess_whiten", "ess_unwhiten", "ess_step_noalloc",
-            "ess_cholesky", "ess_selftest_wait",
+            "ess_cholesky", "ess_selftest_wait", "ess_hdr",
             "ess_set_graphs", "ess_graph_launches", "ess_get_tuning",
             "ess_set_chain_kernel", "ess_get_chain_kernel",
             "ess_whitener_create", "ess_whitener_destroy", "ess_whitener_apply",
@@ -123,6 +123,9 @@ def load(build_if_missing: bool = True):
             "ess_run_few": ([_vp, _vp, c_int, c_int, c_int, c_u64, _vp, c_int, _vp], c_int),
             "ess_cholesky": ([_vp, c_int, c_int, ctypes.POINTER(c_int), _vp], c_int),
             "ess_selftest_wait": ([_vp], c_int),
+            "ess_hdr": ([_vp, c_int, ctypes.c_double, c_int, c_u64, c_int, _vp, _vp, _vp,
+                         ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_double),
+                         ctypes.POINTER(ctypes.c_double), _vp], c_int),
             "ess_step_with_draws": ([_vp, _vp, _vp, _vp, c_int, _vp, _vp, _vp, c_int, _vp, _vp,
                                      _vp], c_int),
             "ess_products": ([_vp, _vp, _vp, c_int, _vp, _vp, _vp], c_int),
@@ -372,6 +375,24 @@ def ess_selftest_wait(state):
     """Bounded-wait self-test (see include/ess.h): raises EssError with
     ESS_ERR_TIMEOUT when the waits gave up as they should."""
     _check(load().ess_selftest_wait(state))
+
+
+def ess_hdr(state, n_samples, rho=0.5, n_between=8, seed=0, max_levels=256, stream=None):
+    """Normal probability P(A x <= b), x ~ N(0, I), of the state's polytope by
+    the HDR splitting estimator (see include/ess.h).  Returns a dict: log_z
+    (HDR), log_z_ss (subset simulation), shifts, counts, counts_ss."""
+    shifts = np.zeros(max_levels)
+    counts = np.zeros(max_levels, dtype=np.int32)
+    counts_ss = np.zeros(max_levels, dtype=np.int32)
+    nl = ctypes.c_int()
+    lz, lzs = ctypes.c_double(), ctypes.c_double()
+    _check(load().ess_hdr(state, int(n_samples), float(rho), int(n_between), int(seed),
+                          int(max_levels), shifts.ctypes.data, counts.ctypes.data,
+                          counts_ss.ctypes.data, ctypes.byref(nl), ctypes.byref(lz),
+                          ctypes.byref(lzs), _stream_ptr(stream)))
+    T = nl.value
+    return dict(log_z=lz.value, log_z_ss=lzs.value, shifts=shifts[:T].copy(),
+                counts=counts[:T].copy(), counts_ss=counts_ss[:T].copy())
 
 
 def ess_cholesky(A, stream=None):

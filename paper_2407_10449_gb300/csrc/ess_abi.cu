@@ -1585,6 +1585,178 @@ ess_status ess_unwhiten(const double* L, const double* mu, int d, int n, const d
   return ESS_OK;
 }
 
+// ---- normal probability of the domain (HDR splitting estimator) -----------
+namespace {
+
+// Device scratch of one ess_hdr call (freed by the destructor).
+struct HdrScratch {
+  double* X64 = nullptr;   // n x d start draws
+  void* Xtmp = nullptr;    // n x d states (T) for the gather
+  double* g = nullptr;     // n level values
+  int* list = nullptr;     // n sample indices
+  double* gamma = nullptr; // 1
+  int* count = nullptr;    // 1
+  double* b0 = nullptr;    // m: saved b (the unshifted bounds)
+  float* b32_0 = nullptr;  // m: saved float b (mixed form)
+  void* slack0 = nullptr;  // m: saved recheck thresholds
+  double* P64 = nullptr;   // n x m FP64 products when the refresh has none to share
+  ~HdrScratch() {
+    for (void* p : {(void*)X64, Xtmp, (void*)g, (void*)list, (void*)gamma, (void*)count,
+                    (void*)b0, (void*)b32_0, slack0, (void*)P64})
+      if (p) cudaFree(p);
+  }
+};
+
+// A x of the loaded states in FP64 for the level values; they also refresh
+// the chains' p.  Mixed form with the split refresh: its exact-split FP64
+// output; mixed form with the FP64 refresh: a separate FP64 product; FP64
+// forms: the refreshed p itself.
+ess_status hdr_products(ess_state* s, int n, HdrScratch& w, cudaStream_t st, const double** P) {
+  if (mixed(s) && s->cfg.refresh_mode == ESS_REFRESH_SPLIT) {
+    // one exact-split product, rounded to float for p and to double here
+    ESS_CUDA(ess::tc_refresh(s->tc_plan, s->Xw, s->d, n, s->x_slices, (size_t)n * s->ld16,
+                             s->row_scale, static_cast<float*>(s->P), s->P64, s->m, nullptr,
+                             s->dstatus, st));
+    *P = s->P64;
+    return ESS_OK;
+  }
+  ess_status rc = refresh_p(s, n, chain_states(s), false, false, st);
+  if (rc != ESS_OK) return rc;
+  if (!mixed(s)) {
+    *P = static_cast<const double*>(s->P);
+  } else {
+    ESS_CUDA((ess::launch_gemm_nt_f64<float, double>(s->Xw, s->d, s->A64, s->d, w.P64, s->m, n,
+                                                      s->m, s->d, nullptr, nullptr, st)));
+    *P = w.P64;
+  }
+  return ESS_OK;
+}
+
+}  // namespace
+
+ess_status ess_hdr(ess_state* s, int n_samples, double rho, int n_between, uint64_t seed,
+                   int max_levels, double* shifts, int* counts, int* counts_ss, int* n_levels,
+                   double* log_z, double* log_z_ss, void* cuda_stream) {
+  g_err.clear();
+  if (!s || !shifts || !n_levels || !log_z) return fail(ESS_ERR_ARG, "NULL argument");
+  const int n = n_samples, d = s->d, m = s->m;
+  if (n < 2 || !(rho > 0.0 && rho < 1.0) || n_between < 1 || max_levels < 1)
+    return fail(ESS_ERR_ARG, "need n_samples >= 2, 0 < rho < 1, n_between >= 1, max_levels >= 1");
+  const double kd = std::ceil(rho * (double)n);
+  if (!(kd >= 1.0 && kd <= (double)(n - 1)))
+    return fail(ESS_ERR_ARG, "need 1 <= ceil(rho n_samples) <= n_samples - 1");
+  const int k = (int)kd;
+  if ((long long)max_levels * n_between > 0x7fffffffLL)
+    return fail(ESS_ERR_ARG, "step index overflow (max_levels * n_between)");
+  DeviceGuard guard(s->device);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  s->n_loaded = 0;
+  ess_status rc = ensure_capacity(s, n);
+  if (rc != ESS_OK) return rc;
+  const size_t esz = elem(s);
+  HdrScratch w;
+  ESS_CUDA(dev_alloc(&w.X64, (size_t)n * d));
+  ESS_CUDA(cudaMalloc(&w.Xtmp, (size_t)n * d * esz));
+  ESS_CUDA(dev_alloc(&w.g, (size_t)n));
+  ESS_CUDA(dev_alloc(&w.list, (size_t)n));
+  ESS_CUDA(dev_alloc(&w.gamma, 1));
+  ESS_CUDA(dev_alloc(&w.count, 1));
+  ESS_CUDA(dev_alloc(&w.b0, (size_t)m));
+  ESS_CUDA(cudaMalloc(&w.slack0, (size_t)m * esz));
+  ESS_CUDA(cudaMemcpyAsync(w.b0, s->b64, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+  ESS_CUDA(cudaMemcpyAsync(w.slack0, s->slack, esz * m, cudaMemcpyDeviceToDevice, st));
+  if (mixed(s)) {
+    ESS_CUDA(dev_alloc(&w.b32_0, (size_t)m));
+    ESS_CUDA(cudaMemcpyAsync(w.b32_0, s->b32, sizeof(float) * m, cudaMemcpyDeviceToDevice, st));
+    if (s->cfg.refresh_mode != ESS_REFRESH_SPLIT) ESS_CUDA(dev_alloc(&w.P64, (size_t)n * m));
+  }
+  // the saved bounds come back whatever happens below
+  auto restore = [&]() {
+    cudaMemcpyAsync(s->b64, w.b0, sizeof(double) * m, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(s->slack, w.slack0, esz * m, cudaMemcpyDeviceToDevice, st);
+    if (w.b32_0) cudaMemcpyAsync(s->b32, w.b32_0, sizeof(float) * m, cudaMemcpyDeviceToDevice, st);
+    cudaStreamSynchronize(st);
+    s->n_loaded = 0;  // the states left are the last level's, not the caller's
+  };
+  ESS_CUDA(cudaMemsetAsync(s->dstatus, 0, sizeof(int), st));
+  int T = 0;
+  double lz[2] = {0.0, 0.0};
+  for (int stage = 0; stage < 2 && rc == ESS_OK; ++stage) {
+    const uint64_t seed_s = seed + (uint64_t)stage;
+    // the stage's start samples: N(0, I) draws, Philox (seed_s, j, t = 0, problem 1)
+    rc = [&]() -> ess_status {
+      ESS_CUDA(ess::launch_draw_nu_f64(w.X64, n, d, d, seed_s, 0u, 1u, 0u, s->bm_tab, st));
+      if (mixed(s)) ESS_CUDA((ess::launch_convert<double, float>(w.X64, d, s->Xw, d, n, d, st)));
+      else ESS_CUDA((ess::launch_convert<double, double>(w.X64, d, s->Xd, d, n, d, st)));
+      return ESS_OK;
+    }();
+    for (int level = 0; rc == ESS_OK; ++level) {
+      const double* P = nullptr;
+      rc = hdr_products(s, n, w, st, &P);
+      if (rc != ESS_OK) break;
+      rc = [&]() -> ess_status {
+        ESS_CUDA(ess::launch_hdr_level(P, m, w.b0, n, m, w.g, st));
+        ESS_CUDA(ess::launch_hdr_select(w.g, n, k, stage == 0 ? NAN : shifts[level], w.gamma,
+                                        w.count, w.list, st));
+        return ESS_OK;
+      }();
+      if (rc != ESS_OK) break;
+      double gamma = 0.0;
+      int cnt = 0;
+      ESS_CUDA(cudaMemcpyAsync(&gamma, w.gamma, sizeof(double), cudaMemcpyDeviceToHost, st));
+      ESS_CUDA(cudaMemcpyAsync(&cnt, w.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+      ESS_CUDA(cudaStreamSynchronize(st));
+      if (stage == 0) {
+        shifts[level] = gamma;
+        if (counts_ss) counts_ss[level] = cnt;
+        T = level + 1;
+      } else if (counts) {
+        counts[level] = cnt;
+      }
+      lz[stage] += cnt > 0 ? std::log((double)cnt / (double)n) : -INFINITY;
+      if (gamma == 0.0 || cnt == 0) break;
+      if (stage == 0 && level + 1 >= max_levels) {
+        rc = fail(ESS_ERR_UNSUPPORTED,
+                  "no level reached the domain within max_levels (the domain may be empty)");
+        break;
+      }
+      if (stage == 1 && level + 1 >= T) break;
+      // the next level: every sample restarts from a listed one, and the
+      // chains run n_between steps on the shifted domain {A x <= b + gamma}
+      rc = [&]() -> ess_status {
+        if (mixed(s)) {
+          ESS_CUDA(ess::launch_hdr_gather<float>(s->Xw, d, w.list, w.count, n, d,
+                                                 static_cast<float*>(w.Xtmp), st));
+          ESS_CUDA(cudaMemcpyAsync(s->Xw, w.Xtmp, sizeof(float) * n * d,
+                                   cudaMemcpyDeviceToDevice, st));
+        } else {
+          ESS_CUDA(ess::launch_hdr_gather<double>(s->Xd, d, w.list, w.count, n, d,
+                                                  static_cast<double*>(w.Xtmp), st));
+          ESS_CUDA(cudaMemcpyAsync(s->Xd, w.Xtmp, sizeof(double) * n * d,
+                                   cudaMemcpyDeviceToDevice, st));
+        }
+        ESS_CUDA(ess::launch_hdr_shift(w.b0, s->anorm, m, gamma, s->cfg.residual_margin, s->b64,
+                                       mixed(s) ? s->b32 : nullptr, s->slack, mixed(s), st));
+        return ESS_OK;
+      }();
+      if (rc != ESS_OK) break;
+      rc = refresh_p(s, n, chain_states(s), false, false, st);
+      if (rc != ESS_OK) break;
+      s->n_loaded = n;
+      s->t_next = level * n_between;
+      s->p_fresh_t = s->t_next;
+      rc = ess_chains_step(s, n_between, seed_s, nullptr, 0, st);
+      if (rc == ESS_OK) rc = read_status(s, st);
+    }
+  }
+  restore();
+  if (rc != ESS_OK) return rc;
+  *n_levels = T;
+  *log_z = lz[1];
+  if (log_z_ss) *log_z_ss = lz[0];
+  return ESS_OK;
+}
+
 const char* ess_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"

@@ -223,6 +223,27 @@ int chain_wide_slots(int device);
 template <typename T>
 cudaError_t launch_chain_step_wide(const ChainParams<T>& p, int slots, cudaStream_t s);
 
+// ------------------------------------------------------------ HDR levels ---
+// The level steps of the normal-probability estimator (k_hdr.cu).
+// g[j] = max_i (P[j, i] - b[i]) (NaN if a product is NaN), one warp per sample.
+cudaError_t launch_hdr_level(const double* P, int ldp, const double* b, int n, int m, double* g,
+                             cudaStream_t s);
+// One CTA: gamma = shift, or (shift NaN) the midpoint of the k-th and
+// (k + 1)-th smallest g (0 once the k-th is <= 0), 1 <= k <= n - 1; *count
+// and list[0 .. count) = the samples with g <= gamma in index order.
+cudaError_t launch_hdr_select(const double* g, int n, int k, double shift, double* gamma_out,
+                              int* count_out, int* list, cudaStream_t s);
+// dst[j] = src[list[j mod *count]] (rows of d elements, stride ld); nothing if
+// *count is 0.
+template <typename T>
+cudaError_t launch_hdr_gather(const T* src, int ld, const int* list, const int* count, int n,
+                              int d, T* dst, cudaStream_t s);
+// b64 = b0 + gamma, b32 = float(b64) (if b32), slack = b64 - margin anorm
+// (float rounded down, or double).
+cudaError_t launch_hdr_shift(const double* b0, const double* anorm, int m, double gamma,
+                             double margin, double* b64, float* b32, void* slack,
+                             bool float_slack, cudaStream_t s);
+
 // ------------------------------------------------------------ few chains ---
 // FP64 chains of one polytope, 1 .. kMaxFew at a time: all steps of a run in
 // one cooperative persistent kernel (k_few.cu).  Buffers (device):

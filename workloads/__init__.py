@@ -122,6 +122,23 @@ def probit_features(seed=0, d=256, m=16384, n_chains=2048, n_iter=200) -> Instan
                     np.tile(x0, (n_chains, 1)), n_iter)
 
 
+def rotated_box(seed=0, d=200, lo=-1.0, hi=1.5, n_chains=1, n_iter=200) -> Instance:
+    """The box lo <= y_j <= hi in a random orthonormal basis Q: A = [Q; -Q],
+    b = [hi 1; -lo 1] (m = 2d).  N(0, I) is rotation invariant, so its
+    probability is (Phi(hi) - Phi(lo))^d exactly (meta["log_z"]): a normal
+    probability with a known value at any dimension."""
+    import math
+    rng = np.random.default_rng(seed)
+    Q, R = np.linalg.qr(rng.standard_normal((d, d)))
+    Q = Q * np.sign(np.diag(R))[None, :]
+    A = np.ascontiguousarray(np.vstack([Q, -Q]))
+    b = np.concatenate([np.full(d, hi), np.full(d, -lo)])
+    phi = lambda x: 0.5 * math.erfc(-x / math.sqrt(2.0))
+    inst = Instance(f"rotated_box_d{d}", A, b, np.zeros((n_chains, d)), n_iter)
+    inst.meta["log_z"] = d * math.log(phi(hi) - phi(lo))
+    return inst
+
+
 def batched(seed=0, n_problems=512, n_iter=1000, d_range=(8, 256), c_range=(8, 64)):
     """Uneven batch: d ~ U{8..256}, m ~ U{d..4d}, chains ~ U{8..64} per polytope."""
     rng = np.random.default_rng(seed)
