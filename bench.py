@@ -57,7 +57,52 @@ def parse_args():
                     help="time only the mixed form (profiling runs)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the short runs of the other configurations")
+    ap.add_argument("--case", choices=sorted(CASES), default=None,
+                    help="run one small named case and exit (the command profiles/ "
+                         "summaries capture under ncu); prints one JSON line")
     return ap.parse_args()
+
+
+def _case_chains(ess, torch, inst, C, prec, steps, seed=7):
+    s = ess.Sampler(inst.A, inst.b, precision=prec)
+    try:
+        X = torch.tensor(inst.X0[0], dtype=torch.float64, device="cuda").repeat(C, 1).contiguous()
+        ess.ess_chains_init(s.state, X, C, 0)
+        ess.ess_chains_step(s.state, steps, seed)
+        torch.cuda.synchronize()
+        st = s.stats()
+    finally:
+        s.close()
+    return {k: st[k] / max(1, st["steps"]) for k in ("residual_rechecks", "tangent_fp64",
+                                                     "sort_keys", "rejections")}
+
+
+def run_case(name):
+    """Small single cases for ncu captures (each a few hundred MB on the
+    device, a few launches of the kernel of interest)."""
+    import torch
+    import paper_2407_10449_gb300 as ess
+    import workloads
+    if name == "wide_metric":
+        # metric family at m = 16384 (> 8192: the wide-row kernel), 1216 chains
+        inst = workloads.metric(n_chains=1, m=16384)
+        out = _case_chains(ess, torch, inst, 1216, ess.ESS_PREC_MIXED, 4)
+    elif name == "wide_probit":
+        inst = workloads.probit_features(n_chains=1)
+        out = _case_chains(ess, torch, inst, 1216, ess.ESS_PREC_MIXED, 4)
+    elif name == "hdr_box":
+        inst = workloads.rotated_box()
+        s = ess.Sampler(inst.A, inst.b, precision=ess.ESS_PREC_MIXED)
+        try:
+            r = ess.ess_hdr(s.state, 2048, 0.5, 4, 3)
+        finally:
+            s.close()
+        out = {"levels": len(r["shifts"]), "log_z": r["log_z"], "exact": inst.meta["log_z"]}
+    print(json.dumps({"case": name, **out}))
+    return 0
+
+
+CASES = ("wide_metric", "wide_probit", "hdr_box")
 
 
 def load_peaks():
@@ -872,6 +917,8 @@ def run_reference(args):
 
 def main():
     args = parse_args()
+    if args.case:
+        return run_case(args.case)
     if args.impl == "reference":
         return run_reference(args)
     if args.warmup < 3:
