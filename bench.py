@@ -964,7 +964,8 @@ def main():
     dominant = max(roof, key=lambda k: roof[k]["share"])
     dom = roof[dominant]
     kernel_src = {"gemm": ("k_gemm_tc.cu",),
-                  "chain": ("k_chain_warp.cu", "chain_math.cuh", "chain_warp_ops.cuh", "k_chain.cu"),
+                  "chain": ("k_chain_warp.cu", "chain_math.cuh", "chain_warp_ops.cuh", "k_chain.cu",
+                            "chain_block_ops.cuh"),
                   "draw": ("k_draw.cu", "ess_common.cuh"), "refresh": ("k_gemm_tc.cu",)}
     src = source_hash(*kernel_src[dominant])
     traffic, inst_count = ncu_counters(f"{dominant}_mixed", src)
