@@ -59,6 +59,56 @@ constexpr int kRowBits = 22;
 constexpr unsigned kRowMask = (1u << kRowBits) - 1u;
 static_assert(kWB <= 512, "bucket field of the candidate code");
 
+// Rows of one loop trip (32 kBatch rows from i0) and the lane slots that hold
+// them.  Lane-strided form: slot k of a lane is row i0 + lane + 32 k, one
+// 32-bit load per row.  Vector form (float rows on 16-byte boundaries, whole
+// trips): a lane takes four consecutive rows per 128-bit load, slot k being
+// row i0 + 4 (lane + 32 (k / 4)) + k % 4; a warp's load still covers 512
+// consecutive bytes.
+template <bool VEC>
+__device__ __forceinline__ int slot_row(int i0, int lane, int k) {
+  return VEC ? i0 + 4 * (lane + 32 * (k >> 2)) + (k & 3) : i0 + lane + 32 * k;
+}
+
+// The slots of a whole trip of float rows, 128 bits at a time (VEC) or one row
+// per slot.
+template <bool VEC, int N>
+__device__ __forceinline__ void load_trip(const float* __restrict__ src, int i0, int lane,
+                                          float (&out)[N]) {
+  if constexpr (VEC) {
+    static_assert(N % 4 == 0, "vector trips take four rows per load");
+#pragma unroll
+    for (int g = 0; g < N / 4; ++g) {
+      const float4 t = *reinterpret_cast<const float4*>(src + i0 + 4 * (lane + 32 * g));
+      out[4 * g] = t.x;
+      out[4 * g + 1] = t.y;
+      out[4 * g + 2] = t.z;
+      out[4 * g + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) out[k] = src[i0 + lane + 32 * k];
+  }
+}
+
+template <bool VEC, int N>
+__device__ __forceinline__ void store_trip(float* __restrict__ dst, int i0, int lane,
+                                           const float (&in)[N]) {
+  if constexpr (VEC) {
+#pragma unroll
+    for (int g = 0; g < N / 4; ++g)
+      *reinterpret_cast<float4*>(dst + i0 + 4 * (lane + 32 * g)) =
+          make_float4(in[4 * g], in[4 * g + 1], in[4 * g + 2], in[4 * g + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) dst[i0 + lane + 32 * k] = in[k];
+  }
+}
+
+__device__ __forceinline__ bool aligned16(const void* p) {
+  return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
+
 template <typename T, int WARPS, bool BATCH>
 __global__ void __launch_bounds__(WARPS * 32,
                                   sizeof(T) == 4 ? ESS_WARP_MINBLOCKS : ESS_WARP_MINBLOCKS_F64)
@@ -102,7 +152,30 @@ chain_warp_kernel(ChainParams<T> prm) {
     // ---- 1a. a first batch of rows builds bucket maxima of beta ---------------
     // (with m <= kCand every row fits the candidate list: no first batch)
     const int m_sub = m > kCand ? min(m, kFirst) : 0;
-    if (m_sub > 0) {
+    // float rows on 16-byte boundaries are read 128 bits at a time
+    // (one problem's chains; packed batches of uneven m keep lane-strided rows)
+    bool vec_rows = false;
+    if constexpr (sizeof(T) == 4 && !BATCH)
+      vec_rows = aligned16(Prow) && aligned16(Qrow) && aligned16(v.b) && aligned16(v.slack) &&
+                 aligned16(v.P_out);
+    if constexpr (sizeof(T) == 4) {
+      static_assert(kFirst == 32 * kBatchF32, "the first batch is one loop trip");
+    }
+    if (sizeof(T) == 4 && !BATCH && m_sub == kFirst && vec_rows) {
+      if constexpr (sizeof(T) == 4 && !BATCH) {
+        float pv[kBatch], qv[kBatch], bv[kBatch];
+        load_trip<true>(Prow, 0, lane, pv);
+        load_trip<true>(Qrow, 0, lane, qv);
+        load_trip<true>(v.b, 0, lane, bv);
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+          float pa = 0.f, pb = 0.f;
+          bool zero = false, nf = false;
+          const int cls = classify_phi_nb(pv[k], qv[k], bv[k], tlo2, thi2, pa, pb, zero, nf);
+          if (cls == kRowApprox) atomicMax(&bsub[bslot(pbucket(pa) + 2)], __float_as_uint(pb));
+        }
+      }
+    } else if (m_sub > 0) {
       for (int i0 = 0; i0 < m_sub; i0 += 32 * kBatch) {
         T pv[kBatch], qv[kBatch], bv[kBatch];
 #pragma unroll
@@ -148,20 +221,28 @@ chain_warp_kernel(ChainParams<T> prm) {
       // One batch of 32 kBatch rows in straight-line form (class, bucket test
       // and candidate code by selects, so the rows interleave); FULL batches
       // skip the bounds checks.
-      auto batch = [&](int i0, auto full_tag) {
+      auto batch = [&](int i0, auto full_tag, auto vec_tag) {
         constexpr bool FULL = decltype(full_tag)::value;
+        constexpr bool VEC = decltype(vec_tag)::value;
+        static_assert(FULL || !VEC, "vector trips are whole trips");
         float pv[kBatch], qv[kBatch], bv[kBatch];
+        if constexpr (FULL) {
+          load_trip<VEC>(Prow, i0, lane, pv);
+          load_trip<VEC>(Qrow, i0, lane, qv);
+          load_trip<VEC>(v.b, i0, lane, bv);
+        } else {
 #pragma unroll
-        for (int k = 0; k < kBatch; ++k) {
-          const int i = i0 + lane + 32 * k;
-          pv[k] = FULL || i < m ? Prow[i] : 0.f;
-          qv[k] = FULL || i < m ? Qrow[i] : 0.f;
-          bv[k] = FULL || i < m ? v.b[i] : 0.f;
+          for (int k = 0; k < kBatch; ++k) {
+            const int i = i0 + lane + 32 * k;
+            pv[k] = i < m ? Prow[i] : 0.f;
+            qv[k] = i < m ? Qrow[i] : 0.f;
+            bv[k] = i < m ? v.b[i] : 0.f;
+          }
         }
         unsigned zmask = 0u;  // rows of the batch with r = 0 (no root)
 #pragma unroll
         for (int k = 0; k < kBatch; ++k) {
-          const int i = i0 + lane + 32 * k;
+          const int i = slot_row<VEC>(i0, lane, k);
           float pa = 0.f, pb = 0.f;
           bool zero = false;
           int cls = classify_phi_nb(pv[k], qv[k], bv[k], tlo2, thi2, pa, pb, zero, nonfinite);
@@ -187,12 +268,20 @@ chain_warp_kernel(ChainParams<T> prm) {
         // rare: r = 0 with b_i < 0 means x violates row i (App. B)
         if (zmask) {
           for (int k = 0; k < kBatch; ++k)
-            if ((zmask >> k) & 1u) infeasible |= v.b64[i0 + lane + 32 * k] < 0.0;
+            if ((zmask >> k) & 1u) infeasible |= v.b64[slot_row<VEC>(i0, lane, k)] < 0.0;
         }
       };
       int i0 = 0;
-      for (; i0 + 32 * kBatch <= m; i0 += 32 * kBatch) batch(i0, std::true_type{});
-      if (i0 < m) batch(i0, std::false_type{});
+      if constexpr (!BATCH) {
+        if (vec_rows)
+          for (; i0 + 32 * kBatch <= m; i0 += 32 * kBatch)
+            batch(i0, std::true_type{}, std::true_type{});
+      }
+      {
+        for (; i0 + 32 * kBatch <= m; i0 += 32 * kBatch)
+          batch(i0, std::true_type{}, std::false_type{});
+      }
+      if (i0 < m) batch(i0, std::false_type{}, std::false_type{});
     } else {
       for (int i0 = 0; i0 < m; i0 += 32 * kBatch) {
         T pv[kBatch], qv[kBatch], bv[kBatch];
@@ -318,35 +407,54 @@ chain_warp_kernel(ChainParams<T> prm) {
       bool violated = false;
       int rechecks = 0;
       double maxres = -INFINITY;
-      for (int i0 = 0; i0 < m; i0 += 32 * kBatch) {
+      // one loop trip of rows: p' for each, rows near their bound rechecked
+      auto move_trip = [&](int i0, auto full_tag, auto vec_tag) {
+        constexpr bool FULL = decltype(full_tag)::value;
+        constexpr bool VEC = decltype(vec_tag)::value;
+        static_assert(FULL || !VEC, "vector trips are whole trips");
         T pv[kBatch], qv[kBatch], sv[kBatch];
+        if constexpr (sizeof(T) == 4 && FULL) {
+          load_trip<VEC>(Prow, i0, lane, pv);
+          load_trip<VEC>(Qrow, i0, lane, qv);
+          load_trip<VEC>(v.slack, i0, lane, sv);  // float chains always carry the thresholds
+        } else {
 #pragma unroll
-        for (int k = 0; k < kBatch; ++k) {
-          const int i = i0 + lane + 32 * k;
-          pv[k] = i < m ? Prow[i] : T(0);
-          qv[k] = i < m ? Qrow[i] : T(0);
-          if constexpr (sizeof(T) == 4) {
-            sv[k] = i < m ? v.slack[i] : T(0);  // float chains always carry the thresholds
-          } else {
-            sv[k] = i < m ? (v.slack ? v.slack[i] : (T)(v.b64[i] - prm.margin * v.anorm[i]))
-                          : T(0);
+          for (int k = 0; k < kBatch; ++k) {
+            const int i = i0 + lane + 32 * k;
+            pv[k] = i < m ? Prow[i] : T(0);
+            qv[k] = i < m ? Qrow[i] : T(0);
+            if constexpr (sizeof(T) == 4) {
+              sv[k] = i < m ? v.slack[i] : T(0);
+            } else {
+              sv[k] = i < m ? (v.slack ? v.slack[i] : (T)(v.b64[i] - prm.margin * v.anorm[i]))
+                            : T(0);
+            }
           }
         }
         unsigned flags = 0u;
+        T pn[kBatch];
 #pragma unroll
         for (int k = 0; k < kBatch; ++k) {
-          const int i = i0 + lane + 32 * k;
-          if (i < m) {
-            const T pn = pv[k] * cs + qv[k] * sn;
-            prow_out[i] = pn;
+          const int i = slot_row<VEC>(i0, lane, k);
+          pn[k] = pv[k] * cs + qv[k] * sn;
+          if (FULL || i < m) {
             if constexpr (sizeof(T) == 8) {
               // pn > sv on the doubles' bits mapped to ordered integers (no
               // FP64 instruction); a NaN pn also marks the chain bad, which
               // rejects the move
-              if (ordered_bits(pn) > ordered_bits(sv[k])) flags |= 1u << k;
+              if (ordered_bits(pn[k]) > ordered_bits(sv[k])) flags |= 1u << k;
             } else {
-              if (!(pn <= sv[k])) flags |= 1u << k;
+              if (!(pn[k] <= sv[k])) flags |= 1u << k;
             }
+          }
+        }
+        if constexpr (sizeof(T) == 4 && FULL) {
+          store_trip<VEC>(prow_out, i0, lane, pn);
+        } else {
+#pragma unroll
+          for (int k = 0; k < kBatch; ++k) {
+            const int i = i0 + lane + 32 * k;
+            if (i < m) prow_out[i] = pn[k];
           }
         }
         // rows near their bound are rare: one vote per batch, then per slot
@@ -357,7 +465,7 @@ chain_warp_kernel(ChainParams<T> prm) {
             while (ball) {
               const int src = __ffs(ball) - 1;
               ball &= ball - 1;
-              const int row = i0 + src + 32 * k;
+              const int row = slot_row<VEC>(i0, src, k);
               const double* arow = v.A64 + (size_t)row * d;
               double acc = 0.0;
               for (int jj = lane; jj < d; jj += 32) {
@@ -372,6 +480,21 @@ chain_warp_kernel(ChainParams<T> prm) {
             }
           }
         }
+      };
+      {
+        int i0 = 0;
+        if constexpr (sizeof(T) == 4) {
+          if constexpr (!BATCH) {
+            if (vec_rows)
+              for (; i0 + 32 * kBatch <= m; i0 += 32 * kBatch)
+                move_trip(i0, std::true_type{}, std::true_type{});
+          }
+          {
+            for (; i0 + 32 * kBatch <= m; i0 += 32 * kBatch)
+              move_trip(i0, std::true_type{}, std::false_type{});
+          }
+        }
+        for (; i0 < m; i0 += 32 * kBatch) move_trip(i0, std::false_type{}, std::false_type{});
       }
       // x' is finite whenever theta, x and nu are (x_0 passes an FP64 check)
       const bool reject = __any_sync(kFull, violated || bad);
@@ -379,7 +502,23 @@ chain_warp_kernel(ChainParams<T> prm) {
       T* xout = v.X_out;
       T* srow = v.S;
       if (!reject) {
-        for (int j0 = 0; j0 < d; j0 += 32 * kBatch) {
+        int j0 = 0;
+        if constexpr (sizeof(T) == 4 && !BATCH) {
+          // whole trips of 16-byte aligned rows: 128-bit loads and stores
+          if (aligned16(xrow) && aligned16(nurow) && aligned16(xout) &&
+              (srow == nullptr || aligned16(srow))) {
+            for (; j0 + 32 * kBatch <= d; j0 += 32 * kBatch) {
+              float xv[kBatch], nv[kBatch], xn[kBatch];
+              load_trip<true>(xrow, j0, lane, xv);
+              load_trip<true>(nurow, j0, lane, nv);
+#pragma unroll
+              for (int k = 0; k < kBatch; ++k) xn[k] = xv[k] * cs + nv[k] * sn;
+              store_trip<true>(xout, j0, lane, xn);
+              if (srow) store_trip<true>(srow, j0, lane, xn);
+            }
+          }
+        }
+        for (; j0 < d; j0 += 32 * kBatch) {
           T xv[kBatch], nv[kBatch];
 #pragma unroll
           for (int k = 0; k < kBatch; ++k) {
