@@ -90,6 +90,18 @@ def run_case(name):
     elif name == "wide_probit":
         inst = workloads.probit_features(n_chains=1)
         out = _case_chains(ess, torch, inst, 1216, ess.ESS_PREC_MIXED, 4)
+    elif name == "batched":
+        # 512 uneven polytopes, mixed form: refresh periods as graphs of
+        # per-step launches and as one persistent launch each
+        insts = workloads.batched()
+        peaks = load_peaks()
+        out = {}
+        for persistent in (False, True):
+            r = time_batch(ess, torch, insts, "mixed", 96, 4, 0, peaks, persistent=persistent,
+                           per_step_graphs=not persistent)
+            out["persistent" if persistent else "graphs"] = {
+                "ms_per_step": r["ms_per_step"], "value": r["value"],
+                "graph_launches": r["graph_launches"], "stats": r["stats"]}
     elif name == "hdr_box":
         inst = workloads.rotated_box()
         s = ess.Sampler(inst.A, inst.b, precision=ess.ESS_PREC_MIXED)
@@ -102,7 +114,7 @@ def run_case(name):
     return 0
 
 
-CASES = ("wide_metric", "wide_probit", "hdr_box")
+CASES = ("wide_metric", "wide_probit", "hdr_box", "batched")
 
 
 def load_peaks():
@@ -490,14 +502,20 @@ def batch_phase_rooflines(insts, timing, precision, torch, peaks):
     return out
 
 
-def time_batch(ess, torch, insts, precision, steps, warmup, seed, peaks):
-    """Batched problems: value from a timed run (CUDA-graph replays), phases
-    from a second run with per-phase events (plain launches)."""
+def time_batch(ess, torch, insts, precision, steps, warmup, seed, peaks, persistent=False,
+               per_step_graphs=False):
+    """Batched problems: value from a timed run (refresh periods replayed as
+    CUDA graphs: in the mixed form by default one persistent cooperative launch
+    each, with `per_step_graphs` a graph of per-step launches), phases from a
+    second run with per-phase events (plain launches; skipped when `persistent`
+    or `per_step_graphs` is set)."""
     prec = ess.ESS_PREC_MIXED if precision == "mixed" else ess.ESS_PREC_FP64
     As = [i.A for i in insts]
     bs = [i.b for i in insts]
     nc = [i.n_chains for i in insts]
     s = ess.BatchSampler(As, bs, precision=prec, refresh_k=REFRESH_K)
+    if persistent or per_step_graphs:
+        ess.ess_batch_set_persistent(s.batch, not per_step_graphs)
     X = s.pack([i.X0 for i in insts])
     stream = torch.cuda.current_stream()
     warmup = aligned_warmup(warmup)
@@ -513,13 +531,15 @@ def time_batch(ess, torch, insts, precision, steps, warmup, seed, peaks):
     ms = e0.elapsed_time(e1)
     stats = s.stats()
     info = ess.ess_batch_info(s.batch)
-    ess.ess_batch_set_timing(s.batch, True)
-    ess.ess_batch_reset_timing(s.batch)
-    s.run(nc, X, steps, seed, t0=warmup + steps)
-    timing = ess.ess_batch_get_timing(s.batch)
+    phases = {}
+    if not (persistent or per_step_graphs):
+        ess.ess_batch_set_timing(s.batch, True)
+        ess.ess_batch_reset_timing(s.batch)
+        s.run(nc, X, steps, seed, t0=warmup + steps)
+        timing = ess.ess_batch_get_timing(s.batch)
+        phases = batch_phase_rooflines(insts, timing, precision, torch, peaks)
     s.close()
     n = sum(nc)
-    phases = batch_phase_rooflines(insts, timing, precision, torch, peaks)
     return {"value": n * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
             "ms_per_step": ms / steps, "chains": n, "graph_launches": info["graph_launches"],
             "window": {"t0": warmup, "steps": steps, "refreshes": refreshes_in(warmup, steps),
@@ -622,6 +642,8 @@ def time_configs(ess, torch, workloads, peaks, seed, errors=True):
     insts = workloads.batched()
     entry = {}
     for form, steps in (("mixed", 64), ("fp64", 32)):
+        # mixed: refresh periods as one persistent launch each (the default);
+        # phases from plain per-step launches
         r = time_batch(ess, torch, insts, form, steps, 4, seed, peaks)
         ph = r["phases"]
         dom = max(ph, key=lambda k: ph[k]["share"]) if ph else None
@@ -630,6 +652,11 @@ def time_configs(ess, torch, workloads, peaks, seed, errors=True):
         if errors:
             r["error_vs_oracle"] = batch_oracle_errors(ess, torch, insts, form, seed)
         entry[form] = r
+    # the same mixed run with refresh periods as graphs of per-step launches
+    r = time_batch(ess, torch, insts, "mixed", 64, 4, seed, peaks, persistent=False,
+                   per_step_graphs=True)
+    entry["mixed_per_step_graphs"] = {k: r[k] for k in ("value", "unit", "ms_per_step",
+                                                        "graph_launches", "window")}
     out["batched_512_problems"] = entry
     out.update(time_paper_hd(ess, torch, workloads, peaks, seed))
     out.update(time_wide(ess, torch, workloads, peaks, seed, errors))

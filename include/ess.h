@@ -509,9 +509,12 @@ ess_status ess_graph_launches(const ess_state *state, long long *launches);
 /* ---- Batched problems -------------------------------------------------------
  * Many independent polytopes {x : A_p x <= b_p} of uneven sizes d_p x m_p,
  * each with its own chains, advanced together: per step one grouped GEMM for
- * q = A_p nu over all problems (work items of up to 4096 row-chain pairs taken
- * from a device work queue by a persistent grid), one chain-step launch for all
- * chains, and whole refresh periods replayed from a CUDA graph.  The sampler
+ * q = A_p nu over all problems (mixed form: tcgen05 items of 128 rows of A_p
+ * x up to 64 of its chains walked by one persistent CTA per SM; FP64 form:
+ * items of up to 4096 row-chain pairs taken from a device work queue by a
+ * persistent grid), one chain-step launch for all chains, and whole refresh
+ * periods replayed from a CUDA graph (or, with ess_batch_set_persistent, run
+ * as one cooperative launch per period).  The sampler
  * of every chain is the one of ess_run (Alg. 1 with the roots of App. B and
  * the intersection of Alg. 3); the batch only changes how the work is laid
  * out.  The paper runs one polytope at a time and has no counterpart.
@@ -582,6 +585,31 @@ ess_status ess_batch_set_graphs(ess_batch *batch, int enable);
 ess_status ess_batch_set_timing(ess_batch *batch, int enable);
 ess_status ess_batch_get_timing(ess_batch *batch, double *ms, long long *launches, int n_phases);
 ess_status ess_batch_reset_timing(ess_batch *batch);
+/* Persistent launch of whole refresh periods (mixed form; enable = 1):
+ * instead of the graph of per-step launches (draw, grouped GEMM, warp step,
+ * CTA step for each step), a refresh period replays as the refresh of p and
+ * the draw of step 0, then ONE cooperative kernel with one 1024-thread CTA
+ * per SM for all refresh_k steps.  Per step its warps 0..5 run the grouped
+ * q GEMM on the tensor cores while warps 6..31 draw nu of the next step;
+ * then every warp takes chains from a device work queue (chains of the most
+ * rows first) for the warp-per-chain step, and whole CTAs take the chains
+ * left with too many arcs; the phases are joined by grid barriers whose
+ * waits are bounded by cfg->wait_limit_us (ESS_ERR_TIMEOUT on expiry).  The
+ * chains are the ones of the graph of per-step launches (the same products,
+ * roots, prune, sort and draws); the chains left with too many arcs take the
+ * same CTA step at 1024 threads (more merge buckets, another summation order
+ * of the piece lengths, FP32 subnormals flushed), which can change their
+ * theta in the last bits.  It applies to runs that
+ * replay graphs (no sample recording, no per-phase timing, refresh_k even).
+ * Errors: ESS_ERR_UNSUPPORTED for the FP64 form, or when the device cannot
+ * hold the launch (cooperative launch, one CTA of 1024 threads and ~213 KB of
+ * shared memory per SM; largest m_p up to 8192).  Default: on for the mixed
+ * form where the device holds the launch (measured at the speed of the
+ * per-step graph: 0.179 ms per step for 512 problems, 18,687 chains);
+ * enable = 0 returns to the per-step graph.
+ * Reference: Alg. 1 (the batch itself has no counterpart in the paper). */
+ess_status ess_batch_set_persistent(ess_batch *batch, int enable);
+
 /* Sizes of the current chain layout: packed state and product lengths, GEMM
  * work items, and the graph replays since the last timing reset. */
 ess_status ess_batch_info(const ess_batch *batch, long long *total_x, long long *total_p,

@@ -51,7 +51,7 @@ EXPORTED = ("ess_default_config", "ess_create", "ess_destroy", "ess_limits", "es
             "ess_whitener_create", "ess_whitener_destroy", "ess_whitener_apply",
             "ess_batch_create", "ess_batch_destroy", "ess_batch_run", "ess_batch_step_with_draws",
             "ess_batch_products", "ess_batch_get_stats", "ess_batch_reset_stats",
-            "ess_batch_set_graphs", "ess_batch_set_timing", "ess_batch_get_timing",
+            "ess_batch_set_graphs", "ess_batch_set_persistent", "ess_batch_set_timing", "ess_batch_get_timing",
             "ess_batch_reset_timing", "ess_batch_info",
             "ess_last_error")
 
@@ -157,6 +157,7 @@ def load(build_if_missing: bool = True):
             "ess_batch_get_stats": ([_vp, ctypes.POINTER(ess_stats)], c_int),
             "ess_batch_reset_stats": ([_vp], c_int),
             "ess_batch_set_graphs": ([_vp, c_int], c_int),
+            "ess_batch_set_persistent": ([_vp, c_int], c_int),
             "ess_batch_set_timing": ([_vp, c_int], c_int),
             "ess_batch_get_timing": ([_vp, _vp, _vp, c_int], c_int),
             "ess_batch_reset_timing": ([_vp], c_int),
@@ -559,6 +560,10 @@ def ess_batch_reset_stats(batch):
 
 def ess_batch_set_graphs(batch, enable=True):
     _check(load().ess_batch_set_graphs(batch, 1 if enable else 0))
+
+
+def ess_batch_set_persistent(batch, enable=True):
+    _check(load().ess_batch_set_persistent(batch, 1 if enable else 0))
 
 
 def ess_batch_set_timing(batch, enable=True):

@@ -29,7 +29,8 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
 # zero: its float operands (p, q, b, angles) are O(1) quantities, and the
 # flush drops the subnormal fix-ups around rsqrt and the reciprocals of the
 # per-row classification.
-FILE_FLAGS = {"k_chain_warp.cu": ["-ftz=true"], "k_chain_stream.cu": ["-ftz=true"]}
+FILE_FLAGS = {"k_chain_warp.cu": ["-ftz=true"], "k_chain_stream.cu": ["-ftz=true"],
+              "k_batch_persist.cu": ["-ftz=true"]}
 
 
 def nvcc() -> str:

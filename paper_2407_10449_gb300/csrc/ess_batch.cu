@@ -20,6 +20,7 @@
 #include "ess.h"
 #include "ess_kernels.cuh"
 #include "ess_gemm_tc.cuh"
+#include "ess_batch_persist.cuh"
 
 void ess_internal_set_error(const std::string& msg);  // ess_abi.cu
 
@@ -134,6 +135,14 @@ struct ess_batch {
   cudaStream_t work_stream = nullptr;  // plain launches: the steps (highest priority)
   cudaStream_t side_stream = nullptr;  // the draws one step ahead (lowest priority)
   cudaEvent_t ev_drawn = nullptr, ev_done = nullptr, ev_fork = nullptr, ev_join = nullptr;
+  // persistent launch (mixed form): a whole refresh period in one cooperative
+  // kernel with work queues (ess_batch_set_persistent)
+  bool persist = false;
+  int* porder = nullptr;      // chain order of its work queue (largest m first)
+  int* pqueue = nullptr;      // 2 ints per step: chain tickets, overflow count
+  int cap_pqueue = 0;
+  unsigned* pbar = nullptr;   // grid barrier state (2) and abort flag (1)
+  long long persist_launches = 0;
   struct GraphEntry {
     int version;
     uint64_t seed;
@@ -221,6 +230,7 @@ void free_work(ess_batch* s) {
   s->cap_h = 0;
   bfree(s->P64);
   bfree(s->ovf);
+  bfree(s->porder);
   s->cap_n = s->cap_items = 0;
   s->cap_x = s->cap_p = 0;
   s->nc.clear();
@@ -336,6 +346,7 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
     BESS_CUDA(cudaMalloc(&s->Q, std::max<long long>(1, po) * e));
     BESS_CUDA(balloc(&s->P64, std::max<long long>(1, po)));
     BESS_CUDA(balloc(&s->ovf, (size_t)n + 1));
+    BESS_CUDA(balloc(&s->porder, std::max<size_t>(1, (size_t)n)));
     if (bmixed(s)) {
       for (int k = 0; k < 4; ++k) {
         __half*& h = k < 2 ? s->H[k] : s->H_alt[k - 2];
@@ -351,8 +362,15 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
     s->cap_p = po;
     s->cap_items = (int)items.size();
   }
-  if (!desc.empty())
+  if (!desc.empty()) {
     BESS_CUDA(cudaMemcpy(s->desc, desc.data(), sizeof(ChainDesc) * desc.size(), cudaMemcpyHostToDevice));
+    // the persistent launch's chain queue: chains of the most rows first
+    std::vector<int> order(desc.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return desc[a].m > desc[b].m; });
+    BESS_CUDA(cudaMemcpy(s->porder, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice));
+  }
   if (!items.empty())
     BESS_CUDA(cudaMemcpy(s->items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
   if (!titems.empty())
@@ -617,6 +635,98 @@ ess_status bgraph_period(ess_batch* s, uint64_t seed, cudaStream_t st) {
   return ESS_OK;
 }
 
+// Replays (capturing on first use) one refresh period as the persistent
+// launch: the refresh of p with the draw of step 0 beside it on the side
+// stream, then one cooperative kernel for the period's refresh_k steps (q
+// GEMM, draws of steps 1 .. k - 1, chain steps and overflow chains, phases
+// joined by grid barriers), starting at the step index in *t_dev.
+ess_status bpersist_period(ess_batch* s, uint64_t seed, cudaStream_t st) {
+  const int k = s->cfg.refresh_k;
+  ess_batch::GraphEntry* hit = nullptr;
+  for (auto& g : s->graphs)
+    if (g.version == s->layout_version && g.seed == seed && g.p_first == s->P) hit = &g;
+  if (!hit) {
+    ess_status rs = bensure_streams(s);
+    if (rs != ESS_OK) return rs;
+    if (s->cap_pqueue < ess::batch_persist_queue_ints(k)) {
+      bfree(s->pqueue);
+      BESS_CUDA(balloc(&s->pqueue, (size_t)ess::batch_persist_queue_ints(k)));
+      s->cap_pqueue = ess::batch_persist_queue_ints(k);
+    }
+    if (!s->pbar) BESS_CUDA(balloc(&s->pbar, 3));
+    ess::BatchPersistArgs a{};
+    a.titems = s->titems;
+    a.n_titems = s->n_titems;
+    a.maps[0] = s->tmaps;
+    a.maps[1] = s->tmaps_alt;
+    a.arow_unscale = s->arow_unscale;
+    a.Q = static_cast<float*>(s->Q);
+    a.desc = s->desc;
+    a.NU[0] = static_cast<float*>(s->NU);
+    a.NU[1] = static_cast<float*>(s->NU_alt);
+    for (int h = 0; h < 2; ++h) {
+      a.H0[h] = h == 0 ? s->H[0] : s->H_alt[0];
+      a.H1[h] = h == 0 ? s->H[1] : s->H_alt[1];
+    }
+    a.prm = bparams<float>(s);
+    a.prm.seed = seed;
+    a.prm.t = 0;
+    a.prm.t_dev = s->t_dev;
+    a.P[0] = static_cast<float*>(s->P);
+    a.P[1] = static_cast<float*>(s->P2);
+    a.order = s->porder;
+    a.queue = s->pqueue;
+    a.ovf_list = s->ovf + 1;
+    a.steps = k;
+    a.bar = s->pbar;
+    a.abort_flag = reinterpret_cast<int*>(s->pbar + 2);
+    a.wait_ns = s->cfg.wait_limit_us > 0 ? 1000ull * (unsigned long long)s->cfg.wait_limit_us
+                                         : 2000000000ull;
+    void* p_first = s->P;
+    cudaStream_t cs = s->cap_stream, ss = s->side_stream;
+    BESS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    ess_status rc = ESS_OK;
+    auto cap_ok = [&](cudaError_t e, const char* what) {
+      if (rc == ESS_OK && e != cudaSuccess) rc = bcuda(e, what);
+      return rc == ESS_OK;
+    };
+    if (cap_ok(cudaEventRecord(s->ev_done, cs), "graph fork") &&
+        cap_ok(cudaStreamWaitEvent(ss, s->ev_done, 0), "graph fork")) {
+      bswap_nu(s);
+      rc = bdraw_alt<float>(s, seed, 0u, s->t_dev, ss);  // into the current buffers
+      bswap_nu(s);
+      if (rc == ESS_OK) cap_ok(cudaEventRecord(s->ev_drawn, ss), "graph draw");
+    }
+    if (rc == ESS_OK) rc = brefresh<float>(s, static_cast<const float*>(s->X), true, false, cs);
+    if (rc == ESS_OK && cap_ok(cudaStreamWaitEvent(cs, s->ev_drawn, 0), "graph join") &&
+        cap_ok(cudaMemsetAsync(s->pqueue, 0, sizeof(int) * ess::batch_persist_queue_ints(k), cs),
+               "persistent queue reset") &&
+        cap_ok(cudaMemsetAsync(s->pbar, 0, 3 * sizeof(unsigned), cs), "grid barrier reset"))
+      cap_ok(ess::launch_batch_persist(a, cs), "persistent batched launch");
+    if (rc == ESS_OK) cap_ok(ess::launch_advance_t(s->t_dev, (unsigned)k, cs), "advance step index");
+    cudaGraph_t graph = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    if (rc != ESS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess) return bcuda(ec, "graph capture");
+    cudaGraphExec_t exec = nullptr;
+    ec = cudaGraphInstantiateWithFlags(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) return bcuda(ec, "graph instantiate");
+    s->graphs.push_back({s->layout_version, seed, p_first, exec});
+    hit = &s->graphs.back();
+  }
+  BESS_CUDA(cudaGraphLaunch(hit->exec, st));
+  ++s->graph_launches;
+  ++s->persist_launches;
+  s->phase_launches[ESS_PHASE_REFRESH] += 1;
+  s->phase_launches[ESS_PHASE_DRAW] += 1;
+  s->phase_launches[ESS_PHASE_CHAIN] += 1;
+  return ESS_OK;
+}
+
 template <typename T>
 ess_status brun(ess_batch* s, double* X, int t0, int n_iter, uint64_t seed, void* samples,
                 int record_every, cudaStream_t st) {
@@ -656,7 +766,8 @@ ess_status brun(ess_batch* s, double* X, int t0, int n_iter, uint64_t seed, void
       if (graph_at(it)) {
         BESS_CUDA(ess::launch_set_t(s->t_dev, (unsigned)t, wst));
         while (n_iter - it >= k) {
-          ess_status r = bgraph_period<T>(s, seed, wst);
+          ess_status r = (sizeof(T) == 4 && s->persist) ? bpersist_period(s, seed, wst)
+                                                        : bgraph_period<T>(s, seed, wst);
           if (r != ESS_OK) return r;
           it += k;
         }
@@ -895,6 +1006,10 @@ ess_status ess_batch_create(int n_problems, const int* d, const int* m, const do
   if (e == cudaSuccess) e = cudaMemset(s->dstats, 0, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMemset(s->dstatus, 0, sizeof(int));
   if (e != cudaSuccess) return cleanup(e);
+  // mixed form: refresh periods run as one persistent launch where the device
+  // holds it (ess_batch_set_persistent switches back to per-step graphs)
+  if (bmixed(s)) s->persist = ess::batch_persist_supported(s->max_m, s->max_d);
+  cudaGetLastError();  // an unsupported probe leaves no error behind
   *out = s;
   return ESS_OK;
 }
@@ -915,6 +1030,8 @@ void ess_batch_destroy(ess_batch* s) {
   bfree(s->anorm);
   if (s->slack) cudaFree(s->slack);
   bfree(s->queue);
+  bfree(s->pqueue);
+  bfree(s->pbar);
   bfree(s->t_dev);
   bfree(s->bm_tab);
   bfree(s->dstats);
@@ -1042,6 +1159,22 @@ ess_status ess_batch_reset_stats(ess_batch* s) {
 ess_status ess_batch_set_graphs(ess_batch* s, int enable) {
   if (!s) return bfail(ESS_ERR_ARG, "NULL argument");
   s->use_graphs = enable != 0;
+  return ESS_OK;
+}
+
+ess_status ess_batch_set_persistent(ess_batch* s, int enable) {
+  if (!s) return bfail(ESS_ERR_ARG, "NULL argument");
+  if (enable) {
+    if (!bmixed(s))
+      return bfail(ESS_ERR_UNSUPPORTED, "the persistent launch runs the mixed form only");
+    BDeviceGuard g(s->device);
+    if (!ess::batch_persist_supported(s->max_m, s->max_d))
+      return bfail(ESS_ERR_UNSUPPORTED,
+                   "the device cannot hold the persistent launch (cooperative launch, one "
+                   "1024-thread CTA per SM) for these problem sizes");
+  }
+  if ((enable != 0) != s->persist) drop_graphs(s);  // captured periods hold the other form
+  s->persist = enable != 0;
   return ESS_OK;
 }
 
