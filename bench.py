@@ -990,10 +990,11 @@ def main():
     roof64s = phase_rooflines(inst, C, timing64s, "fp64_split", peaks) if timing64 else {}
     dominant = max(roof, key=lambda k: roof[k]["share"])
     dom = roof[dominant]
-    kernel_src = {"gemm": ("k_gemm_tc.cu",),
-                  "chain": ("k_chain_warp.cu", "chain_math.cuh", "chain_warp_ops.cuh", "k_chain.cu",
+    kernel_src = {"gemm": ("k_gemm_tc.cu", "tc_ptx.cuh"),
+                  "chain": ("k_chain_warp.cu", "chain_warp_step.cuh", "chain_math.cuh",
+                            "chain_warp_ops.cuh", "k_chain.cu", "chain_cta_step.cuh",
                             "chain_block_ops.cuh"),
-                  "draw": ("k_draw.cu", "ess_common.cuh"), "refresh": ("k_gemm_tc.cu",)}
+                  "draw": ("k_draw.cu", "ess_common.cuh"), "refresh": ("k_gemm_tc.cu", "tc_ptx.cuh")}
     src = source_hash(*kernel_src[dominant])
     traffic, inst_count = ncu_counters(f"{dominant}_mixed", src)
     roofline = {"bound": dom["bound"], "kernel": dominant, "achieved": dom["achieved"],
