@@ -288,6 +288,30 @@ def ncu_counters(kernel_key, src_hash):
     return None, None
 
 
+def step_roofline(roof, ms_per_step):
+    """The whole step's roofline: the sum over its phases of each phase's
+    lower bound (its algorithmic work at its peak; the chain kernel at the
+    larger of its HBM and issue bounds; the refresh amortised over refresh_k
+    steps), against the measured time per step.  The draw runs beside the q
+    GEMM on a side stream and is left out."""
+    parts = {}
+    for ph, r in roof.items():
+        if ph == "draw":
+            continue
+        scale = 1e6 if r["unit"] == "GB/s" else 1e9
+        t = r["work_per_launch"] / (r["peak"] * scale)
+        if ph == "chain" and r.get("issue"):
+            t = max(t, r["issue"]["issue_limited_ms"])
+        if ph == "refresh":
+            t /= REFRESH_K
+        parts[ph] = t
+    bound = sum(parts.values())
+    if not parts or not ms_per_step:
+        return None
+    return {"bound_ms_per_step": bound, "ms_per_step": ms_per_step, "frac": bound / ms_per_step,
+            "phase_bound_ms": parts}
+
+
 def issue_roofline(torch, inst_per_launch, ms_per_launch, sm_mhz):
     """The SM issue bound of a kernel: warp instructions per launch (ncu) over
     its live launch time, against one instruction per clock per scheduler
@@ -1046,15 +1070,18 @@ def main():
         "fp64": None if args.mixed_only else {
             "value": value64, "unit": UNIT, "steps": args.fp64_steps,
             "ms_per_step": ms64 / args.fp64_steps, "dtype": "f64", "window": lc64["window"],
-            "phases": roof64, "stats": stats64, "error_vs_oracle": errors.get("fp64")},
+            "phases": roof64, "stats": stats64, "error_vs_oracle": errors.get("fp64"),
+            "step_roofline": step_roofline(roof64, ms64 / args.fp64_steps)},
         # the FP64 form with q = A nu and p = A x from exact 56-bit splits on the
         # tensor cores (FP64-class products, ess_config.fp64_products = 1)
         "fp64_split": None if args.mixed_only else {
             "value": value64s, "unit": UNIT, "steps": args.fp64_split_steps,
             "ms_per_step": ms64s / args.fp64_split_steps, "dtype": "f64 (products: bf16 slices)",
             "window": lc64s["window"], "phases": roof64s, "stats": stats64s,
-            "error_vs_oracle": errors.get("fp64_split")},
+            "error_vs_oracle": errors.get("fp64_split"),
+            "step_roofline": step_roofline(roof64s, ms64s / args.fp64_split_steps)},
         "roofline": roofline,
+        "step_roofline": step_roofline(roof, ms / args.steps),
         "phases": roof,
         "fp64_peak": {"tflops": fp64_peak, "source": FP64_PEAK_SOURCE},
         "e2e": e2e,
