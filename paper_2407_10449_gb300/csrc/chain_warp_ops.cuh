@@ -71,6 +71,18 @@ __device__ __forceinline__ void prefix_max(unsigned* b, int lane) {
   for (int k = 0; k < kWB / 32; ++k) mine[k] = max(mine[k], before);
 }
 
+// Warp-wide min / max of a float (every lane gets the result).
+__device__ __forceinline__ float warp_min_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_incl_max(T v, int lane) {
 #pragma unroll

@@ -119,7 +119,9 @@ constexpr size_t kWarpStepSmem = ((size_t)2 * kWBP + 2 * kCand + kCap) * 4;
 // One step of chain c by the calling warp (all 32 lanes), with kWarpStepSmem
 // bytes of shared memory at wsm.  Returns the chain's sorted keys (the same
 // on every lane; 0 if the chain was left to the CTA-per-chain step).
-template <typename T, bool BATCH>
+// LONG: compile the long-arc union (used for the chains whose view has
+// long_arcs set); without it the kernel carries none of that code.
+template <typename T, bool BATCH, bool LONG = false>
 __device__ __forceinline__ int warp_chain_step(const ChainParams<T>& prm, int c,
                                                unsigned char* wsm, int lane) {
   constexpr int kBatch = sizeof(T) == 4 ? kBatchF32 : ESS_WARP_BATCH_F64;
@@ -146,6 +148,14 @@ __device__ __forceinline__ int warp_chain_step(const ChainParams<T>& prm, int c,
   const float tlo2 = tlo_s * tlo_s, thi2 = thi_s * thi_s;
   bool infeasible = false, nonfinite = false;
 
+  // Long arcs: a row with b_i <= 0 has h_i >= pi / 2, an infeasible arc of
+  // length >= pi.  Two such open arcs inside (0, 2 pi) (theta = 0 is feasible)
+  // overlap, so all of them form ONE arc (min alpha, max beta); any arc inside
+  // it can be dropped without changing I_act, as long as the rows holding the
+  // two extremes stay.  ua / ub: min pseudo-alpha and max pseudo-beta of the
+  // long arcs seen (+inf / -inf: none).
+  float ua = INFINITY, ub = -INFINITY;
+
   // ---- 1a. a first batch of rows builds bucket maxima of beta ---------------
   // (with m <= kCand every row fits the candidate list: no first batch)
   const int m_sub = m > kCand ? min(m, kFirst) : 0;
@@ -170,6 +180,10 @@ __device__ __forceinline__ int warp_chain_step(const ChainParams<T>& prm, int c,
         bool zero = false, nf = false;
         const int cls = classify_phi_nb(pv[k], qv[k], bv[k], tlo2, thi2, pa, pb, zero, nf);
         if (cls == kRowApprox) atomicMax(&bsub[bslot(pbucket(pa) + 2)], __float_as_uint(pb));
+        if (cls == kRowApprox && (LONG && v.long_arcs) && bv[k] <= 0.f) {
+          ua = fminf(ua, pa);
+          ub = fmaxf(ub, pb);
+        }
       }
     }
   } else if (m_sub > 0) {
@@ -194,16 +208,26 @@ __device__ __forceinline__ int warp_chain_step(const ChainParams<T>& prm, int c,
         else
           cls = classify_phi_d(pv[k], qv[k], bv[k], tlo2, thi2, pa, pb, nf);
         if (cls == kRowApprox) atomicMax(&bsub[bslot(pbucket(pa) + 2)], __float_as_uint(pb));
+        if (cls == kRowApprox && (LONG && v.long_arcs) && bv[k] <= T(0)) {
+          ua = fminf(ua, pa);
+          ub = fmaxf(ub, pb);
+        }
       }
     }
   }
   __syncwarp();
   if (m_sub > 0) prefix_max(bsub, lane);
+  // the first batch's long arcs: one union (ua, ub) in pseudo-angles
+  if ((LONG && v.long_arcs)) {
+    ua = warp_min_f(ua);
+    ub = warp_max_f(ub);
+  }
   __syncwarp();
 
   // ---- 1b. every row: full bucket maxima, candidates not dominated by an
   //          arc of the first batch ------------------------------------------
   int n_cand = 0;
+  float la = INFINITY, lb = -INFINITY;  // every long arc's union (this lane's rows)
   // candidate compaction of one row slot of the batch
   auto push = [&](bool cand, unsigned code, float pb) {
     const unsigned ball = __ballot_sync(kFull, cand);
@@ -218,9 +242,10 @@ __device__ __forceinline__ int warp_chain_step(const ChainParams<T>& prm, int c,
     // One batch of 32 kBatch rows in straight-line form (class, bucket test
     // and candidate code by selects, so the rows interleave); FULL batches
     // skip the bounds checks.
-    auto batch = [&](int i0, auto full_tag, auto vec_tag) {
+    auto batch = [&](int i0, auto full_tag, auto vec_tag, auto union_tag) {
       constexpr bool FULL = decltype(full_tag)::value;
       constexpr bool VEC = decltype(vec_tag)::value;
+      constexpr bool UNION = decltype(union_tag)::value;
       static_assert(FULL || !VEC, "vector trips are whole trips");
       float pv[kBatch], qv[kBatch], bv[kBatch];
       if constexpr (FULL) {
@@ -254,11 +279,20 @@ __device__ __forceinline__ int warp_chain_step(const ChainParams<T>& prm, int c,
         // arcs that start at least two buckets earlier
         const bool undominated = !(pb + 2.f * kPhiMargin <= __uint_as_float(bsub[bslot(bk)]));
         const bool approx = cls == kRowApprox;
+        bool arc = approx && undominated;
+        if constexpr (UNION) {
+          // inside the first batch's long-arc union: covered as well
+          arc = arc && !(pa >= ua + 2.f * kPhiMargin && pb <= ub - 2.f * kPhiMargin);
+          if (approx && bv[k] <= 0.f) {
+            la = fminf(la, pa);
+            lb = fmaxf(lb, pb);
+          }
+        }
         // a row dominated by the first batch adds nothing to the full
         // maxima: the first-batch arc that covers it dominates every arc
         // it would dominate
-        if (approx && undominated) atomicMax(&bfull[bslot(bk + 2)], __float_as_uint(pb));
-        push(cls == kRowKeep || (approx && undominated),
+        if (arc) atomicMax(&bfull[bslot(bk + 2)], __float_as_uint(pb));
+        push(cls == kRowKeep || arc,
              cls == kRowKeep ? (0x80000000u | (unsigned)i) : (((unsigned)bk << kRowBits) | (unsigned)i),
              pb);
       }
@@ -268,17 +302,25 @@ __device__ __forceinline__ int warp_chain_step(const ChainParams<T>& prm, int c,
           if ((zmask >> k) & 1u) infeasible |= v.b64[slot_row<VEC>(i0, lane, k)] < 0.0;
       }
     };
-    int i0 = 0;
-    if constexpr (!BATCH) {
-      if (vec_rows)
-        for (; i0 + 32 * kBatch <= m; i0 += 32 * kBatch)
-          batch(i0, std::true_type{}, std::true_type{});
-    }
-    {
+    auto rows = [&](auto union_tag) {
+      int i0 = 0;
+      if constexpr (!BATCH) {
+        if (vec_rows)
+          for (; i0 + 32 * kBatch <= m; i0 += 32 * kBatch)
+            batch(i0, std::true_type{}, std::true_type{}, union_tag);
+      }
       for (; i0 + 32 * kBatch <= m; i0 += 32 * kBatch)
-        batch(i0, std::true_type{}, std::false_type{});
+        batch(i0, std::true_type{}, std::false_type{}, union_tag);
+      if (i0 < m) batch(i0, std::false_type{}, std::false_type{}, union_tag);
+    };
+    if constexpr (LONG) {
+      if (v.long_arcs)
+        rows(std::true_type{});
+      else
+        rows(std::false_type{});
+    } else {
+      rows(std::false_type{});
     }
-    if (i0 < m) batch(i0, std::false_type{}, std::false_type{});
   } else {
     for (int i0 = 0; i0 < m; i0 += 32 * kBatch) {
       T pv[kBatch], qv[kBatch], bv[kBatch];
@@ -304,7 +346,13 @@ __device__ __forceinline__ int warp_chain_step(const ChainParams<T>& prm, int c,
             code = 0x80000000u | (unsigned)i;
           } else if (cls == kRowApprox) {
             const int bk = pbucket(pa);
-            cand = !(pb + 2.f * kPhiMargin <= __uint_as_float(bsub[bslot(bk)]));
+            const bool in_union = (LONG && v.long_arcs) && pa >= ua + 2.f * kPhiMargin &&
+                                  pb <= ub - 2.f * kPhiMargin;
+            if ((LONG && v.long_arcs) && bv[k] <= T(0)) {
+              la = fminf(la, pa);
+              lb = fmaxf(lb, pb);
+            }
+            cand = !in_union && !(pb + 2.f * kPhiMargin <= __uint_as_float(bsub[bslot(bk)]));
             if (cand) atomicMax(&bfull[bslot(bk + 2)], __float_as_uint(pb));
             code = ((unsigned)bk << kRowBits) | (unsigned)i;
           }
@@ -314,6 +362,13 @@ __device__ __forceinline__ int warp_chain_step(const ChainParams<T>& prm, int c,
     }
   }
   __syncwarp();
+  // the union of every long arc, (la, lb); its arcs holding the two extremes
+  // start in bucket bkl and end at pseudo-beta lb, and stay
+  if ((LONG && v.long_arcs)) {
+    la = warp_min_f(la);
+    lb = warp_max_f(lb);
+  }
+  const int bkl = pbucket(la);
   int n_surv = kCap + 1;  // overflow unless the candidates fit
   if (n_cand <= kCand) {
     prefix_max(bfull, lane);
@@ -331,7 +386,11 @@ __device__ __forceinline__ int warp_chain_step(const ChainParams<T>& prm, int c,
           keep = true;
         } else {
           const int bk = (int)((code >> kRowBits) & 0x1FFu);
+          // dropped if contained in an arc starting two buckets earlier, or
+          // inside the long-arc union (two buckets past its start: more
+          // than 2 kPhiMargin in pseudo-angle)
           keep = !(candb[e] + 2.f * kPhiMargin <= __uint_as_float(bfull[bslot(bk)]));
+          if constexpr (LONG) keep = keep && !(bk >= bkl + 2 && candb[e] <= lb - 2.f * kPhiMargin);
         }
       }
       const unsigned ball = __ballot_sync(kFull, keep);

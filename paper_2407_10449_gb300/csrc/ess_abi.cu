@@ -72,6 +72,9 @@ struct ess_state {
   // m beyond the CTA kernel's 8192 arcs: the wide-row kernel takes the chains
   // the warp kernel leaves (or every chain when sort_threads > 0)
   bool wide = false;
+  // some b_i <= 0: the warp step drops arcs inside the union of those rows'
+  // (long) arcs (ChainParams::long_arcs)
+  int long_arcs = 0;
   void* wide_scratch = nullptr;  // wide_slots x 4 x wide_cap elements of T
   long long wide_cap = 0;
   int wide_slots = 0;
@@ -373,6 +376,7 @@ ess::ChainParams<T> base_params(ess_state* s, int n) {
   p.trim_eps = s->cfg.trim_eps;
   p.tangent_thresh = s->cfg.tangent_thresh;
   p.margin = s->cfg.residual_margin;
+  p.long_arcs = s->long_arcs;
   p.stats = s->dstats;
   p.status = s->dstatus;
   return p;
@@ -867,6 +871,8 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
   }
   if (e == cudaSuccess) e = cudaMemset(s->dstats, 0, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMemset(s->dstatus, 0, sizeof(int));
+  for (int i = 0; i < m; ++i)
+    if (b[i] <= 0.0) s->long_arcs = 1;
   if (e == cudaSuccess && c.precision == ESS_PREC_MIXED) {
     std::vector<float> bf(m);
     for (int i = 0; i < m; ++i) bf[i] = (float)b[i];
@@ -1670,8 +1676,19 @@ ess_status ess_hdr(ess_state* s, int n_samples, double rho, int n_between, uint6
     ESS_CUDA(cudaMemcpyAsync(w.b32_0, s->b32, sizeof(float) * m, cudaMemcpyDeviceToDevice, st));
     if (s->cfg.refresh_mode != ESS_REFRESH_SPLIT) ESS_CUDA(dev_alloc(&w.P64, (size_t)n * m));
   }
+  // the level bounds b - gamma can reach 0: the warp step takes long arcs
+  // as one union while they are in place (captured periods hold the flag)
+  const int long_arcs0 = s->long_arcs;
+  if (!s->long_arcs) {
+    s->long_arcs = 1;
+    drop_graphs(s);
+  }
   // the saved bounds come back whatever happens below
   auto restore = [&]() {
+    if (s->long_arcs != long_arcs0) {
+      s->long_arcs = long_arcs0;
+      drop_graphs(s);
+    }
     cudaMemcpyAsync(s->b64, w.b0, sizeof(double) * m, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(s->slack, w.slack0, esz * m, cudaMemcpyDeviceToDevice, st);
     if (w.b32_0) cudaMemcpyAsync(s->b32, w.b32_0, sizeof(float) * m, cudaMemcpyDeviceToDevice, st);

@@ -79,6 +79,7 @@ struct ess_batch {
   std::vector<int> d, m;
   std::vector<long long> a_off;  // per problem, into A64 / A32
   std::vector<int> b_off;        // per problem, into b, anorm, slack
+  std::vector<int> long_arcs;    // per problem: some b_i <= 0
   std::vector<long long> at_off; // per problem, into AT (K-major copy, rows padded to 4)
   int max_d = 0, max_m = 0;
   int chain_threads = 0;         // CTA kernel width for max_m
@@ -265,6 +266,7 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
       cd.b_off = s->b_off[p];
       cd.dpad = dp;
       cd.h_off = ho + (long long)k * dp;
+      cd.long_arcs = s->long_arcs[p];
       desc.push_back(cd);
     }
     const int ct = ess::batch_ctile(nc[p]), rt = ess::batch_rtile(ct);
@@ -481,6 +483,9 @@ ess::ChainParams<T> bparams(ess_batch* s) {
   p.stats = s->dstats;
   p.status = s->dstatus;
   p.desc = s->desc;
+  // the warp step compiles the long-arc union in if any problem has such rows
+  // (each chain then follows its problem's ChainDesc::long_arcs)
+  p.long_arcs = std::any_of(s->long_arcs.begin(), s->long_arcs.end(), [](int v) { return v != 0; });
   return p;
 }
 
@@ -856,6 +861,9 @@ ess_status ess_batch_create(int n_problems, const int* d, const int* m, const do
     s->m.push_back(m[p]);
     s->a_off.push_back(ta);
     s->b_off.push_back(tb);
+    int long_arcs = 0;  // rows with b_i <= 0 (see ChainParams::long_arcs)
+    for (int i = 0; b && i < m[p]; ++i) long_arcs |= b[tb + i] <= 0.0 ? 1 : 0;
+    s->long_arcs.push_back(long_arcs);
     s->at_off.push_back(tat);
     tat += (long long)d[p] * ((m[p] + 3) & ~3);
     s->dpad.push_back((d[p] + 7) & ~7);

@@ -68,6 +68,7 @@ struct ChainDesc {
   int b_off;            // element offset of the problem's b, b64, anorm, slack
   int dpad;             // row stride of the fp16 nu slices (d rounded up to 8)
   long long h_off;      // element offset of the chain's row in the fp16 nu slices
+  int long_arcs;        // the problem has rows with b_i <= 0 (see ChainParams)
 };
 
 template <typename T>
@@ -117,6 +118,11 @@ struct ChainParams {
   // their merge-sort buffer, used when a chain's arcs outgrow shared memory)
   T* wide_scratch;
   long long wide_cap;
+  // the problem has rows with b_i <= 0 (infeasible arcs of at least a half
+  // circle, which together form one arc): the warp step then drops the arcs
+  // inside that union; 0 skips the test (always correct, faster without such
+  // rows).  Batch mode: per problem, ChainDesc::long_arcs.
+  int long_arcs;
 };
 
 // The rows of one chain as a kernel sees them.
@@ -136,6 +142,7 @@ struct ChainView {
   const T* slack;
   const double* A64;     // m x d
   unsigned chain, problem, t;
+  bool long_arcs;
 };
 
 template <typename T, bool BATCH>
@@ -154,6 +161,7 @@ __device__ __forceinline__ ChainView<T> chain_view(const ChainParams<T>& prm, in
     v.slack = prm.slack ? prm.slack + cd.b_off : nullptr;
     v.A64 = prm.A64 + cd.a_off;
     v.chain = cd.chain;
+    v.long_arcs = cd.long_arcs != 0;
     v.problem = cd.problem;
     v.S = prm.samples ? prm.samples + xo : nullptr;
   } else {
@@ -167,6 +175,7 @@ __device__ __forceinline__ ChainView<T> chain_view(const ChainParams<T>& prm, in
     v.slack = prm.slack;
     v.A64 = prm.A64;
     v.chain = prm.chain0 + (unsigned)c;
+    v.long_arcs = prm.long_arcs != 0;
     v.problem = prm.problem;
     v.S = prm.samples ? prm.samples + (size_t)c * prm.sample_stride : nullptr;
   }

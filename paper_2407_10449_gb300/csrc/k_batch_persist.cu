@@ -221,6 +221,7 @@ __device__ __noinline__ void persist_overflow_chain(const ChainParams<float>& p,
   cta_chain_step<float, kPT, kPItems, true>(p, c, region, bytes);
 }
 
+template <bool LONG>
 __global__ void __launch_bounds__(kPT, 1) batch_persist_kernel(BatchPersistArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);  // full[S], empty[S], accf[2], acce[2]
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(kPT, 1) batch_persist_kernel(BatchPersistArgs 
       ticket = __shfl_sync(0xffffffffu, ticket, 0);
       if (ticket >= n) break;
       const int c = a.order[ticket];
-      sort_keys += warp_chain_step<float, true>(p, c, wsm, lane);
+      sort_keys += warp_chain_step<float, true, LONG>(p, c, wsm, lane);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     ok = grid_barrier(a.bar, a.abort_flag, a.prm.status, a.wait_ns);
@@ -352,17 +353,18 @@ size_t persist_cta_bytes(int max_d) {
          nslot * sizeof(int) + 2 * std::min<size_t>(nslot, 2048) * sizeof(float);
 }
 
+template <bool LONG>
 int persist_grid(size_t smem) {
   int dev = 0, sms = 0, coop = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
     return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaFuncSetAttribute(batch_persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(batch_persist_kernel<LONG>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persist_kernel, kPT, smem) !=
-      cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persist_kernel<LONG>, kPT,
+                                                    smem) != cudaSuccess)
     return 0;
   return per_sm >= 1 ? sms : 0;
 }
@@ -372,7 +374,7 @@ int persist_grid(size_t smem) {
 bool batch_persist_supported(int max_m, int max_d) {
   if (max_m > kPT * kPItems || max_m < 1 || max_d < 1) return false;
   if (persist_cta_bytes(max_d) > persist_region_bytes()) return false;
-  return persist_grid(persist_smem_bytes()) > 0;
+  return persist_grid<false>(persist_smem_bytes()) > 0 && persist_grid<true>(persist_smem_bytes()) > 0;
 }
 
 cudaError_t launch_batch_persist(const BatchPersistArgs& a, cudaStream_t s) {
@@ -381,7 +383,7 @@ cudaError_t launch_batch_persist(const BatchPersistArgs& a, cudaStream_t s) {
       !a.prm.slack || a.P[0] == a.P[1])
     return cudaErrorInvalidValue;
   const size_t smem = persist_smem_bytes();
-  const int grid = persist_grid(smem);
+  const int grid = a.prm.long_arcs ? persist_grid<true>(smem) : persist_grid<false>(smem);
   if (grid <= 0) return cudaErrorNotSupported;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)grid);
@@ -393,7 +395,8 @@ cudaError_t launch_batch_persist(const BatchPersistArgs& a, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, batch_persist_kernel, a);
+  return a.prm.long_arcs ? cudaLaunchKernelEx(&cfg, batch_persist_kernel<true>, a)
+                         : cudaLaunchKernelEx(&cfg, batch_persist_kernel<false>, a);
 }
 
 }  // namespace ess

@@ -9,7 +9,7 @@ namespace {
 
 constexpr int kWarps = 8;  // chains per CTA
 
-template <typename T, int WARPS, bool BATCH>
+template <typename T, int WARPS, bool BATCH, bool LONG>
 __global__ void __launch_bounds__(WARPS * 32,
                                   sizeof(T) == 4 ? ESS_WARP_MINBLOCKS : ESS_WARP_MINBLOCKS_F64)
 chain_warp_kernel(ChainParams<T> prm) {
@@ -20,7 +20,8 @@ chain_warp_kernel(ChainParams<T> prm) {
   __syncthreads();
   const int c = blockIdx.x * WARPS + warp;
   if (c < prm.n_chains) {
-    const int keys = warp_chain_step<T, BATCH>(prm, c, smem_raw + kWarpStepSmem * warp, lane);
+    const int keys =
+        warp_chain_step<T, BATCH, LONG>(prm, c, smem_raw + kWarpStepSmem * warp, lane);
     if (lane == 0 && keys) atomicAdd(&s_sort_keys, (unsigned long long)keys);
   }
   __syncthreads();
@@ -41,7 +42,11 @@ cudaError_t launch_chain_step_warp(const ChainParams<T>& p, cudaStream_t s) {
   if (p.P_out == p.P_in || !p.overflow_list || !p.overflow_count) return cudaErrorInvalidValue;
   if (sizeof(T) == 4 && p.slack == nullptr) return cudaErrorInvalidValue;
   const size_t smem = chain_warp_smem_bytes<T>(p.m);
-  auto k = p.desc ? chain_warp_kernel<T, kWarps, true> : chain_warp_kernel<T, kWarps, false>;
+  // the long-arc union is compiled in only when some row has b_i <= 0
+  auto k = p.desc ? (p.long_arcs ? chain_warp_kernel<T, kWarps, true, true>
+                                 : chain_warp_kernel<T, kWarps, true, false>)
+                  : (p.long_arcs ? chain_warp_kernel<T, kWarps, false, true>
+                                 : chain_warp_kernel<T, kWarps, false, false>);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((p.n_chains + kWarps - 1) / kWarps);

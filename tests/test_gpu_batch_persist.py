@@ -8,7 +8,8 @@ It changes how the work of a step is scheduled, not what is computed: the
 chains must equal, bit for bit, those of the graph of per-step launches, which
 the batch tests hold against the oracle.  The specs mix uneven d, m and chain
 counts (a problem with no chains, d = 1, items crossing the 128-row and
-64-chain tiles) with a cone problem (b = 0): there every arc is a half circle,
+64-chain tiles) with a nearly conic problem (b = 1e-3 on rows that face away
+from the start points): every arc is a little shorter than a half circle and
 no arc contains another, so every chain keeps more arcs than a warp sorts and
 takes the overflow phase.
 """
@@ -28,14 +29,16 @@ SPECS = [(1, 2, 3), (3, 5, 4), (10, 20, 16), (17, 60, 70), (40, 130, 9), (64, 64
 
 
 def cone_instance(rng, d, m, n):
-    """{x : A x <= 0} with rows turned to face away from a point x0 inside,
-    and start points on the ray through x0 (positive multiples stay inside)."""
+    """{x : A x <= 1e-3} with rows turned to face away from a point x0
+    inside, and start points on the ray through x0 (positive multiples stay
+    inside).  b > 0 keeps every arc shorter than pi (arcs of b <= 0 form one
+    union that the warp step reduces to its two extremes)."""
     x0 = rng.standard_normal(d)
     A = rng.standard_normal((m, d)) / math.sqrt(d)
     A[A @ x0 > 0] *= -1.0
     A[np.abs(A @ x0) < 1e-3] = -x0 / np.linalg.norm(x0)  # no row through x0
     X = x0[None, :] * rng.uniform(0.5, 2.0, size=(n, 1))
-    return A, np.zeros(m), X
+    return A, np.full(m, 1e-3), X
 
 
 def make_batch(seed, with_cone=True):
@@ -71,7 +74,7 @@ def run_batch(As, bs, Xs, nc, persistent, n_iter, t0, refresh_k=4, seed=11):
 def test_persistent_periods_equal_graph_of_launches():
     """Three refresh periods of 4 steps after 2 plain steps (t0 = 2): the
     persistent launch and the per-step graph give the same bits, with the
-    cone problem's chains going through the overflow phase every step."""
+    near-conic problem's chains going through the overflow phase every step."""
     As, bs, Xs, nc = make_batch(3)
     got, st_p, info_p = run_batch(As, bs, Xs, nc, True, 14, t0=2)
     want, st_g, info_g = run_batch(As, bs, Xs, nc, False, 14, t0=2)
@@ -83,7 +86,7 @@ def test_persistent_periods_equal_graph_of_launches():
     # sort_keys counts the arcs (or merged bucket intervals) each chain's
     # sweep took: the overflow phase's 1024-thread CTA merges into 2048
     # buckets where the per-step CTA kernel (64 threads at m = 400) has 512,
-    # so only its size is checked: the cone chains keep > 128 arcs each step
+    # so only its size is checked: the near-conic chains keep > 128 arcs each step
     assert st_p["sort_keys"] > 14 * 12 * 128 and st_g["sort_keys"] > 14 * 12 * 128
 
 

@@ -201,8 +201,9 @@ def test_full_size_sampled_chains():
 @pytest.mark.parametrize("sort_threads", [0, 256])
 def test_both_step_kernels(sort_threads):
     """The warp-per-chain kernel (default) and the CTA-per-chain kernel give the
-    oracle's step on the same inputs, including chains whose arcs all survive
-    the domination prune (equal half-widths: b = 0) and go to the CTA kernel."""
+    oracle's step on the same inputs, including a probit-style orthant (equal
+    half-widths, b = 0) where no arc contains another: the warp kernel keeps
+    only the extremes of the long arcs' union, the CTA kernel merges them all."""
     rng = np.random.default_rng(21)
     d, m, n = 40, 600, 96
     A, b, X = feasible_instance(rng, d, m, n)
@@ -210,8 +211,7 @@ def test_both_step_kernels(sort_threads):
     U = rng.uniform(size=n)
     check_fp64(A, b, X, NU, U, sort_threads=sort_threads)
     # a probit-style orthant (A = -diag(y) L, b = 0): every arc has half-width
-    # pi / 2, no arc contains another, so all 200 arcs survive the prune and
-    # the chain goes to the CTA kernel
+    # pi / 2 and no arc contains another; together they form one arc
     M = rng.standard_normal((200, 200))
     L = np.linalg.cholesky(M @ M.T / 200 + np.eye(200))
     z = rng.standard_normal(200)

@@ -222,6 +222,36 @@ def test_mixed_cta_kernel_probit_orthant():
     check_mixed(A, b, X, NU, U, sort_threads=256)
 
 
+@pytest.mark.parametrize("half", [False, True])
+def test_mixed_warp_kernel_long_arc_union(half):
+    """Rows with b_i <= 0 have infeasible arcs of length >= pi; for a feasible
+    x any two overlap, so together they are one arc (min alpha, max beta) and
+    the warp kernel keeps only the rows holding its two extremes (Sec. 3.1's
+    I_act unchanged).  A probit-style orthant (b = 0: no arc contains another,
+    so the bucket prune alone keeps every arc), and the same with half of the
+    rows given b > 0 (short arcs, pruned by the union and by each other).
+    Grid inputs, every chain against the oracle; few arcs reach the sort."""
+    rng = np.random.default_rng(14)
+    k = 256
+    M = rng.standard_normal((k, k))
+    B = grid_bits(k)
+    L = to_grid(np.linalg.cholesky(M @ M.T / k + np.eye(k)), B)
+    z = to_grid(rng.standard_normal(k), B)
+    f = L @ z
+    assert np.all(f != 0.0)
+    A = -np.sign(f)[:, None] * L
+    b = np.zeros(k)
+    if half:
+        b[1::2] = to_grid(rng.uniform(0.05, 0.5, size=k // 2), B)
+    n = 64
+    X = np.tile(z, (n, 1))
+    NU = to_grid(rng.standard_normal((n, k)), B)
+    U = rng.uniform(size=n)
+    stats, _, _ = check_mixed(A, b, X, NU, U)
+    # without the union every chain would sort all 256 arcs (CTA kernel)
+    assert stats["sort_keys"] < 32 * n, stats["sort_keys"]
+
+
 def test_mixed_near_tangent_rows_fp64_branch():
     """Rows with b / r in (1 - 1e-4, 1): the mixed form takes the arccos
     argument and the angles in FP64 (tangent_fp64 counts them).  Grid rows,
