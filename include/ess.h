@@ -479,11 +479,14 @@ ess_status ess_set_graphs(ess_state *state, int enable);
  * to the CTA-per-chain kernel.  For m > 8192 the CTA per chain is the
  * wide-row kernel (rows streamed); there ESS_CHAIN_AUTO and ESS_CHAIN_STREAM
  * run it for every chain (measured faster at m = 12000 and 16384, where most
- * chains keep more than 128 arcs), ESS_CHAIN_WARP runs the warp kernel first.
+ * chains keep more than 128 arcs), ESS_CHAIN_WARP runs the warp kernel first,
+ * and so does ESS_CHAIN_AUTO when some b_i <= 0 (those rows' arcs, half a
+ * circle or more, form one arc that the warp kernel keeps as its two extreme
+ * rows, so such chains rarely keep more than 128 arcs).
  * The kernels compute the same map; their results can differ in the last bits
  * (the order of FP32 roundings).  ess_get_chain_kernel reports the kernel in
  * use: ESS_CHAIN_STREAM, ESS_CHAIN_WARP, or ESS_CHAIN_CTA (sort_threads > 0,
- * or m > 8192 without ESS_CHAIN_WARP: a CTA per chain).
+ * or m > 8192 with the wide-row kernel for every chain).
  * Changing the kernel drops the captured CUDA graphs.  Errors: ESS_ERR_ARG.
  */
 enum { ESS_CHAIN_AUTO = 0, ESS_CHAIN_WARP = 1, ESS_CHAIN_STREAM = 2, ESS_CHAIN_CTA = 3 };

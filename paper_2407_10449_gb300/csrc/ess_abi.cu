@@ -382,6 +382,17 @@ ess::ChainParams<T> base_params(ess_state* s, int n) {
   return p;
 }
 
+// m > 8192: the warp kernel first (the wide-row kernel behind it for the
+// chains it leaves) with ESS_CHAIN_WARP, and by default when some b_i <= 0
+// (the long arcs' union leaves such chains few arcs: the probit-style
+// orthant at m = 16384, d = 256 went from 0.71 to 0.1x ms per step); else the
+// wide-row kernel for every chain.
+bool wide_warp_first(const ess_state* s) {
+  if (s->cfg.sort_threads > 0) return false;
+  return s->chain_kernel == ESS_CHAIN_WARP ||
+         (s->chain_kernel == ESS_CHAIN_AUTO && s->long_arcs != 0);
+}
+
 // One chain step of all chains: the warp-per-chain kernel, then the
 // CTA-per-chain kernel for the chains it left (too many arcs after the prune),
 // reading P and writing P2; the buffers are swapped afterwards.
@@ -396,7 +407,7 @@ ess_status launch_step(ess_state* s, ess::ChainParams<T> p, cudaStream_t st) {
     // wide-row kernel for the chains it leaves
     p.wide_scratch = static_cast<T*>(s->wide_scratch);
     p.wide_cap = s->wide_cap;
-    if (s->cfg.sort_threads > 0 || s->chain_kernel != ESS_CHAIN_WARP) {
+    if (!wide_warp_first(s)) {
       ESS_CUDA(ess::launch_chain_step_wide<T>(p, s->wide_slots, st));
     } else {
       ESS_CUDA(cudaMemsetAsync(s->ovf, 0, 2 * sizeof(int), st));
@@ -1106,7 +1117,7 @@ ess_status ess_set_chain_kernel(ess_state* s, int kind) {
 
 ess_status ess_get_chain_kernel(const ess_state* s, int* kind) {
   if (!s || !kind) return fail(ESS_ERR_ARG, "NULL argument");
-  if (s->cfg.sort_threads > 0 || (s->wide && s->chain_kernel != ESS_CHAIN_WARP))
+  if (s->cfg.sort_threads > 0 || (s->wide && !wide_warp_first(s)))
     *kind = ESS_CHAIN_CTA;
   else if (mixed(s) && s->chain_kernel == ESS_CHAIN_STREAM && ess::chain_stream_supported(s->m, s->d))
     *kind = ESS_CHAIN_STREAM;

@@ -60,6 +60,10 @@ def _run(A, b, X, NU, U, precision, max_pieces, warp_first=False, **cfg):
             assert ess.ess_get_chain_kernel(s.state) == (
                 ess.ESS_CHAIN_CTA if cfg.get("sort_threads") else ess.ESS_CHAIN_WARP)
         else:
+            if np.any(b <= 0.0):
+                # rows with b <= 0 make the default run the warp kernel first;
+                # ESS_CHAIN_STREAM keeps the wide-row kernel for every chain
+                ess.ess_set_chain_kernel(s.state, ess.ESS_CHAIN_STREAM)
             assert ess.ess_get_chain_kernel(s.state) == ess.ESS_CHAIN_CTA
         Xn, th, pcs, npc, rej = s.step_with_draws(dev(X), dev(NU), dev(U), max_pieces=max_pieces)
         out = host(Xn), host(th), host(pcs), host(npc), host(rej), s.stats()
