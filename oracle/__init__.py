@@ -21,9 +21,10 @@ Each wrapper names the part of the paper it follows:
 * ``whiten`` / ``unwhiten``: App. A.
 * ``cholesky``: App. A's factor Sigma = L L^T (Cholesky-Banachiewicz).
 
-Parity of the Philox bit stream with the published known-answer vectors is
-unpinned here (the vectors are not available offline); it is pinned by
-agreement with the independent CUDA implementation and by statistical tests.
+The Philox bit stream is pinned by an independent implementation of the
+published generator (triton's language library, run on the host by its
+interpreter; tests/test_oracle_philox.py), bit for bit, and the draws by
+statistical tests.
 """
 from __future__ import annotations
 

@@ -3,13 +3,11 @@
 * The theta draw is the inverse CDF of the uniform law on I_act: checked by
   the measure identity |I_act and [0, theta(u)]| = u |I_act| and monotonicity.
 * Box-Muller normals and the uniforms are checked against their laws (KS).
-* The Philox bit stream is parity unpinned: the published known-answer
-  vectors are not available offline.  The second implementation written here
-  restates the same round function from the same source, so agreeing with it
-  only cross-checks the C transcription (word order, carries); it does not
-  pin the constants.  The uniformity and normality tests below would not
-  catch a wrong multiplier either.  The bit stream only has to be a good
-  generator for the sampler's law, which the KS tests check.
+* The Philox bit stream is pinned in test_oracle_philox.py, against an
+  independent library implementation.  The second implementation written
+  here restates the same round function from the same source, so agreeing
+  with it only cross-checks the C transcription (word order, carries); the
+  uniformity and normality tests below check the generator's laws.
 * The chain's stationary law is the truncated normal (Sec. 2, citing Murray
   et al.): KS tests against the exact univariate truncated normal at d = 1 and
   d = 2, and the moments printed in the Sec. 4.1 table.
