@@ -169,6 +169,27 @@ __device__ __forceinline__ void cta_chain_step(const ChainParams<T>& prm, int c,
     s_gearly[2 * lane + 1] = lane == 0 ? -1.f : incl1;
   }
   __syncthreads();
+  // Long arcs (b_i <= 0: half a circle or more) overlap pairwise when x is
+  // feasible, so together they are one arc (min alpha, max beta): an arc
+  // inside it changes no piece, and the rows holding the two extremes stay.
+  float ua = INFINITY, ub = -INFINITY;
+  if (v.long_arcs) {
+    __shared__ float s_utmp[NW];
+    float my_na = -INFINITY, my_b = -INFINITY;
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+      const int i = tid + r * NT;
+      if (cls[r] == kRowApprox && v.b[i] <= T(0)) {
+        my_na = fmaxf(my_na, -a_ap[r]);
+        my_b = fmaxf(my_b, b_ap[r]);
+      }
+    }
+    float tot;
+    (void)block_exclusive_scan<NT>(my_na, -INFINITY, OpMax(), s_utmp, tot);
+    ua = -tot;
+    (void)block_exclusive_scan<NT>(my_b, -INFINITY, OpMax(), s_utmp, tot);
+    ub = tot;
+  }
   int my_count = 0;
   bool keep[ITEMS];
 #pragma unroll
@@ -176,7 +197,8 @@ __device__ __forceinline__ void cta_chain_step(const ChainParams<T>& prm, int c,
     keep[r] = cls[r] == kRowKeep;
     if (cls[r] == kRowApprox) {
       const int bk = min(kBuckets - 1, (int)(a_ap[r] * to_bucket));
-      keep[r] = !(b_ap[r] + 2.f * kPruneMargin <= s_gearly[bk]);
+      keep[r] = !(b_ap[r] + 2.f * kPruneMargin <= s_gearly[bk]) &&
+                !(a_ap[r] >= ua + 2.f * kPruneMargin && b_ap[r] <= ub - 2.f * kPruneMargin);
     }
     my_count += keep[r] ? 1 : 0;
   }

@@ -222,12 +222,14 @@ def test_mixed_cta_kernel_probit_orthant():
     check_mixed(A, b, X, NU, U, sort_threads=256)
 
 
+@pytest.mark.parametrize("sort_threads", [0, 256])
 @pytest.mark.parametrize("half", [False, True])
-def test_mixed_warp_kernel_long_arc_union(half):
+def test_mixed_long_arc_union(half, sort_threads):
     """Rows with b_i <= 0 have infeasible arcs of length >= pi; for a feasible
     x any two overlap, so together they are one arc (min alpha, max beta) and
-    the warp kernel keeps only the rows holding its two extremes (Sec. 3.1's
-    I_act unchanged).  A probit-style orthant (b = 0: no arc contains another,
+    the step keeps only the rows holding its two extremes (Sec. 3.1's I_act
+    unchanged): the warp kernel (sort_threads = 0) and the CTA-per-chain
+    kernel (256).  A probit-style orthant (b = 0: no arc contains another,
     so the bucket prune alone keeps every arc), and the same with half of the
     rows given b > 0 (short arcs, pruned by the union and by each other).
     Grid inputs, every chain against the oracle; few arcs reach the sort."""
@@ -247,8 +249,8 @@ def test_mixed_warp_kernel_long_arc_union(half):
     X = np.tile(z, (n, 1))
     NU = to_grid(rng.standard_normal((n, k)), B)
     U = rng.uniform(size=n)
-    stats, _, _ = check_mixed(A, b, X, NU, U)
-    # without the union every chain would sort all 256 arcs (CTA kernel)
+    stats, _, _ = check_mixed(A, b, X, NU, U, sort_threads=sort_threads)
+    # without the union every chain would sort (or merge) all 256 arcs
     assert stats["sort_keys"] < 32 * n, stats["sort_keys"]
 
 
