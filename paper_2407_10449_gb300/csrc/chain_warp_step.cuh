@@ -118,7 +118,8 @@ constexpr size_t kWarpStepSmem = ((size_t)2 * kWBP + 2 * kCand + kCap) * 4;
 
 // One step of chain c by the calling warp (all 32 lanes), with kWarpStepSmem
 // bytes of shared memory at wsm.  Returns the chain's sorted keys (the same
-// on every lane; 0 if the chain was left to the CTA-per-chain step).
+// on every lane), or -1 if the chain was left untouched for the CTA-per-chain
+// step (appended to prm.overflow_list when prm.overflow_count is set).
 // LONG: compile the long-arc union (used for the chains whose view has
 // long_arcs set); without it the kernel carries none of that code.
 template <typename T, bool BATCH, bool LONG = false>
@@ -401,9 +402,11 @@ __device__ __forceinline__ int warp_chain_step(const ChainParams<T>& prm, int c,
   }
   __syncwarp();
 
-  if (n_surv > kCap) {
-    // too many arcs for one warp: the CTA-per-chain kernel takes this chain
-    if (lane == 0) {
+  const bool left = n_surv > kCap;
+  if (left) {
+    // too many arcs for one warp: the CTA-per-chain step takes this chain
+    // (listed here when the launch gives a list; else the caller takes it)
+    if (lane == 0 && prm.overflow_count) {
       const int at = atomicAdd(prm.overflow_count, 1);
       prm.overflow_list[at] = c;
     }
@@ -615,7 +618,7 @@ __device__ __forceinline__ int warp_chain_step(const ChainParams<T>& prm, int c,
       atomicMax(&prm.stats->max_residual_bits, enc_ordered(maxres));
   }
   if (__any_sync(kFull, infeasible) && lane == 0) atomicOr(prm.status, kStatusInfeasible);
-  return my_sort_keys;
+  return left ? -1 : my_sort_keys;
 }
 
 }  // namespace

@@ -489,12 +489,26 @@ ess::ChainParams<T> bparams(ess_batch* s) {
   return p;
 }
 
+// Kernel launches of one chain step: the warp kernel alone when it steps the
+// chains it leaves itself, else it and the CTA kernel.
+int bchain_launches(const ess_batch* s) {
+  return (bmixed(s) ? ess::chain_warp_local_fallback<float>(s->max_m, s->max_d)
+                    : ess::chain_warp_local_fallback<double>(s->max_m, s->max_d)) ? 1 : 2;
+}
+
 // Chain step of every chain: warp kernel, then the CTA kernel for the chains
 // it listed; reads P, writes P2 (the caller swaps them).
 template <typename T>
 ess_status bchain(ess_batch* s, ess::ChainParams<T> p, cudaStream_t st) {
   p.P_in = static_cast<const T*>(s->P);
   p.P_out = static_cast<T*>(s->P2);
+  if (ess::chain_warp_local_fallback<T>(s->max_m, s->max_d)) {
+    // the warp kernel steps the chains it leaves itself (one launch)
+    p.overflow_count = nullptr;
+    p.overflow_list = nullptr;
+    BESS_CUDA(ess::launch_chain_step_warp<T>(p, st));
+    return ESS_OK;
+  }
   BESS_CUDA(cudaMemsetAsync(s->ovf, 0, sizeof(int), st));
   p.overflow_count = s->ovf;
   p.overflow_list = s->ovf + 1;
@@ -560,7 +574,7 @@ ess_status bstep(ess_batch* s, uint64_t seed, uint32_t t, const unsigned* t_dev,
   p.t = t;
   p.t_dev = t_dev;
   p.samples = samples;
-  BPhase ph(s, st, ESS_PHASE_CHAIN, 2);
+  BPhase ph(s, st, ESS_PHASE_CHAIN, bchain_launches(s));
   ess_status rc = bchain<T>(s, p, st);
   std::swap(s->P, s->P2);
   return rc;
@@ -636,7 +650,7 @@ ess_status bgraph_period(ess_batch* s, uint64_t seed, cudaStream_t st) {
   s->phase_launches[ESS_PHASE_REFRESH] += 1;
   s->phase_launches[ESS_PHASE_DRAW] += k;
   s->phase_launches[ESS_PHASE_GEMM] += k;
-  s->phase_launches[ESS_PHASE_CHAIN] += 2 * k;
+  s->phase_launches[ESS_PHASE_CHAIN] += (long long)bchain_launches(s) * k;
   return ESS_OK;
 }
 

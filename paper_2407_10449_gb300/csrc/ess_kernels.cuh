@@ -194,12 +194,19 @@ cudaError_t launch_chain_step(const ChainParams<T>& p, int threads, cudaStream_t
 
 // One warp per chain: prune, sort up to kWarpSortCap arcs in registers, sweep,
 // draw and move.  Chains with more arcs left after the prune are appended to
-// p.overflow_list (untouched) for launch_chain_step in list mode.
+// p.overflow_list (untouched) for launch_chain_step in list mode, or, with
+// p.overflow_list == nullptr (see chain_warp_local_fallback), stepped by the
+// CTA-per-chain step inside the same launch.
 // p.P_out must differ from p.P_in (a rejected move restores p from P_in).
 template <typename T>
 cudaError_t launch_chain_step_warp(const ChainParams<T>& p, cudaStream_t s);
 template <typename T>
 size_t chain_warp_smem_bytes(int m);
+// Whether the warp kernel can step the chains it leaves itself, at the end of
+// each CTA (launch with p.overflow_list == nullptr): float chains with m up to
+// 2048 whose CTA-per-chain step fits the warp kernel's shared memory.
+template <typename T>
+bool chain_warp_local_fallback(int m, int d);
 constexpr int kWarpSortCap = 128;
 
 // One warp per chain, warps taking chains from *p.work_counter (zeroed before

@@ -306,7 +306,8 @@ __global__ void __launch_bounds__(kPT, 1) batch_persist_kernel(BatchPersistArgs 
       ticket = __shfl_sync(0xffffffffu, ticket, 0);
       if (ticket >= n) break;
       const int c = a.order[ticket];
-      sort_keys += warp_chain_step<float, true, LONG>(p, c, wsm, lane);
+      const int keys = warp_chain_step<float, true, LONG>(p, c, wsm, lane);
+      if (keys > 0) sort_keys += keys;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     ok = grid_barrier(a.bar, a.abort_flag, a.prm.status, a.wait_ns);
