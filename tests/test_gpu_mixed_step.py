@@ -254,6 +254,34 @@ def test_mixed_long_arc_union(half, sort_threads):
     assert stats["sort_keys"] < 32 * n, stats["sort_keys"]
 
 
+@pytest.mark.parametrize("path", ["warp", "stream", "cta"])
+def test_mixed_overflow_chains(path):
+    """Chains that keep more arcs than a warp sorts: rows facing away from x
+    with b = 2^-8 (every arc a little shorter than a half circle, none inside
+    another), so each chain keeps ~300 arcs.  The warp kernel steps them at
+    the end of its own CTA ("warp"), the streamed kernel lists them for the
+    CTA kernel ("stream"), or the CTA kernel takes every chain ("cta"); grid
+    inputs, every chain against the oracle."""
+    rng = np.random.default_rng(31)
+    d, m, n = 24, 320, 48
+    B = grid_bits(d)
+    x = to_grid(rng.standard_normal(d), B)
+    A = to_grid(rng.standard_normal((m, d)) / np.sqrt(d), B)
+    A[A @ x > 0] *= -1.0
+    keep = A @ x < -1e-3
+    A = A[keep]
+    A = A[:A.shape[0] // 4 * 4]  # the streamed kernel takes m, d multiples of 4
+    b = np.full(A.shape[0], 2.0**-8)
+    X = np.tile(x, (n, 1))
+    NU = to_grid(rng.standard_normal((n, d)), B)
+    U = rng.uniform(size=n)
+    cfg = {"sort_threads": 256} if path == "cta" else {}
+    kind = ess.ESS_CHAIN_STREAM if path == "stream" else None
+    stats, _, _ = check_mixed(A, b, X, NU, U, chain_kernel=kind, **cfg)
+    # every chain kept more arcs than a warp sorts (128)
+    assert stats["sort_keys"] > 128 * n
+
+
 def test_mixed_near_tangent_rows_fp64_branch():
     """Rows with b / r in (1 - 1e-4, 1): the mixed form takes the arccos
     argument and the angles in FP64 (tangent_fp64 counts them).  Grid rows,
