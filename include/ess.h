@@ -469,7 +469,10 @@ ess_status ess_set_graphs(ess_state *state, int enable);
  *   ESS_CHAIN_AUTO (default): one warp per chain, rows read from global
  *       memory (the fastest form measured at d = 1000, m = 2000, 8192 chains;
  *       the autotuner of ess_config.autotune times both forms).
- *   ESS_CHAIN_WARP: the same kernel, chosen explicitly.
+ *       With fewer chains than SMs and m > 256 it runs one CTA per chain
+ *       instead (the step is then the latency of one chain: at m = 2000, one
+ *       chain, 33 us per step against 81 with one warp).
+ *   ESS_CHAIN_WARP: the warp kernel, chosen explicitly (for any chain count).
  *   ESS_CHAIN_STREAM: in the mixed form, when m and d are multiples of 4 and
  *       m is at most 4096, one warp per chain with the chain's p and q rows
  *       streamed through shared memory in chunks by 1-D bulk copies (for the
@@ -485,8 +488,9 @@ ess_status ess_set_graphs(ess_state *state, int enable);
  * rows, so such chains rarely keep more than 128 arcs).
  * The kernels compute the same map; their results can differ in the last bits
  * (the order of FP32 roundings).  ess_get_chain_kernel reports the kernel in
- * use: ESS_CHAIN_STREAM, ESS_CHAIN_WARP, or ESS_CHAIN_CTA (sort_threads > 0,
- * or m > 8192 with the wide-row kernel for every chain).
+ * use for the loaded chains: ESS_CHAIN_STREAM, ESS_CHAIN_WARP, or
+ * ESS_CHAIN_CTA (sort_threads > 0, fewer chains than SMs under
+ * ESS_CHAIN_AUTO, or m > 8192 with the wide-row kernel for every chain).
  * Changing the kernel drops the captured CUDA graphs.  Errors: ESS_ERR_ARG.
  */
 enum { ESS_CHAIN_AUTO = 0, ESS_CHAIN_WARP = 1, ESS_CHAIN_STREAM = 2, ESS_CHAIN_CTA = 3 };

@@ -79,6 +79,7 @@ struct ess_state {
   long long wide_cap = 0;
   int wide_slots = 0;
   int tuned_n = 0;            // chain count the autotuner last tuned for
+  int sms = 0;                // SM count of the device
   // constants (device)
   double* A64 = nullptr;
   double* b64 = nullptr;
@@ -393,9 +394,21 @@ bool wide_warp_first(const ess_state* s) {
          (s->chain_kernel == ESS_CHAIN_AUTO && s->long_arcs != 0);
 }
 
+// Fewer chains than SMs (ESS_CHAIN_AUTO, m above 256 so that the CTA-per-
+// chain kernel gives a chain 64 or more threads): one CTA per chain.  A warp
+// per chain wins on throughput once the chains fill the GPU; with fewer
+// chains than SMs the step is the latency of one chain, and one warp
+// streaming all m rows took 81 us per step at m = 2000 (1 chain) against 33
+// us for a CTA of 256 threads, 246 against 54 at m = 4000.
+bool few_chains_cta(const ess_state* s, int n) {
+  if (s->wide || s->chain_kernel != ESS_CHAIN_AUTO || s->chain_threads < 64 || s->sms <= 0)
+    return false;
+  return n < s->sms;
+}
+
 // Kernel launches of one chain step (per-phase accounting).
 int chain_launches_per_step(const ess_state* s) {
-  if (s->cfg.sort_threads > 0) return 1;
+  if (s->cfg.sort_threads > 0 || few_chains_cta(s, s->n_loaded)) return 1;
   if (s->wide) return wide_warp_first(s) ? 2 : 1;
   const bool streamed = mixed(s) && s->chain_kernel == ESS_CHAIN_STREAM &&
                         ess::chain_stream_supported(s->m, s->d);
@@ -431,7 +444,7 @@ ess_status launch_step(ess_state* s, ess::ChainParams<T> p, cudaStream_t st) {
     std::swap(s->P, s->P2);
     return ESS_OK;
   }
-  if (s->cfg.sort_threads > 0) {
+  if (s->cfg.sort_threads > 0 || few_chains_cta(s, p.n_chains)) {
     ESS_CUDA(ess::launch_chain_step<T>(p, s->chain_threads, st));
   } else {
     bool streamed = false;
@@ -842,6 +855,7 @@ ess_status ess_create(const double* A, const double* b, int d, int m, const ess_
   s->m = m;
   s->cfg = c;
   s->device = dev;
+  cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
   s->ld16 = (d + 7) & ~7;
   s->chain_threads = threads;
   s->min_chain_threads = min_threads;
@@ -1137,7 +1151,8 @@ ess_status ess_set_chain_kernel(ess_state* s, int kind) {
 
 ess_status ess_get_chain_kernel(const ess_state* s, int* kind) {
   if (!s || !kind) return fail(ESS_ERR_ARG, "NULL argument");
-  if (s->cfg.sort_threads > 0 || (s->wide && !wide_warp_first(s)))
+  if (s->cfg.sort_threads > 0 || (s->wide && !wide_warp_first(s)) ||
+      few_chains_cta(s, s->n_loaded))
     *kind = ESS_CHAIN_CTA;
   else if (mixed(s) && s->chain_kernel == ESS_CHAIN_STREAM && ess::chain_stream_supported(s->m, s->d))
     *kind = ESS_CHAIN_STREAM;

@@ -26,6 +26,10 @@ X_RTOL = 1e-9
 def run_step(A, b, X, NU, U, precision=ess.ESS_PREC_FP64, max_pieces=None, **cfg):
     s = ess.Sampler(A, b, precision=precision, **cfg)
     try:
+        if not cfg.get("sort_threads"):
+            # the warp-per-chain kernel (the default picks a CTA per chain for
+            # fewer chains than SMs, test_few_chains_take_a_cta_per_chain)
+            ess.ess_set_chain_kernel(s.state, ess.ESS_CHAIN_WARP)
         mp = max_pieces or (A.shape[0] + 2)
         Xn, th, pcs, npc, rej = s.step_with_draws(dev(X), dev(NU), dev(U), max_pieces=mp)
         return host(Xn), host(th), host(pcs), host(npc), host(rej), s.stats()
@@ -252,3 +256,37 @@ def test_cta_kernel_short_arcs(sort_threads):
     check_fp64(A, b, X, NU, U, sort_threads=sort_threads)
     # the long-arc rows alone take the bucket merge in the CTA kernel
     check_fp64(A_long, b_long, X, NU, U, sort_threads=sort_threads)
+
+
+@pytest.mark.parametrize("precision", [ess.ESS_PREC_FP64, ess.ESS_PREC_MIXED])
+def test_few_chains_take_a_cta_per_chain(precision):
+    """ESS_CHAIN_AUTO with fewer chains than SMs (m > 256) steps each chain
+    with a CTA (its rows over the CTA's threads) instead of one warp: the
+    kernel reported for the loaded chains, and the step against the oracle."""
+    import torch
+    rng = np.random.default_rng(41)
+    d, m, n = 30, 700, 10
+    A, b, X = feasible_instance(rng, d, m, n, scale=1.0 / math.sqrt(d), slack=(0.1, 1.0))
+    s = ess.Sampler(A, b, precision=precision)
+    try:
+        ess.ess_chains_init(s.state, dev(X), n, 0)
+        assert ess.ess_get_chain_kernel(s.state) == ess.ESS_CHAIN_CTA
+        ess.ess_set_chain_kernel(s.state, ess.ESS_CHAIN_WARP)
+        assert ess.ess_get_chain_kernel(s.state) == ess.ESS_CHAIN_WARP
+    finally:
+        s.close()
+    NU = rng.standard_normal((n, d))
+    U = rng.uniform(size=n)
+    if precision == ess.ESS_PREC_FP64:
+        Xn, th, pcs, npc, rej, _ = run_step(A, b, X, NU, U, sort_threads=0)  # warp
+        s = ess.Sampler(A, b, precision=precision)
+        try:
+            got = s.step_with_draws(dev(X), dev(NU), dev(U), max_pieces=m + 2)
+            Xa, tha = host(got[0]), host(got[1])
+        finally:
+            s.close()
+        ref = oracle_steps(A, b, X, NU, U, 0.0)
+        for c, r in enumerate(ref):
+            assert abs(tha[c] - r.theta) <= ANG_TOL, (c, tha[c], r.theta)
+            assert np.all(np.abs(Xa[c] - r.x_next) <= X_RTOL * np.maximum(1.0, np.abs(r.x_next)))
+

@@ -136,6 +136,10 @@ def check_mixed(A, b, X, NU, U, trim_eps=0.0, eps_p=0.0, eps_q=0.0, sample=None,
     exempt = mixed_exempt(refs, amp, arith, LIMIT, trim_eps)
     s = ess.Sampler(A, b, precision=ess.ESS_PREC_MIXED, trim_eps=trim_eps, **cfg)
     try:
+        if chain_kernel is None and not cfg.get("sort_threads"):
+            # the warp-per-chain kernel (the default picks a CTA per chain for
+            # fewer chains than SMs)
+            chain_kernel = ess.ESS_CHAIN_WARP
         if chain_kernel is not None:
             ess.ess_set_chain_kernel(s.state, chain_kernel)
         mp = max_pieces or (A.shape[0] + 2)
