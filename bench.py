@@ -669,6 +669,9 @@ def time_configs(ess, torch, workloads, peaks, seed, errors=True):
             if errors:
                 entry[form]["error_vs_oracle"] = oracle_errors(ess, torch, inst.A, inst.b,
                                                                lc["states"], form, seed)
+        if C <= 16:
+            # the few-chain FP64 path: every step of the run in one cooperative kernel
+            entry["fp64_few"] = time_few(ess, torch, inst, C, 1000, seed)
         out[name] = entry
     out["probit_n2000_c4096"]["unwhiten"] = time_unwhiten(ess, torch, pb, 4096, peaks)
     out["probit_n2000_c4096"]["cholesky"] = chol
@@ -760,6 +763,29 @@ def time_wide(ess, torch, workloads, peaks, seed, errors=True):
                                                                lc["states"], form, seed)
         out[name] = entry
     return out
+
+
+def time_few(ess, torch, inst, C, steps, seed):
+    """C <= 16 FP64 chains through ess_run_few (all steps in one persistent
+    cooperative kernel), timed with CUDA events after an 8-step warm-up."""
+    s = ess.Sampler(inst.A, inst.b, precision=ess.ESS_PREC_FP64)
+    try:
+        X = torch.tensor(inst.X0[0], dtype=torch.float64, device="cuda").repeat(C, 1).contiguous()
+        ess.ess_run_few(s.state, X, C, 0, 8, seed)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ess.ess_run_few(s.state, X, C, 8, steps, seed)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = s.stats()
+    finally:
+        s.close()
+    return {"value": C * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
+            "us_per_step": 1e3 * ms / steps, "dtype": "f64", "call": "ess_run_few",
+            "rejections": st["rejections"], "numeric_errors": st["numeric_errors"]}
 
 
 def time_paper_hd(ess, torch, workloads, peaks, seed):
