@@ -597,11 +597,14 @@ ess_status ess_batch_reset_timing(ess_batch *batch);
  * CTA step for each step), a refresh period replays as the refresh of p and
  * the draw of step 0, then ONE cooperative kernel with one 1024-thread CTA
  * per SM for all refresh_k steps.  Per step its warps 0..5 run the grouped
- * q GEMM on the tensor cores while warps 6..31 draw nu of the next step;
- * then every warp takes chains from a device work queue (chains of the most
- * rows first) for the warp-per-chain step, and whole CTAs take the chains
- * left with too many arcs; the phases are joined by grid barriers whose
- * waits are bounded by cfg->wait_limit_us (ESS_ERR_TIMEOUT on expiry).  The
+ * q GEMM on the tensor cores, warps 6..21 draw nu of the next step, and
+ * warps 22..31 -- then warps 0..21 too, once the CTA's own q items are done
+ * -- take chains from a device work queue (problems in the order their q
+ * items finish) for the warp-per-chain step, each chain after its problem's
+ * q is complete (a per-problem counter of finished q items); whole CTAs
+ * then take the chains left with too many arcs.  Steps are joined by grid
+ * barriers; every dependency and barrier wait is bounded by
+ * cfg->wait_limit_us (ESS_ERR_TIMEOUT on expiry).  The
  * chains are the ones of the graph of per-step launches (the same products,
  * roots, prune, sort and draws); the chains left with too many arcs take the
  * same CTA step at 1024 threads (more merge buckets, another summation order
@@ -609,13 +612,24 @@ ess_status ess_batch_reset_timing(ess_batch *batch);
  * theta in the last bits.  It applies to runs that
  * replay graphs (no sample recording, no per-phase timing, refresh_k even).
  * Errors: ESS_ERR_UNSUPPORTED for the FP64 form, or when the device cannot
- * hold the launch (cooperative launch, one CTA of 1024 threads and ~213 KB of
+ * hold the launch (cooperative launch, one CTA of 1024 threads and ~217 KB of
  * shared memory per SM; largest m_p up to 8192).  Default: on for the mixed
  * form where the device holds the launch (measured at the speed of the
  * per-step graph: 0.179 ms per step for 512 problems, 18,687 chains);
  * enable = 0 returns to the per-step graph.
  * Reference: Alg. 1 (the batch itself has no counterpart in the paper). */
 ess_status ess_batch_set_persistent(ess_batch *batch, int enable);
+
+/* Self-test of the persistent launch's bounded dependency waits (the paper
+ * has no counterpart): lays out n_chains and runs 2 refresh_k steps of X
+ * (device, packed as in ess_batch_run) with every problem's q dependency
+ * raised by one count that nothing releases.  The first refresh_k steps run
+ * as plain launches; in the persistent launch of the second period every
+ * chain step's wait runs out after cfg->wait_limit_us, the kernel returns,
+ * and so must this call, with ESS_ERR_TIMEOUT; the batch stays usable (X is
+ * left unspecified).  ESS_ERR_UNSUPPORTED unless the persistent launch is on
+ * (mixed form) and refresh_k is even.  Synchronous. */
+ess_status ess_batch_selftest_wait(ess_batch *batch, const int *n_chains, double *X);
 
 /* Sizes of the current chain layout: packed state and product lengths, GEMM
  * work items, and the graph replays since the last timing reset. */

@@ -52,7 +52,7 @@ EXPORTED = ("ess_default_config", "ess_create", "ess_destroy", "ess_limits", "es
             "ess_batch_create", "ess_batch_destroy", "ess_batch_run", "ess_batch_step_with_draws",
             "ess_batch_products", "ess_batch_get_stats", "ess_batch_reset_stats",
             "ess_batch_set_graphs", "ess_batch_set_persistent", "ess_batch_set_timing", "ess_batch_get_timing",
-            "ess_batch_reset_timing", "ess_batch_info",
+            "ess_batch_reset_timing", "ess_batch_info", "ess_batch_selftest_wait",
             "ess_last_error")
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -162,6 +162,7 @@ def load(build_if_missing: bool = True):
             "ess_batch_get_timing": ([_vp, _vp, _vp, c_int], c_int),
             "ess_batch_reset_timing": ([_vp], c_int),
             "ess_batch_info": ([_vp, _vp, _vp, _vp, _vp], c_int),
+            "ess_batch_selftest_wait": ([_vp, _vp, _vp], c_int),
             "ess_last_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -564,6 +565,14 @@ def ess_batch_set_graphs(batch, enable=True):
 
 def ess_batch_set_persistent(batch, enable=True):
     _check(load().ess_batch_set_persistent(batch, 1 if enable else 0))
+
+
+def ess_batch_selftest_wait(batch, n_chains, X):
+    """Bounded dependency-wait self-test of the persistent batched launch (see
+    include/ess.h): raises EssError with ESS_ERR_TIMEOUT when the waits gave
+    up as they should."""
+    nc = _counts(n_chains)
+    _check(load().ess_batch_selftest_wait(batch, nc.ctypes.data, _ptr(X)))
 
 
 def ess_batch_set_timing(batch, enable=True):

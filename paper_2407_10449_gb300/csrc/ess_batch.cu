@@ -105,6 +105,7 @@ struct ess_batch {
   BatchItem* items = nullptr;
   int n_items = 0;
   ess::TcBatchItem* titems = nullptr;  // mixed form: items of the tensor-core q GEMM
+  ess::TcBatchItem* ptitems = nullptr; // the same items in the persistent launch's order
   int n_titems = 0, cap_titems = 0;
   CUtensorMap* tmaps = nullptr;  // mixed form: 4 operand maps per problem (A and nu splits)
   CUtensorMap* tmaps_alt = nullptr;  // the same maps over the second nu splits
@@ -143,6 +144,8 @@ struct ess_batch {
   int* pqueue = nullptr;      // 2 ints per step: chain tickets, overflow count
   int cap_pqueue = 0;
   unsigned* pbar = nullptr;   // grid barrier state (2) and abort flag (1)
+  int* pdep = nullptr;        // per problem: 4 x its q items, then the counters
+  unsigned persist_hold = 0;  // 1 only inside ess_batch_selftest_wait
   long long persist_launches = 0;
   struct GraphEntry {
     int version;
@@ -213,6 +216,7 @@ void free_work(ess_batch* s) {
   bfree(s->desc);
   bfree(s->items);
   bfree(s->titems);
+  bfree(s->ptitems);
   s->cap_titems = 0;
   if (s->tmaps) cudaFree(s->tmaps);
   if (s->tmaps_alt) cudaFree(s->tmaps_alt);
@@ -339,6 +343,7 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
     BESS_CUDA(balloc(&s->desc, std::max<size_t>(1, desc.size())));
     BESS_CUDA(balloc(&s->items, std::max<size_t>(1, items.size())));
     BESS_CUDA(balloc(&s->titems, std::max<size_t>(1, titems.size())));
+    BESS_CUDA(balloc(&s->ptitems, std::max<size_t>(1, titems.size())));
     s->cap_titems = (int)titems.size();
     BESS_CUDA(cudaMalloc(&s->X, std::max<long long>(1, xo) * e));
     BESS_CUDA(cudaMalloc(&s->NU, std::max<long long>(1, xo) * e));
@@ -366,12 +371,31 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
   }
   if (!desc.empty()) {
     BESS_CUDA(cudaMemcpy(s->desc, desc.data(), sizeof(ChainDesc) * desc.size(), cudaMemcpyHostToDevice));
-    // the persistent launch's chain queue: chains of the most rows first
+    // the persistent launch: its chain queue takes chains of the most rows
+    // first (LPT order), problem by problem, and its q GEMM walks the items
+    // problem by problem in the same order (largest first within a problem),
+    // so the problems' q complete in about the order their chains are taken;
+    // the dependency target of a problem is 4 counts (one per epilogue warp)
+    // per item
     std::vector<int> order(desc.size());
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return desc[a].m > desc[b].m; });
+    std::vector<int> rank(s->np, 0), target(s->np, 0);
+    for (int k = (int)order.size() - 1; k >= 0; --k) rank[desc[order[k]].problem] = k;
+    for (const auto& it : titems) target[it.problem] += 4;
+    std::vector<ess::TcBatchItem> pt(titems);
+    std::stable_sort(pt.begin(), pt.end(), [&](const ess::TcBatchItem& a, const ess::TcBatchItem& b) {
+      return rank[a.problem] < rank[b.problem];
+    });
     BESS_CUDA(cudaMemcpy(s->porder, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice));
+    if (bmixed(s)) {
+      if (!s->pdep) BESS_CUDA(balloc(&s->pdep, 2 * (size_t)s->np));
+      BESS_CUDA(cudaMemcpy(s->pdep, target.data(), sizeof(int) * s->np, cudaMemcpyHostToDevice));
+      if (!pt.empty())
+        BESS_CUDA(cudaMemcpy(s->ptitems, pt.data(), sizeof(ess::TcBatchItem) * pt.size(),
+                             cudaMemcpyHostToDevice));
+    }
   }
   if (!items.empty())
     BESS_CUDA(cudaMemcpy(s->items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
@@ -657,8 +681,9 @@ ess_status bgraph_period(ess_batch* s, uint64_t seed, cudaStream_t st) {
 // Replays (capturing on first use) one refresh period as the persistent
 // launch: the refresh of p with the draw of step 0 beside it on the side
 // stream, then one cooperative kernel for the period's refresh_k steps (q
-// GEMM, draws of steps 1 .. k - 1, chain steps and overflow chains, phases
-// joined by grid barriers), starting at the step index in *t_dev.
+// GEMM, draws of steps 1 .. k - 1, chain steps gated by per-problem q
+// counters, overflow chains, steps joined by grid barriers), starting at the
+// step index in *t_dev.
 ess_status bpersist_period(ess_batch* s, uint64_t seed, cudaStream_t st) {
   const int k = s->cfg.refresh_k;
   ess_batch::GraphEntry* hit = nullptr;
@@ -674,7 +699,7 @@ ess_status bpersist_period(ess_batch* s, uint64_t seed, cudaStream_t st) {
     }
     if (!s->pbar) BESS_CUDA(balloc(&s->pbar, 3));
     ess::BatchPersistArgs a{};
-    a.titems = s->titems;
+    a.titems = s->ptitems;
     a.n_titems = s->n_titems;
     a.maps[0] = s->tmaps;
     a.maps[1] = s->tmaps_alt;
@@ -699,6 +724,9 @@ ess_status bpersist_period(ess_batch* s, uint64_t seed, cudaStream_t st) {
     a.steps = k;
     a.bar = s->pbar;
     a.abort_flag = reinterpret_cast<int*>(s->pbar + 2);
+    a.dep_target = s->pdep;
+    a.dep_done = reinterpret_cast<unsigned*>(s->pdep + s->np);
+    a.hold = s->persist_hold;
     a.wait_ns = s->cfg.wait_limit_us > 0 ? 1000ull * (unsigned long long)s->cfg.wait_limit_us
                                          : 2000000000ull;
     void* p_first = s->P;
@@ -720,7 +748,8 @@ ess_status bpersist_period(ess_batch* s, uint64_t seed, cudaStream_t st) {
     if (rc == ESS_OK && cap_ok(cudaStreamWaitEvent(cs, s->ev_drawn, 0), "graph join") &&
         cap_ok(cudaMemsetAsync(s->pqueue, 0, sizeof(int) * ess::batch_persist_queue_ints(k), cs),
                "persistent queue reset") &&
-        cap_ok(cudaMemsetAsync(s->pbar, 0, 3 * sizeof(unsigned), cs), "grid barrier reset"))
+        cap_ok(cudaMemsetAsync(s->pbar, 0, 3 * sizeof(unsigned), cs), "grid barrier reset") &&
+        cap_ok(cudaMemsetAsync(s->pdep + s->np, 0, sizeof(int) * s->np, cs), "dependency reset"))
       cap_ok(ess::launch_batch_persist(a, cs), "persistent batched launch");
     if (rc == ESS_OK) cap_ok(ess::launch_advance_t(s->t_dev, (unsigned)k, cs), "advance step index");
     cudaGraph_t graph = nullptr;
@@ -1054,6 +1083,7 @@ void ess_batch_destroy(ess_batch* s) {
   bfree(s->queue);
   bfree(s->pqueue);
   bfree(s->pbar);
+  bfree(s->pdep);
   bfree(s->t_dev);
   bfree(s->bm_tab);
   bfree(s->dstats);
@@ -1081,6 +1111,31 @@ ess_status ess_batch_run(ess_batch* s, const int* n_chains, double* X, int t0, i
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   return bmixed(s) ? brun<float>(s, X, t0, n_iter, seed, samples, record_every, st)
                    : brun<double>(s, X, t0, n_iter, seed, samples, record_every, st);
+}
+
+ess_status ess_batch_selftest_wait(ess_batch* s, const int* n_chains, double* X) {
+  ess_internal_set_error("");
+  if (!s || !n_chains || !X) return bfail(ESS_ERR_ARG, "NULL argument");
+  if (!bmixed(s) || !s->persist)
+    return bfail(ESS_ERR_UNSUPPORTED, "the self-test runs the persistent launch (mixed form)");
+  if (s->cfg.refresh_k % 2) return bfail(ESS_ERR_UNSUPPORTED, "refresh_k must be even");
+  BDeviceGuard g(s->device);
+  ess_status rc = prepare(s, n_chains);
+  if (rc != ESS_OK) return rc;
+  if (s->n == 0) return bfail(ESS_ERR_ARG, "no chains");
+  const bool graphs = s->use_graphs, timing = s->timing;
+  s->use_graphs = true;
+  s->timing = false;
+  // a period captured with the hold: the first refresh period runs plain
+  // steps, the second one the persistent launch
+  drop_graphs(s);
+  s->persist_hold = 1;
+  rc = brun<float>(s, X, 0, 2 * s->cfg.refresh_k, 0, nullptr, 0, nullptr);
+  s->persist_hold = 0;
+  drop_graphs(s);
+  s->use_graphs = graphs;
+  s->timing = timing;
+  return rc;
 }
 
 ess_status ess_batch_step_with_draws(ess_batch* s, const int* n_chains, const double* X,

@@ -1,7 +1,8 @@
 // ess_batch_persist.cuh -- the persistent launch of the batched mixed-form
 // sampler (k_batch_persist.cu): one cooperative kernel runs a whole refresh
 // period (q GEMM on the tensor cores, draws, chain steps, overflow chains)
-// with work queues and bounded grid barriers (internal to the library).
+// with work queues, per-problem dependency counters and bounded grid barriers
+// (internal to the library).
 #pragma once
 
 #include <cstdint>
@@ -34,9 +35,15 @@ struct BatchPersistArgs {
   int* queue;         // 2 ints per step: chain tickets, overflow count (zero at launch)
   int* ovf_list;      // n_chains ints: chains left to the overflow phase
   int steps;          // even
+  // dependencies: chain steps of problem p in step j wait until dep_done[p]
+  // (4 epilogue counts per q item, kept across steps) reaches
+  // (j + 1) dep_target[p] + hold
+  const int* dep_target;  // per problem: 4 x its q items
+  unsigned* dep_done;     // per problem, zero at launch
+  unsigned hold;          // 0; 1 in the self-test of the bounded wait (never released)
   unsigned* bar;      // 2 unsigned: grid barrier state (zero at launch)
   int* abort_flag;    // zero at launch
-  unsigned long long wait_ns;  // bound of every grid-barrier wait
+  unsigned long long wait_ns;  // bound of every dependency and grid-barrier wait
 };
 
 // Whether the persistent launch can run here: cooperative launches, one

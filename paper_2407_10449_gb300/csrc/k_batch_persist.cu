@@ -1,26 +1,36 @@
 // k_batch_persist.cu -- a whole refresh period of the batched mixed-form
 // sampler (many polytopes of uneven d and m, each with its own chains) in ONE
 // persistent cooperative launch: one CTA of 32 warps per SM, every step's
-// work taken from work queues, phases separated by bounded grid barriers.
+// work taken from work queues, the chain steps gated by per-problem
+// dependency counters, steps separated by bounded grid barriers.
 //
 // Per step j of the period (Alg. 1 for every chain of every problem):
-//   GEMM phase   warps 0..5: q = A_p nu for every problem on the tensor cores
-//                (tcgen05, TMA; the FP16x3 products of the one-problem form,
-//                items of 128 rows of A_p x up to 64 of its chains, walked
-//                b, b + G, ... largest first), with the TMA ring, MMA issue
-//                and TMEM accumulators kept live from step to step;
-//                warps 6..31 meanwhile draw nu of step j + 1 (Philox +
-//                Box-Muller, its fp16 splits) into the other nu buffers;
-//   chain phase  all 32 warps take chains from a device work queue (largest
-//                problems first) and run the warp-per-chain step (App. B
-//                roots, domination prune, Alg. 3 sort and sweep, theta,
-//                move, Sec. 3.3 check); chains with too many arcs go to a list;
-//   overflow     whole CTAs take the listed chains with the CTA-per-chain step.
+//   warps 0..5   q = A_p nu for every problem on the tensor cores (tcgen05,
+//                TMA; the FP16x3 products of the one-problem form, items of
+//                128 rows of A_p x up to 64 of its chains, walked b, b + G,
+//                ... largest first), with the TMA ring, MMA issue and TMEM
+//                accumulators kept live from step to step; each epilogue warp
+//                counts its finished rows of an item on the item's problem
+//                (a release: fence, then atomic add);
+//   warps 6..21  draw nu of step j + 1 (Philox + Box-Muller, its fp16
+//                splits) into the other nu buffers;
+//   warps 22..31 from the start of the step, take chains from a device work
+//                queue (problems in the order their q items finish) and run
+//                the warp-per-chain step (App. B roots, domination prune,
+//                Alg. 3 sort and sweep, theta, move, Sec. 3.3 check), each
+//                after a bounded wait for its problem's count to reach the
+//                problem's items x 4 (an acquire); their shared memory lies
+//                behind the GEMM's ring;
+//   warps 0..21  join the chain queue once the CTA's own q items are done
+//                (a named barrier; the idle ring becomes their step areas);
+//   chains with too many arcs go to a list, which whole CTAs take after a
+//   grid barrier with the CTA-per-chain step (overflow phase).
 // The refresh of p = A x and the draw of step 0 run before the launch (the
-// caller's graph nodes).  Every wait -- the mbarriers of the GEMM phase and
-// the grid barriers -- is bounded: on expiry the CTA sets the time-out status
-// and an abort flag that every other CTA sees at its next barrier, drains its
-// own copies in flight, frees its tensor memory and returns.
+// caller's graph nodes).  Every wait -- the mbarriers of the GEMM, the
+// dependency counters and the grid barriers -- is bounded: on expiry the
+// warp sets the time-out status and an abort flag that every other wait
+// sees, the CTA drains its own copies in flight, frees its tensor memory and
+// returns.
 #include <cuda.h>
 
 #include <algorithm>
@@ -44,11 +54,18 @@ constexpr int kGemmWarps = 6;           // producer, MMA issuer, 4 epilogue warp
 constexpr int kPBK = 64;                // 16-bit elements per 128-byte swizzle row
 constexpr uint32_t kPA = 128 * 64 * 2;  // bytes of one A split tile (128 rows x 64)
 constexpr uint32_t kPStage = 2 * kPA + 2 * 64 * 64 * 2;  // two A and two nu tiles
-constexpr int kPStages = 4;
+constexpr int kPStages = 3;
 constexpr uint32_t kPTmemCols = 256;    // two buffers x (two accumulators x 64 columns)
 constexpr int kPHead = 128;             // mbarriers, TMEM address (before the 1 KB alignment)
 // the CTA-per-chain step of the overflow phase: 1024 threads x 8 rows each
 constexpr int kPItems = kChainItems;
+constexpr int kDrawWarps = 16;                       // warps 6..21
+constexpr int kEarlyWarp = kGemmWarps + kDrawWarps;  // warps 22.. step chains from the start
+constexpr int kLateThreads = kEarlyWarp * 32;        // warps 0..21: the named barrier
+// warp w's step area is the region's w-th kWarpStepSmem bytes: those of the
+// early warps lie behind the ring
+static_assert((size_t)kEarlyWarp * kWarpStepSmem >= (size_t)kPStages * kPStage,
+              "the early warps' step areas overlap the TMA ring");
 
 // nu of chain c at step t (the batch draw: Philox blocks (seed, j / 4, chain,
 // t, problem), Box-Muller, the two-way fp16 split of nu * 2^12), one warp.
@@ -209,11 +226,45 @@ __device__ void persist_epilogue(const BatchPersistArgs& a, uint64_t* bars, uint
         }
       }
     }
-    // TMEM buffer free for the item after next
+    // TMEM buffer free for the item after next; this warp's rows of the
+    // item's q counted for its problem (each lane's stores fenced first)
     tc_fence_before();
+    __threadfence();
     __syncwarp();
-    if (lane == 0) mbar_arrive(acce_bar(buf));
+    if (lane == 0) {
+      mbar_arrive(acce_bar(buf));
+      atomicAdd(a.dep_done + I.problem, 1u);
+    }
   }
+}
+
+// Bounded wait of a warp until problem p's count reaches target (every q item
+// of the problem stored in this step), then an acquire fence.  False if the
+// wait ran out (time-out status and abort flag set) or another CTA aborted.
+__device__ __forceinline__ bool persist_dep_wait(const BatchPersistArgs& a, int p,
+                                                 unsigned target, int lane) {
+  int ok = 1;
+  if (lane == 0) {
+    const volatile unsigned* f = a.dep_done + p;
+    if (*f < target) {
+      const unsigned long long t0 = grid_now();
+      while (*f < target) {
+        if (persist_aborted(a)) {
+          ok = 0;
+          break;
+        }
+        if (grid_now() - t0 > a.wait_ns) {
+          persist_abort(a);
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncwarp();
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 __device__ __noinline__ void persist_overflow_chain(const ChainParams<float>& p, int c,
@@ -263,33 +314,38 @@ __global__ void __launch_bounds__(kPT, 1) batch_persist_kernel(BatchPersistArgs 
   }
   long long sort_keys = 0;
   const int n = a.prm.n_chains;
-  const int draw_warps = gridDim.x * (kPW - kGemmWarps);
-  const int draw_id = blockIdx.x * (kPW - kGemmWarps) + (warp - kGemmWarps);
+  const int draw_warps = gridDim.x * kDrawWarps;
+  const int draw_id = blockIdx.x * kDrawWarps + (warp - kGemmWarps);
   const uint32_t t_base = a.prm.t_dev ? *a.prm.t_dev : 0u;
+  unsigned char* wsm = region + kWarpStepSmem * warp;
   bool ok = true;
 
   for (int j = 0; j < a.steps && ok; ++j) {
     const int cur = j & 1, nxt = cur ^ 1;
-    // ---- GEMM phase: q of step j; nu of step j + 1 drawn beside it ----------
-    if (warp == 0) {
-      if (lane == 0) persist_produce(a, a.maps[cur], sbase, bars, g);
-    } else if (warp == 1) {
-      if (lane == 0) persist_mma(a, sbase, bars, tmem_d, g);
-    } else if (warp < kGemmWarps) {
-      persist_epilogue(a, bars, tmem_d, warp, lane, g);
-    } else if (j + 1 < a.steps) {
-      const uint32_t tt = a.prm.t + (uint32_t)(j + 1) + t_base;
-      for (int c = draw_id; c < n; c += draw_warps)
-        persist_draw_chain(a.desc[c], a.prm.seed, tt, a.NU[nxt], a.H0[nxt], a.H1[nxt], lane);
-      asm volatile("fence.proxy.async.global;" ::: "memory");  // read by TMA next step
+    if (warp < kEarlyWarp) {
+      // ---- q of step j on the tensor cores; nu of step j + 1 beside it ------
+      if (warp == 0) {
+        if (lane == 0) persist_produce(a, a.maps[cur], sbase, bars, g);
+      } else if (warp == 1) {
+        if (lane == 0) persist_mma(a, sbase, bars, tmem_d, g);
+      } else if (warp < kGemmWarps) {
+        persist_epilogue(a, bars, tmem_d, warp, lane, g);
+      } else if (j + 1 < a.steps) {
+        const uint32_t tt = a.prm.t + (uint32_t)(j + 1) + t_base;
+        for (int c = draw_id; c < n; c += draw_warps)
+          persist_draw_chain(a.desc[c], a.prm.seed, tt, a.NU[nxt], a.H0[nxt], a.H1[nxt], lane);
+        asm volatile("fence.proxy.async.global;" ::: "memory");  // read by TMA next step
+      }
+      __syncwarp();
+      // this CTA's items are done: the ring is idle until the next step and
+      // its shared memory becomes the step areas of warps 0..21
+      tc_fence_before();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"n"(kLateThreads) : "memory");
+      tc_fence_after();
     }
-    tc_fence_before();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    ok = grid_barrier(a.bar, a.abort_flag, a.prm.status, a.wait_ns);
-    if (!ok) break;
-    tc_fence_after();
 
-    // ---- chain phase: the work queue of chains -------------------------------
+    // ---- chain steps from the work queue, each after its problem's q --------
     ChainParams<float> p = a.prm;
     p.t = a.prm.t + (uint32_t)j;
     p.P_in = a.P[cur];
@@ -299,19 +355,23 @@ __global__ void __launch_bounds__(kPT, 1) batch_persist_kernel(BatchPersistArgs 
     p.overflow_list = a.ovf_list;
     p.chain_list = nullptr;
     p.list_count = nullptr;
-    unsigned char* wsm = region + kWarpStepSmem * warp;
     for (;;) {
       int ticket = 0;
       if (lane == 0) ticket = atomicAdd(a.queue + 2 * j, 1);
       ticket = __shfl_sync(0xffffffffu, ticket, 0);
       if (ticket >= n) break;
       const int c = a.order[ticket];
+      const int prob = a.desc[c].problem;
+      const unsigned target = (unsigned)(j + 1) * (unsigned)a.dep_target[prob] + a.hold;
+      if (!persist_dep_wait(a, prob, target, lane)) break;
       const int keys = warp_chain_step<float, true, LONG>(p, c, wsm, lane);
       if (keys > 0) sort_keys += keys;
     }
+    tc_fence_before();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     ok = grid_barrier(a.bar, a.abort_flag, a.prm.status, a.wait_ns);
     if (!ok) break;
+    tc_fence_after();
 
     // ---- overflow phase: chains with too many arcs, one CTA each -------------
     const int n_ovf = *reinterpret_cast<volatile int*>(a.queue + 2 * j + 1);
@@ -381,7 +441,7 @@ bool batch_persist_supported(int max_m, int max_d) {
 cudaError_t launch_batch_persist(const BatchPersistArgs& a, cudaStream_t s) {
   if (a.steps <= 0 || a.prm.n_chains <= 0) return cudaSuccess;
   if ((a.steps & 1) || !a.queue || !a.bar || !a.abort_flag || !a.order || !a.ovf_list ||
-      !a.prm.slack || a.P[0] == a.P[1])
+      !a.dep_target || !a.dep_done || !a.prm.slack || a.P[0] == a.P[1])
     return cudaErrorInvalidValue;
   const size_t smem = persist_smem_bytes();
   const int grid = a.prm.long_arcs ? persist_grid<true>(smem) : persist_grid<false>(smem);

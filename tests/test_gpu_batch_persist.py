@@ -1,8 +1,9 @@
 """Batched problems in one persistent launch per refresh period
 (ess_batch_set_persistent): the cooperative kernel that runs the grouped q
 GEMM on the tensor cores, the draws of the next step, the warp-per-chain steps
-from a device work queue and the overflow chains (CTA per chain), phases joined
-by bounded grid barriers.
+from a device work queue (each after a bounded wait for its problem's q
+items, counted by the GEMM's epilogue) and the overflow chains (CTA per
+chain), steps joined by bounded grid barriers.
 
 It changes how the work of a step is scheduled, not what is computed: the
 chains must equal, bit for bit, those of the graph of per-step launches, which
@@ -134,5 +135,47 @@ def test_persistent_refused_for_fp64():
             ess.ess_batch_set_persistent(bs_.batch, True)
         assert ei.value.status == ess.ESS_ERR_UNSUPPORTED
         ess.ess_batch_set_persistent(bs_.batch, False)  # switching off is always allowed
+    finally:
+        bs_.close()
+
+
+def test_dependency_wait_runs_out_and_the_batch_stays_usable():
+    """A q dependency that nothing releases (ess_batch_selftest_wait raises
+    every problem's target by one count): each chain step's wait gives up
+    after the configured limit, the call returns ESS_ERR_TIMEOUT without a
+    hang or a fault, and the same batch then runs periods equal to those of
+    the per-step graph."""
+    import time
+
+    As, bs, Xs, nc = make_batch(9, with_cone=False)
+    bs_ = ess.BatchSampler(As, bs, precision=ess.ESS_PREC_MIXED, refresh_k=4,
+                           wait_limit_us=20000)
+    try:
+        ess.ess_batch_set_persistent(bs_.batch, True)
+        X = bs_.pack(Xs)
+        t0 = time.perf_counter()
+        with pytest.raises(ess.EssError) as e:
+            ess.ess_batch_selftest_wait(bs_.batch, nc, X)
+        assert e.value.status == ess.ESS_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 10.0
+        X = bs_.pack(Xs)
+        before = ess.ess_batch_info(bs_.batch)["graph_launches"]
+        bs_.run(nc, X, 10, seed=11, t0=2)
+        got = host(X)
+        assert ess.ess_batch_info(bs_.batch)["graph_launches"] - before == 2
+    finally:
+        bs_.close()
+    want, _, _ = run_batch(As, bs, Xs, nc, False, 10, t0=2)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_selftest_refused_without_the_persistent_launch():
+    As, bs, Xs, nc = make_batch(1, with_cone=False)
+    bs_ = ess.BatchSampler(As, bs, precision=ess.ESS_PREC_MIXED, refresh_k=4)
+    try:
+        ess.ess_batch_set_persistent(bs_.batch, False)
+        with pytest.raises(ess.EssError) as ei:
+            ess.ess_batch_selftest_wait(bs_.batch, nc, bs_.pack(Xs))
+        assert ei.value.status == ess.ESS_ERR_UNSUPPORTED
     finally:
         bs_.close()
