@@ -135,6 +135,44 @@ def grid_instance(rng, d, m, n_chains, scale=1.0, slack=(0.0, 1.0), x_scale=0.3)
     return A, b, X, NU
 
 
+def long_arc_instance(rng, d, n_chains, kind, extra_rows=0, grid=False):
+    """A polytope with rows of b_i <= 0, whose infeasible arcs are at least a
+    half circle long (Sec. 3.1): the probit-style orthant {x : -sign(f_i)
+    (L x)_i <= 0} around z, with f = L z and L = chol(M M^T / d + I)
+    ("orthant": b = 0, no arc inside another); the same with b_i in
+    [0.05, 0.5] on every other row ("half"); b_i = -|f_i| / 2 < 0 on every
+    other row and b_i in [0.05, 0.5] on the rest ("negative").  extra_rows
+    random rows with b = a.z + U[0.1, 1] follow.  Every chain starts at z,
+    strictly inside.  grid: A, z and NU on the grids of grid_instance (exact
+    mixed-form products); b is any double.  Returns A, b, X, NU."""
+    B = grid_bits(d)
+    M = rng.standard_normal((d, d))
+    L = np.linalg.cholesky(M @ M.T / d + np.eye(d))
+    z = rng.standard_normal(d)
+    if grid:
+        L, z = to_grid(L, B), to_grid(z, B)
+    f = L @ z
+    assert np.all(f != 0.0)
+    A = -np.sign(f)[:, None] * L
+    b = np.zeros(d)
+    if kind in ("half", "negative"):
+        b[1::2] = rng.uniform(0.05, 0.5, size=d // 2)
+    if kind == "negative":
+        b[0::2] = -0.5 * np.abs(f[0::2])
+    if extra_rows:
+        E = rng.standard_normal((extra_rows, d)) / math.sqrt(d)
+        if grid:
+            E = to_grid(E, B)
+        A = np.vstack([A, E])
+        b = np.concatenate([b, E @ z + rng.uniform(0.1, 1.0, size=extra_rows)])
+    X = np.tile(z, (n_chains, 1))
+    NU = rng.standard_normal((n_chains, d))
+    if grid:
+        NU = to_grid(NU, B)
+    assert np.all(X @ A.T - b[None, :] < 0.0)
+    return A, b, X, NU
+
+
 # Error of the FP32 root arithmetic of the mixed form (atan2f 3 ulp, acosf 2
 # ulp, the 2 pi shift and the subtraction tau - h, each at most 2^-21 rad per
 # ulp for angles below 2 pi), and of the float rounding of an FP64 root.

@@ -16,7 +16,7 @@ import oracle
 import paper_2407_10449_gb300 as ess
 import workloads
 from gpu_helpers import dev, host, oracle_steps, feasible_instance, fp16x3_bound, grid_instance, \
-    mixed_endpoint_bounds, mixed_exempt
+    long_arc_instance, mixed_endpoint_bounds, mixed_exempt
 
 pytestmark = pytest.mark.gpu
 
@@ -157,6 +157,84 @@ def test_batch_mixed_step_with_draws():
     for p, (A, b, X, NU) in enumerate(zip(As, bs, Xs, NUs)):
         if X.shape[0]:
             assert np.max(Xn[p] @ A.T - b) <= 0.0, p
+        ref = oracle_steps(A, b, X, NU, U[at:at + X.shape[0]])
+        amp, arith = mixed_endpoint_bounds(A, b, X, NU)
+        exempt = mixed_exempt(ref, amp, arith, 0.5e-5)
+        for c, r in enumerate(ref):
+            total += 1
+            if exempt[c]:
+                exempt_total += 1
+                continue
+            assert abs(th[at + c] - r.theta) <= 1e-5, (p, c, th[at + c], r.theta)
+            if rej[at + c]:
+                np.testing.assert_array_equal(Xn[p][c], X[c])
+            else:
+                scale = (1.0 + np.abs(r.x_next)) * (1.0 + np.abs(NU[c]))
+                assert np.all(np.abs(Xn[p][c] - r.x_next) <= 1e-5 * scale), (p, c)
+        at += X.shape[0]
+    assert exempt_total <= 0.05 * total, (exempt_total, total)
+
+
+# problems with rows of b_i <= 0 (kind, d, extra rows, chains), beside one without
+LONG_SPECS = [("orthant", 32, 0, 12), ("half", 48, 0, 9), ("negative", 40, 40, 10)]
+
+
+def make_long_batch(seed, grid=False):
+    rng = np.random.default_rng(seed)
+    if grid:
+        A, b, X, NU = grid_instance(rng, 10, 20, 16, scale=1.0 / math.sqrt(10), slack=(0.1, 1.0))
+    else:
+        A, b, X = feasible_instance(rng, 10, 20, 16, scale=1.0 / math.sqrt(10), slack=(0.1, 1.0))
+        NU = rng.standard_normal(X.shape)
+    As, bs, Xs, NUs = [A], [b], [X], [NU]
+    for kind, d, extra, n in LONG_SPECS:
+        A, b, X, NU = long_arc_instance(rng, d, n, kind, extra_rows=extra, grid=grid)
+        As.append(A)
+        bs.append(b)
+        Xs.append(X)
+        NUs.append(NU)
+    return As, bs, Xs, NUs, [X.shape[0] for X in Xs]
+
+
+def test_batch_long_arcs_fp64_run_reproduces_oracle():
+    """Problems whose rows with b_i <= 0 give arcs of at least a half circle
+    (an orthant, one with short arcs between, one with b_i < 0 and extra
+    rows) batched with an ordinary polytope: 20 steps with refresh_k = 8, every
+    chain equal to the oracle's (the batch kernels drop the arcs inside the
+    union of the long arcs, which leaves I_act as it is)."""
+    As, bs, Xs, _, nc = make_long_batch(21)
+    bs_ = ess.BatchSampler(As, bs, precision=ess.ESS_PREC_FP64, refresh_k=8)
+    try:
+        X = bs_.pack(Xs)
+        bs_.run(nc, X, 20, seed=4)
+        got = bs_.unpack(X, nc)
+        st = bs_.stats()
+    finally:
+        bs_.close()
+    for p, (A, b, X0) in enumerate(zip(As, bs, Xs)):
+        want, _, _ = oracle.run(A, b, X0, 20, seed=4, problem=p)
+        np.testing.assert_allclose(got[p], want, rtol=0, atol=1e-8, err_msg=f"problem {p}")
+    assert st["numeric_errors"] == 0
+
+
+def test_batch_long_arcs_mixed_step_with_draws():
+    """The same problems in the mixed form on grid inputs, one step with given
+    draws: theta within 1e-5 rad and x' within 1e-5 relative of the oracle's
+    for every chain not exempted by the a-priori bound of its arc endpoints;
+    no infeasible iterate."""
+    As, bs, Xs, NUs, nc = make_long_batch(22, grid=True)
+    rng = np.random.default_rng(23)
+    U = rng.uniform(size=sum(nc))
+    bs_ = ess.BatchSampler(As, bs, precision=ess.ESS_PREC_MIXED)
+    try:
+        Xn, th, rej = bs_.step_with_draws(nc, bs_.pack(Xs), bs_.pack(NUs), dev(U))
+        Xn = bs_.unpack(Xn, nc)
+        th, rej = host(th), host(rej)
+    finally:
+        bs_.close()
+    at, exempt_total, total = 0, 0, 0
+    for p, (A, b, X, NU) in enumerate(zip(As, bs, Xs, NUs)):
+        assert np.max(Xn[p] @ A.T - b) <= 0.0, p
         ref = oracle_steps(A, b, X, NU, U[at:at + X.shape[0]])
         amp, arith = mixed_endpoint_bounds(A, b, X, NU)
         exempt = mixed_exempt(ref, amp, arith, 0.5e-5)

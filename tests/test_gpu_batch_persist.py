@@ -20,7 +20,7 @@ import numpy as np
 import pytest
 
 import paper_2407_10449_gb300 as ess
-from gpu_helpers import feasible_instance, host
+from gpu_helpers import feasible_instance, host, long_arc_instance
 
 pytestmark = pytest.mark.gpu
 
@@ -89,6 +89,27 @@ def test_persistent_periods_equal_graph_of_launches():
     # buckets where the per-step CTA kernel (64 threads at m = 400) has 512,
     # so only its size is checked: the near-conic chains keep > 128 arcs each step
     assert st_p["sort_keys"] > 14 * 12 * 128 and st_g["sort_keys"] > 14 * 12 * 128
+
+
+def test_persistent_long_arcs_equal_graph_of_launches():
+    """Problems with rows of b_i <= 0 (arcs of at least a half circle, reduced
+    to their union: the kernels' long-arc instantiations) batched with the
+    ordinary ones: persistent launch and per-step graph give the same bits."""
+    rng = np.random.default_rng(17)
+    As, bs, Xs, nc = make_batch(19, with_cone=False)
+    for kind, d, extra, n in (("orthant", 32, 0, 12), ("half", 48, 0, 9),
+                              ("negative", 40, 40, 10)):
+        A, b, X, _ = long_arc_instance(rng, d, n, kind, extra_rows=extra)
+        As.append(A)
+        bs.append(b)
+        Xs.append(X)
+        nc.append(n)
+    got, st_p, _ = run_batch(As, bs, Xs, nc, True, 14, t0=2)
+    want, st_g, _ = run_batch(As, bs, Xs, nc, False, 14, t0=2)
+    np.testing.assert_array_equal(got, want)
+    for key in ("steps", "rejections", "residual_rechecks", "tangent_fp64", "numeric_errors"):
+        assert st_p[key] == st_g[key], key
+    assert st_p["numeric_errors"] == 0
 
 
 def test_persistent_repeated_calls_and_layout_change():
