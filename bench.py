@@ -111,6 +111,9 @@ def run_case(name):
             out["persistent" if persistent else "graphs"] = {
                 "ms_per_step": r["ms_per_step"], "value": r["value"],
                 "graph_launches": r["graph_launches"], "stats": r["stats"]}
+    elif name == "paper_hd":
+        # the Sec. 4.2 family with 1 and 10 chains through ess_run_few
+        out = time_paper_hd(ess, torch, workloads, load_peaks(), 0)
     elif name == "hdr_box":
         inst = workloads.rotated_box()
         s = ess.Sampler(inst.A, inst.b, precision=ess.ESS_PREC_MIXED)
@@ -123,7 +126,7 @@ def run_case(name):
     return 0
 
 
-CASES = ("wide_metric", "wide_probit", "hdr_box", "batched", "probit")
+CASES = ("wide_metric", "wide_probit", "hdr_box", "batched", "probit", "paper_hd")
 
 
 def load_peaks():

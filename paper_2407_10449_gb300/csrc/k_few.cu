@@ -46,6 +46,9 @@ constexpr int kFT = 512;            // threads per CTA
 constexpr int kFW = kFT / 32;       // warps per CTA
 constexpr int kFB = kFewBuckets;    // angle buckets per chain
 constexpr double kFewW = kTwoPi / kFB;  // their width
+constexpr int kDW = 4;              // phase D: warps of the FP64 sweep
+constexpr int kDT = kDW * 32;
+constexpr int kFSlots = 256;        // phase B: (row, chain) pairs of a round (RW kFW CM)
 
 // x cos + nu sin with one explicit rounding order (the FP64 recheck of a row
 // evaluates exactly the x' that is written).
@@ -118,6 +121,10 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
       const int chunk = a.chunk;
       double* nu_s = sd;                          // C x chunk
       double* x_s = sd + (size_t)C * chunk;       // C x chunk (refresh)
+      // a round's (row, chain) pairs for the roots: slot (h kFW + warp) CM + c
+      __shared__ double s_rp[kFSlots], s_rq[kFSlots];
+      __shared__ int s_ri[kFSlots];  // the row, or -1
+      static_assert(RW * kFW * CM <= kFSlots, "root slots of a round");
       // each warp: RW rows of this CTA per round, all chains
       for (int base = r0; base < r1; base += RW * kFW) {
         double qs[RW][CM], ps[RW][CM];
@@ -184,6 +191,8 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
 #pragma unroll
           for (int h = 0; h < RW; ++h) {
             const int i = base + h * kFW + warp;
+            const int slot = (h * kFW + warp) * CM + c;
+            s_ri[slot] = i < r1 ? i : -1;
             if (i >= r1) continue;
             double* Pc = a.P[xbc] + (size_t)c * m;
             double p;
@@ -197,21 +206,31 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
             const double q = myq[h];
             a.Q[(size_t)c * m + i] = q;
             if (!(isfinite(p) && isfinite(q))) a.bad[c] = 1;
-            double al, be;
-            bool inf_row = false;
-            if (roots_dp(p, q, a.b[i], al, be, inf_row)) {
-              const int j = min(kFB - 1, (int)(al * (1.0 / kFewW)));
-              if (be >= (j + 1) * kFewW) {
-                atomicMin(&a.bmin[(size_t)c * kFB + j], (unsigned long long)__double_as_longlong(al));
-                atomicMax(&a.bmax[(size_t)c * kFB + j], (unsigned long long)__double_as_longlong(be));
-              } else {
-                const int at = atomicAdd(&a.nshort[c], 1);
-                a.shorts[((size_t)c * m + at) * 2] = al;
-                a.shorts[((size_t)c * m + at) * 2 + 1] = be;
-              }
-            }
-            if (inf_row) atomicOr(a.status, kStatusInfeasible);
+            s_rp[slot] = p;
+            s_rq[slot] = q;
           }
+        }
+        __syncthreads();
+        // the exact roots of the round's (row, chain) pairs, 32 to a warp: an
+        // FP64 instruction costs the SM the same with one lane as with 32
+        for (int slot = tid; slot < RW * kFW * CM; slot += kFT) {
+          const int c = slot % CM;
+          const int i = c < C ? s_ri[slot] : -1;
+          if (i < 0) continue;
+          double al, be;
+          bool inf_row = false;
+          if (roots_dp(s_rp[slot], s_rq[slot], a.b[i], al, be, inf_row)) {
+            const int j = min(kFB - 1, (int)(al * (1.0 / kFewW)));
+            if (be >= (j + 1) * kFewW) {
+              atomicMin(&a.bmin[(size_t)c * kFB + j], (unsigned long long)__double_as_longlong(al));
+              atomicMax(&a.bmax[(size_t)c * kFB + j], (unsigned long long)__double_as_longlong(be));
+            } else {
+              const int at = atomicAdd(&a.nshort[c], 1);
+              a.shorts[((size_t)c * m + at) * 2] = al;
+              a.shorts[((size_t)c * m + at) * 2 + 1] = be;
+            }
+          }
+          if (inf_row) atomicOr(a.status, kStatusInfeasible);
         }
       }
     }
@@ -287,54 +306,66 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
       }
       __syncthreads();
       if (tid == 0) a.nshort[c] = 0;
-      // segments of E consecutive arcs per thread
-      const int E = (n + kFT - 1) / kFT;
-      const int lo = min(n, tid * E), hi = min(n, lo + E);
-      double mloc = 0.0;
-      for (int k = lo; k < hi; ++k) mloc = fmax(mloc, val[k]);
-      // exclusive max scan of mloc over the threads (gamma before the segment)
-      double incl = warp_incl_max<double>(mloc, lane);
-      if (lane == 31) s_red[warp] = incl;
-      double before = __shfl_up_sync(kFull, incl, 1);
-      if (lane == 0) before = 0.0;
-      __syncthreads();
-      for (int w = 0; w < warp; ++w) before = fmax(before, s_red[w]);
-      double gall = 0.0;
-      for (int w = 0; w < kFW; ++w) gall = fmax(gall, s_red[w]);
+      // Alg. 3 over the n merged arcs by the first kDW warps only: an FP64
+      // instruction costs the SM the same with any number of lanes, so the
+      // sweep runs on few warps with longer segments (E consecutive arcs per
+      // thread) while the others wait at the block barriers
+      const bool dw = warp < kDW;
+      const int E = (n + kDT - 1) / kDT;
+      const int lo = dw ? min(n, tid * E) : n, hi = dw ? min(n, lo + E) : n;
       const double eps = a.trim_eps;
-      double g = before, sloc = 0.0;
-      for (int k = lo; k < hi; ++k) {
-        const double plo = k == 0 ? 0.0 : g + eps, phi = key[k] - eps;
-        sloc += phi > plo ? phi - plo : 0.0;
-        g = fmax(g, val[k]);
+      double before = 0.0, gall = 0.0, sloc = 0.0, soff = 0.0, mid = 0.0;
+      if (dw) {
+        double mloc = 0.0;
+        for (int k = lo; k < hi; ++k) mloc = fmax(mloc, val[k]);
+        // exclusive max scan of mloc over the threads (gamma before the segment)
+        const double incl = warp_incl_max<double>(mloc, lane);
+        if (lane == 31) s_red[warp] = incl;
+        before = __shfl_up_sync(kFull, incl, 1);
+        if (lane == 0) before = 0.0;
       }
       __syncthreads();
-      double sincl = warp_incl_sum<double>(sloc, lane);
-      if (lane == 31) s_red[warp] = sincl;
-      double soff = __shfl_up_sync(kFull, sincl, 1);
-      if (lane == 0) soff = 0.0;
-      __syncthreads();
-      double mid = 0.0;
-      for (int w = 0; w < kFW; ++w) {
-        if (w < warp) soff += s_red[w];
-        mid += s_red[w];
+      if (dw) {
+        for (int w = 0; w < warp; ++w) before = fmax(before, s_red[w]);
+        for (int w = 0; w < kDW; ++w) gall = fmax(gall, s_red[w]);
+        double g = before;
+        for (int k = lo; k < hi; ++k) {
+          const double plo = k == 0 ? 0.0 : g + eps, phi = key[k] - eps;
+          sloc += phi > plo ? phi - plo : 0.0;
+          g = fmax(g, val[k]);
+        }
       }
-      const double tail_lo = n > 0 ? gall + eps : 0.0;
-      const double tail_len = kTwoPi > tail_lo ? kTwoPi - tail_lo : 0.0;
-      const double total = mid + tail_len;
-      const double u = theta_uniform(a.seed, (uint32_t)c, (uint32_t)t, 0u);
-      const double s = u * total;
-      if (tid == 0) {
-        s_best = -1;
-        s_theta = 0.0;
-        s_mid = mid;
-        s_tail_lo = tail_lo;
-        s_total = total;
+      __syncthreads();
+      if (dw) {
+        const double sincl = warp_incl_sum<double>(sloc, lane);
+        if (lane == 31) s_red[warp] = sincl;
+        soff = __shfl_up_sync(kFull, sincl, 1);
+        if (lane == 0) soff = 0.0;
+      }
+      __syncthreads();
+      double s = 0.0, tail_len = 0.0;
+      if (dw) {
+        for (int w = 0; w < kDW; ++w) {
+          if (w < warp) soff += s_red[w];
+          mid += s_red[w];
+        }
+        const double tail_lo = n > 0 ? gall + eps : 0.0;
+        tail_len = kTwoPi > tail_lo ? kTwoPi - tail_lo : 0.0;
+        const double total = mid + tail_len;
+        const double u = theta_uniform(a.seed, (uint32_t)c, (uint32_t)t, 0u);
+        s = u * total;
+        if (tid == 0) {
+          s_best = -1;
+          s_theta = 0.0;
+          s_mid = mid;
+          s_tail_lo = tail_lo;
+          s_total = total;
+        }
       }
       __syncthreads();
       // the last positive piece starting at or below s (the tail is the last)
-      int cand = -1;
-      {
+      if (dw) {
+        int cand = -1;
         double gg = before, cum = soff;
         for (int k = lo; k < hi; ++k) {
           const double plo = k == 0 ? 0.0 : gg + eps, phi = key[k] - eps;
@@ -343,12 +374,12 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
           cum += len;
           gg = fmax(gg, val[k]);
         }
+        if (tid == 0 && tail_len > 0.0 && mid <= s) cand = max(cand, n);
+        if (cand >= 0) atomicMax(&s_best, cand);
       }
-      if (tid == 0 && tail_len > 0.0 && mid <= s) cand = max(cand, n);
-      if (cand >= 0) atomicMax(&s_best, cand);
       __syncthreads();
       const int best = s_best;
-      if (best >= 0 && best < n && best >= lo && best < hi) {
+      if (dw && best >= 0 && best < n && best >= lo && best < hi) {
         double gg = before, cum = soff;
         for (int k = lo; k <= best; ++k) {
           const double plo = k == 0 ? 0.0 : gg + eps, phi = key[k] - eps;
