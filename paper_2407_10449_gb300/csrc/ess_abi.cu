@@ -149,10 +149,10 @@ struct ess_state {
   double* few_nu = nullptr;   // 2 x kMaxFew x d
   double* few_p = nullptr;    // 2 x kMaxFew x m
   double* few_q = nullptr;    // kMaxFew x m
-  double* few_short = nullptr; // kMaxFew x m x 2
+  double* few_short = nullptr; // 2 parities x kMaxFew x m x 2
   double* few_th = nullptr;   // 3 x kMaxFew: theta, cos, sin
-  unsigned long long* few_bkt = nullptr;  // 2 x kMaxFew x kFewBuckets: min alpha, max beta
-  int* few_int = nullptr;     // 7 x kMaxFew: rej[2], cur[2], nshort, bad, bad_prev
+  unsigned long long* few_bkt = nullptr;  // 2 parities x (min alpha, max beta) x kMaxFew x kFewBuckets
+  int* few_int = nullptr;     // 9 x kMaxFew: rej[2], cur[2], nshort[2], bad[2], bad_prev
   unsigned* few_bar = nullptr;   // barrier (2) and abort flag (1)
 };
 
@@ -1280,14 +1280,14 @@ ess_status run_few_impl(ess_state* s, double* X, int n_chains, int t0, int n_ite
     ESS_CUDA(dev_alloc(&s->few_nu, (size_t)2 * F * d));
     ESS_CUDA(dev_alloc(&s->few_p, (size_t)2 * F * m));
     ESS_CUDA(dev_alloc(&s->few_q, (size_t)F * m));
-    ESS_CUDA(dev_alloc(&s->few_short, (size_t)2 * F * m));
+    ESS_CUDA(dev_alloc(&s->few_short, (size_t)4 * F * m));
     ESS_CUDA(dev_alloc(&s->few_th, (size_t)3 * F));
-    ESS_CUDA(dev_alloc(&s->few_bkt, (size_t)2 * F * ess::kFewBuckets));
-    ESS_CUDA(dev_alloc(&s->few_int, (size_t)7 * F));
+    ESS_CUDA(dev_alloc(&s->few_bkt, (size_t)4 * F * ess::kFewBuckets));
+    ESS_CUDA(dev_alloc(&s->few_int, (size_t)9 * F));
     ESS_CUDA(dev_alloc(&s->few_bar, (size_t)4));
   }
   // rej[(t0 - 1) & 1] = 1 and cur = 0: step t0 starts from buffer 0
-  int init[7 * ess::kMaxFew] = {0};
+  int init[9 * ess::kMaxFew] = {0};
   for (int c = 0; c < F; ++c) init[((t0 + 1) & 1) * F + c] = 1;
   ESS_CUDA(cudaMemcpyAsync(s->few_int, init, sizeof(init), cudaMemcpyHostToDevice, st));
   ESS_CUDA(cudaMemsetAsync(s->few_bar, 0, sizeof(unsigned) * 4, st));
@@ -1309,12 +1309,14 @@ ess_status run_few_impl(ess_state* s, double* X, int n_chains, int t0, int n_ite
     a.cur[k] = s->few_int + (size_t)(2 + k) * F;
   }
   a.Q = s->few_q;
-  a.bmin = s->few_bkt;
-  a.bmax = s->few_bkt + (size_t)F * ess::kFewBuckets;
-  a.shorts = s->few_short;
-  a.nshort = s->few_int + (size_t)4 * F;
-  a.bad = s->few_int + (size_t)5 * F;
-  a.bad_prev = s->few_int + (size_t)6 * F;
+  for (int k = 0; k < 2; ++k) {
+    a.bmin[k] = s->few_bkt + (size_t)(2 * k) * F * ess::kFewBuckets;
+    a.bmax[k] = s->few_bkt + (size_t)(2 * k + 1) * F * ess::kFewBuckets;
+    a.shorts[k] = s->few_short + (size_t)k * 2 * F * m;
+    a.nshort[k] = s->few_int + (size_t)(4 + k) * F;
+    a.bad[k] = s->few_int + (size_t)(6 + k) * F;
+  }
+  a.bad_prev = s->few_int + (size_t)8 * F;
   a.theta = s->few_th;
   a.cth = s->few_th + F;
   a.sth = s->few_th + 2 * F;

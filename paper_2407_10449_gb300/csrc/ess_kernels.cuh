@@ -286,16 +286,19 @@ struct FewArgs {
   double* P[2];
   double* Q;
   double* NU[2];
-  unsigned long long* bmin;
-  unsigned long long* bmax;
-  double* shorts;
-  int* nshort;
+  // arcs merged per bucket, short arcs and non-finite flags, one set per step
+  // parity (phase D of step t reads the set that phase B of step t wrote;
+  // step t + 1 clears it)
+  unsigned long long* bmin[2];
+  unsigned long long* bmax[2];
+  double* shorts[2];
+  int* nshort[2];
   double* theta;
   double* cth;
   double* sth;
   int* rej[2];
   int* cur[2];
-  int* bad;
+  int* bad[2];
   int* bad_prev;
   unsigned* bar;
   int* abort_flag;

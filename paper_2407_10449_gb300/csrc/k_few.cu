@@ -18,7 +18,10 @@
 //      the short arcs, sorted with them by a bitonic sort when there are any),
 //      runs Alg. 3 (cumulative max of beta, piece lengths, prefix sums) and
 //      draws theta by the inverse CDF.  The union of the arcs, hence I_act, is
-//      that of the arcs themselves.
+//      that of the arcs themselves.  With one chain every CTA runs D for it
+//      (the same data and code give the same theta everywhere), so E needs no
+//      grid barrier after D.  Buckets, short lists and flags come in two sets
+//      by step parity: step t + 1 clears the set step t read.
 //   E  x' = x cos + nu sin and p' = p cos + q sin into the other buffer of
 //      each chain; rows with p' above b - margin ||a|| get their residual
 //      recomputed in FP64 (Sec. 3.3: a positive one rejects the move); nu of
@@ -62,6 +65,7 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
   constexpr int RW = CM <= 4 ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* sd = reinterpret_cast<double*>(smem_raw);
+  __shared__ double s_cs[kMaxFew], s_sn[kMaxFew];  // cos, sin of each chain's theta
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int C = a.C, d = a.d, m = a.m;
   const int G = gridDim.x;
@@ -75,8 +79,8 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
 
   // ---- start: x0 into buffer 0, nu of the first step, per-step state cleared --
   for (long long k = gtid; k < (long long)C * kFB; k += gthreads) {
-    a.bmin[k] = kEmptyBucket;
-    a.bmax[k] = 0ull;
+    a.bmin[0][k] = a.bmin[1][k] = kEmptyBucket;
+    a.bmax[0][k] = a.bmax[1][k] = 0ull;
   }
   for (long long k = gtid; k < (long long)C * d; k += gthreads) {
     const int c = (int)(k / d), j = (int)(k % d);
@@ -113,6 +117,17 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
         const int c = (int)(k / d), j = (int)(k % d);
         a.samples[((size_t)c * a.n_rec + rec) * d + j] = a.X[xbuf(c)][(size_t)c * d + j];
       }
+    }
+
+    // the other parity's arcs, short lists and flags were read in D of the
+    // previous step, which every CTA has finished: cleared for the next step
+    for (long long k = gtid; k < (long long)C * kFB; k += gthreads) {
+      a.bmin[par ^ 1][k] = kEmptyBucket;
+      a.bmax[par ^ 1][k] = 0ull;
+    }
+    if (gtid < C) {
+      a.nshort[par ^ 1][gtid] = 0;
+      a.bad[par ^ 1][gtid] = 0;
     }
 
     // ---- B: q = A nu (p = A x on refresh steps), float classification ----------
@@ -205,7 +220,7 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
             }
             const double q = myq[h];
             a.Q[(size_t)c * m + i] = q;
-            if (!(isfinite(p) && isfinite(q))) a.bad[c] = 1;
+            if (!(isfinite(p) && isfinite(q))) a.bad[par][c] = 1;
             s_rp[slot] = p;
             s_rq[slot] = q;
           }
@@ -222,12 +237,14 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
           if (roots_dp(s_rp[slot], s_rq[slot], a.b[i], al, be, inf_row)) {
             const int j = min(kFB - 1, (int)(al * (1.0 / kFewW)));
             if (be >= (j + 1) * kFewW) {
-              atomicMin(&a.bmin[(size_t)c * kFB + j], (unsigned long long)__double_as_longlong(al));
-              atomicMax(&a.bmax[(size_t)c * kFB + j], (unsigned long long)__double_as_longlong(be));
+              atomicMin(&a.bmin[par][(size_t)c * kFB + j],
+                        (unsigned long long)__double_as_longlong(al));
+              atomicMax(&a.bmax[par][(size_t)c * kFB + j],
+                        (unsigned long long)__double_as_longlong(be));
             } else {
-              const int at = atomicAdd(&a.nshort[c], 1);
-              a.shorts[((size_t)c * m + at) * 2] = al;
-              a.shorts[((size_t)c * m + at) * 2 + 1] = be;
+              const int at = atomicAdd(&a.nshort[par][c], 1);
+              a.shorts[par][((size_t)c * m + at) * 2] = al;
+              a.shorts[par][((size_t)c * m + at) * 2 + 1] = be;
             }
           }
           if (inf_row) atomicOr(a.status, kStatusInfeasible);
@@ -238,12 +255,15 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
     if (t == a.t0 && (*reinterpret_cast<volatile int*>(a.status) & kStatusInfeasible)) return;
 
     // ---- D: one CTA per chain: sort the arcs, Alg. 3 sweep, theta ----------------
-    for (int c = blockIdx.x; c < C; c += G) {
+    // with one chain every CTA runs D itself (the same theta everywhere), so
+    // E follows without a grid barrier; otherwise CTA c takes chain c
+    const bool d_all = C == 1;
+    for (int c = d_all ? 0 : blockIdx.x; c < C; c += d_all ? 1 : G) {
       __shared__ int s_part[kFW];
       // the non-empty buckets, in ascending order, as merged arcs
-      const int ns = a.nshort[c];
-      unsigned long long* bmin = a.bmin + (size_t)c * kFB;
-      unsigned long long* bmax = a.bmax + (size_t)c * kFB;
+      const int ns = a.nshort[par][c];
+      const unsigned long long* bmin = a.bmin[par] + (size_t)c * kFB;
+      const unsigned long long* bmax = a.bmax[par] + (size_t)c * kFB;
       constexpr int kPer = kFB / kFT;  // buckets per thread
       static_assert(kFB % kFT == 0, "whole buckets per thread");
       unsigned long long lo_b[kPer], hi_b[kPer];
@@ -253,8 +273,6 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
         lo_b[k] = bmin[tid * kPer + k];
         hi_b[k] = bmax[tid * kPer + k];
         cnt += lo_b[k] != kEmptyBucket ? 1 : 0;
-        bmin[tid * kPer + k] = kEmptyBucket;   // cleared for the next step
-        bmax[tid * kPer + k] = 0ull;
       }
       const int incl_c = warp_incl_sum<int>(cnt, lane);
       if (lane == 31) s_part[warp] = incl_c;
@@ -284,8 +302,8 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
       if (ns > 0) {
         // the short arcs join the list; then one bitonic sort of all of them
         for (int k = tid; k < N - nb; k += kFT) {
-          key[nb + k] = k < ns ? a.shorts[((size_t)c * m + k) * 2] : INFINITY;
-          val[nb + k] = k < ns ? a.shorts[((size_t)c * m + k) * 2 + 1] : 0.0;
+          key[nb + k] = k < ns ? a.shorts[par][((size_t)c * m + k) * 2] : INFINITY;
+          val[nb + k] = k < ns ? a.shorts[par][((size_t)c * m + k) * 2 + 1] : 0.0;
         }
         __syncthreads();
         for (int kk = 2; kk <= N; kk <<= 1) {
@@ -305,7 +323,6 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
         }
       }
       __syncthreads();
-      if (tid == 0) a.nshort[c] = 0;
       // Alg. 3 over the n merged arcs by the first kDW warps only: an FP64
       // instruction costs the SM the same with any number of lanes, so the
       // sweep runs on few warps with longer segments (E consecutive arcs per
@@ -399,34 +416,41 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
       __syncthreads();
       if (tid == 0) {
         double theta = (best < 0 || !(s_total > 0.0)) ? 0.0 : s_theta;
-        const bool bad = a.bad[c] != 0 || !isfinite(theta);
-        if (bad) {
-          theta = 0.0;
-          a.rej[par][c] = 1;
-          atomicAdd(&a.stats->numeric_errors, 1ull);
-          atomicOr(a.status, kStatusNumeric);
-        }
-        a.bad_prev[c] = bad ? 1 : 0;
-        a.bad[c] = 0;
+        const bool bad = a.bad[par][c] != 0 || !isfinite(theta);
+        if (bad) theta = 0.0;
         double sn, cs;
         sincos(theta, &sn, &cs);
-        a.theta[c] = theta;
-        a.cth[c] = cs;
-        a.sth[c] = sn;
-        sort_keys += n;
+        s_cs[c] = cs;
+        s_sn[c] = sn;
+        // the outputs: written once (by CTA 0 when every CTA runs D)
+        if (!d_all || blockIdx.x == 0) {
+          if (bad) {
+            a.rej[par][c] = 1;
+            atomicAdd(&a.stats->numeric_errors, 1ull);
+            atomicOr(a.status, kStatusNumeric);
+          }
+          a.bad_prev[c] = bad ? 1 : 0;
+          a.theta[c] = theta;
+          a.cth[c] = cs;
+          a.sth[c] = sn;
+          sort_keys += n;
+        }
       }
       __syncthreads();
     }
-    if (!grid_barrier(a.bar, a.abort_flag, a.status, a.wait_ns)) return;
+    if (!d_all && !grid_barrier(a.bar, a.abort_flag, a.status, a.wait_ns)) return;
 
     // ---- E: move, FP64 recheck, nu of the next step, per-step state cleared ------
     {
       const double* NU = a.NU[par];
+      // cos and sin of each chain's theta: this CTA's own (d_all) or chain c's CTA's
+      auto cth = [&](int c) { return d_all ? s_cs[c] : a.cth[c]; };
+      auto sth = [&](int c) { return d_all ? s_sn[c] : a.sth[c]; };
       for (long long k = gtid; k < (long long)C * d; k += gthreads) {
         const int c = (int)(k / d), j = (int)(k % d);
         const size_t o = (size_t)c * d + j;
         const int xbc = xbuf(c);
-        a.X[xbc ^ 1][o] = move_d(a.X[xbc][o], NU[o], a.cth[c], a.sth[c]);
+        a.X[xbc ^ 1][o] = move_d(a.X[xbc][o], NU[o], cth(c), sth(c));
       }
       for (int i = gwarp; i < m; i += gwarps) {
         const double slack = a.b[i] - a.margin * a.anorm[i];
@@ -434,8 +458,8 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
         if (lane < C) {
           const int c = lane;
           const int xbc = xbuf(c);
-          const double pn = fma(a.P[xbc][(size_t)c * m + i], a.cth[c],
-                                a.Q[(size_t)c * m + i] * a.sth[c]);
+          const double pn = fma(a.P[xbc][(size_t)c * m + i], cth(c),
+                                a.Q[(size_t)c * m + i] * sth(c));
           a.P[xbc ^ 1][(size_t)c * m + i] = pn;
           flag = !(pn <= slack);
         }
@@ -446,7 +470,7 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
           const double* arow = a.A + (size_t)i * d;
           const double* xr = a.X[xbuf(c)] + (size_t)c * d;
           const double* vr = NU + (size_t)c * d;
-          const double cs = a.cth[c], sn = a.sth[c];
+          const double cs = cth(c), sn = sth(c);
           double acc = 0.0;
           for (int j = lane; j < d; j += 32) acc = fma(arow[j], move_d(xr[j], vr[j], cs, sn), acc);
 #pragma unroll
