@@ -71,7 +71,12 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
   const int G = gridDim.x;
   const long long gtid = (long long)blockIdx.x * kFT + tid;
   const long long gthreads = (long long)G * kFT;
-  const int gwarp = blockIdx.x * kFW + warp, gwarps = G * kFW;
+  const int gwarps = G * kFW;
+  // the same index sets dealt CTA by CTA (thread tid of every CTA before
+  // thread tid + 1): short FP64 loops (draws, the move, the rows of E) then
+  // spread over all SMs instead of filling the first CTAs
+  const long long sgtid = (long long)tid * G + blockIdx.x;
+  const int sgwarp = warp * G + blockIdx.x;
   // rows of this CTA in phases B and C
   const int R = (m + G - 1) / G;
   const int r0 = min(m, blockIdx.x * R), r1 = min(m, r0 + R);
@@ -86,7 +91,7 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
     const int c = (int)(k / d), j = (int)(k % d);
     a.X[0][(size_t)c * d + j] = a.X_user[(size_t)c * d + j];
   }
-  for (long long k = gtid; k < (long long)C * nblk; k += gthreads) {
+  for (long long k = sgtid; k < (long long)C * nblk; k += gthreads) {
     const int c = (int)(k / nblk), n = (int)(k % nblk);
     uint32_t r[4];
     rng_block(a.seed, (uint32_t)n, (uint32_t)c, (uint32_t)a.t0, 0u, 0u, r);
@@ -446,13 +451,13 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
       // cos and sin of each chain's theta: this CTA's own (d_all) or chain c's CTA's
       auto cth = [&](int c) { return d_all ? s_cs[c] : a.cth[c]; };
       auto sth = [&](int c) { return d_all ? s_sn[c] : a.sth[c]; };
-      for (long long k = gtid; k < (long long)C * d; k += gthreads) {
+      for (long long k = sgtid; k < (long long)C * d; k += gthreads) {
         const int c = (int)(k / d), j = (int)(k % d);
         const size_t o = (size_t)c * d + j;
         const int xbc = xbuf(c);
         a.X[xbc ^ 1][o] = move_d(a.X[xbc][o], NU[o], cth(c), sth(c));
       }
-      for (int i = gwarp; i < m; i += gwarps) {
+      for (int i = sgwarp; i < m; i += gwarps) {
         const double slack = a.b[i] - a.margin * a.anorm[i];
         bool flag = false;
         if (lane < C) {
@@ -484,7 +489,7 @@ __global__ void __launch_bounds__(kFT, 1) few_chains_kernel(FewArgs a) {
         }
       }
       if (t + 1 < a.t0 + a.n_iter) {
-        for (long long k = gtid; k < (long long)C * nblk; k += gthreads) {
+        for (long long k = sgtid; k < (long long)C * nblk; k += gthreads) {
           const int c = (int)(k / nblk), n = (int)(k % nblk);
           uint32_t r[4];
           rng_block(a.seed, (uint32_t)n, (uint32_t)c, (uint32_t)(t + 1), 0u, 0u, r);
