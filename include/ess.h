@@ -122,10 +122,12 @@ typedef struct {
                                    ESS_PRODUCTS_DFMA (ignored by the mixed
                                    form) */
     int wait_limit_us;          /* bounded device waits of the persistent
-                                   few-chain kernel (ess_run_few): a grid
-                                   barrier gives up after this many
-                                   microseconds and the call returns
-                                   ESS_ERR_TIMEOUT; 0 (default): 2 s */
+                                   kernels (ess_run_few's grid barriers; the
+                                   batched persistent launch's q dependency
+                                   counters and grid barriers): a wait gives
+                                   up after this many microseconds and the
+                                   call returns ESS_ERR_TIMEOUT; 0 (default):
+                                   2 s */
     int reserved[4];
 } ess_config;
 
@@ -410,9 +412,10 @@ ess_status ess_step_noalloc(const double *A, const double *b, int d, int m, cons
  * App. B roots, Alg. 3, the Sec. 3.3 rejection), laid out for few chains:
  * all SMs stream the rows of A once per step for q = A nu of every chain
  * and take the exact roots of every row, arcs are merged per angle bucket,
- * one CTA per chain sweeps the merged arcs (Alg. 3) and draws theta, grid
- * barriers separate the phases.  p = A x is recomputed at step t0 and whenever t % refresh_k
- * == 0.
+ * one CTA per chain sweeps the merged arcs (Alg. 3) and draws theta (with
+ * one chain every CTA does, so the move follows without a grid barrier),
+ * grid barriers separate the other phases.  p = A x is recomputed at step
+ * t0 and whenever t % refresh_k == 0.
  *   X          device, n_chains x d doubles: start points in, final states
  *              out.
  *   samples    device or NULL; with record_every > 0, n_chains x
@@ -422,7 +425,7 @@ ess_status ess_step_noalloc(const double *A, const double *b, int d, int m, cons
  * ESS_ERR_ARG for n_chains outside 1..16, ESS_ERR_INFEASIBLE_X0 for a start
  * point outside the polytope (checked in FP64 at step t0; X unchanged),
  * ESS_ERR_NUMERIC if NaN/Inf appeared (that chain stays), ESS_ERR_TIMEOUT if
- * a grid barrier waited more than 2 s.
+ * a grid barrier waited longer than cfg.wait_limit_us (default 2 s).
  */
 ess_status ess_run_few(ess_state *state, double *X, int n_chains, int t0, int n_iter,
                        uint64_t seed, double *samples, int record_every, void *cuda_stream);
