@@ -200,3 +200,42 @@ def test_selftest_refused_without_the_persistent_launch():
         assert ei.value.status == ess.ESS_ERR_UNSUPPORTED
     finally:
         bs_.close()
+
+
+def test_persistent_samples_follow_the_truncated_normal():
+    """The persistent launch samples the target: a d = 1 interval [-0.5, 1.2]
+    and a d = 2 box [-1, 3] x [-0.5, 1.2] (4096 chains each from 0) batched
+    with an ordinary polytope, 64 steps at refresh_k = 16 (the last 48 in
+    three persistent launches).  Each final state is one draw; KS tests
+    against the exact truncated normals, and their means and variances
+    (closed forms from scipy), hold within Monte Carlo error."""
+    from scipy import stats
+
+    rng = np.random.default_rng(41)
+    A0, b0, X0 = feasible_instance(rng, 17, 60, 70, scale=1.0 / math.sqrt(17), slack=(0.1, 1.0))
+    As = [np.array([[1.0], [-1.0]]), np.array([[1.0, 0.0], [-1.0, 0.0], [0.0, 1.0], [0.0, -1.0]]),
+          A0]
+    bs = [np.array([1.2, 0.5]), np.array([3.0, 1.0, 1.2, 0.5]), b0]
+    n = 4096
+    Xs = [np.zeros((n, 1)), np.zeros((n, 2)), X0]
+    nc = [n, n, X0.shape[0]]
+    bs_ = ess.BatchSampler(As, bs, precision=ess.ESS_PREC_MIXED, refresh_k=16)
+    try:
+        ess.ess_batch_set_persistent(bs_.batch, True)
+        X = bs_.pack(Xs)
+        bs_.run(nc, X, 64, seed=5, t0=0)
+        assert ess.ess_batch_info(bs_.batch)["graph_launches"] == 3
+        parts = bs_.unpack(host(X), nc)
+        st = bs_.stats()
+    finally:
+        bs_.close()
+    assert st["numeric_errors"] == 0
+    checks = [(parts[0][:, 0], stats.truncnorm(-0.5, 1.2)),
+              (parts[1][:, 0], stats.truncnorm(-1.0, 3.0)),
+              (parts[1][:, 1], stats.truncnorm(-0.5, 1.2))]
+    for x, law in checks:
+        assert stats.kstest(x, law.cdf).pvalue > 1e-3
+        assert abs(x.mean() - law.mean()) < 5 * math.sqrt(law.var() / n)
+        assert abs(x.var() - law.var()) < 0.1 * law.var()
+    assert abs(np.corrcoef(parts[1][:, 0], parts[1][:, 1])[0, 1]) < 5 / math.sqrt(n)
+    assert (parts[2] @ A0.T - b0[None, :]).max() <= 0.0
