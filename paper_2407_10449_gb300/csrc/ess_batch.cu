@@ -273,7 +273,7 @@ ess_status prepare(ess_batch* s, const int* nc_in) {
       cd.long_arcs = s->long_arcs[p];
       desc.push_back(cd);
     }
-    const int ct = ess::batch_ctile(nc[p]), rt = ess::batch_rtile(ct);
+    const int ct = ess::batch_ctile(nc[p], m), rt = ess::batch_rtile(ct);
     for (int c0 = 0; c0 < nc[p]; c0 += ct)
       for (int r0 = 0; r0 < m; r0 += rt) {
         BatchItem it{};

@@ -345,10 +345,26 @@ struct BatchItem {
   int c_first;         // index of the first chain in the whole batch
   int pad_;
 };
-// Chain tile of a problem with n chains (16, 32 or 64; larger counts are cut
-// into tiles of 64), and the matching row tile.
-inline int batch_ctile(int n) { return n <= 16 ? 16 : n <= 32 ? 32 : 64; }
+// Chain tile of a problem with n chains and m rows: the one of 16, 32 or 64
+// chains (row tile 4096 / chain tile) whose items cover the fewest (row,
+// chain) slots, ceil(m / rt) ceil(n / ct) rt ct; on a tie the smallest chain
+// tile that holds n.  Every output is summed over k in the same order
+// whatever the tile, so the choice changes no result.
 inline int batch_rtile(int ctile) { return 4096 / ctile; }
+inline int batch_ctile(int n, int m) {
+  const int pref = n <= 16 ? 16 : n <= 32 ? 32 : 64;
+  long long best = -1;
+  int pick = pref;
+  for (int ct : {pref, 16, 32, 64}) {
+    const int rt = batch_rtile(ct);
+    const long long slots = (long long)((m + rt - 1) / rt) * ((n + ct - 1) / ct) * rt * ct;
+    if (best < 0 || slots < best) {
+      best = slots;
+      pick = ct;
+    }
+  }
+  return pick;
+}
 
 // nu for every chain of the batch (T = float: float Box-Muller, T = double:
 // 53-bit), written at desc[c].x_off; the step index is t (+ *t_dev if set).
