@@ -232,6 +232,10 @@ batch_gemm_kernel(const BatchItem* __restrict__ items, int n_items, int* queue,
     const int warp = tid >> 5, lane = tid & 31;
     const int tx = (warp % wpr) * 8 + (lane & 7);
     const int ty = (warp / wpr) * 4 + (lane >> 3);
+    // a warp whose 32 rows or 16 chains all lie past the item's edge stores
+    // nothing: it skips the arithmetic (the FP32 and FP64 pipes charge a warp
+    // instruction whatever its lanes hold) but still stages and syncs
+    const bool warp_live = (warp % wpr) * 32 < I.rows && (warp / wpr) * 16 < I.chains;
     T hi[4][4], lo[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -311,7 +315,8 @@ batch_gemm_kernel(const BatchItem* __restrict__ items, int n_items, int* queue,
             for (int j = 0; j < 4; ++j) hi[i][j] = fma(xv[i], (T)av[j], hi[i][j]);
         }
       };
-      if (kn == kBK) {
+      if (!warp_live) {
+      } else if (kn == kBK) {
 #pragma unroll
         for (int kk = 0; kk < kBK; ++kk) kstep(kk);
       } else {
